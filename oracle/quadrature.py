@@ -1,0 +1,85 @@
+"""Quadrature on triangles and tetrahedra (oracle).
+
+Integration rules used to evaluate the exact polynomial integrals of the
+method: collapsed (Duffy) tensor products of Gauss-Legendre points.  With n
+points per direction the triangle rule integrates polynomials of total
+degree <= 2n - 2 exactly and the tetrahedron rule degree <= 2n - 3.
+
+The *load* rules (how f and g_D enter the right-hand side; the paper leaves
+quadrature of data open, Sec. 4.3 remark on b_h and f_h) are fixed
+conventions of this project, implemented here from their published
+definitions and independently in the CUDA library:
+
+* cell load rule for a P0 pressure: one point at the cell barycentre with
+  weight |P| (the midpoint rule, exact for linear f);
+* boundary-face rule: the face is fanned into triangles (x_f, v_i, v_{i+1})
+  and each triangle gets the 6-point degree-4 rule of D.A. Dunavant,
+  "High degree efficient symmetrical Gaussian quadrature rules for the
+  triangle", IJNME 21 (1985), Table for p = 4.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+from numpy.polynomial.legendre import leggauss
+
+
+def gauss01(n: int):
+    x, w = leggauss(n)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def triangle_rule(A, B, C, n: int = 5):
+    """Points (N,3) and weights (N,) on triangle ABC, |weights| summing to the area."""
+    s, ws = gauss01(n)
+    S, T = np.meshgrid(s, s, indexing="ij")
+    WS, WT = np.meshgrid(ws, ws, indexing="ij")
+    xi = S.ravel()
+    eta = (T * (1.0 - S)).ravel()
+    w = (WS * WT * (1.0 - S)).ravel()
+    A = np.asarray(A, float)
+    B = np.asarray(B, float)
+    C = np.asarray(C, float)
+    area2 = np.linalg.norm(np.cross(B - A, C - A))
+    pts = A[None, :] + xi[:, None] * (B - A)[None, :] + eta[:, None] * (C - A)[None, :]
+    return pts, w * area2
+
+
+def tet_rule(A, B, C, D, n: int = 5):
+    """Points and *signed* weights on tetrahedron ABCD (sign of det[B-A, C-A, D-A])."""
+    s, ws = gauss01(n)
+    S, T, R = np.meshgrid(s, s, s, indexing="ij")
+    WS, WT, WR = np.meshgrid(ws, ws, ws, indexing="ij")
+    xi = S.ravel()
+    eta = (T * (1.0 - S)).ravel()
+    zeta = (R * (1.0 - S) * (1.0 - T)).ravel()
+    w = (WS * WT * WR * (1.0 - S) ** 2 * (1.0 - T)).ravel()
+    A = np.asarray(A, float)
+    J = np.stack([np.asarray(B, float) - A, np.asarray(C, float) - A, np.asarray(D, float) - A], 1)
+    det = np.linalg.det(J)
+    pts = A[None, :] + np.stack([xi, eta, zeta], 1) @ J.T
+    return pts, w * det
+
+
+# Dunavant (1985) degree-4 rule, 6 points, barycentric (a, a, 1-2a) orbits;
+# weights are fractions of the triangle area.
+_DUN4_A = (0.445948490915965, 0.091576213509771)
+_DUN4_W = (0.223381589678011, 0.109951743655322)
+
+
+def dunavant4(A, B, C):
+    """Dunavant degree-4 6-point rule on triangle ABC (points, area-weights)."""
+    A = np.asarray(A, float)
+    B = np.asarray(B, float)
+    C = np.asarray(C, float)
+    area = 0.5 * np.linalg.norm(np.cross(B - A, C - A))
+    bary = []
+    wts = []
+    for a, w in zip(_DUN4_A, _DUN4_W):
+        b = 1.0 - 2.0 * a
+        for l in ((a, a, b), (a, b, a), (b, a, a)):
+            bary.append(l)
+            wts.append(w)
+    bary = np.array(bary)
+    pts = bary[:, 0:1] * A + bary[:, 1:2] * B + bary[:, 2:3] * C
+    return pts, np.array(wts) * area

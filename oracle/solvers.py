@@ -1,0 +1,228 @@
+"""Solvers for the saddle-point system (oracle).
+
+Paper Sec. 5: the system matrix [A B^T; B -C] (here C = 0, A = M) is solved
+by GMRES with a block preconditioner.  Block-Schur (eq. block_schur):
+B_1 = diag(A), B_2^{-1} = exact solve with S = B diag(A)^{-1} B^T (the sign of
+the paper's S = -C - B diag(A)^{-1} B^T is absorbed by solving for p~ = -p).
+This module also holds the two variants the project adds around it: the
+same block-diagonal preconditioner inside MINRES (it is SPD, so MINRES
+applies), and the block upper-triangular form
+    P = [diag(M)  B^T; 0  -S],   P^{-1} r: z_p = -S^{-1} r_p,
+                                           z_u = diag(M)^{-1}(r_u - B^T z_p).
+
+Krylov methods, written from their textbook statements:
+* preconditioned MINRES: C.C. Paige & M.A. Saunders, SIAM J. Numer. Anal.
+  12 (1975); the preconditioned Lanczos form of H. Elman, D. Silvester,
+  A. Wathen, "Finite Elements and Fast Iterative Solvers" (2005), Alg. 4.1;
+* FGMRES(m): Y. Saad, SIAM J. Sci. Comput. 14 (1993) -- right
+  preconditioning, modified Gram-Schmidt Arnoldi, Givens rotations;
+* Jacobi-preconditioned CG for S: Hestenes & Stiefel (1952).
+All stop on the TRUE relative residual ||b - A x||_2 / ||b||_2.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+@dataclass
+class Result:
+    x: np.ndarray
+    iters: int
+    relres: float
+    converged: bool
+    inner_iters: int = 0
+
+
+def solve_direct(sys):
+    """Direct sparse solve; returns (u, p) with the physical pressure sign."""
+    x = spla.spsolve(sys.saddle().tocsc(), sys.rhs())
+    return x[:sys.n_u], -x[sys.n_u:]
+
+
+def schur(sys) -> sp.csr_matrix:
+    """S = B diag(M)^{-1} B^T."""
+    dinv = 1.0 / sys.M.diagonal()
+    return (sys.B @ sp.diags(dinv) @ sys.B.T).tocsr()
+
+
+def pcg(S, b, rtol=1e-12, maxit=10000, x0=None):
+    """Jacobi-preconditioned CG on SPD S; stops on ||b - S x|| <= rtol ||b||."""
+    dinv = 1.0 / S.diagonal()
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - S @ x
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return Result(np.zeros_like(b), 0, 0.0, True)
+    z = dinv * r
+    p = z.copy()
+    rz = r @ z
+    for it in range(1, maxit + 1):
+        q = S @ p
+        alpha = rz / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        if np.linalg.norm(r) <= rtol * nb:
+            return Result(x, it, np.linalg.norm(b - S @ x) / nb, True)
+        z = dinv * r
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return Result(x, maxit, np.linalg.norm(b - S @ x) / nb, False)
+
+
+class BlockPreconditioner:
+    """Block-diagonal (kind='diag') or block upper-triangular (kind='tri')
+    preconditioner with diag(M) for the flux block and S = B diag(M)^{-1} B^T
+    for the pressure block.  inner='exact' factorises S (the paper's choice,
+    with MUMPS there and SuperLU here); inner='pcg' uses Jacobi-PCG to
+    inner_rtol."""
+
+    def __init__(self, sys, kind="diag", inner="exact", inner_rtol=1e-12, inner_maxit=10000):
+        self.n_u = sys.n_u
+        self.B = sys.B
+        self.dM = sys.M.diagonal().copy()
+        self.S = schur(sys)
+        self.kind = kind
+        self.inner = inner
+        self.inner_rtol = inner_rtol
+        self.inner_maxit = inner_maxit
+        self.inner_iters = 0
+        if inner == "exact":
+            self.lu = spla.splu(self.S.tocsc())
+
+    def solve_S(self, r):
+        if self.inner == "exact":
+            return self.lu.solve(r)
+        res = pcg(self.S, r, self.inner_rtol, self.inner_maxit)
+        self.inner_iters += res.iters
+        return res.x
+
+    def __call__(self, r):
+        ru, rp = r[:self.n_u], r[self.n_u:]
+        if self.kind == "diag":
+            return np.concatenate([ru / self.dM, self.solve_S(rp)])
+        zp = -self.solve_S(rp)
+        zu = (ru - self.B.T @ zp) / self.dM
+        return np.concatenate([zu, zp])
+
+
+def minres(A, b, Pinv, rtol=1e-12, maxit=5000):
+    """Preconditioned MINRES for symmetric A with SPD preconditioner Pinv."""
+    n = b.size
+    nb = np.linalg.norm(b)
+    x = np.zeros(n)
+    if nb == 0.0:
+        return Result(x, 0, 0.0, True)
+    v_old = np.zeros(n)
+    v = b.copy()
+    z = Pinv(v)
+    gamma = np.sqrt(v @ z)
+    gamma_old = 1.0
+    eta = gamma
+    c_old, c = 1.0, 1.0
+    s_old, s = 0.0, 0.0
+    w_old = np.zeros(n)
+    w = np.zeros(n)
+    for it in range(1, maxit + 1):
+        z = z / gamma
+        Az = A @ z
+        delta = Az @ z
+        v_new = Az - (delta / gamma) * v - (gamma / gamma_old) * v_old
+        z_new = Pinv(v_new)
+        gamma_new = np.sqrt(max(v_new @ z_new, 0.0))
+        a0 = c * delta - c_old * s * gamma
+        a1 = np.hypot(a0, gamma_new)
+        a2 = s * delta + c_old * c * gamma
+        a3 = s_old * gamma
+        c_new, s_new = a0 / a1, gamma_new / a1
+        w_new = (z - a3 * w_old - a2 * w) / a1
+        x = x + c_new * eta * w_new
+        eta = -s_new * eta
+        rel = np.linalg.norm(b - A @ x) / nb
+        if rel <= rtol:
+            return Result(x, it, rel, True)
+        if gamma_new == 0.0:
+            return Result(x, it, rel, False)
+        v_old, v = v, v_new
+        z = z_new
+        gamma_old, gamma = gamma, gamma_new
+        c_old, c = c, c_new
+        s_old, s = s, s_new
+        w_old, w = w, w_new
+    return Result(x, maxit, np.linalg.norm(b - A @ x) / nb, False)
+
+
+def fgmres(A, b, Pinv, restart=30, rtol=1e-12, maxit=5000):
+    """Restarted flexible GMRES with right preconditioning, x0 = 0."""
+    n = b.size
+    nb = np.linalg.norm(b)
+    x = np.zeros(n)
+    if nb == 0.0:
+        return Result(x, 0, 0.0, True)
+    total = 0
+    while total < maxit:
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        if beta <= rtol * nb:
+            return Result(x, total, beta / nb, True)
+        m = restart
+        V = np.zeros((m + 1, n))
+        Z = np.zeros((m, n))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        gvec = np.zeros(m + 1)
+        gvec[0] = beta
+        V[0] = r / beta
+        j_done = 0
+        for j in range(m):
+            Z[j] = Pinv(V[j])
+            w = A @ Z[j]
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            gvec[j + 1] = -sn[j] * gvec[j]
+            gvec[j] = cs[j] * gvec[j]
+            total += 1
+            j_done = j + 1
+            if abs(gvec[j + 1]) <= rtol * nb or total >= maxit:
+                break
+        y = np.linalg.solve(np.triu(H[:j_done, :j_done]), gvec[:j_done])
+        x = x + Z[:j_done].T @ y
+        rel = np.linalg.norm(b - A @ x) / nb
+        if rel <= rtol:
+            return Result(x, total, rel, True)
+    return Result(x, total, np.linalg.norm(b - A @ x) / nb, False)
+
+
+def solve_krylov(sys, method="minres", kind="diag", inner="exact", rtol=1e-12,
+                 inner_rtol=1e-12, restart=30, maxit=5000):
+    """Preconditioned Krylov solve; returns (u, p, Result) with physical p."""
+    A = sys.saddle()
+    P = BlockPreconditioner(sys, kind=kind, inner=inner, inner_rtol=inner_rtol)
+    if method == "minres":
+        if kind != "diag":
+            raise ValueError("MINRES needs the SPD block-diagonal preconditioner")
+        res = minres(A, sys.rhs(), P, rtol=rtol, maxit=maxit)
+    elif method == "fgmres":
+        res = fgmres(A, sys.rhs(), P, restart=restart, rtol=rtol, maxit=maxit)
+    else:
+        raise ValueError(method)
+    res.inner_iters = P.inner_iters
+    return res.x[:sys.n_u], -res.x[sys.n_u:], res
