@@ -1,0 +1,327 @@
+"""Benchmark: time-to-solution and DOFs/s of the mixed-VEM saddle-point solve.
+
+Workload (default): unit cube, 128^3 hexahedra, the paper's k = 1 element
+(face P1 moments + 3 cross moments per cell, P0 pressure; 27,410,432
+unknowns), K = 1, p = sin(pi x) sin(pi y) sin(pi z) with Dirichlet data,
+FP64, FGMRES(30) with the block upper-triangular approximate-Schur
+preconditioner (S = B diag(M)^-1 B^T, Jacobi-PCG inner solve), stopped at a
+true relative residual of 1e-8.
+
+One step = the whole hot path on device-resident inputs: element-batched
+assembly of M_P, B_P and loads, scatter into the CSR saddle matrix, Schur
+build, and the Krylov solve.  value = unknowns / step time (DOFs/s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution (rel.res 1e-8) and DOFs/s"
+UNIT = "DOFs/s"
+WORKLOAD = "hex128-k1-fgmres30-blocktri-fp64"
+N_CELLS = 128
+RTOL = 1e-8
+SAMPLE_N = 10          # oracle sample: 10^3 cubes of the same workload
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_CELLS, help="cells per side (default 128)")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- oracle ---
+def oracle_sample(n: int = SAMPLE_N):
+    """Run the CPU oracle on one n^3 sample of the workload; returns
+    (unknowns, seconds, iterations)."""
+    from oracle import assemble, paper_element, solvers
+    from synth import fields, hex_mesh
+    m = hex_mesh(n)
+    prob = fields.sine_problem()
+    t0 = time.perf_counter()
+    sys_ = assemble(m, paper_element(1), np.ones(m.n_cells), f=prob.f, gD=prob.gD)
+    u, p, res = solvers.solve_krylov(sys_, "fgmres", "tri", "pcg", rtol=RTOL, inner_rtol=1e-4, restart=30)
+    dt = time.perf_counter() - t0
+    return sys_.n, dt, res.iters
+
+
+def cpu_baseline_subprocess():
+    """The oracle timed single-threaded in a fresh process (spawned, never forked
+    from the CUDA process)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"], env=env,
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["n"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"hex{SAMPLE_N}^3 k=1 ({d['n']} unknowns, same element/solver/tolerance), "
+                      f"assembly + FGMRES(30)/block-tri solve in {d['seconds']:.1f}s, {d['iters']} iterations"}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(a.warmup):
+        oracle_sample(SAMPLE_N)
+    times = []
+    n = 0
+    for _ in range(a.steps):
+        n, dt, it = oracle_sample(SAMPLE_N)
+        times.append(dt)
+    tot = sum(times)
+    value = n * a.steps / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": f"hex{SAMPLE_N}^3 per step (oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"hex{SAMPLE_N}^3 k=1, {n} unknowns per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------- ours ---
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, dev=0):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def spmv_bytes(nnz, rows):
+    """Algorithmic bytes of one CSR SpMV: values + int32 columns + int64 row
+    pointers, x read once, y written once."""
+    return 12 * nnz + 8 * (rows + 1) + 16 * rows
+
+
+def run_ours(a):
+    import torch
+    from paper_1901_02330_gb300 import build as b
+    from paper_1901_02330_gb300 import vemsolve as vs
+    from synth import fields, hex_mesh
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    b.build()
+    stream = torch.cuda.current_stream()
+    sid = stream.cuda_stream
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+
+    # independent problems per rank (weak scaling): each rank solves its own copy
+    mesh = hex_mesh(a.n)
+    prob = fields.sine_problem()
+    opts = dict(element=vs.VEM_ELEMENT_K1, krylov=vs.VEM_KRYLOV_FGMRES, restart=30,
+                precond=vs.VEM_PREC_BLOCK_TRI, rtol=RTOL, inner_rtol=1e-4, inner_maxit=500, maxit=1000)
+
+    # ---------------- device-resident path (value) ----------------
+    s = vs.Solver(mesh, stream=sid, device_io=1, **opts)
+    s.set_coefficient(np.ones(mesh.n_cells))
+    s.set_data(prob.f, prob.gD)
+    n_u, n_p = s.sizes()
+    n = n_u + n_p
+    u = torch.empty(n_u, dtype=torch.float64, device="cuda")
+    p = torch.empty(n_p, dtype=torch.float64, device="cuda")
+
+    def step():
+        s.assemble()
+        return s.solve(u_out=u, p_out=p)[2]
+
+    for _ in range(a.warmup):
+        st = step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = Clocks(local)
+    l0 = vs.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = []
+    for _ in range(a.steps):
+        stats.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = vs.launch_count() - l0
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world / (ms * 1e-3)
+    st = stats[-1]
+
+    # ---------------- roofline of the saddle-matrix SpMV ----------------
+    x = torch.randn(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        s.apply_device(x, y)
+    reps = 10
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        s.apply_device(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = e0.elapsed_time(e1) / reps
+    sb = spmv_bytes(st["nnz_A"], n)
+    spmv_gbs = sb / (spmv_ms * 1e-3) / 1e9
+    s.close()
+    del x, y
+
+    # ---------------- end-to-end through the public API (e2e) ----------------
+    def pin(arr):
+        t = torch.from_numpy(np.ascontiguousarray(arr)).pin_memory()
+        return t.numpy()
+
+    pm = type(mesh)(pin(mesh.xyz), pin(mesh.face_vtx_ptr), pin(mesh.face_vtx), pin(mesh.cell_face_ptr),
+                    pin(mesh.cell_face), pin(mesh.face_bc))
+    Kh = pin(np.ones(mesh.n_cells))
+    # data at the library's quadrature points (evaluated once: they depend only on the mesh)
+    s2 = vs.Solver(pm, stream=sid, **opts)
+    fq = pin(prob.f(s2.quadrature_points(vs.VEM_QP_CELL)))
+    pb = s2.quadrature_points(vs.VEM_QP_BFACE)
+    gq = pin(prob.gD(pb))
+    s2.close()
+    uh = pin(np.zeros(n_u))
+    ph = pin(np.zeros(n_p))
+    h2d = sum(x.nbytes for x in (pm.xyz, pm.face_vtx_ptr, pm.face_vtx, pm.cell_face_ptr, pm.cell_face,
+                                 pm.face_bc, Kh, fq, gq))
+    d2h = uh.nbytes + ph.nbytes
+    e2e_times = []
+    for i in range(max(2, min(a.steps, 3)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s3 = vs.Solver(pm, stream=sid, **opts)
+        s3.set_coefficient(Kh)
+        s3.set_source(fq, gq)
+        s3.solve(u_out=uh, p_out=ph)
+        s3.close()
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_value = n * world / statistics.median(e2e_times)
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not a.no_cpu_baseline:
+        cpu = cpu_baseline_subprocess()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": a.n ** 3, "unknowns": n, "n_u": n_u, "n_p": n_p,
+                   "element": "paper k=1 (face P1 + 3 cross moments, P0 pressure)",
+                   "krylov": "FGMRES(30)", "precond": "block upper-triangular, S = B diag(M)^-1 B^T",
+                   "inner": "Jacobi-PCG rtol 1e-4", "rtol": RTOL, "K": "identity",
+                   "l2": "inputs larger than L2 (CSR of A ~%.1f GB streamed every step)" % (st["nnz_A"] * 12 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "iterations": st["iterations"], "inner_iterations": st["inner_iterations"], "relres": st["relres"],
+        "t_assemble_ms": st["t_assemble_ms"], "t_solve_ms": st["t_solve_ms"],
+        "roofline": {"kernel": "k_spmv (saddle matrix CSR, FP64)", "bound": "hbm", "achieved": spmv_gbs,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": spmv_gbs / hbm_peak, "traffic": None,
+                     "algorithmic_bytes": sb, "launch_ms": spmv_ms,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.cpu_sample:
+        n, dt, it = oracle_sample(SAMPLE_N)
+        print(json.dumps({"n": n, "seconds": dt, "iters": it}))
+        return 0
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

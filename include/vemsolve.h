@@ -1,0 +1,218 @@
+/*
+ * vemsolve.h -- C-ABI of the GB300 (sm_103a) mixed virtual element solver.
+ *
+ * The library discretises  -div(K grad p) = f  in mixed form (flux u and
+ * pressure p) on polyhedral meshes of a domain with the mixed virtual
+ * element method of Dassi & Scacchi (arXiv:1901.02330) and solves the
+ * resulting saddle-point system with a block-preconditioned Krylov method:
+ *
+ *   model problem  ...................... Sec. 3, eq. mod_prob_eq, bilin_form
+ *   local velocity space and DOFs ....... Sec. 4.1, eq. vectSpaceDef,
+ *                                         facePoly, gradMom, crossMom
+ *   pressure space and DOFs ............. Sec. 4.2, eq. presSpace, presMom
+ *   local forms, stabilisation .......... Sec. 4.3 (a_{h,P}, b_{h,P}, f_{h,P}, s_P)
+ *   discrete problem .................... Sec. 4.3, eq. mod_prob_eqDisc
+ *   block preconditioners, Krylov ....... Sec. 5, eq. B_D, block_schur
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All functions return a vem_status; none aborts.  On failure the
+ *    handle keeps a message (vem_last_error) and output buffers are left
+ *    untouched.  Passing NULL where a pointer is required, or sizes that
+ *    disagree with the mesh, gives VEM_ERR_BAD_INPUT.
+ *  - Unless stated otherwise pointers are HOST pointers and the library
+ *    copies what it needs before returning; the caller keeps ownership.
+ *    The library owns all device memory it allocates and frees it in
+ *    vem_destroy.
+ *  - Work is issued on the CUDA stream given to vem_create (NULL = the
+ *    legacy default stream).  Calls that return data to the host
+ *    synchronise that stream.
+ *  - Global unknown layout (the layout of u_out / p_out):
+ *      face DOF (f, beta)       -> nfd * f + beta
+ *      interior DOF l of cell c -> nfd * n_faces + nid * c + l
+ *      pressure of cell c       -> c
+ *    E0:  nfd = 1, nid = 0.  The face DOF is the mean normal flux
+ *         (1/|f|) int_f u.n_f along the face's global normal.
+ *    K1 (the paper's k = 1): nfd = 3, nid = 3.  Face DOFs are the moments
+ *         (1/|f|) int_f (u.n_f) m^f_beta, beta = (0,0), (1,0), (0,1), with
+ *         m^f_(1,0) = (x - x_f).t1 / h_f, m^f_(0,1) = (x - x_f).t2 / h_f,
+ *         n_f the face's global normal (right-hand rule on its vertex
+ *         loop), t1 = (v1 - v0)/|v1 - v0| from its first two vertices and
+ *         t2 = n_f x t1.  Interior DOFs are the cross moments
+ *         (1/|P|) int_P u.(m_I ^ e_q), q = x, y, z, m_I = (x - x_P)/h_P.
+ *    The pressure unknown is the cell mean (the P0 moment of eq. presMom)
+ *    with the physical sign.
+ */
+#ifndef VEMSOLVE_H
+#define VEMSOLVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vem_handle vem_handle;   /* opaque */
+
+typedef enum {
+  VEM_OK = 0,
+  VEM_ERR_BAD_INPUT = 1,        /* NULL pointer, size mismatch, K <= 0, bad option */
+  VEM_ERR_DEGENERATE_MESH = 2,  /* zero-area face, zero-volume or non-convex cell */
+  VEM_ERR_NOT_CONVERGED = 3,    /* iteration cap reached; outputs hold the last iterate */
+  VEM_ERR_BREAKDOWN = 4,        /* Krylov breakdown (non-positive curvature, zero norm) */
+  VEM_ERR_NONFINITE = 5,        /* NaN / Inf met in data or in a reduction */
+  VEM_ERR_OOM = 6,              /* device allocation failed */
+  VEM_ERR_CUDA = 7,             /* any other CUDA runtime error */
+  VEM_ERR_UNSUPPORTED = 8       /* option combination not built */
+} vem_status;
+
+/* Mesh (Sec. 4: a polyhedral decomposition Omega_h).  Faces are planar
+ * polygons given by vertex loops; cells list their faces.  A face belongs
+ * to one cell (boundary) or two (interior).  Cells must be convex (every
+ * face plane separates the cell's barycentre from the outside).
+ * face_bc: 0 interior, 1 Dirichlet pressure (g_D enters the right-hand
+ * side as -int_f g_D v.n).  Flag 2 (prescribed flux) is reserved. */
+typedef struct {
+  int64_t n_vertices;
+  const double *xyz;              /* [n_vertices][3] */
+  int64_t n_faces;
+  const int64_t *face_vtx_ptr;    /* [n_faces + 1], face_vtx_ptr[0] = 0 */
+  const int32_t *face_vtx;        /* [face_vtx_ptr[n_faces]] vertex ids, >= 3 per face */
+  int64_t n_cells;
+  const int64_t *cell_face_ptr;   /* [n_cells + 1] */
+  const int32_t *cell_face;       /* [cell_face_ptr[n_cells]] face ids, >= 4 per cell */
+  const int8_t *face_bc;          /* [n_faces] */
+} vem_mesh;
+
+enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1 };
+enum { VEM_KRYLOV_MINRES = 0, VEM_KRYLOV_FGMRES = 1 };
+enum { VEM_PREC_BLOCK_DIAG = 0, VEM_PREC_BLOCK_TRI = 1 };
+enum { VEM_INNER_PCG = 0 };
+enum { VEM_PRECISION_FP64 = 0 };
+
+typedef struct {
+  int element;        /* VEM_ELEMENT_*                                      */
+  int krylov;         /* VEM_KRYLOV_*; MINRES needs VEM_PREC_BLOCK_DIAG     */
+  int restart;        /* FGMRES restart length m (1..256)                   */
+  double rtol;        /* stop when ||b - A x||_2 <= rtol ||b||_2 (true residual) */
+  int maxit;          /* outer iteration cap                                */
+  int precond;        /* VEM_PREC_*                                         */
+  int inner;          /* VEM_INNER_* : solver for S = B diag(M)^-1 B^T      */
+  double inner_rtol;  /* inner relative residual target                     */
+  int inner_maxit;    /* inner iteration cap per application                */
+  int precision;      /* VEM_PRECISION_*                                    */
+  int device_io;      /* 0: vem_solve's x0/u_out/p_out are host pointers;   */
+                      /* 1: device pointers (e.g. torch tensors' data_ptr)  */
+} vem_options;
+
+typedef struct {
+  int32_t iterations;        /* outer Krylov iterations                     */
+  int32_t inner_iterations;  /* total inner (Schur) iterations              */
+  double relres;             /* true final ||b - A x|| / ||b||               */
+  double t_assemble_ms;      /* element kernel + scatter + Schur build      */
+  double t_solve_ms;         /* Krylov solve                                */
+  int64_t n_u, n_p;          /* unknown counts                              */
+  int64_t nnz_A, nnz_S;      /* stored nonzeros of [M B^T; B 0] and of S    */
+} vem_stats;
+
+/* Fill *opt with the defaults: E0, FGMRES(30), block-diagonal, Jacobi-PCG
+ * inner solve to 1e-12 (at most 2000 iterations), rtol 1e-12, maxit 2000,
+ * FP64, host I/O. */
+vem_status vem_default_options(vem_options *opt);
+
+/* Create a solver for a mesh: copies the mesh to the device, computes the
+ * face and cell geometry (Sec. 2: barycentres, diameters, face frames) and
+ * the DOF layout.  cuda_stream: a cudaStream_t (may be NULL).  On success
+ * *out receives the handle; on failure *out is NULL. */
+vem_status vem_create(const vem_mesh *mesh, const vem_options *opt, void *cuda_stream,
+                      vem_handle **out);
+
+/* Replace the options (element changes invalidate the assembly). */
+vem_status vem_set_options(vem_handle *h, const vem_options *opt);
+
+/* Unknown counts for the current element. */
+vem_status vem_sizes(const vem_handle *h, int64_t *n_u, int64_t *n_p);
+
+/* Quadrature points at which the caller evaluates the data (the paper leaves
+ * the quadrature of b_h and f_h open, Sec. 4.3 remark):
+ *   which = VEM_QP_CELL : one point per cell, its barycentre x_P; the load is
+ *                         F_P = |P| f(x_P)  (n = n_cells);
+ *   which = VEM_QP_BFACE: for every face with face_bc == 1, in face order,
+ *                         its fan triangles (x_f, v_i, v_{i+1}) each with
+ *                         the 6-point degree-4 rule of Dunavant (1985)
+ *                         (n = 6 * sum of those faces' vertex counts).
+ * vem_quadrature_count gives n; vem_quadrature_points writes [n][3]
+ * coordinates to the host buffer xyz_out. */
+enum { VEM_QP_CELL = 0, VEM_QP_BFACE = 1 };
+vem_status vem_quadrature_count(const vem_handle *h, int which, int64_t *n);
+vem_status vem_quadrature_points(vem_handle *h, int which, double *xyz_out);
+
+/* Per-cell permeability K > 0 (nu = 1/K in a_h, eq. bilin_form); host array
+ * [n_cells].  Invalidates the assembly. */
+vem_status vem_set_coefficient(vem_handle *h, const double *K_cell);
+
+/* Data at the quadrature points: f at VEM_QP_CELL points, g_D at VEM_QP_BFACE
+ * points (host arrays; NULL means zero).  Invalidates the right-hand side. */
+vem_status vem_set_source(vem_handle *h, const double *f_qp, const double *gD_qp);
+
+/* Same as vem_set_coefficient / vem_set_source with DEVICE arrays. */
+vem_status vem_set_coefficient_device(vem_handle *h, const double *K_cell_dev);
+vem_status vem_set_source_device(vem_handle *h, const double *f_qp_dev, const double *gD_qp_dev);
+
+/* Assemble: element-batched local matrices M_P, B_P and loads (Sec. 4.3),
+ * scatter into the global CSR matrix [M B^T; B 0], and build the Schur
+ * approximation S = B diag(M)^-1 B^T (Sec. 5, eq. block_schur). */
+vem_status vem_assemble(vem_handle *h);
+
+/* Solve [M B^T; B 0][u; -p] = [g; F] with the configured Krylov method and
+ * block preconditioner, from x0 = (u0, p0) (NULL: zero; layout u then p,
+ * physical pressure sign).  Assembles first if needed.  Writes u_out
+ * [n_u] and p_out [n_p] (host or device per options.device_io) and, if
+ * stats != NULL, the statistics.  Returns VEM_ERR_NOT_CONVERGED (outputs
+ * written) if rtol is not reached within maxit. */
+vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_out, vem_stats *stats);
+
+/* ---- inspection entry points (used by the parity tests) ---- */
+
+/* Geometry: face area, barycentre [3], unit normal [3], diameter per face;
+ * cell volume, barycentre [3], diameter per cell.  Host buffers, any may be
+ * NULL. */
+vem_status vem_get_geometry(vem_handle *h, double *face_area, double *face_centroid,
+                            double *face_normal, double *face_diam, double *cell_volume,
+                            double *cell_centroid, double *cell_diam);
+
+/* Local matrices after vem_assemble: for each cell, M_P (n_loc x n_loc,
+ * row-major) and B_P (n_loc) in the cell's local DOF order (its faces in
+ * cell_face order, nfd moments each, then nid interior DOFs), with
+ * n_loc = nfd * n_faces(cell) + nid.  vem_local_size gives the total
+ * lengths; M_offsets[n_cells + 1] receives the start of each cell's M_P in
+ * M_out (in doubles); B_P of cell c starts at nfd * cell_face_ptr[c] + nid * c
+ * in B_out.  Host buffers; any may be NULL. */
+vem_status vem_local_size(const vem_handle *h, int64_t *m_total, int64_t *b_total);
+vem_status vem_get_local(vem_handle *h, double *M_out, int64_t *M_offsets, double *B_out);
+
+/* The assembled system: CSR of [M B^T; B 0] with (n_u + n_p) rows, int64 row
+ * pointers, int32 columns, double values; rhs [n_u + n_p] = [g; F]. */
+vem_status vem_get_system(vem_handle *h, int64_t *row_ptr, int32_t *col, double *val, double *rhs);
+
+/* The Schur approximation S (n_p x n_p CSR) and diag(M) [n_u]. */
+vem_status vem_get_schur(vem_handle *h, int64_t *row_ptr, int32_t *col, double *val, double *diagM);
+
+/* y = [M B^T; B 0] x on the device (x, y device arrays of length n_u + n_p). */
+vem_status vem_apply_device(vem_handle *h, const double *x_dev, double *y_dev);
+
+/* Number of CUDA kernel launches the library has issued in this process
+ * (all handles), for accounting the work of a timed region. */
+vem_status vem_launch_count(int64_t *n);
+
+/* Message for the last failing call on this handle ("" if none). */
+const char *vem_last_error(const vem_handle *h);
+
+/* Free every device and host resource of the handle (NULL is a no-op). */
+void vem_destroy(vem_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VEMSOLVE_H */

@@ -1,0 +1,585 @@
+// C-ABI entry points of include/vemsolve.h: argument checking, device
+// memory, and the order of the assembly / solve phases.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "handle.cuh"
+
+namespace vem {
+
+vem_status fail(vem_handle *h, vem_status code, const char *fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    h->last_error = buf;
+  }
+  return code;
+}
+
+vem_status cuda_check(vem_handle *h, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return VEM_OK;
+  cudaGetLastError();   // clear a non-sticky error
+  if (e == cudaErrorMemoryAllocation)
+    return fail(h, VEM_ERR_OOM, "%s: out of device memory", what);
+  return fail(h, VEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+vem_status dalloc(vem_handle *h, void **p, size_t bytes) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(h, e == cudaErrorMemoryAllocation ? VEM_ERR_OOM : VEM_ERR_CUDA,
+                "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  h->allocations.push_back(*p);
+  return VEM_OK;
+}
+
+void dfree(vem_handle *h, void *p) {
+  if (!p) return;
+  auto it = std::find(h->allocations.begin(), h->allocations.end(), p);
+  if (it != h->allocations.end()) h->allocations.erase(it);
+  cudaFree(p);
+}
+
+vem_status check_device_errors(vem_handle *h, const char *what) {
+  VEM_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int e = *h->h_err;
+  if (e == 0) return VEM_OK;
+  VEM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+  if (e & DEVERR_ADJACENCY)
+    return fail(h, VEM_ERR_BAD_INPUT, "%s: a face is not shared by one or two cells as its flag says", what);
+  if (e & DEVERR_DEGENERATE_FACE) return fail(h, VEM_ERR_DEGENERATE_MESH, "%s: zero-area face", what);
+  if (e & DEVERR_DEGENERATE_CELL) return fail(h, VEM_ERR_DEGENERATE_MESH, "%s: zero-volume cell", what);
+  if (e & DEVERR_NONCONVEX) return fail(h, VEM_ERR_DEGENERATE_MESH, "%s: non-convex cell", what);
+  if (e & DEVERR_SINGULAR_LOCAL) return fail(h, VEM_ERR_DEGENERATE_MESH, "%s: singular local Gram matrix", what);
+  if (e & DEVERR_NONFINITE) return fail(h, VEM_ERR_NONFINITE, "%s: NaN or Inf in data", what);
+  return fail(h, VEM_ERR_CUDA, "%s: device error flags %d", what, e);
+}
+
+static vem_status check_options(vem_handle *h, const vem_options *o) {
+  if (o->element != VEM_ELEMENT_E0 && o->element != VEM_ELEMENT_K1)
+    return fail(h, VEM_ERR_BAD_INPUT, "unknown element %d", o->element);
+  if (o->krylov != VEM_KRYLOV_MINRES && o->krylov != VEM_KRYLOV_FGMRES)
+    return fail(h, VEM_ERR_BAD_INPUT, "unknown Krylov method %d", o->krylov);
+  if (o->precond != VEM_PREC_BLOCK_DIAG && o->precond != VEM_PREC_BLOCK_TRI)
+    return fail(h, VEM_ERR_BAD_INPUT, "unknown preconditioner %d", o->precond);
+  if (o->krylov == VEM_KRYLOV_MINRES && o->precond != VEM_PREC_BLOCK_DIAG)
+    return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs the SPD block-diagonal preconditioner");
+  if (o->inner != VEM_INNER_PCG) return fail(h, VEM_ERR_UNSUPPORTED, "inner solver %d", o->inner);
+  if (o->precision != VEM_PRECISION_FP64) return fail(h, VEM_ERR_UNSUPPORTED, "precision %d", o->precision);
+  if (o->restart < 1 || o->restart > 256) return fail(h, VEM_ERR_BAD_INPUT, "restart %d", o->restart);
+  if (!(o->rtol > 0.0) || !(o->inner_rtol > 0.0) || o->maxit < 1 || o->inner_maxit < 1)
+    return fail(h, VEM_ERR_BAD_INPUT, "tolerances and iteration caps must be positive");
+  return VEM_OK;
+}
+
+static void set_layout(vem_handle *h) {
+  if (h->opt.element == VEM_ELEMENT_K1) {
+    h->nfd = 3;
+    h->nid = 3;
+  } else {
+    h->nfd = 1;
+    h->nid = 0;
+  }
+  h->n_u = h->nfd * h->nf + h->nid * h->nc;
+  h->n_p = h->nc;
+  h->n = h->n_u + h->n_p;
+}
+
+template <class T>
+static vem_status upload(vem_handle *h, T **dst, const T *src, size_t n) {
+  VEM_TRY(dalloc_n(h, dst, n));
+  VEM_CUDA(h, cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  return VEM_OK;
+}
+
+static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
+  if (!m || !m->xyz || !m->face_vtx_ptr || !m->face_vtx || !m->cell_face_ptr || !m->cell_face || !m->face_bc)
+    return fail(h, VEM_ERR_BAD_INPUT, "mesh: NULL array");
+  if (m->n_vertices < 4 || m->n_faces < 4 || m->n_cells < 1)
+    return fail(h, VEM_ERR_BAD_INPUT, "mesh: too few vertices/faces/cells");
+  if (m->n_faces > INT32_MAX / 4 || m->n_cells > INT32_MAX / 4 || m->n_vertices > INT32_MAX)
+    return fail(h, VEM_ERR_UNSUPPORTED, "mesh too large for 32-bit indices");
+  h->nv = m->n_vertices;
+  h->nf = m->n_faces;
+  h->nc = m->n_cells;
+  h->h_fv_ptr.assign(m->face_vtx_ptr, m->face_vtx_ptr + h->nf + 1);
+  h->h_cf_ptr.assign(m->cell_face_ptr, m->cell_face_ptr + h->nc + 1);
+  h->h_fbc.assign(m->face_bc, m->face_bc + h->nf);
+  if (h->h_fv_ptr[0] != 0 || h->h_cf_ptr[0] != 0) return fail(h, VEM_ERR_BAD_INPUT, "mesh: pointers must start at 0");
+  for (int64_t f = 0; f < h->nf; ++f) {
+    const int64_t k = h->h_fv_ptr[f + 1] - h->h_fv_ptr[f];
+    if (k < 3 || k > 4096) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face %lld has %lld vertices", (long long)f, (long long)k);
+    h->max_nv_face = std::max<int>(h->max_nv_face, (int)k);
+    if (h->h_fbc[f] == 2) return fail(h, VEM_ERR_UNSUPPORTED, "prescribed-flux faces (flag 2)");
+    if (h->h_fbc[f] != 0 && h->h_fbc[f] != 1) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face flag %d", (int)h->h_fbc[f]);
+  }
+  for (int64_t c = 0; c < h->nc; ++c) {
+    const int64_t k = h->h_cf_ptr[c + 1] - h->h_cf_ptr[c];
+    if (k < 4 || k > 256) return fail(h, VEM_ERR_BAD_INPUT, "mesh: cell %lld has %lld faces", (long long)c, (long long)k);
+    h->max_nf_cell = std::max<int>(h->max_nf_cell, (int)k);
+  }
+  h->n_fv = h->h_fv_ptr[h->nf];
+  h->n_cf = h->h_cf_ptr[h->nc];
+  for (int64_t i = 0; i < h->n_fv; ++i)
+    if (m->face_vtx[i] < 0 || m->face_vtx[i] >= h->nv) return fail(h, VEM_ERR_BAD_INPUT, "mesh: vertex index out of range");
+  for (int64_t i = 0; i < h->n_cf; ++i)
+    if (m->cell_face[i] < 0 || m->cell_face[i] >= h->nf) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face index out of range");
+  for (int64_t i = 0; i < 3 * h->nv; ++i)
+    if (!std::isfinite(m->xyz[i])) return fail(h, VEM_ERR_NONFINITE, "mesh: non-finite coordinate");
+  set_layout(h);
+
+  VEM_CUDA(h, cudaMallocHost(&h->h_err, sizeof(int)));
+  VEM_CUDA(h, cudaMallocHost(&h->h_scal, 8192 * sizeof(double)));
+  VEM_TRY(upload(h, &h->xyz, m->xyz, 3 * (size_t)h->nv));
+  VEM_TRY(upload(h, &h->fv_ptr, m->face_vtx_ptr, (size_t)h->nf + 1));
+  VEM_TRY(upload(h, &h->fv, m->face_vtx, (size_t)h->n_fv));
+  VEM_TRY(upload(h, &h->cf_ptr, m->cell_face_ptr, (size_t)h->nc + 1));
+  VEM_TRY(upload(h, &h->cf, m->cell_face, (size_t)h->n_cf));
+  VEM_TRY(upload(h, &h->fbc, m->face_bc, (size_t)h->nf));
+  VEM_TRY(dalloc_n(h, &h->f_area, h->nf));
+  VEM_TRY(dalloc_n(h, &h->f_cent, 3 * h->nf));
+  VEM_TRY(dalloc_n(h, &h->f_norm, 3 * h->nf));
+  VEM_TRY(dalloc_n(h, &h->f_t1, 3 * h->nf));
+  VEM_TRY(dalloc_n(h, &h->f_diam, h->nf));
+  VEM_TRY(dalloc_n(h, &h->f_cell, 2 * h->nf));
+  VEM_TRY(dalloc_n(h, &h->f_loc, 2 * h->nf));
+  VEM_TRY(dalloc_n(h, &h->c_vol, h->nc));
+  VEM_TRY(dalloc_n(h, &h->c_cent, 3 * h->nc));
+  VEM_TRY(dalloc_n(h, &h->c_diam, h->nc));
+  VEM_TRY(dalloc_n(h, &h->cf_sigma, h->n_cf));
+  VEM_TRY(dalloc_n(h, &h->d_err, 1));
+  VEM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+  VEM_TRY(dalloc_n(h, &h->part, (size_t)kMaxSlots * kMaxBlocks));
+  VEM_TRY(dalloc_n(h, &h->scal, 8192));
+  VEM_CUDA(h, cudaMemsetAsync(h->scal, 0, 8192 * sizeof(double), h->stream));
+  // boundary-face quadrature offsets (6 points per fan triangle)
+  h->h_bqp_off.assign(h->nf + 1, 0);
+  for (int64_t f = 0; f < h->nf; ++f)
+    h->h_bqp_off[f + 1] = h->h_bqp_off[f] + (h->h_fbc[f] == 1 ? 6 * (h->h_fv_ptr[f + 1] - h->h_fv_ptr[f]) : 0);
+  h->n_bqp = h->h_bqp_off[h->nf];
+  VEM_TRY(upload(h, &h->bqp_off, h->h_bqp_off.data(), (size_t)h->nf + 1));
+  VEM_TRY(dalloc_n(h, &h->bqp_xyz, 3 * (size_t)std::max<int64_t>(h->n_bqp, 1)));
+  // coefficient nu = 1/K, default K = 1
+  VEM_TRY(dalloc_n(h, &h->nu, h->nc));
+  {
+    std::vector<double> ones(h->nc, 1.0);
+    VEM_CUDA(h, cudaMemcpyAsync(h->nu, ones.data(), sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->stream));
+    VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  h->have_coef = true;
+  VEM_TRY(dalloc_n(h, &h->f_qp, h->nc));
+  VEM_TRY(dalloc_n(h, &h->gD_qp, std::max<int64_t>(h->n_bqp, 1)));
+  VEM_CUDA(h, cudaMemsetAsync(h->f_qp, 0, sizeof(double) * h->nc, h->stream));
+  VEM_CUDA(h, cudaMemsetAsync(h->gD_qp, 0, sizeof(double) * std::max<int64_t>(h->n_bqp, 1), h->stream));
+  VEM_CUDA(h, cudaEventCreate(&h->ev0));
+  VEM_CUDA(h, cudaEventCreate(&h->ev1));
+  return geometry_build(h);
+}
+
+static vem_status alloc_local(vem_handle *h) {
+  std::vector<int64_t> off(h->nc + 1, 0);
+  for (int64_t c = 0; c < h->nc; ++c) {
+    const int64_t k = h->h_cf_ptr[c + 1] - h->h_cf_ptr[c];
+    const int64_t nl = h->nfd * k + h->nid;
+    off[c + 1] = off[c] + nl * nl;
+  }
+  const int64_t mt = off[h->nc];
+  const int64_t bt = h->nfd * h->n_cf + h->nid * h->nc;
+  if (h->m_total != mt || !h->Mloc) {
+    dfree(h, h->Mloc);
+    h->Mloc = nullptr;
+    VEM_TRY(dalloc_n(h, &h->Mloc, (size_t)mt));
+    h->m_total = mt;
+  }
+  if (h->b_total != bt || !h->Bloc) {
+    dfree(h, h->Bloc);
+    h->Bloc = nullptr;
+    VEM_TRY(dalloc_n(h, &h->Bloc, (size_t)bt));
+    h->b_total = bt;
+  }
+  if (!h->m_off) VEM_TRY(dalloc_n(h, &h->m_off, (size_t)h->nc + 1));
+  VEM_CUDA(h, cudaMemcpyAsync(h->m_off, off.data(), sizeof(int64_t) * (h->nc + 1), cudaMemcpyHostToDevice, h->stream));
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return VEM_OK;
+}
+
+static vem_status ensure_rhs(vem_handle *h) {
+  if (!h->rhs) VEM_TRY(dalloc_n(h, &h->rhs, (size_t)h->n));
+  if (!h->rhs_ready) VEM_TRY(assemble_rhs(h));
+  return VEM_OK;
+}
+
+static vem_status assemble_impl(vem_handle *h) {
+  VEM_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  VEM_TRY(alloc_local(h));
+  VEM_TRY(assemble_local(h));
+  VEM_TRY(assemble_global(h));
+  h->rhs_ready = false;
+  VEM_TRY(ensure_rhs(h));
+  VEM_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  VEM_CUDA(h, cudaEventSynchronize(h->ev1));
+  float ms = 0.f;
+  VEM_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  h->t_assemble_ms = ms;
+  h->assembled = true;
+  return VEM_OK;
+}
+
+__global__ void k_invert_check(int64_t n, const double *K, double *nu, int *err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double k = K[i];
+    if (!(k > 0.0) || !isfinite(k)) atomicOr(err, DEVERR_NONFINITE);
+    nu[i] = 1.0 / k;
+  }
+}
+
+__global__ void k_export_x(int64_t nu, int64_t np, const double *x, double *u, double *p) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu + np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < nu) {
+      if (u) u[i] = x[i];
+    } else if (p) {
+      p[i - nu] = -x[i];
+    }
+  }
+}
+
+__global__ void k_import_x(int64_t nu, int64_t n, const double *x0, double *x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = x0 ? (i < nu ? x0[i] : -x0[i]) : 0.0;
+}
+
+}  // namespace vem
+
+using namespace vem;
+
+extern "C" {
+
+vem_status vem_default_options(vem_options *o) {
+  if (!o) return VEM_ERR_BAD_INPUT;
+  std::memset(o, 0, sizeof(*o));
+  o->element = VEM_ELEMENT_E0;
+  o->krylov = VEM_KRYLOV_FGMRES;
+  o->restart = 30;
+  o->rtol = 1e-12;
+  o->maxit = 2000;
+  o->precond = VEM_PREC_BLOCK_DIAG;
+  o->inner = VEM_INNER_PCG;
+  o->inner_rtol = 1e-12;
+  o->inner_maxit = 2000;
+  o->precision = VEM_PRECISION_FP64;
+  o->device_io = 0;
+  return VEM_OK;
+}
+
+vem_status vem_create(const vem_mesh *mesh, const vem_options *opt, void *stream, vem_handle **out) {
+  if (!out) return VEM_ERR_BAD_INPUT;
+  *out = nullptr;
+  vem_handle *h = new (std::nothrow) vem_handle();
+  if (!h) return VEM_ERR_OOM;
+  if (opt) {
+    h->opt = *opt;
+  } else {
+    vem_default_options(&h->opt);
+  }
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  vem_status st = check_options(h, &h->opt);
+  if (st == VEM_OK) st = create_impl(h, mesh);
+  if (st != VEM_OK) {
+    vem_destroy(h);
+    return st;
+  }
+  *out = h;
+  return VEM_OK;
+}
+
+vem_status vem_set_options(vem_handle *h, const vem_options *opt) {
+  if (!h || !opt) return VEM_ERR_BAD_INPUT;
+  VEM_TRY(check_options(h, opt));
+  const bool elem_changed = opt->element != h->opt.element;
+  h->opt = *opt;
+  if (elem_changed) {
+    set_layout(h);
+    h->assembled = false;
+    h->rhs_ready = false;
+    dfree(h, h->rhs);
+    h->rhs = nullptr;
+    dfree(h, h->diagM);
+    h->diagM = nullptr;
+    dfree(h, h->a_rp);
+    h->a_rp = nullptr;
+    dfree(h, h->xsol);
+    h->xsol = nullptr;
+    dfree(h, h->cnt_buf);
+    h->cnt_buf = nullptr;
+  }
+  return VEM_OK;
+}
+
+vem_status vem_sizes(const vem_handle *h, int64_t *n_u, int64_t *n_p) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (n_u) *n_u = h->n_u;
+  if (n_p) *n_p = h->n_p;
+  return VEM_OK;
+}
+
+vem_status vem_quadrature_count(const vem_handle *h, int which, int64_t *n) {
+  if (!h || !n) return VEM_ERR_BAD_INPUT;
+  if (which == VEM_QP_CELL) *n = h->nc;
+  else if (which == VEM_QP_BFACE) *n = h->n_bqp;
+  else return VEM_ERR_BAD_INPUT;
+  return VEM_OK;
+}
+
+vem_status vem_quadrature_points(vem_handle *h, int which, double *xyz_out) {
+  if (!h || !xyz_out) return h ? fail(h, VEM_ERR_BAD_INPUT, "NULL output") : VEM_ERR_BAD_INPUT;
+  const double *src = nullptr;
+  int64_t n = 0;
+  if (which == VEM_QP_CELL) {
+    src = h->c_cent;
+    n = h->nc;
+  } else if (which == VEM_QP_BFACE) {
+    src = h->bqp_xyz;
+    n = h->n_bqp;
+  } else {
+    return fail(h, VEM_ERR_BAD_INPUT, "unknown quadrature set %d", which);
+  }
+  if (n > 0)
+    VEM_CUDA(h, cudaMemcpyAsync(xyz_out, src, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return VEM_OK;
+}
+
+vem_status vem_set_coefficient(vem_handle *h, const double *K) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (!K) return fail(h, VEM_ERR_BAD_INPUT, "K: NULL");
+  std::vector<double> nu(h->nc);
+  for (int64_t c = 0; c < h->nc; ++c) {
+    if (!std::isfinite(K[c])) return fail(h, VEM_ERR_NONFINITE, "K[%lld] is not finite", (long long)c);
+    if (!(K[c] > 0.0)) return fail(h, VEM_ERR_BAD_INPUT, "K[%lld] <= 0", (long long)c);
+    nu[c] = 1.0 / K[c];
+  }
+  VEM_CUDA(h, cudaMemcpyAsync(h->nu, nu.data(), sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->stream));
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->assembled = false;
+  return VEM_OK;
+}
+
+vem_status vem_set_coefficient_device(vem_handle *h, const double *K) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (!K) return fail(h, VEM_ERR_BAD_INPUT, "K: NULL");
+  count_launch(); k_invert_check<<<grid_for(h->nc, 256), 256, 0, h->stream>>>(h->nc, K, h->nu, h->d_err);
+  VEM_CUDA(h, cudaGetLastError());
+  h->assembled = false;
+  vem_status st = check_device_errors(h, "coefficient");
+  if (st == VEM_ERR_NONFINITE) return fail(h, VEM_ERR_BAD_INPUT, "K must be finite and > 0");
+  return st;
+}
+
+vem_status vem_set_source(vem_handle *h, const double *f_qp, const double *gD_qp) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (f_qp) {
+    for (int64_t i = 0; i < h->nc; ++i)
+      if (!std::isfinite(f_qp[i])) return fail(h, VEM_ERR_NONFINITE, "f is not finite at point %lld", (long long)i);
+    VEM_CUDA(h, cudaMemcpyAsync(h->f_qp, f_qp, sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->stream));
+  } else {
+    VEM_CUDA(h, cudaMemsetAsync(h->f_qp, 0, sizeof(double) * h->nc, h->stream));
+  }
+  if (h->n_bqp > 0) {
+    if (gD_qp) {
+      for (int64_t i = 0; i < h->n_bqp; ++i)
+        if (!std::isfinite(gD_qp[i])) return fail(h, VEM_ERR_NONFINITE, "g_D is not finite at point %lld", (long long)i);
+      VEM_CUDA(h, cudaMemcpyAsync(h->gD_qp, gD_qp, sizeof(double) * h->n_bqp, cudaMemcpyHostToDevice, h->stream));
+    } else {
+      VEM_CUDA(h, cudaMemsetAsync(h->gD_qp, 0, sizeof(double) * h->n_bqp, h->stream));
+    }
+  }
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->rhs_ready = false;
+  return VEM_OK;
+}
+
+vem_status vem_set_source_device(vem_handle *h, const double *f_qp, const double *gD_qp) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (f_qp)
+    VEM_CUDA(h, cudaMemcpyAsync(h->f_qp, f_qp, sizeof(double) * h->nc, cudaMemcpyDeviceToDevice, h->stream));
+  else
+    VEM_CUDA(h, cudaMemsetAsync(h->f_qp, 0, sizeof(double) * h->nc, h->stream));
+  if (h->n_bqp > 0) {
+    if (gD_qp)
+      VEM_CUDA(h, cudaMemcpyAsync(h->gD_qp, gD_qp, sizeof(double) * h->n_bqp, cudaMemcpyDeviceToDevice, h->stream));
+    else
+      VEM_CUDA(h, cudaMemsetAsync(h->gD_qp, 0, sizeof(double) * h->n_bqp, h->stream));
+  }
+  h->rhs_ready = false;
+  return VEM_OK;
+}
+
+vem_status vem_assemble(vem_handle *h) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  return assemble_impl(h);
+}
+
+vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_out, vem_stats *stats) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (!u_out || !p_out) return fail(h, VEM_ERR_BAD_INPUT, "u_out / p_out: NULL");
+  if (!h->assembled) VEM_TRY(assemble_impl(h));
+  VEM_TRY(ensure_rhs(h));
+  cudaStream_t s = h->stream;
+  if (!h->xsol) VEM_TRY(dalloc_n(h, &h->xsol, (size_t)h->n));
+  double *x = h->xsol;
+  vem_stats st{};
+  st.n_u = h->n_u;
+  st.n_p = h->n_p;
+  st.nnz_A = h->nnz_a;
+  st.nnz_S = h->nnz_s;
+  st.t_assemble_ms = h->t_assemble_ms;
+  vem_status r = VEM_OK;
+  do {
+    const double *x0d = nullptr;
+    double *tmp = nullptr;
+    if (x0 && !h->opt.device_io) {
+      r = dalloc_n(h, &tmp, (size_t)h->n);
+      if (r != VEM_OK) break;
+      cudaError_t e = cudaMemcpyAsync(tmp, x0, sizeof(double) * h->n, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) { r = cuda_check(h, e, "x0"); break; }
+      x0d = tmp;
+    } else if (x0) {
+      x0d = x0;
+    }
+    count_launch(); k_import_x<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n, x0d, x);
+    cudaEventRecord(h->ev0, s);
+    r = krylov_solve(h, x, &st);
+    cudaEventRecord(h->ev1, s);
+    cudaEventSynchronize(h->ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    st.t_solve_ms = ms;
+    if (tmp) dfree(h, tmp);
+    if (r != VEM_OK && r != VEM_ERR_NOT_CONVERGED) break;
+    vem_status w = VEM_OK;
+    if (h->opt.device_io) {
+      count_launch(); k_export_x<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n_p, x, u_out, p_out);
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) w = cuda_check(h, e, "export");
+    } else {
+      cudaError_t e = cudaMemcpyAsync(u_out, x, sizeof(double) * h->n_u, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(p_out, x + h->n_u, sizeof(double) * h->n_p, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) w = cuda_check(h, e, "export");
+      else
+        for (int64_t i = 0; i < h->n_p; ++i) p_out[i] = -p_out[i];
+    }
+    if (w != VEM_OK) r = w;
+  } while (0);
+  if (stats) *stats = st;
+  return r;
+}
+
+vem_status vem_get_geometry(vem_handle *h, double *fa, double *fc, double *fn, double *fd, double *cv,
+                            double *cc, double *cd) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  cudaStream_t s = h->stream;
+  if (fa) VEM_CUDA(h, cudaMemcpyAsync(fa, h->f_area, sizeof(double) * h->nf, cudaMemcpyDeviceToHost, s));
+  if (fc) VEM_CUDA(h, cudaMemcpyAsync(fc, h->f_cent, sizeof(double) * 3 * h->nf, cudaMemcpyDeviceToHost, s));
+  if (fn) VEM_CUDA(h, cudaMemcpyAsync(fn, h->f_norm, sizeof(double) * 3 * h->nf, cudaMemcpyDeviceToHost, s));
+  if (fd) VEM_CUDA(h, cudaMemcpyAsync(fd, h->f_diam, sizeof(double) * h->nf, cudaMemcpyDeviceToHost, s));
+  if (cv) VEM_CUDA(h, cudaMemcpyAsync(cv, h->c_vol, sizeof(double) * h->nc, cudaMemcpyDeviceToHost, s));
+  if (cc) VEM_CUDA(h, cudaMemcpyAsync(cc, h->c_cent, sizeof(double) * 3 * h->nc, cudaMemcpyDeviceToHost, s));
+  if (cd) VEM_CUDA(h, cudaMemcpyAsync(cd, h->c_diam, sizeof(double) * h->nc, cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  return VEM_OK;
+}
+
+vem_status vem_local_size(const vem_handle *h, int64_t *m_total, int64_t *b_total) {
+  if (!h || !m_total || !b_total) return VEM_ERR_BAD_INPUT;
+  int64_t mt = 0;
+  for (int64_t c = 0; c < h->nc; ++c) {
+    const int64_t nl = h->nfd * (h->h_cf_ptr[c + 1] - h->h_cf_ptr[c]) + h->nid;
+    mt += nl * nl;
+  }
+  *m_total = mt;
+  *b_total = h->nfd * h->n_cf + h->nid * h->nc;
+  return VEM_OK;
+}
+
+vem_status vem_get_local(vem_handle *h, double *M_out, int64_t *M_offsets, double *B_out) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (!h->assembled) return fail(h, VEM_ERR_BAD_INPUT, "vem_get_local before vem_assemble");
+  cudaStream_t s = h->stream;
+  if (M_out) VEM_CUDA(h, cudaMemcpyAsync(M_out, h->Mloc, sizeof(double) * h->m_total, cudaMemcpyDeviceToHost, s));
+  if (M_offsets)
+    VEM_CUDA(h, cudaMemcpyAsync(M_offsets, h->m_off, sizeof(int64_t) * (h->nc + 1), cudaMemcpyDeviceToHost, s));
+  if (B_out) VEM_CUDA(h, cudaMemcpyAsync(B_out, h->Bloc, sizeof(double) * h->b_total, cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  return VEM_OK;
+}
+
+vem_status vem_get_system(vem_handle *h, int64_t *rp, int32_t *col, double *val, double *rhs) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (!h->assembled) VEM_TRY(assemble_impl(h));
+  VEM_TRY(ensure_rhs(h));
+  cudaStream_t s = h->stream;
+  if (rp) VEM_CUDA(h, cudaMemcpyAsync(rp, h->a_rp, sizeof(int64_t) * (h->n + 1), cudaMemcpyDeviceToHost, s));
+  if (col) VEM_CUDA(h, cudaMemcpyAsync(col, h->a_col, sizeof(int32_t) * h->nnz_a, cudaMemcpyDeviceToHost, s));
+  if (val) VEM_CUDA(h, cudaMemcpyAsync(val, h->a_val, sizeof(double) * h->nnz_a, cudaMemcpyDeviceToHost, s));
+  if (rhs) VEM_CUDA(h, cudaMemcpyAsync(rhs, h->rhs, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  return VEM_OK;
+}
+
+vem_status vem_get_schur(vem_handle *h, int64_t *rp, int32_t *col, double *val, double *diagM) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (!h->assembled) VEM_TRY(assemble_impl(h));
+  cudaStream_t s = h->stream;
+  if (rp) VEM_CUDA(h, cudaMemcpyAsync(rp, h->s_rp, sizeof(int64_t) * (h->nc + 1), cudaMemcpyDeviceToHost, s));
+  if (col) VEM_CUDA(h, cudaMemcpyAsync(col, h->s_col, sizeof(int32_t) * h->nnz_s, cudaMemcpyDeviceToHost, s));
+  if (val) VEM_CUDA(h, cudaMemcpyAsync(val, h->s_val, sizeof(double) * h->nnz_s, cudaMemcpyDeviceToHost, s));
+  if (diagM) VEM_CUDA(h, cudaMemcpyAsync(diagM, h->diagM, sizeof(double) * h->n_u, cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  return VEM_OK;
+}
+
+vem_status vem_apply_device(vem_handle *h, const double *x, double *y) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (!x || !y) return fail(h, VEM_ERR_BAD_INPUT, "x / y: NULL");
+  if (!h->assembled) VEM_TRY(assemble_impl(h));
+  spmv(h->stream, h->n, h->a_rp, h->a_col, h->a_val, x, y, h->a_lanes);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return VEM_OK;
+}
+
+vem_status vem_launch_count(int64_t *n) {
+  if (!n) return VEM_ERR_BAD_INPUT;
+  *n = launch_count();
+  return VEM_OK;
+}
+
+const char *vem_last_error(const vem_handle *h) { return h ? h->last_error.c_str() : "NULL handle"; }
+
+void vem_destroy(vem_handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void *p : h->allocations) cudaFree(p);
+  h->allocations.clear();
+  if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->h_scal) cudaFreeHost(h->h_scal);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+}
+
+}  // extern "C"

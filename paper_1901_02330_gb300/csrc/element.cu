@@ -1,0 +1,538 @@
+// Element-batched local matrices (paper Sec. 4.1-4.3), one warp per cell.
+//
+// For every cell P the kernels build
+//   M_P = nu (Pi^T H Pi + |P| (I - D Pi)^T (I - D Pi))   (a_{h,P} with the
+//         dofi-dofi stabilisation s_P of Sec. 4.3),
+//   B_P = |P| d                                          (b_{h,P}, P0 pressure)
+// where Pi = H^{-1} G is the L2 projection onto [P_kp]^3 (Sec. 4.1, third
+// bullet), D the DOFs of the vector monomials and d the divergence of the
+// basis functions.  M_P is evaluated as
+//   M_P = nu (|P| I - |P| (D Pi + Pi^T D^T) + Pi^T W Pi),  W = H + |P| D^T D,
+// so each entry costs three length-12 dot products.
+//
+// E0: face moments against M_0(f) only, Pi^0_0; closed form with
+//   N_f = sigma_f |f| (x_f - x_P), D_f = n_f:  Pi = N^T/|P|, H = |P| I.
+// K1 (the paper's k = 1): three face moments (M_1(f)), three cross moments
+//   (m_I ^ e_q), Pi^0_1 through the decomposition of Props 2.1-2.3.
+#include "handle.cuh"
+#include "geom_device.cuh"
+
+namespace vem {
+
+// index of y_a * y_d among the degree <= 2 monomials
+// (1, y0, y1, y2, y0^2, y0y1, y0y2, y1^2, y1y2, y2^2); a = 0 means 1
+__constant__ int c_prod[4][3] = {{1, 2, 3}, {4, 5, 6}, {5, 7, 8}, {6, 8, 9}};
+// H1[a][b] = int m_a m_b -> index into the 10 cell moments
+__constant__ int c_h1[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
+
+__device__ __forceinline__ void upper_decode(int e, int n, int &i, int &j) {
+  i = 0;
+  while (e >= n - i) {
+    e -= n - i;
+    ++i;
+  }
+  j = i + e;
+}
+
+// ---------------------------------------------------------------- E0 ----
+__global__ void k_elem_e0(int64_t nc, int max_nf, const int64_t *__restrict__ cfp,
+                          const int32_t *__restrict__ cf, const int8_t *__restrict__ sig,
+                          const double *__restrict__ f_area, const double *__restrict__ f_cent,
+                          const double *__restrict__ f_norm, const double *__restrict__ c_vol,
+                          const double *__restrict__ c_cent, const double *__restrict__ nu,
+                          const int64_t *__restrict__ m_off, double *Mloc, double *Bloc) {
+  extern __shared__ double sm[];
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double *N = sm + (size_t)warp * (6 * max_nf + 9);
+  double *nn = N + 3 * max_nf;
+  double *Q = nn + 3 * max_nf;
+  for (int64_t c = (int64_t)blockIdx.x * wpb + warp; c < nc; c += (int64_t)gridDim.x * wpb) {
+    const int64_t b = cfp[c];
+    const int k = (int)(cfp[c + 1] - b);
+    const double vol = c_vol[c], nuc = nu[c];
+    const double3 xP = load3(c_cent, c);
+    for (int i = lane; i < k; i += 32) {
+      const int f = cf[b + i];
+      const double s = (double)sig[b + i] * f_area[f];
+      const double3 d = sub3(load3(f_cent, f), xP);
+      N[3 * i] = s * d.x;
+      N[3 * i + 1] = s * d.y;
+      N[3 * i + 2] = s * d.z;
+      nn[3 * i] = f_norm[3 * f];
+      nn[3 * i + 1] = f_norm[3 * f + 1];
+      nn[3 * i + 2] = f_norm[3 * f + 2];
+      Bloc[b + i] = s;
+    }
+    __syncwarp();
+    if (lane < 9) {
+      const int p = lane / 3, q = lane % 3;
+      double t = 0;
+      for (int i = 0; i < k; ++i) t += nn[3 * i + p] * nn[3 * i + q];
+      Q[lane] = t;
+    }
+    __syncwarp();
+    double *M = Mloc + m_off[c];
+    const int T = k * (k + 1) / 2;
+    for (int e = lane; e < T; e += 32) {
+      int i, j;
+      upper_decode(e, k, i, j);
+      const double *Ni = N + 3 * i, *Nj = N + 3 * j, *ni = nn + 3 * i, *nj = nn + 3 * j;
+      const double nij = Ni[0] * Nj[0] + Ni[1] * Nj[1] + Ni[2] * Nj[2];
+      const double cr = (ni[0] * Nj[0] + ni[1] * Nj[1] + ni[2] * Nj[2]) +
+                        (Ni[0] * nj[0] + Ni[1] * nj[1] + Ni[2] * nj[2]);
+      double nqn = 0;
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) nqn += Ni[p] * Q[3 * p + q] * Nj[q];
+      const double v = nuc * (nij / vol + (i == j ? vol : 0.0) - cr + nqn / vol);
+      M[(int64_t)i * k + j] = v;
+      M[(int64_t)j * k + i] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- K1 ----
+// Shared-memory layout per warp (doubles):
+//   FG[max_nf][5]   sigma, |f|, n_f
+//   FA[max_nf][36]  face Gram G_f (6, then its inverse) and J_f[g][t] (30)
+//   MU[10] cell moments int_P m_t, H1I[16], W[144]
+//   U[...]          chunk buffer (32 x 36) / Pi (12 x nu), D (nu x 12), W Pi (12 x nu)
+// plus ints FO[max_nf + 1] (prefix of fan-triangle counts).
+__host__ __device__ inline int k1_union(int max_nf) {
+  const int nu = 3 * max_nf + 3;
+  const int a = 32 * 36, b = 36 * nu;
+  return a > b ? a : b;
+}
+__host__ __device__ inline int k1_doubles(int max_nf) {
+  return max_nf * 41 + 10 + 16 + 144 + k1_union(max_nf);
+}
+__host__ __device__ inline int k1_ints(int max_nf) { return ((max_nf + 2) + 1) & ~1; }
+
+__global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cfp,
+                          const int32_t *__restrict__ cf, const int8_t *__restrict__ sig,
+                          const int64_t *__restrict__ fvp, const int32_t *__restrict__ fv,
+                          const double *__restrict__ xyz, const double *__restrict__ f_area,
+                          const double *__restrict__ f_cent, const double *__restrict__ f_norm,
+                          const double *__restrict__ f_t1, const double *__restrict__ f_diam,
+                          const double *__restrict__ c_cent, const double *__restrict__ c_diam,
+                          const double *__restrict__ nu, const int64_t *__restrict__ m_off,
+                          double *Mloc, double *Bloc, int *err) {
+  extern __shared__ double sm[];
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nd = k1_doubles(max_nf);
+  double *FG = sm + (size_t)warp * nd;
+  double *FA = FG + 5 * max_nf;
+  double *MU = FA + 36 * max_nf;
+  double *H1I = MU + 10;
+  double *W = H1I + 16;
+  double *U = W + 144;
+  int *FO = reinterpret_cast<int *>(sm + (size_t)wpb * nd) + warp * k1_ints(max_nf);
+
+  for (int64_t c = (int64_t)blockIdx.x * wpb + warp; c < nc; c += (int64_t)gridDim.x * wpb) {
+    const int64_t b = cfp[c];
+    const int k = (int)(cfp[c + 1] - b);
+    const int nu_l = 3 * k + 3;
+    const double3 xP = load3(c_cent, c);
+    const double hP = c_diam[c], ihP = 1.0 / hP;
+    const double nuc = nu[c];
+
+    // per-face data and fan-triangle prefix
+    for (int i = lane; i < k; i += 32) {
+      const int f = cf[b + i];
+      FG[5 * i] = (double)sig[b + i];
+      FG[5 * i + 1] = f_area[f];
+      FG[5 * i + 2] = f_norm[3 * f];
+      FG[5 * i + 3] = f_norm[3 * f + 1];
+      FG[5 * i + 4] = f_norm[3 * f + 2];
+      for (int t = 0; t < 36; ++t) FA[36 * i + t] = 0.0;
+    }
+    if (lane == 0) {
+      int acc = 0;
+      for (int i = 0; i < k; ++i) {
+        FO[i] = acc;
+        const int f = cf[b + i];
+        acc += (int)(fvp[f + 1] - fvp[f]);
+      }
+      FO[k] = acc;
+    }
+    __syncwarp();
+    const int T = FO[k];
+
+    // (1) face Gram matrices, face-cell integrals J and cell moments by
+    //     quadrature over the fan triangles (x_f, v_j, v_{j+1}); one lane per
+    //     triangle, summed per face in triangle order.
+    double mu[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) mu[t] = 0.0;
+    for (int base = 0; base < T; base += 32) {
+      const int p = base + lane;
+      double acc[36];
+#pragma unroll
+      for (int t = 0; t < 36; ++t) acc[t] = 0.0;
+      if (p < T) {
+        int i = 0;
+        while (FO[i + 1] <= p) ++i;
+        const int j = p - FO[i];
+        const int f = cf[b + i];
+        const int64_t vb = fvp[f];
+        const int m = (int)(fvp[f + 1] - vb);
+        const double3 A = load3(xyz, fv[vb + j]);
+        const double3 B = load3(xyz, fv[vb + (j + 1) % m]);
+        const double3 xf = load3(f_cent, f);
+        const double3 n = load3(f_norm, f);
+        const double3 t1 = load3(f_t1, f);
+        const double3 t2 = cross3(n, t1);
+        const double ihf = 1.0 / f_diam[f];
+        const double areaT = 0.5 * dot3(cross3(sub3(A, xf), sub3(B, xf)), n);
+        for (int q = 0; q < 6; ++q) {
+          double l0, l1, l2, wq;
+          dunavant4_point(q, l0, l1, l2, wq);
+          const double3 x = add3(add3(scale3(xf, l0), scale3(A, l1)), scale3(B, l2));
+          const double w = wq * areaT;
+          const double3 dx = sub3(x, xf);
+          const double mf[3] = {1.0, dot3(dx, t1) * ihf, dot3(dx, t2) * ihf};
+          const double3 y = scale3(sub3(x, xP), ihP);
+          const double m3[10] = {1.0, y.x, y.y, y.z, y.x * y.x, y.x * y.y, y.x * y.z,
+                                 y.y * y.y, y.y * y.z, y.z * y.z};
+          acc[0] += w * mf[0] * mf[0];
+          acc[1] += w * mf[0] * mf[1];
+          acc[2] += w * mf[0] * mf[2];
+          acc[3] += w * mf[1] * mf[1];
+          acc[4] += w * mf[1] * mf[2];
+          acc[5] += w * mf[2] * mf[2];
+#pragma unroll
+          for (int g = 0; g < 3; ++g)
+#pragma unroll
+            for (int t = 0; t < 10; ++t) acc[6 + 10 * g + t] += w * mf[g] * m3[t];
+        }
+        // cell moments from the tetrahedron (x_P, x_f, v_j, v_{j+1}) in y-units
+        const double3 p1 = scale3(sub3(xf, xP), ihP);
+        const double3 p2 = scale3(sub3(A, xP), ihP);
+        const double3 p3 = scale3(sub3(B, xP), ihP);
+        const double vy = FG[5 * i] * dot3(p1, cross3(p2, p3)) / 6.0;
+        const double3 S = add3(add3(p1, p2), p3);
+        mu[0] += vy;
+        mu[1] += vy * S.x * 0.25;
+        mu[2] += vy * S.y * 0.25;
+        mu[3] += vy * S.z * 0.25;
+        const double s20 = vy / 20.0;
+        mu[4] += s20 * (p1.x * p1.x + p2.x * p2.x + p3.x * p3.x + S.x * S.x);
+        mu[5] += s20 * (p1.x * p1.y + p2.x * p2.y + p3.x * p3.y + S.x * S.y);
+        mu[6] += s20 * (p1.x * p1.z + p2.x * p2.z + p3.x * p3.z + S.x * S.z);
+        mu[7] += s20 * (p1.y * p1.y + p2.y * p2.y + p3.y * p3.y + S.y * S.y);
+        mu[8] += s20 * (p1.y * p1.z + p2.y * p2.z + p3.y * p3.z + S.y * S.z);
+        mu[9] += s20 * (p1.z * p1.z + p2.z * p2.z + p3.z * p3.z + S.z * S.z);
+      }
+#pragma unroll
+      for (int t = 0; t < 36; ++t) U[36 * lane + t] = acc[t];
+      __syncwarp();
+      const int hi = base + 32 < T ? base + 32 : T;
+      for (int i = lane; i < k; i += 32) {
+        const int lo_p = FO[i] > base ? FO[i] : base;
+        const int hi_p = FO[i + 1] < hi ? FO[i + 1] : hi;
+        for (int pp = lo_p; pp < hi_p; ++pp)
+          for (int t = 0; t < 36; ++t) FA[36 * i + t] += U[36 * (pp - base) + t];
+      }
+      __syncwarp();
+    }
+    const double h3 = hP * hP * hP;
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+      double v = warp_sum(mu[t]);
+      if (lane == 0) MU[t] = v * h3;
+    }
+    // face Gram inverses (symmetric 3x3 by cofactors)
+    for (int i = lane; i < k; i += 32) {
+      double *G = FA + 36 * i;
+      const double a = G[0], bb = G[1], cc = G[2], d = G[3], e = G[4], ff = G[5];
+      const double A11 = d * ff - e * e, A12 = -(bb * ff - cc * e), A13 = bb * e - cc * d;
+      const double A22 = a * ff - cc * cc, A23 = -(a * e - bb * cc), A33 = a * d - bb * bb;
+      const double det = a * A11 + bb * A12 + cc * A13;
+      if (!(fabs(det) > 0.0) || !isfinite(det)) atomicOr(err, DEVERR_SINGULAR_LOCAL);
+      const double id = 1.0 / det;
+      G[0] = A11 * id;
+      G[1] = A12 * id;
+      G[2] = A13 * id;
+      G[3] = A22 * id;
+      G[4] = A23 * id;
+      G[5] = A33 * id;
+    }
+    __syncwarp();
+    // H1 = int m_a m_b (a, b <= 1) and its inverse (Gauss-Jordan, SPD)
+    if (lane == 0) {
+      double a[4][8];
+      for (int r = 0; r < 4; ++r)
+        for (int s = 0; s < 4; ++s) {
+          a[r][s] = MU[c_h1[r][s]];
+          a[r][4 + s] = (r == s) ? 1.0 : 0.0;
+        }
+      for (int r = 0; r < 4; ++r) {
+        const double piv = a[r][r];
+        if (!(piv > 0.0)) atomicOr(err, DEVERR_SINGULAR_LOCAL);
+        const double ip = 1.0 / piv;
+        for (int s = 0; s < 8; ++s) a[r][s] *= ip;
+        for (int q = 0; q < 4; ++q)
+          if (q != r) {
+            const double fct = a[q][r];
+            for (int s = 0; s < 8; ++s) a[q][s] -= fct * a[r][s];
+          }
+      }
+      for (int r = 0; r < 4; ++r)
+        for (int s = 0; s < 4; ++s) H1I[4 * r + s] = a[r][4 + s];
+    }
+    __syncwarp();
+
+    const double vol = MU[0];
+    double *PI = U;                      // [12][nu_l]
+    double *DD = U + 12 * nu_l;          // [nu_l][12]
+    double *WP = DD + 12 * nu_l;         // [12][nu_l]
+    const int nfl = 3 * k;
+    const int64_t boff = 3 * b + 3 * c;
+
+    // (2)-(3) columns j of G, D and B; Pi[:, j] = blockdiag(H1^{-1}) G[:, j]
+    for (int j = lane; j < nu_l; j += 32) {
+      double Gc[12], Dr[12], Bj = 0.0;
+      if (j < nfl) {
+        const int i = j / 3, beta = j % 3;
+        const double sg = FG[5 * i], ar = FG[5 * i + 1];
+        const double *Gi = FA + 36 * i;
+        const double *J = Gi + 6;
+        // column beta of the symmetric inverse
+        const double gb[3] = {beta == 0 ? Gi[0] : (beta == 1 ? Gi[1] : Gi[2]),
+                              beta == 0 ? Gi[1] : (beta == 1 ? Gi[3] : Gi[4]),
+                              beta == 0 ? Gi[2] : (beta == 1 ? Gi[4] : Gi[5])};
+        double bnd[10];
+#pragma unroll
+        for (int t = 0; t < 10; ++t)
+          bnd[t] = sg * ar * (gb[0] * J[t] + gb[1] * J[10 + t] + gb[2] * J[20 + t]);
+        const double dv = bnd[0] / vol;     // div(phi_j), constant
+        Bj = vol * dv;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          // int phi . grad m_beta by parts, beta = e_c (a = 0) or e_d + e_c (a = 1 + d)
+          const int t0 = 1 + cc;
+          Gc[4 * cc] = hP * (-dv * MU[t0] + bnd[t0]);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const int t = c_prod[1 + d][cc];
+            Gc[4 * cc + 1 + d] = 0.5 * hP * (-dv * MU[t] + bnd[t]);
+          }
+          const double ncomp = FG[5 * i + 2 + cc];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) Dr[4 * cc + a] = ncomp * J[10 * beta + a] / ar;
+        }
+      } else {
+        const int q = j - nfl;
+#pragma unroll
+        for (int t = 0; t < 12; ++t) Gc[t] = 0.0;
+        // Props 2.1-2.3 at degree 1: the m_I ^ e_q coefficients
+        if (q == 2) { Gc[0 * 4 + 2] = 0.5 * vol; Gc[1 * 4 + 1] = -0.5 * vol; }
+        if (q == 1) { Gc[0 * 4 + 3] = -0.5 * vol; Gc[2 * 4 + 1] = 0.5 * vol; }
+        if (q == 0) { Gc[1 * 4 + 3] = 0.5 * vol; Gc[2 * 4 + 2] = -0.5 * vol; }
+        // D: (1/|P|) int m_a (m_I ^ e_q)_c
+        const double iv = 1.0 / vol;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          int dsel = -1;
+          double sgn = 0.0;
+          if (q == 0) { if (cc == 1) { dsel = 2; sgn = 1.0; } else if (cc == 2) { dsel = 1; sgn = -1.0; } }
+          if (q == 1) { if (cc == 0) { dsel = 2; sgn = -1.0; } else if (cc == 2) { dsel = 0; sgn = 1.0; } }
+          if (q == 2) { if (cc == 0) { dsel = 1; sgn = 1.0; } else if (cc == 1) { dsel = 0; sgn = -1.0; } }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+            Dr[4 * cc + a] = (dsel < 0) ? 0.0 : sgn * MU[c_prod[a][dsel]] * iv;
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          double s = 0.0;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) s += H1I[4 * r + t] * Gc[4 * cc + t];
+          PI[(4 * cc + r) * nu_l + j] = s;
+        }
+#pragma unroll
+      for (int v = 0; v < 12; ++v) DD[12 * j + v] = Dr[v];
+      Bloc[boff + j] = Bj;
+    }
+    __syncwarp();
+    // W = H + |P| D^T D (symmetric, entries v <= w computed once)
+    for (int e = lane; e < 78; e += 32) {
+      int v, w;
+      upper_decode(e, 12, v, w);
+      double s = 0.0;
+      for (int j = 0; j < nu_l; ++j) s += DD[12 * j + v] * DD[12 * j + w];
+      double hv = (v / 4 == w / 4) ? MU[c_h1[v % 4][w % 4]] : 0.0;
+      const double val = hv + vol * s;
+      W[12 * v + w] = val;
+      W[12 * w + v] = val;
+    }
+    __syncwarp();
+    for (int j = lane; j < nu_l; j += 32)
+      for (int v = 0; v < 12; ++v) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < 12; ++w) s += W[12 * v + w] * PI[w * nu_l + j];
+        WP[v * nu_l + j] = s;
+      }
+    __syncwarp();
+    // (4) M_P entries
+    double *M = Mloc + m_off[c];
+    const int TT = nu_l * (nu_l + 1) / 2;
+    for (int e = lane; e < TT; e += 32) {
+      int j, jp;
+      upper_decode(e, nu_l, j, jp);
+      double dpa = 0.0, dpb = 0.0, pwp = 0.0;
+#pragma unroll
+      for (int v = 0; v < 12; ++v) {
+        dpa += DD[12 * j + v] * PI[v * nu_l + jp];
+        dpb += DD[12 * jp + v] * PI[v * nu_l + j];
+        pwp += PI[v * nu_l + j] * WP[v * nu_l + jp];
+      }
+      const double val = nuc * ((j == jp ? vol : 0.0) - vol * (dpa + dpb) + pwp);
+      M[(int64_t)j * nu_l + jp] = val;
+      M[(int64_t)jp * nu_l + j] = val;
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------- loads ----
+// F_P = |P| f(x_P) (midpoint rule at the barycentre).
+__global__ void k_rhs_cells(int64_t nc, const double *__restrict__ c_vol,
+                            const double *__restrict__ f_qp, double *F, int *err) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const double fv = f_qp ? f_qp[c] : 0.0;
+    if (!isfinite(fv)) atomicOr(err, DEVERR_NONFINITE);
+    F[c] = c_vol[c] * fv;
+  }
+}
+
+// g_(f,beta) = -sigma |f| sum_g Ginv[g][beta] int_f g_D m^f_g on Dirichlet
+// faces (zero elsewhere), with the Dunavant fan rule of the bface points.
+__global__ void k_rhs_faces(int64_t nf, int nfd, const int8_t *__restrict__ fbc,
+                            const int64_t *__restrict__ off, const int64_t *__restrict__ fvp,
+                            const int32_t *__restrict__ fv, const double *__restrict__ xyz,
+                            const double *__restrict__ f_area, const double *__restrict__ f_cent,
+                            const double *__restrict__ f_norm, const double *__restrict__ f_t1,
+                            const double *__restrict__ f_diam, const int32_t *__restrict__ f_cell,
+                            const int32_t *__restrict__ f_loc, const int64_t *__restrict__ cfp,
+                            const int8_t *__restrict__ sig, const double *__restrict__ gD, double *g,
+                            int *err) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    for (int bta = 0; bta < nfd; ++bta) g[nfd * f + bta] = 0.0;
+    if (fbc[f] != 1 || gD == nullptr) continue;
+    const int64_t vb = fvp[f];
+    const int m = (int)(fvp[f + 1] - vb);
+    const double3 xf = load3(f_cent, f);
+    const double3 n = load3(f_norm, f);
+    const double3 t1 = load3(f_t1, f);
+    const double3 t2 = cross3(n, t1);
+    const double ihf = 1.0 / f_diam[f];
+    const double sg = (double)sig[cfp[f_cell[2 * f]] + f_loc[2 * f]];
+    double G[6] = {0, 0, 0, 0, 0, 0}, gm[3] = {0, 0, 0};
+    int64_t o = off[f];
+    for (int i = 0; i < m; ++i) {
+      const double3 A = load3(xyz, fv[vb + i]);
+      const double3 B = load3(xyz, fv[vb + (i + 1) % m]);
+      const double areaT = 0.5 * dot3(cross3(sub3(A, xf), sub3(B, xf)), n);
+      for (int q = 0; q < 6; ++q, ++o) {
+        double l0, l1, l2, wq;
+        dunavant4_point(q, l0, l1, l2, wq);
+        const double3 x = add3(add3(scale3(xf, l0), scale3(A, l1)), scale3(B, l2));
+        const double w = wq * areaT;
+        const double3 dx = sub3(x, xf);
+        const double mf[3] = {1.0, dot3(dx, t1) * ihf, dot3(dx, t2) * ihf};
+        const double gv = gD[o];
+        if (!isfinite(gv)) atomicOr(err, DEVERR_NONFINITE);
+        G[0] += w * mf[0] * mf[0];
+        G[1] += w * mf[0] * mf[1];
+        G[2] += w * mf[0] * mf[2];
+        G[3] += w * mf[1] * mf[1];
+        G[4] += w * mf[1] * mf[2];
+        G[5] += w * mf[2] * mf[2];
+        gm[0] += w * gv * mf[0];
+        gm[1] += w * gv * mf[1];
+        gm[2] += w * gv * mf[2];
+      }
+    }
+    const double ar = f_area[f];
+    if (nfd == 1) {
+      g[f] = -sg * gm[0];
+    } else {
+      const double a = G[0], bb = G[1], cc = G[2], d = G[3], e = G[4], ff = G[5];
+      const double A11 = d * ff - e * e, A12 = -(bb * ff - cc * e), A13 = bb * e - cc * d;
+      const double A22 = a * ff - cc * cc, A23 = -(a * e - bb * cc), A33 = a * d - bb * bb;
+      const double id = 1.0 / (a * A11 + bb * A12 + cc * A13);
+      const double Gi[3][3] = {{A11 * id, A12 * id, A13 * id},
+                               {A12 * id, A22 * id, A23 * id},
+                               {A13 * id, A23 * id, A33 * id}};
+      for (int bta = 0; bta < 3; ++bta)
+        g[3 * f + bta] = -sg * ar * (Gi[0][bta] * gm[0] + Gi[1][bta] * gm[1] + Gi[2][bta] * gm[2]);
+    }
+  }
+}
+
+static int warps_per_block(size_t bytes_per_warp, size_t limit = 96 * 1024) {
+  int w = (int)(limit / bytes_per_warp);
+  if (w > 8) w = 8;
+  if (w < 1) w = 1;
+  return w;
+}
+
+vem_status assemble_local(vem_handle *h) {
+  cudaStream_t s = h->stream;
+  const int mx = h->max_nf_cell;
+  if (h->opt.element == VEM_ELEMENT_E0) {
+    const size_t bpw = sizeof(double) * (6 * mx + 9);
+    if (bpw > 200 * 1024) return fail(h, VEM_ERR_UNSUPPORTED, "cell with %d faces", mx);
+    const int wpb = warps_per_block(bpw);
+    const size_t smem = bpw * wpb;
+    VEM_CUDA(h, cudaFuncSetAttribute(k_elem_e0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t blocks = (h->nc + wpb - 1) / wpb;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    count_launch(); k_elem_e0<<<(int)blocks, 32 * wpb, smem, s>>>(h->nc, mx, h->cf_ptr, h->cf, h->cf_sigma, h->f_area,
+                                                   h->f_cent, h->f_norm, h->c_vol, h->c_cent, h->nu,
+                                                   h->m_off, h->Mloc, h->Bloc);
+    VEM_CUDA(h, cudaGetLastError());
+  } else if (h->opt.element == VEM_ELEMENT_K1) {
+    const size_t bpw = sizeof(double) * k1_doubles(mx) + sizeof(int) * k1_ints(mx);
+    if (bpw > 200 * 1024) return fail(h, VEM_ERR_UNSUPPORTED, "cell with %d faces", mx);
+    const int wpb = warps_per_block(bpw);
+    const size_t smem = bpw * wpb;
+    VEM_CUDA(h, cudaFuncSetAttribute(k_elem_k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t blocks = (h->nc + wpb - 1) / wpb;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    count_launch(); k_elem_k1<<<(int)blocks, 32 * wpb, smem, s>>>(
+        h->nc, mx, h->cf_ptr, h->cf, h->cf_sigma, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent,
+        h->f_norm, h->f_t1, h->f_diam, h->c_cent, h->c_diam, h->nu, h->m_off, h->Mloc, h->Bloc,
+        h->d_err);
+    VEM_CUDA(h, cudaGetLastError());
+  } else {
+    return fail(h, VEM_ERR_UNSUPPORTED, "element %d", h->opt.element);
+  }
+  return check_device_errors(h, "element matrices");
+}
+
+vem_status assemble_rhs(vem_handle *h) {
+  cudaStream_t s = h->stream;
+  const int T = 128;
+  count_launch(); k_rhs_faces<<<grid_for(h->nf, T), T, 0, s>>>(
+      h->nf, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm,
+      h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, h->gD_qp, h->rhs, h->d_err);
+  VEM_CUDA(h, cudaGetLastError());
+  if (h->nid > 0)
+    VEM_CUDA(h, cudaMemsetAsync(h->rhs + h->nfd * h->nf, 0, sizeof(double) * h->nid * h->nc, s));
+  count_launch(); k_rhs_cells<<<grid_for(h->nc, T), T, 0, s>>>(h->nc, h->c_vol, h->f_qp, h->rhs + h->n_u, h->d_err);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_TRY(check_device_errors(h, "right-hand side"));
+  h->rhs_ready = true;
+  return VEM_OK;
+}
+
+}  // namespace vem

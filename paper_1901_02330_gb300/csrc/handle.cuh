@@ -1,0 +1,136 @@
+// Host-side state of a solver handle and the host helpers shared by the
+// translation units of the library.
+#pragma once
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+struct vem_handle {
+  vem_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+
+  // ---- mesh sizes ----
+  int64_t nv = 0, nf = 0, nc = 0, n_fv = 0, n_cf = 0;
+  int max_nf_cell = 0, max_nv_face = 0;
+
+  // ---- DOF layout (depends on the element) ----
+  int nfd = 1, nid = 0;
+  int64_t n_u = 0, n_p = 0, n = 0;
+
+  // ---- host copies of small topology arrays ----
+  std::vector<int8_t> h_fbc;
+  std::vector<int64_t> h_fv_ptr, h_cf_ptr, h_bqp_off;
+
+  // ---- device mesh ----
+  double *xyz = nullptr;
+  int64_t *fv_ptr = nullptr, *cf_ptr = nullptr;
+  int32_t *fv = nullptr, *cf = nullptr;
+  int8_t *fbc = nullptr;
+
+  // ---- geometry ----
+  double *f_area = nullptr, *f_cent = nullptr, *f_norm = nullptr, *f_t1 = nullptr,
+         *f_diam = nullptr;
+  int32_t *f_cell = nullptr, *f_loc = nullptr;   // [2 nf]; second cell -1 on the boundary
+  double *c_vol = nullptr, *c_cent = nullptr, *c_diam = nullptr;
+  int8_t *cf_sigma = nullptr;                    // [n_cf] orientation of face in cell
+  int *d_err = nullptr;                          // device error flags
+  int *h_err = nullptr;                          // pinned mirror
+
+  // ---- data ----
+  int64_t n_bqp = 0;
+  int64_t *bqp_off = nullptr;                    // [nf + 1] offsets of bface points
+  double *bqp_xyz = nullptr;                     // [n_bqp][3]
+  double *nu = nullptr;                          // 1/K per cell
+  double *f_qp = nullptr, *gD_qp = nullptr;
+  bool have_coef = false, assembled = false, rhs_ready = false;
+
+  // ---- local matrices ----
+  int64_t *m_off = nullptr;                      // [nc + 1]
+  int64_t m_total = 0, b_total = 0;
+  double *Mloc = nullptr, *Bloc = nullptr;
+
+  // ---- global system ----
+  int64_t *a_rp = nullptr;
+  int32_t *a_col = nullptr;
+  double *a_val = nullptr;
+  int64_t nnz_a = 0;
+  int a_lanes = 8;
+  double *rhs = nullptr;                         // [n] = [g; F]
+  double *bt_face = nullptr;                     // [2 nf] B entries of each face's cells
+  double *diagM = nullptr;                       // [n_u]
+  int64_t *s_rp = nullptr;
+  int32_t *s_col = nullptr;
+  double *s_val = nullptr, *s_dinv = nullptr;
+  int64_t nnz_s = 0;
+  int s_lanes = 8;
+
+  // ---- workspace ----
+  double *part = nullptr;                        // kMaxSlots * kMaxBlocks partial sums
+  double *scal = nullptr;                        // device scalars
+  double *h_scal = nullptr;                      // pinned host mirror
+  double *work = nullptr;                        // Krylov vectors
+  double *xsol = nullptr;                        // [n] solution iterate
+  int64_t *cnt_buf = nullptr;                    // [n] row counts for the scans
+  int64_t *scan_buf = nullptr;                   // scan block sums
+  size_t work_n = 0;
+
+  std::vector<void *> allocations;               // everything cudaMalloc'ed
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double t_assemble_ms = 0.0;
+};
+
+namespace vem {
+
+// Record an error on the handle and return its code.
+vem_status fail(vem_handle *h, vem_status code, const char *fmt, ...);
+
+// cudaMalloc that records the allocation; returns VEM_ERR_OOM on failure.
+vem_status dalloc(vem_handle *h, void **p, size_t bytes);
+template <class T>
+vem_status dalloc_n(vem_handle *h, T **p, size_t n) {
+  return dalloc(h, reinterpret_cast<void **>(p), n * sizeof(T) + 16);
+}
+void dfree(vem_handle *h, void *p);
+
+// Map a CUDA error to a status.
+vem_status cuda_check(vem_handle *h, cudaError_t e, const char *what);
+
+// Read the device error flags (synchronises the stream) and map them.
+vem_status check_device_errors(vem_handle *h, const char *what);
+
+int grid_for(int64_t n, int threads, int per_sm = 8);
+
+// ---- entry points implemented in the translation units ----
+vem_status geometry_build(vem_handle *h);
+vem_status assemble_local(vem_handle *h);
+vem_status assemble_rhs(vem_handle *h);
+vem_status assemble_global(vem_handle *h);
+
+// BLAS-like launches (blas.cu)
+void spmv(cudaStream_t s, int64_t rows, const int64_t *rp, const int32_t *col, const double *val,
+          const double *x, double *y, int lanes, double *dot_part = nullptr);
+int nblocks_vec(int64_t n);
+void dot_partials(cudaStream_t s, int64_t n, const double *x, const double *y, double *part);
+int choose_lanes(double avg_nnz);
+
+// Krylov solve (krylov.cu)
+vem_status krylov_solve(vem_handle *h, double *x, vem_stats *st);
+
+}  // namespace vem
+
+#define VEM_CUDA(h, call)                                                  \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) return vem::cuda_check((h), e_, #call);         \
+  } while (0)
+
+#define VEM_TRY(call)                        \
+  do {                                       \
+    vem_status s_ = (call);                  \
+    if (s_ != VEM_OK) return s_;             \
+  } while (0)

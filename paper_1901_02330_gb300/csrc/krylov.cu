@@ -1,0 +1,664 @@
+// Krylov solvers of the saddle-point system (paper Sec. 5): the outer
+// Krylov method (preconditioned MINRES or restarted FGMRES) with the block
+// preconditioner built on diag(M) and S = B diag(M)^{-1} B^T, and the inner
+// Jacobi-PCG on S.
+//
+// Every scalar of the recurrences lives in device memory; reductions are
+// deterministic two-pass sums (block partials, then a fixed-order sum by the
+// consumer), so a solve is bitwise reproducible.  The host only polls a
+// convergence flag / residual estimate.
+//
+//   MINRES: Paige & Saunders (1975), preconditioned Lanczos form.
+//   FGMRES(m): Saad (1993), right preconditioning, classical Gram-Schmidt
+//   applied twice (CGS2) for the Arnoldi step, Givens rotations.
+//   PCG: Hestenes & Stiefel (1952) with the Jacobi preconditioner.
+#include <cmath>
+#include <cstdlib>
+
+#include "handle.cuh"
+
+namespace vem {
+
+static bool debug_on() {
+  static int v = -1;
+  if (v < 0) v = std::getenv("VEM_DEBUG") ? 1 : 0;
+  return v == 1;
+}
+
+// ---------------------------------------------------------------- slots ----
+enum Slot {
+  P_RZ0 = 0, P_RZ1, P_PQ, P_RR, P_BB,       // PCG
+  P_DELTA, P_G2U, P_G2P, P_R2, P_B2,        // MINRES and residual checks
+  P_NRM, P_H0                               // FGMRES: ||w||^2, then h_0..h_m
+};
+enum Scal {
+  S_PCG_DONE = 0, S_PCG_IT, S_PCG_BAD, S_R2 = 4, S_B2 = 5,
+  S_MR = 8,   // MINRES: gamma_old, gamma, c_old, c, s_old, s, eta, a1, a2, a3, ceta, inv_gamma
+  S_GM = 32,  // FGMRES: beta, inv_beta, est, inv_hnext, bad, then H, cs, sn, g, y, h1, h2
+};
+enum { MR_GOLD = 0, MR_G, MR_COLD, MR_C, MR_SOLD, MR_S, MR_ETA, MR_A1, MR_A2, MR_A3, MR_CETA,
+       MR_IG, MR_BAD };
+
+__host__ __device__ inline double *slot(double *part, int s) { return part + (size_t)s * kMaxBlocks; }
+
+int spmv_nblocks(int64_t rows, int lanes) { return nblocks_vec(rows * lanes); }
+
+// --------------------------------------------------------------- PCG -------
+// The converged flag read once per block and broadcast, so an early return is
+// uniform across the block even if another block sets the flag meanwhile.
+__device__ __forceinline__ bool block_done(const double *sc) {
+  __shared__ int f;
+  if (threadIdx.x == 0) f = (sc[S_PCG_DONE] != 0.0);
+  __syncthreads();
+  const bool r = f != 0;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_pcg_init(int64_t n, const double *__restrict__ b,
+                                                          const double *__restrict__ dinv,
+                                                          double *x, double *r, double *z,
+                                                          double *p, double *part, double *sc) {
+  double rz = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i], zi = dinv[i] * bi;
+    x[i] = 0.0;
+    r[i] = bi;
+    z[i] = zi;
+    p[i] = zi;
+    rz += bi * zi;
+    bb += bi * bi;
+  }
+  block_partial(rz, slot(part, P_RZ0));
+  block_partial(bb, slot(part, P_BB));
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc[S_PCG_DONE] = 0.0;
+    sc[S_PCG_IT] = 0.0;
+    sc[S_PCG_BAD] = 0.0;
+  }
+}
+
+// q = S p and the partials of p . q; skipped once converged.
+template <int L>
+__global__ void __launch_bounds__(256) k_pcg_spmv(int64_t rows, const int64_t *__restrict__ rp,
+                                                  const int32_t *__restrict__ col,
+                                                  const double *__restrict__ val,
+                                                  const double *__restrict__ p, double *q,
+                                                  double *part, const double *sc) {
+  if (block_done(sc)) return;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % L;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / L;
+  double dacc = 0.0;
+  for (int64_t base = warp * (32 / L); base < rows; base += stride) {
+    const int64_t r = base + lane / L;
+    const bool ok = r < rows;
+    double s = 0.0;
+    if (ok) {
+      const int64_t b = rp[r], e = rp[r + 1];
+      for (int64_t k = b + sub; k < e; k += L) s += val[k] * __ldg(p + col[k]);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, L);
+    if (ok && sub == 0) {
+      q[r] = s;
+      dacc += s * p[r];
+    }
+  }
+  block_partial(dacc, slot(part, P_PQ));
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_pcg_update(int64_t n, double *x, double *r, double *z,
+                                                            const double *__restrict__ p,
+                                                            const double *__restrict__ q,
+                                                            const double *__restrict__ dinv,
+                                                            double *part, int cur, int nb, int nbs,
+                                                            double *sc) {
+  if (block_done(sc)) return;
+  const double rz = sum_partials(slot(part, cur), nb);
+  const double pq = sum_partials(slot(part, P_PQ), nbs);
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sc[S_PCG_BAD] = 1.0;
+      sc[S_PCG_DONE] = 1.0;
+    }
+    return;
+  }
+  const double alpha = rz / pq;
+  double rr = 0.0, rzn = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    const double zi = dinv[i] * ri;
+    z[i] = zi;
+    rr += ri * ri;
+    rzn += ri * zi;
+  }
+  block_partial(rr, slot(part, P_RR));
+  block_partial(rzn, slot(part, cur ^ 1));
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_pcg_dir(int64_t n, const double *__restrict__ z,
+                                                         double *p, double *part, int cur, int nb,
+                                                         double tol2, int it, double *sc) {
+  if (block_done(sc)) return;
+  const double rr = sum_partials(slot(part, P_RR), nb);
+  const double bb = sum_partials(slot(part, P_BB), nb);
+  if (!isfinite(rr)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sc[S_PCG_BAD] = 2.0;
+      sc[S_PCG_DONE] = 1.0;
+    }
+    return;
+  }
+  if (rr <= tol2 * bb) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sc[S_PCG_DONE] = 1.0;
+      sc[S_PCG_IT] = (double)it;
+    }
+    return;
+  }
+  const double beta = sum_partials(slot(part, cur ^ 1), nb) / sum_partials(slot(part, cur), nb);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[S_PCG_IT] = (double)it;
+}
+
+// bb == 0: the solution is zero.
+__global__ void k_pcg_zero_check(double *part, int nb, double *sc) {
+  const double bb = sum_partials(slot(part, P_BB), nb);
+  if (threadIdx.x == 0 && bb == 0.0) sc[S_PCG_DONE] = 1.0;
+}
+
+// Solve S x = b (length n_p) to relative residual rtol; returns iterations.
+static vem_status pcg_solve(vem_handle *h, const double *b, double *x, double *wk, int *iters) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n_p;
+  double *r = wk, *z = wk + n, *p = wk + 2 * n, *q = wk + 3 * n;
+  const int nb = nblocks_vec(n);
+  const int nbs = spmv_nblocks(n, h->s_lanes);
+  double *sc = h->scal;
+  count_launch(); k_pcg_init<<<nb, kRedThreads, 0, s>>>(n, b, h->s_dinv, x, r, z, p, h->part, sc);
+  count_launch(); k_pcg_zero_check<<<1, kRedThreads, 0, s>>>(h->part, nb, sc);
+  const double tol2 = h->opt.inner_rtol * h->opt.inner_rtol;
+  const int maxit = h->opt.inner_maxit;
+  const int chunk = 8;
+  int it = 0;
+  while (it < maxit) {
+    const int end = it + chunk < maxit ? it + chunk : maxit;
+    for (; it < end; ++it) {
+      const int cur = it & 1;   // rz of this iteration lives in slot cur
+      switch (h->s_lanes) {
+        case 4: count_launch(); k_pcg_spmv<4><<<nbs, 256, 0, s>>>(n, h->s_rp, h->s_col, h->s_val, p, q, h->part, sc); break;
+        case 8: count_launch(); k_pcg_spmv<8><<<nbs, 256, 0, s>>>(n, h->s_rp, h->s_col, h->s_val, p, q, h->part, sc); break;
+        case 16: count_launch(); k_pcg_spmv<16><<<nbs, 256, 0, s>>>(n, h->s_rp, h->s_col, h->s_val, p, q, h->part, sc); break;
+        default: count_launch(); k_pcg_spmv<32><<<nbs, 256, 0, s>>>(n, h->s_rp, h->s_col, h->s_val, p, q, h->part, sc); break;
+      }
+      count_launch(); k_pcg_update<<<nb, kRedThreads, 0, s>>>(n, x, r, z, p, q, h->s_dinv, h->part, P_RZ0 + cur, nb,
+                                               nbs, sc);
+      count_launch(); k_pcg_dir<<<nb, kRedThreads, 0, s>>>(n, z, p, h->part, P_RZ0 + cur, nb, tol2, it + 1, sc);
+    }
+    VEM_CUDA(h, cudaGetLastError());
+    VEM_CUDA(h, cudaMemcpyAsync(h->h_scal, sc, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+    if (h->h_scal[S_PCG_DONE] != 0.0) break;
+  }
+  if (h->h_scal[S_PCG_BAD] != 0.0)
+    return fail(h, h->h_scal[S_PCG_BAD] == 2.0 ? VEM_ERR_NONFINITE : VEM_ERR_BREAKDOWN,
+                "inner PCG breakdown");
+  *iters = (int)h->h_scal[S_PCG_IT];
+  if (h->h_scal[S_PCG_DONE] == 0.0) *iters = maxit;   // cap reached: use the iterate
+  if (debug_on()) fprintf(stderr, "[vem] pcg n=%lld iters=%d done=%g\n", (long long)n, *iters, h->h_scal[S_PCG_DONE]);
+  return VEM_OK;
+}
+
+// --------------------------------------------------------- vector ops -----
+__global__ void k_residual(int64_t n, const double *__restrict__ b, const double *__restrict__ Ax,
+                           double *r, double *part_r2, double *part_b2) {
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = b[i] - Ax[i];
+    r[i] = ri;
+    rr += ri * ri;
+    bb += b[i] * b[i];
+  }
+  block_partial(rr, part_r2);
+  block_partial(bb, part_b2);
+}
+
+__global__ void k_read_sum(const double *part, int nb, double *out) {
+  const double v = sum_partials(part, nb);
+  if (threadIdx.x == 0) *out = v;
+}
+
+// z_u = v_u / diag(M) (first n_u entries) and the partial of v_u . z_u
+__global__ void k_diag_scale(int64_t nu, const double *__restrict__ v, const double *__restrict__ dM,
+                             double *z, double *part) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = v[i] / dM[i];
+    z[i] = zi;
+    s += v[i] * zi;
+  }
+  if (part) block_partial(s, part);
+}
+
+// Block upper-triangular flux part: z_u = (v_u - B^T z_p) / diag(M), with
+// B^T z_p gathered per face from its (at most two) cells.
+__global__ void k_tri_flux(int64_t nf, int nfd, int64_t n_u, const double *__restrict__ v,
+                           const double *__restrict__ dM, const int32_t *__restrict__ f_cell,
+                           const double *__restrict__ bt, const double *__restrict__ zp, double *z) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_u;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double t = v[r];
+    if (r < nfd * nf && r % nfd == 0) {
+      const int64_t f = r / nfd;
+      const int32_t c0 = f_cell[2 * f], c1 = f_cell[2 * f + 1];
+      double g = bt[2 * f] * zp[c0];
+      if (c1 >= 0) g += bt[2 * f + 1] * zp[c1];
+      t -= g;
+    }
+    z[r] = t / dM[r];
+  }
+}
+
+__global__ void k_negate(int64_t n, double *x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = -x[i];
+}
+
+// ------------------------------------------------------------ MINRES -----
+__global__ void k_mr_init(double *sc, const double *part, int nbu, int nbp) {
+  const double g2 = sum_partials(slot((double *)part, P_G2U), nbu) + sum_partials(slot((double *)part, P_G2P), nbp);
+  if (threadIdx.x == 0) {
+    double *m = sc + S_MR;
+    const double g = sqrt(g2 > 0.0 ? g2 : 0.0);
+    m[MR_GOLD] = 1.0;
+    m[MR_G] = g;
+    m[MR_COLD] = 1.0;
+    m[MR_C] = 1.0;
+    m[MR_SOLD] = 0.0;
+    m[MR_S] = 0.0;
+    m[MR_ETA] = g;
+    m[MR_IG] = g > 0.0 ? 1.0 / g : 0.0;
+    m[MR_BAD] = (g2 >= 0.0 && isfinite(g2)) ? 0.0 : 1.0;
+  }
+}
+
+__global__ void k_scale_by(int64_t n, double *x, const double *factor) {
+  const double f = *factor;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= f;
+}
+
+// v_new = Az - (delta/gamma) v - (gamma/gamma_old) v_old, written over v_old.
+__global__ void __launch_bounds__(kRedThreads) k_mr_lanczos(int64_t n, const double *__restrict__ Az,
+                                                            const double *__restrict__ v, double *vold,
+                                                            const double *part, int nbd, const double *sc) {
+  const double delta = sum_partials(slot((double *)part, P_DELTA), nbd);
+  const double *m = sc + S_MR;
+  const double a = delta / m[MR_G], bcoef = m[MR_G] / m[MR_GOLD];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    vold[i] = Az[i] - a * v[i] - bcoef * vold[i];
+}
+
+__global__ void k_mr_scalars(double *sc, const double *part, int nbd, int nbu, int nbp) {
+  const double delta = sum_partials(slot((double *)part, P_DELTA), nbd);
+  const double g2 = sum_partials(slot((double *)part, P_G2U), nbu) + sum_partials(slot((double *)part, P_G2P), nbp);
+  if (threadIdx.x != 0) return;
+  double *m = sc + S_MR;
+  if (!(g2 >= 0.0) || !isfinite(g2) || !isfinite(delta)) {
+    m[MR_BAD] = 1.0;
+    return;
+  }
+  const double gn = sqrt(g2);
+  const double g = m[MR_G], c = m[MR_C], cold = m[MR_COLD], s = m[MR_S], sold = m[MR_SOLD];
+  const double a0 = c * delta - cold * s * g;
+  const double a1 = hypot(a0, gn);
+  const double a2 = s * delta + cold * c * g;
+  const double a3 = sold * g;
+  const double cn = a0 / a1, sn = gn / a1;
+  m[MR_A1] = a1;
+  m[MR_A2] = a2;
+  m[MR_A3] = a3;
+  m[MR_CETA] = cn * m[MR_ETA];
+  m[MR_ETA] = -sn * m[MR_ETA];
+  m[MR_GOLD] = g;
+  m[MR_G] = gn;
+  m[MR_IG] = gn > 0.0 ? 1.0 / gn : 0.0;
+  m[MR_COLD] = c;
+  m[MR_C] = cn;
+  m[MR_SOLD] = s;
+  m[MR_S] = sn;
+  if (!(a1 > 0.0)) m[MR_BAD] = 2.0;
+}
+
+// w_new = (z - a3 w_old - a2 w)/a1 over w_old; x += c eta w_new
+__global__ void k_mr_update(int64_t n, const double *__restrict__ z, double *wold,
+                            const double *__restrict__ w, double *x, const double *sc) {
+  const double *m = sc + S_MR;
+  const double ia1 = 1.0 / m[MR_A1], a2 = m[MR_A2], a3 = m[MR_A3], ce = m[MR_CETA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double wn = (z[i] - a3 * wold[i] - a2 * w[i]) * ia1;
+    wold[i] = wn;
+    x[i] += ce * wn;
+  }
+}
+
+// ------------------------------------------------------------ FGMRES -----
+constexpr int kMD = 8;   // vectors per multi-dot pass
+
+// partials of V_i . w for i in [i0, i0 + cnt), cnt <= kMD
+__global__ void __launch_bounds__(kRedThreads) k_multidot(int64_t n, const double *__restrict__ V,
+                                                          int i0, int cnt,
+                                                          const double *__restrict__ w, double *part) {
+  double acc[kMD];
+#pragma unroll
+  for (int t = 0; t < kMD; ++t) acc[t] = 0.0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const double wr = w[r];
+#pragma unroll
+    for (int t = 0; t < kMD; ++t)
+      if (t < cnt) acc[t] += V[(size_t)(i0 + t) * n + r] * wr;
+  }
+#pragma unroll
+  for (int t = 0; t < kMD; ++t)
+    if (t < cnt) block_partial(acc[t], slot(part, P_H0 + i0 + t));
+}
+
+// out[i] = sum of the partials of slot P_H0 + i, one block per i
+__global__ void k_multidot_fin(const double *part, int nb, double *out) {
+  const double v = sum_partials(slot((double *)part, P_H0 + blockIdx.x), nb);
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
+// w += sgn * sum_i c[i] V_i  (i < cnt), optional partial of ||w||^2
+__global__ void __launch_bounds__(kRedThreads) k_multiaxpy(int64_t n, const double *__restrict__ V, int cnt,
+                                                           const double *__restrict__ c, double sgn,
+                                                           double *w, double *part_nrm) {
+  __shared__ double cs[260];
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) cs[i] = sgn * c[i];
+  __syncthreads();
+  double nn = 0.0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double t = w[r];
+    for (int i = 0; i < cnt; ++i) t += cs[i] * V[(size_t)i * n + r];
+    w[r] = t;
+    nn += t * t;
+  }
+  if (part_nrm) block_partial(nn, part_nrm);
+}
+
+struct GmLayout {
+  int m;
+  __host__ __device__ int H(int i, int j) const { return S_GM + 16 + i * m + j; }
+  __host__ __device__ int CS(int i) const { return S_GM + 16 + (m + 1) * m + i; }
+  __host__ __device__ int SN(int i) const { return CS(m) + i; }
+  __host__ __device__ int G(int i) const { return SN(m) + i; }
+  __host__ __device__ int Y(int i) const { return G(m + 1) + i; }
+  __host__ __device__ int H1(int i) const { return Y(m) + i; }
+  __host__ __device__ int H2(int i) const { return H1(m + 1) + i; }
+  __host__ __device__ int end() const { return H2(m + 1); }
+};
+enum { GM_BETA = S_GM, GM_IBETA, GM_EST, GM_IHN, GM_BAD };
+
+__global__ void k_gm_start(double *sc, const double *part, int nb, GmLayout L) {
+  const double r2 = sum_partials(slot((double *)part, P_R2), nb);
+  if (threadIdx.x != 0) return;
+  const double beta = sqrt(r2);
+  sc[GM_BETA] = beta;
+  sc[GM_IBETA] = beta > 0.0 ? 1.0 / beta : 0.0;
+  sc[GM_EST] = beta;
+  sc[GM_BAD] = isfinite(r2) ? 0.0 : 1.0;
+  for (int i = 0; i <= L.m; ++i) sc[L.G(i)] = 0.0;
+  sc[L.G(0)] = beta;
+}
+
+// H[:, j] = h1 + h2, H[j+1, j] = ||w||, apply the rotations, new rotation
+__global__ void k_gm_givens(double *sc, const double *part, int nb, int j, GmLayout L) {
+  const double w2 = sum_partials(slot((double *)part, P_NRM), nb);
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i <= j; ++i) sc[L.H(i, j)] = sc[L.H1(i)] + sc[L.H2(i)];
+  const double hn = sqrt(w2 > 0.0 ? w2 : 0.0);
+  sc[GM_IHN] = hn > 0.0 ? 1.0 / hn : 0.0;
+  for (int i = 0; i < j; ++i) {
+    const double a = sc[L.H(i, j)], b = sc[L.H(i + 1, j)];
+    const double c = sc[L.CS(i)], s = sc[L.SN(i)];
+    sc[L.H(i, j)] = c * a + s * b;
+    sc[L.H(i + 1, j)] = -s * a + c * b;
+  }
+  const double a = sc[L.H(j, j)];
+  const double den = hypot(a, hn);
+  if (!(den > 0.0) || !isfinite(den) || !isfinite(w2)) {
+    sc[GM_BAD] = 1.0;
+    return;
+  }
+  const double c = a / den, s = hn / den;
+  sc[L.CS(j)] = c;
+  sc[L.SN(j)] = s;
+  sc[L.H(j, j)] = den;
+  const double gj = sc[L.G(j)];
+  sc[L.G(j + 1)] = -s * gj;
+  sc[L.G(j)] = c * gj;
+  sc[GM_EST] = fabs(sc[L.G(j + 1)]);
+}
+
+// back substitution H y = g for the leading k x k upper triangle
+__global__ void k_gm_solve(double *sc, int k, GmLayout L) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double t = sc[L.G(i)];
+    for (int q = i + 1; q < k; ++q) t -= sc[L.H(i, q)] * sc[L.Y(q)];
+    sc[L.Y(i)] = t / sc[L.H(i, i)];
+  }
+}
+
+// ------------------------------------------------------- preconditioner ---
+// z = P^{-1} v for the block preconditioner (diag or upper triangular).
+// wk: 4 n_p PCG work vectors.  If part_g2 != nullptr (MINRES) also leaves
+// the partials of v.z in slots P_G2U (flux part) and P_G2P (pressure part).
+static vem_status precond(vem_handle *h, const double *v, double *z, double *wk, int *inner,
+                          bool minres_partials) {
+  cudaStream_t s = h->stream;
+  const int64_t nu = h->n_u, np = h->n_p;
+  int it = 0;
+  if (h->opt.precond == VEM_PREC_BLOCK_DIAG) {
+    if (!minres_partials)
+      count_launch(); k_diag_scale<<<nblocks_vec(nu), kRedThreads, 0, s>>>(nu, v, h->diagM, z, nullptr);
+    VEM_TRY(pcg_solve(h, v + nu, z + nu, wk, &it));
+  } else {
+    VEM_TRY(pcg_solve(h, v + nu, z + nu, wk, &it));
+    count_launch(); k_negate<<<grid_for(np, 256), 256, 0, s>>>(np, z + nu);
+    count_launch(); k_tri_flux<<<grid_for(nu, 256), 256, 0, s>>>(h->nf, h->nfd, nu, v, h->diagM, h->f_cell,
+                                                  h->bt_face, z + nu, z);
+  }
+  VEM_CUDA(h, cudaGetLastError());
+  if (minres_partials)
+    dot_partials(s, np, v + nu, z + nu, slot(h->part, P_G2P));
+  *inner += it;
+  return VEM_OK;
+}
+
+// true relative residual ||b - A x|| / ||b|| (synchronises)
+static vem_status true_relres(vem_handle *h, const double *x, double *tmp, double *rel) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
+  spmv(s, n, h->a_rp, h->a_col, h->a_val, x, tmp, h->a_lanes);
+  const int nb = nblocks_vec(n);
+  count_launch(); k_residual<<<nb, kRedThreads, 0, s>>>(n, h->rhs, tmp, tmp, slot(h->part, P_R2), slot(h->part, P_B2));
+  count_launch(); k_read_sum<<<1, kRedThreads, 0, s>>>(slot(h->part, P_R2), nb, h->scal + S_R2);
+  count_launch(); k_read_sum<<<1, kRedThreads, 0, s>>>(slot(h->part, P_B2), nb, h->scal + S_B2);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_CUDA(h, cudaMemcpyAsync(h->h_scal + S_R2, h->scal + S_R2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  const double r2 = h->h_scal[S_R2], b2 = h->h_scal[S_B2];
+  if (!std::isfinite(r2)) return fail(h, VEM_ERR_NONFINITE, "non-finite residual");
+  *rel = b2 > 0.0 ? std::sqrt(r2 / b2) : std::sqrt(r2);
+  return VEM_OK;
+}
+
+// ------------------------------------------------------------- drivers ---
+static vem_status ensure_work(vem_handle *h, size_t n) {
+  if (h->work_n >= n) return VEM_OK;
+  dfree(h, h->work);
+  h->work = nullptr;
+  h->work_n = 0;
+  VEM_TRY(dalloc_n(h, &h->work, n));
+  h->work_n = n;
+  return VEM_OK;
+}
+
+static vem_status run_minres(vem_handle *h, double *x, vem_stats *st) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n, nu = h->n_u, np = h->n_p;
+  VEM_TRY(ensure_work(h, 8 * (size_t)n + 4 * (size_t)np));
+  double *vA = h->work, *vB = vA + n, *z = vB + n, *zn = z + n, *Az = zn + n, *wA = Az + n,
+         *wB = wA + n, *tmp = wB + n, *pw = tmp + n;
+  double *vold = vA, *v = vB, *wold = wA, *w = wB;
+  int inner = 0;
+  const int nbn = nblocks_vec(n), nbu = nblocks_vec(nu), nbp = nblocks_vec(np);
+  // v = b - A x0
+  spmv(s, n, h->a_rp, h->a_col, h->a_val, x, tmp, h->a_lanes);
+  count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, h->rhs, tmp, v, slot(h->part, P_R2), slot(h->part, P_B2));
+  VEM_CUDA(h, cudaMemsetAsync(vold, 0, sizeof(double) * n, s));
+  VEM_CUDA(h, cudaMemsetAsync(wold, 0, sizeof(double) * n, s));
+  VEM_CUDA(h, cudaMemsetAsync(w, 0, sizeof(double) * n, s));
+  count_launch(); k_diag_scale<<<nbu, kRedThreads, 0, s>>>(nu, v, h->diagM, z, slot(h->part, P_G2U));
+  VEM_TRY(precond(h, v, z, pw, &inner, true));
+  count_launch(); k_mr_init<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbu, nbp);
+  VEM_CUDA(h, cudaGetLastError());
+  double rel = 1.0;
+  VEM_TRY(true_relres(h, x, tmp, &rel));
+  VEM_CUDA(h, cudaMemcpyAsync(h->h_scal + S_MR, h->scal + S_MR, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  const double eta0 = h->h_scal[S_MR + MR_ETA];
+  int it = 0;
+  const int nbd = spmv_nblocks(n, h->a_lanes);
+  vem_status result = VEM_ERR_NOT_CONVERGED;
+  if (rel <= h->opt.rtol || eta0 == 0.0) result = VEM_OK;
+  while (result != VEM_OK && it < h->opt.maxit) {
+    ++it;
+    count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, z, h->scal + S_MR + MR_IG);
+    spmv(s, n, h->a_rp, h->a_col, h->a_val, z, Az, h->a_lanes, slot(h->part, P_DELTA));
+    count_launch(); k_mr_lanczos<<<nbn, kRedThreads, 0, s>>>(n, Az, v, vold, h->part, nbd, h->scal);
+    count_launch(); k_diag_scale<<<nbu, kRedThreads, 0, s>>>(nu, vold, h->diagM, zn, slot(h->part, P_G2U));
+    VEM_TRY(precond(h, vold, zn, pw, &inner, true));
+    count_launch(); k_mr_scalars<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbd, nbu, nbp);
+    count_launch(); k_mr_update<<<grid_for(n, 256), 256, 0, s>>>(n, z, wold, w, x, h->scal);
+    VEM_CUDA(h, cudaGetLastError());
+    // rotate: v_old <- v, v <- v_new (in v_old's buffer); w likewise
+    std::swap(vold, v);
+    std::swap(wold, w);
+    std::swap(z, zn);
+    VEM_CUDA(h, cudaMemcpyAsync(h->h_scal + S_MR, h->scal + S_MR, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+    const double *m = h->h_scal + S_MR;
+    if (debug_on())
+      fprintf(stderr, "[vem] minres it=%d eta=%.3e eta0=%.3e gamma=%.3e a1=%.3e bad=%g inner=%d\n", it,
+              m[MR_ETA], eta0, m[MR_G], m[MR_A1], m[MR_BAD], inner);
+    if (m[MR_BAD] != 0.0)
+      return fail(h, m[MR_BAD] == 1.0 ? VEM_ERR_NONFINITE : VEM_ERR_BREAKDOWN, "MINRES breakdown");
+    const bool lucky = m[MR_G] == 0.0;
+    if (std::fabs(m[MR_ETA]) <= 0.5 * h->opt.rtol * eta0 || lucky) {
+      VEM_TRY(true_relres(h, x, tmp, &rel));
+      if (rel <= h->opt.rtol) result = VEM_OK;
+      else if (lucky) break;
+    }
+  }
+  if (result != VEM_OK) VEM_TRY(true_relres(h, x, tmp, &rel));
+  st->iterations = it;
+  st->inner_iterations = inner;
+  st->relres = rel;
+  if (result != VEM_OK) return fail(h, VEM_ERR_NOT_CONVERGED, "MINRES: relres %.3e after %d iterations", rel, it);
+  return VEM_OK;
+}
+
+static vem_status run_fgmres(vem_handle *h, double *x, vem_stats *st) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n, np = h->n_p;
+  const int m = h->opt.restart;
+  GmLayout L{m};
+  if (L.end() > 8192) return fail(h, VEM_ERR_BAD_INPUT, "restart too large");
+  VEM_TRY(ensure_work(h, (size_t)(2 * m + 2) * n + 4 * (size_t)np));
+  double *V = h->work, *Z = V + (size_t)(m + 1) * n, *tmp = Z + (size_t)m * n, *pw = tmp + n;
+  int inner = 0, it = 0;
+  const int nbn = nblocks_vec(n);
+  double rel = 1.0;
+  VEM_TRY(true_relres(h, x, tmp, &rel));
+  vem_status result = rel <= h->opt.rtol ? VEM_OK : VEM_ERR_NOT_CONVERGED;
+  double bnorm = std::sqrt(h->h_scal[S_B2]);
+  if (bnorm == 0.0) bnorm = 1.0;
+  while (result != VEM_OK && it < h->opt.maxit) {
+    // V_0 = (b - A x) / beta
+    spmv(s, n, h->a_rp, h->a_col, h->a_val, x, tmp, h->a_lanes);
+    count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, h->rhs, tmp, V, slot(h->part, P_R2), slot(h->part, P_B2));
+    count_launch(); k_gm_start<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbn, L);
+    count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, V, h->scal + GM_IBETA);
+    int jd = 0;
+    for (int j = 0; j < m && it < h->opt.maxit; ++j) {
+      ++it;
+      double *Vj = V + (size_t)j * n, *Zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
+      VEM_TRY(precond(h, Vj, Zj, pw, &inner, false));
+      spmv(s, n, h->a_rp, h->a_col, h->a_val, Zj, w, h->a_lanes);
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int i0 = 0; i0 <= j; i0 += kMD) {
+          const int cnt = (j + 1 - i0) < kMD ? (j + 1 - i0) : kMD;
+          count_launch(); k_multidot<<<nbn, kRedThreads, 0, s>>>(n, V, i0, cnt, w, h->part);
+        }
+        double *hc = h->scal + (pass == 0 ? L.H1(0) : L.H2(0));
+        count_launch(); k_multidot_fin<<<j + 1, kRedThreads, 0, s>>>(h->part, nbn, hc);
+        count_launch(); k_multiaxpy<<<nbn, kRedThreads, 0, s>>>(n, V, j + 1, hc, -1.0, w,
+                                                pass == 1 ? slot(h->part, P_NRM) : nullptr);
+      }
+      count_launch(); k_gm_givens<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbn, j, L);
+      count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, w, h->scal + GM_IHN);
+      VEM_CUDA(h, cudaGetLastError());
+      VEM_CUDA(h, cudaMemcpyAsync(h->h_scal + S_GM, h->scal + S_GM, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      VEM_CUDA(h, cudaStreamSynchronize(s));
+      if (h->h_scal[GM_BAD] != 0.0) {
+        // an exactly converged Krylov space (zero new direction) is not an error
+        if (h->h_scal[GM_EST] == 0.0) { jd = j + 1; break; }
+        return fail(h, VEM_ERR_BREAKDOWN, "FGMRES breakdown at iteration %d", it);
+      }
+      jd = j + 1;
+      if (debug_on())
+        fprintf(stderr, "[vem] fgmres it=%d est=%.3e bnorm=%.3e inner=%d\n", it, h->h_scal[GM_EST], bnorm, inner);
+      if (h->h_scal[GM_EST] <= 0.5 * h->opt.rtol * bnorm) break;
+    }
+    count_launch(); k_gm_solve<<<1, 32, 0, s>>>(h->scal, jd, L);
+    count_launch(); k_multiaxpy<<<nbn, kRedThreads, 0, s>>>(n, Z, jd, h->scal + L.Y(0), 1.0, x, nullptr);
+    VEM_CUDA(h, cudaGetLastError());
+    VEM_TRY(true_relres(h, x, tmp, &rel));
+    if (rel <= h->opt.rtol) result = VEM_OK;
+  }
+  st->iterations = it;
+  st->inner_iterations = inner;
+  st->relres = rel;
+  if (result != VEM_OK) return fail(h, VEM_ERR_NOT_CONVERGED, "FGMRES: relres %.3e after %d iterations", rel, it);
+  return VEM_OK;
+}
+
+vem_status krylov_solve(vem_handle *h, double *x, vem_stats *st) {
+  if (h->opt.krylov == VEM_KRYLOV_MINRES) {
+    if (h->opt.precond != VEM_PREC_BLOCK_DIAG)
+      return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs the block-diagonal preconditioner");
+    return run_minres(h, x, st);
+  }
+  if (h->opt.krylov == VEM_KRYLOV_FGMRES) return run_fgmres(h, x, st);
+  return fail(h, VEM_ERR_BAD_INPUT, "unknown Krylov method %d", h->opt.krylov);
+}
+
+}  // namespace vem

@@ -1,0 +1,296 @@
+"""Thin ctypes binding of include/vemsolve.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/libvemsolve.so``; this
+module converts numpy arrays / torch tensors to pointers and status codes to
+exceptions.  It fails loudly when the library is missing: there is no CPU
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libvemsolve.so")
+
+VEM_OK = 0
+STATUS = {0: "VEM_OK", 1: "VEM_ERR_BAD_INPUT", 2: "VEM_ERR_DEGENERATE_MESH", 3: "VEM_ERR_NOT_CONVERGED",
+          4: "VEM_ERR_BREAKDOWN", 5: "VEM_ERR_NONFINITE", 6: "VEM_ERR_OOM", 7: "VEM_ERR_CUDA",
+          8: "VEM_ERR_UNSUPPORTED"}
+VEM_ELEMENT_E0, VEM_ELEMENT_K1 = 0, 1
+VEM_KRYLOV_MINRES, VEM_KRYLOV_FGMRES = 0, 1
+VEM_PREC_BLOCK_DIAG, VEM_PREC_BLOCK_TRI = 0, 1
+VEM_INNER_PCG = 0
+VEM_PRECISION_FP64 = 0
+VEM_QP_CELL, VEM_QP_BFACE = 0, 1
+
+
+class vem_mesh(C.Structure):
+    _fields_ = [("n_vertices", C.c_int64), ("xyz", C.c_void_p),
+                ("n_faces", C.c_int64), ("face_vtx_ptr", C.c_void_p), ("face_vtx", C.c_void_p),
+                ("n_cells", C.c_int64), ("cell_face_ptr", C.c_void_p), ("cell_face", C.c_void_p),
+                ("face_bc", C.c_void_p)]
+
+
+class vem_options(C.Structure):
+    _fields_ = [("element", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("rtol", C.c_double),
+                ("maxit", C.c_int), ("precond", C.c_int), ("inner", C.c_int), ("inner_rtol", C.c_double),
+                ("inner_maxit", C.c_int), ("precision", C.c_int), ("device_io", C.c_int)]
+
+
+class vem_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("inner_iterations", C.c_int32), ("relres", C.c_double),
+                ("t_assemble_ms", C.c_double), ("t_solve_ms", C.c_double),
+                ("n_u", C.c_int64), ("n_p", C.c_int64), ("nnz_A", C.c_int64), ("nnz_S", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class VemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes); the exported C-ABI, one entry per declaration
+_SIGS = {
+    "vem_default_options": (C.c_int, [C.POINTER(vem_options)]),
+    "vem_create": (C.c_int, [C.POINTER(vem_mesh), C.POINTER(vem_options), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vem_set_options": (C.c_int, [C.c_void_p, C.POINTER(vem_options)]),
+    "vem_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "vem_quadrature_count": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64)]),
+    "vem_quadrature_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "vem_set_coefficient": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "vem_set_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vem_set_coefficient_device": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "vem_set_source_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vem_assemble": (C.c_int, [C.c_void_p]),
+    "vem_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(vem_stats)]),
+    "vem_get_geometry": (C.c_int, [C.c_void_p] + [C.c_void_p] * 7),
+    "vem_local_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "vem_get_local": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vem_get_system": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vem_get_schur": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vem_apply_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vem_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
+    "vem_last_error": (C.c_char_p, [C.c_void_p]),
+    "vem_destroy": (None, [C.c_void_p]),
+}
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {_LIB_PATH} is missing "
+                               "(run python -m paper_1901_02330_gb300.build)")
+        L = C.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def launch_count() -> int:
+    n = C.c_int64()
+    lib().vem_launch_count(C.byref(n))
+    return n.value
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def default_options(**kw) -> vem_options:
+    o = vem_options()
+    lib().vem_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One vem_handle.  ``mesh`` has the synth.Mesh fields; stream is a
+    cudaStream_t as an int (e.g. torch.cuda.current_stream().cuda_stream)."""
+
+    def __init__(self, mesh, options: vem_options | None = None, stream: int = 0, **kw):
+        self._h = C.c_void_p()
+        self._keep = [np.ascontiguousarray(mesh.xyz, dtype=np.float64),
+                      np.ascontiguousarray(mesh.face_vtx_ptr, dtype=np.int64),
+                      np.ascontiguousarray(mesh.face_vtx, dtype=np.int32),
+                      np.ascontiguousarray(mesh.cell_face_ptr, dtype=np.int64),
+                      np.ascontiguousarray(mesh.cell_face, dtype=np.int32),
+                      np.ascontiguousarray(mesh.face_bc, dtype=np.int8)]
+        xyz, fvp, fv, cfp, cf, fbc = self._keep
+        m = vem_mesh(xyz.shape[0], _ptr(xyz), fvp.shape[0] - 1, _ptr(fvp), _ptr(fv),
+                     cfp.shape[0] - 1, _ptr(cfp), _ptr(cf), _ptr(fbc))
+        self.options = options if options is not None else default_options(**kw)
+        st = lib().vem_create(C.byref(m), C.byref(self.options), C.c_void_p(stream or None), C.byref(self._h))
+        if st != VEM_OK:
+            raise VemError(st, "vem_create failed")
+        self.n_faces = int(fvp.shape[0] - 1)
+        self.n_cells = int(cfp.shape[0] - 1)
+        self.cell_face_ptr = cfp.copy()
+
+    # -- status handling
+    def _check(self, st, what=""):
+        if st != VEM_OK:
+            msg = lib().vem_last_error(self._h)
+            raise VemError(st, (msg.decode() if msg else "") or what)
+
+    def close(self):
+        if self._h:
+            lib().vem_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- C-ABI calls
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            setattr(self.options, k, v)
+        self._check(lib().vem_set_options(self._h, C.byref(self.options)))
+
+    def sizes(self):
+        nu, np_ = C.c_int64(), C.c_int64()
+        self._check(lib().vem_sizes(self._h, C.byref(nu), C.byref(np_)))
+        return nu.value, np_.value
+
+    def quadrature_points(self, which: int) -> np.ndarray:
+        n = C.c_int64()
+        self._check(lib().vem_quadrature_count(self._h, which, C.byref(n)))
+        out = np.zeros((n.value, 3))
+        if n.value:
+            self._check(lib().vem_quadrature_points(self._h, which, _ptr(out)))
+        return out
+
+    def set_coefficient(self, K):
+        if hasattr(K, "data_ptr"):
+            self._check(lib().vem_set_coefficient_device(self._h, _ptr(K)))
+        else:
+            K = np.ascontiguousarray(K, dtype=np.float64)
+            assert K.shape == (self.n_cells,)
+            self._check(lib().vem_set_coefficient(self._h, _ptr(K)))
+
+    def set_source(self, f_qp=None, gD_qp=None):
+        dev = any(hasattr(a, "data_ptr") for a in (f_qp, gD_qp) if a is not None)
+        if dev:
+            self._check(lib().vem_set_source_device(self._h, _ptr(f_qp), _ptr(gD_qp)))
+        else:
+            f = None if f_qp is None else np.ascontiguousarray(f_qp, dtype=np.float64)
+            g = None if gD_qp is None else np.ascontiguousarray(gD_qp, dtype=np.float64)
+            self._check(lib().vem_set_source(self._h, _ptr(f), _ptr(g)))
+
+    def set_data(self, f=None, gD=None):
+        """Evaluate callables f, gD at the library's quadrature points."""
+        fq = f(self.quadrature_points(VEM_QP_CELL)) if f is not None else None
+        pb = self.quadrature_points(VEM_QP_BFACE)
+        gq = gD(pb) if (gD is not None and pb.shape[0]) else None
+        self.set_source(fq, gq)
+
+    def assemble(self):
+        self._check(lib().vem_assemble(self._h))
+
+    def solve(self, x0=None, u_out=None, p_out=None, allow_not_converged=False):
+        """Host I/O (numpy) unless options.device_io, then torch/device arrays."""
+        nu, np_ = self.sizes()
+        if u_out is None:
+            u_out = np.zeros(nu)
+        if p_out is None:
+            p_out = np.zeros(np_)
+        st = vem_stats()
+        x0p = None
+        if x0 is not None:
+            x0 = x0 if hasattr(x0, "data_ptr") else np.ascontiguousarray(x0, dtype=np.float64)
+            x0p = _ptr(x0)
+        code = lib().vem_solve(self._h, x0p, _ptr(u_out), _ptr(p_out), C.byref(st))
+        if not (code == 3 and allow_not_converged):
+            self._check(code)
+        return u_out, p_out, st.as_dict()
+
+    def geometry(self):
+        nf, nc = self.n_faces, self.n_cells
+        out = dict(face_area=np.zeros(nf), face_centroid=np.zeros((nf, 3)), face_normal=np.zeros((nf, 3)),
+                   face_diam=np.zeros(nf), cell_volume=np.zeros(nc), cell_centroid=np.zeros((nc, 3)),
+                   cell_diam=np.zeros(nc))
+        self._check(lib().vem_get_geometry(self._h, *[_ptr(out[k]) for k in
+                                                      ("face_area", "face_centroid", "face_normal", "face_diam",
+                                                       "cell_volume", "cell_centroid", "cell_diam")]))
+        return out
+
+    def local_matrices(self):
+        """List of (M_P, B_P) per cell in the cell's local DOF order."""
+        mt, bt = C.c_int64(), C.c_int64()
+        self._check(lib().vem_local_size(self._h, C.byref(mt), C.byref(bt)))
+        M = np.zeros(mt.value)
+        off = np.zeros(self.n_cells + 1, dtype=np.int64)
+        B = np.zeros(bt.value)
+        self._check(lib().vem_get_local(self._h, _ptr(M), _ptr(off), _ptr(B)))
+        nfd = 3 if self.options.element == VEM_ELEMENT_K1 else 1
+        nid = 3 if self.options.element == VEM_ELEMENT_K1 else 0
+        out = []
+        for c in range(self.n_cells):
+            k = int(self.cell_face_ptr[c + 1] - self.cell_face_ptr[c])
+            nl = nfd * k + nid
+            b0 = nfd * int(self.cell_face_ptr[c]) + nid * c
+            out.append((M[off[c]:off[c] + nl * nl].reshape(nl, nl), B[b0:b0 + nl]))
+        return out
+
+    def system(self):
+        """(A as scipy CSR [M B^T; B 0], rhs [g; F])."""
+        import scipy.sparse as sp
+        nu, np_ = self.sizes()
+        n = nu + np_
+        rp = np.zeros(n + 1, dtype=np.int64)
+        self._check(lib().vem_get_system(self._h, _ptr(rp), None, None, None))
+        col = np.zeros(rp[-1], dtype=np.int32)
+        val = np.zeros(rp[-1])
+        rhs = np.zeros(n)
+        self._check(lib().vem_get_system(self._h, _ptr(rp), _ptr(col), _ptr(val), _ptr(rhs)))
+        return sp.csr_matrix((val, col, rp), shape=(n, n)), rhs
+
+    def schur(self):
+        import scipy.sparse as sp
+        nu, np_ = self.sizes()
+        rp = np.zeros(np_ + 1, dtype=np.int64)
+        self._check(lib().vem_get_schur(self._h, _ptr(rp), None, None, None))
+        col = np.zeros(rp[-1], dtype=np.int32)
+        val = np.zeros(rp[-1])
+        dM = np.zeros(nu)
+        self._check(lib().vem_get_schur(self._h, _ptr(rp), _ptr(col), _ptr(val), _ptr(dM)))
+        return sp.csr_matrix((val, col, rp), shape=(np_, np_)), dM
+
+    def apply_device(self, x, y):
+        self._check(lib().vem_apply_device(self._h, _ptr(x), _ptr(y)))
