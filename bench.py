@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_CELLS, help="cells per side (default 128)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="one step only (for an ncu launch list); prints a short JSON line")
     return ap.parse_args()
 
 
@@ -203,6 +205,12 @@ def run_ours(a):
         s.assemble()
         return s.solve(u_out=u, p_out=p)[2]
 
+    if a.profile:
+        st = step()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": st}))
+        s.close()
+        return 0
     for _ in range(a.warmup):
         st = step()
     torch.cuda.synchronize()
