@@ -201,6 +201,36 @@ vem_status vem_get_schur(vem_handle *h, int64_t *row_ptr, int32_t *col, double *
 /* y = [M B^T; B 0] x on the device (x, y device arrays of length n_u + n_p). */
 vem_status vem_apply_device(vem_handle *h, const double *x_dev, double *y_dev);
 
+/* Residual norm without any device allocation.  (The paper has no
+ * counterpart: this is a service for callers that must not let a library
+ * allocate device memory -- frameworks that own all device memory through
+ * their own pool or budget, where a foreign cudaMalloc can fail or fragment
+ * the pool, and latency-sensitive pipelines where cudaFree's implicit
+ * device-wide synchronisation would stall other streams.)
+ *
+ * For a CSR matrix A (rows rows, int64 row_ptr[rows + 1], int32 col, double
+ * val) and vectors x, b, computes out[0] = ||b - A x||_2, out[1] = ||b||_2 and
+ * out[2] = out[0] / out[1] (out[0] when b = 0).  Every pointer is a DEVICE
+ * pointer owned by the caller; the work is enqueued on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream) and the call returns without
+ * synchronising.  It is the same reduction the solver uses for its true
+ * residual, e.g. on vem_get_system's matrix and right-hand side with
+ * x = (u, -p).
+ *
+ * Scratch: a static device array of 1 MiB (one pair of partial sums per
+ * 2048-row tile), present on every GPU that loads the library until the
+ * process exits.  rows above 134,217,728 (65,536 tiles) give
+ * VEM_ERR_BAD_INPUT.  The first call on a device resolves the array's
+ * device address with that device current; make that first call before any
+ * stream capture.  Each call overwrites every partial it reads, so nothing
+ * needs clearing, but all calls share the one array: calls that overlap on
+ * the GPU (other streams, other host threads) race and must be ordered by
+ * the caller.  No cudaMalloc, cudaFree or allocating library routine is
+ * called. */
+vem_status vem_residual_norm_noalloc(int64_t rows, const int64_t *row_ptr, const int32_t *col,
+                                     const double *val, const double *x, const double *b,
+                                     double *out, void *cuda_stream);
+
 /* Number of CUDA kernel launches the library has issued in this process
  * (all handles), for accounting the work of a timed region. */
 vem_status vem_launch_count(int64_t *n);

@@ -77,6 +77,8 @@ _SIGS = {
     "vem_get_system": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_get_schur": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_apply_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vem_residual_norm_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
     "vem_last_error": (C.c_char_p, [C.c_void_p]),
     "vem_destroy": (None, [C.c_void_p]),
@@ -103,6 +105,18 @@ def launch_count() -> int:
     n = C.c_int64()
     lib().vem_launch_count(C.byref(n))
     return n.value
+
+
+def residual_norm_noalloc(row_ptr, col, val, x, b, out, stream: int = 0) -> None:
+    """vem_residual_norm_noalloc on device tensors: out[0] = ||b - A x||,
+    out[1] = ||b||, out[2] = their ratio.  Allocates nothing on the device
+    (for callers whose device memory is owned by another allocator); the
+    result is ready when the stream reaches it."""
+    rows = int(row_ptr.shape[0]) - 1
+    st = lib().vem_residual_norm_noalloc(rows, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(x), _ptr(b),
+                                         _ptr(out), C.c_void_p(stream or None))
+    if st != VEM_OK:
+        raise VemError(st, "vem_residual_norm_noalloc")
 
 
 def library_path() -> str:
