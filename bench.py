@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_CELLS, help="cells per side (default 128)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inner-rtol", type=float, default=1e-8, help="inner Jacobi-PCG tolerance")
+    ap.add_argument("--element", default="k1", choices=["k1", "e0"])
     ap.add_argument("--profile", action="store_true",
                     help="one step only (for an ncu launch list); prints a short JSON line")
     return ap.parse_args()
@@ -160,9 +162,34 @@ class Clocks:
 
 
 def spmv_bytes(nnz, rows):
-    """Algorithmic bytes of one CSR SpMV: values + int32 columns + int64 row
-    pointers, x read once, y written once."""
-    return 12 * nnz + 8 * (rows + 1) + 16 * rows
+    """Algorithmic bytes of one SpMV with FP64 values and int32 column ids:
+    12 per nonzero, x read once and y written once (16 per row); padding of
+    the sliced-ELL layout is not counted."""
+    return 12 * nnz + 16 * rows
+
+
+def k1_cell_flops(m):
+    """FP64 operations of the paper-k=1 element kernel for one cell whose faces
+    have m[i] vertices (hand count of the kernel's formulas, FMA = 2):
+    quadrature items 4 (m_i - 2) at 102 + 36 (accumulation) each; per face
+    62; H1 inverse 250; 210 per face-DOF column and 115 per cross column;
+    W 78 (2 n_u + 2); V 12 n_u 26; M n_u (n_u + 1)/2 52, n_u = 3 nf + 3."""
+    nf = len(m)
+    items = sum(4 * (mi - 2) for mi in m)
+    nu = 3 * nf + 3
+    return (138 * items + 62 * nf + 250 + 210 * 3 * nf + 115 * 3 + 78 * (2 * nu + 2)
+            + 12 * nu * 26 + nu * (nu + 1) // 2 * 52)
+
+
+def e0_cell_flops(nf):
+    """FP64 operations of the E0 element kernel for one cell with nf faces:
+    N_f, n_f (10 per face), Q = sum n n^T (2 nf per entry, 9 entries), and per
+    upper-triangle entry 3 dot3 + N^T Q N (about 38)."""
+    return 10 * nf + 18 * nf + nf * (nf + 1) // 2 * 38
+
+
+# Nominal GB300 FP64 rate: 1.25 TFLOP/s = 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2.
+FP64_PEAK_GFLOPS = 152 * 2.070 * 2 * 2
 
 
 def run_ours(a):
@@ -189,8 +216,10 @@ def run_ours(a):
     # independent problems per rank (weak scaling): each rank solves its own copy
     mesh = hex_mesh(a.n)
     prob = fields.sine_problem()
-    opts = dict(element=vs.VEM_ELEMENT_K1, krylov=vs.VEM_KRYLOV_FGMRES, restart=30,
-                precond=vs.VEM_PREC_BLOCK_TRI, rtol=RTOL, inner_rtol=1e-4, inner_maxit=500, maxit=1000)
+    elem = vs.VEM_ELEMENT_K1 if a.element == "k1" else vs.VEM_ELEMENT_E0
+    opts = dict(element=elem, krylov=vs.VEM_KRYLOV_FGMRES, restart=30,
+                precond=vs.VEM_PREC_BLOCK_TRI, rtol=RTOL, inner_rtol=a.inner_rtol, inner_maxit=2000,
+                maxit=1000)
 
     # ---------------- device-resident path (value) ----------------
     s = vs.Solver(mesh, stream=sid, device_io=1, **opts)
@@ -208,7 +237,7 @@ def run_ours(a):
     if a.profile:
         st = step()
         torch.cuda.synchronize()
-        print(json.dumps({"profile_step": st}))
+        print(json.dumps({"profile_step": st, "n": a.n, "element": a.element, "inner_rtol": a.inner_rtol}))
         s.close()
         return 0
     for _ in range(a.warmup):
@@ -254,6 +283,14 @@ def run_ours(a):
     spmv_gbs = sb / (spmv_ms * 1e-3) / 1e9
     s.close()
     del x, y
+    # element kernel: timed by the library with events on its stream, every step
+    el_ms = statistics.median([x_["t_element_ms"] for x_ in stats])
+    if a.element == "k1":
+        cell_flops = k1_cell_flops([4] * 6)
+    else:
+        cell_flops = e0_cell_flops(6)
+    el_flops = cell_flops * mesh.n_cells
+    el_gflops = el_flops / (el_ms * 1e-3) / 1e9
 
     # ---------------- end-to-end through the public API (e2e) ----------------
     def pin(arr):
@@ -300,15 +337,22 @@ def run_ours(a):
         "config": {"workload": WORKLOAD, "cells": a.n ** 3, "unknowns": n, "n_u": n_u, "n_p": n_p,
                    "element": "paper k=1 (face P1 + 3 cross moments, P0 pressure)",
                    "krylov": "FGMRES(30)", "precond": "block upper-triangular, S = B diag(M)^-1 B^T",
-                   "inner": "Jacobi-PCG rtol 1e-4", "rtol": RTOL, "K": "identity",
-                   "l2": "inputs larger than L2 (CSR of A ~%.1f GB streamed every step)" % (st["nnz_A"] * 12 / 1e9),
+                   "inner": f"Jacobi-PCG rtol {a.inner_rtol:g}", "rtol": RTOL, "K": "identity",
+                   "l2": "inputs larger than L2 (saddle matrix ~%.1f GB streamed every step)" % (st["nnz_A"] * 12 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "iterations": st["iterations"], "inner_iterations": st["inner_iterations"], "relres": st["relres"],
         "t_assemble_ms": st["t_assemble_ms"], "t_solve_ms": st["t_solve_ms"],
-        "roofline": {"kernel": "k_spmv (saddle matrix CSR, FP64)", "bound": "hbm", "achieved": spmv_gbs,
-                     "peak": hbm_peak, "unit": "GB/s", "frac": spmv_gbs / hbm_peak, "traffic": None,
-                     "algorithmic_bytes": sb, "launch_ms": spmv_ms,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800"},
+        "roofline": {"kernel": "k_elem_%s (element matrices, dominant kernel)" % a.element, "bound": "alu",
+                     "achieved": el_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                     "frac": el_gflops / FP64_PEAK_GFLOPS, "traffic": None,
+                     "algorithmic_flops": el_flops, "flops_per_cell": cell_flops, "launch_ms": el_ms,
+                     "peak_source": "FP64 nominal 1.25 TFLOP/s = 152 SM x 2070 MHz x 2 DFMA/clk x 2 (derived)"},
+        "roofline_spmv": {"kernel": "k_sell_spmv (saddle matrix, SELL-32, FP64)", "bound": "hbm",
+                          "achieved": spmv_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": spmv_gbs / hbm_peak,
+                          "traffic": None, "algorithmic_bytes": sb, "launch_ms": spmv_ms,
+                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800"},
+        "phases_ms": {"element": el_ms, "scatter": st["t_scatter_ms"], "assemble": st["t_assemble_ms"],
+                      "solve": st["t_solve_ms"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clocks,

@@ -112,7 +112,9 @@ typedef struct {
   double t_assemble_ms;      /* element kernel + scatter + Schur build      */
   double t_solve_ms;         /* Krylov solve                                */
   int64_t n_u, n_p;          /* unknown counts                              */
-  int64_t nnz_A, nnz_S;      /* stored nonzeros of [M B^T; B 0] and of S    */
+  int64_t nnz_A, nnz_S;      /* nonzeros of [M B^T; B 0] and of S           */
+  double t_element_ms;       /* of t_assemble_ms: the element kernel        */
+  double t_scatter_ms;       /* of t_assemble_ms: scatter + Schur build     */
 } vem_stats;
 
 /* Fill *opt with the defaults: E0, FGMRES(30), block-diagonal, Jacobi-PCG

@@ -161,6 +161,8 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
   VEM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   VEM_TRY(dalloc_n(h, &h->part, (size_t)kMaxSlots * kMaxBlocks));
   VEM_TRY(dalloc_n(h, &h->scal, 8192));
+  VEM_TRY(dalloc_n(h, &h->ctr, 64));
+  VEM_CUDA(h, cudaMemsetAsync(h->ctr, 0, 64 * sizeof(unsigned int), h->stream));
   VEM_CUDA(h, cudaMemsetAsync(h->scal, 0, 8192 * sizeof(double), h->stream));
   // boundary-face quadrature offsets (6 points per fan triangle)
   h->h_bqp_off.assign(h->nf + 1, 0);
@@ -183,6 +185,8 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
   VEM_CUDA(h, cudaMemsetAsync(h->gD_qp, 0, sizeof(double) * std::max<int64_t>(h->n_bqp, 1), h->stream));
   VEM_CUDA(h, cudaEventCreate(&h->ev0));
   VEM_CUDA(h, cudaEventCreate(&h->ev1));
+  VEM_CUDA(h, cudaEventCreate(&h->ev2));
+  VEM_CUDA(h, cudaEventCreate(&h->ev3));
   return geometry_build(h);
 }
 
@@ -222,15 +226,21 @@ static vem_status ensure_rhs(vem_handle *h) {
 static vem_status assemble_impl(vem_handle *h) {
   VEM_CUDA(h, cudaEventRecord(h->ev0, h->stream));
   VEM_TRY(alloc_local(h));
+  VEM_CUDA(h, cudaEventRecord(h->ev2, h->stream));
   VEM_TRY(assemble_local(h));
+  VEM_CUDA(h, cudaEventRecord(h->ev3, h->stream));
   VEM_TRY(assemble_global(h));
   h->rhs_ready = false;
   VEM_TRY(ensure_rhs(h));
   VEM_CUDA(h, cudaEventRecord(h->ev1, h->stream));
   VEM_CUDA(h, cudaEventSynchronize(h->ev1));
-  float ms = 0.f;
+  float ms = 0.f, me = 0.f, mg = 0.f;
   VEM_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  VEM_CUDA(h, cudaEventElapsedTime(&me, h->ev2, h->ev3));
+  VEM_CUDA(h, cudaEventElapsedTime(&mg, h->ev3, h->ev1));
   h->t_assemble_ms = ms;
+  h->t_element_ms = me;
+  h->t_scatter_ms = mg;
   h->assembled = true;
   return VEM_OK;
 }
@@ -318,8 +328,6 @@ vem_status vem_set_options(vem_handle *h, const vem_options *opt) {
     h->rhs = nullptr;
     dfree(h, h->diagM);
     h->diagM = nullptr;
-    dfree(h, h->a_rp);
-    h->a_rp = nullptr;
     dfree(h, h->xsol);
     h->xsol = nullptr;
     dfree(h, h->cnt_buf);
@@ -443,9 +451,11 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
   vem_stats st{};
   st.n_u = h->n_u;
   st.n_p = h->n_p;
-  st.nnz_A = h->nnz_a;
-  st.nnz_S = h->nnz_s;
+  st.nnz_A = h->A.nnz;
+  st.nnz_S = h->S.nnz;
   st.t_assemble_ms = h->t_assemble_ms;
+  st.t_element_ms = h->t_element_ms;
+  st.t_scatter_ms = h->t_scatter_ms;
   vem_status r = VEM_OK;
   do {
     const double *x0d = nullptr;
@@ -531,32 +541,28 @@ vem_status vem_get_system(vem_handle *h, int64_t *rp, int32_t *col, double *val,
   if (!h) return VEM_ERR_BAD_INPUT;
   if (!h->assembled) VEM_TRY(assemble_impl(h));
   VEM_TRY(ensure_rhs(h));
-  cudaStream_t s = h->stream;
-  if (rp) VEM_CUDA(h, cudaMemcpyAsync(rp, h->a_rp, sizeof(int64_t) * (h->n + 1), cudaMemcpyDeviceToHost, s));
-  if (col) VEM_CUDA(h, cudaMemcpyAsync(col, h->a_col, sizeof(int32_t) * h->nnz_a, cudaMemcpyDeviceToHost, s));
-  if (val) VEM_CUDA(h, cudaMemcpyAsync(val, h->a_val, sizeof(double) * h->nnz_a, cudaMemcpyDeviceToHost, s));
-  if (rhs) VEM_CUDA(h, cudaMemcpyAsync(rhs, h->rhs, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
-  VEM_CUDA(h, cudaStreamSynchronize(s));
-  return VEM_OK;
+  if (rhs) {
+    VEM_CUDA(h, cudaMemcpyAsync(rhs, h->rhs, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream));
+    VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return sell_to_host_csr(h, h->A, rp, col, val);
 }
 
 vem_status vem_get_schur(vem_handle *h, int64_t *rp, int32_t *col, double *val, double *diagM) {
   if (!h) return VEM_ERR_BAD_INPUT;
   if (!h->assembled) VEM_TRY(assemble_impl(h));
-  cudaStream_t s = h->stream;
-  if (rp) VEM_CUDA(h, cudaMemcpyAsync(rp, h->s_rp, sizeof(int64_t) * (h->nc + 1), cudaMemcpyDeviceToHost, s));
-  if (col) VEM_CUDA(h, cudaMemcpyAsync(col, h->s_col, sizeof(int32_t) * h->nnz_s, cudaMemcpyDeviceToHost, s));
-  if (val) VEM_CUDA(h, cudaMemcpyAsync(val, h->s_val, sizeof(double) * h->nnz_s, cudaMemcpyDeviceToHost, s));
-  if (diagM) VEM_CUDA(h, cudaMemcpyAsync(diagM, h->diagM, sizeof(double) * h->n_u, cudaMemcpyDeviceToHost, s));
-  VEM_CUDA(h, cudaStreamSynchronize(s));
-  return VEM_OK;
+  if (diagM) {
+    VEM_CUDA(h, cudaMemcpyAsync(diagM, h->diagM, sizeof(double) * h->n_u, cudaMemcpyDeviceToHost, h->stream));
+    VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return sell_to_host_csr(h, h->S, rp, col, val);
 }
 
 vem_status vem_apply_device(vem_handle *h, const double *x, double *y) {
   if (!h) return VEM_ERR_BAD_INPUT;
   if (!x || !y) return fail(h, VEM_ERR_BAD_INPUT, "x / y: NULL");
   if (!h->assembled) VEM_TRY(assemble_impl(h));
-  spmv(h->stream, h->n, h->a_rp, h->a_col, h->a_val, x, y, h->a_lanes);
+  spmv(h->stream, h->A, x, y);
   VEM_CUDA(h, cudaGetLastError());
   VEM_CUDA(h, cudaStreamSynchronize(h->stream));
   return VEM_OK;
@@ -579,6 +585,8 @@ void vem_destroy(vem_handle *h) {
   if (h->h_scal) cudaFreeHost(h->h_scal);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->ev2) cudaEventDestroy(h->ev2);
+  if (h->ev3) cudaEventDestroy(h->ev3);
   delete h;
 }
 

@@ -1,7 +1,7 @@
 // Global assembly (paper Sec. 4.3, global forms a_h, b_h, f_h glued across
-// cells) into one CSR matrix of the saddle-point operator [M B^T; B 0]
-// (Sec. 5), and the Schur approximation S = B diag(M)^{-1} B^T of the
-// Block-Schur preconditioner (eq. block_schur).
+// cells) into one sliced-ELL (SELL-32) matrix of the saddle-point operator
+// [M B^T; B 0] (Sec. 5), and the Schur approximation S = B diag(M)^{-1} B^T of
+// the Block-Schur preconditioner (eq. block_schur), also in SELL-32.
 //
 // Row layout: face DOF rows (nfd per face), interior DOF rows (nid per
 // cell), pressure rows (one per cell).  A face row gathers the matching
@@ -56,13 +56,28 @@ __global__ void k_rowcount(Layout L, int64_t *cnt) {
   }
 }
 
-__global__ void k_fill(Layout L, const int64_t *__restrict__ rp, int32_t *col, double *val,
-                       double *diagM) {
+// One thread per row, consecutive rows on consecutive lanes, so element j of
+// the 32 rows of a slice is written by one coalesced store.  Ghost rows of
+// the last slice and the padding of short rows get value 0, column 0.
+__global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
+                       int64_t nrows_pad, int32_t *col, double *val, double *diagM) {
   const int64_t n = L.n_u + L.nc;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows_pad;
        r += (int64_t)gridDim.x * blockDim.x) {
-    int64_t o = rp[r];
-    if (r < L.nfd * L.nf) {
+    const int64_t s0 = off[r >> 5];
+    const int width = (int)((off[(r >> 5) + 1] - s0) >> 5);
+    const int64_t lane = r & 31;
+    int j = 0;
+#define PUT(c_, v_)                          \
+  do {                                       \
+    const int64_t q_ = s0 + ((int64_t)j << 5) + lane; \
+    col[q_] = (int32_t)(c_);                 \
+    val[q_] = (v_);                          \
+    ++j;                                     \
+  } while (0)
+    if (r >= n) {
+      // ghost row
+    } else if (r < L.nfd * L.nf) {
       const int64_t f = r / L.nfd;
       const int beta = (int)(r % L.nfd);
       const int32_t c0 = L.f_cell[2 * f], c1 = L.f_cell[2 * f + 1];
@@ -76,33 +91,23 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ rp, int32_t *col, d
         M1 = L.Mloc + L.m_off[c1] + (int64_t)(l1 * L.nfd + beta) * n1;
       }
       double dg = 0.0;
-      for (int j = 0; j < n0; ++j) {
-        double v = M0[j];
-        const bool shared = (j < n0 - L.nid) && (j / L.nfd == l0);
-        if (c1 >= 0 && shared) v += M1[l1 * L.nfd + j % L.nfd];
-        if (shared && j % L.nfd == beta) dg = v;
-        col[o] = (int32_t)gcol(L, c0, j);
-        val[o] = v;
-        ++o;
+      for (int jl = 0; jl < n0; ++jl) {
+        double v = M0[jl];
+        const bool shared = (jl < n0 - L.nid) && (jl / L.nfd == l0);
+        if (c1 >= 0 && shared) v += M1[l1 * L.nfd + jl % L.nfd];
+        if (shared && jl % L.nfd == beta) dg = v;
+        PUT(gcol(L, c0, jl), v);
       }
       if (c1 >= 0) {
         const int k1 = (n1 - L.nid) / L.nfd;
-        for (int j = 0; j < n1; ++j) {
-          if (j < L.nfd * k1 && j / L.nfd == l1) continue;
-          col[o] = (int32_t)gcol(L, c1, j);
-          val[o] = M1[j];
-          ++o;
+        for (int jl = 0; jl < n1; ++jl) {
+          if (jl < L.nfd * k1 && jl / L.nfd == l1) continue;
+          PUT(gcol(L, c1, jl), M1[jl]);
         }
       }
       if (beta == 0) {
-        col[o] = (int32_t)(L.n_u + c0);
-        val[o] = L.Bloc[boff(L, c0) + l0 * L.nfd];
-        ++o;
-        if (c1 >= 0) {
-          col[o] = (int32_t)(L.n_u + c1);
-          val[o] = L.Bloc[boff(L, c1) + l1 * L.nfd];
-          ++o;
-        }
+        PUT(L.n_u + c0, L.Bloc[boff(L, c0) + l0 * L.nfd]);
+        if (c1 >= 0) PUT(L.n_u + c1, L.Bloc[boff(L, c1) + l1 * L.nfd]);
       }
       diagM[r] = dg;
     } else if (r < L.n_u) {
@@ -112,21 +117,15 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ rp, int32_t *col, d
       const int nl = nloc(L, c);
       const int jr = nl - L.nid + l;
       const double *Mr = L.Mloc + L.m_off[c] + (int64_t)jr * nl;
-      for (int j = 0; j < nl; ++j) {
-        col[o] = (int32_t)gcol(L, c, j);
-        val[o] = Mr[j];
-        ++o;
-      }
+      for (int jl = 0; jl < nl; ++jl) PUT(gcol(L, c, jl), Mr[jl]);
       diagM[r] = Mr[jr];
     } else {
       const int64_t c = r - L.n_u;
       const int k = (int)(L.cfp[c + 1] - L.cfp[c]);
-      for (int i = 0; i < k; ++i) {
-        col[o] = (int32_t)((int64_t)L.nfd * L.cf[L.cfp[c] + i]);
-        val[o] = L.Bloc[boff(L, c) + i * L.nfd];
-        ++o;
-      }
+      for (int i = 0; i < k; ++i) PUT((int64_t)L.nfd * L.cf[L.cfp[c] + i], L.Bloc[boff(L, c) + i * L.nfd]);
     }
+    while (j < width) PUT(0, 0.0);
+#undef PUT
   }
 }
 
@@ -141,33 +140,44 @@ __global__ void k_schur_count(Layout L, int64_t *cnt) {
   }
 }
 
-__global__ void k_schur_fill(Layout L, const double *__restrict__ diagM, const int64_t *__restrict__ rp,
-                             int32_t *col, double *val, double *dinv, int *err) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < L.nc;
+__global__ void k_schur_fill(Layout L, const double *__restrict__ diagM, const int64_t *__restrict__ off,
+                             int64_t nrows_pad, int32_t *col, double *val, double *dinv, int *err) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nrows_pad;
        c += (int64_t)gridDim.x * blockDim.x) {
-    int64_t o = rp[c];
-    const int64_t b = L.cfp[c];
-    const int k = (int)(L.cfp[c + 1] - b);
-    const int64_t bo = boff(L, c);
-    double dg = 0.0;
-    const int64_t od = o++;
-    for (int i = 0; i < k; ++i) {
-      const int f = L.cf[b + i];
-      const double bp = L.Bloc[bo + i * L.nfd];
-      const double mf = diagM[(int64_t)L.nfd * f];
-      dg += bp * bp / mf;
-      const int32_t c0 = L.f_cell[2 * f], c1 = L.f_cell[2 * f + 1];
-      if (c1 < 0) continue;
-      const int32_t q = (c0 == c) ? c1 : c0;
-      const int lq = (c0 == c) ? L.f_loc[2 * f + 1] : L.f_loc[2 * f];
-      col[o] = q;
-      val[o] = bp * L.Bloc[boff(L, q) + lq * L.nfd] / mf;
-      ++o;
+    const int64_t s0 = off[c >> 5];
+    const int width = (int)((off[(c >> 5) + 1] - s0) >> 5);
+    const int64_t lane = c & 31;
+    int j = 0;
+    if (c < L.nc) {
+      const int64_t b = L.cfp[c];
+      const int k = (int)(L.cfp[c + 1] - b);
+      const int64_t bo = boff(L, c);
+      double dg = 0.0;
+      j = 1;   // slot 0 holds the diagonal
+      for (int i = 0; i < k; ++i) {
+        const int f = L.cf[b + i];
+        const double bp = L.Bloc[bo + i * L.nfd];
+        const double mf = diagM[(int64_t)L.nfd * f];
+        dg += bp * bp / mf;
+        const int32_t c0 = L.f_cell[2 * f], c1 = L.f_cell[2 * f + 1];
+        if (c1 < 0) continue;
+        const int32_t q = (c0 == c) ? c1 : c0;
+        const int lq = (c0 == c) ? L.f_loc[2 * f + 1] : L.f_loc[2 * f];
+        const int64_t p = s0 + ((int64_t)j << 5) + lane;
+        col[p] = q;
+        val[p] = bp * L.Bloc[boff(L, q) + lq * L.nfd] / mf;
+        ++j;
+      }
+      col[s0 + lane] = (int32_t)c;
+      val[s0 + lane] = dg;
+      if (!(dg > 0.0) || !isfinite(dg)) atomicOr(err, DEVERR_NONFINITE);
+      dinv[c] = 1.0 / dg;
     }
-    col[od] = (int32_t)c;
-    val[od] = dg;
-    if (!(dg > 0.0) || !isfinite(dg)) atomicOr(err, DEVERR_NONFINITE);
-    dinv[c] = 1.0 / dg;
+    for (; j < width; ++j) {
+      const int64_t p = s0 + ((int64_t)j << 5) + lane;
+      col[p] = 0;
+      val[p] = 0.0;
+    }
   }
 }
 
@@ -259,6 +269,62 @@ __global__ void k_scan_apply(int64_t n, const int64_t *in, const int64_t *bsum, 
   }
 }
 
+// Per slice: 32 x (longest row) elements; row lengths copied to int32.
+__global__ void k_slice_sizes(int64_t rows, int64_t nslices, const int64_t *__restrict__ cnt,
+                              int64_t *ssz, int32_t *len) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslices;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t w = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int64_t r = 32 * s + l;
+      const int64_t c = r < rows ? cnt[r] : 0;
+      len[r] = (int32_t)c;
+      w = c > w ? c : w;
+    }
+    ssz[s] = 32 * w;
+  }
+}
+
+static vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *out,
+                              int64_t *total);
+
+// Allocate / lay out a SELL matrix from device row counts cnt[rows].
+static vem_status sell_layout(vem_handle *h, SellMat &M, int64_t rows, const int64_t *cnt) {
+  const int64_t ns = (rows + 31) / 32;
+  if (M.rows != rows) {
+    dfree(h, M.off);
+    dfree(h, M.len);
+    M.off = nullptr;
+    M.len = nullptr;
+  }
+  if (!M.off) VEM_TRY(dalloc_n(h, &M.off, (size_t)ns + 1));
+  if (!M.len) VEM_TRY(dalloc_n(h, &M.len, (size_t)ns * 32));
+  if (h->slice_buf_n < ns) {
+    dfree(h, h->slice_buf);
+    h->slice_buf = nullptr;
+    VEM_TRY(dalloc_n(h, &h->slice_buf, (size_t)ns));
+    h->slice_buf_n = ns;
+  }
+  int64_t *ssz = h->slice_buf;
+  count_launch();
+  k_slice_sizes<<<grid_for(ns, 256), 256, 0, h->stream>>>(rows, ns, cnt, ssz, M.len);
+  VEM_CUDA(h, cudaGetLastError());
+  int64_t stored = 0;
+  VEM_TRY(scan_counts(h, ns, ssz, M.off, &stored));
+  if (stored != M.stored || !M.val) {
+    dfree(h, M.col);
+    dfree(h, M.val);
+    M.col = nullptr;
+    M.val = nullptr;
+    VEM_TRY(dalloc_n(h, &M.col, (size_t)stored));
+    VEM_TRY(dalloc_n(h, &M.val, (size_t)stored));
+  }
+  M.rows = rows;
+  M.nslices = ns;
+  M.stored = stored;
+  return VEM_OK;
+}
+
 static vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *out,
                               int64_t *total) {
   cudaStream_t s = h->stream;
@@ -273,6 +339,44 @@ static vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int6
   return VEM_OK;
 }
 
+// Sum of true row lengths.
+static vem_status sell_nnz(vem_handle *h, SellMat &M) {
+  std::vector<int32_t> len(M.nslices * 32);
+  VEM_CUDA(h, cudaMemcpyAsync(len.data(), M.len, sizeof(int32_t) * len.size(), cudaMemcpyDeviceToHost, h->stream));
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  int64_t t = 0;
+  for (int32_t v : len) t += v;
+  M.nnz = t;
+  return VEM_OK;
+}
+
+vem_status sell_to_host_csr(vem_handle *h, const SellMat &M, int64_t *rp, int32_t *col, double *val) {
+  std::vector<int32_t> len(M.nslices * 32);
+  std::vector<int64_t> off(M.nslices + 1);
+  VEM_CUDA(h, cudaMemcpyAsync(len.data(), M.len, sizeof(int32_t) * len.size(), cudaMemcpyDeviceToHost, h->stream));
+  VEM_CUDA(h, cudaMemcpyAsync(off.data(), M.off, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost, h->stream));
+  std::vector<int32_t> c;
+  std::vector<double> v;
+  if (col || val) {
+    c.resize(M.stored);
+    v.resize(M.stored);
+    VEM_CUDA(h, cudaMemcpyAsync(c.data(), M.col, sizeof(int32_t) * M.stored, cudaMemcpyDeviceToHost, h->stream));
+    VEM_CUDA(h, cudaMemcpyAsync(v.data(), M.val, sizeof(double) * M.stored, cudaMemcpyDeviceToHost, h->stream));
+  }
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  int64_t o = 0;
+  for (int64_t r = 0; r < M.rows; ++r) {
+    if (rp) rp[r] = o;
+    const int64_t base = off[r >> 5] + (r & 31);
+    for (int j = 0; j < len[r]; ++j, ++o) {
+      if (col) col[o] = c[base + 32 * (int64_t)j];
+      if (val) val[o] = v[base + 32 * (int64_t)j];
+    }
+  }
+  if (rp) rp[M.rows] = o;
+  return VEM_OK;
+}
+
 vem_status assemble_global(vem_handle *h) {
   cudaStream_t s = h->stream;
   Layout L{h->nfd, h->nid, h->nf, h->nc, h->n_u, h->cf_ptr, h->cf, h->f_cell, h->f_loc,
@@ -284,48 +388,28 @@ vem_status assemble_global(vem_handle *h) {
   int64_t *cnt = h->cnt_buf;
   count_launch(); k_rowcount<<<grid_for(n, T), T, 0, s>>>(L, cnt);
   VEM_CUDA(h, cudaGetLastError());
-  if (!h->a_rp) VEM_TRY(dalloc_n(h, &h->a_rp, (size_t)n + 1));
-  int64_t nnz = 0;
-  VEM_TRY(scan_counts(h, n, cnt, h->a_rp, &nnz));
-  if (nnz >= (int64_t)1 << 62) return fail(h, VEM_ERR_UNSUPPORTED, "nnz overflow");
-  if (h->nnz_a != nnz) {
-    dfree(h, h->a_col);
-    dfree(h, h->a_val);
-    h->a_col = nullptr;
-    h->a_val = nullptr;
-    VEM_TRY(dalloc_n(h, &h->a_col, (size_t)nnz));
-    VEM_TRY(dalloc_n(h, &h->a_val, (size_t)nnz));
-    h->nnz_a = nnz;
-  }
+  VEM_TRY(sell_layout(h, h->A, n, cnt));
   if (!h->diagM) VEM_TRY(dalloc_n(h, &h->diagM, (size_t)h->n_u));
-  count_launch(); k_fill<<<grid_for(n, T), T, 0, s>>>(L, h->a_rp, h->a_col, h->a_val, h->diagM);
+  const int64_t npad = h->A.nslices * 32;
+  count_launch(); k_fill<<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, h->A.len, npad, h->A.col, h->A.val, h->diagM);
   VEM_CUDA(h, cudaGetLastError());
-  h->a_lanes = choose_lanes((double)nnz / (double)n);
   // ---- S ----
-  int64_t *scnt = h->cnt_buf;
-  count_launch(); k_schur_count<<<grid_for(h->nc, T), T, 0, s>>>(L, scnt);
+  count_launch(); k_schur_count<<<grid_for(h->nc, T), T, 0, s>>>(L, cnt);
   VEM_CUDA(h, cudaGetLastError());
-  if (!h->s_rp) VEM_TRY(dalloc_n(h, &h->s_rp, (size_t)h->nc + 1));
-  int64_t snnz = 0;
-  VEM_TRY(scan_counts(h, h->nc, scnt, h->s_rp, &snnz));
-  if (h->nnz_s != snnz) {
-    dfree(h, h->s_col);
-    dfree(h, h->s_val);
-    h->s_col = nullptr;
-    h->s_val = nullptr;
-    VEM_TRY(dalloc_n(h, &h->s_col, (size_t)snnz));
-    VEM_TRY(dalloc_n(h, &h->s_val, (size_t)snnz));
-    h->nnz_s = snnz;
-  }
+  VEM_TRY(sell_layout(h, h->S, h->nc, cnt));
   if (!h->s_dinv) VEM_TRY(dalloc_n(h, &h->s_dinv, (size_t)h->nc));
-  count_launch(); k_schur_fill<<<grid_for(h->nc, T), T, 0, s>>>(L, h->diagM, h->s_rp, h->s_col, h->s_val, h->s_dinv,
-                                                 h->d_err);
+  const int64_t spad = h->S.nslices * 32;
+  count_launch(); k_schur_fill<<<grid_for(spad, T), T, 0, s>>>(L, h->diagM, h->S.off, spad, h->S.col, h->S.val,
+                                                          h->s_dinv, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
-  h->s_lanes = choose_lanes((double)snnz / (double)h->nc);
   if (!h->bt_face) VEM_TRY(dalloc_n(h, &h->bt_face, 2 * (size_t)h->nf));
   count_launch(); k_bt_face<<<grid_for(h->nf, T), T, 0, s>>>(L, h->bt_face);
   VEM_CUDA(h, cudaGetLastError());
-  return check_device_errors(h, "global assembly");
+  VEM_TRY(check_device_errors(h, "global assembly"));
+  // true nonzero counts (for statistics)
+  VEM_TRY(sell_nnz(h, h->A));
+  VEM_TRY(sell_nnz(h, h->S));
+  return VEM_OK;
 }
 
 }  // namespace vem

@@ -39,55 +39,43 @@ int nblocks_vec(int64_t n) {
   return (int)b;
 }
 
-int choose_lanes(double avg) {
-  if (avg <= 6) return 4;
-  if (avg <= 20) return 8;
-  if (avg <= 48) return 16;
-  return 32;
+int spmv_nblocks(const SellMat &A) {
+  int64_t b = (A.nslices + 7) / 8;   // one warp per slice, 8 warps per block
+  int64_t cap = (int64_t)num_sms() * 8;
+  if (cap > kMaxBlocks) cap = kMaxBlocks;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
 }
 
-// Rows are taken in warp-uniform batches (every lane of a warp runs the same
-// number of loop trips), so the full-mask shuffles are always convergent.
-template <int L>
-__global__ void __launch_bounds__(256) k_spmv(int64_t rows, const int64_t *__restrict__ rp,
-                                              const int32_t *__restrict__ col,
-                                              const double *__restrict__ val,
-                                              const double *__restrict__ x, double *__restrict__ y,
-                                              double *dot_part) {
+// y = A x for a SELL-32 matrix: one warp per slice, one thread per row, one
+// FP64 FMA per stored element and lane (no shuffles), coalesced loads of the
+// matrix (streamed, evict-first) and read-only-path gathers of x.  With
+// dot_part, also the partials of x . (A x).
+__global__ void __launch_bounds__(256) k_sell_spmv(int64_t rows, int64_t nslices,
+                                                   const int64_t *__restrict__ off,
+                                                   const int32_t *__restrict__ col,
+                                                   const double *__restrict__ val,
+                                                   const double *__restrict__ x, double *__restrict__ y,
+                                                   double *dot_part) {
   const int lane = threadIdx.x & 31;
-  const int sub = lane % L;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / L;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double dacc = 0.0;
-  for (int64_t base = warp * (32 / L); base < rows; base += stride) {
-    const int64_t r = base + lane / L;
-    const bool ok = r < rows;
-    double s = 0.0;
-    if (ok) {
-      const int64_t b = rp[r], e = rp[r + 1];
-      for (int64_t p = b + sub; p < e; p += L) s += val[p] * __ldg(x + col[p]);
-    }
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, L);
-    if (ok && sub == 0) {
-      y[r] = s;
-      if (dot_part) dacc += s * x[r];
+  for (int64_t s = warp; s < nslices; s += nwarps) {
+    const double t = sell_row_dot(off, col, val, x, s, lane);
+    const int64_t r = 32 * s + lane;
+    if (r < rows) {
+      y[r] = t;
+      if (dot_part) dacc += t * x[r];
     }
   }
   if (dot_part) block_partial(dacc, dot_part);
 }
 
-void spmv(cudaStream_t s, int64_t rows, const int64_t *rp, const int32_t *col, const double *val,
-          const double *x, double *y, int lanes, double *dot_part) {
-  const int T = 256;
-  // a fixed grid for a given size keeps the fused dot deterministic
-  int blocks = nblocks_vec(rows * lanes);
-  switch (lanes) {
-    case 4: count_launch(); k_spmv<4><<<blocks, T, 0, s>>>(rows, rp, col, val, x, y, dot_part); break;
-    case 8: count_launch(); k_spmv<8><<<blocks, T, 0, s>>>(rows, rp, col, val, x, y, dot_part); break;
-    case 16: count_launch(); k_spmv<16><<<blocks, T, 0, s>>>(rows, rp, col, val, x, y, dot_part); break;
-    default: count_launch(); k_spmv<32><<<blocks, T, 0, s>>>(rows, rp, col, val, x, y, dot_part); break;
-  }
+void spmv(cudaStream_t s, const SellMat &A, const double *x, double *y, double *dot_part) {
+  count_launch();
+  k_sell_spmv<<<spmv_nblocks(A), 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, A.val, x, y, dot_part);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_dot(int64_t n, const double *__restrict__ x,

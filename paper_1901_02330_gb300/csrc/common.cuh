@@ -33,7 +33,18 @@ struct DBuf {
   size_t n = 0;
 };
 
-struct Handle;
+// Sliced ELL matrix (slices of 32 rows, column-major inside a slice).
+struct SellMat {
+  int64_t rows = 0, nslices = 0, stored = 0, nnz = 0;
+  int64_t *off = nullptr;   // [nslices + 1] element offset of each slice
+  int32_t *len = nullptr;   // [nslices * 32] true row lengths (0 for ghost rows)
+  int32_t *col = nullptr;   // [stored] column ids (padding: 0)
+  double *val = nullptr;    // [stored] values (padding: 0)
+};
+
+__device__ __forceinline__ int64_t sell_pos(const int64_t *off, int64_t r, int j) {
+  return off[r >> 5] + ((int64_t)j << 5) + (r & 31);
+}
 
 // Launch geometry: a multiple of the SM count.
 int num_sms();
@@ -91,6 +102,72 @@ __device__ __forceinline__ void block_partial(double v, double *part) {
     if (l == 0) part[blockIdx.x] = t;
   }
   __syncthreads();
+}
+
+// Row (32 s + lane) of a SELL-32 matrix times x: elements in column order,
+// four independent loads in flight.
+__device__ __forceinline__ double sell_row_dot(const int64_t *__restrict__ off,
+                                               const int32_t *__restrict__ col,
+                                               const double *__restrict__ val,
+                                               const double *__restrict__ x, int64_t s, int lane) {
+  const int64_t o = off[s];
+  const int w = (int)((off[s + 1] - o) >> 5);
+  const double *vp = val + o + lane;
+  const int32_t *cp = col + o + lane;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int j = 0;
+  for (; j + 3 < w; j += 4) {
+    const int32_t c0 = __ldcs(cp + 32 * j), c1 = __ldcs(cp + 32 * (j + 1));
+    const int32_t c2 = __ldcs(cp + 32 * (j + 2)), c3 = __ldcs(cp + 32 * (j + 3));
+    const double v0 = __ldcs(vp + 32 * j), v1 = __ldcs(vp + 32 * (j + 1));
+    const double v2 = __ldcs(vp + 32 * (j + 2)), v3 = __ldcs(vp + 32 * (j + 3));
+    s0 += v0 * __ldg(x + c0);
+    s1 += v1 * __ldg(x + c1);
+    s2 += v2 * __ldg(x + c2);
+    s3 += v3 * __ldg(x + c3);
+  }
+  for (; j < w; ++j) s0 += __ldcs(vp + 32 * j) * __ldg(x + __ldcs(cp + 32 * j));
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Last-block-done pattern: after each block has stored its partials, the
+// block that arrives last at *counter returns true and may read them all
+// (then sums them in a fixed order, so results stay deterministic).  It
+// resets the counter for the next use.
+__device__ __forceinline__ bool last_block(unsigned int *counter) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x - 1);
+    if (is_last) *counter = 0u;
+  }
+  __syncthreads();
+  const bool r = is_last != 0;
+  if (r) __threadfence();
+  return r;
+}
+
+// Fixed-order sum of nb partials read through L2 (for use by the last block).
+__device__ __forceinline__ double sum_partials_cg(const double *part, int nb) {
+  __shared__ double rs[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v += __ldcg(part + i);
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) rs[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = (l < (int)(blockDim.x >> 5)) ? rs[l] : 0.0;
+    t = warp_sum(t);
+    if (l == 0) rs[0] = t;
+  }
+  __syncthreads();
+  const double out = rs[0];
+  __syncthreads();
+  return out;
 }
 
 }  // namespace vem

@@ -49,7 +49,7 @@ __global__ void k_elem_e0(int64_t nc, int max_nf, const int64_t *__restrict__ cf
   for (int64_t c = (int64_t)blockIdx.x * wpb + warp; c < nc; c += (int64_t)gridDim.x * wpb) {
     const int64_t b = cfp[c];
     const int k = (int)(cfp[c + 1] - b);
-    const double vol = c_vol[c], nuc = nu[c];
+    const double vol = c_vol[c], nuc = nu[c], ivol = 1.0 / vol;
     const double3 xP = load3(c_cent, c);
     for (int i = lane; i < k; i += 32) {
       const int f = cf[b + i];
@@ -83,7 +83,7 @@ __global__ void k_elem_e0(int64_t nc, int max_nf, const int64_t *__restrict__ cf
       double nqn = 0;
       for (int p = 0; p < 3; ++p)
         for (int q = 0; q < 3; ++q) nqn += Ni[p] * Q[3 * p + q] * Nj[q];
-      const double v = nuc * (nij / vol + (i == j ? vol : 0.0) - cr + nqn / vol);
+      const double v = nuc * ((nij + nqn) * ivol + (i == j ? vol : 0.0) - cr);
       M[(int64_t)i * k + j] = v;
       M[(int64_t)j * k + i] = v;
     }
@@ -92,21 +92,45 @@ __global__ void k_elem_e0(int64_t nc, int max_nf, const int64_t *__restrict__ cf
 }
 
 // ---------------------------------------------------------------- K1 ----
+// Work per cell is dominated by FP64 instructions (GB300 issues one FP64 warp
+// instruction per 16 cycles per SM whatever the number of active lanes), so
+// the kernel spreads every phase over as many lanes as possible:
+//  * face integrals G_f = int_f m^f m^f and J_f = int_f m^f m_t (degree <= 3)
+//    by an exact degree-3 rule (Strang & Fix 4 points: centroid weight
+//    -27/48, (3/5, 1/5, 1/5) orbit weight 25/48) on the fan (v0, v_j, v_j+1)
+//    of each (convex) face, one (triangle, point) item per lane;
+//  * cell moments int_P m_t from the face integrals by Euler's identity for
+//    a homogeneous q of degree d: int_P q = (1/(d+3)) sum_f h_f int_f q, with
+//    h_f = (x_f - x_P).n_f^out constant on the planar face;
+//  * M_P = nu (|P| I + Pi^T V - |P| D Pi),  V = W Pi - |P| D^T,
+//    W = H + |P| D^T D  (two length-12 dots per entry).
 // Shared-memory layout per warp (doubles):
-//   FG[max_nf][5]   sigma, |f|, n_f
+//   FG[max_nf][8]   sigma, |f|, n_f (3), 1/|f|, h_f, -
 //   FA[max_nf][36]  face Gram G_f (6, then its inverse) and J_f[g][t] (30)
 //   MU[10] cell moments int_P m_t, H1I[16], W[144]
-//   U[...]          chunk buffer (32 x 36) / Pi (12 x nu), D (nu x 12), W Pi (12 x nu)
-// plus ints FO[max_nf + 1] (prefix of fan-triangle counts).
+//   U[...]          chunk buffer (32 x 36) / Pi (12 x nu), D (nu x 12), V (12 x nu)
+// plus ints FO[max_nf + 1] (prefix of quadrature items per face).
 __host__ __device__ inline int k1_union(int max_nf) {
   const int nu = 3 * max_nf + 3;
   const int a = 32 * 36, b = 36 * nu;
   return a > b ? a : b;
 }
 __host__ __device__ inline int k1_doubles(int max_nf) {
-  return max_nf * 41 + 10 + 16 + 144 + k1_union(max_nf);
+  return max_nf * 44 + 10 + 16 + 144 + k1_union(max_nf);
 }
 __host__ __device__ inline int k1_ints(int max_nf) { return ((max_nf + 2) + 1) & ~1; }
+
+__device__ __forceinline__ void sf3_point(int q, double &l0, double &l1, double &l2, double &w) {
+  if (q == 0) {
+    l0 = l1 = l2 = 1.0 / 3.0;
+    w = -27.0 / 48.0;
+  } else {
+    l0 = (q == 1) ? 0.6 : 0.2;
+    l1 = (q == 2) ? 0.6 : 0.2;
+    l2 = (q == 3) ? 0.6 : 0.2;
+    w = 25.0 / 48.0;
+  }
+}
 
 __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cfp,
                           const int32_t *__restrict__ cf, const int8_t *__restrict__ sig,
@@ -121,7 +145,7 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nd = k1_doubles(max_nf);
   double *FG = sm + (size_t)warp * nd;
-  double *FA = FG + 5 * max_nf;
+  double *FA = FG + 8 * max_nf;
   double *MU = FA + 36 * max_nf;
   double *H1I = MU + 10;
   double *W = H1I + 16;
@@ -136,34 +160,34 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
     const double hP = c_diam[c], ihP = 1.0 / hP;
     const double nuc = nu[c];
 
-    // per-face data and fan-triangle prefix
+    // (0) per-face data and the prefix of quadrature items (4 per fan triangle)
     for (int i = lane; i < k; i += 32) {
       const int f = cf[b + i];
-      FG[5 * i] = (double)sig[b + i];
-      FG[5 * i + 1] = f_area[f];
-      FG[5 * i + 2] = f_norm[3 * f];
-      FG[5 * i + 3] = f_norm[3 * f + 1];
-      FG[5 * i + 4] = f_norm[3 * f + 2];
-      for (int t = 0; t < 36; ++t) FA[36 * i + t] = 0.0;
+      const double sg = (double)sig[b + i];
+      const double3 n = load3(f_norm, f);
+      FG[8 * i] = sg;
+      FG[8 * i + 1] = f_area[f];
+      FG[8 * i + 2] = n.x;
+      FG[8 * i + 3] = n.y;
+      FG[8 * i + 4] = n.z;
+      FG[8 * i + 5] = 1.0 / f_area[f];
+      FG[8 * i + 6] = sg * dot3(sub3(load3(f_cent, f), xP), n);
     }
+    for (int e = lane; e < 36 * k; e += 32) FA[e] = 0.0;
     if (lane == 0) {
       int acc = 0;
       for (int i = 0; i < k; ++i) {
         FO[i] = acc;
         const int f = cf[b + i];
-        acc += (int)(fvp[f + 1] - fvp[f]);
+        acc += 4 * (int)(fvp[f + 1] - fvp[f] - 2);
       }
       FO[k] = acc;
     }
     __syncwarp();
     const int T = FO[k];
 
-    // (1) face Gram matrices, face-cell integrals J and cell moments by
-    //     quadrature over the fan triangles (x_f, v_j, v_{j+1}); one lane per
-    //     triangle, summed per face in triangle order.
-    double mu[10];
-#pragma unroll
-    for (int t = 0; t < 10; ++t) mu[t] = 0.0;
+    // (1) face Gram matrices and face-cell integrals J, one quadrature item
+    //     per lane, summed per face in item order.
     for (int base = 0; base < T; base += 32) {
       const int p = base + lane;
       double acc[36];
@@ -172,81 +196,67 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
       if (p < T) {
         int i = 0;
         while (FO[i + 1] <= p) ++i;
-        const int j = p - FO[i];
+        const int it = p - FO[i];
+        const int j = 1 + (it >> 2), q = it & 3;
         const int f = cf[b + i];
         const int64_t vb = fvp[f];
-        const int m = (int)(fvp[f + 1] - vb);
+        const double3 A0 = load3(xyz, fv[vb]);
         const double3 A = load3(xyz, fv[vb + j]);
-        const double3 B = load3(xyz, fv[vb + (j + 1) % m]);
+        const double3 B = load3(xyz, fv[vb + j + 1]);
         const double3 xf = load3(f_cent, f);
-        const double3 n = load3(f_norm, f);
+        const double3 n = make_double3(FG[8 * i + 2], FG[8 * i + 3], FG[8 * i + 4]);
         const double3 t1 = load3(f_t1, f);
         const double3 t2 = cross3(n, t1);
         const double ihf = 1.0 / f_diam[f];
-        const double areaT = 0.5 * dot3(cross3(sub3(A, xf), sub3(B, xf)), n);
-        for (int q = 0; q < 6; ++q) {
-          double l0, l1, l2, wq;
-          dunavant4_point(q, l0, l1, l2, wq);
-          const double3 x = add3(add3(scale3(xf, l0), scale3(A, l1)), scale3(B, l2));
-          const double w = wq * areaT;
-          const double3 dx = sub3(x, xf);
-          const double mf[3] = {1.0, dot3(dx, t1) * ihf, dot3(dx, t2) * ihf};
-          const double3 y = scale3(sub3(x, xP), ihP);
-          const double m3[10] = {1.0, y.x, y.y, y.z, y.x * y.x, y.x * y.y, y.x * y.z,
-                                 y.y * y.y, y.y * y.z, y.z * y.z};
-          acc[0] += w * mf[0] * mf[0];
-          acc[1] += w * mf[0] * mf[1];
-          acc[2] += w * mf[0] * mf[2];
-          acc[3] += w * mf[1] * mf[1];
-          acc[4] += w * mf[1] * mf[2];
-          acc[5] += w * mf[2] * mf[2];
+        const double areaT = 0.5 * dot3(cross3(sub3(A, A0), sub3(B, A0)), n);
+        double l0, l1, l2, wq;
+        sf3_point(q, l0, l1, l2, wq);
+        const double3 x = add3(add3(scale3(A0, l0), scale3(A, l1)), scale3(B, l2));
+        const double w = wq * areaT;
+        const double3 dx = sub3(x, xf);
+        const double s1 = dot3(dx, t1) * ihf, s2 = dot3(dx, t2) * ihf;
+        const double mf[3] = {w, w * s1, w * s2};   // weighted face monomials
+        const double3 y = scale3(sub3(x, xP), ihP);
+        const double m3[10] = {1.0, y.x, y.y, y.z, y.x * y.x, y.x * y.y, y.x * y.z,
+                               y.y * y.y, y.y * y.z, y.z * y.z};
+        acc[0] = mf[0];
+        acc[1] = mf[1];
+        acc[2] = mf[2];
+        acc[3] = mf[1] * s1;
+        acc[4] = mf[1] * s2;
+        acc[5] = mf[2] * s2;
 #pragma unroll
-          for (int g = 0; g < 3; ++g)
+        for (int g = 0; g < 3; ++g)
 #pragma unroll
-            for (int t = 0; t < 10; ++t) acc[6 + 10 * g + t] += w * mf[g] * m3[t];
-        }
-        // cell moments from the tetrahedron (x_P, x_f, v_j, v_{j+1}) in y-units
-        const double3 p1 = scale3(sub3(xf, xP), ihP);
-        const double3 p2 = scale3(sub3(A, xP), ihP);
-        const double3 p3 = scale3(sub3(B, xP), ihP);
-        const double vy = FG[5 * i] * dot3(p1, cross3(p2, p3)) / 6.0;
-        const double3 S = add3(add3(p1, p2), p3);
-        mu[0] += vy;
-        mu[1] += vy * S.x * 0.25;
-        mu[2] += vy * S.y * 0.25;
-        mu[3] += vy * S.z * 0.25;
-        const double s20 = vy / 20.0;
-        mu[4] += s20 * (p1.x * p1.x + p2.x * p2.x + p3.x * p3.x + S.x * S.x);
-        mu[5] += s20 * (p1.x * p1.y + p2.x * p2.y + p3.x * p3.y + S.x * S.y);
-        mu[6] += s20 * (p1.x * p1.z + p2.x * p2.z + p3.x * p3.z + S.x * S.z);
-        mu[7] += s20 * (p1.y * p1.y + p2.y * p2.y + p3.y * p3.y + S.y * S.y);
-        mu[8] += s20 * (p1.y * p1.z + p2.y * p2.z + p3.y * p3.z + S.y * S.z);
-        mu[9] += s20 * (p1.z * p1.z + p2.z * p2.z + p3.z * p3.z + S.z * S.z);
+          for (int t = 0; t < 10; ++t) acc[6 + 10 * g + t] = mf[g] * m3[t];
       }
 #pragma unroll
       for (int t = 0; t < 36; ++t) U[36 * lane + t] = acc[t];
       __syncwarp();
       const int hi = base + 32 < T ? base + 32 : T;
-      for (int i = lane; i < k; i += 32) {
+      for (int e = lane; e < 36 * k; e += 32) {
+        const int i = e / 36, t = e - 36 * i;
         const int lo_p = FO[i] > base ? FO[i] : base;
         const int hi_p = FO[i + 1] < hi ? FO[i + 1] : hi;
-        for (int pp = lo_p; pp < hi_p; ++pp)
-          for (int t = 0; t < 36; ++t) FA[36 * i + t] += U[36 * (pp - base) + t];
+        double acc_e = FA[e];
+        for (int pp = lo_p; pp < hi_p; ++pp) acc_e += U[36 * (pp - base) + t];
+        FA[e] = acc_e;
       }
       __syncwarp();
     }
-    const double h3 = hP * hP * hP;
-#pragma unroll
-    for (int t = 0; t < 10; ++t) {
-      double v = warp_sum(mu[t]);
-      if (lane == 0) MU[t] = v * h3;
+    // cell moments by Euler's identity: int_P m_t = sum_f h_f int_f m_t / (|t| + 3)
+    if (lane < 10) {
+      double s = 0.0;
+      for (int i = 0; i < k; ++i) s += FG[8 * i + 6] * FA[36 * i + 6 + lane];
+      const double deg = (lane == 0) ? 3.0 : ((lane < 4) ? 4.0 : 5.0);
+      MU[lane] = s / deg;
     }
     // face Gram inverses (symmetric 3x3 by cofactors)
     for (int i = lane; i < k; i += 32) {
       double *G = FA + 36 * i;
-      const double a = G[0], bb = G[1], cc = G[2], d = G[3], e = G[4], ff = G[5];
-      const double A11 = d * ff - e * e, A12 = -(bb * ff - cc * e), A13 = bb * e - cc * d;
-      const double A22 = a * ff - cc * cc, A23 = -(a * e - bb * cc), A33 = a * d - bb * bb;
+      const double a = G[0], bb = G[1], cc = G[2], d = G[3], e2 = G[4], ff = G[5];
+      const double A11 = d * ff - e2 * e2, A12 = -(bb * ff - cc * e2), A13 = bb * e2 - cc * d;
+      const double A22 = a * ff - cc * cc, A23 = -(a * e2 - bb * cc), A33 = a * d - bb * bb;
       const double det = a * A11 + bb * A12 + cc * A13;
       if (!(fabs(det) > 0.0) || !isfinite(det)) atomicOr(err, DEVERR_SINGULAR_LOCAL);
       const double id = 1.0 / det;
@@ -258,34 +268,37 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
       G[5] = A33 * id;
     }
     __syncwarp();
-    // H1 = int m_a m_b (a, b <= 1) and its inverse (Gauss-Jordan, SPD)
-    if (lane == 0) {
-      double a[4][8];
-      for (int r = 0; r < 4; ++r)
-        for (int s = 0; s < 4; ++s) {
-          a[r][s] = MU[c_h1[r][s]];
-          a[r][4 + s] = (r == s) ? 1.0 : 0.0;
-        }
-      for (int r = 0; r < 4; ++r) {
-        const double piv = a[r][r];
-        if (!(piv > 0.0)) atomicOr(err, DEVERR_SINGULAR_LOCAL);
-        const double ip = 1.0 / piv;
-        for (int s = 0; s < 8; ++s) a[r][s] *= ip;
-        for (int q = 0; q < 4; ++q)
-          if (q != r) {
-            const double fct = a[q][r];
-            for (int s = 0; s < 8; ++s) a[q][s] -= fct * a[r][s];
-          }
+    // H1 = int m_a m_b (a, b <= 1) inverted by cofactors, one per lane
+    {
+      double cof = 0.0;
+      if (lane < 16) {
+        const int ri = lane >> 2, cj = lane & 3;
+        int rr[3], cc[3];
+        for (int q = 0, t = 0; q < 4; ++q)
+          if (q != ri) rr[t++] = q;
+        for (int q = 0, t = 0; q < 4; ++q)
+          if (q != cj) cc[t++] = q;
+        double m[3][3];
+        for (int a = 0; a < 3; ++a)
+          for (int bq = 0; bq < 3; ++bq) m[a][bq] = MU[c_h1[rr[a]][cc[bq]]];
+        const double d3 = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+                          m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+                          m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+        cof = ((ri + cj) & 1) ? -d3 : d3;
       }
-      for (int r = 0; r < 4; ++r)
-        for (int s = 0; s < 4; ++s) H1I[4 * r + s] = a[r][4 + s];
+      double det = 0.0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) det += MU[c_h1[0][q]] * __shfl_sync(0xffffffffu, cof, q);
+      if (lane == 0 && (!(det > 0.0) || !isfinite(det))) atomicOr(err, DEVERR_SINGULAR_LOCAL);
+      const double idet = 1.0 / det;
+      if (lane < 16) H1I[4 * (lane & 3) + (lane >> 2)] = cof * idet;
     }
     __syncwarp();
 
-    const double vol = MU[0];
+    const double vol = MU[0], ivol = 1.0 / vol;
     double *PI = U;                      // [12][nu_l]
     double *DD = U + 12 * nu_l;          // [nu_l][12]
-    double *WP = DD + 12 * nu_l;         // [12][nu_l]
+    double *VV = DD + 12 * nu_l;         // [12][nu_l]
     const int nfl = 3 * k;
     const int64_t boff = 3 * b + 3 * c;
 
@@ -293,33 +306,31 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
     for (int j = lane; j < nu_l; j += 32) {
       double Gc[12], Dr[12], Bj = 0.0;
       if (j < nfl) {
-        const int i = j / 3, beta = j % 3;
-        const double sg = FG[5 * i], ar = FG[5 * i + 1];
+        const int i = j / 3, beta = j - 3 * (j / 3);
+        const double sa = FG[8 * i] * FG[8 * i + 1], iar = FG[8 * i + 5];
         const double *Gi = FA + 36 * i;
         const double *J = Gi + 6;
-        // column beta of the symmetric inverse
         const double gb[3] = {beta == 0 ? Gi[0] : (beta == 1 ? Gi[1] : Gi[2]),
                               beta == 0 ? Gi[1] : (beta == 1 ? Gi[3] : Gi[4]),
                               beta == 0 ? Gi[2] : (beta == 1 ? Gi[4] : Gi[5])};
         double bnd[10];
 #pragma unroll
-        for (int t = 0; t < 10; ++t)
-          bnd[t] = sg * ar * (gb[0] * J[t] + gb[1] * J[10 + t] + gb[2] * J[20 + t]);
-        const double dv = bnd[0] / vol;     // div(phi_j), constant
-        Bj = vol * dv;
+        for (int t = 0; t < 10; ++t) bnd[t] = sa * (gb[0] * J[t] + gb[1] * J[10 + t] + gb[2] * J[20 + t]);
+        const double dv = bnd[0] * ivol;     // div(phi_j), constant
+        Bj = bnd[0];
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
           // int phi . grad m_beta by parts, beta = e_c (a = 0) or e_d + e_c (a = 1 + d)
           const int t0 = 1 + cc;
-          Gc[4 * cc] = hP * (-dv * MU[t0] + bnd[t0]);
+          Gc[4 * cc] = hP * (bnd[t0] - dv * MU[t0]);
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
             const int t = c_prod[1 + d][cc];
-            Gc[4 * cc + 1 + d] = 0.5 * hP * (-dv * MU[t] + bnd[t]);
+            Gc[4 * cc + 1 + d] = 0.5 * hP * (bnd[t] - dv * MU[t]);
           }
-          const double ncomp = FG[5 * i + 2 + cc];
+          const double nci = FG[8 * i + 2 + cc] * iar;
 #pragma unroll
-          for (int a = 0; a < 4; ++a) Dr[4 * cc + a] = ncomp * J[10 * beta + a] / ar;
+          for (int a = 0; a < 4; ++a) Dr[4 * cc + a] = nci * J[10 * beta + a];
         }
       } else {
         const int q = j - nfl;
@@ -330,7 +341,6 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
         if (q == 1) { Gc[0 * 4 + 3] = -0.5 * vol; Gc[2 * 4 + 1] = 0.5 * vol; }
         if (q == 0) { Gc[1 * 4 + 3] = 0.5 * vol; Gc[2 * 4 + 2] = -0.5 * vol; }
         // D: (1/|P|) int m_a (m_I ^ e_q)_c
-        const double iv = 1.0 / vol;
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
           int dsel = -1;
@@ -340,7 +350,7 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
           if (q == 2) { if (cc == 0) { dsel = 1; sgn = 1.0; } else if (cc == 1) { dsel = 0; sgn = -1.0; } }
 #pragma unroll
           for (int a = 0; a < 4; ++a)
-            Dr[4 * cc + a] = (dsel < 0) ? 0.0 : sgn * MU[c_prod[a][dsel]] * iv;
+            Dr[4 * cc + a] = (dsel < 0) ? 0.0 : sgn * MU[c_prod[a][dsel]] * ivol;
         }
       }
 #pragma unroll
@@ -363,34 +373,34 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
       upper_decode(e, 12, v, w);
       double s = 0.0;
       for (int j = 0; j < nu_l; ++j) s += DD[12 * j + v] * DD[12 * j + w];
-      double hv = (v / 4 == w / 4) ? MU[c_h1[v % 4][w % 4]] : 0.0;
+      const double hv = (v / 4 == w / 4) ? MU[c_h1[v % 4][w % 4]] : 0.0;
       const double val = hv + vol * s;
       W[12 * v + w] = val;
       W[12 * w + v] = val;
     }
     __syncwarp();
-    for (int j = lane; j < nu_l; j += 32)
-      for (int v = 0; v < 12; ++v) {
-        double s = 0.0;
+    // V = W Pi - |P| D^T, one (row v, column j) entry per lane
+    for (int e = lane; e < 12 * nu_l; e += 32) {
+      const int v = e / nu_l, j = e - v * nu_l;
+      double s = -vol * DD[12 * j + v];
 #pragma unroll
-        for (int w = 0; w < 12; ++w) s += W[12 * v + w] * PI[w * nu_l + j];
-        WP[v * nu_l + j] = s;
-      }
+      for (int w = 0; w < 12; ++w) s += W[12 * v + w] * PI[w * nu_l + j];
+      VV[e] = s;
+    }
     __syncwarp();
-    // (4) M_P entries
+    // (4) M_P entries: nu (|P| delta + Pi_j . V_j' - |P| D_j . Pi_j'), j <= j'
     double *M = Mloc + m_off[c];
     const int TT = nu_l * (nu_l + 1) / 2;
     for (int e = lane; e < TT; e += 32) {
       int j, jp;
       upper_decode(e, nu_l, j, jp);
-      double dpa = 0.0, dpb = 0.0, pwp = 0.0;
+      double pv = 0.0, dp = 0.0;
 #pragma unroll
       for (int v = 0; v < 12; ++v) {
-        dpa += DD[12 * j + v] * PI[v * nu_l + jp];
-        dpb += DD[12 * jp + v] * PI[v * nu_l + j];
-        pwp += PI[v * nu_l + j] * WP[v * nu_l + jp];
+        pv += PI[v * nu_l + j] * VV[v * nu_l + jp];
+        dp += DD[12 * j + v] * PI[v * nu_l + jp];
       }
-      const double val = nuc * ((j == jp ? vol : 0.0) - vol * (dpa + dpb) + pwp);
+      const double val = nuc * ((j == jp ? vol : 0.0) + pv - vol * dp);
       M[(int64_t)j * nu_l + jp] = val;
       M[(int64_t)jp * nu_l + j] = val;
     }

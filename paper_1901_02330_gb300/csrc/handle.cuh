@@ -55,33 +55,31 @@ struct vem_handle {
   double *Mloc = nullptr, *Bloc = nullptr;
 
   // ---- global system ----
-  int64_t *a_rp = nullptr;
-  int32_t *a_col = nullptr;
-  double *a_val = nullptr;
-  int64_t nnz_a = 0;
-  int a_lanes = 8;
+  // [M B^T; B 0] and S in sliced ELL (SELL-32): rows in slices of 32, each
+  // slice padded to its longest row and stored column-major, so a warp reads
+  // element j of 32 consecutive rows with one coalesced load.
+  vem::SellMat A, S;
   double *rhs = nullptr;                         // [n] = [g; F]
   double *bt_face = nullptr;                     // [2 nf] B entries of each face's cells
   double *diagM = nullptr;                       // [n_u]
-  int64_t *s_rp = nullptr;
-  int32_t *s_col = nullptr;
-  double *s_val = nullptr, *s_dinv = nullptr;
-  int64_t nnz_s = 0;
-  int s_lanes = 8;
+  double *s_dinv = nullptr;                      // [n_p] 1 / diag(S)
 
   // ---- workspace ----
   double *part = nullptr;                        // kMaxSlots * kMaxBlocks partial sums
   double *scal = nullptr;                        // device scalars
   double *h_scal = nullptr;                      // pinned host mirror
+  unsigned int *ctr = nullptr;                   // last-block counters (zeroed)
   double *work = nullptr;                        // Krylov vectors
   double *xsol = nullptr;                        // [n] solution iterate
   int64_t *cnt_buf = nullptr;                    // [n] row counts for the scans
   int64_t *scan_buf = nullptr;                   // scan block sums
+  int64_t *slice_buf = nullptr;                  // per-slice sizes
+  int64_t slice_buf_n = 0;
   size_t work_n = 0;
 
   std::vector<void *> allocations;               // everything cudaMalloc'ed
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  double t_assemble_ms = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  double t_assemble_ms = 0.0, t_element_ms = 0.0, t_scatter_ms = 0.0;
 };
 
 namespace vem {
@@ -112,11 +110,12 @@ vem_status assemble_rhs(vem_handle *h);
 vem_status assemble_global(vem_handle *h);
 
 // BLAS-like launches (blas.cu)
-void spmv(cudaStream_t s, int64_t rows, const int64_t *rp, const int32_t *col, const double *val,
-          const double *x, double *y, int lanes, double *dot_part = nullptr);
+void spmv(cudaStream_t s, const SellMat &A, const double *x, double *y, double *dot_part = nullptr);
+int spmv_nblocks(const SellMat &A);
 int nblocks_vec(int64_t n);
 void dot_partials(cudaStream_t s, int64_t n, const double *x, const double *y, double *part);
-int choose_lanes(double avg_nnz);
+// CSR view of a SELL matrix on the host (row_ptr[rows + 1], col, val)
+vem_status sell_to_host_csr(vem_handle *h, const SellMat &A, int64_t *rp, int32_t *col, double *val);
 
 // Krylov solve (krylov.cu)
 vem_status krylov_solve(vem_handle *h, double *x, vem_stats *st);

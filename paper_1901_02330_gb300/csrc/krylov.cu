@@ -41,11 +41,17 @@ enum { MR_GOLD = 0, MR_G, MR_COLD, MR_C, MR_SOLD, MR_S, MR_ETA, MR_A1, MR_A2, MR
 
 __host__ __device__ inline double *slot(double *part, int s) { return part + (size_t)s * kMaxBlocks; }
 
-int spmv_nblocks(int64_t rows, int lanes) { return nblocks_vec(rows * lanes); }
 
 // --------------------------------------------------------------- PCG -------
+// Jacobi-preconditioned CG in the single-reduction form of Chronopoulos &
+// Gear (J. Comput. Appl. Math. 25, 1989): one fused kernel computes
+// w = S u with the three dot products (r,u), (w,u), (r,r), and its
+// last-arriving block turns them into alpha, beta and the convergence test;
+// one fused kernel then updates p, s, x, r, u.  Two launches per iteration.
+enum { CG_ALPHA = 24, CG_BETA, CG_GPREV, CG_APREV, CG_BB };
+
 // The converged flag read once per block and broadcast, so an early return is
-// uniform across the block even if another block sets the flag meanwhile.
+// uniform across the block.
 __device__ __forceinline__ bool block_done(const double *sc) {
   __shared__ int f;
   if (threadIdx.x == 0) f = (sc[S_PCG_DONE] != 0.0);
@@ -55,153 +61,140 @@ __device__ __forceinline__ bool block_done(const double *sc) {
   return r;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_pcg_init(int64_t n, const double *__restrict__ b,
-                                                          const double *__restrict__ dinv,
-                                                          double *x, double *r, double *z,
-                                                          double *p, double *part, double *sc) {
-  double rz = 0.0, bb = 0.0;
+__global__ void __launch_bounds__(kRedThreads) k_cg_init(int64_t n, const double *__restrict__ b,
+                                                         const double *__restrict__ dinv, double *x,
+                                                         double *r, double *u, double *p, double *s,
+                                                         double *part, double *sc, unsigned int *ctr) {
+  double bb = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double bi = b[i], zi = dinv[i] * bi;
+    const double bi = b[i];
     x[i] = 0.0;
     r[i] = bi;
-    z[i] = zi;
-    p[i] = zi;
-    rz += bi * zi;
+    u[i] = dinv[i] * bi;
+    p[i] = 0.0;
+    s[i] = 0.0;
     bb += bi * bi;
   }
-  block_partial(rz, slot(part, P_RZ0));
   block_partial(bb, slot(part, P_BB));
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    sc[S_PCG_DONE] = 0.0;
-    sc[S_PCG_IT] = 0.0;
-    sc[S_PCG_BAD] = 0.0;
+  if (last_block(ctr)) {
+    const double t = sum_partials_cg(slot(part, P_BB), gridDim.x);
+    if (threadIdx.x == 0) {
+      sc[CG_BB] = t;
+      sc[S_PCG_DONE] = (t == 0.0) ? 1.0 : 0.0;
+      sc[S_PCG_IT] = 0.0;
+      sc[S_PCG_BAD] = isfinite(t) ? 0.0 : 2.0;
+      if (!isfinite(t)) sc[S_PCG_DONE] = 1.0;
+    }
   }
 }
 
-// q = S p and the partials of p . q; skipped once converged.
-template <int L>
-__global__ void __launch_bounds__(256) k_pcg_spmv(int64_t rows, const int64_t *__restrict__ rp,
-                                                  const int32_t *__restrict__ col,
-                                                  const double *__restrict__ val,
-                                                  const double *__restrict__ p, double *q,
-                                                  double *part, const double *sc) {
+// w = S u, partials of (r,u), (w,u), (r,r); the last block decides.
+__global__ void __launch_bounds__(256) k_cg_spmv(int64_t rows, int64_t nslices,
+                                                 const int64_t *__restrict__ off,
+                                                 const int32_t *__restrict__ col,
+                                                 const double *__restrict__ val,
+                                                 const double *__restrict__ u,
+                                                 const double *__restrict__ r, double *w, double *part,
+                                                 double *sc, unsigned int *ctr, double tol2, int it) {
   if (block_done(sc)) return;
   const int lane = threadIdx.x & 31;
-  const int sub = lane % L;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / L;
-  double dacc = 0.0;
-  for (int64_t base = warp * (32 / L); base < rows; base += stride) {
-    const int64_t r = base + lane / L;
-    const bool ok = r < rows;
-    double s = 0.0;
-    if (ok) {
-      const int64_t b = rp[r], e = rp[r + 1];
-      for (int64_t k = b + sub; k < e; k += L) s += val[k] * __ldg(p + col[k]);
-    }
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, L);
-    if (ok && sub == 0) {
-      q[r] = s;
-      dacc += s * p[r];
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double gam = 0.0, del = 0.0, rr = 0.0;
+  for (int64_t s = warp; s < nslices; s += nwarps) {
+    const double t = sell_row_dot(off, col, val, u, s, lane);
+    const int64_t i = 32 * s + lane;
+    if (i < rows) {
+      w[i] = t;
+      const double ui = u[i], ri = r[i];
+      gam += ri * ui;
+      del += t * ui;
+      rr += ri * ri;
     }
   }
-  block_partial(dacc, slot(part, P_PQ));
-}
-
-__global__ void __launch_bounds__(kRedThreads) k_pcg_update(int64_t n, double *x, double *r, double *z,
-                                                            const double *__restrict__ p,
-                                                            const double *__restrict__ q,
-                                                            const double *__restrict__ dinv,
-                                                            double *part, int cur, int nb, int nbs,
-                                                            double *sc) {
-  if (block_done(sc)) return;
-  const double rz = sum_partials(slot(part, cur), nb);
-  const double pq = sum_partials(slot(part, P_PQ), nbs);
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      sc[S_PCG_BAD] = 1.0;
-      sc[S_PCG_DONE] = 1.0;
-    }
+  block_partial(gam, slot(part, P_RZ0));
+  block_partial(del, slot(part, P_RZ1));
+  block_partial(rr, slot(part, P_RR));
+  if (!last_block(ctr)) return;
+  const double G = sum_partials_cg(slot(part, P_RZ0), gridDim.x);
+  const double D = sum_partials_cg(slot(part, P_RZ1), gridDim.x);
+  const double R = sum_partials_cg(slot(part, P_RR), gridDim.x);
+  if (threadIdx.x != 0) return;
+  if (!isfinite(R) || !isfinite(G) || !isfinite(D)) {
+    sc[S_PCG_BAD] = 2.0;
+    sc[S_PCG_DONE] = 1.0;
     return;
   }
-  const double alpha = rz / pq;
-  double rr = 0.0, rzn = 0.0;
+  sc[S_PCG_IT] = (double)it;
+  if (R <= tol2 * sc[CG_BB]) {
+    sc[S_PCG_DONE] = 1.0;
+    return;
+  }
+  double beta = 0.0, den = D;
+  if (it > 0) {
+    beta = G / sc[CG_GPREV];
+    den = D - beta * G / sc[CG_APREV];
+  }
+  if (!(den > 0.0) || !(G > 0.0)) {
+    sc[S_PCG_BAD] = 1.0;
+    sc[S_PCG_DONE] = 1.0;
+    return;
+  }
+  const double alpha = G / den;
+  sc[CG_ALPHA] = alpha;
+  sc[CG_BETA] = beta;
+  sc[CG_GPREV] = G;
+  sc[CG_APREV] = alpha;
+}
+
+// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r
+__global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, double *x, double *r, double *u,
+                                                           double *p, double *s,
+                                                           const double *__restrict__ w,
+                                                           const double *__restrict__ dinv,
+                                                           const double *sc) {
+  if (block_done(sc)) return;
+  const double alpha = sc[CG_ALPHA], beta = sc[CG_BETA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
+    const double pi = u[i] + beta * p[i];
+    const double si = w[i] + beta * s[i];
+    x[i] += alpha * pi;
+    const double ri = r[i] - alpha * si;
+    p[i] = pi;
+    s[i] = si;
     r[i] = ri;
-    const double zi = dinv[i] * ri;
-    z[i] = zi;
-    rr += ri * ri;
-    rzn += ri * zi;
+    u[i] = dinv[i] * ri;
   }
-  block_partial(rr, slot(part, P_RR));
-  block_partial(rzn, slot(part, cur ^ 1));
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_pcg_dir(int64_t n, const double *__restrict__ z,
-                                                         double *p, double *part, int cur, int nb,
-                                                         double tol2, int it, double *sc) {
-  if (block_done(sc)) return;
-  const double rr = sum_partials(slot(part, P_RR), nb);
-  const double bb = sum_partials(slot(part, P_BB), nb);
-  if (!isfinite(rr)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      sc[S_PCG_BAD] = 2.0;
-      sc[S_PCG_DONE] = 1.0;
-    }
-    return;
-  }
-  if (rr <= tol2 * bb) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      sc[S_PCG_DONE] = 1.0;
-      sc[S_PCG_IT] = (double)it;
-    }
-    return;
-  }
-  const double beta = sum_partials(slot(part, cur ^ 1), nb) / sum_partials(slot(part, cur), nb);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc[S_PCG_IT] = (double)it;
-}
-
-// bb == 0: the solution is zero.
-__global__ void k_pcg_zero_check(double *part, int nb, double *sc) {
-  const double bb = sum_partials(slot(part, P_BB), nb);
-  if (threadIdx.x == 0 && bb == 0.0) sc[S_PCG_DONE] = 1.0;
-}
-
-// Solve S x = b (length n_p) to relative residual rtol; returns iterations.
+// Solve S x = b (length n_p) to relative residual inner_rtol; returns iterations.
 static vem_status pcg_solve(vem_handle *h, const double *b, double *x, double *wk, int *iters) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n_p;
-  double *r = wk, *z = wk + n, *p = wk + 2 * n, *q = wk + 3 * n;
+  double *r = wk, *u = wk + n, *p = wk + 2 * n, *sv = wk + 3 * n, *w = wk + 4 * n;
   const int nb = nblocks_vec(n);
-  const int nbs = spmv_nblocks(n, h->s_lanes);
+  const int nbs = spmv_nblocks(h->S);
   double *sc = h->scal;
-  count_launch(); k_pcg_init<<<nb, kRedThreads, 0, s>>>(n, b, h->s_dinv, x, r, z, p, h->part, sc);
-  count_launch(); k_pcg_zero_check<<<1, kRedThreads, 0, s>>>(h->part, nb, sc);
   const double tol2 = h->opt.inner_rtol * h->opt.inner_rtol;
+  count_launch();
+  k_cg_init<<<nb, kRedThreads, 0, s>>>(n, b, h->s_dinv, x, r, u, p, sv, h->part, sc, h->ctr);
+  auto spmv_it = [&](int it) {
+    count_launch();
+    k_cg_spmv<<<nbs, 256, 0, s>>>(n, h->S.nslices, h->S.off, h->S.col, h->S.val, u, r, w, h->part, sc,
+                                  h->ctr + 1, tol2, it);
+  };
+  spmv_it(0);
   const int maxit = h->opt.inner_maxit;
   const int chunk = 8;
   int it = 0;
   while (it < maxit) {
     const int end = it + chunk < maxit ? it + chunk : maxit;
     for (; it < end; ++it) {
-      const int cur = it & 1;   // rz of this iteration lives in slot cur
-      switch (h->s_lanes) {
-        case 4: count_launch(); k_pcg_spmv<4><<<nbs, 256, 0, s>>>(n, h->s_rp, h->s_col, h->s_val, p, q, h->part, sc); break;
-        case 8: count_launch(); k_pcg_spmv<8><<<nbs, 256, 0, s>>>(n, h->s_rp, h->s_col, h->s_val, p, q, h->part, sc); break;
-        case 16: count_launch(); k_pcg_spmv<16><<<nbs, 256, 0, s>>>(n, h->s_rp, h->s_col, h->s_val, p, q, h->part, sc); break;
-        default: count_launch(); k_pcg_spmv<32><<<nbs, 256, 0, s>>>(n, h->s_rp, h->s_col, h->s_val, p, q, h->part, sc); break;
-      }
-      count_launch(); k_pcg_update<<<nb, kRedThreads, 0, s>>>(n, x, r, z, p, q, h->s_dinv, h->part, P_RZ0 + cur, nb,
-                                               nbs, sc);
-      count_launch(); k_pcg_dir<<<nb, kRedThreads, 0, s>>>(n, z, p, h->part, P_RZ0 + cur, nb, tol2, it + 1, sc);
+      count_launch();
+      k_cg_update<<<nb, kRedThreads, 0, s>>>(n, x, r, u, p, sv, w, h->s_dinv, sc);
+      spmv_it(it + 1);
     }
     VEM_CUDA(h, cudaGetLastError());
     VEM_CUDA(h, cudaMemcpyAsync(h->h_scal, sc, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
@@ -468,7 +461,7 @@ __global__ void k_gm_solve(double *sc, int k, GmLayout L) {
 
 // ------------------------------------------------------- preconditioner ---
 // z = P^{-1} v for the block preconditioner (diag or upper triangular).
-// wk: 4 n_p PCG work vectors.  If part_g2 != nullptr (MINRES) also leaves
+// wk: 5 n_p PCG work vectors.  If part_g2 != nullptr (MINRES) also leaves
 // the partials of v.z in slots P_G2U (flux part) and P_G2P (pressure part).
 static vem_status precond(vem_handle *h, const double *v, double *z, double *wk, int *inner,
                           bool minres_partials) {
@@ -496,7 +489,7 @@ static vem_status precond(vem_handle *h, const double *v, double *z, double *wk,
 static vem_status true_relres(vem_handle *h, const double *x, double *tmp, double *rel) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
-  spmv(s, n, h->a_rp, h->a_col, h->a_val, x, tmp, h->a_lanes);
+  spmv(s, h->A, x, tmp);
   const int nb = nblocks_vec(n);
   count_launch(); k_residual<<<nb, kRedThreads, 0, s>>>(n, h->rhs, tmp, tmp, slot(h->part, P_R2), slot(h->part, P_B2));
   count_launch(); k_read_sum<<<1, kRedThreads, 0, s>>>(slot(h->part, P_R2), nb, h->scal + S_R2);
@@ -524,14 +517,14 @@ static vem_status ensure_work(vem_handle *h, size_t n) {
 static vem_status run_minres(vem_handle *h, double *x, vem_stats *st) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n, nu = h->n_u, np = h->n_p;
-  VEM_TRY(ensure_work(h, 8 * (size_t)n + 4 * (size_t)np));
+  VEM_TRY(ensure_work(h, 8 * (size_t)n + 5 * (size_t)np));
   double *vA = h->work, *vB = vA + n, *z = vB + n, *zn = z + n, *Az = zn + n, *wA = Az + n,
          *wB = wA + n, *tmp = wB + n, *pw = tmp + n;
   double *vold = vA, *v = vB, *wold = wA, *w = wB;
   int inner = 0;
   const int nbn = nblocks_vec(n), nbu = nblocks_vec(nu), nbp = nblocks_vec(np);
   // v = b - A x0
-  spmv(s, n, h->a_rp, h->a_col, h->a_val, x, tmp, h->a_lanes);
+  spmv(s, h->A, x, tmp);
   count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, h->rhs, tmp, v, slot(h->part, P_R2), slot(h->part, P_B2));
   VEM_CUDA(h, cudaMemsetAsync(vold, 0, sizeof(double) * n, s));
   VEM_CUDA(h, cudaMemsetAsync(wold, 0, sizeof(double) * n, s));
@@ -546,13 +539,13 @@ static vem_status run_minres(vem_handle *h, double *x, vem_stats *st) {
   VEM_CUDA(h, cudaStreamSynchronize(s));
   const double eta0 = h->h_scal[S_MR + MR_ETA];
   int it = 0;
-  const int nbd = spmv_nblocks(n, h->a_lanes);
+  const int nbd = spmv_nblocks(h->A);
   vem_status result = VEM_ERR_NOT_CONVERGED;
   if (rel <= h->opt.rtol || eta0 == 0.0) result = VEM_OK;
   while (result != VEM_OK && it < h->opt.maxit) {
     ++it;
     count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, z, h->scal + S_MR + MR_IG);
-    spmv(s, n, h->a_rp, h->a_col, h->a_val, z, Az, h->a_lanes, slot(h->part, P_DELTA));
+    spmv(s, h->A, z, Az, slot(h->part, P_DELTA));
     count_launch(); k_mr_lanczos<<<nbn, kRedThreads, 0, s>>>(n, Az, v, vold, h->part, nbd, h->scal);
     count_launch(); k_diag_scale<<<nbu, kRedThreads, 0, s>>>(nu, vold, h->diagM, zn, slot(h->part, P_G2U));
     VEM_TRY(precond(h, vold, zn, pw, &inner, true));
@@ -592,7 +585,7 @@ static vem_status run_fgmres(vem_handle *h, double *x, vem_stats *st) {
   const int m = h->opt.restart;
   GmLayout L{m};
   if (L.end() > 8192) return fail(h, VEM_ERR_BAD_INPUT, "restart too large");
-  VEM_TRY(ensure_work(h, (size_t)(2 * m + 2) * n + 4 * (size_t)np));
+  VEM_TRY(ensure_work(h, (size_t)(2 * m + 2) * n + 5 * (size_t)np));
   double *V = h->work, *Z = V + (size_t)(m + 1) * n, *tmp = Z + (size_t)m * n, *pw = tmp + n;
   int inner = 0, it = 0;
   const int nbn = nblocks_vec(n);
@@ -603,7 +596,7 @@ static vem_status run_fgmres(vem_handle *h, double *x, vem_stats *st) {
   if (bnorm == 0.0) bnorm = 1.0;
   while (result != VEM_OK && it < h->opt.maxit) {
     // V_0 = (b - A x) / beta
-    spmv(s, n, h->a_rp, h->a_col, h->a_val, x, tmp, h->a_lanes);
+    spmv(s, h->A, x, tmp);
     count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, h->rhs, tmp, V, slot(h->part, P_R2), slot(h->part, P_B2));
     count_launch(); k_gm_start<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbn, L);
     count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, V, h->scal + GM_IBETA);
@@ -612,7 +605,7 @@ static vem_status run_fgmres(vem_handle *h, double *x, vem_stats *st) {
       ++it;
       double *Vj = V + (size_t)j * n, *Zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
       VEM_TRY(precond(h, Vj, Zj, pw, &inner, false));
-      spmv(s, n, h->a_rp, h->a_col, h->a_val, Zj, w, h->a_lanes);
+      spmv(s, h->A, Zj, w);
       for (int pass = 0; pass < 2; ++pass) {
         for (int i0 = 0; i0 <= j; i0 += kMD) {
           const int cnt = (j + 1 - i0) < kMD ? (j + 1 - i0) : kMD;

@@ -43,7 +43,8 @@ class vem_options(C.Structure):
 class vem_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("inner_iterations", C.c_int32), ("relres", C.c_double),
                 ("t_assemble_ms", C.c_double), ("t_solve_ms", C.c_double),
-                ("n_u", C.c_int64), ("n_p", C.c_int64), ("nnz_A", C.c_int64), ("nnz_S", C.c_int64)]
+                ("n_u", C.c_int64), ("n_p", C.c_int64), ("nnz_A", C.c_int64), ("nnz_S", C.c_int64),
+                ("t_element_ms", C.c_double), ("t_scatter_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
