@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--n", type=int, default=N_CELLS, help="cells per side (default 128)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--inner-rtol", type=float, default=1e-8, help="inner Jacobi-PCG tolerance")
     ap.add_argument("--element", default="k1", choices=["k1", "e0"])
     ap.add_argument("--profile", action="store_true",
@@ -292,6 +293,38 @@ def run_ours(a):
     el_flops = cell_flops * mesh.n_cells
     el_gflops = el_flops / (el_ms * 1e-3) / 1e9
 
+    # ---------------- mixed precision at equal accuracy ----------------
+    mixed = None
+    if not a.no_mixed:
+        sm = vs.Solver(mesh, stream=sid, device_io=1, **dict(opts, precision=vs.VEM_PRECISION_MIXED,
+                                                                inner_rtol=max(a.inner_rtol, 1e-5)))
+        sm.set_coefficient(np.ones(mesh.n_cells))
+        sm.set_data(prob.f, prob.gD)
+        um = torch.empty_like(u)
+        pm_ = torch.empty_like(p)
+
+        def mstep():
+            sm.assemble()
+            return sm.solve(u_out=um, p_out=pm_)[2]
+
+        for _ in range(2):
+            mst = mstep()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.steps):
+            mst = mstep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mms = e0.elapsed_time(e1) / a.steps
+        sm.close()
+        mixed = {"value": n * world / (mms * 1e-3), "unit": UNIT, "ms_per_step": mms,
+                 "speedup_vs_fp64": ms / mms, "relres": mst["relres"], "iterations": mst["iterations"],
+                 "inner_iterations": mst["inner_iterations"], "t_solve_ms": mst["t_solve_ms"],
+                 "inner": "FP32 Jacobi-PCG rtol %g" % max(a.inner_rtol, 1e-5),
+                 "rel_diff_vs_fp64_u": float(torch.linalg.norm(um - u) / torch.linalg.norm(u)),
+                 "rel_diff_vs_fp64_p": float(torch.linalg.norm(pm_ - p) / torch.linalg.norm(p))}
+        del um, pm_
+
     # ---------------- end-to-end through the public API (e2e) ----------------
     def pin(arr):
         t = torch.from_numpy(np.ascontiguousarray(arr)).pin_memory()
@@ -351,6 +384,7 @@ def run_ours(a):
                           "achieved": spmv_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": spmv_gbs / hbm_peak,
                           "traffic": None, "algorithmic_bytes": sb, "launch_ms": spmv_ms,
                           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800"},
+        "mixed_precision": mixed,
         "phases_ms": {"element": el_ms, "scatter": st["t_scatter_ms"], "assemble": st["t_assemble_ms"],
                       "solve": st["t_solve_ms"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

@@ -88,7 +88,7 @@ enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1 };
 enum { VEM_KRYLOV_MINRES = 0, VEM_KRYLOV_FGMRES = 1 };
 enum { VEM_PREC_BLOCK_DIAG = 0, VEM_PREC_BLOCK_TRI = 1 };
 enum { VEM_INNER_PCG = 0 };
-enum { VEM_PRECISION_FP64 = 0 };
+enum { VEM_PRECISION_FP64 = 0, VEM_PRECISION_MIXED = 1 };
 
 typedef struct {
   int element;        /* VEM_ELEMENT_*                                      */
@@ -100,7 +100,11 @@ typedef struct {
   int inner;          /* VEM_INNER_* : solver for S = B diag(M)^-1 B^T      */
   double inner_rtol;  /* inner relative residual target                     */
   int inner_maxit;    /* inner iteration cap per application                */
-  int precision;      /* VEM_PRECISION_*                                    */
+  int precision;      /* VEM_PRECISION_*: MIXED runs the Schur solve of the */
+                      /* preconditioner in FP32 (values, vectors and        */
+                      /* arithmetic); the outer Krylov method, its A-apply, */
+                      /* orthogonalisation and restart residuals stay FP64. */
+                      /* Needs FGMRES; inner_rtol >= 1e-6 is meaningful.    */
   int device_io;      /* 0: vem_solve's x0/u_out/p_out are host pointers;   */
                       /* 1: device pointers (e.g. torch tensors' data_ptr)  */
 } vem_options;

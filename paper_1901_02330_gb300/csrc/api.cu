@@ -75,7 +75,10 @@ static vem_status check_options(vem_handle *h, const vem_options *o) {
   if (o->krylov == VEM_KRYLOV_MINRES && o->precond != VEM_PREC_BLOCK_DIAG)
     return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs the SPD block-diagonal preconditioner");
   if (o->inner != VEM_INNER_PCG) return fail(h, VEM_ERR_UNSUPPORTED, "inner solver %d", o->inner);
-  if (o->precision != VEM_PRECISION_FP64) return fail(h, VEM_ERR_UNSUPPORTED, "precision %d", o->precision);
+  if (o->precision != VEM_PRECISION_FP64 && o->precision != VEM_PRECISION_MIXED)
+    return fail(h, VEM_ERR_BAD_INPUT, "unknown precision %d", o->precision);
+  if (o->precision == VEM_PRECISION_MIXED && o->krylov != VEM_KRYLOV_FGMRES)
+    return fail(h, VEM_ERR_BAD_INPUT, "mixed precision needs FGMRES (its FP32 inner solve is not a fixed operator)");
   if (o->restart < 1 || o->restart > 256) return fail(h, VEM_ERR_BAD_INPUT, "restart %d", o->restart);
   if (!(o->rtol > 0.0) || !(o->inner_rtol > 0.0) || o->maxit < 1 || o->inner_maxit < 1)
     return fail(h, VEM_ERR_BAD_INPUT, "tolerances and iteration caps must be positive");

@@ -181,6 +181,12 @@ __global__ void k_schur_fill(Layout L, const double *__restrict__ diagM, const i
   }
 }
 
+__global__ void k_f64_to_f32(int64_t n, const double *__restrict__ a, float *b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
 // B entries of the (f, 0) DOF in each of the face's two cells (0 for a
 // missing second cell), for the block-triangular flux update.
 __global__ void k_bt_face(Layout L, double *bt) {
@@ -401,6 +407,17 @@ vem_status assemble_global(vem_handle *h) {
   const int64_t spad = h->S.nslices * 32;
   count_launch(); k_schur_fill<<<grid_for(spad, T), T, 0, s>>>(L, h->diagM, h->S.off, spad, h->S.col, h->S.val,
                                                           h->s_dinv, h->d_err);
+  VEM_CUDA(h, cudaGetLastError());
+  // FP32 copies of S for the mixed-precision inner solve
+  if (h->s32_stored != h->S.stored) {
+    dfree(h, h->S_val32);
+    h->S_val32 = nullptr;
+    VEM_TRY(dalloc_n(h, &h->S_val32, (size_t)h->S.stored));
+    h->s32_stored = h->S.stored;
+  }
+  if (!h->s_dinv32) VEM_TRY(dalloc_n(h, &h->s_dinv32, (size_t)h->nc));
+  count_launch(); k_f64_to_f32<<<grid_for(h->S.stored, T), T, 0, s>>>(h->S.stored, h->S.val, h->S_val32);
+  count_launch(); k_f64_to_f32<<<grid_for(h->nc, T), T, 0, s>>>(h->nc, h->s_dinv, h->s_dinv32);
   VEM_CUDA(h, cudaGetLastError());
   if (!h->bt_face) VEM_TRY(dalloc_n(h, &h->bt_face, 2 * (size_t)h->nf));
   count_launch(); k_bt_face<<<grid_for(h->nf, T), T, 0, s>>>(L, h->bt_face);

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int64_t rows, int64_t nslices
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double dacc = 0.0;
   for (int64_t s = warp; s < nslices; s += nwarps) {
-    const double t = sell_row_dot(off, col, val, x, s, lane);
+    const double t = sell_row_dot<double>(off, col, val, x, s, lane);
     const int64_t r = 32 * s + lane;
     if (r < rows) {
       y[r] = t;

@@ -105,22 +105,24 @@ __device__ __forceinline__ void block_partial(double v, double *part) {
 }
 
 // Row (32 s + lane) of a SELL-32 matrix times x: elements in column order,
-// four independent loads in flight.
-__device__ __forceinline__ double sell_row_dot(const int64_t *__restrict__ off,
-                                               const int32_t *__restrict__ col,
-                                               const double *__restrict__ val,
-                                               const double *__restrict__ x, int64_t s, int lane) {
+// four independent loads in flight; T = double or float (values, x and the
+// arithmetic share the type).
+template <class T>
+__device__ __forceinline__ T sell_row_dot(const int64_t *__restrict__ off,
+                                          const int32_t *__restrict__ col,
+                                          const T *__restrict__ val, const T *__restrict__ x,
+                                          int64_t s, int lane) {
   const int64_t o = off[s];
   const int w = (int)((off[s + 1] - o) >> 5);
-  const double *vp = val + o + lane;
+  const T *vp = val + o + lane;
   const int32_t *cp = col + o + lane;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   int j = 0;
   for (; j + 3 < w; j += 4) {
     const int32_t c0 = __ldcs(cp + 32 * j), c1 = __ldcs(cp + 32 * (j + 1));
     const int32_t c2 = __ldcs(cp + 32 * (j + 2)), c3 = __ldcs(cp + 32 * (j + 3));
-    const double v0 = __ldcs(vp + 32 * j), v1 = __ldcs(vp + 32 * (j + 1));
-    const double v2 = __ldcs(vp + 32 * (j + 2)), v3 = __ldcs(vp + 32 * (j + 3));
+    const T v0 = __ldcs(vp + 32 * j), v1 = __ldcs(vp + 32 * (j + 1));
+    const T v2 = __ldcs(vp + 32 * (j + 2)), v3 = __ldcs(vp + 32 * (j + 3));
     s0 += v0 * __ldg(x + c0);
     s1 += v1 * __ldg(x + c1);
     s2 += v2 * __ldg(x + c2);

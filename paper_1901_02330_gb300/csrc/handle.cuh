@@ -63,6 +63,9 @@ struct vem_handle {
   double *bt_face = nullptr;                     // [2 nf] B entries of each face's cells
   double *diagM = nullptr;                       // [n_u]
   double *s_dinv = nullptr;                      // [n_p] 1 / diag(S)
+  float *S_val32 = nullptr;                      // FP32 copy of S's values
+  float *s_dinv32 = nullptr;                     // FP32 copy of 1 / diag(S)
+  int64_t s32_stored = 0;
 
   // ---- workspace ----
   double *part = nullptr;                        // kMaxSlots * kMaxBlocks partial sums

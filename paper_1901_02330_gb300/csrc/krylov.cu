@@ -61,20 +61,22 @@ __device__ __forceinline__ bool block_done(const double *sc) {
   return r;
 }
 
+template <class T>
 __global__ void __launch_bounds__(kRedThreads) k_cg_init(int64_t n, const double *__restrict__ b,
-                                                         const double *__restrict__ dinv, double *x,
-                                                         double *r, double *u, double *p, double *s,
-                                                         double *part, double *sc, unsigned int *ctr) {
+                                                         const T *__restrict__ dinv, T *x, T *r, T *u,
+                                                         T *p, T *s, double *part, double *sc,
+                                                         unsigned int *ctr) {
   double bb = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double bi = b[i];
-    x[i] = 0.0;
-    r[i] = bi;
-    u[i] = dinv[i] * bi;
-    p[i] = 0.0;
-    s[i] = 0.0;
-    bb += bi * bi;
+    const T bt = (T)bi;
+    x[i] = 0;
+    r[i] = bt;
+    u[i] = dinv[i] * bt;
+    p[i] = 0;
+    s[i] = 0;
+    bb += (double)bt * (double)bt;
   }
   block_partial(bb, slot(part, P_BB));
   if (last_block(ctr)) {
@@ -89,33 +91,34 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_init(int64_t n, const double
   }
 }
 
-// w = S u, partials of (r,u), (w,u), (r,r); the last block decides.
+// w = S u, partials of (r,u), (w,u), (r,r); the last block decides.  The
+// per-thread sums are in T, the block partials and scalars in FP64.
+template <class T>
 __global__ void __launch_bounds__(256) k_cg_spmv(int64_t rows, int64_t nslices,
                                                  const int64_t *__restrict__ off,
                                                  const int32_t *__restrict__ col,
-                                                 const double *__restrict__ val,
-                                                 const double *__restrict__ u,
-                                                 const double *__restrict__ r, double *w, double *part,
+                                                 const T *__restrict__ val, const T *__restrict__ u,
+                                                 const T *__restrict__ r, T *w, double *part,
                                                  double *sc, unsigned int *ctr, double tol2, int it) {
   if (block_done(sc)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double gam = 0.0, del = 0.0, rr = 0.0;
+  T gam = 0, del = 0, rr = 0;
   for (int64_t s = warp; s < nslices; s += nwarps) {
-    const double t = sell_row_dot(off, col, val, u, s, lane);
+    const T t = sell_row_dot<T>(off, col, val, u, s, lane);
     const int64_t i = 32 * s + lane;
     if (i < rows) {
       w[i] = t;
-      const double ui = u[i], ri = r[i];
+      const T ui = u[i], ri = r[i];
       gam += ri * ui;
       del += t * ui;
       rr += ri * ri;
     }
   }
-  block_partial(gam, slot(part, P_RZ0));
-  block_partial(del, slot(part, P_RZ1));
-  block_partial(rr, slot(part, P_RR));
+  block_partial((double)gam, slot(part, P_RZ0));
+  block_partial((double)del, slot(part, P_RZ1));
+  block_partial((double)rr, slot(part, P_RR));
   if (!last_block(ctr)) return;
   const double G = sum_partials_cg(slot(part, P_RZ0), gridDim.x);
   const double D = sum_partials_cg(slot(part, P_RZ1), gridDim.x);
@@ -149,19 +152,19 @@ __global__ void __launch_bounds__(256) k_cg_spmv(int64_t rows, int64_t nslices,
 }
 
 // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r
-__global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, double *x, double *r, double *u,
-                                                           double *p, double *s,
-                                                           const double *__restrict__ w,
-                                                           const double *__restrict__ dinv,
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, T *x, T *r, T *u, T *p, T *s,
+                                                           const T *__restrict__ w,
+                                                           const T *__restrict__ dinv,
                                                            const double *sc) {
   if (block_done(sc)) return;
-  const double alpha = sc[CG_ALPHA], beta = sc[CG_BETA];
+  const T alpha = (T)sc[CG_ALPHA], beta = (T)sc[CG_BETA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double pi = u[i] + beta * p[i];
-    const double si = w[i] + beta * s[i];
+    const T pi = u[i] + beta * p[i];
+    const T si = w[i] + beta * s[i];
     x[i] += alpha * pi;
-    const double ri = r[i] - alpha * si;
+    const T ri = r[i] - alpha * si;
     p[i] = pi;
     s[i] = si;
     r[i] = ri;
@@ -169,21 +172,30 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, double *x,
   }
 }
 
-// Solve S x = b (length n_p) to relative residual inner_rtol; returns iterations.
-static vem_status pcg_solve(vem_handle *h, const double *b, double *x, double *wk, int *iters) {
+__global__ void k_f32_to_f64(int64_t n, const float *__restrict__ a, double *b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+// Solve S x = b (length n_p) to relative residual inner_rtol with vectors,
+// matrix values and arithmetic in T; returns the iterations.
+template <class T>
+static vem_status pcg_solve_t(vem_handle *h, const T *sval, const T *dinv, const double *b, T *x,
+                              T *wk, int *iters) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n_p;
-  double *r = wk, *u = wk + n, *p = wk + 2 * n, *sv = wk + 3 * n, *w = wk + 4 * n;
+  T *r = wk, *u = wk + n, *p = wk + 2 * n, *sv = wk + 3 * n, *w = wk + 4 * n;
   const int nb = nblocks_vec(n);
   const int nbs = spmv_nblocks(h->S);
   double *sc = h->scal;
   const double tol2 = h->opt.inner_rtol * h->opt.inner_rtol;
   count_launch();
-  k_cg_init<<<nb, kRedThreads, 0, s>>>(n, b, h->s_dinv, x, r, u, p, sv, h->part, sc, h->ctr);
+  k_cg_init<T><<<nb, kRedThreads, 0, s>>>(n, b, dinv, x, r, u, p, sv, h->part, sc, h->ctr);
   auto spmv_it = [&](int it) {
     count_launch();
-    k_cg_spmv<<<nbs, 256, 0, s>>>(n, h->S.nslices, h->S.off, h->S.col, h->S.val, u, r, w, h->part, sc,
-                                  h->ctr + 1, tol2, it);
+    k_cg_spmv<T><<<nbs, 256, 0, s>>>(n, h->S.nslices, h->S.off, h->S.col, sval, u, r, w, h->part, sc,
+                                     h->ctr + 1, tol2, it);
   };
   spmv_it(0);
   const int maxit = h->opt.inner_maxit;
@@ -193,7 +205,7 @@ static vem_status pcg_solve(vem_handle *h, const double *b, double *x, double *w
     const int end = it + chunk < maxit ? it + chunk : maxit;
     for (; it < end; ++it) {
       count_launch();
-      k_cg_update<<<nb, kRedThreads, 0, s>>>(n, x, r, u, p, sv, w, h->s_dinv, sc);
+      k_cg_update<T><<<nb, kRedThreads, 0, s>>>(n, x, r, u, p, sv, w, dinv, sc);
       spmv_it(it + 1);
     }
     VEM_CUDA(h, cudaGetLastError());
@@ -208,6 +220,21 @@ static vem_status pcg_solve(vem_handle *h, const double *b, double *x, double *w
   if (h->h_scal[S_PCG_DONE] == 0.0) *iters = maxit;   // cap reached: use the iterate
   if (debug_on()) fprintf(stderr, "[vem] pcg n=%lld iters=%d done=%g\n", (long long)n, *iters, h->h_scal[S_PCG_DONE]);
   return VEM_OK;
+}
+
+// S x = b with x, b FP64; the solve runs in FP64 or, with the mixed
+// precision option, entirely in FP32 (values, vectors, arithmetic).
+static vem_status pcg_solve(vem_handle *h, const double *b, double *x, double *wk, int *iters) {
+  if (h->opt.precision == VEM_PRECISION_MIXED) {
+    float *w32 = reinterpret_cast<float *>(wk);
+    float *x32 = w32 + 5 * h->n_p;
+    VEM_TRY(pcg_solve_t<float>(h, h->S_val32, h->s_dinv32, b, x32, w32, iters));
+    count_launch();
+    k_f32_to_f64<<<grid_for(h->n_p, 256), 256, 0, h->stream>>>(h->n_p, x32, x);
+    VEM_CUDA(h, cudaGetLastError());
+    return VEM_OK;
+  }
+  return pcg_solve_t<double>(h, h->S.val, h->s_dinv, b, x, wk, iters);
 }
 
 // --------------------------------------------------------- vector ops -----
@@ -461,7 +488,7 @@ __global__ void k_gm_solve(double *sc, int k, GmLayout L) {
 
 // ------------------------------------------------------- preconditioner ---
 // z = P^{-1} v for the block preconditioner (diag or upper triangular).
-// wk: 5 n_p PCG work vectors.  If part_g2 != nullptr (MINRES) also leaves
+// wk: 5 n_p PCG work vectors (FP64 units; the FP32 solve uses 6 n_p floats of it).  If part_g2 != nullptr (MINRES) also leaves
 // the partials of v.z in slots P_G2U (flux part) and P_G2P (pressure part).
 static vem_status precond(vem_handle *h, const double *v, double *z, double *wk, int *inner,
                           bool minres_partials) {

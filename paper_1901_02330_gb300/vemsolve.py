@@ -23,7 +23,7 @@ VEM_ELEMENT_E0, VEM_ELEMENT_K1 = 0, 1
 VEM_KRYLOV_MINRES, VEM_KRYLOV_FGMRES = 0, 1
 VEM_PREC_BLOCK_DIAG, VEM_PREC_BLOCK_TRI = 0, 1
 VEM_INNER_PCG = 0
-VEM_PRECISION_FP64 = 0
+VEM_PRECISION_FP64, VEM_PRECISION_MIXED = 0, 1
 VEM_QP_CELL, VEM_QP_BFACE = 0, 1
 
 
