@@ -178,6 +178,19 @@ vem_status vem_assemble(vem_handle *h);
  * written) if rtol is not reached within maxit. */
 vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_out, vem_stats *stats);
 
+/* Adjoint gradient with respect to per-cell log K (theta_P = log K_P), for
+ * a loss L(u, p) of the last vem_solve's solution: solves the adjoint system
+ * A lambda = (dL/du, -dL/dp) (A is symmetric; the sign converts to the
+ * p~ = -p unknown) with the same Krylov method and preconditioner, then
+ * returns dL/dtheta_P = lambda_{u,P}^T M_P u_P for every cell (M_P is
+ * proportional to nu_P = exp(-theta_P), so dM_P/dtheta_P = -M_P;
+ * Sec. 4.3, a_{h,P}).  dL_du [n_u] and dL_dp [n_p] may be NULL (zero);
+ * dL_dlogK receives [n_cells].  Host or device pointers per
+ * options.device_io.  VEM_ERR_BAD_INPUT if no solution of the current
+ * assembly is held. */
+vem_status vem_adjoint(vem_handle *h, const double *dL_du, const double *dL_dp, double *dL_dlogK,
+                       vem_stats *stats);
+
 /* ---- inspection entry points (used by the parity tests) ---- */
 
 /* Geometry: face area, barycentre [3], unit normal [3], diameter per face;

@@ -327,8 +327,13 @@ vem_status vem_set_options(vem_handle *h, const vem_options *opt) {
     set_layout(h);
     h->assembled = false;
     h->rhs_ready = false;
+    h->have_solution = false;
     dfree(h, h->rhs);
     h->rhs = nullptr;
+    dfree(h, h->lam);
+    h->lam = nullptr;
+    dfree(h, h->arhs);
+    h->arhs = nullptr;
     dfree(h, h->diagM);
     h->diagM = nullptr;
     dfree(h, h->xsol);
@@ -385,6 +390,7 @@ vem_status vem_set_coefficient(vem_handle *h, const double *K) {
   VEM_CUDA(h, cudaMemcpyAsync(h->nu, nu.data(), sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->stream));
   VEM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->assembled = false;
+  h->have_solution = false;
   return VEM_OK;
 }
 
@@ -394,6 +400,7 @@ vem_status vem_set_coefficient_device(vem_handle *h, const double *K) {
   count_launch(); k_invert_check<<<grid_for(h->nc, 256), 256, 0, h->stream>>>(h->nc, K, h->nu, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   h->assembled = false;
+  h->have_solution = false;
   vem_status st = check_device_errors(h, "coefficient");
   if (st == VEM_ERR_NONFINITE) return fail(h, VEM_ERR_BAD_INPUT, "K must be finite and > 0");
   return st;
@@ -474,7 +481,7 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     }
     count_launch(); k_import_x<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n, x0d, x);
     cudaEventRecord(h->ev0, s);
-    r = krylov_solve(h, x, &st);
+    r = krylov_solve(h, h->rhs, x, &st);
     cudaEventRecord(h->ev1, s);
     cudaEventSynchronize(h->ev1);
     float ms = 0.f;
@@ -482,6 +489,7 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     st.t_solve_ms = ms;
     if (tmp) dfree(h, tmp);
     if (r != VEM_OK && r != VEM_ERR_NOT_CONVERGED) break;
+    h->have_solution = true;
     vem_status w = VEM_OK;
     if (h->opt.device_io) {
       count_launch(); k_export_x<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n_p, x, u_out, p_out);
@@ -499,6 +507,61 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
   } while (0);
   if (stats) *stats = st;
   return r;
+}
+
+__global__ void k_adjoint_rhs(int64_t nu, int64_t n, const double *gu, const double *gp, double *r) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = i < nu ? (gu ? gu[i] : 0.0) : (gp ? -gp[i - nu] : 0.0);
+}
+
+vem_status vem_adjoint(vem_handle *h, const double *dL_du, const double *dL_dp, double *dL_dlogK,
+                       vem_stats *stats) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (!dL_dlogK) return fail(h, VEM_ERR_BAD_INPUT, "dL_dlogK: NULL");
+  if (!h->have_solution || !h->assembled)
+    return fail(h, VEM_ERR_BAD_INPUT, "vem_adjoint needs a preceding vem_solve with the same K");
+  cudaStream_t s = h->stream;
+  if (!h->lam) VEM_TRY(dalloc_n(h, &h->lam, (size_t)h->n));
+  if (!h->arhs) VEM_TRY(dalloc_n(h, &h->arhs, (size_t)h->n));
+  if (!h->grad) VEM_TRY(dalloc_n(h, &h->grad, (size_t)h->nc));
+  const double *gu = dL_du, *gp = dL_dp;
+  double *tmp = nullptr;
+  if (!h->opt.device_io && (dL_du || dL_dp)) {
+    VEM_TRY(dalloc_n(h, &tmp, (size_t)h->n));
+    if (dL_du) VEM_CUDA(h, cudaMemcpyAsync(tmp, dL_du, sizeof(double) * h->n_u, cudaMemcpyHostToDevice, s));
+    if (dL_dp) VEM_CUDA(h, cudaMemcpyAsync(tmp + h->n_u, dL_dp, sizeof(double) * h->n_p, cudaMemcpyHostToDevice, s));
+    gu = dL_du ? tmp : nullptr;
+    gp = dL_dp ? tmp + h->n_u : nullptr;
+  }
+  count_launch();
+  k_adjoint_rhs<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n, gu, gp, h->arhs);
+  VEM_CUDA(h, cudaGetLastError());
+  count_launch();
+  k_import_x<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n, nullptr, h->lam);
+  vem_stats st{};
+  st.n_u = h->n_u;
+  st.n_p = h->n_p;
+  st.nnz_A = h->A.nnz;
+  st.nnz_S = h->S.nnz;
+  cudaEventRecord(h->ev0, s);
+  vem_status r = krylov_solve(h, h->arhs, h->lam, &st);
+  cudaEventRecord(h->ev1, s);
+  cudaEventSynchronize(h->ev1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  st.t_solve_ms = ms;
+  if (tmp) dfree(h, tmp);
+  if (stats) *stats = st;
+  if (r != VEM_OK) return r;
+  VEM_TRY(adjoint_contract(h, h->lam, h->xsol, h->grad));
+  if (h->opt.device_io) {
+    VEM_CUDA(h, cudaMemcpyAsync(dL_dlogK, h->grad, sizeof(double) * h->nc, cudaMemcpyDeviceToDevice, s));
+  } else {
+    VEM_CUDA(h, cudaMemcpyAsync(dL_dlogK, h->grad, sizeof(double) * h->nc, cudaMemcpyDeviceToHost, s));
+  }
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  return VEM_OK;
 }
 
 vem_status vem_get_geometry(vem_handle *h, double *fa, double *fc, double *fn, double *fd, double *cv,

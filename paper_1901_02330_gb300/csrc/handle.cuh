@@ -74,6 +74,10 @@ struct vem_handle {
   unsigned int *ctr = nullptr;                   // last-block counters (zeroed)
   double *work = nullptr;                        // Krylov vectors
   double *xsol = nullptr;                        // [n] solution iterate
+  double *lam = nullptr;                         // [n] adjoint solution
+  double *arhs = nullptr;                        // [n] adjoint right-hand side
+  double *grad = nullptr;                        // [n_cells] adjoint gradient
+  bool have_solution = false;
   int64_t *cnt_buf = nullptr;                    // [n] row counts for the scans
   int64_t *scan_buf = nullptr;                   // scan block sums
   int64_t *slice_buf = nullptr;                  // per-slice sizes
@@ -121,7 +125,10 @@ void dot_partials(cudaStream_t s, int64_t n, const double *x, const double *y, d
 vem_status sell_to_host_csr(vem_handle *h, const SellMat &A, int64_t *rp, int32_t *col, double *val);
 
 // Krylov solve (krylov.cu)
-vem_status krylov_solve(vem_handle *h, double *x, vem_stats *st);
+vem_status krylov_solve(vem_handle *h, const double *rhs, double *x, vem_stats *st);
+
+// Adjoint contraction (adjoint.cu): g_c = lam_{u,c}^T M_c u_c per cell.
+vem_status adjoint_contract(vem_handle *h, const double *lam, const double *x, double *g);
 
 }  // namespace vem
 

@@ -513,12 +513,12 @@ static vem_status precond(vem_handle *h, const double *v, double *z, double *wk,
 }
 
 // true relative residual ||b - A x|| / ||b|| (synchronises)
-static vem_status true_relres(vem_handle *h, const double *x, double *tmp, double *rel) {
+static vem_status true_relres(vem_handle *h, const double *rhs, const double *x, double *tmp, double *rel) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
   spmv(s, h->A, x, tmp);
   const int nb = nblocks_vec(n);
-  count_launch(); k_residual<<<nb, kRedThreads, 0, s>>>(n, h->rhs, tmp, tmp, slot(h->part, P_R2), slot(h->part, P_B2));
+  count_launch(); k_residual<<<nb, kRedThreads, 0, s>>>(n, rhs, tmp, tmp, slot(h->part, P_R2), slot(h->part, P_B2));
   count_launch(); k_read_sum<<<1, kRedThreads, 0, s>>>(slot(h->part, P_R2), nb, h->scal + S_R2);
   count_launch(); k_read_sum<<<1, kRedThreads, 0, s>>>(slot(h->part, P_B2), nb, h->scal + S_B2);
   VEM_CUDA(h, cudaGetLastError());
@@ -541,7 +541,7 @@ static vem_status ensure_work(vem_handle *h, size_t n) {
   return VEM_OK;
 }
 
-static vem_status run_minres(vem_handle *h, double *x, vem_stats *st) {
+static vem_status run_minres(vem_handle *h, const double *rhs, double *x, vem_stats *st) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n, nu = h->n_u, np = h->n_p;
   VEM_TRY(ensure_work(h, 8 * (size_t)n + 5 * (size_t)np));
@@ -552,7 +552,7 @@ static vem_status run_minres(vem_handle *h, double *x, vem_stats *st) {
   const int nbn = nblocks_vec(n), nbu = nblocks_vec(nu), nbp = nblocks_vec(np);
   // v = b - A x0
   spmv(s, h->A, x, tmp);
-  count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, h->rhs, tmp, v, slot(h->part, P_R2), slot(h->part, P_B2));
+  count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, rhs, tmp, v, slot(h->part, P_R2), slot(h->part, P_B2));
   VEM_CUDA(h, cudaMemsetAsync(vold, 0, sizeof(double) * n, s));
   VEM_CUDA(h, cudaMemsetAsync(wold, 0, sizeof(double) * n, s));
   VEM_CUDA(h, cudaMemsetAsync(w, 0, sizeof(double) * n, s));
@@ -561,7 +561,7 @@ static vem_status run_minres(vem_handle *h, double *x, vem_stats *st) {
   count_launch(); k_mr_init<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbu, nbp);
   VEM_CUDA(h, cudaGetLastError());
   double rel = 1.0;
-  VEM_TRY(true_relres(h, x, tmp, &rel));
+  VEM_TRY(true_relres(h, rhs, x, tmp, &rel));
   VEM_CUDA(h, cudaMemcpyAsync(h->h_scal + S_MR, h->scal + S_MR, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
   VEM_CUDA(h, cudaStreamSynchronize(s));
   const double eta0 = h->h_scal[S_MR + MR_ETA];
@@ -593,12 +593,12 @@ static vem_status run_minres(vem_handle *h, double *x, vem_stats *st) {
       return fail(h, m[MR_BAD] == 1.0 ? VEM_ERR_NONFINITE : VEM_ERR_BREAKDOWN, "MINRES breakdown");
     const bool lucky = m[MR_G] == 0.0;
     if (std::fabs(m[MR_ETA]) <= 0.5 * h->opt.rtol * eta0 || lucky) {
-      VEM_TRY(true_relres(h, x, tmp, &rel));
+      VEM_TRY(true_relres(h, rhs, x, tmp, &rel));
       if (rel <= h->opt.rtol) result = VEM_OK;
       else if (lucky) break;
     }
   }
-  if (result != VEM_OK) VEM_TRY(true_relres(h, x, tmp, &rel));
+  if (result != VEM_OK) VEM_TRY(true_relres(h, rhs, x, tmp, &rel));
   st->iterations = it;
   st->inner_iterations = inner;
   st->relres = rel;
@@ -606,7 +606,7 @@ static vem_status run_minres(vem_handle *h, double *x, vem_stats *st) {
   return VEM_OK;
 }
 
-static vem_status run_fgmres(vem_handle *h, double *x, vem_stats *st) {
+static vem_status run_fgmres(vem_handle *h, const double *rhs, double *x, vem_stats *st) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n, np = h->n_p;
   const int m = h->opt.restart;
@@ -617,14 +617,14 @@ static vem_status run_fgmres(vem_handle *h, double *x, vem_stats *st) {
   int inner = 0, it = 0;
   const int nbn = nblocks_vec(n);
   double rel = 1.0;
-  VEM_TRY(true_relres(h, x, tmp, &rel));
+  VEM_TRY(true_relres(h, rhs, x, tmp, &rel));
   vem_status result = rel <= h->opt.rtol ? VEM_OK : VEM_ERR_NOT_CONVERGED;
   double bnorm = std::sqrt(h->h_scal[S_B2]);
   if (bnorm == 0.0) bnorm = 1.0;
   while (result != VEM_OK && it < h->opt.maxit) {
     // V_0 = (b - A x) / beta
     spmv(s, h->A, x, tmp);
-    count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, h->rhs, tmp, V, slot(h->part, P_R2), slot(h->part, P_B2));
+    count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, rhs, tmp, V, slot(h->part, P_R2), slot(h->part, P_B2));
     count_launch(); k_gm_start<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbn, L);
     count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, V, h->scal + GM_IBETA);
     int jd = 0;
@@ -661,7 +661,7 @@ static vem_status run_fgmres(vem_handle *h, double *x, vem_stats *st) {
     count_launch(); k_gm_solve<<<1, 32, 0, s>>>(h->scal, jd, L);
     count_launch(); k_multiaxpy<<<nbn, kRedThreads, 0, s>>>(n, Z, jd, h->scal + L.Y(0), 1.0, x, nullptr);
     VEM_CUDA(h, cudaGetLastError());
-    VEM_TRY(true_relres(h, x, tmp, &rel));
+    VEM_TRY(true_relres(h, rhs, x, tmp, &rel));
     if (rel <= h->opt.rtol) result = VEM_OK;
   }
   st->iterations = it;
@@ -671,13 +671,13 @@ static vem_status run_fgmres(vem_handle *h, double *x, vem_stats *st) {
   return VEM_OK;
 }
 
-vem_status krylov_solve(vem_handle *h, double *x, vem_stats *st) {
+vem_status krylov_solve(vem_handle *h, const double *rhs, double *x, vem_stats *st) {
   if (h->opt.krylov == VEM_KRYLOV_MINRES) {
     if (h->opt.precond != VEM_PREC_BLOCK_DIAG)
       return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs the block-diagonal preconditioner");
-    return run_minres(h, x, st);
+    return run_minres(h, rhs, x, st);
   }
-  if (h->opt.krylov == VEM_KRYLOV_FGMRES) return run_fgmres(h, x, st);
+  if (h->opt.krylov == VEM_KRYLOV_FGMRES) return run_fgmres(h, rhs, x, st);
   return fail(h, VEM_ERR_BAD_INPUT, "unknown Krylov method %d", h->opt.krylov);
 }
 

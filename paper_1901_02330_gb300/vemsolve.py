@@ -72,6 +72,7 @@ _SIGS = {
     "vem_set_source_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_assemble": (C.c_int, [C.c_void_p]),
     "vem_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(vem_stats)]),
+    "vem_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(vem_stats)]),
     "vem_get_geometry": (C.c_int, [C.c_void_p] + [C.c_void_p] * 7),
     "vem_local_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "vem_get_local": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -168,6 +169,7 @@ class Solver:
         self.n_faces = int(fvp.shape[0] - 1)
         self.n_cells = int(cfp.shape[0] - 1)
         self.cell_face_ptr = cfp.copy()
+        self.generation = 0          # counts solves (the adjoint uses the latest)
 
     # -- status handling
     def _check(self, st, what=""):
@@ -251,9 +253,21 @@ class Solver:
             x0 = x0 if hasattr(x0, "data_ptr") else np.ascontiguousarray(x0, dtype=np.float64)
             x0p = _ptr(x0)
         code = lib().vem_solve(self._h, x0p, _ptr(u_out), _ptr(p_out), C.byref(st))
+        self.generation += 1
         if not (code == 3 and allow_not_converged):
             self._check(code)
         return u_out, p_out, st.as_dict()
+
+    def adjoint(self, dL_du=None, dL_dp=None, out=None):
+        """dL/dlog K per cell for the last solve (host numpy unless device_io)."""
+        if out is None:
+            out = np.zeros(self.n_cells)
+        if not self.options.device_io:
+            dL_du = None if dL_du is None else np.ascontiguousarray(dL_du, dtype=np.float64)
+            dL_dp = None if dL_dp is None else np.ascontiguousarray(dL_dp, dtype=np.float64)
+        st = vem_stats()
+        self._check(lib().vem_adjoint(self._h, _ptr(dL_du), _ptr(dL_dp), _ptr(out), C.byref(st)))
+        return out, st.as_dict()
 
     def geometry(self):
         nf, nc = self.n_faces, self.n_cells
