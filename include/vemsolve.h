@@ -178,6 +178,24 @@ vem_status vem_assemble(vem_handle *h);
  * written) if rtol is not reached within maxit. */
 vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_out, vem_stats *stats);
 
+/* Batched solve of nbatch problems on the same mesh (the batched form of the
+ * same discretisation: per-system coefficient and data, Sec. 4.3 forms):
+ * K [nbatch][n_cells] (> 0), f_qp [nbatch][n_cells] and gD_qp
+ * [nbatch][n_bqp] at the VEM_QP_CELL / VEM_QP_BFACE points (NULL = zero).
+ * The systems share the sparsity structure: their saddle matrices and Schur
+ * approximations are stored as one structure with per-system values, every
+ * A-apply is one launch over all systems, and the Krylov method and
+ * preconditioner of the options run on the block-diagonal stacked system
+ * (one Krylov process for all systems, stopped when every system's true
+ * relative residual is <= rtol).  Writes u_out [nbatch][n_u], p_out
+ * [nbatch][n_p] (host or device per options.device_io) and, if not NULL,
+ * relres_out [nbatch] (host).  stats->relres is the worst system's.
+ * Invalidates the single-system assembly (local matrices are rebuilt with
+ * nu = 1 and scaled per system). */
+vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, const double *f_qp,
+                             const double *gD_qp, double *u_out, double *p_out, double *relres_out,
+                             vem_stats *stats);
+
 /* Adjoint gradient with respect to per-cell log K (theta_P = log K_P), for
  * a loss L(u, p) of the last vem_solve's solution: solves the adjoint system
  * A lambda = (dL/du, -dL/dp) (A is symmetric; the sign converts to the

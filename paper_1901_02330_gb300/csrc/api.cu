@@ -274,6 +274,38 @@ __global__ void k_import_x(int64_t nu, int64_t n, const double *x0, double *x) {
     x[i] = x0 ? (i < nu ? x0[i] : -x0[i]) : 0.0;
 }
 
+// Euclidean norm of each stacked system's entries (one block per system).
+__global__ void k_segment_norms(int nb, int64_t nu1, int64_t np1, const double *__restrict__ v, double *out) {
+  const int64_t b = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < nu1; i += blockDim.x) {
+    const double t = v[b * nu1 + i];
+    s += t * t;
+  }
+  for (int64_t i = threadIdx.x; i < np1; i += blockDim.x) {
+    const double t = v[(int64_t)nb * nu1 + b * np1 + i];
+    s += t * t;
+  }
+  block_partial(s, out);
+  if (threadIdx.x == 0) out[blockIdx.x] = sqrt(out[blockIdx.x]);
+}
+
+__global__ void k_sub(int64_t n, const double *__restrict__ a, const double *__restrict__ b, double *c) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c[i] = a[i] - b[i];
+}
+
+template <class T>
+static vem_status batch_buf(vem_handle *h, T **p, size_t n, bool grow) {
+  if (grow || !*p) {
+    dfree(h, *p);
+    *p = nullptr;
+    VEM_TRY(dalloc_n(h, p, n));
+  }
+  return VEM_OK;
+}
+
 }  // namespace vem
 
 using namespace vem;
@@ -481,7 +513,7 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     }
     count_launch(); k_import_x<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n, x0d, x);
     cudaEventRecord(h->ev0, s);
-    r = krylov_solve(h, h->rhs, x, &st);
+    r = krylov_solve(h, single_op(h), h->rhs, x, &st);
     cudaEventRecord(h->ev1, s);
     cudaEventSynchronize(h->ev1);
     float ms = 0.f;
@@ -545,7 +577,7 @@ vem_status vem_adjoint(vem_handle *h, const double *dL_du, const double *dL_dp, 
   st.nnz_A = h->A.nnz;
   st.nnz_S = h->S.nnz;
   cudaEventRecord(h->ev0, s);
-  vem_status r = krylov_solve(h, h->arhs, h->lam, &st);
+  vem_status r = krylov_solve(h, single_op(h), h->arhs, h->lam, &st);
   cudaEventRecord(h->ev1, s);
   cudaEventSynchronize(h->ev1);
   float ms = 0.f;
@@ -562,6 +594,149 @@ vem_status vem_adjoint(vem_handle *h, const double *dL_du, const double *dL_dp, 
   }
   VEM_CUDA(h, cudaStreamSynchronize(s));
   return VEM_OK;
+}
+
+vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, const double *f_qp,
+                             const double *gD_qp, double *u_out, double *p_out, double *relres_out,
+                             vem_stats *stats) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (nbatch < 1 || nbatch > 65535) return fail(h, VEM_ERR_BAD_INPUT, "nbatch %lld", (long long)nbatch);
+  if (!K || !u_out || !p_out) return fail(h, VEM_ERR_BAD_INPUT, "K / u_out / p_out: NULL");
+  cudaStream_t s = h->stream;
+  const int nb = (int)nbatch;
+  const bool dev = h->opt.device_io != 0;
+  // structure of A and S from a single-system assembly
+  if (!h->assembled) VEM_TRY(assemble_impl(h));
+  const bool grow = nb > h->b_cap;
+  const int64_t nbq = std::max<int64_t>(h->n_bqp, 1);
+  VEM_TRY(batch_buf(h, &h->b_nu, (size_t)nb * h->nc, grow));
+  VEM_TRY(batch_buf(h, &h->b_fqp, (size_t)nb * h->nc, grow));
+  VEM_TRY(batch_buf(h, &h->b_gqp, (size_t)nb * nbq, grow));
+  VEM_TRY(batch_buf(h, &h->b_rhs, (size_t)nb * h->n, grow));
+  VEM_TRY(batch_buf(h, &h->b_x, (size_t)nb * h->n, grow));
+  VemOp &op = h->bop;
+  const bool regrow = grow || op.A.stored != h->A.stored || op.S.stored != h->S.stored || op.n_u1 != h->n_u;
+  VEM_TRY(batch_buf(h, &op.A.val, (size_t)nb * h->A.stored, regrow));
+  VEM_TRY(batch_buf(h, &op.diagM, (size_t)nb * h->n_u, regrow));
+  VEM_TRY(batch_buf(h, &op.S.val, (size_t)nb * h->S.stored, regrow));
+  VEM_TRY(batch_buf(h, &op.s_dinv, (size_t)nb * h->nc, regrow));
+  VEM_TRY(batch_buf(h, &op.S_val32, (size_t)nb * h->S.stored, regrow));
+  VEM_TRY(batch_buf(h, &op.s_dinv32, (size_t)nb * h->nc, regrow));
+  if (grow) h->b_cap = nb;
+  op.A.rows = h->A.rows; op.A.nslices = h->A.nslices; op.A.stored = h->A.stored; op.A.nnz = h->A.nnz;
+  op.A.off = h->A.off; op.A.len = h->A.len; op.A.col = h->A.col;
+  op.S.rows = h->S.rows; op.S.nslices = h->S.nslices; op.S.stored = h->S.stored; op.S.nnz = h->S.nnz;
+  op.S.off = h->S.off; op.S.len = h->S.len; op.S.col = h->S.col;
+  op.n_u1 = h->n_u;
+  op.n_p1 = h->n_p;
+  op.n_u = (int64_t)nb * h->n_u;
+  op.n_p = (int64_t)nb * h->n_p;
+  op.n = op.n_u + op.n_p;
+  op.nbatch = nb;
+  // inputs
+  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  VEM_CUDA(h, cudaMemcpyAsync(h->b_fqp, K, sizeof(double) * nb * h->nc, kind, s));   // staging
+  count_launch();
+  k_invert_check<<<grid_for((int64_t)nb * h->nc, 256), 256, 0, s>>>((int64_t)nb * h->nc, h->b_fqp, h->b_nu, h->d_err);
+  VEM_CUDA(h, cudaGetLastError());
+  {
+    vem_status e = check_device_errors(h, "batched coefficient");
+    if (e == VEM_ERR_NONFINITE) return fail(h, VEM_ERR_BAD_INPUT, "K must be finite and > 0");
+    if (e != VEM_OK) return e;
+  }
+  if (f_qp) VEM_CUDA(h, cudaMemcpyAsync(h->b_fqp, f_qp, sizeof(double) * nb * h->nc, kind, s));
+  else VEM_CUDA(h, cudaMemsetAsync(h->b_fqp, 0, sizeof(double) * nb * h->nc, s));
+  if (gD_qp && h->n_bqp > 0) VEM_CUDA(h, cudaMemcpyAsync(h->b_gqp, gD_qp, sizeof(double) * nb * h->n_bqp, kind, s));
+  else VEM_CUDA(h, cudaMemsetAsync(h->b_gqp, 0, sizeof(double) * nb * nbq, s));
+  // geometry-only local matrices (nu = 1), then the per-system values
+  if (!h->unit_nu) {
+    VEM_TRY(dalloc_n(h, &h->unit_nu, (size_t)h->nc));
+    std::vector<double> ones(h->nc, 1.0);
+    VEM_CUDA(h, cudaMemcpyAsync(h->unit_nu, ones.data(), sizeof(double) * h->nc, cudaMemcpyHostToDevice, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+  }
+  cudaEventRecord(h->ev0, s);
+  VEM_TRY(assemble_local_nu(h, h->unit_nu));
+  h->assembled = false;      // the local matrices no longer carry the single system's nu
+  h->have_solution = false;
+  VEM_TRY(assemble_batched_values(h, nb, h->b_nu, op));
+  for (int b = 0; b < nb; ++b)
+    VEM_TRY(assemble_rhs_into(h, h->b_fqp + (int64_t)b * h->nc, (gD_qp && h->n_bqp > 0) ? h->b_gqp + (int64_t)b * nbq : nullptr,
+                              h->b_rhs + (int64_t)b * h->n_u, h->b_rhs + op.n_u + (int64_t)b * h->n_p));
+  VEM_TRY(check_device_errors(h, "batched right-hand side"));
+  cudaEventRecord(h->ev1, s);
+  cudaEventSynchronize(h->ev1);
+  float tas = 0.f;
+  cudaEventElapsedTime(&tas, h->ev0, h->ev1);
+  // per-system right-hand-side norms: the shared Krylov process stops when
+  // ||r|| <= rtol min_b ||b_b||, so that every system meets rtol
+  std::vector<double> bn(nb), rn(nb);
+  double *dn = h->part;   // nb <= 65535 norms fit in the partial-sum buffer
+  count_launch();
+  k_segment_norms<<<nb, 256, 0, s>>>(nb, h->n_u, h->n_p, h->b_rhs, dn);
+  VEM_CUDA(h, cudaMemcpyAsync(bn.data(), dn, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  double bmin = 0.0, btot = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    btot += bn[b] * bn[b];
+    if (bn[b] > 0.0) bmin = (bmin == 0.0) ? bn[b] : std::min(bmin, bn[b]);
+  }
+  btot = std::sqrt(btot);
+  const double rtol = h->opt.rtol;
+  if (btot > 0.0 && bmin > 0.0) h->opt.rtol = rtol * bmin / btot;
+  count_launch();
+  k_import_x<<<grid_for(op.n, 256), 256, 0, s>>>(op.n_u, op.n, nullptr, h->b_x);
+  vem_stats st{};
+  st.n_u = op.n_u;
+  st.n_p = op.n_p;
+  st.nnz_A = h->A.nnz;
+  st.nnz_S = h->S.nnz;
+  st.t_assemble_ms = tas;
+  cudaEventRecord(h->ev0, s);
+  vem_status r = krylov_solve(h, op, h->b_rhs, h->b_x, &st);
+  cudaEventRecord(h->ev1, s);
+  cudaEventSynchronize(h->ev1);
+  h->opt.rtol = rtol;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  st.t_solve_ms = ms;
+  if (r != VEM_OK && r != VEM_ERR_NOT_CONVERGED) {
+    if (stats) *stats = st;
+    return r;
+  }
+  // per-system true relative residuals
+  double *tmp = nullptr;
+  VEM_TRY(dalloc_n(h, &tmp, (size_t)op.n));
+  spmv_batched(s, op.A, nb, h->n_u, op.A.val, h->b_x, tmp);
+  count_launch();
+  k_sub<<<grid_for(op.n, 256), 256, 0, s>>>(op.n, h->b_rhs, tmp, tmp);
+  count_launch();
+  k_segment_norms<<<nb, 256, 0, s>>>(nb, h->n_u, h->n_p, tmp, dn);
+  VEM_CUDA(h, cudaMemcpyAsync(rn.data(), dn, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  dfree(h, tmp);
+  double worst = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    rn[b] = bn[b] > 0.0 ? rn[b] / bn[b] : rn[b];
+    worst = std::max(worst, rn[b]);
+  }
+  st.relres = worst;
+  if (stats) *stats = st;
+  if (relres_out) std::memcpy(relres_out, rn.data(), sizeof(double) * nb);
+  // outputs: u_b contiguous, p_b = -p~_b
+  if (dev) {
+    count_launch();
+    k_export_x<<<grid_for(op.n, 256), 256, 0, s>>>(op.n_u, op.n_p, h->b_x, u_out, p_out);
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+  } else {
+    VEM_CUDA(h, cudaMemcpyAsync(u_out, h->b_x, sizeof(double) * op.n_u, cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaMemcpyAsync(p_out, h->b_x + op.n_u, sizeof(double) * op.n_p, cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < op.n_p; ++i) p_out[i] = -p_out[i];
+  }
+  if (r == VEM_OK && worst > rtol)
+    return fail(h, VEM_ERR_NOT_CONVERGED, "batched solve: worst relres %.3e", worst);
+  return r;
 }
 
 vem_status vem_get_geometry(vem_handle *h, double *fa, double *fc, double *fn, double *fd, double *cv,

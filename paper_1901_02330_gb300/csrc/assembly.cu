@@ -59,9 +59,18 @@ __global__ void k_rowcount(Layout L, int64_t *cnt) {
 // One thread per row, consecutive rows on consecutive lanes, so element j of
 // the 32 rows of a slice is written by one coalesced store.  Ghost rows of
 // the last slice and the padding of short rows get value 0, column 0.
+// Batched use (gridDim.y systems): values of system b at val + b * stored,
+// diag(M) at diagM + b * n_u, local matrices scaled by nu_scale[b * nc + c]
+// (the local matrices then hold nu = 1); col == nullptr skips the (shared)
+// column ids.
 __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                       int64_t nrows_pad, int32_t *col, double *val, double *diagM) {
+                       int64_t nrows_pad, int32_t *col, double *val, double *diagM,
+                       const double *__restrict__ nu_scale, int64_t stored) {
   const int64_t n = L.n_u + L.nc;
+  const int64_t bb = blockIdx.y;
+  val += bb * stored;
+  diagM += bb * L.n_u;
+  const double *nsc = nu_scale ? nu_scale + bb * L.nc : nullptr;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows_pad;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s0 = off[r >> 5];
@@ -71,7 +80,7 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t 
 #define PUT(c_, v_)                          \
   do {                                       \
     const int64_t q_ = s0 + ((int64_t)j << 5) + lane; \
-    col[q_] = (int32_t)(c_);                 \
+    if (col) col[q_] = (int32_t)(c_);        \
     val[q_] = (v_);                          \
     ++j;                                     \
   } while (0)
@@ -90,11 +99,12 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t 
         n1 = nloc(L, c1);
         M1 = L.Mloc + L.m_off[c1] + (int64_t)(l1 * L.nfd + beta) * n1;
       }
+      const double w0 = nsc ? nsc[c0] : 1.0, w1 = (nsc && c1 >= 0) ? nsc[c1] : 1.0;
       double dg = 0.0;
       for (int jl = 0; jl < n0; ++jl) {
-        double v = M0[jl];
+        double v = w0 * M0[jl];
         const bool shared = (jl < n0 - L.nid) && (jl / L.nfd == l0);
-        if (c1 >= 0 && shared) v += M1[l1 * L.nfd + jl % L.nfd];
+        if (c1 >= 0 && shared) v += w1 * M1[l1 * L.nfd + jl % L.nfd];
         if (shared && jl % L.nfd == beta) dg = v;
         PUT(gcol(L, c0, jl), v);
       }
@@ -102,7 +112,7 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t 
         const int k1 = (n1 - L.nid) / L.nfd;
         for (int jl = 0; jl < n1; ++jl) {
           if (jl < L.nfd * k1 && jl / L.nfd == l1) continue;
-          PUT(gcol(L, c1, jl), M1[jl]);
+          PUT(gcol(L, c1, jl), w1 * M1[jl]);
         }
       }
       if (beta == 0) {
@@ -117,8 +127,9 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t 
       const int nl = nloc(L, c);
       const int jr = nl - L.nid + l;
       const double *Mr = L.Mloc + L.m_off[c] + (int64_t)jr * nl;
-      for (int jl = 0; jl < nl; ++jl) PUT(gcol(L, c, jl), Mr[jl]);
-      diagM[r] = Mr[jr];
+      const double wc = nsc ? nsc[c] : 1.0;
+      for (int jl = 0; jl < nl; ++jl) PUT(gcol(L, c, jl), wc * Mr[jl]);
+      diagM[r] = wc * Mr[jr];
     } else {
       const int64_t c = r - L.n_u;
       const int k = (int)(L.cfp[c + 1] - L.cfp[c]);
@@ -141,7 +152,12 @@ __global__ void k_schur_count(Layout L, int64_t *cnt) {
 }
 
 __global__ void k_schur_fill(Layout L, const double *__restrict__ diagM, const int64_t *__restrict__ off,
-                             int64_t nrows_pad, int32_t *col, double *val, double *dinv, int *err) {
+                             int64_t nrows_pad, int32_t *col, double *val, double *dinv, int *err,
+                             int64_t stored) {
+  const int64_t bb = blockIdx.y;
+  diagM += bb * L.n_u;
+  val += bb * stored;
+  dinv += bb * L.nc;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nrows_pad;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s0 = off[c >> 5];
@@ -164,18 +180,18 @@ __global__ void k_schur_fill(Layout L, const double *__restrict__ diagM, const i
         const int32_t q = (c0 == c) ? c1 : c0;
         const int lq = (c0 == c) ? L.f_loc[2 * f + 1] : L.f_loc[2 * f];
         const int64_t p = s0 + ((int64_t)j << 5) + lane;
-        col[p] = q;
+        if (col) col[p] = q;
         val[p] = bp * L.Bloc[boff(L, q) + lq * L.nfd] / mf;
         ++j;
       }
-      col[s0 + lane] = (int32_t)c;
+      if (col) col[s0 + lane] = (int32_t)c;
       val[s0 + lane] = dg;
       if (!(dg > 0.0) || !isfinite(dg)) atomicOr(err, DEVERR_NONFINITE);
       dinv[c] = 1.0 / dg;
     }
     for (; j < width; ++j) {
       const int64_t p = s0 + ((int64_t)j << 5) + lane;
-      col[p] = 0;
+      if (col) col[p] = 0;
       val[p] = 0.0;
     }
   }
@@ -397,7 +413,8 @@ vem_status assemble_global(vem_handle *h) {
   VEM_TRY(sell_layout(h, h->A, n, cnt));
   if (!h->diagM) VEM_TRY(dalloc_n(h, &h->diagM, (size_t)h->n_u));
   const int64_t npad = h->A.nslices * 32;
-  count_launch(); k_fill<<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, h->A.len, npad, h->A.col, h->A.val, h->diagM);
+  count_launch(); k_fill<<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, h->A.len, npad, h->A.col, h->A.val, h->diagM,
+                                                      nullptr, h->A.stored);
   VEM_CUDA(h, cudaGetLastError());
   // ---- S ----
   count_launch(); k_schur_count<<<grid_for(h->nc, T), T, 0, s>>>(L, cnt);
@@ -406,7 +423,7 @@ vem_status assemble_global(vem_handle *h) {
   if (!h->s_dinv) VEM_TRY(dalloc_n(h, &h->s_dinv, (size_t)h->nc));
   const int64_t spad = h->S.nslices * 32;
   count_launch(); k_schur_fill<<<grid_for(spad, T), T, 0, s>>>(L, h->diagM, h->S.off, spad, h->S.col, h->S.val,
-                                                          h->s_dinv, h->d_err);
+                                                          h->s_dinv, h->d_err, h->S.stored);
   VEM_CUDA(h, cudaGetLastError());
   // FP32 copies of S for the mixed-precision inner solve
   if (h->s32_stored != h->S.stored) {
@@ -427,6 +444,28 @@ vem_status assemble_global(vem_handle *h) {
   VEM_TRY(sell_nnz(h, h->A));
   VEM_TRY(sell_nnz(h, h->S));
   return VEM_OK;
+}
+
+// Values of nb systems that share the mesh and the structure of h->A / h->S:
+// A_b, diag(M_b), S_b, 1/diag(S_b) (and FP32 copies), from local matrices
+// computed with nu = 1 and scaled per cell by nu_b = 1/K_b.
+vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, VemOp &op) {
+  cudaStream_t s = h->stream;
+  Layout L{h->nfd, h->nid, h->nf, h->nc, h->n_u, h->cf_ptr, h->cf, h->f_cell, h->f_loc,
+           h->m_off, h->Mloc, h->Bloc};
+  const int T = 256;
+  const int64_t npad = h->A.nslices * 32, spad = h->S.nslices * 32;
+  dim3 ga(grid_for(npad, T, 2), nb), gs(grid_for(spad, T, 2), nb);
+  count_launch();
+  k_fill<<<ga, T, 0, s>>>(L, h->A.off, h->A.len, npad, nullptr, op.A.val, op.diagM, nu_b, h->A.stored);
+  count_launch();
+  k_schur_fill<<<gs, T, 0, s>>>(L, op.diagM, h->S.off, spad, nullptr, op.S.val, op.s_dinv, h->d_err, h->S.stored);
+  count_launch();
+  k_f64_to_f32<<<grid_for(nb * h->S.stored, T), T, 0, s>>>(nb * h->S.stored, op.S.val, op.S_val32);
+  count_launch();
+  k_f64_to_f32<<<grid_for(nb * h->nc, T), T, 0, s>>>(nb * h->nc, op.s_dinv, op.s_dinv32);
+  VEM_CUDA(h, cudaGetLastError());
+  return check_device_errors(h, "batched assembly");
 }
 
 }  // namespace vem

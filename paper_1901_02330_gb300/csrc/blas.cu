@@ -39,8 +39,8 @@ int nblocks_vec(int64_t n) {
   return (int)b;
 }
 
-int spmv_nblocks(const SellMat &A) {
-  int64_t b = (A.nslices + 7) / 8;   // one warp per slice, 8 warps per block
+int spmv_nblocks(const SellMat &A, int nbatch) {
+  int64_t b = (A.nslices * nbatch + 7) / 8;   // one warp per slice, 8 warps per block
   int64_t cap = (int64_t)num_sms() * 8;
   if (cap > kMaxBlocks) cap = kMaxBlocks;
   if (b > cap) b = cap;
@@ -75,7 +75,59 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int64_t rows, int64_t nslices
 
 void spmv(cudaStream_t s, const SellMat &A, const double *x, double *y, double *dot_part) {
   count_launch();
-  k_sell_spmv<<<spmv_nblocks(A), 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, A.val, x, y, dot_part);
+  k_sell_spmv<<<spmv_nblocks(A, 1), 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, A.val, x, y, dot_part);
+}
+
+// Batched y = A_b x_b for nb systems sharing one SELL structure (column ids
+// read once per system from the shared arrays), values of system b at
+// vals + b * stored.  Stacked vector layout: local index i < split of system
+// b at b * split + i, the others at nb * split + b * (rows - split) + (i - split).
+__global__ void __launch_bounds__(256) k_sell_spmv_b(int64_t rows, int64_t nslices, int nb, int64_t split,
+                                                     int64_t stored, const int64_t *__restrict__ off,
+                                                     const int32_t *__restrict__ col,
+                                                     const double *__restrict__ vals,
+                                                     const double *__restrict__ x, double *__restrict__ y,
+                                                     double *dot_part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double dacc = 0.0;
+  const int64_t tasks = nslices * nb;
+  for (int64_t tk = warp; tk < tasks; tk += nwarps) {
+    const int64_t b = tk / nslices, s = tk - b * nslices;
+    const int64_t olo = b * split, ohi = (int64_t)(nb - 1) * split + b * (rows - split);
+    const int64_t o = off[s];
+    const int w = (int)((off[s + 1] - o) >> 5);
+    const double *vp = vals + b * stored + o + lane;
+    const int32_t *cp = col + o + lane;
+    double s0 = 0.0, s1 = 0.0;
+    int j = 0;
+    for (; j + 1 < w; j += 2) {
+      const int64_t c0 = __ldcs(cp + 32 * j), c1 = __ldcs(cp + 32 * (j + 1));
+      const double v0 = __ldcs(vp + 32 * j), v1 = __ldcs(vp + 32 * (j + 1));
+      s0 += v0 * __ldg(x + c0 + (c0 < split ? olo : ohi));
+      s1 += v1 * __ldg(x + c1 + (c1 < split ? olo : ohi));
+    }
+    if (j < w) {
+      const int64_t c0 = __ldcs(cp + 32 * j);
+      s0 += __ldcs(vp + 32 * j) * __ldg(x + c0 + (c0 < split ? olo : ohi));
+    }
+    const double t = s0 + s1;
+    const int64_t r = 32 * s + lane;
+    if (r < rows) {
+      const int64_t R = r + (r < split ? olo : ohi);
+      y[R] = t;
+      if (dot_part) dacc += t * x[R];
+    }
+  }
+  if (dot_part) block_partial(dacc, dot_part);
+}
+
+void spmv_batched(cudaStream_t s, const SellMat &A, int nb, int64_t split, const double *vals,
+                  const double *x, double *y, double *dot_part) {
+  count_launch();
+  k_sell_spmv_b<<<spmv_nblocks(A, nb), 256, 0, s>>>(A.rows, A.nslices, nb, split, A.stored, A.off, A.col, vals,
+                                                    x, y, dot_part);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_dot(int64_t n, const double *__restrict__ x,

@@ -493,7 +493,9 @@ static int warps_per_block(size_t bytes_per_warp, size_t limit = 96 * 1024) {
   return w;
 }
 
-vem_status assemble_local(vem_handle *h) {
+vem_status assemble_local(vem_handle *h) { return assemble_local_nu(h, h->nu); }
+
+vem_status assemble_local_nu(vem_handle *h, const double *nu) {
   cudaStream_t s = h->stream;
   const int mx = h->max_nf_cell;
   if (h->opt.element == VEM_ELEMENT_E0) {
@@ -506,7 +508,7 @@ vem_status assemble_local(vem_handle *h) {
     const int64_t cap = (int64_t)num_sms() * 16;
     if (blocks > cap) blocks = cap;
     count_launch(); k_elem_e0<<<(int)blocks, 32 * wpb, smem, s>>>(h->nc, mx, h->cf_ptr, h->cf, h->cf_sigma, h->f_area,
-                                                   h->f_cent, h->f_norm, h->c_vol, h->c_cent, h->nu,
+                                                   h->f_cent, h->f_norm, h->c_vol, h->c_cent, nu,
                                                    h->m_off, h->Mloc, h->Bloc);
     VEM_CUDA(h, cudaGetLastError());
   } else if (h->opt.element == VEM_ELEMENT_K1) {
@@ -520,7 +522,7 @@ vem_status assemble_local(vem_handle *h) {
     if (blocks > cap) blocks = cap;
     count_launch(); k_elem_k1<<<(int)blocks, 32 * wpb, smem, s>>>(
         h->nc, mx, h->cf_ptr, h->cf, h->cf_sigma, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent,
-        h->f_norm, h->f_t1, h->f_diam, h->c_cent, h->c_diam, h->nu, h->m_off, h->Mloc, h->Bloc,
+        h->f_norm, h->f_t1, h->f_diam, h->c_cent, h->c_diam, nu, h->m_off, h->Mloc, h->Bloc,
         h->d_err);
     VEM_CUDA(h, cudaGetLastError());
   } else {
@@ -529,17 +531,22 @@ vem_status assemble_local(vem_handle *h) {
   return check_device_errors(h, "element matrices");
 }
 
-vem_status assemble_rhs(vem_handle *h) {
+vem_status assemble_rhs_into(vem_handle *h, const double *f_qp, const double *gD_qp, double *g, double *F) {
   cudaStream_t s = h->stream;
   const int T = 128;
   count_launch(); k_rhs_faces<<<grid_for(h->nf, T), T, 0, s>>>(
       h->nf, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm,
-      h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, h->gD_qp, h->rhs, h->d_err);
+      h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, gD_qp, g, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   if (h->nid > 0)
-    VEM_CUDA(h, cudaMemsetAsync(h->rhs + h->nfd * h->nf, 0, sizeof(double) * h->nid * h->nc, s));
-  count_launch(); k_rhs_cells<<<grid_for(h->nc, T), T, 0, s>>>(h->nc, h->c_vol, h->f_qp, h->rhs + h->n_u, h->d_err);
+    VEM_CUDA(h, cudaMemsetAsync(g + h->nfd * h->nf, 0, sizeof(double) * h->nid * h->nc, s));
+  count_launch(); k_rhs_cells<<<grid_for(h->nc, T), T, 0, s>>>(h->nc, h->c_vol, f_qp, F, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
+vem_status assemble_rhs(vem_handle *h) {
+  VEM_TRY(assemble_rhs_into(h, h->f_qp, h->gD_qp, h->rhs, h->rhs + h->n_u));
   VEM_TRY(check_device_errors(h, "right-hand side"));
   h->rhs_ready = true;
   return VEM_OK;

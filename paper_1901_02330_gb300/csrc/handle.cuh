@@ -9,6 +9,19 @@
 
 #include "common.cuh"
 
+// The operator a Krylov solve works on: the saddle matrix A, the Schur
+// approximation S and the preconditioner's diagonals, with sizes.  nbatch > 1
+// stacks nbatch systems that share the mesh as one block-diagonal system with
+// the vector layout [u_0 .. u_{nb-1}; p_0 .. p_{nb-1}].
+struct VemOp {
+  vem::SellMat A, S;
+  double *diagM = nullptr, *s_dinv = nullptr;
+  float *S_val32 = nullptr, *s_dinv32 = nullptr;
+  int64_t n_u = 0, n_p = 0, n = 0;       // stacked sizes
+  int64_t n_u1 = 0, n_p1 = 0;            // sizes of one system
+  int nbatch = 1;
+};
+
 struct vem_handle {
   vem_options opt{};
   cudaStream_t stream = nullptr;
@@ -87,6 +100,12 @@ struct vem_handle {
   std::vector<void *> allocations;               // everything cudaMalloc'ed
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   double t_assemble_ms = 0.0, t_element_ms = 0.0, t_scatter_ms = 0.0;
+
+  // ---- batched systems ----
+  VemOp bop;                                     // stacked operator (values per batch)
+  double *b_nu = nullptr, *b_rhs = nullptr, *b_x = nullptr, *b_fqp = nullptr, *b_gqp = nullptr;
+  double *unit_nu = nullptr;                     // nu = 1 (geometry-only local matrices)
+  int b_cap = 0;                                 // batches the buffers hold
 };
 
 namespace vem {
@@ -114,19 +133,28 @@ int grid_for(int64_t n, int threads, int per_sm = 8);
 vem_status geometry_build(vem_handle *h);
 vem_status assemble_local(vem_handle *h);
 vem_status assemble_rhs(vem_handle *h);
+vem_status assemble_rhs_into(vem_handle *h, const double *f_qp, const double *gD_qp, double *g, double *F);
 vem_status assemble_global(vem_handle *h);
 
 // BLAS-like launches (blas.cu)
 void spmv(cudaStream_t s, const SellMat &A, const double *x, double *y, double *dot_part = nullptr);
-int spmv_nblocks(const SellMat &A);
+// batched: nb systems sharing A's structure, values of system b at
+// vals + b * A.stored, vectors in the stacked layout with split `split`
+void spmv_batched(cudaStream_t s, const SellMat &A, int nb, int64_t split, const double *vals,
+                  const double *x, double *y, double *dot_part = nullptr);
+int spmv_nblocks(const SellMat &A, int nbatch = 1);
 int nblocks_vec(int64_t n);
 void dot_partials(cudaStream_t s, int64_t n, const double *x, const double *y, double *part);
 // CSR view of a SELL matrix on the host (row_ptr[rows + 1], col, val)
 vem_status sell_to_host_csr(vem_handle *h, const SellMat &A, int64_t *rp, int32_t *col, double *val);
 
 // Krylov solve (krylov.cu)
-vem_status krylov_solve(vem_handle *h, const double *rhs, double *x, vem_stats *st);
+vem_status krylov_solve(vem_handle *h, const VemOp &op, const double *rhs, double *x, vem_stats *st);
+// The single-system operator view of the handle.
+VemOp single_op(vem_handle *h);
 
+vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, VemOp &op);
+vem_status assemble_local_nu(vem_handle *h, const double *nu);
 // Adjoint contraction (adjoint.cu): g_c = lam_{u,c}^T M_c u_c per cell.
 vem_status adjoint_contract(vem_handle *h, const double *lam, const double *x, double *g);
 

@@ -42,6 +42,12 @@ enum { MR_GOLD = 0, MR_G, MR_COLD, MR_C, MR_SOLD, MR_S, MR_ETA, MR_A1, MR_A2, MR
 __host__ __device__ inline double *slot(double *part, int s) { return part + (size_t)s * kMaxBlocks; }
 
 
+// y = A x for the operator (one system or a stacked batch)
+static void op_apply(cudaStream_t s, const VemOp &op, const double *x, double *y, double *dot_part = nullptr) {
+  if (op.nbatch == 1) spmv(s, op.A, x, y, dot_part);
+  else spmv_batched(s, op.A, op.nbatch, op.n_u1, op.A.val, x, y, dot_part);
+}
+
 // --------------------------------------------------------------- PCG -------
 // Jacobi-preconditioned CG in the single-reduction form of Chronopoulos &
 // Gear (J. Comput. Appl. Math. 25, 1989): one fused kernel computes
@@ -94,7 +100,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_init(int64_t n, const double
 // w = S u, partials of (r,u), (w,u), (r,r); the last block decides.  The
 // per-thread sums are in T, the block partials and scalars in FP64.
 template <class T>
-__global__ void __launch_bounds__(256) k_cg_spmv(int64_t rows, int64_t nslices,
+__global__ void __launch_bounds__(256) k_cg_spmv(int64_t rows, int64_t nslices, int nbatch, int64_t stored,
                                                  const int64_t *__restrict__ off,
                                                  const int32_t *__restrict__ col,
                                                  const T *__restrict__ val, const T *__restrict__ u,
@@ -105,12 +111,16 @@ __global__ void __launch_bounds__(256) k_cg_spmv(int64_t rows, int64_t nslices,
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   T gam = 0, del = 0, rr = 0;
-  for (int64_t s = warp; s < nslices; s += nwarps) {
-    const T t = sell_row_dot<T>(off, col, val, u, s, lane);
+  const int64_t tasks = nslices * nbatch;
+  for (int64_t tk = warp; tk < tasks; tk += nwarps) {
+    const int64_t bb = tk / nslices, s = tk - bb * nslices;
+    const T *ub = u + bb * rows;
+    const T t = sell_row_dot<T>(off, col, val + bb * stored, ub, s, lane);
     const int64_t i = 32 * s + lane;
     if (i < rows) {
-      w[i] = t;
-      const T ui = u[i], ri = r[i];
+      const int64_t gi = bb * rows + i;
+      w[gi] = t;
+      const T ui = u[gi], ri = r[gi];
       gam += ri * ui;
       del += t * ui;
       rr += ri * ri;
@@ -181,21 +191,21 @@ __global__ void k_f32_to_f64(int64_t n, const float *__restrict__ a, double *b) 
 // Solve S x = b (length n_p) to relative residual inner_rtol with vectors,
 // matrix values and arithmetic in T; returns the iterations.
 template <class T>
-static vem_status pcg_solve_t(vem_handle *h, const T *sval, const T *dinv, const double *b, T *x,
-                              T *wk, int *iters) {
+static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, const T *dinv, const double *b,
+                              T *x, T *wk, int *iters) {
   cudaStream_t s = h->stream;
-  const int64_t n = h->n_p;
+  const int64_t n = op.n_p;
   T *r = wk, *u = wk + n, *p = wk + 2 * n, *sv = wk + 3 * n, *w = wk + 4 * n;
   const int nb = nblocks_vec(n);
-  const int nbs = spmv_nblocks(h->S);
+  const int nbs = spmv_nblocks(op.S, op.nbatch);
   double *sc = h->scal;
   const double tol2 = h->opt.inner_rtol * h->opt.inner_rtol;
   count_launch();
   k_cg_init<T><<<nb, kRedThreads, 0, s>>>(n, b, dinv, x, r, u, p, sv, h->part, sc, h->ctr);
   auto spmv_it = [&](int it) {
     count_launch();
-    k_cg_spmv<T><<<nbs, 256, 0, s>>>(n, h->S.nslices, h->S.off, h->S.col, sval, u, r, w, h->part, sc,
-                                     h->ctr + 1, tol2, it);
+    k_cg_spmv<T><<<nbs, 256, 0, s>>>(op.S.rows, op.S.nslices, op.nbatch, op.S.stored, op.S.off, op.S.col,
+                                     sval, u, r, w, h->part, sc, h->ctr + 1, tol2, it);
   };
   spmv_it(0);
   const int maxit = h->opt.inner_maxit;
@@ -224,17 +234,17 @@ static vem_status pcg_solve_t(vem_handle *h, const T *sval, const T *dinv, const
 
 // S x = b with x, b FP64; the solve runs in FP64 or, with the mixed
 // precision option, entirely in FP32 (values, vectors, arithmetic).
-static vem_status pcg_solve(vem_handle *h, const double *b, double *x, double *wk, int *iters) {
+static vem_status pcg_solve(vem_handle *h, const VemOp &op, const double *b, double *x, double *wk, int *iters) {
   if (h->opt.precision == VEM_PRECISION_MIXED) {
     float *w32 = reinterpret_cast<float *>(wk);
-    float *x32 = w32 + 5 * h->n_p;
-    VEM_TRY(pcg_solve_t<float>(h, h->S_val32, h->s_dinv32, b, x32, w32, iters));
+    float *x32 = w32 + 5 * op.n_p;
+    VEM_TRY(pcg_solve_t<float>(h, op, op.S_val32, op.s_dinv32, b, x32, w32, iters));
     count_launch();
-    k_f32_to_f64<<<grid_for(h->n_p, 256), 256, 0, h->stream>>>(h->n_p, x32, x);
+    k_f32_to_f64<<<grid_for(op.n_p, 256), 256, 0, h->stream>>>(op.n_p, x32, x);
     VEM_CUDA(h, cudaGetLastError());
     return VEM_OK;
   }
-  return pcg_solve_t<double>(h, h->S.val, h->s_dinv, b, x, wk, iters);
+  return pcg_solve_t<double>(h, op, op.S.val, op.s_dinv, b, x, wk, iters);
 }
 
 // --------------------------------------------------------- vector ops -----
@@ -272,20 +282,24 @@ __global__ void k_diag_scale(int64_t nu, const double *__restrict__ v, const dou
 
 // Block upper-triangular flux part: z_u = (v_u - B^T z_p) / diag(M), with
 // B^T z_p gathered per face from its (at most two) cells.
-__global__ void k_tri_flux(int64_t nf, int nfd, int64_t n_u, const double *__restrict__ v,
-                           const double *__restrict__ dM, const int32_t *__restrict__ f_cell,
-                           const double *__restrict__ bt, const double *__restrict__ zp, double *z) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_u;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    double t = v[r];
+// (stacked rows R = b * n_u1 + r; pressure of cell c of system b at b * n_p1 + c)
+__global__ void k_tri_flux(int64_t nf, int nfd, int64_t n_u, int64_t n_u1, int64_t n_p1,
+                           const double *__restrict__ v, const double *__restrict__ dM,
+                           const int32_t *__restrict__ f_cell, const double *__restrict__ bt,
+                           const double *__restrict__ zp, double *z) {
+  for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < n_u;
+       R += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = R / n_u1, r = R - b * n_u1;
+    double t = v[R];
     if (r < nfd * nf && r % nfd == 0) {
       const int64_t f = r / nfd;
       const int32_t c0 = f_cell[2 * f], c1 = f_cell[2 * f + 1];
-      double g = bt[2 * f] * zp[c0];
-      if (c1 >= 0) g += bt[2 * f + 1] * zp[c1];
+      const double *zb = zp + b * n_p1;
+      double g = bt[2 * f] * zb[c0];
+      if (c1 >= 0) g += bt[2 * f + 1] * zb[c1];
       t -= g;
     }
-    z[r] = t / dM[r];
+    z[R] = t / dM[R];
   }
 }
 
@@ -490,20 +504,21 @@ __global__ void k_gm_solve(double *sc, int k, GmLayout L) {
 // z = P^{-1} v for the block preconditioner (diag or upper triangular).
 // wk: 5 n_p PCG work vectors (FP64 units; the FP32 solve uses 6 n_p floats of it).  If part_g2 != nullptr (MINRES) also leaves
 // the partials of v.z in slots P_G2U (flux part) and P_G2P (pressure part).
-static vem_status precond(vem_handle *h, const double *v, double *z, double *wk, int *inner,
+static vem_status precond(vem_handle *h, const VemOp &op, const double *v, double *z, double *wk, int *inner,
                           bool minres_partials) {
   cudaStream_t s = h->stream;
-  const int64_t nu = h->n_u, np = h->n_p;
+  const int64_t nu = op.n_u, np = op.n_p;
   int it = 0;
   if (h->opt.precond == VEM_PREC_BLOCK_DIAG) {
-    if (!minres_partials)
-      count_launch(); k_diag_scale<<<nblocks_vec(nu), kRedThreads, 0, s>>>(nu, v, h->diagM, z, nullptr);
-    VEM_TRY(pcg_solve(h, v + nu, z + nu, wk, &it));
+    if (!minres_partials) {
+      count_launch(); k_diag_scale<<<nblocks_vec(nu), kRedThreads, 0, s>>>(nu, v, op.diagM, z, nullptr);
+    }
+    VEM_TRY(pcg_solve(h, op, v + nu, z + nu, wk, &it));
   } else {
-    VEM_TRY(pcg_solve(h, v + nu, z + nu, wk, &it));
+    VEM_TRY(pcg_solve(h, op, v + nu, z + nu, wk, &it));
     count_launch(); k_negate<<<grid_for(np, 256), 256, 0, s>>>(np, z + nu);
-    count_launch(); k_tri_flux<<<grid_for(nu, 256), 256, 0, s>>>(h->nf, h->nfd, nu, v, h->diagM, h->f_cell,
-                                                  h->bt_face, z + nu, z);
+    count_launch(); k_tri_flux<<<grid_for(nu, 256), 256, 0, s>>>(h->nf, h->nfd, nu, op.n_u1, op.n_p1, v, op.diagM,
+                                                  h->f_cell, h->bt_face, z + nu, z);
   }
   VEM_CUDA(h, cudaGetLastError());
   if (minres_partials)
@@ -513,10 +528,10 @@ static vem_status precond(vem_handle *h, const double *v, double *z, double *wk,
 }
 
 // true relative residual ||b - A x|| / ||b|| (synchronises)
-static vem_status true_relres(vem_handle *h, const double *rhs, const double *x, double *tmp, double *rel) {
+static vem_status true_relres(vem_handle *h, const VemOp &op, const double *rhs, const double *x, double *tmp, double *rel) {
   cudaStream_t s = h->stream;
-  const int64_t n = h->n;
-  spmv(s, h->A, x, tmp);
+  const int64_t n = op.n;
+  op_apply(s, op, x, tmp);
   const int nb = nblocks_vec(n);
   count_launch(); k_residual<<<nb, kRedThreads, 0, s>>>(n, rhs, tmp, tmp, slot(h->part, P_R2), slot(h->part, P_B2));
   count_launch(); k_read_sum<<<1, kRedThreads, 0, s>>>(slot(h->part, P_R2), nb, h->scal + S_R2);
@@ -541,9 +556,9 @@ static vem_status ensure_work(vem_handle *h, size_t n) {
   return VEM_OK;
 }
 
-static vem_status run_minres(vem_handle *h, const double *rhs, double *x, vem_stats *st) {
+static vem_status run_minres(vem_handle *h, const VemOp &op, const double *rhs, double *x, vem_stats *st) {
   cudaStream_t s = h->stream;
-  const int64_t n = h->n, nu = h->n_u, np = h->n_p;
+  const int64_t n = op.n, nu = op.n_u, np = op.n_p;
   VEM_TRY(ensure_work(h, 8 * (size_t)n + 5 * (size_t)np));
   double *vA = h->work, *vB = vA + n, *z = vB + n, *zn = z + n, *Az = zn + n, *wA = Az + n,
          *wB = wA + n, *tmp = wB + n, *pw = tmp + n;
@@ -551,31 +566,31 @@ static vem_status run_minres(vem_handle *h, const double *rhs, double *x, vem_st
   int inner = 0;
   const int nbn = nblocks_vec(n), nbu = nblocks_vec(nu), nbp = nblocks_vec(np);
   // v = b - A x0
-  spmv(s, h->A, x, tmp);
+  op_apply(s, op, x, tmp);
   count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, rhs, tmp, v, slot(h->part, P_R2), slot(h->part, P_B2));
   VEM_CUDA(h, cudaMemsetAsync(vold, 0, sizeof(double) * n, s));
   VEM_CUDA(h, cudaMemsetAsync(wold, 0, sizeof(double) * n, s));
   VEM_CUDA(h, cudaMemsetAsync(w, 0, sizeof(double) * n, s));
-  count_launch(); k_diag_scale<<<nbu, kRedThreads, 0, s>>>(nu, v, h->diagM, z, slot(h->part, P_G2U));
-  VEM_TRY(precond(h, v, z, pw, &inner, true));
+  count_launch(); k_diag_scale<<<nbu, kRedThreads, 0, s>>>(nu, v, op.diagM, z, slot(h->part, P_G2U));
+  VEM_TRY(precond(h, op, v, z, pw, &inner, true));
   count_launch(); k_mr_init<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbu, nbp);
   VEM_CUDA(h, cudaGetLastError());
   double rel = 1.0;
-  VEM_TRY(true_relres(h, rhs, x, tmp, &rel));
+  VEM_TRY(true_relres(h, op, rhs, x, tmp, &rel));
   VEM_CUDA(h, cudaMemcpyAsync(h->h_scal + S_MR, h->scal + S_MR, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
   VEM_CUDA(h, cudaStreamSynchronize(s));
   const double eta0 = h->h_scal[S_MR + MR_ETA];
   int it = 0;
-  const int nbd = spmv_nblocks(h->A);
+  const int nbd = spmv_nblocks(op.A, op.nbatch);
   vem_status result = VEM_ERR_NOT_CONVERGED;
   if (rel <= h->opt.rtol || eta0 == 0.0) result = VEM_OK;
   while (result != VEM_OK && it < h->opt.maxit) {
     ++it;
     count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, z, h->scal + S_MR + MR_IG);
-    spmv(s, h->A, z, Az, slot(h->part, P_DELTA));
+    op_apply(s, op, z, Az, slot(h->part, P_DELTA));
     count_launch(); k_mr_lanczos<<<nbn, kRedThreads, 0, s>>>(n, Az, v, vold, h->part, nbd, h->scal);
-    count_launch(); k_diag_scale<<<nbu, kRedThreads, 0, s>>>(nu, vold, h->diagM, zn, slot(h->part, P_G2U));
-    VEM_TRY(precond(h, vold, zn, pw, &inner, true));
+    count_launch(); k_diag_scale<<<nbu, kRedThreads, 0, s>>>(nu, vold, op.diagM, zn, slot(h->part, P_G2U));
+    VEM_TRY(precond(h, op, vold, zn, pw, &inner, true));
     count_launch(); k_mr_scalars<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbd, nbu, nbp);
     count_launch(); k_mr_update<<<grid_for(n, 256), 256, 0, s>>>(n, z, wold, w, x, h->scal);
     VEM_CUDA(h, cudaGetLastError());
@@ -593,12 +608,12 @@ static vem_status run_minres(vem_handle *h, const double *rhs, double *x, vem_st
       return fail(h, m[MR_BAD] == 1.0 ? VEM_ERR_NONFINITE : VEM_ERR_BREAKDOWN, "MINRES breakdown");
     const bool lucky = m[MR_G] == 0.0;
     if (std::fabs(m[MR_ETA]) <= 0.5 * h->opt.rtol * eta0 || lucky) {
-      VEM_TRY(true_relres(h, rhs, x, tmp, &rel));
+      VEM_TRY(true_relres(h, op, rhs, x, tmp, &rel));
       if (rel <= h->opt.rtol) result = VEM_OK;
       else if (lucky) break;
     }
   }
-  if (result != VEM_OK) VEM_TRY(true_relres(h, rhs, x, tmp, &rel));
+  if (result != VEM_OK) VEM_TRY(true_relres(h, op, rhs, x, tmp, &rel));
   st->iterations = it;
   st->inner_iterations = inner;
   st->relres = rel;
@@ -606,9 +621,9 @@ static vem_status run_minres(vem_handle *h, const double *rhs, double *x, vem_st
   return VEM_OK;
 }
 
-static vem_status run_fgmres(vem_handle *h, const double *rhs, double *x, vem_stats *st) {
+static vem_status run_fgmres(vem_handle *h, const VemOp &op, const double *rhs, double *x, vem_stats *st) {
   cudaStream_t s = h->stream;
-  const int64_t n = h->n, np = h->n_p;
+  const int64_t n = op.n, np = op.n_p;
   const int m = h->opt.restart;
   GmLayout L{m};
   if (L.end() > 8192) return fail(h, VEM_ERR_BAD_INPUT, "restart too large");
@@ -617,13 +632,13 @@ static vem_status run_fgmres(vem_handle *h, const double *rhs, double *x, vem_st
   int inner = 0, it = 0;
   const int nbn = nblocks_vec(n);
   double rel = 1.0;
-  VEM_TRY(true_relres(h, rhs, x, tmp, &rel));
+  VEM_TRY(true_relres(h, op, rhs, x, tmp, &rel));
   vem_status result = rel <= h->opt.rtol ? VEM_OK : VEM_ERR_NOT_CONVERGED;
   double bnorm = std::sqrt(h->h_scal[S_B2]);
   if (bnorm == 0.0) bnorm = 1.0;
   while (result != VEM_OK && it < h->opt.maxit) {
     // V_0 = (b - A x) / beta
-    spmv(s, h->A, x, tmp);
+    op_apply(s, op, x, tmp);
     count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, rhs, tmp, V, slot(h->part, P_R2), slot(h->part, P_B2));
     count_launch(); k_gm_start<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbn, L);
     count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, V, h->scal + GM_IBETA);
@@ -631,8 +646,8 @@ static vem_status run_fgmres(vem_handle *h, const double *rhs, double *x, vem_st
     for (int j = 0; j < m && it < h->opt.maxit; ++j) {
       ++it;
       double *Vj = V + (size_t)j * n, *Zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
-      VEM_TRY(precond(h, Vj, Zj, pw, &inner, false));
-      spmv(s, h->A, Zj, w);
+      VEM_TRY(precond(h, op, Vj, Zj, pw, &inner, false));
+      op_apply(s, op, Zj, w);
       for (int pass = 0; pass < 2; ++pass) {
         for (int i0 = 0; i0 <= j; i0 += kMD) {
           const int cnt = (j + 1 - i0) < kMD ? (j + 1 - i0) : kMD;
@@ -661,7 +676,7 @@ static vem_status run_fgmres(vem_handle *h, const double *rhs, double *x, vem_st
     count_launch(); k_gm_solve<<<1, 32, 0, s>>>(h->scal, jd, L);
     count_launch(); k_multiaxpy<<<nbn, kRedThreads, 0, s>>>(n, Z, jd, h->scal + L.Y(0), 1.0, x, nullptr);
     VEM_CUDA(h, cudaGetLastError());
-    VEM_TRY(true_relres(h, rhs, x, tmp, &rel));
+    VEM_TRY(true_relres(h, op, rhs, x, tmp, &rel));
     if (rel <= h->opt.rtol) result = VEM_OK;
   }
   st->iterations = it;
@@ -671,13 +686,28 @@ static vem_status run_fgmres(vem_handle *h, const double *rhs, double *x, vem_st
   return VEM_OK;
 }
 
-vem_status krylov_solve(vem_handle *h, const double *rhs, double *x, vem_stats *st) {
+VemOp single_op(vem_handle *h) {
+  VemOp op;
+  op.A = h->A;
+  op.S = h->S;
+  op.diagM = h->diagM;
+  op.s_dinv = h->s_dinv;
+  op.S_val32 = h->S_val32;
+  op.s_dinv32 = h->s_dinv32;
+  op.n_u = op.n_u1 = h->n_u;
+  op.n_p = op.n_p1 = h->n_p;
+  op.n = h->n;
+  op.nbatch = 1;
+  return op;
+}
+
+vem_status krylov_solve(vem_handle *h, const VemOp &op, const double *rhs, double *x, vem_stats *st) {
   if (h->opt.krylov == VEM_KRYLOV_MINRES) {
     if (h->opt.precond != VEM_PREC_BLOCK_DIAG)
       return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs the block-diagonal preconditioner");
-    return run_minres(h, rhs, x, st);
+    return run_minres(h, op, rhs, x, st);
   }
-  if (h->opt.krylov == VEM_KRYLOV_FGMRES) return run_fgmres(h, rhs, x, st);
+  if (h->opt.krylov == VEM_KRYLOV_FGMRES) return run_fgmres(h, op, rhs, x, st);
   return fail(h, VEM_ERR_BAD_INPUT, "unknown Krylov method %d", h->opt.krylov);
 }
 

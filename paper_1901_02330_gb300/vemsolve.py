@@ -72,6 +72,8 @@ _SIGS = {
     "vem_set_source_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_assemble": (C.c_int, [C.c_void_p]),
     "vem_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(vem_stats)]),
+    "vem_solve_batched": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.POINTER(vem_stats)]),
     "vem_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(vem_stats)]),
     "vem_get_geometry": (C.c_int, [C.c_void_p] + [C.c_void_p] * 7),
     "vem_local_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -257,6 +259,28 @@ class Solver:
         if not (code == 3 and allow_not_converged):
             self._check(code)
         return u_out, p_out, st.as_dict()
+
+    def solve_batched(self, K, f_qp=None, gD_qp=None, u_out=None, p_out=None, allow_not_converged=False):
+        """K, f_qp, gD_qp with a leading batch axis; host numpy unless device_io."""
+        nb = int(K.shape[0])
+        nu, np_ = self.sizes()
+        dev = bool(self.options.device_io)
+        if not dev:
+            K = np.ascontiguousarray(K, dtype=np.float64)
+            f_qp = None if f_qp is None else np.ascontiguousarray(f_qp, dtype=np.float64)
+            gD_qp = None if gD_qp is None else np.ascontiguousarray(gD_qp, dtype=np.float64)
+            if u_out is None:
+                u_out = np.zeros((nb, nu))
+            if p_out is None:
+                p_out = np.zeros((nb, np_))
+        rel = np.zeros(nb)
+        st = vem_stats()
+        code = lib().vem_solve_batched(self._h, nb, _ptr(K), _ptr(f_qp), _ptr(gD_qp), _ptr(u_out), _ptr(p_out),
+                                       _ptr(rel), C.byref(st))
+        self.generation += 1
+        if not (code == 3 and allow_not_converged):
+            self._check(code)
+        return u_out, p_out, rel, st.as_dict()
 
     def adjoint(self, dL_du=None, dL_dp=None, out=None):
         """dL/dlog K per cell for the last solve (host numpy unless device_io)."""
