@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--inner-rtol", type=float, default=1e-8, help="inner Jacobi-PCG tolerance")
     ap.add_argument("--element", default="k1", choices=["k1", "e0"])
+    ap.add_argument("--workload", default="hex128-k1",
+                    choices=["hex128-k1", "hex8-e0-minres", "cvt200k-e0-mixed", "hex64-e0-batch64",
+                             "cvt100k-adjoint"],
+                    help="hex128-k1 is the headline; the others are the remaining configurations")
     ap.add_argument("--profile", action="store_true",
                     help="one step only (for an ncu launch list); prints a short JSON line")
     return ap.parse_args()
@@ -398,8 +402,202 @@ def run_ours(a):
     return 0
 
 
+# --------------------------------------------------------- other workloads ---
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        out = fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, out
+
+
+def _line(a, metric, value, unit, ms, dtype, config, **extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic", "config": config}
+    line.update(extra)
+    return line
+
+
+def run_workload(a):
+    """The configurations other than the headline, one JSON line each."""
+    import torch
+    from paper_1901_02330_gb300 import build as b_
+    from paper_1901_02330_gb300 import vemsolve as vs
+    from synth import fields, hex_mesh
+    from synth.voronoi import voronoi_mesh
+    b_.build()
+    stream = torch.cuda.current_stream()
+    sid = stream.cuda_stream
+    w = a.workload
+    if w == "hex8-e0-minres":
+        # 8^3 cubes, E0, K = 1, sine data, MINRES + block-diagonal, rtol 1e-12
+        from oracle import E0, assemble, solvers
+        mesh = hex_mesh(8)
+        prob = fields.sine_problem()
+        s = vs.Solver(mesh, stream=sid, element=0, krylov=0, precond=0, rtol=1e-12, inner_rtol=1e-13)
+        s.set_data(prob.f, prob.gD)
+
+        def step():
+            s.assemble()
+            return s.solve()
+        ms, (u, p, st) = _timed(step, a.steps, a.warmup, stream)
+        sys_ = assemble(mesh, E0, np.ones(mesh.n_cells), f=prob.f, gD=prob.gD)
+        ud, pd = solvers.solve_direct(sys_)
+        n = st["n_u"] + st["n_p"]
+        line = _line(a, "time-to-solution (rel.res 1e-12) and DOFs/s", n / (ms * 1e-3), "DOFs/s", ms, "f64",
+                     {"workload": w, "cells": 512, "n_u": st["n_u"], "n_p": st["n_p"], "element": "E0",
+                      "krylov": "MINRES", "precond": "block-diagonal, S = B diag(M)^-1 B^T, Jacobi-PCG 1e-13"},
+                     iterations=st["iterations"], inner_iterations=st["inner_iterations"], relres=st["relres"],
+                     rel_err_vs_oracle_u=float(np.linalg.norm(u - ud) / np.linalg.norm(ud)),
+                     rel_err_vs_oracle_p=float(np.linalg.norm(p - pd) / np.linalg.norm(pd)),
+                     note="host I/O per step; latency-bound (all data L2-resident)")
+        s.close()
+    elif w == "cvt200k-e0-mixed":
+        # 200k seeds U[0,1]^3 (seed 0), 10 Lloyd iterations, E0, K = 10^U, U ~ U[-4,4] (seed 1)
+        mesh = voronoi_mesh(200000, seed=0, lloyd=10)
+        K = fields.K_high_contrast(mesh.n_cells, seed=1, decades=4.0)
+        prob = fields.sine_problem()
+        res = {}
+        for prec in (1, 0):
+            s = vs.Solver(mesh, stream=sid, device_io=1, element=0, krylov=1, precond=1, precision=prec,
+                          rtol=1e-8, inner_rtol=1e-5 if prec else 1e-8, inner_maxit=5000, maxit=2000)
+            s.set_coefficient(K)
+            s.set_data(prob.f, prob.gD)
+            n_u, n_p = s.sizes()
+            u = torch.empty(n_u, dtype=torch.float64, device="cuda")
+            p = torch.empty(n_p, dtype=torch.float64, device="cuda")
+
+            def step():
+                s.assemble()
+                return s.solve(u_out=u, p_out=p)[2]
+            ms, st = _timed(step, a.steps, a.warmup, stream)
+            res[prec] = (ms, st, u.clone(), p.clone())
+            s.close()
+        (ms, st, u, p), (ms64, st64, u64, p64) = res[1], res[0]
+        n = st["n_u"] + st["n_p"]
+        line = _line(a, "time-to-solution (rel.res 1e-8) and DOFs/s", n / (ms * 1e-3), "DOFs/s", ms,
+                     "f64 outer / f32 Schur solve",
+                     {"workload": w, "cells": mesh.n_cells, "faces": mesh.n_faces, "n_u": st["n_u"], "n_p": st["n_p"],
+                      "faces_per_cell": float(np.diff(mesh.cell_face_ptr).mean()), "element": "E0",
+                      "K": "10^U, U ~ U[-4,4]", "krylov": "FGMRES(30)", "precond": "block upper-triangular"},
+                     iterations=st["iterations"], inner_iterations=st["inner_iterations"], relres=st["relres"],
+                     fp64={"ms_per_step": ms64, "iterations": st64["iterations"],
+                           "inner_iterations": st64["inner_iterations"], "relres": st64["relres"]},
+                     speedup_mixed_vs_fp64=ms64 / ms,
+                     rel_diff_vs_fp64_u=float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64)),
+                     rel_diff_vs_fp64_p=float(torch.linalg.norm(p - p64) / torch.linalg.norm(p64)))
+    elif w == "hex64-e0-batch64":
+        # 64 systems on 64^3 cubes, E0, K_b = exp(2 xi) (seed 100 + b), f_b = 8 Fourier modes (seed 200 + b)
+        mesh = hex_mesh(64)
+        nb = 64
+        Ks = np.stack([fields.K_lognormal(mesh.n_cells, seed=100 + b, sigma=2.0) for b in range(nb)])
+        s = vs.Solver(mesh, stream=sid, element=0, krylov=1, precond=1, precision=1, rtol=1e-8,
+                      inner_rtol=1e-5, inner_maxit=5000, maxit=3000)
+        xc = s.quadrature_points(vs.VEM_QP_CELL)
+        F = np.stack([fields.fourier_source(200 + b)(xc) for b in range(nb)])
+        Kd = torch.from_numpy(Ks).cuda()
+        Fd = torch.from_numpy(F).cuda()
+        s.set_options(device_io=1)
+        n_u, n_p = s.sizes()
+        U = torch.empty(nb, n_u, dtype=torch.float64, device="cuda")
+        P = torch.empty(nb, n_p, dtype=torch.float64, device="cuda")
+
+        def step():
+            return s.solve_batched(Kd, Fd, None, U, P)
+        ms, (_, _, rel, st) = _timed(step, a.steps, a.warmup, stream)
+        # the same 64 problems one at a time in plain FP64 (first 8, scaled)
+        s64 = vs.Solver(mesh, stream=sid, device_io=1, element=0, krylov=1, precond=1, rtol=1e-8,
+                        inner_rtol=1e-8, inner_maxit=5000, maxit=3000)
+        u1 = torch.empty(n_u, dtype=torch.float64, device="cuda")
+        p1 = torch.empty(n_p, dtype=torch.float64, device="cuda")
+        m8 = 8
+        diffs = []
+
+        def seq():
+            for b in range(m8):
+                s64.set_coefficient(Kd[b])
+                s64.set_source(Fd[b], None)
+                s64.solve(u_out=u1, p_out=p1)
+                diffs.append(float(torch.linalg.norm(u1 - U[b]) / torch.linalg.norm(u1)))
+        ms_seq, _ = _timed(seq, 1, 0, stream)
+        n = nb * (n_u + n_p)
+        line = _line(a, "time-to-solution (rel.res 1e-8) and DOFs/s", n / (ms * 1e-3), "DOFs/s", ms,
+                     "f64 outer / f32 Schur solve",
+                     {"workload": w, "systems": nb, "cells": mesh.n_cells, "n_per_system": n_u + n_p, "element": "E0",
+                      "K": "exp(2 xi) per cell and system", "f": "8 Fourier modes per system",
+                      "krylov": "FGMRES(30) on the stacked block-diagonal system",
+                      "precond": "block upper-triangular, FP32 Jacobi-PCG 1e-5"},
+                     iterations=st["iterations"], inner_iterations=st["inner_iterations"],
+                     worst_relres=float(np.max(rel)),
+                     sequential_fp64={"systems_timed": m8, "ms_per_system": ms_seq / m8,
+                                      "ms_for_all": ms_seq / m8 * nb},
+                     speedup_vs_sequential_fp64=(ms_seq / m8 * nb) / ms,
+                     max_rel_diff_vs_fp64_u=max(diffs))
+        s.close()
+        s64.close()
+    else:
+        # adjoint: 100k seeds (seed 2), 10 Lloyd; theta ~ N(0,1) (seed 3); p_target from theta' (seed 4)
+        from paper_1901_02330_gb300.autograd import solve as vsolve
+        mesh = voronoi_mesh(100000, seed=2, lloyd=10)
+        prob = fields.sine_problem()
+        s = vs.Solver(mesh, stream=sid, device_io=1, element=0, krylov=1, precond=1, rtol=1e-12,
+                      inner_rtol=1e-12, inner_maxit=20000, maxit=2000)
+        s.set_data(prob.f, prob.gD)
+        rng3 = np.random.default_rng(3)
+        rng4 = np.random.default_rng(4)
+        theta = torch.tensor(rng3.standard_normal(mesh.n_cells), device="cuda")
+        with torch.no_grad():
+            _, ptarget = vsolve(torch.tensor(rng4.standard_normal(mesh.n_cells), device="cuda"), s)
+            ptarget = ptarget.clone()
+
+        def loss_of(th):
+            u, p = vsolve(th, s)
+            return 0.5 * torch.sum((p - ptarget) ** 2)
+
+        def step():
+            th = theta.clone().requires_grad_(True)
+            L = loss_of(th)
+            L.backward()
+            return th.grad
+        ms, g = _timed(step, a.steps, a.warmup, stream)
+        g = g.detach().cpu().numpy()
+        cells = np.random.default_rng(5).choice(mesh.n_cells, size=20, replace=False)
+        eps = 1e-6
+        errs = []
+        with torch.no_grad():
+            for P in cells:
+                tp = theta.clone()
+                tm = theta.clone()
+                tp[P] += eps
+                tm[P] -= eps
+                fd = (loss_of(tp).item() - loss_of(tm).item()) / (2 * eps)
+                errs.append((abs(fd - g[P]) / max(abs(fd), 1e-300), abs(fd - g[P]) / np.abs(g).max()))
+        n = mesh.n_cells
+        line = _line(a, "forward + adjoint gradient time and cells/s", n / (ms * 1e-3), "cells/s", ms, "f64",
+                     {"workload": w, "cells": mesh.n_cells, "faces": mesh.n_faces, "element": "E0",
+                      "loss": "0.5 ||p_h - p_target||^2", "krylov": "FGMRES(30)", "precond": "block upper-triangular",
+                      "rtol": 1e-12},
+                     fd_check={"cells": 20, "step": eps,
+                               "max_rel_err": float(max(e[0] for e in errs)),
+                               "median_rel_err": float(np.median([e[0] for e in errs])),
+                               "max_err_rel_to_max_grad": float(max(e[1] for e in errs))})
+        s.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     a = parse()
+    if a.workload != "hex128-k1" and not a.cpu_sample and a.impl == "ours":
+        return run_workload(a)
     if a.cpu_sample:
         n, dt, it = oracle_sample(SAMPLE_N)
         print(json.dumps({"n": n, "seconds": dt, "iters": it}))
