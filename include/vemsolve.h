@@ -107,6 +107,11 @@ typedef struct {
                       /* Needs FGMRES; inner_rtol >= 1e-6 is meaningful.    */
   int device_io;      /* 0: vem_solve's x0/u_out/p_out are host pointers;   */
                       /* 1: device pointers (e.g. torch tensors' data_ptr)  */
+  int reuse;          /* 1: cells that are translates of one another (same  */
+                      /* vertex offsets from the barycentre, to 2^-40 of    */
+                      /* the mesh diagonal, and same face/vertex order)     */
+                      /* share one evaluation of their geometry-only local  */
+                      /* matrices, scaled by nu_P; 0: every cell evaluated. */
 } vem_options;
 
 typedef struct {
@@ -119,11 +124,15 @@ typedef struct {
   int64_t nnz_A, nnz_S;      /* nonzeros of [M B^T; B 0] and of S           */
   double t_element_ms;       /* of t_assemble_ms: the element kernel        */
   double t_scatter_ms;       /* of t_assemble_ms: scatter + Schur build     */
+  int64_t n_classes;         /* congruence classes of cells evaluated by the */
+                             /* element kernel (= n_cells without reuse)    */
+  double t_schur_spmv_ms;    /* of t_solve_ms: the Schur-complement SpMV    */
+  int64_t n_schur_spmv;      /* its launches (each timed with CUDA events)  */
 } vem_stats;
 
 /* Fill *opt with the defaults: E0, FGMRES(30), block-diagonal, Jacobi-PCG
  * inner solve to 1e-12 (at most 2000 iterations), rtol 1e-12, maxit 2000,
- * FP64, host I/O. */
+ * FP64, host I/O, reuse on. */
 vem_status vem_default_options(vem_options *opt);
 
 /* Create a solver for a mesh: copies the mesh to the device, computes the
@@ -189,9 +198,7 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
  * (one Krylov process for all systems, stopped when every system's true
  * relative residual is <= rtol).  Writes u_out [nbatch][n_u], p_out
  * [nbatch][n_p] (host or device per options.device_io) and, if not NULL,
- * relres_out [nbatch] (host).  stats->relres is the worst system's.
- * Invalidates the single-system assembly (local matrices are rebuilt with
- * nu = 1 and scaled per system). */
+ * relres_out [nbatch] (host).  stats->relres is the worst system's. */
 vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, const double *f_qp,
                              const double *gD_qp, double *u_out, double *p_out, double *relres_out,
                              vem_stats *stats);

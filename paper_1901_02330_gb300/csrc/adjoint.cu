@@ -12,6 +12,7 @@ namespace vem {
 
 __global__ void k_adjoint_contract(int64_t nc, int nfd, int nid, int64_t nf, int max_nl,
                                    const int64_t *__restrict__ cfp, const int32_t *__restrict__ cf,
+                                   const int32_t *__restrict__ cls_of, const double *__restrict__ nu,
                                    const int64_t *__restrict__ m_off, const double *__restrict__ Mloc,
                                    const double *__restrict__ lam, const double *__restrict__ x,
                                    double *g) {
@@ -30,7 +31,7 @@ __global__ void k_adjoint_contract(int64_t nc, int nfd, int nid, int64_t nf, int
       ll[j] = lam[gj];
     }
     __syncwarp();
-    const double *M = Mloc + m_off[c];
+    const double *M = Mloc + m_off[cls_of[c]];   // nu = 1 class matrix
     double acc = 0.0;
     for (int j = lane; j < nl; j += 32) {
       double t = 0.0;
@@ -38,7 +39,7 @@ __global__ void k_adjoint_contract(int64_t nc, int nfd, int nid, int64_t nf, int
       acc += ll[j] * t;
     }
     acc = warp_sum(acc);
-    if (lane == 0) g[c] = acc;
+    if (lane == 0) g[c] = nu[c] * acc;
     __syncwarp();
   }
 }
@@ -54,7 +55,7 @@ vem_status adjoint_contract(vem_handle *h, const double *lam, const double *x, d
   if (blocks > cap) blocks = cap;
   count_launch();
   k_adjoint_contract<<<(int)blocks, 32 * wpb, smem, h->stream>>>(h->nc, h->nfd, h->nid, h->nf, max_nl, h->cf_ptr,
-                                                                 h->cf, h->m_off, h->Mloc, lam, x, g);
+                                                                 h->cf, h->cls_of, h->nu, h->m_off, h->Mloc, lam, x, g);
   VEM_CUDA(h, cudaGetLastError());
   return VEM_OK;
 }

@@ -80,6 +80,7 @@ static vem_status check_options(vem_handle *h, const vem_options *o) {
   if (o->precision == VEM_PRECISION_MIXED && o->krylov != VEM_KRYLOV_FGMRES)
     return fail(h, VEM_ERR_BAD_INPUT, "mixed precision needs FGMRES (its FP32 inner solve is not a fixed operator)");
   if (o->restart < 1 || o->restart > 256) return fail(h, VEM_ERR_BAD_INPUT, "restart %d", o->restart);
+  if (o->reuse != 0 && o->reuse != 1) return fail(h, VEM_ERR_BAD_INPUT, "reuse %d", o->reuse);
   if (!(o->rtol > 0.0) || !(o->inner_rtol > 0.0) || o->maxit < 1 || o->inner_maxit < 1)
     return fail(h, VEM_ERR_BAD_INPUT, "tolerances and iteration caps must be positive");
   return VEM_OK;
@@ -137,8 +138,15 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
     if (m->face_vtx[i] < 0 || m->face_vtx[i] >= h->nv) return fail(h, VEM_ERR_BAD_INPUT, "mesh: vertex index out of range");
   for (int64_t i = 0; i < h->n_cf; ++i)
     if (m->cell_face[i] < 0 || m->cell_face[i] >= h->nf) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face index out of range");
-  for (int64_t i = 0; i < 3 * h->nv; ++i)
+  double lo[3] = {m->xyz[0], m->xyz[1], m->xyz[2]}, hi[3] = {lo[0], lo[1], lo[2]};
+  for (int64_t i = 0; i < 3 * h->nv; ++i) {
     if (!std::isfinite(m->xyz[i])) return fail(h, VEM_ERR_NONFINITE, "mesh: non-finite coordinate");
+    lo[i % 3] = std::min(lo[i % 3], m->xyz[i]);
+    hi[i % 3] = std::max(hi[i % 3], m->xyz[i]);
+  }
+  h->lref = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                      (hi[2] - lo[2]) * (hi[2] - lo[2]));
+  if (!(h->lref > 0.0)) return fail(h, VEM_ERR_DEGENERATE_MESH, "mesh: zero extent");
   set_layout(h);
 
   VEM_CUDA(h, cudaMallocHost(&h->h_err, sizeof(int)));
@@ -190,34 +198,8 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
   VEM_CUDA(h, cudaEventCreate(&h->ev1));
   VEM_CUDA(h, cudaEventCreate(&h->ev2));
   VEM_CUDA(h, cudaEventCreate(&h->ev3));
+  for (auto &e : h->tev) VEM_CUDA(h, cudaEventCreate(&e));
   return geometry_build(h);
-}
-
-static vem_status alloc_local(vem_handle *h) {
-  std::vector<int64_t> off(h->nc + 1, 0);
-  for (int64_t c = 0; c < h->nc; ++c) {
-    const int64_t k = h->h_cf_ptr[c + 1] - h->h_cf_ptr[c];
-    const int64_t nl = h->nfd * k + h->nid;
-    off[c + 1] = off[c] + nl * nl;
-  }
-  const int64_t mt = off[h->nc];
-  const int64_t bt = h->nfd * h->n_cf + h->nid * h->nc;
-  if (h->m_total != mt || !h->Mloc) {
-    dfree(h, h->Mloc);
-    h->Mloc = nullptr;
-    VEM_TRY(dalloc_n(h, &h->Mloc, (size_t)mt));
-    h->m_total = mt;
-  }
-  if (h->b_total != bt || !h->Bloc) {
-    dfree(h, h->Bloc);
-    h->Bloc = nullptr;
-    VEM_TRY(dalloc_n(h, &h->Bloc, (size_t)bt));
-    h->b_total = bt;
-  }
-  if (!h->m_off) VEM_TRY(dalloc_n(h, &h->m_off, (size_t)h->nc + 1));
-  VEM_CUDA(h, cudaMemcpyAsync(h->m_off, off.data(), sizeof(int64_t) * (h->nc + 1), cudaMemcpyHostToDevice, h->stream));
-  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
-  return VEM_OK;
 }
 
 static vem_status ensure_rhs(vem_handle *h) {
@@ -228,7 +210,7 @@ static vem_status ensure_rhs(vem_handle *h) {
 
 static vem_status assemble_impl(vem_handle *h) {
   VEM_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-  VEM_TRY(alloc_local(h));
+  VEM_TRY(classify_cells(h));
   VEM_CUDA(h, cudaEventRecord(h->ev2, h->stream));
   VEM_TRY(assemble_local(h));
   VEM_CUDA(h, cudaEventRecord(h->ev3, h->stream));
@@ -326,6 +308,7 @@ vem_status vem_default_options(vem_options *o) {
   o->inner_maxit = 2000;
   o->precision = VEM_PRECISION_FP64;
   o->device_io = 0;
+  o->reuse = 1;
   return VEM_OK;
 }
 
@@ -498,6 +481,7 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
   st.t_assemble_ms = h->t_assemble_ms;
   st.t_element_ms = h->t_element_ms;
   st.t_scatter_ms = h->t_scatter_ms;
+  st.n_classes = h->ncls;
   vem_status r = VEM_OK;
   do {
     const double *x0d = nullptr;
@@ -512,6 +496,8 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
       x0d = x0;
     }
     count_launch(); k_import_x<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n, x0d, x);
+    h->t_schur_spmv_ms = 0.0;
+    h->n_schur_spmv = 0;
     cudaEventRecord(h->ev0, s);
     r = krylov_solve(h, single_op(h), h->rhs, x, &st);
     cudaEventRecord(h->ev1, s);
@@ -519,6 +505,8 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     st.t_solve_ms = ms;
+    st.t_schur_spmv_ms = h->t_schur_spmv_ms;
+    st.n_schur_spmv = h->n_schur_spmv;
     if (tmp) dfree(h, tmp);
     if (r != VEM_OK && r != VEM_ERR_NOT_CONVERGED) break;
     h->have_solution = true;
@@ -649,16 +637,9 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   if (gD_qp && h->n_bqp > 0) VEM_CUDA(h, cudaMemcpyAsync(h->b_gqp, gD_qp, sizeof(double) * nb * h->n_bqp, kind, s));
   else VEM_CUDA(h, cudaMemsetAsync(h->b_gqp, 0, sizeof(double) * nb * nbq, s));
   // geometry-only local matrices (nu = 1), then the per-system values
-  if (!h->unit_nu) {
-    VEM_TRY(dalloc_n(h, &h->unit_nu, (size_t)h->nc));
-    std::vector<double> ones(h->nc, 1.0);
-    VEM_CUDA(h, cudaMemcpyAsync(h->unit_nu, ones.data(), sizeof(double) * h->nc, cudaMemcpyHostToDevice, s));
-    VEM_CUDA(h, cudaStreamSynchronize(s));
-  }
   cudaEventRecord(h->ev0, s);
-  VEM_TRY(assemble_local_nu(h, h->unit_nu));
-  h->assembled = false;      // the local matrices no longer carry the single system's nu
-  h->have_solution = false;
+  VEM_TRY(classify_cells(h));
+  VEM_TRY(assemble_local(h));
   VEM_TRY(assemble_batched_values(h, nb, h->b_nu, op));
   for (int b = 0; b < nb; ++b)
     VEM_TRY(assemble_rhs_into(h, h->b_fqp + (int64_t)b * h->nc, (gD_qp && h->n_bqp > 0) ? h->b_gqp + (int64_t)b * nbq : nullptr,
@@ -770,11 +751,30 @@ vem_status vem_get_local(vem_handle *h, double *M_out, int64_t *M_offsets, doubl
   if (!h) return VEM_ERR_BAD_INPUT;
   if (!h->assembled) return fail(h, VEM_ERR_BAD_INPUT, "vem_get_local before vem_assemble");
   cudaStream_t s = h->stream;
-  if (M_out) VEM_CUDA(h, cudaMemcpyAsync(M_out, h->Mloc, sizeof(double) * h->m_total, cudaMemcpyDeviceToHost, s));
-  if (M_offsets)
-    VEM_CUDA(h, cudaMemcpyAsync(M_offsets, h->m_off, sizeof(int64_t) * (h->nc + 1), cudaMemcpyDeviceToHost, s));
-  if (B_out) VEM_CUDA(h, cudaMemcpyAsync(B_out, h->Bloc, sizeof(double) * h->b_total, cudaMemcpyDeviceToHost, s));
+  // stored per congruence class with nu = 1: expand to M_P = nu_P Mhat, B_P = Bhat
+  std::vector<double> Mc(h->m_total), Bc(h->b_total), nu(h->nc);
+  std::vector<int64_t> mo(h->ncls + 1), bo(h->ncls + 1);
+  std::vector<int32_t> cls(h->nc);
+  VEM_CUDA(h, cudaMemcpyAsync(Mc.data(), h->Mloc, sizeof(double) * h->m_total, cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaMemcpyAsync(Bc.data(), h->Bloc, sizeof(double) * h->b_total, cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaMemcpyAsync(nu.data(), h->nu, sizeof(double) * h->nc, cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaMemcpyAsync(mo.data(), h->m_off, sizeof(int64_t) * (h->ncls + 1), cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaMemcpyAsync(bo.data(), h->b_off, sizeof(int64_t) * (h->ncls + 1), cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaMemcpyAsync(cls.data(), h->cls_of, sizeof(int32_t) * h->nc, cudaMemcpyDeviceToHost, s));
   VEM_CUDA(h, cudaStreamSynchronize(s));
+  int64_t om = 0, ob = 0;
+  for (int64_t c = 0; c < h->nc; ++c) {
+    const int64_t nl = h->nfd * (h->h_cf_ptr[c + 1] - h->h_cf_ptr[c]) + h->nid;
+    const int k = cls[c];
+    if (M_offsets) M_offsets[c] = om;
+    if (M_out)
+      for (int64_t e = 0; e < nl * nl; ++e) M_out[om + e] = nu[c] * Mc[mo[k] + e];
+    if (B_out)
+      for (int64_t e = 0; e < nl; ++e) B_out[ob + e] = Bc[bo[k] + e];
+    om += nl * nl;
+    ob += nl;
+  }
+  if (M_offsets) M_offsets[h->nc] = om;
   return VEM_OK;
 }
 
@@ -828,6 +828,8 @@ void vem_destroy(vem_handle *h) {
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ev2) cudaEventDestroy(h->ev2);
   if (h->ev3) cudaEventDestroy(h->ev3);
+  for (auto &e : h->tev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 

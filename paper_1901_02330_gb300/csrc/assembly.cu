@@ -14,13 +14,16 @@
 
 namespace vem {
 
+// Local matrices are stored per congruence class with nu = 1: cell c uses
+// Mloc + m_off[cls_of[c]] (scaled by its nu) and Bloc + b_off[cls_of[c]].
 struct Layout {
   int nfd, nid;
   int64_t nf, nc, n_u;
   const int64_t *cfp;
   const int32_t *cf;
   const int32_t *f_cell, *f_loc;
-  const int64_t *m_off;
+  const int64_t *m_off, *b_off;
+  const int32_t *cls_of;
   const double *Mloc, *Bloc;
 };
 
@@ -32,8 +35,9 @@ __device__ __forceinline__ int64_t gcol(const Layout &L, int64_t c, int jl) {
   if (jl < L.nfd * k) return (int64_t)L.nfd * L.cf[L.cfp[c] + jl / L.nfd] + jl % L.nfd;
   return (int64_t)L.nfd * L.nf + (int64_t)L.nid * c + (jl - L.nfd * k);
 }
-__device__ __forceinline__ int64_t boff(const Layout &L, int64_t c) {
-  return L.cfp[c] * L.nfd + (int64_t)L.nid * c;
+__device__ __forceinline__ int64_t boff(const Layout &L, int64_t c) { return L.b_off[L.cls_of[c]]; }
+__device__ __forceinline__ const double *mloc(const Layout &L, int64_t c) {
+  return L.Mloc + L.m_off[L.cls_of[c]];
 }
 
 __global__ void k_rowcount(Layout L, int64_t *cnt) {
@@ -92,12 +96,12 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t 
       const int32_t c0 = L.f_cell[2 * f], c1 = L.f_cell[2 * f + 1];
       const int l0 = L.f_loc[2 * f], l1 = L.f_loc[2 * f + 1];
       const int n0 = nloc(L, c0);
-      const double *M0 = L.Mloc + L.m_off[c0] + (int64_t)(l0 * L.nfd + beta) * n0;
+      const double *M0 = mloc(L, c0) + (int64_t)(l0 * L.nfd + beta) * n0;
       const double *M1 = nullptr;
       int n1 = 0;
       if (c1 >= 0) {
         n1 = nloc(L, c1);
-        M1 = L.Mloc + L.m_off[c1] + (int64_t)(l1 * L.nfd + beta) * n1;
+        M1 = mloc(L, c1) + (int64_t)(l1 * L.nfd + beta) * n1;
       }
       const double w0 = nsc ? nsc[c0] : 1.0, w1 = (nsc && c1 >= 0) ? nsc[c1] : 1.0;
       double dg = 0.0;
@@ -126,7 +130,7 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t 
       const int l = (int)(q % L.nid);
       const int nl = nloc(L, c);
       const int jr = nl - L.nid + l;
-      const double *Mr = L.Mloc + L.m_off[c] + (int64_t)jr * nl;
+      const double *Mr = mloc(L, c) + (int64_t)jr * nl;
       const double wc = nsc ? nsc[c] : 1.0;
       for (int jl = 0; jl < nl; ++jl) PUT(gcol(L, c, jl), wc * Mr[jl]);
       diagM[r] = wc * Mr[jr];
@@ -195,6 +199,12 @@ __global__ void k_schur_fill(Layout L, const double *__restrict__ diagM, const i
       val[p] = 0.0;
     }
   }
+}
+
+__global__ void k_iota32(int64_t n, int32_t *a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = (int32_t)i;
 }
 
 __global__ void k_f64_to_f32(int64_t n, const double *__restrict__ a, float *b) {
@@ -361,13 +371,29 @@ static vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int6
   return VEM_OK;
 }
 
-// Sum of true row lengths.
+// Sum of true row lengths by one block (one scalar goes to the host).
+__global__ void k_len_sum(int64_t n, const int32_t *__restrict__ len, int64_t *out) {
+  __shared__ int64_t ws[32];
+  int64_t s = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += len[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += ws[i];
+    *out = t;
+  }
+}
+
 static vem_status sell_nnz(vem_handle *h, SellMat &M) {
-  std::vector<int32_t> len(M.nslices * 32);
-  VEM_CUDA(h, cudaMemcpyAsync(len.data(), M.len, sizeof(int32_t) * len.size(), cudaMemcpyDeviceToHost, h->stream));
-  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  int64_t *cnt = h->slice_buf;   // reuse: the per-slice sizes are no longer needed
+  count_launch();
+  k_len_sum<<<1, 1024, 0, h->stream>>>(M.nslices * 32, M.len, cnt);
+  VEM_CUDA(h, cudaGetLastError());
   int64_t t = 0;
-  for (int32_t v : len) t += v;
+  VEM_CUDA(h, cudaMemcpyAsync(&t, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
   M.nnz = t;
   return VEM_OK;
 }
@@ -402,7 +428,7 @@ vem_status sell_to_host_csr(vem_handle *h, const SellMat &M, int64_t *rp, int32_
 vem_status assemble_global(vem_handle *h) {
   cudaStream_t s = h->stream;
   Layout L{h->nfd, h->nid, h->nf, h->nc, h->n_u, h->cf_ptr, h->cf, h->f_cell, h->f_loc,
-           h->m_off, h->Mloc, h->Bloc};
+           h->m_off, h->b_off, h->cls_of, h->Mloc, h->Bloc};
   const int T = 256;
   const int64_t n = h->n;
   // ---- [M B^T; B 0] ----
@@ -414,7 +440,7 @@ vem_status assemble_global(vem_handle *h) {
   if (!h->diagM) VEM_TRY(dalloc_n(h, &h->diagM, (size_t)h->n_u));
   const int64_t npad = h->A.nslices * 32;
   count_launch(); k_fill<<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, h->A.len, npad, h->A.col, h->A.val, h->diagM,
-                                                      nullptr, h->A.stored);
+                                                      h->nu, h->A.stored);
   VEM_CUDA(h, cudaGetLastError());
   // ---- S ----
   count_launch(); k_schur_count<<<grid_for(h->nc, T), T, 0, s>>>(L, cnt);
@@ -446,13 +472,212 @@ vem_status assemble_global(vem_handle *h) {
   return VEM_OK;
 }
 
+// ---------------------------------------------------------------- classes --
+// Cells that are translates of one another (same vertex offsets from the
+// barycentre, same face and vertex order, same orientations) have the same
+// geometry-only local matrices.  Each cell gets a key hashed from its vertex
+// offsets quantised at 2^-40 of the mesh diagonal; equal keys go to one
+// hash-table slot whose smallest cell id represents the class, and every cell
+// is checked against its representative exactly (quantised values) before it
+// joins the class.
+__device__ __forceinline__ uint64_t mix64(uint64_t h, uint64_t v) {
+  h ^= v + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
+  h *= 0xff51afd7ed558ccdULL;
+  return h ^ (h >> 33);
+}
+
+__device__ __forceinline__ long long qcoord(double v, double x, double inv_q) { return llrint((v - x) * inv_q); }
+
+__global__ void k_class_key(int64_t nc, const int64_t *__restrict__ cfp, const int32_t *__restrict__ cf,
+                            const int64_t *__restrict__ fvp, const int32_t *__restrict__ fv,
+                            const double *__restrict__ xyz, const double *__restrict__ c_cent,
+                            const int8_t *__restrict__ sig, double inv_q, uint64_t *key) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = cfp[c];
+    const int k = (int)(cfp[c + 1] - b);
+    const double x0 = c_cent[3 * c], x1 = c_cent[3 * c + 1], x2 = c_cent[3 * c + 2];
+    uint64_t h = mix64(0x1234567ULL, (uint64_t)k);
+    for (int i = 0; i < k; ++i) {
+      const int f = cf[b + i];
+      h = mix64(h, (uint64_t)(sig[b + i] + 2));
+      h = mix64(h, (uint64_t)(fvp[f + 1] - fvp[f]));
+      for (int64_t p = fvp[f]; p < fvp[f + 1]; ++p) {
+        const int64_t v = fv[p];
+        h = mix64(h, (uint64_t)qcoord(xyz[3 * v], x0, inv_q));
+        h = mix64(h, (uint64_t)qcoord(xyz[3 * v + 1], x1, inv_q));
+        h = mix64(h, (uint64_t)qcoord(xyz[3 * v + 2], x2, inv_q));
+      }
+    }
+    key[c] = h | 1ULL;
+  }
+}
+
+__global__ void k_class_insert(int64_t nc, const uint64_t *__restrict__ key, unsigned long long *tkey,
+                               int *trep, uint64_t mask) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = key[c];
+    uint64_t s = (k ^ (k >> 31)) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+      const unsigned long long prev = atomicCAS(&tkey[s], 0ULL, k);
+      if (prev == 0ULL || prev == k) {
+        atomicMin(&trep[s], (int)c);
+        break;
+      }
+      s = (s + 1) & mask;
+    }
+  }
+}
+
+// rep[c] from the table, then the exact check against the representative
+__global__ void k_class_lookup(int64_t nc, const uint64_t *__restrict__ key,
+                               const unsigned long long *__restrict__ tkey, const int *__restrict__ trep,
+                               uint64_t mask, const int64_t *__restrict__ cfp, const int32_t *__restrict__ cf,
+                               const int64_t *__restrict__ fvp, const int32_t *__restrict__ fv,
+                               const double *__restrict__ xyz, const double *__restrict__ c_cent,
+                               const int8_t *__restrict__ sig, double inv_q, int32_t *rep) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = key[c];
+    uint64_t s = (k ^ (k >> 31)) & mask;
+    int r = (int)c;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+      if (tkey[s] == k) {
+        r = trep[s];
+        break;
+      }
+      s = (s + 1) & mask;
+    }
+    bool same = r != (int)c;
+    if (same) {
+      const int64_t b = cfp[c], br = cfp[r];
+      const int kc = (int)(cfp[c + 1] - b);
+      same = kc == (int)(cfp[r + 1] - br);
+      for (int i = 0; same && i < kc; ++i) {
+        const int f = cf[b + i], g = cf[br + i];
+        const int64_t m = fvp[f + 1] - fvp[f];
+        same = sig[b + i] == sig[br + i] && m == fvp[g + 1] - fvp[g];
+        for (int64_t p = 0; same && p < m; ++p) {
+          const int64_t v = fv[fvp[f] + p], w = fv[fvp[g] + p];
+          for (int d = 0; d < 3; ++d)
+            same = same && qcoord(xyz[3 * v + d], c_cent[3 * c + d], inv_q) ==
+                               qcoord(xyz[3 * w + d], c_cent[3 * r + d], inv_q);
+        }
+      }
+    }
+    rep[c] = same ? r : (int)c;
+  }
+}
+
+__global__ void k_class_flags(int64_t nc, const int32_t *__restrict__ rep, int64_t *flag) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x)
+    flag[c] = rep[c] == (int32_t)c ? 1 : 0;
+}
+
+// idx = exclusive scan of the flags: class of c = idx[rep[c]]; class sizes
+__global__ void k_class_assign(int64_t nc, int nfd, int nid, const int32_t *__restrict__ rep,
+                               const int64_t *__restrict__ idx, const int64_t *__restrict__ cfp,
+                               int32_t *cls_of, int32_t *cls_rep, int64_t *msz, int64_t *bsz) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = idx[rep[c]];
+    cls_of[c] = (int32_t)k;
+    if (rep[c] == (int32_t)c) {
+      cls_rep[k] = (int32_t)c;
+      const int64_t nl = nfd * (cfp[c + 1] - cfp[c]) + nid;
+      msz[k] = nl * nl;
+      bsz[k] = nl;
+    }
+  }
+}
+
+vem_status classify_cells(vem_handle *h) {
+  cudaStream_t s = h->stream;
+  const int T = 256;
+  const int64_t nc = h->nc;
+  if (!h->cls_of) VEM_TRY(dalloc_n(h, &h->cls_of, (size_t)nc));
+  if (!h->cls_rep) VEM_TRY(dalloc_n(h, &h->cls_rep, (size_t)nc));
+  if (!h->m_off) VEM_TRY(dalloc_n(h, &h->m_off, (size_t)nc + 1));
+  if (!h->b_off) VEM_TRY(dalloc_n(h, &h->b_off, (size_t)nc + 1));
+  uint64_t tsize = 1;
+  while (tsize < 2 * (uint64_t)nc) tsize <<= 1;
+  // persistent scratch (sizes depend on the mesh only)
+  const size_t need = sizeof(uint64_t) * (3 * (size_t)tsize / 2 + 6 * (size_t)nc + 8);
+  if (h->cls_scratch_bytes < need) {
+    dfree(h, h->cls_scratch);
+    h->cls_scratch = nullptr;
+    VEM_TRY(dalloc(h, &h->cls_scratch, need));
+    h->cls_scratch_bytes = need;
+  }
+  char *sp = static_cast<char *>(h->cls_scratch);
+  unsigned long long *tkey = reinterpret_cast<unsigned long long *>(sp);
+  sp += sizeof(unsigned long long) * tsize;
+  int *trep = reinterpret_cast<int *>(sp);
+  sp += sizeof(int) * tsize;
+  uint64_t *key = reinterpret_cast<uint64_t *>(sp);
+  sp += sizeof(uint64_t) * nc;
+  int64_t *flag = reinterpret_cast<int64_t *>(sp);
+  sp += sizeof(int64_t) * nc;
+  int64_t *idx = reinterpret_cast<int64_t *>(sp);
+  sp += sizeof(int64_t) * (nc + 1);
+  int64_t *msz = reinterpret_cast<int64_t *>(sp);
+  sp += sizeof(int64_t) * nc;
+  int64_t *bsz = reinterpret_cast<int64_t *>(sp);
+  sp += sizeof(int64_t) * nc;
+  int32_t *rep = reinterpret_cast<int32_t *>(sp);
+  const double inv_q = 1099511627776.0 / h->lref;   // 2^40 / diagonal
+  if (h->opt.reuse) {
+    VEM_CUDA(h, cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tsize, s));
+    VEM_CUDA(h, cudaMemsetAsync(trep, 0x7f, sizeof(int) * tsize, s));
+    count_launch();
+    k_class_key<<<grid_for(nc, T), T, 0, s>>>(nc, h->cf_ptr, h->cf, h->fv_ptr, h->fv, h->xyz, h->c_cent,
+                                               h->cf_sigma, inv_q, key);
+    count_launch();
+    k_class_insert<<<grid_for(nc, T), T, 0, s>>>(nc, key, tkey, trep, tsize - 1);
+    count_launch();
+    k_class_lookup<<<grid_for(nc, T), T, 0, s>>>(nc, key, tkey, trep, tsize - 1, h->cf_ptr, h->cf, h->fv_ptr,
+                                                  h->fv, h->xyz, h->c_cent, h->cf_sigma, inv_q, rep);
+  } else {
+    count_launch();
+    k_iota32<<<grid_for(nc, T), T, 0, s>>>(nc, rep);
+  }
+  count_launch();
+  k_class_flags<<<grid_for(nc, T), T, 0, s>>>(nc, rep, flag);
+  VEM_CUDA(h, cudaGetLastError());
+  int64_t ncls = 0;
+  VEM_TRY(scan_counts(h, nc, flag, idx, &ncls));
+  count_launch();
+  k_class_assign<<<grid_for(nc, T), T, 0, s>>>(nc, h->nfd, h->nid, rep, idx, h->cf_ptr, h->cls_of, h->cls_rep,
+                                                msz, bsz);
+  VEM_CUDA(h, cudaGetLastError());
+  int64_t mt = 0, bt = 0;
+  VEM_TRY(scan_counts(h, ncls, msz, h->m_off, &mt));
+  VEM_TRY(scan_counts(h, ncls, bsz, h->b_off, &bt));
+  h->ncls = ncls;
+  if (h->m_total != mt || !h->Mloc) {
+    dfree(h, h->Mloc);
+    h->Mloc = nullptr;
+    VEM_TRY(dalloc_n(h, &h->Mloc, (size_t)mt));
+    h->m_total = mt;
+  }
+  if (h->b_total != bt || !h->Bloc) {
+    dfree(h, h->Bloc);
+    h->Bloc = nullptr;
+    VEM_TRY(dalloc_n(h, &h->Bloc, (size_t)bt));
+    h->b_total = bt;
+  }
+  return VEM_OK;
+}
+
 // Values of nb systems that share the mesh and the structure of h->A / h->S:
 // A_b, diag(M_b), S_b, 1/diag(S_b) (and FP32 copies), from local matrices
 // computed with nu = 1 and scaled per cell by nu_b = 1/K_b.
 vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, VemOp &op) {
   cudaStream_t s = h->stream;
   Layout L{h->nfd, h->nid, h->nf, h->nc, h->n_u, h->cf_ptr, h->cf, h->f_cell, h->f_loc,
-           h->m_off, h->Mloc, h->Bloc};
+           h->m_off, h->b_off, h->cls_of, h->Mloc, h->Bloc};
   const int T = 256;
   const int64_t npad = h->A.nslices * 32, spad = h->S.nslices * 32;
   dim3 ga(grid_for(npad, T, 2), nb), gs(grid_for(spad, T, 2), nb);

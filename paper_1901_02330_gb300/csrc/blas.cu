@@ -39,15 +39,6 @@ int nblocks_vec(int64_t n) {
   return (int)b;
 }
 
-int spmv_nblocks(const SellMat &A, int nbatch) {
-  int64_t b = (A.nslices * nbatch + 7) / 8;   // one warp per slice, 8 warps per block
-  int64_t cap = (int64_t)num_sms() * 8;
-  if (cap > kMaxBlocks) cap = kMaxBlocks;
-  if (b > cap) b = cap;
-  if (b < 1) b = 1;
-  return (int)b;
-}
-
 // y = A x for a SELL-32 matrix: one warp per slice, one thread per row, one
 // FP64 FMA per stored element and lane (no shuffles), coalesced loads of the
 // matrix (streamed, evict-first) and read-only-path gathers of x.  With
@@ -71,6 +62,28 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int64_t rows, int64_t nslices
     }
   }
   if (dot_part) block_partial(dacc, dot_part);
+}
+
+// Blocks of 256 threads that fit on the GPU at once for this kernel: grid-
+// stride kernels launched with exactly one wave avoid a partial second wave.
+int one_wave_blocks(const void *kernel) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 4;
+  }
+  int64_t cap = (int64_t)num_sms() * occ;
+  if (cap > kMaxBlocks) cap = kMaxBlocks;
+  return (int)cap;
+}
+
+int spmv_nblocks(const SellMat &A, int nbatch) {
+  static int cap = 0;
+  if (cap == 0) cap = one_wave_blocks((const void *)k_sell_spmv);
+  int64_t b = (A.nslices * nbatch + 7) / 8;   // one warp per slice, 8 warps per block
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
 }
 
 void spmv(cudaStream_t s, const SellMat &A, const double *x, double *y, double *dot_part) {

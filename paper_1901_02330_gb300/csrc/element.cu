@@ -35,21 +35,24 @@ __device__ __forceinline__ void upper_decode(int e, int n, int &i, int &j) {
 }
 
 // ---------------------------------------------------------------- E0 ----
-__global__ void k_elem_e0(int64_t nc, int max_nf, const int64_t *__restrict__ cfp,
+// One warp per congruence class (its representative cell), nu = 1.
+__global__ void k_elem_e0(int64_t ncls, int max_nf, const int64_t *__restrict__ cfp,
                           const int32_t *__restrict__ cf, const int8_t *__restrict__ sig,
                           const double *__restrict__ f_area, const double *__restrict__ f_cent,
                           const double *__restrict__ f_norm, const double *__restrict__ c_vol,
-                          const double *__restrict__ c_cent, const double *__restrict__ nu,
-                          const int64_t *__restrict__ m_off, double *Mloc, double *Bloc) {
+                          const double *__restrict__ c_cent, const int32_t *__restrict__ cls_rep,
+                          const int64_t *__restrict__ m_off, const int64_t *__restrict__ b_off,
+                          double *Mloc, double *Bloc) {
   extern __shared__ double sm[];
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double *N = sm + (size_t)warp * (6 * max_nf + 9);
   double *nn = N + 3 * max_nf;
   double *Q = nn + 3 * max_nf;
-  for (int64_t c = (int64_t)blockIdx.x * wpb + warp; c < nc; c += (int64_t)gridDim.x * wpb) {
+  for (int64_t kk = (int64_t)blockIdx.x * wpb + warp; kk < ncls; kk += (int64_t)gridDim.x * wpb) {
+    const int64_t c = cls_rep[kk];
     const int64_t b = cfp[c];
     const int k = (int)(cfp[c + 1] - b);
-    const double vol = c_vol[c], nuc = nu[c], ivol = 1.0 / vol;
+    const double vol = c_vol[c], nuc = 1.0, ivol = 1.0 / vol;
     const double3 xP = load3(c_cent, c);
     for (int i = lane; i < k; i += 32) {
       const int f = cf[b + i];
@@ -61,7 +64,7 @@ __global__ void k_elem_e0(int64_t nc, int max_nf, const int64_t *__restrict__ cf
       nn[3 * i] = f_norm[3 * f];
       nn[3 * i + 1] = f_norm[3 * f + 1];
       nn[3 * i + 2] = f_norm[3 * f + 2];
-      Bloc[b + i] = s;
+      Bloc[b_off[kk] + i] = s;
     }
     __syncwarp();
     if (lane < 9) {
@@ -71,7 +74,7 @@ __global__ void k_elem_e0(int64_t nc, int max_nf, const int64_t *__restrict__ cf
       Q[lane] = t;
     }
     __syncwarp();
-    double *M = Mloc + m_off[c];
+    double *M = Mloc + m_off[kk];
     const int T = k * (k + 1) / 2;
     for (int e = lane; e < T; e += 32) {
       int i, j;
@@ -132,15 +135,15 @@ __device__ __forceinline__ void sf3_point(int q, double &l0, double &l1, double 
   }
 }
 
-__global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cfp,
+__global__ void k_elem_k1(int64_t ncls, int max_nf, const int64_t *__restrict__ cfp,
                           const int32_t *__restrict__ cf, const int8_t *__restrict__ sig,
                           const int64_t *__restrict__ fvp, const int32_t *__restrict__ fv,
                           const double *__restrict__ xyz, const double *__restrict__ f_area,
                           const double *__restrict__ f_cent, const double *__restrict__ f_norm,
                           const double *__restrict__ f_t1, const double *__restrict__ f_diam,
                           const double *__restrict__ c_cent, const double *__restrict__ c_diam,
-                          const double *__restrict__ nu, const int64_t *__restrict__ m_off,
-                          double *Mloc, double *Bloc, int *err) {
+                          const int32_t *__restrict__ cls_rep, const int64_t *__restrict__ m_off,
+                          const int64_t *__restrict__ b_off, double *Mloc, double *Bloc, int *err) {
   extern __shared__ double sm[];
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nd = k1_doubles(max_nf);
@@ -152,13 +155,14 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
   double *U = W + 144;
   int *FO = reinterpret_cast<int *>(sm + (size_t)wpb * nd) + warp * k1_ints(max_nf);
 
-  for (int64_t c = (int64_t)blockIdx.x * wpb + warp; c < nc; c += (int64_t)gridDim.x * wpb) {
+  for (int64_t kk = (int64_t)blockIdx.x * wpb + warp; kk < ncls; kk += (int64_t)gridDim.x * wpb) {
+    const int64_t c = cls_rep[kk];
     const int64_t b = cfp[c];
     const int k = (int)(cfp[c + 1] - b);
     const int nu_l = 3 * k + 3;
     const double3 xP = load3(c_cent, c);
     const double hP = c_diam[c], ihP = 1.0 / hP;
-    const double nuc = nu[c];
+    const double nuc = 1.0;
 
     // (0) per-face data and the prefix of quadrature items (4 per fan triangle)
     for (int i = lane; i < k; i += 32) {
@@ -300,7 +304,7 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
     double *DD = U + 12 * nu_l;          // [nu_l][12]
     double *VV = DD + 12 * nu_l;         // [12][nu_l]
     const int nfl = 3 * k;
-    const int64_t boff = 3 * b + 3 * c;
+    const int64_t boff = b_off[kk];
 
     // (2)-(3) columns j of G, D and B; Pi[:, j] = blockdiag(H1^{-1}) G[:, j]
     for (int j = lane; j < nu_l; j += 32) {
@@ -389,7 +393,7 @@ __global__ void k_elem_k1(int64_t nc, int max_nf, const int64_t *__restrict__ cf
     }
     __syncwarp();
     // (4) M_P entries: nu (|P| delta + Pi_j . V_j' - |P| D_j . Pi_j'), j <= j'
-    double *M = Mloc + m_off[c];
+    double *M = Mloc + m_off[kk];
     const int TT = nu_l * (nu_l + 1) / 2;
     for (int e = lane; e < TT; e += 32) {
       int j, jp;
@@ -493,23 +497,24 @@ static int warps_per_block(size_t bytes_per_warp, size_t limit = 96 * 1024) {
   return w;
 }
 
-vem_status assemble_local(vem_handle *h) { return assemble_local_nu(h, h->nu); }
-
-vem_status assemble_local_nu(vem_handle *h, const double *nu) {
+// Geometry-only local matrices (nu = 1), one per congruence class.
+vem_status assemble_local(vem_handle *h) {
   cudaStream_t s = h->stream;
   const int mx = h->max_nf_cell;
+  const int64_t ncls = h->ncls;
   if (h->opt.element == VEM_ELEMENT_E0) {
     const size_t bpw = sizeof(double) * (6 * mx + 9);
     if (bpw > 200 * 1024) return fail(h, VEM_ERR_UNSUPPORTED, "cell with %d faces", mx);
     const int wpb = warps_per_block(bpw);
     const size_t smem = bpw * wpb;
     VEM_CUDA(h, cudaFuncSetAttribute(k_elem_e0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int64_t blocks = (h->nc + wpb - 1) / wpb;
+    int64_t blocks = (ncls + wpb - 1) / wpb;
     const int64_t cap = (int64_t)num_sms() * 16;
     if (blocks > cap) blocks = cap;
-    count_launch(); k_elem_e0<<<(int)blocks, 32 * wpb, smem, s>>>(h->nc, mx, h->cf_ptr, h->cf, h->cf_sigma, h->f_area,
-                                                   h->f_cent, h->f_norm, h->c_vol, h->c_cent, nu,
-                                                   h->m_off, h->Mloc, h->Bloc);
+    count_launch();
+    k_elem_e0<<<(int)blocks, 32 * wpb, smem, s>>>(ncls, mx, h->cf_ptr, h->cf, h->cf_sigma, h->f_area, h->f_cent,
+                                                   h->f_norm, h->c_vol, h->c_cent, h->cls_rep, h->m_off,
+                                                   h->b_off, h->Mloc, h->Bloc);
     VEM_CUDA(h, cudaGetLastError());
   } else if (h->opt.element == VEM_ELEMENT_K1) {
     const size_t bpw = sizeof(double) * k1_doubles(mx) + sizeof(int) * k1_ints(mx);
@@ -517,13 +522,13 @@ vem_status assemble_local_nu(vem_handle *h, const double *nu) {
     const int wpb = warps_per_block(bpw);
     const size_t smem = bpw * wpb;
     VEM_CUDA(h, cudaFuncSetAttribute(k_elem_k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int64_t blocks = (h->nc + wpb - 1) / wpb;
+    int64_t blocks = (ncls + wpb - 1) / wpb;
     const int64_t cap = (int64_t)num_sms() * 16;
     if (blocks > cap) blocks = cap;
-    count_launch(); k_elem_k1<<<(int)blocks, 32 * wpb, smem, s>>>(
-        h->nc, mx, h->cf_ptr, h->cf, h->cf_sigma, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent,
-        h->f_norm, h->f_t1, h->f_diam, h->c_cent, h->c_diam, nu, h->m_off, h->Mloc, h->Bloc,
-        h->d_err);
+    count_launch();
+    k_elem_k1<<<(int)blocks, 32 * wpb, smem, s>>>(
+        ncls, mx, h->cf_ptr, h->cf, h->cf_sigma, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm,
+        h->f_t1, h->f_diam, h->c_cent, h->c_diam, h->cls_rep, h->m_off, h->b_off, h->Mloc, h->Bloc, h->d_err);
     VEM_CUDA(h, cudaGetLastError());
   } else {
     return fail(h, VEM_ERR_UNSUPPORTED, "element %d", h->opt.element);

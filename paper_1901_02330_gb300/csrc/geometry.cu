@@ -89,17 +89,21 @@ __global__ void k_cell_geom(int64_t nc, const int64_t *__restrict__ cfp,
       int8_t s = hc > 0.0 ? 1 : -1;
       if (s != cf_sigma[b + i] || hc == 0.0) bad = 1;
     }
-    double dm = 0;
+    double dm2 = 0;   // squared diameter (one square root at the end)
     for (int i = 0; i < k; ++i) {
       const int f = cf[b + i];
       for (int64_t p = fvp[f]; p < fvp[f + 1]; ++p) {
         double3 A = load3(xyz, fv[p]);
         for (int j = i; j < k; ++j) {
           const int g = cf[b + j];
-          for (int64_t q = fvp[g]; q < fvp[g + 1]; ++q) dm = fmax(dm, norm3(sub3(A, load3(xyz, fv[q]))));
+          for (int64_t q = fvp[g]; q < fvp[g + 1]; ++q) {
+            const double3 d = sub3(A, load3(xyz, fv[q]));
+            dm2 = fmax(dm2, dot3(d, d));
+          }
         }
       }
     }
+    const double dm = sqrt(dm2);
     if (!(vol > 0.0) || !isfinite(vol)) atomicOr(err, DEVERR_DEGENERATE_CELL);
     if (bad) atomicOr(err, DEVERR_NONCONVEX);
     c_vol[c] = vol;

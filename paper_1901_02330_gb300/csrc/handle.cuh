@@ -62,8 +62,16 @@ struct vem_handle {
   double *f_qp = nullptr, *gD_qp = nullptr;
   bool have_coef = false, assembled = false, rhs_ready = false;
 
-  // ---- local matrices ----
-  int64_t *m_off = nullptr;                      // [nc + 1]
+  // ---- local matrices: one per congruence class of cells, computed with
+  // nu = 1 (M_P = nu_P Mhat_class, B_P = Bhat_class) ----
+  int64_t *m_off = nullptr;                      // [nc + 1] class offsets in Mloc (ncls + 1 used)
+  int64_t *b_off = nullptr;                      // [nc + 1] class offsets in Bloc
+  int32_t *cls_of = nullptr;                     // [nc] class of every cell
+  int32_t *cls_rep = nullptr;                    // [nc] representative cell of every class
+  int64_t ncls = 0;
+  double lref = 1.0;                             // mesh bounding-box diagonal
+  void *cls_scratch = nullptr;                   // classification scratch
+  size_t cls_scratch_bytes = 0;
   int64_t m_total = 0, b_total = 0;
   double *Mloc = nullptr, *Bloc = nullptr;
 
@@ -99,12 +107,15 @@ struct vem_handle {
 
   std::vector<void *> allocations;               // everything cudaMalloc'ed
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  static constexpr int kTimed = 16;              // timed Schur SpMV launches per poll
+  cudaEvent_t tev[2 * kTimed] = {};
+  double t_schur_spmv_ms = 0.0;                  // accumulated over a solve
+  int64_t n_schur_spmv = 0;
   double t_assemble_ms = 0.0, t_element_ms = 0.0, t_scatter_ms = 0.0;
 
   // ---- batched systems ----
   VemOp bop;                                     // stacked operator (values per batch)
   double *b_nu = nullptr, *b_rhs = nullptr, *b_x = nullptr, *b_fqp = nullptr, *b_gqp = nullptr;
-  double *unit_nu = nullptr;                     // nu = 1 (geometry-only local matrices)
   int b_cap = 0;                                 // batches the buffers hold
 };
 
@@ -143,6 +154,7 @@ void spmv(cudaStream_t s, const SellMat &A, const double *x, double *y, double *
 void spmv_batched(cudaStream_t s, const SellMat &A, int nb, int64_t split, const double *vals,
                   const double *x, double *y, double *dot_part = nullptr);
 int spmv_nblocks(const SellMat &A, int nbatch = 1);
+int one_wave_blocks(const void *kernel);
 int nblocks_vec(int64_t n);
 void dot_partials(cudaStream_t s, int64_t n, const double *x, const double *y, double *part);
 // CSR view of a SELL matrix on the host (row_ptr[rows + 1], col, val)
@@ -154,7 +166,8 @@ vem_status krylov_solve(vem_handle *h, const VemOp &op, const double *rhs, doubl
 VemOp single_op(vem_handle *h);
 
 vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, VemOp &op);
-vem_status assemble_local_nu(vem_handle *h, const double *nu);
+// Congruence classes of cells and the per-class layout of Mloc / Bloc.
+vem_status classify_cells(vem_handle *h);
 // Adjoint contraction (adjoint.cu): g_c = lam_{u,c}^T M_c u_c per cell.
 vem_status adjoint_contract(vem_handle *h, const double *lam, const double *x, double *g);
 

@@ -197,15 +197,36 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   const int64_t n = op.n_p;
   T *r = wk, *u = wk + n, *p = wk + 2 * n, *sv = wk + 3 * n, *w = wk + 4 * n;
   const int nb = nblocks_vec(n);
-  const int nbs = spmv_nblocks(op.S, op.nbatch);
+  static int cap_s = 0;
+  if (cap_s == 0) cap_s = one_wave_blocks((const void *)k_cg_spmv<T>);
+  int nbs = (int)((op.S.nslices * op.nbatch + 7) / 8);
+  if (nbs > cap_s) nbs = cap_s;
+  if (nbs < 1) nbs = 1;
   double *sc = h->scal;
   const double tol2 = h->opt.inner_rtol * h->opt.inner_rtol;
   count_launch();
   k_cg_init<T><<<nb, kRedThreads, 0, s>>>(n, b, dinv, x, r, u, p, sv, h->part, sc, h->ctr);
+  // every launch of the Schur SpMV is timed with a pair of events
+  int ntimed = 0;
   auto spmv_it = [&](int it) {
+    if (ntimed < vem_handle::kTimed) cudaEventRecord(h->tev[2 * ntimed], s);
     count_launch();
     k_cg_spmv<T><<<nbs, 256, 0, s>>>(op.S.rows, op.S.nslices, op.nbatch, op.S.stored, op.S.off, op.S.col,
                                      sval, u, r, w, h->part, sc, h->ctr + 1, tol2, it);
+    if (ntimed < vem_handle::kTimed) cudaEventRecord(h->tev[2 * ntimed + 1], s);
+    ++ntimed;
+  };
+  auto collect = [&]() {
+    const int m = ntimed < vem_handle::kTimed ? ntimed : vem_handle::kTimed;
+    for (int i = 0; i < m; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->tev[2 * i], h->tev[2 * i + 1]) == cudaSuccess) {
+        h->t_schur_spmv_ms += ms;
+        h->n_schur_spmv += 1;
+      }
+    }
+    cudaGetLastError();
+    ntimed = 0;
   };
   spmv_it(0);
   const int maxit = h->opt.inner_maxit;
@@ -221,6 +242,7 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
     VEM_CUDA(h, cudaGetLastError());
     VEM_CUDA(h, cudaMemcpyAsync(h->h_scal, sc, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
     VEM_CUDA(h, cudaStreamSynchronize(s));
+    collect();
     if (h->h_scal[S_PCG_DONE] != 0.0) break;
   }
   if (h->h_scal[S_PCG_BAD] != 0.0)

@@ -37,14 +37,15 @@ class vem_mesh(C.Structure):
 class vem_options(C.Structure):
     _fields_ = [("element", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("rtol", C.c_double),
                 ("maxit", C.c_int), ("precond", C.c_int), ("inner", C.c_int), ("inner_rtol", C.c_double),
-                ("inner_maxit", C.c_int), ("precision", C.c_int), ("device_io", C.c_int)]
+                ("inner_maxit", C.c_int), ("precision", C.c_int), ("device_io", C.c_int), ("reuse", C.c_int)]
 
 
 class vem_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("inner_iterations", C.c_int32), ("relres", C.c_double),
                 ("t_assemble_ms", C.c_double), ("t_solve_ms", C.c_double),
                 ("n_u", C.c_int64), ("n_p", C.c_int64), ("nnz_A", C.c_int64), ("nnz_S", C.c_int64),
-                ("t_element_ms", C.c_double), ("t_scatter_ms", C.c_double)]
+                ("t_element_ms", C.c_double), ("t_scatter_ms", C.c_double), ("n_classes", C.c_int64),
+                ("t_schur_spmv_ms", C.c_double), ("n_schur_spmv", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -245,3 +245,31 @@ def test_mixed_precision_needs_fgmres(vs):
     with pytest.raises(vs.VemError) as e:
         vs.Solver(hex_mesh(2), krylov=0, precond=0, precision=vs.VEM_PRECISION_MIXED)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("mname,expect_few", [("hex3", True), ("sheared", True), ("cvt", False)])
+@pytest.mark.parametrize("ename", list(ELEMENTS))
+def test_reuse_of_congruent_cells(vs, mname, expect_few, ename):
+    """Cells that are translates of one another share one evaluation of their
+    geometry-only local matrices: same solution (to rounding) with reuse on
+    and off, and the class count is tiny on structured meshes and equals the
+    cell count on a Voronoi mesh."""
+    spec, elem = ELEMENTS[ename]
+    mesh = MESHES[mname]()
+    K = fields.K_lognormal(mesh.n_cells, seed=9, sigma=1.0)
+    prob = fields.sine_problem()
+    out = {}
+    for reuse in (1, 0):
+        s = _solver(vs, mesh, elem, krylov=1, precond=1, rtol=1e-12, inner_rtol=1e-13, reuse=reuse)
+        s.set_coefficient(K)
+        s.set_data(prob.f, prob.gD)
+        out[reuse] = s.solve()
+        s.close()
+    (u1, p1, st1), (u0, p0, st0) = out[1], out[0]
+    assert st0["n_classes"] == mesh.n_cells
+    if expect_few:
+        assert st1["n_classes"] <= 3
+    else:
+        assert st1["n_classes"] == mesh.n_cells
+    assert np.linalg.norm(u1 - u0) <= 1e-11 * np.linalg.norm(u0)
+    assert np.linalg.norm(p1 - p0) <= 1e-11 * np.linalg.norm(p0)
