@@ -113,19 +113,19 @@ __global__ void __launch_bounds__(256) k_sell_spmv_b(int64_t rows, int64_t nslic
     const int w = (int)((off[s + 1] - o) >> 5);
     const double *vp = vals + b * stored + o + lane;
     const int32_t *cp = col + o + lane;
-    double s0 = 0.0, s1 = 0.0;
+    double t = 0.0;
     int j = 0;
     for (; j + 1 < w; j += 2) {
       const int64_t c0 = __ldcs(cp + 32 * j), c1 = __ldcs(cp + 32 * (j + 1));
       const double v0 = __ldcs(vp + 32 * j), v1 = __ldcs(vp + 32 * (j + 1));
-      s0 += v0 * __ldg(x + c0 + (c0 < split ? olo : ohi));
-      s1 += v1 * __ldg(x + c1 + (c1 < split ? olo : ohi));
+      const double x0 = __ldg(x + c0 + (c0 < split ? olo : ohi)), x1 = __ldg(x + c1 + (c1 < split ? olo : ohi));
+      t += v0 * x0;
+      t += v1 * x1;
     }
     if (j < w) {
       const int64_t c0 = __ldcs(cp + 32 * j);
-      s0 += __ldcs(vp + 32 * j) * __ldg(x + c0 + (c0 < split ? olo : ohi));
+      t += __ldcs(vp + 32 * j) * __ldg(x + c0 + (c0 < split ? olo : ohi));
     }
-    const double t = s0 + s1;
     const int64_t r = 32 * s + lane;
     if (r < rows) {
       const int64_t R = r + (r < split ? olo : ohi);

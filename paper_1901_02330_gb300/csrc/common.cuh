@@ -105,8 +105,9 @@ __device__ __forceinline__ void block_partial(double v, double *part) {
 }
 
 // Row (32 s + lane) of a SELL-32 matrix times x: elements in column order,
-// four independent loads in flight; T = double or float (values, x and the
-// arithmetic share the type).
+// four independent loads in flight, one FMA chain (GB300 issues FP64 at 1/16
+// of the lane rate, so combining partial accumulators would cost FP64 adds
+// per row); T = double or float (values, x and arithmetic share the type).
 template <class T>
 __device__ __forceinline__ T sell_row_dot(const int64_t *__restrict__ off,
                                           const int32_t *__restrict__ col,
@@ -116,20 +117,21 @@ __device__ __forceinline__ T sell_row_dot(const int64_t *__restrict__ off,
   const int w = (int)((off[s + 1] - o) >> 5);
   const T *vp = val + o + lane;
   const int32_t *cp = col + o + lane;
-  T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  T acc = 0;
   int j = 0;
   for (; j + 3 < w; j += 4) {
     const int32_t c0 = __ldcs(cp + 32 * j), c1 = __ldcs(cp + 32 * (j + 1));
     const int32_t c2 = __ldcs(cp + 32 * (j + 2)), c3 = __ldcs(cp + 32 * (j + 3));
     const T v0 = __ldcs(vp + 32 * j), v1 = __ldcs(vp + 32 * (j + 1));
     const T v2 = __ldcs(vp + 32 * (j + 2)), v3 = __ldcs(vp + 32 * (j + 3));
-    s0 += v0 * __ldg(x + c0);
-    s1 += v1 * __ldg(x + c1);
-    s2 += v2 * __ldg(x + c2);
-    s3 += v3 * __ldg(x + c3);
+    const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+    acc += v0 * x0;
+    acc += v1 * x1;
+    acc += v2 * x2;
+    acc += v3 * x3;
   }
-  for (; j < w; ++j) s0 += __ldcs(vp + 32 * j) * __ldg(x + __ldcs(cp + 32 * j));
-  return (s0 + s1) + (s2 + s3);
+  for (; j < w; ++j) acc += __ldcs(vp + 32 * j) * __ldg(x + __ldcs(cp + 32 * j));
+  return acc;
 }
 
 // Last-block-done pattern: after each block has stored its partials, the

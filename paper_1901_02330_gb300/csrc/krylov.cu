@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_init(int64_t n, const double
     bb += (double)bt * (double)bt;
   }
   block_partial(bb, slot(part, P_BB));
+  block_partial(bb, slot(part, P_RR));   // ||r_0||^2 for the first convergence test
   if (last_block(ctr)) {
     const double t = sum_partials_cg(slot(part, P_BB), gridDim.x);
     if (threadIdx.x == 0) {
@@ -105,12 +106,13 @@ __global__ void __launch_bounds__(256) k_cg_spmv(int64_t rows, int64_t nslices, 
                                                  const int32_t *__restrict__ col,
                                                  const T *__restrict__ val, const T *__restrict__ u,
                                                  const T *__restrict__ r, T *w, double *part,
-                                                 double *sc, unsigned int *ctr, double tol2, int it) {
+                                                 double *sc, unsigned int *ctr, double tol2, int it,
+                                                 int nb_rr) {
   if (block_done(sc)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  T gam = 0, del = 0, rr = 0;
+  T gam = 0, del = 0;
   const int64_t tasks = nslices * nbatch;
   for (int64_t tk = warp; tk < tasks; tk += nwarps) {
     const int64_t bb = tk / nslices, s = tk - bb * nslices;
@@ -123,16 +125,14 @@ __global__ void __launch_bounds__(256) k_cg_spmv(int64_t rows, int64_t nslices, 
       const T ui = u[gi], ri = r[gi];
       gam += ri * ui;
       del += t * ui;
-      rr += ri * ri;
     }
   }
   block_partial((double)gam, slot(part, P_RZ0));
   block_partial((double)del, slot(part, P_RZ1));
-  block_partial((double)rr, slot(part, P_RR));
   if (!last_block(ctr)) return;
   const double G = sum_partials_cg(slot(part, P_RZ0), gridDim.x);
   const double D = sum_partials_cg(slot(part, P_RZ1), gridDim.x);
-  const double R = sum_partials_cg(slot(part, P_RR), gridDim.x);
+  const double R = sum_partials_cg(slot(part, P_RR), nb_rr);   // from the update (or init) kernel
   if (threadIdx.x != 0) return;
   if (!isfinite(R) || !isfinite(G) || !isfinite(D)) {
     sc[S_PCG_BAD] = 2.0;
@@ -166,9 +166,10 @@ template <class T>
 __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, T *x, T *r, T *u, T *p, T *s,
                                                            const T *__restrict__ w,
                                                            const T *__restrict__ dinv,
-                                                           const double *sc) {
+                                                           const double *sc, double *part) {
   if (block_done(sc)) return;
   const T alpha = (T)sc[CG_ALPHA], beta = (T)sc[CG_BETA];
+  T rr = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const T pi = u[i] + beta * p[i];
@@ -179,7 +180,9 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, T *x, T *r
     s[i] = si;
     r[i] = ri;
     u[i] = dinv[i] * ri;
+    rr += ri * ri;
   }
+  block_partial((double)rr, slot(part, P_RR));
 }
 
 __global__ void k_f32_to_f64(int64_t n, const float *__restrict__ a, double *b) {
@@ -212,7 +215,7 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
     if (ntimed < vem_handle::kTimed) cudaEventRecord(h->tev[2 * ntimed], s);
     count_launch();
     k_cg_spmv<T><<<nbs, 256, 0, s>>>(op.S.rows, op.S.nslices, op.nbatch, op.S.stored, op.S.off, op.S.col,
-                                     sval, u, r, w, h->part, sc, h->ctr + 1, tol2, it);
+                                     sval, u, r, w, h->part, sc, h->ctr + 1, tol2, it, nb);
     if (ntimed < vem_handle::kTimed) cudaEventRecord(h->tev[2 * ntimed + 1], s);
     ++ntimed;
   };
@@ -236,7 +239,7 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
     const int end = it + chunk < maxit ? it + chunk : maxit;
     for (; it < end; ++it) {
       count_launch();
-      k_cg_update<T><<<nb, kRedThreads, 0, s>>>(n, x, r, u, p, sv, w, dinv, sc);
+      k_cg_update<T><<<nb, kRedThreads, 0, s>>>(n, x, r, u, p, sv, w, dinv, sc, h->part);
       spmv_it(it + 1);
     }
     VEM_CUDA(h, cudaGetLastError());
