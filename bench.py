@@ -166,6 +166,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, device: str = "cuda") -> float:
+    """Largest value over the ranks of the default process group (the
+    slowest rank's time defines a multi-GPU step); the value itself when
+    torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def spmv_bytes(nnz, rows):
     """Algorithmic bytes of one SpMV with FP64 values and int32 column ids:
     12 per nonzero, x read once and y written once (16 per row); padding of
@@ -263,11 +276,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     launches = vs.launch_count() - l0
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / a.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / a.steps)
     value = n * world / (ms * 1e-3)
     st = stats[-1]
 

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_init(int64_t n, const double
 // w = S u, partials of (r,u), (w,u), (r,r); the last block decides.  The
 // per-thread sums are in T, the block partials and scalars in FP64.
 template <class T>
-__global__ void __launch_bounds__(256) k_cg_spmv(int64_t rows, int64_t nslices, int nbatch, int64_t stored,
+__global__ void __launch_bounds__(256, 5) k_cg_spmv(int64_t rows, int64_t nslices, int nbatch, int64_t stored,
                                                  const int64_t *__restrict__ off,
                                                  const int32_t *__restrict__ col,
                                                  const T *__restrict__ val, const T *__restrict__ u,
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_cg_spmv(int64_t rows, int64_t nslices, 
   T gam = 0, del = 0;
   const int64_t tasks = nslices * nbatch;
   for (int64_t tk = warp; tk < tasks; tk += nwarps) {
-    const int64_t bb = tk / nslices, s = tk - bb * nslices;
+    const int64_t bb = nbatch == 1 ? 0 : tk / nslices, s = tk - bb * nslices;
     const T *ub = u + bb * rows;
     const T t = sell_row_dot<T>(off, col, val + bb * stored, ub, s, lane);
     const int64_t i = 32 * s + lane;
