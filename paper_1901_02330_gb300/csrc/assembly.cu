@@ -371,30 +371,35 @@ static vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int6
   return VEM_OK;
 }
 
-// Sum of true row lengths by one block (one scalar goes to the host).
-__global__ void k_len_sum(int64_t n, const int32_t *__restrict__ len, int64_t *out) {
+// Sum of true row lengths: one partial per block, added with an integer
+// atomic (exact, so the order does not matter).
+__global__ void k_len_sum(int64_t n, const int32_t *__restrict__ len, unsigned long long *out) {
   __shared__ int64_t ws[32];
   int64_t s = 0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += len[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += len[i];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     int64_t t = 0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += ws[i];
-    *out = t;
+    atomicAdd(out, (unsigned long long)t);
   }
 }
 
 static vem_status sell_nnz(vem_handle *h, SellMat &M) {
-  int64_t *cnt = h->slice_buf;   // reuse: the per-slice sizes are no longer needed
+  // reuse: the per-slice sizes are no longer needed
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(h->slice_buf);
+  VEM_CUDA(h, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), h->stream));
+  const int64_t n = M.nslices * 32;
   count_launch();
-  k_len_sum<<<1, 1024, 0, h->stream>>>(M.nslices * 32, M.len, cnt);
+  k_len_sum<<<grid_for(n, 256), 256, 0, h->stream>>>(n, M.len, cnt);
   VEM_CUDA(h, cudaGetLastError());
-  int64_t t = 0;
-  VEM_CUDA(h, cudaMemcpyAsync(&t, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+  unsigned long long t = 0;
+  VEM_CUDA(h, cudaMemcpyAsync(&t, cnt, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
   VEM_CUDA(h, cudaStreamSynchronize(h->stream));
-  M.nnz = t;
+  M.nnz = (int64_t)t;
   return VEM_OK;
 }
 

@@ -100,12 +100,15 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_init(int64_t n, const double
 
 // w = S u, partials of (r,u), (w,u), (r,r); the last block decides.  The
 // per-thread sums are in T, the block partials and scalars in FP64.
+#ifndef VEM_CG_MINB
+#define VEM_CG_MINB 4
+#endif
 template <class T>
-__global__ void __launch_bounds__(256, 5) k_cg_spmv(int64_t rows, int64_t nslices, int nbatch, int64_t stored,
+__global__ void __launch_bounds__(256, VEM_CG_MINB) k_cg_spmv(int64_t rows, int64_t nslices, int nbatch, int64_t stored,
                                                  const int64_t *__restrict__ off,
                                                  const int32_t *__restrict__ col,
                                                  const T *__restrict__ val, const T *__restrict__ u,
-                                                 const T *__restrict__ r, T *w, double *part,
+                                                 const T *__restrict__ r, T *__restrict__ w, double *part,
                                                  double *sc, unsigned int *ctr, double tol2, int it,
                                                  int nb_rr) {
   if (block_done(sc)) return;
@@ -117,12 +120,17 @@ __global__ void __launch_bounds__(256, 5) k_cg_spmv(int64_t rows, int64_t nslice
   for (int64_t tk = warp; tk < tasks; tk += nwarps) {
     const int64_t bb = nbatch == 1 ? 0 : tk / nslices, s = tk - bb * nslices;
     const T *ub = u + bb * rows;
-    const T t = sell_row_dot<T>(off, col, val + bb * stored, ub, s, lane);
     const int64_t i = 32 * s + lane;
+    const int64_t gi = bb * rows + i;
+    // own-row operands first, so their loads overlap the row's gathers
+    T ui = 0, ri = 0;
     if (i < rows) {
-      const int64_t gi = bb * rows + i;
+      ui = __ldg(u + gi);
+      ri = __ldg(r + gi);
+    }
+    const T t = sell_row_dot<T, VEM_CG_KB, VEM_CG_PRED>(off, col, val + bb * stored, ub, s, lane);
+    if (i < rows) {
       w[gi] = t;
-      const T ui = u[gi], ri = r[gi];
       gam += ri * ui;
       del += t * ui;
     }
