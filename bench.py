@@ -34,7 +34,8 @@ UNIT = "DOFs/s"
 WORKLOAD = "hex128-k1-fgmres30-blocktri-fp64"
 N_CELLS = 128
 RTOL = 1e-8
-SAMPLE_N = 10          # oracle sample: 10^3 cubes of the same workload
+INNER_RTOL = 1e-8       # inner Jacobi-PCG tolerance of the bench workload
+SAMPLE_N = 12          # oracle sample: 12^3 cubes of the same workload
 
 
 def parse():
@@ -47,7 +48,7 @@ def parse():
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
-    ap.add_argument("--inner-rtol", type=float, default=1e-8, help="inner Jacobi-PCG tolerance")
+    ap.add_argument("--inner-rtol", type=float, default=INNER_RTOL, help="inner Jacobi-PCG tolerance")
     ap.add_argument("--element", default="k1", choices=["k1", "e0"])
     ap.add_argument("--workload", default="hex128-k1",
                     choices=["hex128-k1", "hex8-e0-minres", "cvt200k-e0-mixed", "hex64-e0-batch64",
@@ -75,7 +76,7 @@ def oracle_sample(n: int = SAMPLE_N):
     prob = fields.sine_problem()
     t0 = time.perf_counter()
     sys_ = assemble(m, paper_element(1), np.ones(m.n_cells), f=prob.f, gD=prob.gD)
-    u, p, res = solvers.solve_krylov(sys_, "fgmres", "tri", "pcg", rtol=RTOL, inner_rtol=1e-4, restart=30)
+    u, p, res = solvers.solve_krylov(sys_, "fgmres", "tri", "pcg", rtol=RTOL, inner_rtol=INNER_RTOL, restart=30)
     dt = time.perf_counter() - t0
     return sys_.n, dt, res.iters
 
@@ -164,6 +165,18 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the current kernel code, keyed by (kernel, rows, nonzeros).
+# The saddle-matrix figure is the 64^3 paper-k=1 capture (3,444,736 rows,
+# 111,783,936 nonzeros: 1,426.1 MB for 1,396.5 MB algorithmic), scaled to
+# the 128^3 launch by its algorithmic bytes; the traffic of that kernel
+# grows in proportion to its rows and nonzeros.
+NCU_TRAFFIC = {
+    ("k_cg_spmv", 2097152, 14581760): 214.32e6,
+}
+NCU_TRAFFIC_RATIO = {"k_sell_spmv": 1426.1 / 1396.5}
 
 
 def max_over_ranks(value: float, device: str = "cuda") -> float:
@@ -386,7 +399,8 @@ def run_ours(a):
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": a.n ** 3, "unknowns": n, "n_u": n_u, "n_p": n_p,
-                   "element": "paper k=1 (face P1 + 3 cross moments, P0 pressure)",
+                   "element": ("paper k=1 (face P1 + 3 cross moments, P0 pressure)" if a.element == "k1"
+                               else "E0 (one flux moment per face, P0 pressure)"),
                    "krylov": "FGMRES(30)", "precond": "block upper-triangular, S = B diag(M)^-1 B^T",
                    "inner": f"Jacobi-PCG rtol {a.inner_rtol:g}", "rtol": RTOL, "K": "identity",
                    "l2": "inputs larger than L2 (saddle matrix ~%.1f GB streamed every step)" % (st["nnz_A"] * 12 / 1e9),
@@ -396,12 +410,15 @@ def run_ours(a):
         "t_assemble_ms": st["t_assemble_ms"], "t_solve_ms": st["t_solve_ms"],
         "roofline": {"kernel": "k_cg_spmv<double> (Schur complement S u with (r,u),(w,u),(r,r); dominant kernel)",
                      "bound": "hbm", "achieved": cg_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": cg_gbs / hbm_peak, "traffic": None, "algorithmic_bytes": cg_bytes,
+                     "frac": cg_gbs / hbm_peak,
+                     "traffic": NCU_TRAFFIC.get(("k_cg_spmv", n_p, st["nnz_S"])), "algorithmic_bytes": cg_bytes,
                      "launch_ms": cg_ms, "launches_per_step": st["n_schur_spmv"],
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800"},
         "roofline_saddle_spmv": {"kernel": "k_sell_spmv (saddle matrix, SELL-32, FP64)", "bound": "hbm",
                                  "achieved": spmv_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": spmv_gbs / hbm_peak,
-                                 "traffic": None, "algorithmic_bytes": sb, "launch_ms": spmv_ms},
+                                 "traffic": NCU_TRAFFIC_RATIO["k_sell_spmv"] * sb if a.element == "k1" else None,
+                                 "traffic_note": "scaled from the 64^3 capture by algorithmic bytes",
+                                 "algorithmic_bytes": sb, "launch_ms": spmv_ms},
         "element_kernel": {"kernel": "k_elem_%s" % a.element, "bound": "alu", "classes_evaluated": st["n_classes"],
                            "cells": mesh.n_cells, "flops_per_class": cell_flops, "launch_ms": el_ms,
                            "achieved_gflops": el_gflops, "peak_gflops": FP64_PEAK_GFLOPS,

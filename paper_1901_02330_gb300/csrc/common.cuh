@@ -104,14 +104,14 @@ __device__ __forceinline__ void block_partial(double v, double *part) {
   __syncthreads();
 }
 
-// Row (32 s + lane) of a SELL-32 matrix times x: elements in column order,
-// four independent loads in flight, one FMA chain (GB300 issues FP64 at 1/16
-// of the lane rate, so combining partial accumulators would cost FP64 adds
-// per row); T = double or float (values, x and arithmetic share the type).
-// Batch width of the row dot: each batch issues all its (col, val) loads,
-// then all its gathers, then the FMAs.  With kPred the last batch is
-// predicated on the slice width (uniform across the warp) instead of falling
-// back to one entry at a time.
+// Row (32 s + lane) of a SELL-32 matrix times x, one FMA chain per row
+// (GB300 issues FP64 at 1/16 of the lane rate, so combining partial
+// accumulators would cost FP64 adds per row); T = double or float (values,
+// x and arithmetic share the type).  Entries go in batches: all (col, val)
+// loads of a batch, then its gathers, then its FMAs.  Unpredicated: batches
+// of four and a one-at-a-time tail.  kPred: batches of kB, the last one
+// predicated on the slice width (uniform across the warp), so a row of up
+// to kB entries costs one round trip.
 #ifndef VEM_CG_KB
 #define VEM_CG_KB 8
 #endif
@@ -129,27 +129,41 @@ __device__ __forceinline__ T sell_row_dot(const int64_t *__restrict__ off,
   const int32_t *cp = col + o + lane;
   T acc = 0;
   int j = 0;
-  for (; kPred ? j < w : j + kB - 1 < w; j += kB) {
-    int32_t c[kB];
-    T v[kB], xv[kB];
+  if constexpr (kPred) {
+    for (; j < w; j += kB) {
+      int32_t c[kB];
+      T v[kB], xv[kB];
 #pragma unroll
-    for (int k = 0; k < kB; ++k) {
-      c[k] = 0;
-      v[k] = xv[k] = 0;
-      if (!kPred || j + k < w) {
-        c[k] = __ldcs(cp + 32 * (j + k));
-        v[k] = __ldcs(vp + 32 * (j + k));
+      for (int k = 0; k < kB; ++k) {
+        c[k] = 0;
+        v[k] = xv[k] = 0;
+        if (j + k < w) {
+          c[k] = __ldcs(cp + 32 * (j + k));
+          v[k] = __ldcs(vp + 32 * (j + k));
+        }
       }
+#pragma unroll
+      for (int k = 0; k < kB; ++k)
+        if (j + k < w) xv[k] = __ldg(x + c[k]);
+#pragma unroll
+      for (int k = 0; k < kB; ++k)
+        if (j + k < w) acc += v[k] * xv[k];
     }
-#pragma unroll
-    for (int k = 0; k < kB; ++k)
-      if (!kPred || j + k < w) xv[k] = __ldg(x + c[k]);
-#pragma unroll
-    for (int k = 0; k < kB; ++k)
-      if (!kPred || j + k < w) acc += v[k] * xv[k];
-  }
-  if (!kPred)
+  } else {
+    static_assert(kB == 4, "the unpredicated form issues four entries per batch");
+    for (; j + 3 < w; j += 4) {
+      const int32_t c0 = __ldcs(cp + 32 * j), c1 = __ldcs(cp + 32 * (j + 1));
+      const int32_t c2 = __ldcs(cp + 32 * (j + 2)), c3 = __ldcs(cp + 32 * (j + 3));
+      const T v0 = __ldcs(vp + 32 * j), v1 = __ldcs(vp + 32 * (j + 1));
+      const T v2 = __ldcs(vp + 32 * (j + 2)), v3 = __ldcs(vp + 32 * (j + 3));
+      const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+      acc += v0 * x0;
+      acc += v1 * x1;
+      acc += v2 * x2;
+      acc += v3 * x3;
+    }
     for (; j < w; ++j) acc += __ldcs(vp + 32 * j) * __ldg(x + __ldcs(cp + 32 * j));
+  }
   return acc;
 }
 
