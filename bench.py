@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--inner-rtol", type=float, default=INNER_RTOL, help="inner Jacobi-PCG tolerance")
     ap.add_argument("--element", default="k1", choices=["k1", "e0"])
+    ap.add_argument("--inner", default="pcg", choices=["pcg", "amg"],
+                    help="inner Schur solver: Jacobi-PCG or AMG-preconditioned CG")
     ap.add_argument("--workload", default="hex128-k1",
                     choices=["hex128-k1", "hex8-e0-minres", "cvt200k-e0-mixed", "hex64-e0-batch64",
                              "cvt100k-adjoint"],
@@ -112,7 +114,7 @@ def run_reference(a):
             "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": f"hex{SAMPLE_N}^3 per step (oracle)"},
+            "config": {"workload": workload_name(a), "sample": f"hex{SAMPLE_N}^3 per step (oracle)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"hex{SAMPLE_N}^3 k=1, {n} unknowns per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -177,6 +179,11 @@ NCU_TRAFFIC = {
     ("k_cg_spmv", 2097152, 14581760): 214.32e6,
 }
 NCU_TRAFFIC_RATIO = {"k_sell_spmv": 1426.1 / 1396.5}
+
+
+def workload_name(a) -> str:
+    name = f"hex{a.n}-{a.element}-fgmres30-blocktri-" + ("amg-" if a.inner == "amg" else "") + "fp64"
+    return name
 
 
 def max_over_ranks(value: float, device: str = "cuda") -> float:
@@ -248,9 +255,10 @@ def run_ours(a):
     mesh = hex_mesh(a.n)
     prob = fields.sine_problem()
     elem = vs.VEM_ELEMENT_K1 if a.element == "k1" else vs.VEM_ELEMENT_E0
+    inner = vs.VEM_INNER_AMG if a.inner == "amg" else vs.VEM_INNER_PCG
     opts = dict(element=elem, krylov=vs.VEM_KRYLOV_FGMRES, restart=30,
                 precond=vs.VEM_PREC_BLOCK_TRI, rtol=RTOL, inner_rtol=a.inner_rtol, inner_maxit=2000,
-                maxit=1000)
+                maxit=1000, inner=inner)
 
     # ---------------- device-resident path (value) ----------------
     s = vs.Solver(mesh, stream=sid, device_io=1, **opts)
@@ -328,6 +336,7 @@ def run_ours(a):
     mixed = None
     if not a.no_mixed:
         sm = vs.Solver(mesh, stream=sid, device_io=1, **dict(opts, precision=vs.VEM_PRECISION_MIXED,
+                                                                inner=vs.VEM_INNER_PCG,
                                                                 inner_rtol=max(a.inner_rtol, 1e-5)))
         sm.set_coefficient(np.ones(mesh.n_cells))
         sm.set_data(prob.f, prob.gD)
@@ -398,15 +407,17 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": a.n ** 3, "unknowns": n, "n_u": n_u, "n_p": n_p,
+        "config": {"workload": workload_name(a), "cells": a.n ** 3, "unknowns": n, "n_u": n_u, "n_p": n_p,
                    "element": ("paper k=1 (face P1 + 3 cross moments, P0 pressure)" if a.element == "k1"
                                else "E0 (one flux moment per face, P0 pressure)"),
                    "krylov": "FGMRES(30)", "precond": "block upper-triangular, S = B diag(M)^-1 B^T",
-                   "inner": f"Jacobi-PCG rtol {a.inner_rtol:g}", "rtol": RTOL, "K": "identity",
+                   "inner": (f"AMG-PCG (smoothed aggregation, V(1,1)) rtol {a.inner_rtol:g}" if a.inner == "amg"
+                             else f"Jacobi-PCG rtol {a.inner_rtol:g}"), "rtol": RTOL, "K": "identity",
                    "l2": "inputs larger than L2 (saddle matrix ~%.1f GB streamed every step)" % (st["nnz_A"] * 12 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "iterations": st["iterations"], "inner_iterations": st["inner_iterations"], "relres": st["relres"],
         "element_classes": st["n_classes"],
+        "amg_levels": st["amg_levels"], "t_amg_setup_ms": st["t_amg_setup_ms"],
         "t_assemble_ms": st["t_assemble_ms"], "t_solve_ms": st["t_solve_ms"],
         "roofline": {"kernel": "k_cg_spmv<double> (Schur complement S u with (r,u),(w,u),(r,r); dominant kernel)",
                      "bound": "hbm", "achieved": cg_gbs, "peak": hbm_peak, "unit": "GB/s",

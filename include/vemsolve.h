@@ -87,7 +87,12 @@ typedef struct {
 enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1 };
 enum { VEM_KRYLOV_MINRES = 0, VEM_KRYLOV_FGMRES = 1 };
 enum { VEM_PREC_BLOCK_DIAG = 0, VEM_PREC_BLOCK_TRI = 1 };
-enum { VEM_INNER_PCG = 0 };
+/* Inner solver for S: Jacobi-preconditioned CG, or CG preconditioned by one
+ * V(1,1) cycle of a smoothed-aggregation AMG built from S (Vanek, Mandel &
+ * Brezina 1996; aggregates from a distance-2 maximal independent set, Bell,
+ * Dalton & Olson 2012).  The AMG is FP64 and single-system: with
+ * VEM_PRECISION_MIXED or vem_solve_batched it gives VEM_ERR_UNSUPPORTED. */
+enum { VEM_INNER_PCG = 0, VEM_INNER_AMG = 1 };
 enum { VEM_PRECISION_FP64 = 0, VEM_PRECISION_MIXED = 1 };
 
 typedef struct {
@@ -128,6 +133,9 @@ typedef struct {
                              /* element kernel (= n_cells without reuse)    */
   double t_schur_spmv_ms;    /* of t_solve_ms: the Schur-complement SpMV    */
   int64_t n_schur_spmv;      /* its launches (each timed with CUDA events)  */
+  double t_amg_setup_ms;     /* of t_solve_ms: building the AMG hierarchy   */
+                             /* (0 when it was reused or not used)          */
+  int32_t amg_levels;        /* levels of the AMG hierarchy (0: none)       */
 } vem_stats;
 
 /* Fill *opt with the defaults: E0, FGMRES(30), block-diagonal, Jacobi-PCG
@@ -274,6 +282,25 @@ vem_status vem_apply_device(vem_handle *h, const double *x_dev, double *y_dev);
 vem_status vem_residual_norm_noalloc(int64_t rows, const int64_t *row_ptr, const int32_t *col,
                                      const double *val, const double *x, const double *b,
                                      double *out, void *cuda_stream);
+
+/* ---- AMG inspection (VEM_INNER_AMG) ----
+ * vem_amg_setup builds the hierarchy from the assembled S (vem_solve does
+ * this on demand after every vem_assemble).  Level 0 is S itself.
+ * vem_amg_levels: *nlev levels (at most 12); rows[l], nnz[l] of each
+ * level's operator and nnz_p[l] of its prolongator (0 on the coarsest);
+ * arrays of at least 12 entries, any may be NULL.
+ * vem_amg_get_level: host CSR of level l's operator (row_ptr[rows + 1],
+ * col[nnz], val[nnz]), its aggregate of every row (agg[rows], -1 for rows
+ * outside the coarse space) and its prolongator P (rows x rows of level
+ * l + 1; prow_ptr[rows + 1], pcol/pval[nnz_p]); any pointer may be NULL,
+ * agg and P are left untouched on the coarsest level.
+ * vem_amg_vcycle_device: x = V(b), one cycle, device vectors of n_p.
+ * All return VEM_ERR_BAD_INPUT before vem_amg_setup / after vem_assemble. */
+vem_status vem_amg_setup(vem_handle *h);
+vem_status vem_amg_levels(vem_handle *h, int32_t *nlev, int64_t *rows, int64_t *nnz, int64_t *nnz_p);
+vem_status vem_amg_get_level(vem_handle *h, int32_t level, int64_t *row_ptr, int32_t *col, double *val,
+                             int32_t *agg, int64_t *prow_ptr, int32_t *pcol, double *pval);
+vem_status vem_amg_vcycle_device(vem_handle *h, const double *b_dev, double *x_dev);
 
 /* Number of CUDA kernel launches the library has issued in this process
  * (all handles), for accounting the work of a timed region. */

@@ -62,6 +62,9 @@ vem_status check_device_errors(vem_handle *h, const char *what) {
   if (e & DEVERR_NONCONVEX) return fail(h, VEM_ERR_DEGENERATE_MESH, "%s: non-convex cell", what);
   if (e & DEVERR_SINGULAR_LOCAL) return fail(h, VEM_ERR_DEGENERATE_MESH, "%s: singular local Gram matrix", what);
   if (e & DEVERR_NONFINITE) return fail(h, VEM_ERR_NONFINITE, "%s: NaN or Inf in data", what);
+  if (e & DEVERR_AMG_DIAG) return fail(h, VEM_ERR_BREAKDOWN, "%s: non-positive diagonal or pivot", what);
+  if (e & DEVERR_AMG_ROW)
+    return fail(h, VEM_ERR_UNSUPPORTED, "%s: a row of an AMG product has too many distinct columns", what);
   return fail(h, VEM_ERR_CUDA, "%s: device error flags %d", what, e);
 }
 
@@ -74,7 +77,10 @@ static vem_status check_options(vem_handle *h, const vem_options *o) {
     return fail(h, VEM_ERR_BAD_INPUT, "unknown preconditioner %d", o->precond);
   if (o->krylov == VEM_KRYLOV_MINRES && o->precond != VEM_PREC_BLOCK_DIAG)
     return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs the SPD block-diagonal preconditioner");
-  if (o->inner != VEM_INNER_PCG) return fail(h, VEM_ERR_UNSUPPORTED, "inner solver %d", o->inner);
+  if (o->inner != VEM_INNER_PCG && o->inner != VEM_INNER_AMG)
+    return fail(h, VEM_ERR_BAD_INPUT, "unknown inner solver %d", o->inner);
+  if (o->inner == VEM_INNER_AMG && o->precision != VEM_PRECISION_FP64)
+    return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver runs in FP64 only");
   if (o->precision != VEM_PRECISION_FP64 && o->precision != VEM_PRECISION_MIXED)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown precision %d", o->precision);
   if (o->precision == VEM_PRECISION_MIXED && o->krylov != VEM_KRYLOV_FGMRES)
@@ -209,6 +215,7 @@ static vem_status ensure_rhs(vem_handle *h) {
 }
 
 static vem_status assemble_impl(vem_handle *h) {
+  amg_invalidate(h);
   VEM_CUDA(h, cudaEventRecord(h->ev0, h->stream));
   VEM_TRY(classify_cells(h));
   VEM_CUDA(h, cudaEventRecord(h->ev2, h->stream));
@@ -498,6 +505,7 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     count_launch(); k_import_x<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n, x0d, x);
     h->t_schur_spmv_ms = 0.0;
     h->n_schur_spmv = 0;
+    const bool had_amg = amg_valid(h);
     cudaEventRecord(h->ev0, s);
     r = krylov_solve(h, single_op(h), h->rhs, x, &st);
     cudaEventRecord(h->ev1, s);
@@ -507,6 +515,8 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     st.t_solve_ms = ms;
     st.t_schur_spmv_ms = h->t_schur_spmv_ms;
     st.n_schur_spmv = h->n_schur_spmv;
+    st.t_amg_setup_ms = (!had_amg && amg_valid(h)) ? amg_setup_ms(h) : 0.0;
+    st.amg_levels = amg_levels(h);
     if (tmp) dfree(h, tmp);
     if (r != VEM_OK && r != VEM_ERR_NOT_CONVERGED) break;
     h->have_solution = true;
@@ -590,6 +600,8 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   if (!h) return VEM_ERR_BAD_INPUT;
   if (nbatch < 1 || nbatch > 65535) return fail(h, VEM_ERR_BAD_INPUT, "nbatch %lld", (long long)nbatch);
   if (!K || !u_out || !p_out) return fail(h, VEM_ERR_BAD_INPUT, "K / u_out / p_out: NULL");
+  if (h->opt.inner == VEM_INNER_AMG)
+    return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver is single-system (no batched solves)");
   cudaStream_t s = h->stream;
   const int nb = (int)nbatch;
   const bool dev = h->opt.device_io != 0;
@@ -817,9 +829,39 @@ vem_status vem_launch_count(int64_t *n) {
 
 const char *vem_last_error(const vem_handle *h) { return h ? h->last_error.c_str() : "NULL handle"; }
 
+vem_status vem_amg_setup(vem_handle *h) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (!h->assembled) VEM_TRY(assemble_impl(h));
+  return amg_setup(h, h->S);
+}
+
+vem_status vem_amg_levels(vem_handle *h, int32_t *nlev, int64_t *rows, int64_t *nnz, int64_t *nnz_p) {
+  if (!h || !nlev) return VEM_ERR_BAD_INPUT;
+  int nl = 0;
+  VEM_TRY(amg_level_info(h, &nl, rows, nnz, nnz_p));
+  *nlev = nl;
+  return VEM_OK;
+}
+
+vem_status vem_amg_get_level(vem_handle *h, int32_t level, int64_t *row_ptr, int32_t *col, double *val,
+                             int32_t *agg, int64_t *prow_ptr, int32_t *pcol, double *pval) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  return amg_level_copy(h, level, row_ptr, col, val, agg, prow_ptr, pcol, pval);
+}
+
+vem_status vem_amg_vcycle_device(vem_handle *h, const double *b_dev, double *x_dev) {
+  if (!h || !b_dev || !x_dev) return VEM_ERR_BAD_INPUT;
+  if (!amg_valid(h)) return fail(h, VEM_ERR_BAD_INPUT, "no AMG hierarchy: call vem_amg_setup first");
+  amg_vcycle(h, b_dev, x_dev, nullptr);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return VEM_OK;
+}
+
 void vem_destroy(vem_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  vem::amg_free(h);
   for (void *p : h->allocations) cudaFree(p);
   h->allocations.clear();
   if (h->h_err) cudaFreeHost(h->h_err);

@@ -317,8 +317,6 @@ __global__ void k_slice_sizes(int64_t rows, int64_t nslices, const int64_t *__re
   }
 }
 
-static vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *out,
-                              int64_t *total);
 
 // Allocate / lay out a SELL matrix from device row counts cnt[rows].
 static vem_status sell_layout(vem_handle *h, SellMat &M, int64_t rows, const int64_t *cnt) {
@@ -357,8 +355,7 @@ static vem_status sell_layout(vem_handle *h, SellMat &M, int64_t rows, const int
   return VEM_OK;
 }
 
-static vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *out,
-                              int64_t *total) {
+vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *out, int64_t *total) {
   cudaStream_t s = h->stream;
   if (!h->scan_buf) VEM_TRY(dalloc_n(h, &h->scan_buf, kScanBlocks));
   int64_t *bsum = h->scan_buf;

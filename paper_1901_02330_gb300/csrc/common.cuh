@@ -19,6 +19,8 @@ enum : int {
   DEVERR_ADJACENCY = 8,
   DEVERR_NONFINITE = 16,
   DEVERR_SINGULAR_LOCAL = 32,
+  DEVERR_AMG_DIAG = 64,        // AMG: non-positive diagonal or pivot
+  DEVERR_AMG_ROW = 128,        // AMG: a product row exceeds its column list
 };
 
 struct Status {

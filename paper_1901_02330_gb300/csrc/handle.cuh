@@ -9,6 +9,10 @@
 
 #include "common.cuh"
 
+namespace vem {
+struct AmgState;   // smoothed-aggregation hierarchy of S (amg.cu)
+}
+
 // The operator a Krylov solve works on: the saddle matrix A, the Schur
 // approximation S and the preconditioner's diagonals, with sizes.  nbatch > 1
 // stacks nbatch systems that share the mesh as one block-diagonal system with
@@ -117,6 +121,9 @@ struct vem_handle {
   VemOp bop;                                     // stacked operator (values per batch)
   double *b_nu = nullptr, *b_rhs = nullptr, *b_x = nullptr, *b_fqp = nullptr, *b_gqp = nullptr;
   int b_cap = 0;                                 // batches the buffers hold
+
+  // ---- AMG for the inner Schur solve ----
+  vem::AmgState *amg = nullptr;
 };
 
 namespace vem {
@@ -170,6 +177,25 @@ vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, Ve
 vem_status classify_cells(vem_handle *h);
 // Adjoint contraction (adjoint.cu): g_c = lam_{u,c}^T M_c u_c per cell.
 vem_status adjoint_contract(vem_handle *h, const double *lam, const double *x, double *g);
+
+// Exclusive scan of cnt[n] into out[n + 1] (out[0] = 0); *total = out[n]
+// (synchronises the stream).
+vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *out, int64_t *total);
+
+// Smoothed-aggregation AMG for S (amg.cu)
+vem_status amg_setup(vem_handle *h, const SellMat &S);
+bool amg_valid(const vem_handle *h);
+void amg_invalidate(vem_handle *h);
+double amg_setup_ms(const vem_handle *h);
+int amg_levels(const vem_handle *h);
+void amg_free(vem_handle *h);
+// x = V(b) on the finest level (device vectors of n_p); sc: the PCG scalars
+// whose first entry, when non-zero, turns the launches into no-ops (NULL: run)
+void amg_vcycle(vem_handle *h, const double *b, double *x, const double *sc);
+vem_status amg_level_info(vem_handle *h, int *nlev, int64_t *rows, int64_t *nnz, int64_t *nnz_p);
+vem_status amg_level_copy(vem_handle *h, int l, int64_t *rp, int32_t *col, double *val, int32_t *agg,
+                          int64_t *prp, int32_t *pcol, double *pval);
+double amg_omega(const vem_handle *h, int l);
 
 }  // namespace vem
 

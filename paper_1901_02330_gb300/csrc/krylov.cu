@@ -11,7 +11,8 @@
 //   MINRES: Paige & Saunders (1975), preconditioned Lanczos form.
 //   FGMRES(m): Saad (1993), right preconditioning, classical Gram-Schmidt
 //   applied twice (CGS2) for the Arnoldi step, Givens rotations.
-//   PCG: Hestenes & Stiefel (1952) with the Jacobi preconditioner.
+//   PCG: Hestenes & Stiefel (1952) with the Jacobi preconditioner or one
+//   V-cycle of the smoothed-aggregation AMG of amg.cu.
 #include <cmath>
 #include <cstdlib>
 
@@ -169,8 +170,9 @@ __global__ void __launch_bounds__(256, VEM_CG_MINB) k_cg_spmv(int64_t rows, int6
   sc[CG_APREV] = alpha;
 }
 
-// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r
-template <class T>
+// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, and with the
+// Jacobi preconditioner u = D^-1 r (the AMG cycle computes u separately)
+template <class T, bool kJacobi = true>
 __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, T *x, T *r, T *u, T *p, T *s,
                                                            const T *__restrict__ w,
                                                            const T *__restrict__ dinv,
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, T *x, T *r
     p[i] = pi;
     s[i] = si;
     r[i] = ri;
-    u[i] = dinv[i] * ri;
+    if (kJacobi) u[i] = dinv[i] * ri;
     rr += ri * ri;
   }
   block_partial((double)rr, slot(part, P_RR));
@@ -215,8 +217,15 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   if (nbs < 1) nbs = 1;
   double *sc = h->scal;
   const double tol2 = h->opt.inner_rtol * h->opt.inner_rtol;
+  // the AMG-preconditioned form replaces u = D^-1 r by one V-cycle u = V(r)
+  bool amg = false;
+  if constexpr (sizeof(T) == sizeof(double)) amg = h->opt.inner == VEM_INNER_AMG;
   count_launch();
   k_cg_init<T><<<nb, kRedThreads, 0, s>>>(n, b, dinv, x, r, u, p, sv, h->part, sc, h->ctr);
+  auto precondition = [&]() {
+    if constexpr (sizeof(T) == sizeof(double)) amg_vcycle(h, r, u, sc);
+  };
+  if (amg) precondition();
   // every launch of the Schur SpMV is timed with a pair of events
   int ntimed = 0;
   auto spmv_it = [&](int it) {
@@ -247,7 +256,12 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
     const int end = it + chunk < maxit ? it + chunk : maxit;
     for (; it < end; ++it) {
       count_launch();
-      k_cg_update<T><<<nb, kRedThreads, 0, s>>>(n, x, r, u, p, sv, w, dinv, sc, h->part);
+      if (amg) {
+        k_cg_update<T, false><<<nb, kRedThreads, 0, s>>>(n, x, r, u, p, sv, w, dinv, sc, h->part);
+        precondition();
+      } else {
+        k_cg_update<T><<<nb, kRedThreads, 0, s>>>(n, x, r, u, p, sv, w, dinv, sc, h->part);
+      }
       spmv_it(it + 1);
     }
     VEM_CUDA(h, cudaGetLastError());
@@ -277,6 +291,7 @@ static vem_status pcg_solve(vem_handle *h, const VemOp &op, const double *b, dou
     VEM_CUDA(h, cudaGetLastError());
     return VEM_OK;
   }
+  if (h->opt.inner == VEM_INNER_AMG && !amg_valid(h)) VEM_TRY(amg_setup(h, op.S));
   return pcg_solve_t<double>(h, op, op.S.val, op.s_dinv, b, x, wk, iters);
 }
 
