@@ -33,6 +33,7 @@
 // contributions in a fixed order, so the hierarchy is bitwise reproducible.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "handle.cuh"
 
@@ -43,31 +44,41 @@ constexpr int kCoarseMax = 64;
 constexpr int kDenseMax = 512;
 constexpr int kCoarseSweeps = 4;
 constexpr double kTheta0 = 0.08;
-constexpr int kCapP = 128;     // distinct columns of a row of P
-constexpr int kCapAP = 256;    // of a row of A P
-constexpr int kCapRAP = 512;   // of a row of P^T A P
+constexpr int kCapP = 128;       // distinct columns of a row of P
+constexpr int kHashSlots = 512;  // per-warp hash table of a product row
+constexpr int kHashMax = 384;    // distinct columns of a product row
+constexpr int kSortMax = 512;    // entries of a row sorted by one warp
+constexpr int kProdWarps = 4;    // warps per block of the product kernels
+constexpr int kCapThreadRow = 64;  // distinct columns of a thread-per-row product row
+constexpr int64_t kSellMinRows = 65536;  // smaller cycle operators stay in CSR
 constexpr int kMaxRounds = 200;
 
 constexpr uint64_t kStIn = 2ull << 62, kStUnd = 1ull << 62;
 
-// A SELL matrix with the capacities of its buffers (grown, never shrunk).
+// A CSR matrix in device memory with the capacities of its buffers (grown,
+// never shrunk) and the lanes per row used to apply it.
+struct CsrBuf {
+  int64_t rows = 0, cols = 0, nnz = 0;
+  int64_t *rp = nullptr;
+  int32_t *col = nullptr;
+  double *val = nullptr;
+  size_t c_rp = 0, c_nz = 0;
+  int lanes = 4;
+};
+
+// A SELL-32 copy of a CSR matrix for the cycle, with buffer capacities.
 struct SellBuf {
   SellMat m;
   size_t c_off = 0, c_len = 0, c_st = 0;
 };
 
-// A CSR matrix in device memory with capacities.
-struct CsrBuf {
-  int64_t rows = 0, nnz = 0;
-  int64_t *rp = nullptr;
-  int32_t *col = nullptr;
-  double *val = nullptr;
-  size_t c_rp = 0, c_nz = 0;
-};
-
 struct AmgLevel {
-  SellBuf A, P, R;          // level 0's A is the handle's S (a view, not owned)
+  CsrBuf A;                 // levels >= 1 (level 0 is the handle's S in SELL-32)
+  CsrBuf P, R;              // prolongator n x nc and restriction R = P^T
+  SellBuf As, Rs;           // SELL-32 copies of A (levels >= 1) and R for the cycle
   double *dinv = nullptr;
+  double *wd = nullptr;     // omega * dinv (the Jacobi step)
+  size_t c_wd = 0;
   int32_t *agg = nullptr;
   double *vec = nullptr;    // x, x2, b, r: four vectors of n
   size_t c_dinv = 0, c_agg = 0, c_vec = 0;
@@ -81,6 +92,7 @@ struct AmgLevel {
 
 struct AmgState {
   AmgLevel lv[kMaxLevels];
+  SellMat S0;               // level 0 operator (a view of the handle's S)
   int nlev = 0;
   bool valid = false;
   double *cinv = nullptr;   // dense inverse of the coarsest level
@@ -90,12 +102,12 @@ struct AmgState {
   uint8_t *flag = nullptr;  size_t c_flag = 0;
   int32_t *nstr = nullptr;  size_t c_nstr = 0;
   uint64_t *tup = nullptr;  size_t c_tup = 0;     // tuples and t1: 2 n
-  int64_t *cnt = nullptr;   size_t c_cnt = 0;     // counts (n)
+  int64_t *cnt = nullptr;   size_t c_cnt = 0;     // counts (n + 1)
   int64_t *scn = nullptr;   size_t c_scn = 0;     // scans (n + 1)
   int32_t *agg1 = nullptr;  size_t c_agg1 = 0;
   double *dg = nullptr;     size_t c_dg = 0;      // diagonal
   unsigned long long *ctr = nullptr;              // [kMaxRounds + 4] counters / maxima
-  CsrBuf Pc, Rc, APc, Ac;
+  CsrBuf AP;
   int64_t *cur = nullptr;   size_t c_cur = 0;     // transpose cursors
   double t_setup_ms = 0.0;
 };
@@ -115,6 +127,49 @@ static vem_status grow(vem_handle *h, T *&p, size_t &cap, size_t n) {
 static AmgState *state(vem_handle *h) {
   if (!h->amg) h->amg = new AmgState();
   return h->amg;
+}
+
+// Device view of a SELL-32 (off != nullptr) or CSR matrix: entry k of row i
+// sits at position base + stride * k.
+struct DMat {
+  const int64_t *off = nullptr;
+  const int32_t *len = nullptr;
+  const int64_t *rp = nullptr;
+  const int32_t *col = nullptr;
+  const double *val = nullptr;
+  int64_t rows = 0, stored = 0;
+  __device__ __forceinline__ void row(int64_t i, int64_t &base, int &stride, int &L) const {
+    if (off) {
+      base = off[i >> 5] + (i & 31);
+      stride = 32;
+      L = len[i];
+    } else {
+      base = rp[i];
+      stride = 1;
+      L = (int)(rp[i + 1] - base);
+    }
+  }
+};
+
+static DMat dview(const SellMat &m) {
+  DMat d;
+  d.off = m.off;
+  d.len = m.len;
+  d.col = m.col;
+  d.val = m.val;
+  d.rows = m.rows;
+  d.stored = m.stored;
+  return d;
+}
+
+static DMat dview(const CsrBuf &m) {
+  DMat d;
+  d.rp = m.rp;
+  d.col = m.col;
+  d.val = m.val;
+  d.rows = m.rows;
+  d.stored = m.nnz;
+  return d;
 }
 
 // ------------------------------------------------------------ helpers -----
@@ -162,15 +217,14 @@ struct RowMap {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
 // --------------------------------------------------------- strength -------
-__global__ void k_amg_diag(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                           const int32_t *__restrict__ col, const double *__restrict__ val, double *dg,
-                           double *dinv, int *err) {
-  ROWS_LOOP(i, n) {
-    const int64_t base = off[i >> 5] + (i & 31);
-    const int L = len[i];
+__global__ void k_amg_diag(DMat A, double *dg, double *dinv, int *err) {
+  ROWS_LOOP(i, A.rows) {
+    int64_t base;
+    int st, L;
+    A.row(i, base, st, L);
     double d = 0.0;
     for (int k = 0; k < L; ++k)
-      if (col[base + 32 * k] == (int32_t)i) d = val[base + 32 * k];
+      if (A.col[base + (int64_t)st * k] == (int32_t)i) d = A.val[base + (int64_t)st * k];
     if (!(d > 0.0) || !isfinite(d)) {
       atomicOr(err, DEVERR_AMG_DIAG);
       d = 1.0;
@@ -182,21 +236,20 @@ __global__ void k_amg_diag(int64_t n, const int64_t *__restrict__ off, const int
 
 // Strong flags per stored entry, strong count per row and the two Gershgorin
 // maxima (non-negative doubles compared as their bit patterns).
-__global__ void k_amg_strength(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                               const int32_t *__restrict__ col, const double *__restrict__ val,
-                               const double *__restrict__ dg, double theta, uint8_t *flag, int32_t *nstr,
+__global__ void k_amg_strength(DMat A, const double *__restrict__ dg, double theta, uint8_t *flag, int32_t *nstr,
                                unsigned long long *mx) {
   double rho = 0.0, rhof = 0.0;
-  ROWS_LOOP(i, n) {
-    const int64_t base = off[i >> 5] + (i & 31);
-    const int L = len[i];
+  ROWS_LOOP(i, A.rows) {
+    int64_t base;
+    int stp, L;
+    A.row(i, base, stp, L);
     const double di = dg[i];
     double sa = 0.0, sf = 0.0;
     int ns = 0;
     for (int k = 0; k < L; ++k) {
-      const int64_t p = base + 32 * k;
-      const int32_t j = col[p];
-      const double a = fabs(val[p]);
+      const int64_t p = base + (int64_t)stp * k;
+      const int32_t j = A.col[p];
+      const double a = fabs(A.val[p]);
       sa += a;
       bool st = false;
       if (j != (int32_t)i) st = a >= theta * sqrt(di * dg[j]);
@@ -226,34 +279,33 @@ __global__ void k_mis_init(int64_t n, uint64_t *tup) {
   ROWS_LOOP(i, n) tup[i] = kStUnd | node_key(i);
 }
 
-__global__ void k_mis_max1(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                           const int32_t *__restrict__ col, const uint8_t *__restrict__ flag,
-                           const uint64_t *__restrict__ tup, uint64_t *t1) {
-  ROWS_LOOP(i, n) {
-    const int64_t base = off[i >> 5] + (i & 31);
-    const int L = len[i];
+__global__ void k_mis_max1(DMat A, const uint8_t *__restrict__ flag, const uint64_t *__restrict__ tup, uint64_t *t1) {
+  ROWS_LOOP(i, A.rows) {
+    int64_t base;
+    int st, L;
+    A.row(i, base, st, L);
     uint64_t m = tup[i];
     for (int k = 0; k < L; ++k) {
-      const int64_t p = base + 32 * k;
-      if (flag[p]) m = max(m, tup[col[p]]);
+      const int64_t p = base + (int64_t)st * k;
+      if (flag[p]) m = max(m, tup[A.col[p]]);
     }
     t1[i] = m;
   }
 }
 
-__global__ void k_mis_max2(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                           const int32_t *__restrict__ col, const uint8_t *__restrict__ flag,
-                           const uint64_t *__restrict__ t1, uint64_t *tup, unsigned long long *und) {
+__global__ void k_mis_max2(DMat A, const uint8_t *__restrict__ flag, const uint64_t *__restrict__ t1, uint64_t *tup,
+                           unsigned long long *und) {
   unsigned long long c = 0;
-  ROWS_LOOP(i, n) {
+  ROWS_LOOP(i, A.rows) {
     const uint64_t own = tup[i];
     if ((own >> 62) != 1) continue;
-    const int64_t base = off[i >> 5] + (i & 31);
-    const int L = len[i];
+    int64_t base;
+    int st, L;
+    A.row(i, base, st, L);
     uint64_t m = t1[i];
     for (int k = 0; k < L; ++k) {
-      const int64_t p = base + 32 * k;
-      if (flag[p]) m = max(m, t1[col[p]]);
+      const int64_t p = base + (int64_t)st * k;
+      if (flag[p]) m = max(m, t1[A.col[p]]);
     }
     const uint64_t key = own & ~(3ull << 62);
     if (m == own) tup[i] = kStIn | key;
@@ -270,22 +322,21 @@ __global__ void k_agg_root(int64_t n, const uint64_t *__restrict__ tup, const in
   ROWS_LOOP(i, n) cnt[i] = ((tup[i] >> 62) == 2 && nstr[i] > 0) ? 1 : 0;
 }
 
-__global__ void k_agg_pass1(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                            const int32_t *__restrict__ col, const uint8_t *__restrict__ flag,
-                            const uint64_t *__restrict__ tup, const int32_t *__restrict__ nstr,
-                            const int64_t *__restrict__ rid, int32_t *agg1) {
-  ROWS_LOOP(i, n) {
+__global__ void k_agg_pass1(DMat A, const uint8_t *__restrict__ flag, const uint64_t *__restrict__ tup,
+                            const int32_t *__restrict__ nstr, const int64_t *__restrict__ rid, int32_t *agg1) {
+  ROWS_LOOP(i, A.rows) {
     int32_t a = -1;
     if (nstr[i] > 0) {
       if ((tup[i] >> 62) == 2) {
         a = (int32_t)rid[i];
       } else {
-        const int64_t base = off[i >> 5] + (i & 31);
-        const int L = len[i];
+        int64_t base;
+        int st, L;
+        A.row(i, base, st, L);
         for (int k = 0; k < L; ++k) {
-          const int64_t p = base + 32 * k;
+          const int64_t p = base + (int64_t)st * k;
           if (!flag[p]) continue;
-          const int32_t j = col[p];
+          const int32_t j = A.col[p];
           if ((tup[j] >> 62) == 2 && nstr[j] > 0) {
             const int32_t r = (int32_t)rid[j];
             if (a < 0 || r < a) a = r;
@@ -297,19 +348,18 @@ __global__ void k_agg_pass1(int64_t n, const int64_t *__restrict__ off, const in
   }
 }
 
-__global__ void k_agg_pass2(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                            const int32_t *__restrict__ col, const uint8_t *__restrict__ flag,
-                            const int32_t *__restrict__ nstr, const int32_t *__restrict__ agg1, int32_t *agg,
-                            int64_t *freecnt) {
-  ROWS_LOOP(i, n) {
+__global__ void k_agg_pass2(DMat A, const uint8_t *__restrict__ flag, const int32_t *__restrict__ nstr,
+                            const int32_t *__restrict__ agg1, int32_t *agg, int64_t *freecnt) {
+  ROWS_LOOP(i, A.rows) {
     int32_t a = agg1[i];
     if (a < 0 && nstr[i] > 0) {
-      const int64_t base = off[i >> 5] + (i & 31);
-      const int L = len[i];
+      int64_t base;
+      int st, L;
+      A.row(i, base, st, L);
       for (int k = 0; k < L; ++k) {
-        const int64_t p = base + 32 * k;
+        const int64_t p = base + (int64_t)st * k;
         if (!flag[p]) continue;
-        const int32_t b = agg1[col[p]];
+        const int32_t b = agg1[A.col[p]];
         if (b >= 0 && (a < 0 || b < a)) a = b;
       }
     }
@@ -330,26 +380,25 @@ __global__ void k_agg_pass3(int64_t n, int64_t nroot, const int32_t *__restrict_
 // strong neighbours j; value [I = agg(i)] - omega_F dinv_i sum a_ij over the
 // diagonal and the strong entries with agg(j) = I (stored order).
 template <bool kFill>
-__global__ void k_p_rows(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                         const int32_t *__restrict__ col, const double *__restrict__ val,
-                         const uint8_t *__restrict__ flag, const double *__restrict__ dinv,
+__global__ void k_p_rows(DMat A, const uint8_t *__restrict__ flag, const double *__restrict__ dinv,
                          const int32_t *__restrict__ agg, double omega_f, int64_t *cnt,
                          const int64_t *__restrict__ rp, int32_t *pcol, double *pval, int *err) {
-  ROWS_LOOP(i, n) {
+  ROWS_LOOP(i, A.rows) {
     const int32_t ai = agg[i];
     RowMap<kCapP> m;
     bool ok = true;
     if (ai >= 0) {
-      const int64_t base = off[i >> 5] + (i & 31);
-      const int L = len[i];
+      int64_t base;
+      int st, L;
+      A.row(i, base, st, L);
       for (int k = 0; k < L && ok; ++k) {
-        const int64_t p = base + 32 * k;
-        const int32_t j = col[p];
+        const int64_t p = base + (int64_t)st * k;
+        const int32_t j = A.col[p];
         if (j == (int32_t)i) {
-          ok = m.add(ai, val[p]);
+          ok = m.add(ai, A.val[p]);
         } else if (flag[p]) {
           const int32_t aj = agg[j];
-          if (aj >= 0) ok = m.add(aj, val[p]);
+          if (aj >= 0) ok = m.add(aj, A.val[p]);
         }
       }
     }
@@ -386,49 +435,200 @@ __global__ void k_t_fill(int64_t n, const int64_t *__restrict__ rp, const int32_
   }
 }
 
-// Insertion sort of every row by column (columns within a row are distinct).
-__global__ void k_sort_rows(int64_t n, const int64_t *__restrict__ rp, int32_t *col, double *val) {
-  ROWS_LOOP(i, n) {
-    const int64_t lo = rp[i], hi = rp[i + 1];
-    for (int64_t a = lo + 1; a < hi; ++a) {
-      const int32_t c = col[a];
-      const double v = val[a];
-      int64_t b = a - 1;
-      while (b >= lo && col[b] > c) {
-        col[b + 1] = col[b];
-        val[b + 1] = val[b];
-        --b;
+// Bitonic sort by key of the first m entries of (key, val) in shared memory,
+// padded to a power of two with INT_MAX keys; one warp.
+__device__ void warp_sort(int32_t *key, double *val, int m) {
+  const int lane = threadIdx.x & 31;
+  int np2 = 1;
+  while (np2 < m) np2 <<= 1;
+  for (int t = m + lane; t < np2; t += 32) {
+    key[t] = 0x7fffffff;
+    val[t] = 0.0;
+  }
+  __syncwarp();
+  for (int k = 2; k <= np2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < np2; t += 32) {
+        const int u = t ^ j;
+        if (u > t) {
+          const bool up = (t & k) == 0;
+          if ((key[t] > key[u]) == up) {
+            const int32_t tk = key[t];
+            key[t] = key[u];
+            key[u] = tk;
+            const double tv = val[t];
+            val[t] = val[u];
+            val[u] = tv;
+          }
+        }
       }
-      col[b + 1] = c;
-      val[b + 1] = v;
+      __syncwarp();
     }
+  }
+}
+
+// Sort every row of a CSR matrix by column (distinct columns), one warp per
+// row, rows of at most kSortMax entries.
+__global__ void __launch_bounds__(32 * kProdWarps) k_sort_rows(int64_t n, const int64_t *__restrict__ rp, int32_t *col,
+                                                              double *val, int *err) {
+  __shared__ int32_t sk[kProdWarps][kSortMax];
+  __shared__ double sv[kProdWarps][kSortMax];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * kProdWarps + w, nw = (int64_t)gridDim.x * kProdWarps;
+  for (int64_t i = gw; i < n; i += nw) {
+    const int64_t lo = rp[i];
+    const int m = (int)(rp[i + 1] - lo);
+    if (m > kSortMax) {
+      if (lane == 0) atomicOr(err, DEVERR_AMG_ROW);
+      continue;
+    }
+    for (int t = lane; t < m; t += 32) {
+      sk[w][t] = col[lo + t];
+      sv[w][t] = val[lo + t];
+    }
+    __syncwarp();
+    warp_sort(sk[w], sv[w], m);
+    for (int t = lane; t < m; t += 32) {
+      col[lo + t] = sk[w][t];
+      val[lo + t] = sv[w][t];
+    }
+    __syncwarp();
   }
 }
 
 // ---------------------------------------------------------- products ------
-// Row i of A P (A in SELL, P in CSR).
+// Row r of C = X Y (X in SELL or CSR, Y in CSR), one warp per row: for each
+// entry (k, x) of X's row in stored order the lanes take Y's row k (distinct
+// columns, so no two lanes meet in one round) and add x * y into a hash table
+// in shared memory; every column's sum therefore runs in a fixed order.  The
+// count pass stores the number of distinct columns; the fill pass sorts the
+// table by column and writes the row.
 template <bool kFill>
-__global__ void k_ap_rows(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                          const int32_t *__restrict__ col, const double *__restrict__ val,
-                          const int64_t *__restrict__ prp, const int32_t *__restrict__ pcol,
-                          const double *__restrict__ pval, int64_t *cnt, const int64_t *__restrict__ rp,
-                          int32_t *ocol, double *oval, int *err) {
-  ROWS_LOOP(i, n) {
-    RowMap<kCapAP> m;
-    bool ok = true;
-    const int64_t base = off[i >> 5] + (i & 31);
-    const int L = len[i];
-    for (int k = 0; k < L && ok; ++k) {
-      const int64_t p = base + 32 * k;
-      const int32_t j = col[p];
-      const double a = val[p];
-      for (int64_t q = prp[j]; q < prp[j + 1] && ok; ++q) ok = m.add(pcol[q], a * pval[q]);
+__global__ void __launch_bounds__(32 * kProdWarps) k_prod_rows(DMat X, const int64_t *__restrict__ yrp,
+                                                              const int32_t *__restrict__ ycol,
+                                                              const double *__restrict__ yval, int64_t *cnt,
+                                                              const int64_t *__restrict__ rp, int32_t *ocol,
+                                                              double *oval, int *err) {
+  __shared__ int32_t tk[kProdWarps][kHashSlots];
+  __shared__ double tv[kProdWarps][kHashSlots];
+  __shared__ int tn[kProdWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * kProdWarps + w, nw = (int64_t)gridDim.x * kProdWarps;
+  int32_t *K = tk[w];
+  double *V = tv[w];
+  for (int64_t r = gw; r < X.rows; r += nw) {
+    int64_t base;
+    int st, L;
+    X.row(r, base, st, L);
+    // table size: a power of two of at least twice the candidate count
+    // (capped), so short rows initialise and compact a small table
+    int64_t cand = 0;
+    for (int e = lane; e < L; e += 32) {
+      const int32_t k = X.col[base + (int64_t)st * e];
+      cand += yrp[k + 1] - yrp[k];
     }
-    if (!ok) atomicOr(err, DEVERR_AMG_ROW);
+    for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
+    int bits = 5;
+    while (bits < 9 && (1ll << bits) < 2 * cand) ++bits;
+    const int slots = 1 << bits;
+    for (int t = lane; t < slots; t += 32) {
+      K[t] = -1;
+      V[t] = 0.0;
+    }
+    if (lane == 0) tn[w] = 0;
+    __syncwarp();
+    bool over = false;
+    for (int e = 0; e < L; ++e) {
+      const int64_t p = base + (int64_t)st * e;
+      const int32_t k = X.col[p];
+      const double xv = X.val[p];
+      const int64_t q0 = yrp[k], q1 = yrp[k + 1];
+      for (int64_t q = q0 + lane; q < q1; q += 32) {
+        const int32_t c = ycol[q];
+        const double v = xv * yval[q];
+        unsigned h = ((unsigned)c * 0x9E3779B1u) >> (32 - bits);
+        for (int probe = 0; probe < slots; ++probe) {
+          const int32_t old = atomicCAS(&K[h], -1, c);
+          if (old == -1) atomicAdd(&tn[w], 1);
+          if (old == -1 || old == c) {
+            V[h] += v;
+            break;
+          }
+          h = (h + 1) & (slots - 1);
+        }
+      }
+      __syncwarp();
+      if (tn[w] > kHashMax) over = true;
+      if (over) break;
+    }
+    __syncwarp();
+    const int m = tn[w];
+    if (over) {
+      if (lane == 0) {
+        atomicOr(err, DEVERR_AMG_ROW);
+        if (!kFill) cnt[r] = 0;
+      }
+      __syncwarp();
+      continue;
+    }
     if (!kFill) {
-      cnt[i] = ok ? m.n : 0;
+      if (lane == 0) cnt[r] = m;
+      __syncwarp();
+      continue;
+    }
+    // compact the occupied slots to the front in place (slot order; a slot
+    // moves only backwards, and each chunk is read before it is written),
+    // then sort by column
+    int done = 0;
+    for (int t0 = 0; t0 < slots; t0 += 32) {
+      const int t = t0 + lane;
+      const int32_t kk = K[t];
+      const double vv = V[t];
+      const bool occ = kk >= 0;
+      const unsigned b = __ballot_sync(0xffffffffu, occ);
+      __syncwarp();
+      if (occ) {
+        const int pos = done + __popc(b & ((1u << lane) - 1));
+        K[pos] = kk;
+        V[pos] = vv;
+      }
+      done += __popc(b);
+      __syncwarp();
+    }
+    warp_sort(K, V, m);
+    const int64_t o = rp[r];
+    for (int t = lane; t < m; t += 32) {
+      ocol[o + t] = K[t];
+      oval[o + t] = V[t];
+    }
+    __syncwarp();
+  }
+}
+
+// Row r of C = X Y with one thread per row (short rows: the finest level's
+// A P), the row's distinct columns in a sorted list, contributions summed in
+// stored order.
+template <bool kFill>
+__global__ void k_prod_rows_thread(DMat X, const int64_t *__restrict__ yrp, const int32_t *__restrict__ ycol,
+                                   const double *__restrict__ yval, int64_t *cnt, const int64_t *__restrict__ rp,
+                                   int32_t *ocol, double *oval, unsigned long long *ovf) {
+  ROWS_LOOP(r, X.rows) {
+    RowMap<kCapThreadRow> m;
+    bool ok = true;
+    int64_t base;
+    int st, L;
+    X.row(r, base, st, L);
+    for (int e = 0; e < L && ok; ++e) {
+      const int64_t p = base + (int64_t)st * e;
+      const int32_t k = X.col[p];
+      const double xv = X.val[p];
+      for (int64_t q = yrp[k]; q < yrp[k + 1] && ok; ++q) ok = m.add(ycol[q], xv * yval[q]);
+    }
+    if (!ok) atomicOr(ovf, 1ull);   // the host redoes the product a warp per row
+    if (!kFill) {
+      cnt[r] = ok ? m.n : 0;
     } else if (ok) {
-      const int64_t o = rp[i];
+      const int64_t o = rp[r];
       for (int t = 0; t < m.n; ++t) {
         ocol[o + t] = m.key[t];
         oval[o + t] = m.val[t];
@@ -437,73 +637,15 @@ __global__ void k_ap_rows(int64_t n, const int64_t *__restrict__ off, const int3
   }
 }
 
-// Row I of R (A P), R = P^T in CSR with rows sorted by fine index.
-template <bool kFill>
-__global__ void k_rap_rows(int64_t nc, const int64_t *__restrict__ rrp, const int32_t *__restrict__ rcol,
-                           const double *__restrict__ rval, const int64_t *__restrict__ arp,
-                           const int32_t *__restrict__ acol, const double *__restrict__ aval, int64_t *cnt,
-                           const int64_t *__restrict__ rp, int32_t *ocol, double *oval, int *err) {
-  ROWS_LOOP(I, nc) {
-    RowMap<kCapRAP> m;
-    bool ok = true;
-    for (int64_t p = rrp[I]; p < rrp[I + 1] && ok; ++p) {
-      const int32_t i = rcol[p];
-      const double r = rval[p];
-      for (int64_t q = arp[i]; q < arp[i + 1] && ok; ++q) ok = m.add(acol[q], r * aval[q]);
-    }
-    if (!ok) atomicOr(err, DEVERR_AMG_ROW);
-    if (!kFill) {
-      cnt[I] = ok ? m.n : 0;
-    } else if (ok) {
-      const int64_t o = rp[I];
-      for (int t = 0; t < m.n; ++t) {
-        ocol[o + t] = m.key[t];
-        oval[o + t] = m.val[t];
-      }
-    }
-  }
-}
-
-// ------------------------------------------------------ CSR <-> SELL ------
-__global__ void k_rp_counts(int64_t n, const int64_t *__restrict__ rp, int64_t *cnt) {
-  ROWS_LOOP(i, n) cnt[i] = rp[i + 1] - rp[i];
-}
-
-__global__ void k_sell_slices(int64_t rows, int64_t ns, const int64_t *__restrict__ cnt, int64_t *ssz,
-                              int32_t *len) {
-  ROWS_LOOP(s, ns) {
-    int64_t w = 0;
-    for (int l = 0; l < 32; ++l) {
-      const int64_t r = 32 * s + l;
-      const int64_t c = r < rows ? cnt[r] : 0;
-      len[r] = (int32_t)c;
-      w = c > w ? c : w;
-    }
-    ssz[s] = 32 * w;
-  }
-}
-
-__global__ void k_csr_to_sell(int64_t ns, const int64_t *__restrict__ rp, int64_t rows,
-                              const int32_t *__restrict__ ccol, const double *__restrict__ cval,
-                              const int64_t *__restrict__ off, int32_t *scol, double *sval) {
-  ROWS_LOOP(t, ns * 32) {
-    const int64_t s = t >> 5, lane = t & 31, r = t;
-    const int64_t w = (off[s + 1] - off[s]) >> 5;
-    const int64_t lo = r < rows ? rp[r] : 0, L = r < rows ? rp[r + 1] - lo : 0;
-    for (int64_t k = 0; k < w; ++k) {
-      const int64_t p = off[s] + 32 * k + lane;
-      scol[p] = k < L ? ccol[lo + k] : 0;
-      sval[p] = k < L ? cval[lo + k] : 0.0;
-    }
-  }
-}
-
-__global__ void k_dense_from_sell(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                                  const int32_t *__restrict__ col, const double *__restrict__ val, double *M) {
+// ------------------------------------------------------ coarsest level ----
+__global__ void k_dense_from(DMat A, double *M) {
+  const int64_t n = A.rows;
   ROWS_LOOP(i, n) {
-    const int64_t base = off[i >> 5] + (i & 31);
+    int64_t base;
+    int st, L;
+    A.row(i, base, st, L);
     for (int64_t c = 0; c < n; ++c) M[i * n + c] = 0.0;
-    for (int k = 0; k < len[i]; ++k) M[i * n + col[base + 32 * k]] += val[base + 32 * k];
+    for (int k = 0; k < L; ++k) M[i * n + A.col[base + (int64_t)st * k]] += A.val[base + (int64_t)st * k];
   }
 }
 
@@ -549,56 +691,69 @@ __device__ __forceinline__ bool cycle_done(const double *sc) {
   return r;
 }
 
-__global__ void __launch_bounds__(256) k_vc_pre(int64_t n, const double *__restrict__ b,
-                                                const double *__restrict__ dinv, double omega, double *x,
-                                                const double *sc) {
-  if (cycle_done(sc)) return;
-  ROWS_LOOP(i, n) x[i] = omega * (dinv[i] * b[i]);
+// Cycle operations on one matrix (row r, t = sum_j a_rj x_j); wd = w D^-1:
+//   kResid  y = b - A x
+//   kPost   y = x + wd (b - A x)
+//   kAdd    y += A x
+//   kApply  y = A x
+enum { kResid = 0, kPost = 1, kAdd = 2, kApply = 3 };
+
+template <int kMode>
+__device__ __forceinline__ void cycle_out(int64_t r, double t, const double *__restrict__ x,
+                                          const double *__restrict__ b, const double *__restrict__ wd, double *y) {
+  if (kMode == kResid) y[r] = b[r] - t;
+  else if (kMode == kPost) y[r] = x[r] + wd[r] * (b[r] - t);
+  else if (kMode == kAdd) y[r] += t;
+  else y[r] = t;
 }
 
-// mode 0: y = b - A x;  mode 1: y = x + omega dinv (b - A x);  mode 2: y += A x
+__global__ void __launch_bounds__(256) k_vc_pre(int64_t n, const double *__restrict__ b,
+                                                const double *__restrict__ wd, double *x, const double *sc) {
+  if (cycle_done(sc)) return;
+  ROWS_LOOP(i, n) x[i] = wd[i] * b[i];
+}
+
+// SELL-32: one warp per slice, one thread per row, batches of 8 entries
+// predicated on the slice width.
 template <int kMode>
 __global__ void __launch_bounds__(256) k_vc_sell(int64_t rows, int64_t nslices, const int64_t *__restrict__ off,
                                                  const int32_t *__restrict__ col, const double *__restrict__ val,
                                                  const double *__restrict__ x, const double *__restrict__ b,
-                                                 const double *__restrict__ dinv, double omega, double *y,
-                                                 const double *sc) {
+                                                 const double *__restrict__ wd, double *y, const double *sc) {
   if (cycle_done(sc)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = warp; s < nslices; s += nwarps) {
+    const double acc = sell_row_dot<double, 8, true>(off, col, val, x, s, lane);
     const int64_t r = 32 * s + lane;
-    double bi = 0.0, xi = 0.0, di = 0.0, yi = 0.0;
-    if (r < rows) {
-      if (kMode != 2) bi = b[r];
-      if (kMode == 1) {
-        xi = x[r];
-        di = dinv[r];
-      }
-      if (kMode == 2) yi = y[r];
-    }
-    const double t = sell_row_dot<double>(off, col, val, x, s, lane);
-    if (r < rows) {
-      if (kMode == 0) y[r] = bi - t;
-      else if (kMode == 1) y[r] = xi + omega * (di * (bi - t));
-      else y[r] = yi + t;
-    }
+    if (r < rows) cycle_out<kMode>(r, acc, x, b, wd, y);
   }
 }
 
-// y = R x for the restriction (plain SELL SpMV with the cycle's early exit)
-__global__ void __launch_bounds__(256) k_vc_spmv(int64_t rows, int64_t nslices, const int64_t *__restrict__ off,
-                                                 const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                 const double *__restrict__ x, double *y, const double *sc) {
+// CSR with G lanes per row (consecutive rows per warp, so the warp reads one
+// contiguous stretch), partial sums combined by shuffles in a fixed pattern:
+// used for the short rows of P.
+template <int G, int kMode>
+__global__ void __launch_bounds__(256) k_vc_csr(int64_t rows, const int64_t *__restrict__ rp,
+                                                const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                const double *__restrict__ x, const double *__restrict__ b,
+                                                const double *__restrict__ wd, double *y, const double *sc) {
   if (cycle_done(sc)) return;
-  const int lane = threadIdx.x & 31;
+  constexpr int R = 32 / G;   // rows per warp
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1), grp = lane / G;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t s = warp; s < nslices; s += nwarps) {
-    const double t = sell_row_dot<double>(off, col, val, x, s, lane);
-    const int64_t r = 32 * s + lane;
-    if (r < rows) y[r] = t;
+  for (int64_t r0 = warp * R; r0 < rows; r0 += nwarps * R) {
+    const int64_t r = r0 + grp;
+    double acc = 0.0;
+    if (r < rows) {
+      const int64_t q1 = rp[r + 1];
+      for (int64_t q = rp[r] + sub; q < q1; q += G) acc += __ldcs(val + q) * __ldg(x + __ldcs(col + q));
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (r < rows && sub == 0) cycle_out<kMode>(r, acc, x, b, wd, y);
   }
 }
 
@@ -619,17 +774,92 @@ __global__ void __launch_bounds__(256) k_vc_dense(int n, const double *__restric
 
 static int rows_grid(int64_t n) { return grid_for(n, 256, 8); }
 
-static int sell_grid(const SellMat &A) {
-  int64_t b = (A.nslices + 7) / 8;
+static int warps_grid(int64_t warps) {   // blocks of 8 warps, one wave at most
+  int64_t b = (warps + 7) / 8;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
 }
 
+static int prod_grid(int64_t rows) {     // blocks of kProdWarps warps
+  int64_t b = (rows + kProdWarps - 1) / kProdWarps;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// Lanes per row for a CSR matrix: about three entries per lane.
+static int lanes_for(int64_t rows, int64_t nnz) {
+  const double avg = rows > 0 ? (double)nnz / rows : 1.0;
+  int g = 2;
+  while (g < 32 && 3.0 * g < avg) g <<= 1;
+  return g;
+}
+
+template <int kMode>
+static void csr_launch(cudaStream_t s, const CsrBuf &M, const double *x, const double *b, const double *wd,
+                       double *y, const double *sc) {
+  const int64_t warps = (M.rows * M.lanes + 31) / 32;
+  const int g = warps_grid(warps);
+  count_launch();
+  switch (M.lanes) {
+    case 2: k_vc_csr<2, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, M.val, x, b, wd, y, sc); break;
+    case 4: k_vc_csr<4, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, M.val, x, b, wd, y, sc); break;
+    case 8: k_vc_csr<8, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, M.val, x, b, wd, y, sc); break;
+    case 16: k_vc_csr<16, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, M.val, x, b, wd, y, sc); break;
+    default: k_vc_csr<32, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, M.val, x, b, wd, y, sc); break;
+  }
+}
+
+template <int kMode>
+static void sell_launch(cudaStream_t s, const SellMat &A, const double *x, const double *b, const double *wd,
+                        double *y, const double *sc) {
+  count_launch();
+  k_vc_sell<kMode><<<warps_grid(A.nslices), 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, A.val, x, b, wd, y, sc);
+}
+
+__global__ void k_rp_counts(int64_t n, const int64_t *__restrict__ rp, int64_t *cnt) {
+  ROWS_LOOP(i, n) cnt[i] = rp[i + 1] - rp[i];
+}
+
+__global__ void k_sell_slices(int64_t rows, int64_t ns, const int64_t *__restrict__ cnt, int64_t *ssz,
+                              int32_t *len) {
+  ROWS_LOOP(s, ns) {
+    int64_t w = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int64_t r = 32 * s + l;
+      const int64_t c = r < rows ? cnt[r] : 0;
+      len[r] = (int32_t)c;
+      w = c > w ? c : w;
+    }
+    ssz[s] = 32 * w;
+  }
+}
+
+__global__ void k_csr_to_sell(int64_t ns, const int64_t *__restrict__ rp, int64_t rows,
+                              const int32_t *__restrict__ ccol, const double *__restrict__ cval,
+                              const int64_t *__restrict__ off, int32_t *scol, double *sval) {
+  ROWS_LOOP(t, ns * 32) {
+    const int64_t s = t >> 5, lane = t & 31, r = t;
+    const int64_t w = (off[s + 1] - off[s]) >> 5;
+    const int64_t lo = r < rows ? rp[r] : 0, L = r < rows ? rp[r + 1] - lo : 0;
+    for (int64_t k = 0; k < w; ++k) {
+      const int64_t p = off[s] + 32 * k + lane;
+      scol[p] = k < L ? ccol[lo + k] : 0;
+      sval[p] = k < L ? cval[lo + k] : 0.0;
+    }
+  }
+}
+
+__global__ void k_scale_into(int64_t n, const double *__restrict__ a, double w, double *y) {
+  ROWS_LOOP(i, n) y[i] = w * a[i];
+}
+
 // ------------------------------------------------------------ host --------
 // Row counts cnt[rows] -> CSR with that pattern (row pointers from the scan).
-static vem_status csr_layout(vem_handle *h, CsrBuf &C, int64_t rows, const int64_t *cnt) {
+static vem_status csr_layout(vem_handle *h, CsrBuf &C, int64_t rows, int64_t cols, const int64_t *cnt) {
   VEM_TRY(grow(h, C.rp, C.c_rp, (size_t)rows + 1));
   int64_t nnz = 0;
   VEM_TRY(scan_counts(h, rows, cnt, C.rp, &nnz));
@@ -645,25 +875,27 @@ static vem_status csr_layout(vem_handle *h, CsrBuf &C, int64_t rows, const int64
     C.c_nz = c;
   }
   C.rows = rows;
+  C.cols = cols;
   C.nnz = nnz;
+  C.lanes = lanes_for(rows, nnz);
   return VEM_OK;
 }
 
-// CSR -> SELL-32 into a growable SELL buffer.
+// SELL-32 copy of a CSR matrix (slice width = longest row of the slice).
 static vem_status csr_to_sell(vem_handle *h, AmgState *S, const CsrBuf &C, SellBuf &B) {
   cudaStream_t s = h->stream;
   const int64_t rows = C.rows, ns = (rows + 31) / 32;
   VEM_TRY(grow(h, B.m.off, B.c_off, (size_t)ns + 1));
   VEM_TRY(grow(h, B.m.len, B.c_len, (size_t)ns * 32));
-  VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)(rows > ns ? rows : ns) + 1));
+  VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)rows + 1));
+  VEM_TRY(grow(h, S->cur, S->c_cur, (size_t)ns + 1));   // per-slice sizes
   count_launch();
   k_rp_counts<<<rows_grid(rows), 256, 0, s>>>(rows, C.rp, S->cnt);
-  VEM_TRY(grow(h, S->cur, S->c_cur, (size_t)ns + 1));   // per-slice sizes
   count_launch();
   k_sell_slices<<<rows_grid(ns), 256, 0, s>>>(rows, ns, S->cnt, S->cur, B.m.len);
   int64_t stored = 0;
   VEM_TRY(scan_counts(h, ns, S->cur, B.m.off, &stored));
-  if (!B.m.col || (size_t)stored > B.c_st) {
+  if (!B.m.col || (size_t)stored + 1 > B.c_st) {
     dfree(h, B.m.col);
     dfree(h, B.m.val);
     B.m.col = nullptr;
@@ -690,12 +922,47 @@ static double bits_to_double(unsigned long long b) {
   return d;
 }
 
+static DMat level_op(AmgState *S, int l) { return l == 0 ? dview(S->S0) : dview(S->lv[l].A); }
+
+// C = X Y (two passes: count, fill).  With short_rows one thread per row
+// (at most 64 distinct columns, else the product is redone a warp per row).
+static vem_status product(vem_handle *h, AmgState *S, const DMat &X, const CsrBuf &Y, CsrBuf &C,
+                          bool short_rows) {
+  cudaStream_t s = h->stream;
+  VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)X.rows + 1));
+  unsigned long long *ovf = S->ctr + kMaxRounds + 3;
+  unsigned long long over = 0;
+  if (short_rows) {
+    const int g = rows_grid(X.rows);
+    VEM_CUDA(h, cudaMemsetAsync(ovf, 0, sizeof(*ovf), s));
+    count_launch();
+    k_prod_rows_thread<false><<<g, 256, 0, s>>>(X, Y.rp, Y.col, Y.val, S->cnt, nullptr, nullptr, nullptr, ovf);
+    VEM_CUDA(h, cudaMemcpyAsync(&over, ovf, sizeof(over), cudaMemcpyDeviceToHost, s));
+    VEM_TRY(csr_layout(h, C, X.rows, Y.cols, S->cnt));   // synchronises
+  }
+  if (short_rows && !over) {
+    count_launch();
+    k_prod_rows_thread<true><<<rows_grid(X.rows), 256, 0, s>>>(X, Y.rp, Y.col, Y.val, nullptr, C.rp, C.col, C.val,
+                                                               ovf);
+  } else {
+    const int g = prod_grid(X.rows);
+    count_launch();
+    k_prod_rows<false><<<g, 32 * kProdWarps, 0, s>>>(X, Y.rp, Y.col, Y.val, S->cnt, nullptr, nullptr, nullptr,
+                                                      h->d_err);
+    VEM_TRY(csr_layout(h, C, X.rows, Y.cols, S->cnt));
+    count_launch();
+    k_prod_rows<true><<<g, 32 * kProdWarps, 0, s>>>(X, Y.rp, Y.col, Y.val, nullptr, C.rp, C.col, C.val, h->d_err);
+  }
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
 // One level: strength, MIS-2, aggregates, P, R and the coarse operator.
 // Returns nc = 0 when the level is not coarsened.
 static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64_t *nc_out) {
   cudaStream_t s = h->stream;
   AmgLevel &L = S->lv[l];
-  const SellMat &A = L.A.m;
+  const DMat A = level_op(S, l);
   const int64_t n = A.rows;
   *nc_out = 0;
   VEM_TRY(grow(h, S->flag, S->c_flag, (size_t)A.stored));
@@ -704,14 +971,13 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)n + 1));
   VEM_TRY(grow(h, S->scn, S->c_scn, (size_t)n + 1));
   VEM_TRY(grow(h, S->agg1, S->c_agg1, (size_t)n));
-  VEM_TRY(grow(h, S->dg, S->c_dg, (size_t)n));
   VEM_TRY(grow(h, L.agg, L.c_agg, (size_t)n));
   const int g = rows_grid(n);
 
   // strength and the Gershgorin maxima (diagonal and dinv already computed)
   VEM_CUDA(h, cudaMemsetAsync(S->ctr, 0, sizeof(unsigned long long) * (kMaxRounds + 4), s));
   count_launch();
-  k_amg_strength<<<g, 256, 0, s>>>(n, A.off, A.len, A.col, A.val, S->dg, theta, S->flag, S->nstr, S->ctr);
+  k_amg_strength<<<g, 256, 0, s>>>(A, S->dg, theta, S->flag, S->nstr, S->ctr);
   // MIS-2 rounds; the host reads the undecided count every second round
   count_launch();
   k_mis_init<<<g, 256, 0, s>>>(n, S->tup);
@@ -722,9 +988,9 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
     if (round + 2 > kMaxRounds) return fail(h, VEM_ERR_CUDA, "AMG aggregation did not finish in %d rounds", kMaxRounds);
     for (int k = 0; k < 2; ++k, ++round) {
       count_launch();
-      k_mis_max1<<<g, 256, 0, s>>>(n, A.off, A.len, A.col, S->flag, S->tup, t1);
+      k_mis_max1<<<g, 256, 0, s>>>(A, S->flag, S->tup, t1);
       count_launch();
-      k_mis_max2<<<g, 256, 0, s>>>(n, A.off, A.len, A.col, S->flag, t1, S->tup, S->ctr + 2 + round);
+      k_mis_max2<<<g, 256, 0, s>>>(A, S->flag, t1, S->tup, S->ctr + 2 + round);
     }
     VEM_CUDA(h, cudaGetLastError());
     VEM_CUDA(h, cudaMemcpyAsync(&und, S->ctr + 2 + round - 1, sizeof(und), cudaMemcpyDeviceToHost, s));
@@ -738,9 +1004,9 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   int64_t nroot = 0;
   VEM_TRY(scan_counts(h, n, S->cnt, S->scn, &nroot));
   count_launch();
-  k_agg_pass1<<<g, 256, 0, s>>>(n, A.off, A.len, A.col, S->flag, S->tup, S->nstr, S->scn, S->agg1);
+  k_agg_pass1<<<g, 256, 0, s>>>(A, S->flag, S->tup, S->nstr, S->scn, S->agg1);
   count_launch();
-  k_agg_pass2<<<g, 256, 0, s>>>(n, A.off, A.len, A.col, S->flag, S->nstr, S->agg1, L.agg, S->cnt);
+  k_agg_pass2<<<g, 256, 0, s>>>(A, S->flag, S->nstr, S->agg1, L.agg, S->cnt);
   int64_t nfree = 0;
   VEM_TRY(scan_counts(h, n, S->cnt, S->scn, &nfree));
   count_launch();
@@ -752,52 +1018,36 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   L.omega = 4.0 / (3.0 * rho);
   const double omega_f = 4.0 / (3.0 * rhof);
 
-  // P (CSR, then SELL)
+  // P
   count_launch();
-  k_p_rows<false><<<g, 256, 0, s>>>(n, A.off, A.len, A.col, A.val, S->flag, L.dinv, L.agg, omega_f, S->cnt,
-                                    nullptr, nullptr, nullptr, h->d_err);
-  VEM_TRY(csr_layout(h, S->Pc, n, S->cnt));
+  k_p_rows<false><<<g, 256, 0, s>>>(A, S->flag, L.dinv, L.agg, omega_f, S->cnt, nullptr, nullptr, nullptr, h->d_err);
+  VEM_TRY(csr_layout(h, L.P, n, nc, S->cnt));
   count_launch();
-  k_p_rows<true><<<g, 256, 0, s>>>(n, A.off, A.len, A.col, A.val, S->flag, L.dinv, L.agg, omega_f, nullptr,
-                                   S->Pc.rp, S->Pc.col, S->Pc.val, h->d_err);
+  k_p_rows<true><<<g, 256, 0, s>>>(A, S->flag, L.dinv, L.agg, omega_f, nullptr, L.P.rp, L.P.col, L.P.val, h->d_err);
   VEM_TRY(check_device_errors(h, "AMG prolongator"));
-  // R = P^T (CSR with rows sorted by fine index)
+  // R = P^T, rows sorted by fine index
   VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)nc + 1));
   VEM_CUDA(h, cudaMemsetAsync(S->cnt, 0, sizeof(int64_t) * nc, s));
   count_launch();
-  k_t_count<<<g, 256, 0, s>>>(n, S->Pc.rp, S->Pc.col, reinterpret_cast<unsigned long long *>(S->cnt));
-  VEM_TRY(csr_layout(h, S->Rc, nc, S->cnt));
+  k_t_count<<<g, 256, 0, s>>>(n, L.P.rp, L.P.col, reinterpret_cast<unsigned long long *>(S->cnt));
+  VEM_TRY(csr_layout(h, L.R, nc, n, S->cnt));
   VEM_TRY(grow(h, S->cur, S->c_cur, (size_t)nc + 1));
-  VEM_CUDA(h, cudaMemcpyAsync(S->cur, S->Rc.rp, sizeof(int64_t) * nc, cudaMemcpyDeviceToDevice, s));
+  VEM_CUDA(h, cudaMemcpyAsync(S->cur, L.R.rp, sizeof(int64_t) * nc, cudaMemcpyDeviceToDevice, s));
   count_launch();
-  k_t_fill<<<g, 256, 0, s>>>(n, S->Pc.rp, S->Pc.col, S->Pc.val, reinterpret_cast<unsigned long long *>(S->cur),
-                             S->Rc.col, S->Rc.val);
+  k_t_fill<<<g, 256, 0, s>>>(n, L.P.rp, L.P.col, L.P.val, reinterpret_cast<unsigned long long *>(S->cur), L.R.col,
+                             L.R.val);
   count_launch();
-  k_sort_rows<<<rows_grid(nc), 256, 0, s>>>(nc, S->Rc.rp, S->Rc.col, S->Rc.val);
+  k_sort_rows<<<prod_grid(nc), 32 * kProdWarps, 0, s>>>(nc, L.R.rp, L.R.col, L.R.val, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
-  // A P, then P^T (A P)
-  VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)n + 1));
-  count_launch();
-  k_ap_rows<false><<<g, 256, 0, s>>>(n, A.off, A.len, A.col, A.val, S->Pc.rp, S->Pc.col, S->Pc.val, S->cnt,
-                                     nullptr, nullptr, nullptr, h->d_err);
-  VEM_TRY(csr_layout(h, S->APc, n, S->cnt));
-  count_launch();
-  k_ap_rows<true><<<g, 256, 0, s>>>(n, A.off, A.len, A.col, A.val, S->Pc.rp, S->Pc.col, S->Pc.val, nullptr,
-                                    S->APc.rp, S->APc.col, S->APc.val, h->d_err);
-  VEM_TRY(check_device_errors(h, "AMG product A P"));
-  const int gc = rows_grid(nc);
-  count_launch();
-  k_rap_rows<false><<<gc, 256, 0, s>>>(nc, S->Rc.rp, S->Rc.col, S->Rc.val, S->APc.rp, S->APc.col, S->APc.val,
-                                       S->cnt, nullptr, nullptr, nullptr, h->d_err);
-  VEM_TRY(csr_layout(h, S->Ac, nc, S->cnt));
-  count_launch();
-  k_rap_rows<true><<<gc, 256, 0, s>>>(nc, S->Rc.rp, S->Rc.col, S->Rc.val, S->APc.rp, S->APc.col, S->APc.val,
-                                      nullptr, S->Ac.rp, S->Ac.col, S->Ac.val, h->d_err);
+  // A P, then R (A P)
+  // the finest level's A P has short rows: try one thread per row first
+  VEM_TRY(product(h, S, A, L.P, S->AP, l == 0));
+  VEM_TRY(product(h, S, dview(L.R), S->AP, S->lv[l + 1].A, false));
   VEM_TRY(check_device_errors(h, "AMG Galerkin product"));
-  // SELL copies: P and R for the cycle, the coarse operator as the next A
-  VEM_TRY(csr_to_sell(h, S, S->Pc, L.P));
-  VEM_TRY(csr_to_sell(h, S, S->Rc, L.R));
-  VEM_TRY(csr_to_sell(h, S, S->Ac, S->lv[l + 1].A));
+  L.Rs.m.rows = 0;
+  S->lv[l + 1].As.m.rows = 0;
+  if (L.R.rows >= kSellMinRows) VEM_TRY(csr_to_sell(h, S, L.R, L.Rs));
+  if (nc >= kSellMinRows) VEM_TRY(csr_to_sell(h, S, S->lv[l + 1].A, S->lv[l + 1].As));
   L.nc = nc;
   *nc_out = nc;
   return VEM_OK;
@@ -805,13 +1055,13 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
 
 static vem_status level_vectors(vem_handle *h, AmgState *S, int l) {
   AmgLevel &L = S->lv[l];
-  L.n = L.A.m.rows;
+  const DMat A = level_op(S, l);
+  L.n = A.rows;
   VEM_TRY(grow(h, L.dinv, L.c_dinv, (size_t)L.n));
   VEM_TRY(grow(h, L.vec, L.c_vec, 4 * (size_t)L.n));
   VEM_TRY(grow(h, S->dg, S->c_dg, (size_t)L.n));
-  const SellMat &A = L.A.m;
   count_launch();
-  k_amg_diag<<<rows_grid(L.n), 256, 0, h->stream>>>(L.n, A.off, A.len, A.col, A.val, S->dg, L.dinv, h->d_err);
+  k_amg_diag<<<rows_grid(L.n), 256, 0, h->stream>>>(A, S->dg, L.dinv, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   return VEM_OK;
 }
@@ -822,7 +1072,7 @@ vem_status amg_setup(vem_handle *h, const SellMat &Sm) {
   cudaStream_t s = h->stream;
   VEM_CUDA(h, cudaEventRecord(h->ev2, s));
   if (!S->ctr) VEM_TRY(dalloc_n(h, &S->ctr, kMaxRounds + 4));
-  S->lv[0].A.m = Sm;   // a view of the handle's S
+  S->S0 = Sm;
   S->nlev = 1;
   double theta = kTheta0;
   for (int l = 0;; ++l) {
@@ -837,23 +1087,28 @@ vem_status amg_setup(vem_handle *h, const SellMat &Sm) {
   }
   // Jacobi weight of the coarsest level (coarsen() sets it for the others)
   AmgLevel &C = S->lv[S->nlev - 1];
+  const DMat CA = level_op(S, S->nlev - 1);
   {
-    const SellMat &A = C.A.m;
-    VEM_TRY(grow(h, S->flag, S->c_flag, (size_t)A.stored));
+    VEM_TRY(grow(h, S->flag, S->c_flag, (size_t)CA.stored));
     VEM_TRY(grow(h, S->nstr, S->c_nstr, (size_t)C.n));
     VEM_CUDA(h, cudaMemsetAsync(S->ctr, 0, sizeof(unsigned long long) * 2, s));
     count_launch();
-    k_amg_strength<<<rows_grid(C.n), 256, 0, s>>>(C.n, A.off, A.len, A.col, A.val, S->dg, 0.0, S->flag, S->nstr,
-                                                  S->ctr);
+    k_amg_strength<<<rows_grid(C.n), 256, 0, s>>>(CA, S->dg, 0.0, S->flag, S->nstr, S->ctr);
     unsigned long long mx[2] = {0, 0};
     VEM_CUDA(h, cudaMemcpyAsync(mx, S->ctr, sizeof(mx), cudaMemcpyDeviceToHost, s));
     VEM_CUDA(h, cudaStreamSynchronize(s));
     C.omega = 4.0 / (3.0 * bits_to_double(mx[0]));
   }
+  for (int l = 0; l < S->nlev; ++l) {
+    AmgLevel &L = S->lv[l];
+    VEM_TRY(grow(h, L.wd, L.c_wd, (size_t)L.n));
+    count_launch();
+    k_scale_into<<<rows_grid(L.n), 256, 0, s>>>(L.n, L.dinv, L.omega, L.wd);
+  }
   if (C.n <= kDenseMax) {
     VEM_TRY(grow(h, S->cinv, S->c_cinv, (size_t)C.n * C.n));
     count_launch();
-    k_dense_from_sell<<<rows_grid(C.n), 256, 0, s>>>(C.n, C.A.m.off, C.A.m.len, C.A.m.col, C.A.m.val, S->cinv);
+    k_dense_from<<<rows_grid(C.n), 256, 0, s>>>(CA, S->cinv);
     count_launch();
     k_gauss_jordan<<<1, 256, 0, s>>>((int)C.n, S->cinv, h->d_err);
     S->csweeps = 0;
@@ -882,44 +1137,49 @@ void amg_free(vem_handle *h) {
   h->amg = nullptr;
 }
 
+// One operator application of a level (SELL-32: S on level 0, copies above).
+template <int kMode>
+static void op_launch(cudaStream_t s, AmgState *S, int l, const double *x, const double *b, const double *wd,
+                      double *y, const double *sc) {
+  if (l == 0) sell_launch<kMode>(s, S->S0, x, b, wd, y, sc);
+  else if (S->lv[l].As.m.rows) sell_launch<kMode>(s, S->lv[l].As.m, x, b, wd, y, sc);
+  else csr_launch<kMode>(s, S->lv[l].A, x, b, wd, y, sc);
+}
+
+static void pre_launch(cudaStream_t s, const AmgLevel &L, const double *b, double *x, const double *sc) {
+  count_launch();
+  k_vc_pre<<<rows_grid(L.n), 256, 0, s>>>(L.n, b, L.wd, x, sc);
+}
+
 // x = V(b) on level l; b and x are device vectors of that level's size.
 static void cycle(vem_handle *h, AmgState *S, int l, const double *b, double *x, const double *sc) {
   cudaStream_t s = h->stream;
   AmgLevel &L = S->lv[l];
-  const SellMat &A = L.A.m;
-  const int gv = rows_grid(L.n), gs = sell_grid(A);
   if (l == S->nlev - 1) {
     if (S->csweeps == 0) {
       count_launch();
       k_vc_dense<<<(int)std::min<int64_t>((L.n + 7) / 8, 1024), 256, 0, s>>>((int)L.n, S->cinv, b, x, sc);
       return;
     }
-    double *xa = L.x(), *xb = L.x2();
-    count_launch();
-    k_vc_pre<<<gv, 256, 0, s>>>(L.n, b, L.dinv, L.omega, xa, sc);
+    // damped-Jacobi sweeps from zero: x1 = wd b, then x_{k+1} = post(x_k)
+    double *xa = L.x(), *xb = L.r();
+    pre_launch(s, L, b, xa, sc);
     for (int k = 1; k < S->csweeps; ++k) {
       double *out = (k == S->csweeps - 1) ? x : xb;
-      count_launch();
-      k_vc_sell<1><<<gs, 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, A.val, xa, b, L.dinv, L.omega, out, sc);
+      op_launch<kPost>(s, S, l, xa, b, L.wd, out, sc);
       std::swap(xa, xb);
     }
     return;
   }
   AmgLevel &C = S->lv[l + 1];
   double *xa = L.x();
-  count_launch();
-  k_vc_pre<<<gv, 256, 0, s>>>(L.n, b, L.dinv, L.omega, xa, sc);
-  count_launch();
-  k_vc_sell<0><<<gs, 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, A.val, xa, b, nullptr, 0.0, L.r(), sc);
-  const SellMat &R = L.R.m, &P = L.P.m;
-  count_launch();
-  k_vc_spmv<<<sell_grid(R), 256, 0, s>>>(R.rows, R.nslices, R.off, R.col, R.val, L.r(), C.b(), sc);
+  pre_launch(s, L, b, xa, sc);                                     // xa = w D^-1 b
+  op_launch<kResid>(s, S, l, xa, b, nullptr, L.r(), sc);           // r = b - A xa
+  if (L.Rs.m.rows) sell_launch<kApply>(s, L.Rs.m, L.r(), nullptr, nullptr, C.b(), sc);
+  else csr_launch<kApply>(s, L.R, L.r(), nullptr, nullptr, C.b(), sc);
   cycle(h, S, l + 1, C.b(), C.x2(), sc);
-  count_launch();
-  k_vc_sell<2><<<sell_grid(P), 256, 0, s>>>(P.rows, P.nslices, P.off, P.col, P.val, C.x2(), nullptr, nullptr, 0.0,
-                                            xa, sc);
-  count_launch();
-  k_vc_sell<1><<<gs, 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, A.val, xa, b, L.dinv, L.omega, x, sc);
+  csr_launch<kAdd>(s, L.P, C.x2(), nullptr, nullptr, xa, sc);      // xa += P x_c
+  op_launch<kPost>(s, S, l, xa, b, L.wd, x, sc);                   // x = xa + wd (b - A xa)
 }
 
 void amg_vcycle(vem_handle *h, const double *b, double *x, const double *sc) {
@@ -927,14 +1187,21 @@ void amg_vcycle(vem_handle *h, const double *b, double *x, const double *sc) {
 }
 
 // ---- inspection (host copies for the tests) ----
+static vem_status csr_to_host(vem_handle *h, const CsrBuf &C, int64_t *rp, int32_t *col, double *val) {
+  if (rp) VEM_CUDA(h, cudaMemcpy(rp, C.rp, sizeof(int64_t) * (C.rows + 1), cudaMemcpyDeviceToHost));
+  if (col) VEM_CUDA(h, cudaMemcpy(col, C.col, sizeof(int32_t) * C.nnz, cudaMemcpyDeviceToHost));
+  if (val) VEM_CUDA(h, cudaMemcpy(val, C.val, sizeof(double) * C.nnz, cudaMemcpyDeviceToHost));
+  return VEM_OK;
+}
+
 vem_status amg_level_info(vem_handle *h, int *nlev, int64_t *rows, int64_t *nnz, int64_t *nnz_p) {
   if (!amg_valid(h)) return fail(h, VEM_ERR_BAD_INPUT, "no AMG hierarchy: call vem_amg_setup first");
   AmgState *S = h->amg;
   *nlev = S->nlev;
   for (int l = 0; l < S->nlev; ++l) {
-    if (rows) rows[l] = S->lv[l].A.m.rows;
-    if (nnz) nnz[l] = S->lv[l].A.m.nnz;
-    if (nnz_p) nnz_p[l] = l + 1 < S->nlev ? S->lv[l].P.m.nnz : 0;
+    if (rows) rows[l] = S->lv[l].n;
+    if (nnz) nnz[l] = l == 0 ? S->S0.nnz : S->lv[l].A.nnz;
+    if (nnz_p) nnz_p[l] = l + 1 < S->nlev ? S->lv[l].P.nnz : 0;
   }
   return VEM_OK;
 }
@@ -945,11 +1212,15 @@ vem_status amg_level_copy(vem_handle *h, int l, int64_t *rp, int32_t *col, doubl
   AmgState *S = h->amg;
   if (l < 0 || l >= S->nlev) return fail(h, VEM_ERR_BAD_INPUT, "AMG level %d of %d", l, S->nlev);
   AmgLevel &L = S->lv[l];
-  if (rp || col || val) VEM_TRY(sell_to_host_csr(h, L.A.m, rp, col, val));
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (rp || col || val) {
+    if (l == 0) VEM_TRY(sell_to_host_csr(h, S->S0, rp, col, val));
+    else VEM_TRY(csr_to_host(h, L.A, rp, col, val));
+  }
   const bool coarse = l + 1 < S->nlev;
   if (agg && coarse)
     VEM_CUDA(h, cudaMemcpy(agg, L.agg, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost));
-  if ((prp || pcol || pval) && coarse) VEM_TRY(sell_to_host_csr(h, L.P.m, prp, pcol, pval));
+  if ((prp || pcol || pval) && coarse) VEM_TRY(csr_to_host(h, L.P, prp, pcol, pval));
   return VEM_OK;
 }
 
