@@ -90,8 +90,10 @@ enum { VEM_PREC_BLOCK_DIAG = 0, VEM_PREC_BLOCK_TRI = 1 };
 /* Inner solver for S: Jacobi-preconditioned CG, or CG preconditioned by one
  * V(1,1) cycle of a smoothed-aggregation AMG built from S (Vanek, Mandel &
  * Brezina 1996; aggregates from a distance-2 maximal independent set, Bell,
- * Dalton & Olson 2012).  The AMG is FP64 and single-system: with
- * VEM_PRECISION_MIXED or vem_solve_batched it gives VEM_ERR_UNSUPPORTED. */
+ * Dalton & Olson 2012).  With the AMG the inner CG is always FP64;
+ * VEM_PRECISION_MIXED runs the V-cycle (matrix values, vectors and
+ * arithmetic of every level) in FP32.  The AMG is single-system:
+ * vem_solve_batched gives VEM_ERR_UNSUPPORTED with it. */
 enum { VEM_INNER_PCG = 0, VEM_INNER_AMG = 1 };
 enum { VEM_PRECISION_FP64 = 0, VEM_PRECISION_MIXED = 1 };
 

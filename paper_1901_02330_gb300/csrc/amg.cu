@@ -64,21 +64,27 @@ struct CsrBuf {
   double *val = nullptr;
   size_t c_rp = 0, c_nz = 0;
   int lanes = 4;
+  float *val32 = nullptr;   // FP32 copy of the values (FP32 cycle)
+  size_t c_v32 = 0;
 };
 
 // A SELL-32 copy of a CSR matrix for the cycle, with buffer capacities.
 struct SellBuf {
   SellMat m;
   size_t c_off = 0, c_len = 0, c_st = 0;
+  float *val32 = nullptr;   // FP32 copy of the values (FP32 cycle)
+  size_t c_v32 = 0;
 };
 
 struct AmgLevel {
   CsrBuf A;                 // levels >= 1 (level 0 is the handle's S in SELL-32)
   CsrBuf P, R;              // prolongator n x nc and restriction R = P^T
-  SellBuf As, Rs;           // SELL-32 copies of A (levels >= 1) and R for the cycle
+  SellBuf As, Rs, Ps;       // SELL-32 copies of A (levels >= 1), R and P for the cycle
   double *dinv = nullptr;
   double *wd = nullptr;     // omega * dinv (the Jacobi step)
   size_t c_wd = 0;
+  float *wd32 = nullptr, *vec32 = nullptr;   // FP32 cycle: wd and x, x2, b, r
+  size_t c_wd32 = 0, c_vec32 = 0;
   int32_t *agg = nullptr;
   double *vec = nullptr;    // x, x2, b, r: four vectors of n
   size_t c_dinv = 0, c_agg = 0, c_vec = 0;
@@ -88,11 +94,18 @@ struct AmgLevel {
   double *x2() const { return vec + n; }
   double *b() const { return vec + 2 * n; }
   double *r() const { return vec + 3 * n; }
+  template <class T> T *vx(int k) const;
 };
+template <> double *AmgLevel::vx<double>(int k) const { return vec + k * n; }
+template <> float *AmgLevel::vx<float>(int k) const { return vec32 + k * n; }
 
 struct AmgState {
   AmgLevel lv[kMaxLevels];
   SellMat S0;               // level 0 operator (a view of the handle's S)
+  const float *S0_val32 = nullptr;   // its FP32 values (the handle's copy)
+  bool fp32 = false;                 // cycle in FP32
+  float *cinv32 = nullptr;
+  size_t c_cinv32 = 0;
   int nlev = 0;
   bool valid = false;
   double *cinv = nullptr;   // dense inverse of the coarsest level
@@ -698,34 +711,41 @@ __device__ __forceinline__ bool cycle_done(const double *sc) {
 //   kApply  y = A x
 enum { kResid = 0, kPost = 1, kAdd = 2, kApply = 3 };
 
-template <int kMode>
-__device__ __forceinline__ void cycle_out(int64_t r, double t, const double *__restrict__ x,
-                                          const double *__restrict__ b, const double *__restrict__ wd, double *y) {
-  if (kMode == kResid) y[r] = b[r] - t;
-  else if (kMode == kPost) y[r] = x[r] + wd[r] * (b[r] - t);
-  else if (kMode == kAdd) y[r] += t;
-  else y[r] = t;
+template <int kMode, class T, class Ty>
+__device__ __forceinline__ void cycle_out(int64_t r, T t, const T *__restrict__ x, const T *__restrict__ b,
+                                          const T *__restrict__ wd, Ty *y) {
+  if (kMode == kResid) y[r] = (Ty)(b[r] - t);
+  else if (kMode == kPost) y[r] = (Ty)(x[r] + wd[r] * (b[r] - t));
+  else if (kMode == kAdd) y[r] += (Ty)t;
+  else y[r] = (Ty)t;
 }
 
-__global__ void __launch_bounds__(256) k_vc_pre(int64_t n, const double *__restrict__ b,
-                                                const double *__restrict__ wd, double *x, const double *sc) {
+template <class T>
+__global__ void __launch_bounds__(256) k_vc_pre(int64_t n, const T *__restrict__ b, const T *__restrict__ wd, T *x,
+                                                const double *sc) {
   if (cycle_done(sc)) return;
   ROWS_LOOP(i, n) x[i] = wd[i] * b[i];
 }
 
+template <class Ta, class Tb>
+__global__ void k_vc_convert(int64_t n, const Ta *__restrict__ a, Tb *b, const double *sc) {
+  if (cycle_done(sc)) return;
+  ROWS_LOOP(i, n) b[i] = (Tb)a[i];
+}
+
 // SELL-32: one warp per slice, one thread per row, batches of 8 entries
 // predicated on the slice width.
-template <int kMode>
+template <class T, class Ty, int kMode>
 __global__ void __launch_bounds__(256) k_vc_sell(int64_t rows, int64_t nslices, const int64_t *__restrict__ off,
-                                                 const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                 const double *__restrict__ x, const double *__restrict__ b,
-                                                 const double *__restrict__ wd, double *y, const double *sc) {
+                                                 const int32_t *__restrict__ col, const T *__restrict__ val,
+                                                 const T *__restrict__ x, const T *__restrict__ b,
+                                                 const T *__restrict__ wd, Ty *y, const double *sc) {
   if (cycle_done(sc)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = warp; s < nslices; s += nwarps) {
-    const double acc = sell_row_dot<double, 8, true>(off, col, val, x, s, lane);
+    const T acc = sell_row_dot<T, 8, true>(off, col, val, x, s, lane);
     const int64_t r = 32 * s + lane;
     if (r < rows) cycle_out<kMode>(r, acc, x, b, wd, y);
   }
@@ -733,12 +753,12 @@ __global__ void __launch_bounds__(256) k_vc_sell(int64_t rows, int64_t nslices, 
 
 // CSR with G lanes per row (consecutive rows per warp, so the warp reads one
 // contiguous stretch), partial sums combined by shuffles in a fixed pattern:
-// used for the short rows of P.
-template <int G, int kMode>
+// the operators of the small levels.
+template <int G, class T, class Ty, int kMode>
 __global__ void __launch_bounds__(256) k_vc_csr(int64_t rows, const int64_t *__restrict__ rp,
-                                                const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                const double *__restrict__ x, const double *__restrict__ b,
-                                                const double *__restrict__ wd, double *y, const double *sc) {
+                                                const int32_t *__restrict__ col, const T *__restrict__ val,
+                                                const T *__restrict__ x, const T *__restrict__ b,
+                                                const T *__restrict__ wd, Ty *y, const double *sc) {
   if (cycle_done(sc)) return;
   constexpr int R = 32 / G;   // rows per warp
   const int lane = threadIdx.x & 31, sub = lane & (G - 1), grp = lane / G;
@@ -746,7 +766,7 @@ __global__ void __launch_bounds__(256) k_vc_csr(int64_t rows, const int64_t *__r
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r0 = warp * R; r0 < rows; r0 += nwarps * R) {
     const int64_t r = r0 + grp;
-    double acc = 0.0;
+    T acc = 0;
     if (r < rows) {
       const int64_t q1 = rp[r + 1];
       for (int64_t q = rp[r] + sub; q < q1; q += G) acc += __ldcs(val + q) * __ldg(x + __ldcs(col + q));
@@ -758,16 +778,17 @@ __global__ void __launch_bounds__(256) k_vc_csr(int64_t rows, const int64_t *__r
 }
 
 // x = Minv b with the dense coarsest inverse: one warp per row.
-__global__ void __launch_bounds__(256) k_vc_dense(int n, const double *__restrict__ Minv,
-                                                  const double *__restrict__ b, double *x, const double *sc) {
+template <class T>
+__global__ void __launch_bounds__(256) k_vc_dense(int n, const T *__restrict__ Minv, const T *__restrict__ b, T *x,
+                                                  const double *sc) {
   if (cycle_done(sc)) return;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int r = warp; r < n; r += nwarps) {
-    double acc = 0.0;
+    T acc = 0;
     for (int c = lane; c < n; c += 32) acc += Minv[(int64_t)r * n + c] * b[c];
-    acc = warp_sum(acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) x[r] = acc;
   }
 }
@@ -798,26 +819,35 @@ static int lanes_for(int64_t rows, int64_t nnz) {
   return g;
 }
 
-template <int kMode>
-static void csr_launch(cudaStream_t s, const CsrBuf &M, const double *x, const double *b, const double *wd,
-                       double *y, const double *sc) {
+template <class T> static const T *vals(const CsrBuf &M);
+template <> const double *vals<double>(const CsrBuf &M) { return M.val; }
+template <> const float *vals<float>(const CsrBuf &M) { return M.val32; }
+template <class T> static const T *vals(const SellBuf &M);
+template <> const double *vals<double>(const SellBuf &M) { return M.m.val; }
+template <> const float *vals<float>(const SellBuf &M) { return M.val32; }
+
+template <int kMode, class T, class Ty>
+static void csr_launch(cudaStream_t s, const CsrBuf &M, const T *x, const T *b, const T *wd, Ty *y,
+                       const double *sc) {
   const int64_t warps = (M.rows * M.lanes + 31) / 32;
   const int g = warps_grid(warps);
+  const T *v = vals<T>(M);
   count_launch();
   switch (M.lanes) {
-    case 2: k_vc_csr<2, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, M.val, x, b, wd, y, sc); break;
-    case 4: k_vc_csr<4, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, M.val, x, b, wd, y, sc); break;
-    case 8: k_vc_csr<8, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, M.val, x, b, wd, y, sc); break;
-    case 16: k_vc_csr<16, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, M.val, x, b, wd, y, sc); break;
-    default: k_vc_csr<32, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, M.val, x, b, wd, y, sc); break;
+    case 2: k_vc_csr<2, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc); break;
+    case 4: k_vc_csr<4, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc); break;
+    case 8: k_vc_csr<8, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc); break;
+    case 16: k_vc_csr<16, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc); break;
+    default: k_vc_csr<32, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc); break;
   }
 }
 
-template <int kMode>
-static void sell_launch(cudaStream_t s, const SellMat &A, const double *x, const double *b, const double *wd,
-                        double *y, const double *sc) {
+template <int kMode, class T, class Ty>
+static void sell_launch(cudaStream_t s, const SellMat &A, const T *val, const T *x, const T *b, const T *wd, Ty *y,
+                        const double *sc) {
   count_launch();
-  k_vc_sell<kMode><<<warps_grid(A.nslices), 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, A.val, x, b, wd, y, sc);
+  k_vc_sell<T, Ty, kMode><<<warps_grid(A.nslices), 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, val, x, b, wd, y,
+                                                                sc);
 }
 
 __global__ void k_rp_counts(int64_t n, const int64_t *__restrict__ rp, int64_t *cnt) {
@@ -1045,8 +1075,10 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   VEM_TRY(product(h, S, dview(L.R), S->AP, S->lv[l + 1].A, false));
   VEM_TRY(check_device_errors(h, "AMG Galerkin product"));
   L.Rs.m.rows = 0;
+  L.Ps.m.rows = 0;
   S->lv[l + 1].As.m.rows = 0;
   if (L.R.rows >= kSellMinRows) VEM_TRY(csr_to_sell(h, S, L.R, L.Rs));
+  if (L.P.rows >= kSellMinRows) VEM_TRY(csr_to_sell(h, S, L.P, L.Ps));
   if (nc >= kSellMinRows) VEM_TRY(csr_to_sell(h, S, S->lv[l + 1].A, S->lv[l + 1].As));
   L.nc = nc;
   *nc_out = nc;
@@ -1066,9 +1098,47 @@ static vem_status level_vectors(vem_handle *h, AmgState *S, int l) {
   return VEM_OK;
 }
 
-vem_status amg_setup(vem_handle *h, const SellMat &Sm) {
+template <class Tb>
+static vem_status to_f32(vem_handle *h, float *&dst, size_t &cap, const Tb *src, int64_t n) {
+  VEM_TRY(grow(h, dst, cap, (size_t)std::max<int64_t>(n, 1)));
+  if (n > 0) {
+    count_launch();
+    k_vc_convert<Tb, float><<<rows_grid(n), 256, 0, h->stream>>>(n, src, dst, nullptr);
+  }
+  return VEM_OK;
+}
+
+// FP32 copies of everything the cycle reads (values, wd, the coarsest inverse)
+static vem_status make_fp32(vem_handle *h, AmgState *S) {
+  for (int l = 0; l < S->nlev; ++l) {
+    AmgLevel &L = S->lv[l];
+    VEM_TRY(to_f32(h, L.wd32, L.c_wd32, L.wd, L.n));
+    VEM_TRY(grow(h, L.vec32, L.c_vec32, 4 * (size_t)L.n));
+    if (l > 0) {
+      if (L.As.m.rows) VEM_TRY(to_f32(h, L.As.val32, L.As.c_v32, L.As.m.val, L.As.m.stored));
+      else VEM_TRY(to_f32(h, L.A.val32, L.A.c_v32, L.A.val, L.A.nnz));
+    }
+    if (l + 1 < S->nlev) {
+      if (L.Rs.m.rows) VEM_TRY(to_f32(h, L.Rs.val32, L.Rs.c_v32, L.Rs.m.val, L.Rs.m.stored));
+      else VEM_TRY(to_f32(h, L.R.val32, L.R.c_v32, L.R.val, L.R.nnz));
+      if (L.Ps.m.rows) VEM_TRY(to_f32(h, L.Ps.val32, L.Ps.c_v32, L.Ps.m.val, L.Ps.m.stored));
+      else VEM_TRY(to_f32(h, L.P.val32, L.P.c_v32, L.P.val, L.P.nnz));
+    }
+  }
+  if (S->csweeps == 0) {
+    const int64_t cn = S->lv[S->nlev - 1].n;
+    VEM_TRY(to_f32(h, S->cinv32, S->c_cinv32, S->cinv, cn * cn));
+  }
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
+vem_status amg_setup(vem_handle *h, const SellMat &Sm, const float *S_val32, bool fp32) {
   AmgState *S = state(h);
   S->valid = false;
+  S->fp32 = fp32;
+  S->S0_val32 = S_val32;
+  if (fp32 && !S_val32) return fail(h, VEM_ERR_BAD_INPUT, "FP32 AMG cycle without FP32 values of S");
   cudaStream_t s = h->stream;
   VEM_CUDA(h, cudaEventRecord(h->ev2, s));
   if (!S->ctr) VEM_TRY(dalloc_n(h, &S->ctr, kMaxRounds + 4));
@@ -1116,6 +1186,7 @@ vem_status amg_setup(vem_handle *h, const SellMat &Sm) {
     S->csweeps = kCoarseSweeps;
   }
   VEM_CUDA(h, cudaGetLastError());
+  if (fp32) VEM_TRY(make_fp32(h, S));
   VEM_TRY(check_device_errors(h, "AMG setup"));
   VEM_CUDA(h, cudaEventRecord(h->ev3, s));
   VEM_CUDA(h, cudaEventSynchronize(h->ev3));
@@ -1127,6 +1198,7 @@ vem_status amg_setup(vem_handle *h, const SellMat &Sm) {
 }
 
 bool amg_valid(const vem_handle *h) { return h->amg && h->amg->valid; }
+bool amg_is_fp32(const vem_handle *h) { return h->amg && h->amg->fp32; }
 void amg_invalidate(vem_handle *h) {
   if (h->amg) h->amg->valid = false;
 }
@@ -1138,52 +1210,87 @@ void amg_free(vem_handle *h) {
 }
 
 // One operator application of a level (SELL-32: S on level 0, copies above).
-template <int kMode>
-static void op_launch(cudaStream_t s, AmgState *S, int l, const double *x, const double *b, const double *wd,
-                      double *y, const double *sc) {
-  if (l == 0) sell_launch<kMode>(s, S->S0, x, b, wd, y, sc);
-  else if (S->lv[l].As.m.rows) sell_launch<kMode>(s, S->lv[l].As.m, x, b, wd, y, sc);
-  else csr_launch<kMode>(s, S->lv[l].A, x, b, wd, y, sc);
+template <int kMode, class T, class Ty>
+static void op_launch(cudaStream_t s, AmgState *S, int l, const T *x, const T *b, const T *wd, Ty *y,
+                      const double *sc) {
+  if (l == 0) {
+    const T *v;
+    if constexpr (sizeof(T) == sizeof(double)) v = S->S0.val;
+    else v = S->S0_val32;
+    sell_launch<kMode>(s, S->S0, v, x, b, wd, y, sc);
+  } else if (S->lv[l].As.m.rows) {
+    sell_launch<kMode>(s, S->lv[l].As.m, vals<T>(S->lv[l].As), x, b, wd, y, sc);
+  } else {
+    csr_launch<kMode>(s, S->lv[l].A, x, b, wd, y, sc);
+  }
 }
 
-static void pre_launch(cudaStream_t s, const AmgLevel &L, const double *b, double *x, const double *sc) {
-  count_launch();
-  k_vc_pre<<<rows_grid(L.n), 256, 0, s>>>(L.n, b, L.wd, x, sc);
-}
+template <class T> static const T *wdv(const AmgLevel &L);
+template <> const double *wdv<double>(const AmgLevel &L) { return L.wd; }
+template <> const float *wdv<float>(const AmgLevel &L) { return L.wd32; }
 
-// x = V(b) on level l; b and x are device vectors of that level's size.
-static void cycle(vem_handle *h, AmgState *S, int l, const double *b, double *x, const double *sc) {
+// x = V(b) on level l, values and vectors in T; the level's output is Ty
+// (FP64 on level 0 of an FP32 cycle, so u needs no conversion pass).
+template <class T, class Ty>
+static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const double *sc) {
   cudaStream_t s = h->stream;
   AmgLevel &L = S->lv[l];
+  const T *wd = wdv<T>(L);
   if (l == S->nlev - 1) {
     if (S->csweeps == 0) {
+      const int g = (int)std::min<int64_t>((L.n + 7) / 8, 1024);
+      T *xo = L.vx<T>(1);
+      const T *inv;
+      if constexpr (sizeof(T) == sizeof(double)) inv = S->cinv;
+      else inv = S->cinv32;
       count_launch();
-      k_vc_dense<<<(int)std::min<int64_t>((L.n + 7) / 8, 1024), 256, 0, s>>>((int)L.n, S->cinv, b, x, sc);
+      if constexpr (sizeof(T) == sizeof(Ty)) {
+        k_vc_dense<T><<<g, 256, 0, s>>>((int)L.n, inv, b, x, sc);
+      } else {
+        k_vc_dense<T><<<g, 256, 0, s>>>((int)L.n, inv, b, xo, sc);
+        count_launch();
+        k_vc_convert<T, Ty><<<rows_grid(L.n), 256, 0, s>>>(L.n, xo, x, sc);
+      }
       return;
     }
     // damped-Jacobi sweeps from zero: x1 = wd b, then x_{k+1} = post(x_k)
-    double *xa = L.x(), *xb = L.r();
-    pre_launch(s, L, b, xa, sc);
+    T *xa = L.vx<T>(0), *xb = L.vx<T>(3);
+    count_launch();
+    k_vc_pre<T><<<rows_grid(L.n), 256, 0, s>>>(L.n, b, wd, xa, sc);
     for (int k = 1; k < S->csweeps; ++k) {
-      double *out = (k == S->csweeps - 1) ? x : xb;
-      op_launch<kPost>(s, S, l, xa, b, L.wd, out, sc);
+      if (k == S->csweeps - 1) op_launch<kPost>(s, S, l, (const T *)xa, b, wd, x, sc);
+      else op_launch<kPost>(s, S, l, (const T *)xa, b, wd, xb, sc);
       std::swap(xa, xb);
     }
     return;
   }
   AmgLevel &C = S->lv[l + 1];
-  double *xa = L.x();
-  pre_launch(s, L, b, xa, sc);                                     // xa = w D^-1 b
-  op_launch<kResid>(s, S, l, xa, b, nullptr, L.r(), sc);           // r = b - A xa
-  if (L.Rs.m.rows) sell_launch<kApply>(s, L.Rs.m, L.r(), nullptr, nullptr, C.b(), sc);
-  else csr_launch<kApply>(s, L.R, L.r(), nullptr, nullptr, C.b(), sc);
-  cycle(h, S, l + 1, C.b(), C.x2(), sc);
-  csr_launch<kAdd>(s, L.P, C.x2(), nullptr, nullptr, xa, sc);      // xa += P x_c
-  op_launch<kPost>(s, S, l, xa, b, L.wd, x, sc);                   // x = xa + wd (b - A xa)
+  T *xa = L.vx<T>(0), *r = L.vx<T>(3);
+  T *cb = C.vx<T>(2), *cx = C.vx<T>(1);
+  count_launch();
+  k_vc_pre<T><<<rows_grid(L.n), 256, 0, s>>>(L.n, b, wd, xa, sc);               // xa = w D^-1 b
+  op_launch<kResid>(s, S, l, (const T *)xa, b, (const T *)nullptr, r, sc);      // r = b - A xa
+  if (L.Rs.m.rows) sell_launch<kApply>(s, L.Rs.m, vals<T>(L.Rs), (const T *)r, (const T *)nullptr,
+                                       (const T *)nullptr, cb, sc);
+  else csr_launch<kApply>(s, L.R, (const T *)r, (const T *)nullptr, (const T *)nullptr, cb, sc);
+  cycle<T, T>(h, S, l + 1, (const T *)cb, cx, sc);
+  if (L.Ps.m.rows) sell_launch<kAdd>(s, L.Ps.m, vals<T>(L.Ps), (const T *)cx, (const T *)nullptr,
+                                     (const T *)nullptr, xa, sc);                // xa += P x_c
+  else csr_launch<kAdd>(s, L.P, (const T *)cx, (const T *)nullptr, (const T *)nullptr, xa, sc);
+  op_launch<kPost>(s, S, l, (const T *)xa, b, wd, x, sc);                        // x = xa + wd (b - A xa)
 }
 
 void amg_vcycle(vem_handle *h, const double *b, double *x, const double *sc) {
-  cycle(h, h->amg, 0, b, x, sc);
+  AmgState *S = h->amg;
+  if (!S->fp32) {
+    cycle<double, double>(h, S, 0, b, x, sc);
+    return;
+  }
+  AmgLevel &L = S->lv[0];
+  float *b32 = L.vx<float>(2);
+  count_launch();
+  k_vc_convert<double, float><<<rows_grid(L.n), 256, 0, h->stream>>>(L.n, b, b32, sc);
+  cycle<float, double>(h, S, 0, (const float *)b32, x, sc);
 }
 
 // ---- inspection (host copies for the tests) ----

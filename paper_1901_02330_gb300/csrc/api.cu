@@ -79,8 +79,6 @@ static vem_status check_options(vem_handle *h, const vem_options *o) {
     return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs the SPD block-diagonal preconditioner");
   if (o->inner != VEM_INNER_PCG && o->inner != VEM_INNER_AMG)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown inner solver %d", o->inner);
-  if (o->inner == VEM_INNER_AMG && o->precision != VEM_PRECISION_FP64)
-    return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver runs in FP64 only");
   if (o->precision != VEM_PRECISION_FP64 && o->precision != VEM_PRECISION_MIXED)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown precision %d", o->precision);
   if (o->precision == VEM_PRECISION_MIXED && o->krylov != VEM_KRYLOV_FGMRES)
@@ -832,7 +830,7 @@ const char *vem_last_error(const vem_handle *h) { return h ? h->last_error.c_str
 vem_status vem_amg_setup(vem_handle *h) {
   if (!h) return VEM_ERR_BAD_INPUT;
   if (!h->assembled) VEM_TRY(assemble_impl(h));
-  return amg_setup(h, h->S);
+  return amg_setup(h, h->S, h->S_val32, h->opt.precision == VEM_PRECISION_MIXED);
 }
 
 vem_status vem_amg_levels(vem_handle *h, int32_t *nlev, int64_t *rows, int64_t *nnz, int64_t *nnz_p) {

@@ -183,8 +183,10 @@ vem_status adjoint_contract(vem_handle *h, const double *lam, const double *x, d
 vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *out, int64_t *total);
 
 // Smoothed-aggregation AMG for S (amg.cu)
-vem_status amg_setup(vem_handle *h, const SellMat &S);
+// S_val32: FP32 values of S in its SELL layout, used by an FP32 cycle (fp32)
+vem_status amg_setup(vem_handle *h, const SellMat &S, const float *S_val32, bool fp32);
 bool amg_valid(const vem_handle *h);
+bool amg_is_fp32(const vem_handle *h);
 void amg_invalidate(vem_handle *h);
 double amg_setup_ms(const vem_handle *h);
 int amg_levels(const vem_handle *h);

@@ -282,6 +282,12 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
 // S x = b with x, b FP64; the solve runs in FP64 or, with the mixed
 // precision option, entirely in FP32 (values, vectors, arithmetic).
 static vem_status pcg_solve(vem_handle *h, const VemOp &op, const double *b, double *x, double *wk, int *iters) {
+  if (h->opt.inner == VEM_INNER_AMG) {
+    // FP64 CG; with the mixed option the V-cycle runs in FP32
+    const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
+    if (!amg_valid(h) || amg_is_fp32(h) != fp32) VEM_TRY(amg_setup(h, op.S, op.S_val32, fp32));
+    return pcg_solve_t<double>(h, op, op.S.val, op.s_dinv, b, x, wk, iters);
+  }
   if (h->opt.precision == VEM_PRECISION_MIXED) {
     float *w32 = reinterpret_cast<float *>(wk);
     float *x32 = w32 + 5 * op.n_p;
@@ -291,7 +297,6 @@ static vem_status pcg_solve(vem_handle *h, const VemOp &op, const double *b, dou
     VEM_CUDA(h, cudaGetLastError());
     return VEM_OK;
   }
-  if (h->opt.inner == VEM_INNER_AMG && !amg_valid(h)) VEM_TRY(amg_setup(h, op.S));
   return pcg_solve_t<double>(h, op, op.S.val, op.s_dinv, b, x, wk, iters);
 }
 
