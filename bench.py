@@ -4,12 +4,14 @@ Workload (default): unit cube, 128^3 hexahedra, the paper's k = 1 element
 (face P1 moments + 3 cross moments per cell, P0 pressure; 27,410,432
 unknowns), K = 1, p = sin(pi x) sin(pi y) sin(pi z) with Dirichlet data,
 FP64, FGMRES(30) with the block upper-triangular approximate-Schur
-preconditioner (S = B diag(M)^-1 B^T, Jacobi-PCG inner solve), stopped at a
-true relative residual of 1e-8.
+preconditioner (S = B diag(M)^-1 B^T; inner solve to 1e-8 by CG with one
+V-cycle of the smoothed-aggregation AMG, or with --inner pcg by Jacobi-PCG),
+stopped at a true relative residual of 1e-8.
 
 One step = the whole hot path on device-resident inputs: element-batched
-assembly of M_P, B_P and loads, scatter into the CSR saddle matrix, Schur
-build, and the Krylov solve.  value = unknowns / step time (DOFs/s).
+assembly of M_P, B_P and loads, scatter into the SELL-32 saddle matrix,
+Schur build, AMG setup and the Krylov solve.  value = unknowns / step time
+(DOFs/s).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -34,7 +36,7 @@ UNIT = "DOFs/s"
 WORKLOAD = "hex128-k1-fgmres30-blocktri-fp64"
 N_CELLS = 128
 RTOL = 1e-8
-INNER_RTOL = 1e-8       # inner Jacobi-PCG tolerance of the bench workload
+INNER_RTOL = 1e-8       # inner (Schur) tolerance of the bench workload
 SAMPLE_N = 12          # oracle sample: 12^3 cubes of the same workload
 
 
@@ -48,9 +50,9 @@ def parse():
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
-    ap.add_argument("--inner-rtol", type=float, default=INNER_RTOL, help="inner Jacobi-PCG tolerance")
+    ap.add_argument("--inner-rtol", type=float, default=INNER_RTOL, help="inner Schur solve tolerance")
     ap.add_argument("--element", default="k1", choices=["k1", "e0"])
-    ap.add_argument("--inner", default="pcg", choices=["pcg", "amg"],
+    ap.add_argument("--inner", default="amg", choices=["pcg", "amg"],
                     help="inner Schur solver: Jacobi-PCG or AMG-preconditioned CG")
     ap.add_argument("--workload", default="hex128-k1",
                     choices=["hex128-k1", "hex8-e0-minres", "cvt200k-e0-mixed", "hex64-e0-batch64",
@@ -69,25 +71,26 @@ def dist_env():
 
 
 # ----------------------------------------------------------------- oracle ---
-def oracle_sample(n: int = SAMPLE_N):
-    """Run the CPU oracle on one n^3 sample of the workload; returns
-    (unknowns, seconds, iterations)."""
+def oracle_sample(n: int = SAMPLE_N, inner: str = "amg"):
+    """Run the CPU oracle on one n^3 sample of the workload (same element,
+    preconditioner, inner solver and tolerances); returns (unknowns,
+    seconds, iterations)."""
     from oracle import assemble, paper_element, solvers
     from synth import fields, hex_mesh
     m = hex_mesh(n)
     prob = fields.sine_problem()
     t0 = time.perf_counter()
     sys_ = assemble(m, paper_element(1), np.ones(m.n_cells), f=prob.f, gD=prob.gD)
-    u, p, res = solvers.solve_krylov(sys_, "fgmres", "tri", "pcg", rtol=RTOL, inner_rtol=INNER_RTOL, restart=30)
+    u, p, res = solvers.solve_krylov(sys_, "fgmres", "tri", inner, rtol=RTOL, inner_rtol=INNER_RTOL, restart=30)
     dt = time.perf_counter() - t0
     return sys_.n, dt, res.iters
 
 
-def cpu_baseline_subprocess():
+def cpu_baseline_subprocess(inner: str):
     """The oracle timed single-threaded in a fresh process (spawned, never forked
     from the CUDA process)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"], env=env,
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--inner", inner], env=env,
                        capture_output=True, text=True, timeout=600)
     if r.returncode != 0:
         return {"error": r.stderr[-300:]}
@@ -101,12 +104,13 @@ def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    inner = "amg" if a.inner == "amg" else "pcg"
     for _ in range(a.warmup):
-        oracle_sample(SAMPLE_N)
+        oracle_sample(SAMPLE_N, inner)
     times = []
     n = 0
     for _ in range(a.steps):
-        n, dt, it = oracle_sample(SAMPLE_N)
+        n, dt, it = oracle_sample(SAMPLE_N, inner)
         times.append(dt)
     tot = sum(times)
     value = n * a.steps / tot
@@ -335,9 +339,12 @@ def run_ours(a):
     # ---------------- mixed precision at equal accuracy ----------------
     mixed = None
     if not a.no_mixed:
+        # mixed precision: with the AMG the inner CG stays FP64 and the V-cycle
+        # runs in FP32 (same inner tolerance); with Jacobi the whole inner PCG
+        # is FP32 and cannot go below ~1e-6
+        mixed_inner_rtol = a.inner_rtol if a.inner == "amg" else max(a.inner_rtol, 1e-5)
         sm = vs.Solver(mesh, stream=sid, device_io=1, **dict(opts, precision=vs.VEM_PRECISION_MIXED,
-                                                                inner=vs.VEM_INNER_PCG,
-                                                                inner_rtol=max(a.inner_rtol, 1e-5)))
+                                                                inner_rtol=mixed_inner_rtol))
         sm.set_coefficient(np.ones(mesh.n_cells))
         sm.set_data(prob.f, prob.gD)
         um = torch.empty_like(u)
@@ -360,7 +367,8 @@ def run_ours(a):
         mixed = {"value": n * world / (mms * 1e-3), "unit": UNIT, "ms_per_step": mms,
                  "speedup_vs_fp64": ms / mms, "relres": mst["relres"], "iterations": mst["iterations"],
                  "inner_iterations": mst["inner_iterations"], "t_solve_ms": mst["t_solve_ms"],
-                 "inner": "FP32 Jacobi-PCG rtol %g" % max(a.inner_rtol, 1e-5),
+                 "inner": ("FP64 CG with FP32 AMG V-cycle rtol %g" % mixed_inner_rtol if a.inner == "amg"
+                           else "FP32 Jacobi-PCG rtol %g" % mixed_inner_rtol),
                  "rel_diff_vs_fp64_u": float(torch.linalg.norm(um - u) / torch.linalg.norm(u)),
                  "rel_diff_vs_fp64_p": float(torch.linalg.norm(pm_ - p) / torch.linalg.norm(p))}
         del um, pm_
@@ -402,7 +410,7 @@ def run_ours(a):
         return 0
     cpu = None
     if not a.no_cpu_baseline:
-        cpu = cpu_baseline_subprocess()
+        cpu = cpu_baseline_subprocess(a.inner)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -511,10 +519,19 @@ def run_workload(a):
         mesh = voronoi_mesh(200000, seed=0, lloyd=10)
         K = fields.K_high_contrast(mesh.n_cells, seed=1, decades=4.0)
         prob = fields.sine_problem()
+        # (precision, inner solver, inner tolerance): the plain FP64 solve and the
+        # mixed forms with each inner solver.  Mixed + Jacobi: the whole inner
+        # PCG in FP32 (it stagnates near 1e-6, so 1e-5); mixed + AMG: FP64 CG
+        # with the V-cycle in FP32.
+        # On this mesh the outer FGMRES takes 57 iterations whatever the inner
+        # tolerance (diag(M) is the limiting approximation), so every variant
+        # solves S to 1e-1 only; the outer tolerance 1e-8 fixes the accuracy.
+        variants = {"fp64-jacobi": (0, vs.VEM_INNER_PCG, 1e-1), "mixed-jacobi": (1, vs.VEM_INNER_PCG, 1e-1),
+                    "fp64-amg": (0, vs.VEM_INNER_AMG, 1e-1), "mixed-amg": (1, vs.VEM_INNER_AMG, 1e-1)}
         res = {}
-        for prec in (1, 0):
+        for name, (prec, inner, irt) in variants.items():
             s = vs.Solver(mesh, stream=sid, device_io=1, element=0, krylov=1, precond=1, precision=prec,
-                          rtol=1e-8, inner_rtol=1e-5 if prec else 1e-8, inner_maxit=5000, maxit=2000)
+                          inner=inner, rtol=1e-8, inner_rtol=irt, inner_maxit=5000, maxit=2000)
             s.set_coefficient(K)
             s.set_data(prob.f, prob.gD)
             n_u, n_p = s.sizes()
@@ -525,21 +542,27 @@ def run_workload(a):
                 s.assemble()
                 return s.solve(u_out=u, p_out=p)[2]
             ms, st = _timed(step, a.steps, a.warmup, stream)
-            res[prec] = (ms, st, u.clone(), p.clone())
+            res[name] = (ms, st, u.clone(), p.clone())
             s.close()
-        (ms, st, u, p), (ms64, st64, u64, p64) = res[1], res[0]
+        ms, st, u, p = res["mixed-amg"]
+        ms64, st64, u64, p64 = res["fp64-jacobi"]
         n = st["n_u"] + st["n_p"]
+        table = {k: {"ms_per_step": v[0], "iterations": v[1]["iterations"], "inner_iterations": v[1]["inner_iterations"],
+                     "relres": v[1]["relres"], "t_amg_setup_ms": v[1]["t_amg_setup_ms"],
+                     "rel_diff_vs_fp64_jacobi_u": float(torch.linalg.norm(v[2] - u64) / torch.linalg.norm(u64)),
+                     "rel_diff_vs_fp64_jacobi_p": float(torch.linalg.norm(v[3] - p64) / torch.linalg.norm(p64))}
+                 for k, v in res.items()}
         line = _line(a, "time-to-solution (rel.res 1e-8) and DOFs/s", n / (ms * 1e-3), "DOFs/s", ms,
-                     "f64 outer / f32 Schur solve",
+                     "f64 outer and inner CG / f32 AMG V-cycle",
                      {"workload": w, "cells": mesh.n_cells, "faces": mesh.n_faces, "n_u": st["n_u"], "n_p": st["n_p"],
                       "faces_per_cell": float(np.diff(mesh.cell_face_ptr).mean()), "element": "E0",
-                      "K": "10^U, U ~ U[-4,4]", "krylov": "FGMRES(30)", "precond": "block upper-triangular"},
+                      "K": "10^U, U ~ U[-4,4]", "krylov": "FGMRES(30)", "precond": "block upper-triangular",
+                      "inner": "AMG-PCG, V-cycle in FP32"},
                      iterations=st["iterations"], inner_iterations=st["inner_iterations"], relres=st["relres"],
-                     fp64={"ms_per_step": ms64, "iterations": st64["iterations"],
-                           "inner_iterations": st64["inner_iterations"], "relres": st64["relres"]},
-                     speedup_mixed_vs_fp64=ms64 / ms,
-                     rel_diff_vs_fp64_u=float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64)),
-                     rel_diff_vs_fp64_p=float(torch.linalg.norm(p - p64) / torch.linalg.norm(p64)))
+                     variants=table,
+                     speedup_vs_fp64_jacobi=res["fp64-jacobi"][0] / ms,
+                     speedup_vs_fp64_amg=res["fp64-amg"][0] / ms,
+                     speedup_mixed_vs_fp64_jacobi_solver=res["fp64-jacobi"][0] / res["mixed-jacobi"][0])
     elif w == "hex64-e0-batch64":
         # 64 systems on 64^3 cubes, E0, K_b = exp(2 xi) (seed 100 + b), f_b = 8 Fourier modes (seed 200 + b)
         mesh = hex_mesh(64)
@@ -645,7 +668,7 @@ def main():
     if a.workload != "hex128-k1" and not a.cpu_sample and a.impl == "ours":
         return run_workload(a)
     if a.cpu_sample:
-        n, dt, it = oracle_sample(SAMPLE_N)
+        n, dt, it = oracle_sample(SAMPLE_N, "amg" if a.inner == "amg" else "pcg")
         print(json.dumps({"n": n, "seconds": dt, "iters": it}))
         return 0
     if a.impl == "reference":

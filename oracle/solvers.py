@@ -80,7 +80,8 @@ class BlockPreconditioner:
     preconditioner with diag(M) for the flux block and S = B diag(M)^{-1} B^T
     for the pressure block.  inner='exact' factorises S (the paper's choice,
     with MUMPS there and SuperLU here); inner='pcg' uses Jacobi-PCG to
-    inner_rtol."""
+    inner_rtol; inner='amg' uses CG preconditioned by one V-cycle of the
+    smoothed-aggregation AMG of oracle/amg.py to inner_rtol."""
 
     def __init__(self, sys, kind="diag", inner="exact", inner_rtol=1e-12, inner_maxit=10000):
         self.n_u = sys.n_u
@@ -94,11 +95,18 @@ class BlockPreconditioner:
         self.inner_iters = 0
         if inner == "exact":
             self.lu = spla.splu(self.S.tocsc())
+        elif inner == "amg":
+            from . import amg
+            self.amg = amg
+            self.H = amg.setup(self.S)
 
     def solve_S(self, r):
         if self.inner == "exact":
             return self.lu.solve(r)
-        res = pcg(self.S, r, self.inner_rtol, self.inner_maxit)
+        if self.inner == "amg":
+            res = self.amg.amg_pcg(self.S, r, self.H, self.inner_rtol, self.inner_maxit)
+        else:
+            res = pcg(self.S, r, self.inner_rtol, self.inner_maxit)
         self.inner_iters += res.iters
         return res.x
 
