@@ -138,6 +138,8 @@ typedef struct {
   double t_amg_setup_ms;     /* of t_solve_ms: building the AMG hierarchy   */
                              /* (0 when it was reused or not used)          */
   int32_t amg_levels;        /* levels of the AMG hierarchy (0: none)       */
+  double t_saddle_spmv_ms;   /* of t_solve_ms: the saddle-matrix SpMV       */
+  int64_t n_saddle_spmv;     /* its timed launches (at most 16 per solve)   */
 } vem_stats;
 
 /* Fill *opt with the defaults: E0, FGMRES(30), block-diagonal, Jacobi-PCG

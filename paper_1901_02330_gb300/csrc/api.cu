@@ -203,6 +203,7 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
   VEM_CUDA(h, cudaEventCreate(&h->ev2));
   VEM_CUDA(h, cudaEventCreate(&h->ev3));
   for (auto &e : h->tev) VEM_CUDA(h, cudaEventCreate(&e));
+  for (auto &e : h->aev) VEM_CUDA(h, cudaEventCreate(&e));
   return geometry_build(h);
 }
 
@@ -503,6 +504,8 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     count_launch(); k_import_x<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n, x0d, x);
     h->t_schur_spmv_ms = 0.0;
     h->n_schur_spmv = 0;
+    h->t_saddle_spmv_ms = 0.0;
+    h->n_saddle_spmv = 0;
     const bool had_amg = amg_valid(h);
     cudaEventRecord(h->ev0, s);
     r = krylov_solve(h, single_op(h), h->rhs, x, &st);
@@ -515,6 +518,8 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     st.n_schur_spmv = h->n_schur_spmv;
     st.t_amg_setup_ms = (!had_amg && amg_valid(h)) ? amg_setup_ms(h) : 0.0;
     st.amg_levels = amg_levels(h);
+    st.t_saddle_spmv_ms = h->t_saddle_spmv_ms;
+    st.n_saddle_spmv = h->n_saddle_spmv;
     if (tmp) dfree(h, tmp);
     if (r != VEM_OK && r != VEM_ERR_NOT_CONVERGED) break;
     h->have_solution = true;
@@ -869,6 +874,8 @@ void vem_destroy(vem_handle *h) {
   if (h->ev2) cudaEventDestroy(h->ev2);
   if (h->ev3) cudaEventDestroy(h->ev3);
   for (auto &e : h->tev)
+    if (e) cudaEventDestroy(e);
+  for (auto &e : h->aev)
     if (e) cudaEventDestroy(e);
   delete h;
 }

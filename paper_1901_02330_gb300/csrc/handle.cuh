@@ -115,6 +115,11 @@ struct vem_handle {
   cudaEvent_t tev[2 * kTimed] = {};
   double t_schur_spmv_ms = 0.0;                  // accumulated over a solve
   int64_t n_schur_spmv = 0;
+  static constexpr int kTimedA = 16;             // timed saddle SpMV launches per solve
+  cudaEvent_t aev[2 * kTimedA] = {};
+  int n_saddle_pending = 0;
+  double t_saddle_spmv_ms = 0.0;
+  int64_t n_saddle_spmv = 0;
   double t_assemble_ms = 0.0, t_element_ms = 0.0, t_scatter_ms = 0.0;
 
   // ---- batched systems ----

@@ -49,6 +49,32 @@ static void op_apply(cudaStream_t s, const VemOp &op, const double *x, double *y
   else spmv_batched(s, op.A, op.nbatch, op.n_u1, op.A.val, x, y, dot_part);
 }
 
+// op_apply with its launch timed by a pair of CUDA events on the stream
+// (the first kTimedA launches of a solve; read back by collect_saddle()).
+static void op_apply_timed(vem_handle *h, const VemOp &op, const double *x, double *y,
+                           double *dot_part = nullptr) {
+  const int k = h->n_saddle_pending;
+  if (k < vem_handle::kTimedA) cudaEventRecord(h->aev[2 * k], h->stream);
+  op_apply(h->stream, op, x, y, dot_part);
+  if (k < vem_handle::kTimedA) {
+    cudaEventRecord(h->aev[2 * k + 1], h->stream);
+    h->n_saddle_pending = k + 1;
+  }
+}
+
+// Accumulate the timed saddle SpMV launches (the stream has been synchronised).
+static void collect_saddle(vem_handle *h) {
+  for (int i = 0; i < h->n_saddle_pending; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->aev[2 * i], h->aev[2 * i + 1]) == cudaSuccess) {
+      h->t_saddle_spmv_ms += ms;
+      h->n_saddle_spmv += 1;
+    }
+  }
+  cudaGetLastError();
+  h->n_saddle_pending = 0;
+}
+
 // --------------------------------------------------------------- PCG -------
 // Jacobi-preconditioned CG in the single-reduction form of Chronopoulos &
 // Gear (J. Comput. Appl. Math. 25, 1989): one fused kernel computes
@@ -584,7 +610,7 @@ static vem_status precond(vem_handle *h, const VemOp &op, const double *v, doubl
 static vem_status true_relres(vem_handle *h, const VemOp &op, const double *rhs, const double *x, double *tmp, double *rel) {
   cudaStream_t s = h->stream;
   const int64_t n = op.n;
-  op_apply(s, op, x, tmp);
+  op_apply_timed(h, op, x, tmp);
   const int nb = nblocks_vec(n);
   count_launch(); k_residual<<<nb, kRedThreads, 0, s>>>(n, rhs, tmp, tmp, slot(h->part, P_R2), slot(h->part, P_B2));
   count_launch(); k_read_sum<<<1, kRedThreads, 0, s>>>(slot(h->part, P_R2), nb, h->scal + S_R2);
@@ -619,7 +645,7 @@ static vem_status run_minres(vem_handle *h, const VemOp &op, const double *rhs, 
   int inner = 0;
   const int nbn = nblocks_vec(n), nbu = nblocks_vec(nu), nbp = nblocks_vec(np);
   // v = b - A x0
-  op_apply(s, op, x, tmp);
+  op_apply_timed(h, op, x, tmp);
   count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, rhs, tmp, v, slot(h->part, P_R2), slot(h->part, P_B2));
   VEM_CUDA(h, cudaMemsetAsync(vold, 0, sizeof(double) * n, s));
   VEM_CUDA(h, cudaMemsetAsync(wold, 0, sizeof(double) * n, s));
@@ -640,7 +666,7 @@ static vem_status run_minres(vem_handle *h, const VemOp &op, const double *rhs, 
   while (result != VEM_OK && it < h->opt.maxit) {
     ++it;
     count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, z, h->scal + S_MR + MR_IG);
-    op_apply(s, op, z, Az, slot(h->part, P_DELTA));
+    op_apply_timed(h, op, z, Az, slot(h->part, P_DELTA));
     count_launch(); k_mr_lanczos<<<nbn, kRedThreads, 0, s>>>(n, Az, v, vold, h->part, nbd, h->scal);
     count_launch(); k_diag_scale<<<nbu, kRedThreads, 0, s>>>(nu, vold, op.diagM, zn, slot(h->part, P_G2U));
     VEM_TRY(precond(h, op, vold, zn, pw, &inner, true));
@@ -691,7 +717,7 @@ static vem_status run_fgmres(vem_handle *h, const VemOp &op, const double *rhs, 
   if (bnorm == 0.0) bnorm = 1.0;
   while (result != VEM_OK && it < h->opt.maxit) {
     // V_0 = (b - A x) / beta
-    op_apply(s, op, x, tmp);
+    op_apply_timed(h, op, x, tmp);
     count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, rhs, tmp, V, slot(h->part, P_R2), slot(h->part, P_B2));
     count_launch(); k_gm_start<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbn, L);
     count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, V, h->scal + GM_IBETA);
@@ -700,7 +726,7 @@ static vem_status run_fgmres(vem_handle *h, const VemOp &op, const double *rhs, 
       ++it;
       double *Vj = V + (size_t)j * n, *Zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
       VEM_TRY(precond(h, op, Vj, Zj, pw, &inner, false));
-      op_apply(s, op, Zj, w);
+      op_apply_timed(h, op, Zj, w);
       for (int pass = 0; pass < 2; ++pass) {
         for (int i0 = 0; i0 <= j; i0 += kMD) {
           const int cnt = (j + 1 - i0) < kMD ? (j + 1 - i0) : kMD;
@@ -755,13 +781,20 @@ VemOp single_op(vem_handle *h) {
 }
 
 vem_status krylov_solve(vem_handle *h, const VemOp &op, const double *rhs, double *x, vem_stats *st) {
+  h->n_saddle_pending = 0;
+  vem_status r;
   if (h->opt.krylov == VEM_KRYLOV_MINRES) {
     if (h->opt.precond != VEM_PREC_BLOCK_DIAG)
       return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs the block-diagonal preconditioner");
-    return run_minres(h, op, rhs, x, st);
+    r = run_minres(h, op, rhs, x, st);
+  } else if (h->opt.krylov == VEM_KRYLOV_FGMRES) {
+    r = run_fgmres(h, op, rhs, x, st);
+  } else {
+    return fail(h, VEM_ERR_BAD_INPUT, "unknown Krylov method %d", h->opt.krylov);
   }
-  if (h->opt.krylov == VEM_KRYLOV_FGMRES) return run_fgmres(h, op, rhs, x, st);
-  return fail(h, VEM_ERR_BAD_INPUT, "unknown Krylov method %d", h->opt.krylov);
+  if (cudaStreamSynchronize(h->stream) == cudaSuccess) collect_saddle(h);
+  cudaGetLastError();
+  return r;
 }
 
 }  // namespace vem

@@ -46,7 +46,8 @@ class vem_stats(C.Structure):
                 ("n_u", C.c_int64), ("n_p", C.c_int64), ("nnz_A", C.c_int64), ("nnz_S", C.c_int64),
                 ("t_element_ms", C.c_double), ("t_scatter_ms", C.c_double), ("n_classes", C.c_int64),
                 ("t_schur_spmv_ms", C.c_double), ("n_schur_spmv", C.c_int64),
-                ("t_amg_setup_ms", C.c_double), ("amg_levels", C.c_int32)]
+                ("t_amg_setup_ms", C.c_double), ("amg_levels", C.c_int32),
+                ("t_saddle_spmv_ms", C.c_double), ("n_saddle_spmv", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
