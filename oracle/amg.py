@@ -183,7 +183,11 @@ class Hierarchy:
 
 
 def setup(A: sp.csr_matrix, theta: float = 0.08, coarse_max: int = 64, max_levels: int = 12,
-          dense_max: int = 512, coarse_sweeps: int = 4) -> Hierarchy:
+          dense_max: int = 512, coarse_sweeps: int = 4, pin_last: bool = False) -> Hierarchy:
+    """pin_last: A is singular with the constants as null space (flux data
+    on the whole boundary); the coarsest matrix then keeps the diagonal of its
+    last row and column and drops their other entries before inversion,
+    which leaves a symmetric positive definite cycle."""
     H = Hierarchy()
     A = A.tocsr()
     th = theta
@@ -206,7 +210,13 @@ def setup(A: sp.csr_matrix, theta: float = 0.08, coarse_max: int = 64, max_level
         A = (P.T @ A @ P).tocsr()
         th *= 0.5
     if H.levels[-1].A.shape[0] <= dense_max:
-        H.coarse_inv = np.linalg.inv(H.levels[-1].A.toarray())
+        Ac = H.levels[-1].A.toarray()
+        if pin_last:
+            d = Ac[-1, -1]
+            Ac[-1, :] = 0.0
+            Ac[:, -1] = 0.0
+            Ac[-1, -1] = d
+        H.coarse_inv = np.linalg.inv(Ac)
     else:
         H.coarse_sweeps = coarse_sweeps
     return H

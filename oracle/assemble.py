@@ -9,8 +9,16 @@ The discrete problem  a_h(u, v) - b_h(v, p) = -<g_D, v.n>,  b_h(u, q) = (f, q)
 is written with p~ = -p as the symmetric indefinite system
     [M  B^T] [u ]   [g]
     [B  0  ] [p~] = [F].
-Face flags: 1 = Dirichlet pressure (natural, enters g); 2 (prescribed
-flux) is not part of this oracle yet.
+Face flags: 1 = Dirichlet pressure (natural, enters g); 2 = prescribed normal
+flux u.n = u_N (Sec. 3, the space V): the face DOFs of such a face are fixed
+to the moments (1/|f|) int_f (u.n_f) m_beta of the given flux, the
+corresponding rows and columns are eliminated (identity rows, their
+coupling moved to the right-hand side).  With no Dirichlet face the pressure
+lives in Q = {int q = 0} (Sec. 3): the mean-zero constraint enters through
+one Lagrange multiplier, the "+1" of the paper's DOF counts,
+    [M  B^T 0] [u ]   [g]
+    [B  0   c] [p~] = [F],   c_P = int_P q_P = |P|  (P0 pressure).
+    [0  c^T 0] [l ]   [0]
 """
 
 from __future__ import annotations
@@ -36,16 +44,44 @@ class System:
     cells: list = field(repr=False, default=None)
     local: list = field(repr=False, default=None)
     dofmap: list = field(repr=False, default=None)
+    vol: np.ndarray = field(repr=False, default=None)          # cell volumes
+    fixed: np.ndarray = field(repr=False, default=None)        # prescribed flux DOFs
+    fixed_val: np.ndarray = field(repr=False, default=None)
+    multiplier: bool = False                                    # mean-zero pressure
 
     @property
     def n(self) -> int:
         return self.n_u + self.n_p
 
-    def saddle(self) -> sp.csr_matrix:
+    def _full(self) -> sp.csr_matrix:
         return sp.bmat([[self.M, self.B.T], [self.B, None]], format="csr")
 
+    def saddle(self) -> sp.csr_matrix:
+        """[M B^T; B 0] with the prescribed flux DOFs eliminated (identity rows
+        and zero columns)."""
+        A = self._full()
+        if self.fixed is None or self.fixed.size == 0:
+            return A
+        keep = np.ones(self.n)
+        keep[self.fixed] = 0.0
+        K = sp.diags(keep)
+        return (K @ A @ K + sp.diags(1.0 - keep)).tocsr()
+
     def rhs(self) -> np.ndarray:
-        return np.concatenate([self.g, self.F])
+        b = np.concatenate([self.g, self.F])
+        if self.fixed is None or self.fixed.size == 0:
+            return b
+        x0 = np.zeros(self.n)
+        x0[self.fixed] = self.fixed_val
+        b = b - self._full() @ x0
+        b[self.fixed] = self.fixed_val
+        return b
+
+    def augmented(self):
+        """The system with the mean-zero multiplier row and column."""
+        e = np.concatenate([np.zeros(self.n_u), self.vol])[:, None]
+        A = sp.bmat([[self.saddle(), sp.csr_matrix(e)], [sp.csr_matrix(e.T), None]], format="csr")
+        return A, np.concatenate([self.rhs(), [0.0]])
 
 
 def cell_dofmap(mesh, c: int, spec: ElementSpec):
@@ -56,10 +92,10 @@ def cell_dofmap(mesh, c: int, spec: ElementSpec):
     return np.array(idx, dtype=np.int64)
 
 
-def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False, nq=5) -> System:
-    """Assemble M, B, g, F.  nu_cell = 1/K per cell (eq. bilin_form, nu = K^-1)."""
-    if np.any(mesh.face_bc == 2):
-        raise NotImplementedError("prescribed-flux faces")
+def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False, nq=5, flux=None) -> System:
+    """Assemble M, B, g, F.  nu_cell = 1/K per cell (eq. bilin_form, nu = K^-1).
+    flux: the vector field u (callable (N,3) -> (N,3)) whose normal component
+    is prescribed on faces with flag 2."""
     nu_cell = np.asarray(nu_cell, dtype=np.float64)
     faces = all_faces(mesh, nq)
     n_u = spec.nfd * mesh.n_faces + spec.nid * mesh.n_cells
@@ -69,8 +105,10 @@ def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False
     g = np.zeros(n_u)
     F = np.zeros(n_p)
     cells, locs, maps = [], [], []
+    vol = np.zeros(mesh.n_cells)
     for c in range(mesh.n_cells):
         cell = cell_geometry(mesh, c, faces, nq)
+        vol[c] = cell.volume
         loc = local_system(cell, spec, float(nu_cell[c]), f=f, gD=gD)
         dm = cell_dofmap(mesh, c, spec)
         pm = spec.nq * c + np.arange(spec.nq)
@@ -90,10 +128,39 @@ def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False
     B = sp.csr_matrix((np.concatenate(bvals), (np.concatenate(brows), np.concatenate(bcols))), shape=(n_p, n_u))
     M.sum_duplicates()
     B.sum_duplicates()
+    fixed, fixed_val = prescribed_flux_dofs(mesh, spec, faces, flux)
     return System(spec=spec, M=M, B=B, g=g, F=F, n_u=n_u, n_p=n_p,
                   cells=cells if keep_local else None,
                   local=locs if keep_local else None,
-                  dofmap=maps if keep_local else None)
+                  dofmap=maps if keep_local else None,
+                  vol=vol, fixed=fixed, fixed_val=fixed_val,
+                  multiplier=bool(np.any(mesh.face_bc == 2)) and not bool(np.any(mesh.face_bc == 1)))
+
+
+def prescribed_flux_dofs(mesh, spec: ElementSpec, faces, flux):
+    """Indices and values of the face DOFs fixed by the flux datum: on a face
+    with flag 2, DOF (f, beta) = (1/|f|) int_f (u . n_f) m_beta^f with n_f
+    the face's global normal and the boundary-face load rule (Dunavant
+    degree 4 on the fan triangles)."""
+    from .element import load_face_points
+    from .monomials import eval_mono2, mono2
+    fl = np.nonzero(mesh.face_bc == 2)[0]
+    if fl.size == 0:
+        return np.zeros(0, dtype=np.int64), np.zeros(0)
+    if flux is None:
+        raise ValueError("faces with flag 2 need the flux datum")
+    betas = mono2(spec.kf)
+    idx, val = [], []
+    for f in fl:
+        F = faces[f]
+        pts, wts = load_face_points(F)
+        un = flux(pts) @ F.normal
+        Mf = eval_mono2(betas, pts, F)
+        mom = (wts * un) @ Mf / F.area
+        for b in range(spec.nfd):
+            idx.append(spec.nfd * int(f) + b)
+            val.append(mom[b])
+    return np.array(idx, dtype=np.int64), np.array(val)
 
 
 def mesh_cells(mesh, nq=5):

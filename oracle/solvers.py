@@ -38,16 +38,31 @@ class Result:
     inner_iters: int = 0
 
 
-def solve_direct(sys):
-    """Direct sparse solve; returns (u, p) with the physical pressure sign."""
-    x = spla.spsolve(sys.saddle().tocsc(), sys.rhs())
-    return x[:sys.n_u], -x[sys.n_u:]
+def solve_direct(sys, return_multiplier=False):
+    """Direct sparse solve; returns (u, p) with the physical pressure sign
+    (and the mean-zero multiplier when asked; 0 without one)."""
+    if sys.multiplier:
+        A, b = sys.augmented()
+        x = spla.spsolve(A.tocsc(), b)
+        lam = x[-1]
+        x = x[:-1]
+    else:
+        x = spla.spsolve(sys.saddle().tocsc(), sys.rhs())
+        lam = 0.0
+    u, p = x[:sys.n_u], -x[sys.n_u:sys.n_u + sys.n_p]
+    return (u, p, lam) if return_multiplier else (u, p)
 
 
 def schur(sys) -> sp.csr_matrix:
-    """S = B diag(M)^{-1} B^T."""
+    """S = B diag(M)^{-1} B^T over the free flux DOFs (prescribed-flux DOFs
+    are eliminated, so their columns of B do not enter)."""
     dinv = 1.0 / sys.M.diagonal()
-    return (sys.B @ sp.diags(dinv) @ sys.B.T).tocsr()
+    B = sys.B
+    if sys.fixed is not None and sys.fixed.size:
+        keep = np.ones(sys.n_u)
+        keep[sys.fixed] = 0.0
+        B = B @ sp.diags(keep)
+    return (B @ sp.diags(dinv) @ B.T).tocsr()
 
 
 def pcg(S, b, rtol=1e-12, maxit=10000, x0=None):
@@ -93,15 +108,29 @@ class BlockPreconditioner:
         self.inner_rtol = inner_rtol
         self.inner_maxit = inner_maxit
         self.inner_iters = 0
+        self.fixed = sys.fixed if sys.fixed is not None else np.zeros(0, dtype=np.int64)
+        if self.fixed.size:
+            self.B = (self.B @ sp.diags(np.where(np.isin(np.arange(sys.n_u), self.fixed), 0.0, 1.0))).tocsr()
+            self.dM[self.fixed] = 1.0
+        self.multiplier = sys.multiplier
         if inner == "exact":
-            self.lu = spla.splu(self.S.tocsc())
+            if sys.multiplier:
+                # singular S (constants): factorise [[S, c], [c^T, 0]]
+                c = sp.csr_matrix(sys.vol[:, None])
+                self.lu = spla.splu(sp.bmat([[self.S, c], [c.T, None]], format="csc"))
+            else:
+                self.lu = spla.splu(self.S.tocsc())
         elif inner == "amg":
             from . import amg
             self.amg = amg
-            self.H = amg.setup(self.S)
+            self.H = amg.setup(self.S, pin_last=sys.multiplier)
 
     def solve_S(self, r):
+        if self.multiplier:
+            r = r - r.mean()               # the consistent part (range of S)
         if self.inner == "exact":
+            if self.multiplier:
+                return self.lu.solve(np.concatenate([r, [0.0]]))[:-1]
             return self.lu.solve(r)
         if self.inner == "amg":
             res = self.amg.amg_pcg(self.S, r, self.H, self.inner_rtol, self.inner_maxit)
@@ -221,16 +250,26 @@ def fgmres(A, b, Pinv, restart=30, rtol=1e-12, maxit=5000):
 
 def solve_krylov(sys, method="minres", kind="diag", inner="exact", rtol=1e-12,
                  inner_rtol=1e-12, restart=30, maxit=5000):
-    """Preconditioned Krylov solve; returns (u, p, Result) with physical p."""
+    """Preconditioned Krylov solve; returns (u, p, Result) with physical p.
+    With the mean-zero multiplier the pressure equations are made consistent
+    first (F - c lambda with lambda = sum F / sum c, the multiplier's value),
+    the singular system is solved and p is shifted to mean zero."""
     A = sys.saddle()
+    b = sys.rhs()
+    if sys.multiplier:
+        lam = b[sys.n_u:].sum() / sys.vol.sum()
+        b[sys.n_u:] -= sys.vol * lam
     P = BlockPreconditioner(sys, kind=kind, inner=inner, inner_rtol=inner_rtol)
     if method == "minres":
         if kind != "diag":
             raise ValueError("MINRES needs the SPD block-diagonal preconditioner")
-        res = minres(A, sys.rhs(), P, rtol=rtol, maxit=maxit)
+        res = minres(A, b, P, rtol=rtol, maxit=maxit)
     elif method == "fgmres":
-        res = fgmres(A, sys.rhs(), P, restart=restart, rtol=rtol, maxit=maxit)
+        res = fgmres(A, b, P, restart=restart, rtol=rtol, maxit=maxit)
     else:
         raise ValueError(method)
     res.inner_iters = P.inner_iters
-    return res.x[:sys.n_u], -res.x[sys.n_u:], res
+    u, pt = res.x[:sys.n_u], res.x[sys.n_u:]
+    if sys.multiplier:
+        pt = pt - (sys.vol @ pt) / sys.vol.sum()
+    return u, -pt, res

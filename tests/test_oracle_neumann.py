@@ -1,0 +1,115 @@
+"""Pins for prescribed-flux (Neumann) faces and the mean-zero pressure of
+the paper's model problem (Sec. 3: u.n = u_N on the boundary, pressure in
+Q = {int q = 0}, one Lagrange multiplier)."""
+
+import numpy as np
+import pytest
+
+from oracle import E0, assemble, paper_element, solvers
+from oracle.assemble import mesh_cells
+from oracle.element import interpolate
+from synth import affine, fields, hex_mesh, prism_mesh, tet_mesh
+from synth.voronoi import voronoi_mesh
+
+A_SHEAR = np.array([[1.0, 0.3, 0.1], [0.0, 0.8, -0.2], [0.1, 0.0, 1.2]])
+MESHES = {
+    "hex": lambda bc: hex_mesh(3, bc=bc),
+    "tet": lambda bc: tet_mesh(2, bc=bc),
+    "prism": lambda bc: prism_mesh(2, bc=bc),
+    "voronoi": lambda bc: _with_bc(voronoi_mesh(30, seed=3, lloyd=2), bc),
+}
+
+
+def _with_bc(m, bc):
+    m.face_bc = np.where(m.face_bc != 0, bc, 0).astype(np.int8)
+    return m
+
+
+def _mixed_bc(m):
+    """Dirichlet on the faces whose centroid has x < 1e-9, flux elsewhere."""
+    fb = m.face_bc.copy()
+    for f in np.nonzero(fb)[0]:
+        xs = m.xyz[m.face_vertices(f)]
+        fb[f] = 1 if np.all(np.abs(xs[:, 0]) < 1e-9) else 2
+    m.face_bc = fb.astype(np.int8)
+    return m
+
+
+def _interp(sys, spec, cells, mesh, v):
+    from oracle.assemble import cell_dofmap
+    uI = np.zeros(sys.n_u)
+    for c, cell in enumerate(cells):
+        uI[cell_dofmap(mesh, c, spec)] = interpolate(cell, spec, v)
+    return uI
+
+
+@pytest.mark.parametrize("mesh", list(MESHES))
+@pytest.mark.parametrize("spec,probname", [(E0, "linear"), (paper_element(1), "linear"),
+                                           (paper_element(1), "quadratic")],
+                         ids=["E0-lin", "E1-lin", "E1-quad"])
+def test_neumann_patch(mesh, spec, probname):
+    """All-flux boundary, constant K, p in P_{kp+1}: u_h is the interpolant
+    of the exact flux and p_h the cell means of p minus their volume-weighted
+    mean (the mean-zero member of the solution family)."""
+    m = MESHES[mesh](2)
+    K = 2.5
+    prob = fields.linear_problem(K=K) if probname == "linear" else fields.quadratic_problem(K=K)
+    sys = assemble(m, spec, np.full(m.n_cells, 1.0 / K), f=prob.f, flux=prob.u)
+    assert sys.multiplier and sys.fixed.size == spec.nfd * int((m.face_bc == 2).sum())
+    u, p, lam = solvers.solve_direct(sys, return_multiplier=True)
+    cells = mesh_cells(m)
+    uI = _interp(sys, spec, cells, m, prob.u)
+    pI = np.array([(cell.qw @ prob.p(cell.qp)) / cell.volume for cell in cells])
+    pI -= sys.vol @ pI / sys.vol.sum()
+    np.testing.assert_allclose(u, uI, atol=1e-10 * max(1, np.abs(uI).max()))
+    np.testing.assert_allclose(p, pI, atol=1e-10)
+    assert abs(sys.vol @ p) <= 1e-12
+    assert abs(lam) <= 1e-10          # compatible data: the multiplier vanishes
+
+
+def test_multiplier_is_mean_of_incompatible_source():
+    """f = 1 with zero boundary flux has no solution in the plain sense; the
+    multiplier absorbs the mean of f (lambda = int f / |Omega| = 1)."""
+    m = hex_mesh(3, bc=2)
+    sys = assemble(m, E0, np.ones(m.n_cells), f=lambda x: np.ones(x.shape[0]),
+                   flux=lambda x: np.zeros_like(x))
+    u, p, lam = solvers.solve_direct(sys, return_multiplier=True)
+    assert lam == pytest.approx(1.0, rel=1e-12)
+    np.testing.assert_allclose(u, 0.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("spec", [E0, paper_element(1)], ids=lambda s: s.name)
+def test_mixed_boundary_patch(spec):
+    """Dirichlet on x = 0, flux elsewhere: no multiplier, exact for linear p."""
+    m = affine(_mixed_bc(hex_mesh(2)), A_SHEAR, (0.0, 0.0, 0.0))
+    prob = fields.linear_problem(K=1.0)
+    sys = assemble(m, spec, np.ones(m.n_cells), f=prob.f, gD=prob.gD, flux=prob.u)
+    assert not sys.multiplier
+    u, p = solvers.solve_direct(sys)
+    cells = mesh_cells(m)
+    uI = _interp(sys, spec, cells, m, prob.u)
+    pI = np.array([(cell.qw @ prob.p(cell.qp)) / cell.volume for cell in cells])
+    np.testing.assert_allclose(u, uI, atol=1e-10 * max(1, np.abs(uI).max()))
+    np.testing.assert_allclose(p, pI, atol=1e-10)
+
+
+@pytest.mark.parametrize("spec", [E0, paper_element(1)], ids=lambda s: s.name)
+def test_neumann_conservation_and_krylov(spec):
+    """Paper's polynomial solution with flux data: B u_h = F - c lambda per
+    cell (local conservation up to the multiplier), and the Block-Schur
+    Krylov solves (exact S on the augmented Schur block, or AMG-PCG) reach the
+    direct solution."""
+    m = prism_mesh(2, bc=2)
+    prob = fields.paper_polynomial_problem()
+    nu = 1.0 / fields.K_lognormal(m.n_cells, seed=4, sigma=0.5)
+    sys = assemble(m, spec, nu, f=prob.f, flux=prob.u)
+    u, p, lam = solvers.solve_direct(sys, return_multiplier=True)
+    keep = np.ones(sys.n_u)
+    keep[sys.fixed] = 0.0
+    r = sys.rhs()[sys.n_u:] - sys.vol * lam
+    np.testing.assert_allclose(sys.B @ (u * keep), r, atol=1e-10 * np.abs(r).max())
+    for method, kind, inner in [("fgmres", "diag", "exact"), ("fgmres", "tri", "amg"), ("minres", "diag", "exact")]:
+        uk, pk, res = solvers.solve_krylov(sys, method, kind, inner, rtol=1e-11, inner_rtol=1e-13)
+        assert res.converged
+        np.testing.assert_allclose(uk, u, atol=1e-8 * np.abs(u).max())
+        np.testing.assert_allclose(pk, p, atol=1e-8 * np.abs(p).max())
