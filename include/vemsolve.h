@@ -71,7 +71,15 @@ typedef enum {
  * to one cell (boundary) or two (interior).  Cells must be convex (every
  * face plane separates the cell's barycentre from the outside).
  * face_bc: 0 interior, 1 Dirichlet pressure (g_D enters the right-hand
- * side as -int_f g_D v.n).  Flag 2 (prescribed flux) is reserved. */
+ * side as -int_f g_D v.n), 2 prescribed normal flux u.n = u_N (paper Sec. 3,
+ * the space V): the face's flux DOFs are fixed to (1/|f|) int_f (u.n_f)
+ * m_beta and eliminated (unit rows in the assembled matrix, their coupling
+ * moved to the right-hand side, no contribution to S).  When every boundary
+ * face has flag 2 the pressure is taken in Q = {int p = 0} (Sec. 3) with the
+ * paper's mean-zero Lagrange multiplier: vem_solve returns the mean-zero
+ * pressure (sum |P| p_P = 0) and the multiplier in vem_stats.  Prescribed
+ * flux faces are not supported by vem_solve_batched and vem_adjoint
+ * (VEM_ERR_UNSUPPORTED). */
 typedef struct {
   int64_t n_vertices;
   const double *xyz;              /* [n_vertices][3] */
@@ -140,6 +148,8 @@ typedef struct {
   int32_t amg_levels;        /* levels of the AMG hierarchy (0: none)       */
   double t_saddle_spmv_ms;   /* of t_solve_ms: the saddle-matrix SpMV       */
   int64_t n_saddle_spmv;     /* its timed launches (at most 16 per solve)   */
+  double multiplier;         /* the mean-zero Lagrange multiplier (flux     */
+                             /* data on the whole boundary; 0 otherwise)    */
 } vem_stats;
 
 /* Fill *opt with the defaults: E0, FGMRES(30), block-diagonal, Jacobi-PCG
@@ -164,13 +174,16 @@ vem_status vem_sizes(const vem_handle *h, int64_t *n_u, int64_t *n_p);
  * the quadrature of b_h and f_h open, Sec. 4.3 remark):
  *   which = VEM_QP_CELL : one point per cell, its barycentre x_P; the load is
  *                         F_P = |P| f(x_P)  (n = n_cells);
- *   which = VEM_QP_BFACE: for every face with face_bc == 1, in face order,
- *                         its fan triangles (x_f, v_i, v_{i+1}) each with
- *                         the 6-point degree-4 rule of Dunavant (1985)
+ *   which = VEM_QP_BFACE: for every face with face_bc 1 or 2, in face
+ *                         order, its fan triangles (x_f, v_i, v_{i+1}) each
+ *                         with the 6-point degree-4 rule of Dunavant (1985)
  *                         (n = 6 * sum of those faces' vertex counts).
  * vem_quadrature_count gives n; vem_quadrature_points writes [n][3]
- * coordinates to the host buffer xyz_out. */
+ * coordinates to the host buffer xyz_out.  vem_bface_info writes, for every
+ * VEM_QP_BFACE point, the outward unit normal of its face ([n][3]) and the
+ * face flag ([n]); either pointer may be NULL. */
 enum { VEM_QP_CELL = 0, VEM_QP_BFACE = 1 };
+vem_status vem_bface_info(vem_handle *h, double *normals_out, int8_t *flags_out);
 vem_status vem_quadrature_count(const vem_handle *h, int which, int64_t *n);
 vem_status vem_quadrature_points(vem_handle *h, int which, double *xyz_out);
 
@@ -178,8 +191,10 @@ vem_status vem_quadrature_points(vem_handle *h, int which, double *xyz_out);
  * [n_cells].  Invalidates the assembly. */
 vem_status vem_set_coefficient(vem_handle *h, const double *K_cell);
 
-/* Data at the quadrature points: f at VEM_QP_CELL points, g_D at VEM_QP_BFACE
- * points (host arrays; NULL means zero).  Invalidates the right-hand side. */
+/* Data at the quadrature points: f at VEM_QP_CELL points; at VEM_QP_BFACE
+ * points g_D on Dirichlet faces and the outward normal flux u_N = u.n on
+ * prescribed-flux faces (host arrays; NULL means zero).  Invalidates the
+ * right-hand side (and the assembly when prescribed-flux faces exist). */
 vem_status vem_set_source(vem_handle *h, const double *f_qp, const double *gD_qp);
 
 /* Same as vem_set_coefficient / vem_set_source with DEVICE arrays. */

@@ -662,6 +662,14 @@ __global__ void k_dense_from(DMat A, double *M) {
   }
 }
 
+__global__ void k_pin_last(int n, double *M) {
+  const int64_t l = n - 1;
+  for (int i = threadIdx.x; i < n - 1; i += blockDim.x) {
+    M[l * n + i] = 0.0;
+    M[(int64_t)i * n + l] = 0.0;
+  }
+}
+
 // In-place Gauss-Jordan inverse of an SPD n x n matrix (no pivoting needed),
 // one block.
 __global__ void k_gauss_jordan(int n, double *M, int *err) {
@@ -1179,6 +1187,12 @@ vem_status amg_setup(vem_handle *h, const SellMat &Sm, const float *S_val32, boo
     VEM_TRY(grow(h, S->cinv, S->c_cinv, (size_t)C.n * C.n));
     count_launch();
     k_dense_from<<<rows_grid(C.n), 256, 0, s>>>(CA, S->cinv);
+    if (h->multiplier) {
+      // S is singular (constants): keep the diagonal of the last coarse row
+      // and column, drop their other entries
+      count_launch();
+      k_pin_last<<<1, 256, 0, s>>>((int)C.n, S->cinv);
+    }
     count_launch();
     k_gauss_jordan<<<1, 256, 0, s>>>((int)C.n, S->cinv, h->d_err);
     S->csweeps = 0;

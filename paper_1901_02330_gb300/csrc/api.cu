@@ -128,14 +128,16 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
     const int64_t k = h->h_fv_ptr[f + 1] - h->h_fv_ptr[f];
     if (k < 3 || k > 4096) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face %lld has %lld vertices", (long long)f, (long long)k);
     h->max_nv_face = std::max<int>(h->max_nv_face, (int)k);
-    if (h->h_fbc[f] == 2) return fail(h, VEM_ERR_UNSUPPORTED, "prescribed-flux faces (flag 2)");
-    if (h->h_fbc[f] != 0 && h->h_fbc[f] != 1) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face flag %d", (int)h->h_fbc[f]);
+    if (h->h_fbc[f] < 0 || h->h_fbc[f] > 2) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face flag %d", (int)h->h_fbc[f]);
+    h->n_flux_faces += h->h_fbc[f] == 2;
+    h->n_dir_faces += h->h_fbc[f] == 1;
   }
   for (int64_t c = 0; c < h->nc; ++c) {
     const int64_t k = h->h_cf_ptr[c + 1] - h->h_cf_ptr[c];
     if (k < 4 || k > 256) return fail(h, VEM_ERR_BAD_INPUT, "mesh: cell %lld has %lld faces", (long long)c, (long long)k);
     h->max_nf_cell = std::max<int>(h->max_nf_cell, (int)k);
   }
+  h->multiplier = h->n_flux_faces > 0 && h->n_dir_faces == 0;
   h->n_fv = h->h_fv_ptr[h->nf];
   h->n_cf = h->h_cf_ptr[h->nc];
   for (int64_t i = 0; i < h->n_fv; ++i)
@@ -182,7 +184,7 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
   // boundary-face quadrature offsets (6 points per fan triangle)
   h->h_bqp_off.assign(h->nf + 1, 0);
   for (int64_t f = 0; f < h->nf; ++f)
-    h->h_bqp_off[f + 1] = h->h_bqp_off[f] + (h->h_fbc[f] == 1 ? 6 * (h->h_fv_ptr[f + 1] - h->h_fv_ptr[f]) : 0);
+    h->h_bqp_off[f + 1] = h->h_bqp_off[f] + (h->h_fbc[f] != 0 ? 6 * (h->h_fv_ptr[f + 1] - h->h_fv_ptr[f]) : 0);
   h->n_bqp = h->h_bqp_off[h->nf];
   VEM_TRY(upload(h, &h->bqp_off, h->h_bqp_off.data(), (size_t)h->nf + 1));
   VEM_TRY(dalloc_n(h, &h->bqp_xyz, 3 * (size_t)std::max<int64_t>(h->n_bqp, 1)));
@@ -463,6 +465,7 @@ vem_status vem_set_source_device(vem_handle *h, const double *f_qp, const double
       VEM_CUDA(h, cudaMemsetAsync(h->gD_qp, 0, sizeof(double) * h->n_bqp, h->stream));
   }
   h->rhs_ready = false;
+  if (h->n_flux_faces > 0) h->assembled = false;   // the flux data is eliminated at assembly
   return VEM_OK;
 }
 
@@ -522,6 +525,11 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     st.n_saddle_spmv = h->n_saddle_spmv;
     if (tmp) dfree(h, tmp);
     if (r != VEM_OK && r != VEM_ERR_NOT_CONVERGED) break;
+    {
+      const vem_status sh = neumann_shift(h, x + h->n_u);   // mean-zero pressure
+      if (sh != VEM_OK) { r = sh; break; }
+    }
+    st.multiplier = h->lambda;
     h->have_solution = true;
     vem_status w = VEM_OK;
     if (h->opt.device_io) {
@@ -554,6 +562,7 @@ vem_status vem_adjoint(vem_handle *h, const double *dL_du, const double *dL_dp, 
   if (!dL_dlogK) return fail(h, VEM_ERR_BAD_INPUT, "dL_dlogK: NULL");
   if (!h->have_solution || !h->assembled)
     return fail(h, VEM_ERR_BAD_INPUT, "vem_adjoint needs a preceding vem_solve with the same K");
+  if (h->n_flux_faces > 0) return fail(h, VEM_ERR_UNSUPPORTED, "adjoint with prescribed-flux faces");
   cudaStream_t s = h->stream;
   if (!h->lam) VEM_TRY(dalloc_n(h, &h->lam, (size_t)h->n));
   if (!h->arhs) VEM_TRY(dalloc_n(h, &h->arhs, (size_t)h->n));
@@ -605,6 +614,8 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   if (!K || !u_out || !p_out) return fail(h, VEM_ERR_BAD_INPUT, "K / u_out / p_out: NULL");
   if (h->opt.inner == VEM_INNER_AMG)
     return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver is single-system (no batched solves)");
+  if (h->n_flux_faces > 0)
+    return fail(h, VEM_ERR_UNSUPPORTED, "prescribed-flux faces in batched solves");
   cudaStream_t s = h->stream;
   const int nb = (int)nbatch;
   const bool dev = h->opt.device_io != 0;
@@ -831,6 +842,23 @@ vem_status vem_launch_count(int64_t *n) {
 }
 
 const char *vem_last_error(const vem_handle *h) { return h ? h->last_error.c_str() : "NULL handle"; }
+
+vem_status vem_bface_info(vem_handle *h, double *normals_out, int8_t *flags_out) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (h->n_bqp == 0) return VEM_OK;
+  double *dn = nullptr;
+  int8_t *df = nullptr;
+  VEM_TRY(dalloc_n(h, &dn, 3 * (size_t)h->n_bqp));
+  VEM_TRY(dalloc_n(h, &df, (size_t)h->n_bqp));
+  vem_status r = bface_info(h, dn, df);
+  if (r == VEM_OK && normals_out)
+    r = cuda_check(h, cudaMemcpy(normals_out, dn, sizeof(double) * 3 * h->n_bqp, cudaMemcpyDeviceToHost), "normals");
+  if (r == VEM_OK && flags_out)
+    r = cuda_check(h, cudaMemcpy(flags_out, df, h->n_bqp, cudaMemcpyDeviceToHost), "flags");
+  dfree(h, dn);
+  dfree(h, df);
+  return r;
+}
 
 vem_status vem_amg_setup(vem_handle *h) {
   if (!h) return VEM_ERR_BAD_INPUT;

@@ -25,6 +25,7 @@ struct Layout {
   const int64_t *m_off, *b_off;
   const int32_t *cls_of;
   const double *Mloc, *Bloc;
+  const int8_t *fbc;      // face flags (2: prescribed flux, DOFs eliminated)
 };
 
 __device__ __forceinline__ int nloc(const Layout &L, int64_t c) {
@@ -176,6 +177,7 @@ __global__ void k_schur_fill(Layout L, const double *__restrict__ diagM, const i
       j = 1;   // slot 0 holds the diagonal
       for (int i = 0; i < k; ++i) {
         const int f = L.cf[b + i];
+        if (L.fbc[f] == 2) continue;   // eliminated flux DOF: no column of B
         const double bp = L.Bloc[bo + i * L.nfd];
         const double mf = diagM[(int64_t)L.nfd * f];
         dg += bp * bp / mf;
@@ -201,6 +203,27 @@ __global__ void k_schur_fill(Layout L, const double *__restrict__ diagM, const i
   }
 }
 
+// Eliminate the prescribed flux DOFs (faces with flag 2): their rows become
+// unit rows, their columns are zeroed elsewhere, diag(M) there is 1.
+__global__ void k_eliminate(int64_t rows, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
+                            const int32_t *__restrict__ col, double *val, int nfd, int64_t nf,
+                            const int8_t *__restrict__ fbc, double *diagM) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const bool fixed_row = r < (int64_t)nfd * nf && fbc[r / nfd] == 2;
+    const int64_t base = off[r >> 5] + (r & 31);
+    const int L = len[r];
+    for (int k = 0; k < L; ++k) {
+      const int64_t p = base + 32 * (int64_t)k;
+      const int64_t c = col[p];
+      const bool fixed_col = c < (int64_t)nfd * nf && fbc[c / nfd] == 2;
+      if (fixed_row) val[p] = (c == r) ? 1.0 : 0.0;
+      else if (fixed_col) val[p] = 0.0;
+    }
+    if (fixed_row) diagM[r] = 1.0;
+  }
+}
+
 __global__ void k_iota32(int64_t n, int32_t *a) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -220,7 +243,7 @@ __global__ void k_bt_face(Layout L, double *bt) {
        f += (int64_t)gridDim.x * blockDim.x) {
     for (int s = 0; s < 2; ++s) {
       const int32_t c = L.f_cell[2 * f + s];
-      bt[2 * f + s] = c >= 0 ? L.Bloc[boff(L, c) + L.f_loc[2 * f + s] * L.nfd] : 0.0;
+      bt[2 * f + s] = (c >= 0 && L.fbc[f] != 2) ? L.Bloc[boff(L, c) + L.f_loc[2 * f + s] * L.nfd] : 0.0;
     }
   }
 }
@@ -430,7 +453,7 @@ vem_status sell_to_host_csr(vem_handle *h, const SellMat &M, int64_t *rp, int32_
 vem_status assemble_global(vem_handle *h) {
   cudaStream_t s = h->stream;
   Layout L{h->nfd, h->nid, h->nf, h->nc, h->n_u, h->cf_ptr, h->cf, h->f_cell, h->f_loc,
-           h->m_off, h->b_off, h->cls_of, h->Mloc, h->Bloc};
+           h->m_off, h->b_off, h->cls_of, h->Mloc, h->Bloc, h->fbc};
   const int T = 256;
   const int64_t n = h->n;
   // ---- [M B^T; B 0] ----
@@ -444,6 +467,19 @@ vem_status assemble_global(vem_handle *h) {
   count_launch(); k_fill<<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, h->A.len, npad, h->A.col, h->A.val, h->diagM,
                                                       h->nu, h->A.stored);
   VEM_CUDA(h, cudaGetLastError());
+  if (h->n_flux_faces > 0) {
+    // prescribed flux DOFs: values, A x_fix with the full matrix (moved to the
+    // right-hand side), then the symmetric elimination
+    if (!h->xfix) VEM_TRY(dalloc_n(h, &h->xfix, (size_t)n));
+    if (!h->rhs_corr) VEM_TRY(dalloc_n(h, &h->rhs_corr, (size_t)n));
+    VEM_CUDA(h, cudaMemsetAsync(h->xfix, 0, sizeof(double) * n, s));
+    VEM_TRY(flux_fixed(h, h->xfix));
+    spmv(s, h->A, h->xfix, h->rhs_corr);
+    count_launch();
+    k_eliminate<<<grid_for(n, T), T, 0, s>>>(n, h->A.off, h->A.len, h->A.col, h->A.val, h->nfd, h->nf, h->fbc,
+                                            h->diagM);
+    VEM_CUDA(h, cudaGetLastError());
+  }
   // ---- S ----
   count_launch(); k_schur_count<<<grid_for(h->nc, T), T, 0, s>>>(L, cnt);
   VEM_CUDA(h, cudaGetLastError());
@@ -679,7 +715,7 @@ vem_status classify_cells(vem_handle *h) {
 vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, VemOp &op) {
   cudaStream_t s = h->stream;
   Layout L{h->nfd, h->nid, h->nf, h->nc, h->n_u, h->cf_ptr, h->cf, h->f_cell, h->f_loc,
-           h->m_off, h->b_off, h->cls_of, h->Mloc, h->Bloc};
+           h->m_off, h->b_off, h->cls_of, h->Mloc, h->Bloc, h->fbc};
   const int T = 256;
   const int64_t npad = h->A.nslices * 32, spad = h->S.nslices * 32;
   dim3 ga(grid_for(npad, T, 2), nb), gs(grid_for(spad, T, 2), nb);

@@ -536,6 +536,62 @@ vem_status assemble_local(vem_handle *h) {
   return check_device_errors(h, "element matrices");
 }
 
+// Prescribed face DOFs on flux faces (flag 2): (f, beta) = (1/|f|) int_f
+// (u.n_f) m^f_beta with u.n_f = sigma u_N (u_N given along the outward
+// normal), by the Dunavant fan rule of the bface points; zero elsewhere.
+__global__ void k_flux_fixed(int64_t nf, int nfd, const int8_t *__restrict__ fbc,
+                             const int64_t *__restrict__ off, const int64_t *__restrict__ fvp,
+                             const int32_t *__restrict__ fv, const double *__restrict__ xyz,
+                             const double *__restrict__ f_area, const double *__restrict__ f_cent,
+                             const double *__restrict__ f_norm, const double *__restrict__ f_t1,
+                             const double *__restrict__ f_diam, const int32_t *__restrict__ f_cell,
+                             const int32_t *__restrict__ f_loc, const int64_t *__restrict__ cfp,
+                             const int8_t *__restrict__ sig, const double *__restrict__ uN, double *xfix,
+                             int *err) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    for (int bta = 0; bta < nfd; ++bta) xfix[nfd * f + bta] = 0.0;
+    if (fbc[f] != 2 || uN == nullptr) continue;
+    const int64_t vb = fvp[f];
+    const int m = (int)(fvp[f + 1] - vb);
+    const double3 xf = load3(f_cent, f);
+    const double3 n = load3(f_norm, f);
+    const double3 t1 = load3(f_t1, f);
+    const double3 t2 = cross3(n, t1);
+    const double ihf = 1.0 / f_diam[f];
+    const double sg = (double)sig[cfp[f_cell[2 * f]] + f_loc[2 * f]];
+    double mom[3] = {0, 0, 0};
+    int64_t o = off[f];
+    for (int i = 0; i < m; ++i) {
+      const double3 A = load3(xyz, fv[vb + i]);
+      const double3 B = load3(xyz, fv[vb + (i + 1) % m]);
+      const double areaT = 0.5 * dot3(cross3(sub3(A, xf), sub3(B, xf)), n);
+      for (int q = 0; q < 6; ++q, ++o) {
+        double l0, l1, l2, wq;
+        dunavant4_point(q, l0, l1, l2, wq);
+        const double3 x = add3(add3(scale3(xf, l0), scale3(A, l1)), scale3(B, l2));
+        const double w = wq * areaT;
+        const double3 dx = sub3(x, xf);
+        const double mf[3] = {1.0, dot3(dx, t1) * ihf, dot3(dx, t2) * ihf};
+        const double un = uN[o];
+        if (!isfinite(un)) atomicOr(err, DEVERR_NONFINITE);
+        for (int bta = 0; bta < nfd; ++bta) mom[bta] += w * un * mf[bta];
+      }
+    }
+    const double ia = 1.0 / f_area[f];
+    for (int bta = 0; bta < nfd; ++bta) xfix[nfd * f + bta] = sg * mom[bta] * ia;
+  }
+}
+
+vem_status flux_fixed(vem_handle *h, double *xfix) {
+  count_launch();
+  k_flux_fixed<<<grid_for(h->nf, 128), 128, 0, h->stream>>>(
+      h->nf, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm, h->f_t1,
+      h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, h->gD_qp, xfix, h->d_err);
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
 vem_status assemble_rhs_into(vem_handle *h, const double *f_qp, const double *gD_qp, double *g, double *F) {
   cudaStream_t s = h->stream;
   const int T = 128;
@@ -552,6 +608,7 @@ vem_status assemble_rhs_into(vem_handle *h, const double *f_qp, const double *gD
 
 vem_status assemble_rhs(vem_handle *h) {
   VEM_TRY(assemble_rhs_into(h, h->f_qp, h->gD_qp, h->rhs, h->rhs + h->n_u));
+  VEM_TRY(neumann_rhs(h, h->rhs));   // prescribed flux DOFs and the multiplier
   VEM_TRY(check_device_errors(h, "right-hand side"));
   h->rhs_ready = true;
   return VEM_OK;

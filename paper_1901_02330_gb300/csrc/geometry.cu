@@ -158,14 +158,14 @@ __global__ void k_adjacency_fix(int64_t nf, const int *cnt, const int8_t *fbc, i
 }
 
 // Boundary-face load points: Dunavant degree-4 (6 points) on every fan
-// triangle (x_f, v_i, v_{i+1}) of every Dirichlet face.
+// triangle (x_f, v_i, v_{i+1}) of every Dirichlet or prescribed-flux face.
 __global__ void k_bface_points(int64_t nf, const int8_t *__restrict__ fbc,
                                const int64_t *__restrict__ off, const int64_t *__restrict__ fvp,
                                const int32_t *__restrict__ fv, const double *__restrict__ xyz,
                                const double *__restrict__ f_cent, double *out) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
        f += (int64_t)gridDim.x * blockDim.x) {
-    if (fbc[f] != 1) continue;
+    if (fbc[f] == 0) continue;
     const int64_t b = fvp[f];
     const int m = (int)(fvp[f + 1] - b);
     const double3 xf = load3(f_cent, f);
@@ -180,6 +180,32 @@ __global__ void k_bface_points(int64_t nf, const int8_t *__restrict__ fbc,
       }
     }
   }
+}
+
+// Outward unit normal and face flag at every boundary-face load point:
+// sigma n_f with sigma the orientation of the face in its one cell.
+__global__ void k_bface_info(int64_t nf, const int8_t *__restrict__ fbc, const int64_t *__restrict__ off,
+                             const double *__restrict__ f_norm, const int32_t *__restrict__ f_cell,
+                             const int32_t *__restrict__ f_loc, const int64_t *__restrict__ cfp,
+                             const int8_t *__restrict__ sig, double *nout, int8_t *flag) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    if (fbc[f] == 0) continue;
+    const double sg = (double)sig[cfp[f_cell[2 * f]] + f_loc[2 * f]];
+    const double3 n = scale3(load3(f_norm, f), sg);
+    for (int64_t o = off[f]; o < off[f + 1]; ++o) {
+      if (nout) store3(nout, o, n);
+      if (flag) flag[o] = fbc[f];
+    }
+  }
+}
+
+vem_status bface_info(vem_handle *h, double *nout, int8_t *flag) {
+  count_launch();
+  k_bface_info<<<grid_for(h->nf, 128), 128, 0, h->stream>>>(h->nf, h->fbc, h->bqp_off, h->f_norm, h->f_cell,
+                                                           h->f_loc, h->cf_ptr, h->cf_sigma, nout, flag);
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
 }
 
 vem_status geometry_build(vem_handle *h) {

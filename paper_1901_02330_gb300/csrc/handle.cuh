@@ -129,6 +129,15 @@ struct vem_handle {
 
   // ---- AMG for the inner Schur solve ----
   vem::AmgState *amg = nullptr;
+
+  // ---- prescribed-flux faces and the mean-zero pressure ----
+  int64_t n_flux_faces = 0, n_dir_faces = 0;
+  bool multiplier = false;                       // flux data on the whole boundary
+  double *xfix = nullptr;                        // [n] prescribed values (0 elsewhere)
+  double *rhs_corr = nullptr;                    // [n] A x_fix with the full matrix
+  double *npart = nullptr;                       // partial sums of the projections
+  double *bproj = nullptr;                       // [n_p] mean-free inner right-hand side
+  double lambda = 0.0;                           // the mean-zero multiplier
 };
 
 namespace vem {
@@ -182,6 +191,14 @@ vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, Ve
 vem_status classify_cells(vem_handle *h);
 // Adjoint contraction (adjoint.cu): g_c = lam_{u,c}^T M_c u_c per cell.
 vem_status adjoint_contract(vem_handle *h, const double *lam, const double *x, double *g);
+
+// Prescribed-flux faces and the mean-zero pressure (neumann.cu, element.cu,
+// geometry.cu)
+vem_status flux_fixed(vem_handle *h, double *xfix);
+vem_status bface_info(vem_handle *h, double *nout, int8_t *flag);
+vem_status neumann_rhs(vem_handle *h, double *rhs);
+vem_status neumann_mean_free(vem_handle *h, int64_t n, const double *b, double *out);
+vem_status neumann_shift(vem_handle *h, double *xp);
 
 // Exclusive scan of cnt[n] into out[n + 1] (out[0] = 0); *total = out[n]
 // (synchronises the stream).

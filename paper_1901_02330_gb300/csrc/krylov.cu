@@ -308,6 +308,12 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
 // S x = b with x, b FP64; the solve runs in FP64 or, with the mixed
 // precision option, entirely in FP32 (values, vectors, arithmetic).
 static vem_status pcg_solve(vem_handle *h, const VemOp &op, const double *b, double *x, double *wk, int *iters) {
+  if (h->multiplier && op.nbatch == 1) {
+    // singular S (constant pressures): solve for the consistent part of b
+    if (!h->bproj) VEM_TRY(dalloc_n(h, &h->bproj, (size_t)op.n_p));
+    VEM_TRY(neumann_mean_free(h, op.n_p, b, h->bproj));
+    b = h->bproj;
+  }
   if (h->opt.inner == VEM_INNER_AMG) {
     // FP64 CG; with the mixed option the V-cycle runs in FP32
     const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;

@@ -47,7 +47,8 @@ class vem_stats(C.Structure):
                 ("t_element_ms", C.c_double), ("t_scatter_ms", C.c_double), ("n_classes", C.c_int64),
                 ("t_schur_spmv_ms", C.c_double), ("n_schur_spmv", C.c_int64),
                 ("t_amg_setup_ms", C.c_double), ("amg_levels", C.c_int32),
-                ("t_saddle_spmv_ms", C.c_double), ("n_saddle_spmv", C.c_int64)]
+                ("t_saddle_spmv_ms", C.c_double), ("n_saddle_spmv", C.c_int64),
+                ("multiplier", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,6 +87,7 @@ _SIGS = {
     "vem_apply_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_residual_norm_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vem_bface_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_amg_setup": (C.c_int, [C.c_void_p]),
     "vem_amg_levels": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_amg_get_level": (C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 7),
@@ -239,11 +241,30 @@ class Solver:
             g = None if gD_qp is None else np.ascontiguousarray(gD_qp, dtype=np.float64)
             self._check(lib().vem_set_source(self._h, _ptr(f), _ptr(g)))
 
-    def set_data(self, f=None, gD=None):
-        """Evaluate callables f, gD at the library's quadrature points."""
+    def bface_info(self):
+        """(outward unit normals [n][3], face flags [n]) at the boundary points."""
+        n = C.c_int64()
+        self._check(lib().vem_quadrature_count(self._h, VEM_QP_BFACE, C.byref(n)))
+        nrm = np.zeros((n.value, 3))
+        flg = np.zeros(n.value, dtype=np.int8)
+        if n.value:
+            self._check(lib().vem_bface_info(self._h, _ptr(nrm), _ptr(flg)))
+        return nrm, flg
+
+    def set_data(self, f=None, gD=None, flux=None):
+        """Evaluate callables at the library's quadrature points: f at the cell
+        points, g_D on Dirichlet faces and u.n_out of the vector field flux on
+        prescribed-flux faces."""
         fq = f(self.quadrature_points(VEM_QP_CELL)) if f is not None else None
         pb = self.quadrature_points(VEM_QP_BFACE)
-        gq = gD(pb) if (gD is not None and pb.shape[0]) else None
+        gq = None
+        if pb.shape[0] and (gD is not None or flux is not None):
+            nrm, flg = self.bface_info()
+            gq = np.zeros(pb.shape[0])
+            if gD is not None and np.any(flg == 1):
+                gq[flg == 1] = gD(pb[flg == 1])
+            if flux is not None and np.any(flg == 2):
+                gq[flg == 2] = np.einsum("ij,ij->i", flux(pb[flg == 2]), nrm[flg == 2])
         self.set_source(fq, gq)
 
     def assemble(self):
