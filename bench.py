@@ -56,7 +56,7 @@ def parse():
                     help="inner Schur solver: Jacobi-PCG or AMG-preconditioned CG")
     ap.add_argument("--workload", default="hex128-k1",
                     choices=["hex128-k1", "hex8-e0-minres", "cvt200k-e0-mixed", "hex64-e0-batch64",
-                             "cvt100k-adjoint"],
+                             "cvt100k-adjoint", "cube32-k1-neumann"],
                     help="hex128-k1 is the headline; the others are the remaining configurations")
     ap.add_argument("--profile", action="store_true",
                     help="one step only (for an ncu launch list); prints a short JSON line")
@@ -524,6 +524,43 @@ def run_workload(a):
                      rel_err_vs_oracle_p=float(np.linalg.norm(p - pd) / np.linalg.norm(pd)),
                      note="host I/O per step; latency-bound (all data L2-resident)")
         s.close()
+    elif w == "cube32-k1-neumann":
+        # The paper's own setting on its 32^3 Cube mesh at k = 1 (Sec. 3 and
+        # Sec. 5, first strong-scaling table): flux data on the whole boundary,
+        # mean-zero pressure (one Lagrange multiplier), the polynomial solution
+        # of the convergence section, K = 1, GMRES with the Block-Schur
+        # preconditioner (diag(A) and S solved to 1e-12: exact in effect).
+        mesh = hex_mesh(32, bc=2)
+        prob = fields.paper_polynomial_problem()
+        s = vs.Solver(mesh, stream=sid, device_io=1, element=1, krylov=1, precond=0, restart=30, rtol=1e-8,
+                      inner=vs.VEM_INNER_AMG, inner_rtol=1e-12, inner_maxit=2000, maxit=3000)
+        s.set_data(prob.f, prob.gD, flux=prob.u)
+        n_u, n_p = s.sizes()
+        u = torch.empty(n_u, dtype=torch.float64, device="cuda")
+        p = torch.empty(n_p, dtype=torch.float64, device="cuda")
+
+        def step():
+            s.assemble()
+            return s.solve(u_out=u, p_out=p)[2]
+        ms, st = _timed(step, a.steps, a.warmup, stream)
+        # pressure error against the exact solution (cell centroids, mean-zero)
+        h = 1.0 / 32
+        g = (np.arange(32) + 0.5) * h
+        X = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+        pe = prob.p(X)
+        pe -= pe.mean()
+        s.close()
+        n = n_u + n_p
+        line = _line(a, "time-to-solution (rel.res 1e-8) and DOFs/s", n / (ms * 1e-3), "DOFs/s", ms, "f64",
+                     {"workload": w, "cells": mesh.n_cells, "dofs_with_multiplier": n + 1,
+                      "paper_dofs": 435201, "element": "paper k=1", "bc": "flux on the whole boundary, mean-zero p",
+                      "krylov": "FGMRES(30), right preconditioning", "precond": "Block-Schur (diag(A), S to 1e-12 by AMG-PCG)"},
+                     iterations=st["iterations"], inner_iterations=st["inner_iterations"], relres=st["relres"],
+                     multiplier=st["multiplier"],
+                     paper_block_schur_iterations=66,
+                     paper_note="paper: 66 GMRES iterations (PETSc GMRES, tolerance not stated), T_sol 50 s on 1 "
+                                "core / 9 s on 32 cores of 2x Xeon E5-2683 v4 (MUMPS for S); context only",
+                     pressure_max_err_vs_exact=float(np.abs(p.cpu().numpy() - pe).max()))
     elif w == "cvt200k-e0-mixed":
         # 200k seeds U[0,1]^3 (seed 0), 10 Lloyd iterations, E0, K = 10^U, U ~ U[-4,4] (seed 1)
         mesh = voronoi_mesh(200000, seed=0, lloyd=10)

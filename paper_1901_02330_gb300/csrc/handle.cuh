@@ -137,6 +137,7 @@ struct vem_handle {
   double *rhs_corr = nullptr;                    // [n] A x_fix with the full matrix
   double *npart = nullptr;                       // partial sums of the projections
   double *bproj = nullptr;                       // [n_p] mean-free inner right-hand side
+  int last_pcg_iters = 0;                        // iterations of the last inner solve
   double lambda = 0.0;                           // the mean-zero multiplier
 };
 

@@ -276,10 +276,14 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   };
   spmv_it(0);
   const int maxit = h->opt.inner_maxit;
-  const int chunk = 8;
+  // the host polls the convergence flag first after as many iterations as
+  // the previous inner solve took (consecutive solves need similar counts),
+  // then every 4; launches past convergence return at once
+  int chunk = h->last_pcg_iters > 0 ? h->last_pcg_iters : 8;
   int it = 0;
   while (it < maxit) {
     const int end = it + chunk < maxit ? it + chunk : maxit;
+    chunk = 4;
     for (; it < end; ++it) {
       count_launch();
       if (amg) {
@@ -301,6 +305,7 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
                 "inner PCG breakdown");
   *iters = (int)h->h_scal[S_PCG_IT];
   if (h->h_scal[S_PCG_DONE] == 0.0) *iters = maxit;   // cap reached: use the iterate
+  h->last_pcg_iters = *iters;
   if (debug_on()) fprintf(stderr, "[vem] pcg n=%lld iters=%d done=%g\n", (long long)n, *iters, h->h_scal[S_PCG_DONE]);
   return VEM_OK;
 }
