@@ -56,7 +56,7 @@ def parse():
                     help="inner Schur solver: Jacobi-PCG or AMG-preconditioned CG")
     ap.add_argument("--workload", default="hex128-k1",
                     choices=["hex128-k1", "hex8-e0-minres", "cvt200k-e0-mixed", "hex64-e0-batch64",
-                             "cvt100k-adjoint", "cube32-k1-neumann"],
+                             "cvt100k-adjoint", "cube32-k1-neumann", "optimality-k1"],
                     help="hex128-k1 is the headline; the others are the remaining configurations")
     ap.add_argument("--profile", action="store_true",
                     help="one step only (for an ncu launch list); prints a short JSON line")
@@ -561,6 +561,43 @@ def run_workload(a):
                      paper_note="paper: 66 GMRES iterations (PETSc GMRES, tolerance not stated), T_sol 50 s on 1 "
                                 "core / 9 s on 32 cores of 2x Xeon E5-2683 v4 (MUMPS for S); context only",
                      pressure_max_err_vs_exact=float(np.abs(p.cpu().numpy() - pe).max()))
+    elif w == "optimality-k1":
+        # Optimality under refinement (the paper's optimality test, at k = 1
+        # here): flux data on the whole boundary, mean-zero pressure, the
+        # polynomial solution, Block-Schur with S to 1e-12, FGMRES(30) to 1e-8,
+        # on Cube meshes n^3 and CVT meshes of growing size.
+        prob = fields.paper_polynomial_problem()
+        rows = []
+        total_ms = 0.0
+        cases = [("cube", n) for n in (8, 16, 24, 32, 48)] + [("cvt", n) for n in (1000, 8000, 27000, 64000)]
+        for kind, n in cases:
+            if kind == "cube":
+                mesh = hex_mesh(n, bc=2)
+            else:
+                mesh = voronoi_mesh(n, seed=7, lloyd=10)
+                mesh.face_bc = np.where(mesh.face_bc != 0, 2, 0).astype(np.int8)
+            s = vs.Solver(mesh, stream=sid, device_io=1, element=1, krylov=1, precond=0, restart=30, rtol=1e-8,
+                          inner=vs.VEM_INNER_AMG, inner_rtol=1e-12, inner_maxit=2000, maxit=3000)
+            s.set_data(prob.f, prob.gD, flux=prob.u)
+            n_u, n_p = s.sizes()
+            u = torch.empty(n_u, dtype=torch.float64, device="cuda")
+            p = torch.empty(n_p, dtype=torch.float64, device="cuda")
+
+            def step():
+                s.assemble()
+                return s.solve(u_out=u, p_out=p)[2]
+            ms, st = _timed(step, max(1, a.steps), 1, stream)
+            s.close()
+            total_ms += ms
+            rows.append({"mesh": f"{kind}{n}", "cells": mesh.n_cells, "dofs_with_multiplier": n_u + n_p + 1,
+                         "outer_iterations": st["iterations"], "inner_iterations": st["inner_iterations"],
+                         "relres": st["relres"], "ms": ms})
+        n_all = sum(r["dofs_with_multiplier"] for r in rows)
+        line = _line(a, "GMRES iterations under refinement (Block-Schur) and DOFs/s", n_all / (total_ms * 1e-3),
+                     "DOFs/s", total_ms, "f64",
+                     {"workload": w, "element": "paper k=1", "bc": "flux on the whole boundary, mean-zero p",
+                      "precond": "Block-Schur (diag(A), S to 1e-12 by AMG-PCG)", "krylov": "FGMRES(30)"},
+                     runs=rows)
     elif w == "cvt200k-e0-mixed":
         # 200k seeds U[0,1]^3 (seed 0), 10 Lloyd iterations, E0, K = 10^U, U ~ U[-4,4] (seed 1)
         mesh = voronoi_mesh(200000, seed=0, lloyd=10)
