@@ -104,6 +104,7 @@ struct AmgState {
   SellMat S0;               // level 0 operator (a view of the handle's S)
   const float *S0_val32 = nullptr;   // its FP32 values (the handle's copy)
   bool fp32 = false;                 // cycle in FP32
+  int64_t generation = 0;            // counts setups (graphs of the cycle key on it)
   float *cinv32 = nullptr;
   size_t c_cinv32 = 0;
   int nlev = 0;
@@ -1208,11 +1209,13 @@ vem_status amg_setup(vem_handle *h, const SellMat &Sm, const float *S_val32, boo
   VEM_CUDA(h, cudaEventElapsedTime(&ms, h->ev2, h->ev3));
   S->t_setup_ms = ms;
   S->valid = true;
+  ++S->generation;
   return VEM_OK;
 }
 
 bool amg_valid(const vem_handle *h) { return h->amg && h->amg->valid; }
 bool amg_is_fp32(const vem_handle *h) { return h->amg && h->amg->fp32; }
+int64_t amg_generation(const vem_handle *h) { return h->amg ? h->amg->generation : 0; }
 void amg_invalidate(vem_handle *h) {
   if (h->amg) h->amg->valid = false;
 }

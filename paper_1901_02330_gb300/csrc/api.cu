@@ -893,6 +893,8 @@ void vem_destroy(vem_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   vem::amg_free(h);
+  if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void *p : h->allocations) cudaFree(p);
   h->allocations.clear();
   if (h->h_err) cudaFreeHost(h->h_err);

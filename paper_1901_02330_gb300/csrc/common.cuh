@@ -53,6 +53,7 @@ int num_sms();
 
 // Process-wide count of kernel launches issued by the library.
 void count_launch();
+void count_launches(int64_t n);   // n may be negative (launches recorded into a graph)
 int64_t launch_count();
 
 // ---- reductions -----------------------------------------------------------

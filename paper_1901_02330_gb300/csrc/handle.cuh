@@ -138,6 +138,13 @@ struct vem_handle {
   double *npart = nullptr;                       // partial sums of the projections
   double *bproj = nullptr;                       // [n_p] mean-free inner right-hand side
   int last_pcg_iters = 0;                        // iterations of the last inner solve
+  int schur_tile = 1;                            // systems per tile of the batched Schur SpMV
+  // CUDA graph of a chunk of inner CG iterations (captured on cap_stream,
+  // launched on stream; rebuilt when any launch argument changes)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pcg_graph = nullptr;
+  std::vector<uintptr_t> pcg_graph_key;
+  int64_t pcg_graph_kernels = 0;
   double lambda = 0.0;                           // the mean-zero multiplier
 };
 
@@ -210,6 +217,7 @@ vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *ou
 vem_status amg_setup(vem_handle *h, const SellMat &S, const float *S_val32, bool fp32);
 bool amg_valid(const vem_handle *h);
 bool amg_is_fp32(const vem_handle *h);
+int64_t amg_generation(const vem_handle *h);
 void amg_invalidate(vem_handle *h);
 double amg_setup_ms(const vem_handle *h);
 int amg_levels(const vem_handle *h);

@@ -15,6 +15,9 @@
 //   V-cycle of the smoothed-aggregation AMG of amg.cu.
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
+#include <map>
+#include <tuple>
 
 #include "handle.cuh"
 
@@ -81,7 +84,7 @@ static void collect_saddle(vem_handle *h) {
 // w = S u with the three dot products (r,u), (w,u), (r,r), and its
 // last-arriving block turns them into alpha, beta and the convergence test;
 // one fused kernel then updates p, s, x, r, u.  Two launches per iteration.
-enum { CG_ALPHA = 24, CG_BETA, CG_GPREV, CG_APREV, CG_BB };
+enum { CG_ALPHA = 24, CG_BETA, CG_GPREV, CG_APREV, CG_BB, CG_ITER };
 
 // The converged flag read once per block and broadcast, so an early return is
 // uniform across the block.
@@ -119,56 +122,28 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_init(int64_t n, const double
       sc[CG_BB] = t;
       sc[S_PCG_DONE] = (t == 0.0) ? 1.0 : 0.0;
       sc[S_PCG_IT] = 0.0;
+      sc[CG_ITER] = 0.0;
       sc[S_PCG_BAD] = isfinite(t) ? 0.0 : 2.0;
       if (!isfinite(t)) sc[S_PCG_DONE] = 1.0;
     }
   }
 }
 
-// w = S u, partials of (r,u), (w,u), (r,r); the last block decides.  The
-// per-thread sums are in T, the block partials and scalars in FP64.
-#ifndef VEM_CG_MINB
-#define VEM_CG_MINB 4
-#endif
-template <class T>
-__global__ void __launch_bounds__(256, VEM_CG_MINB) k_cg_spmv(int64_t rows, int64_t nslices, int nbatch, int64_t stored,
-                                                 const int64_t *__restrict__ off,
-                                                 const int32_t *__restrict__ col,
-                                                 const T *__restrict__ val, const T *__restrict__ u,
-                                                 const T *__restrict__ r, T *__restrict__ w, double *part,
-                                                 double *sc, unsigned int *ctr, double tol2, int it,
-                                                 int nb_rr) {
-  if (block_done(sc)) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  T gam = 0, del = 0;
-  const int64_t tasks = nslices * nbatch;
-  for (int64_t tk = warp; tk < tasks; tk += nwarps) {
-    const int64_t bb = nbatch == 1 ? 0 : tk / nslices, s = tk - bb * nslices;
-    const T *ub = u + bb * rows;
-    const int64_t i = 32 * s + lane;
-    const int64_t gi = bb * rows + i;
-    // own-row operands first, so their loads overlap the row's gathers
-    T ui = 0, ri = 0;
-    if (i < rows) {
-      ui = __ldg(u + gi);
-      ri = __ldg(r + gi);
-    }
-    const T t = sell_row_dot<T, VEM_CG_KB, VEM_CG_PRED>(off, col, val + bb * stored, ub, s, lane);
-    if (i < rows) {
-      w[gi] = t;
-      gam += ri * ui;
-      del += t * ui;
-    }
-  }
-  block_partial((double)gam, slot(part, P_RZ0));
-  block_partial((double)del, slot(part, P_RZ1));
+// Block partials of (r,u) and (w,u); the last block to arrive turns them
+// and (r,r) (from the update or init kernel) into the convergence test,
+// alpha and beta.  The iteration number is a device counter, so every
+// iteration launches the same arguments (the launches can be graph-captured).
+__device__ __forceinline__ void cg_spmv_finish(double gam, double del, double *part, double *sc,
+                                               unsigned int *ctr, double tol2, int nb_rr) {
+  block_partial(gam, slot(part, P_RZ0));
+  block_partial(del, slot(part, P_RZ1));
   if (!last_block(ctr)) return;
   const double G = sum_partials_cg(slot(part, P_RZ0), gridDim.x);
   const double D = sum_partials_cg(slot(part, P_RZ1), gridDim.x);
-  const double R = sum_partials_cg(slot(part, P_RR), nb_rr);   // from the update (or init) kernel
+  const double R = sum_partials_cg(slot(part, P_RR), nb_rr);
   if (threadIdx.x != 0) return;
+  const int it = (int)sc[CG_ITER];
+  sc[CG_ITER] = (double)(it + 1);
   if (!isfinite(R) || !isfinite(G) || !isfinite(D)) {
     sc[S_PCG_BAD] = 2.0;
     sc[S_PCG_DONE] = 1.0;
@@ -194,6 +169,108 @@ __global__ void __launch_bounds__(256, VEM_CG_MINB) k_cg_spmv(int64_t rows, int6
   sc[CG_BETA] = beta;
   sc[CG_GPREV] = G;
   sc[CG_APREV] = alpha;
+}
+
+// w = S u with the partials of (r,u), (w,u) for one system: one warp per
+// slice, one thread per row.
+#ifndef VEM_CG_MINB
+#define VEM_CG_MINB 4
+#endif
+template <class T>
+__global__ void __launch_bounds__(256, VEM_CG_MINB) k_cg_spmv(int64_t rows, int64_t nslices, int64_t stored,
+                                                             const int64_t *__restrict__ off,
+                                                             const int32_t *__restrict__ col,
+                                                             const T *__restrict__ val, const T *__restrict__ u,
+                                                             const T *__restrict__ r, T *__restrict__ w,
+                                                             double *part, double *sc, unsigned int *ctr,
+                                                             double tol2, int nb_rr) {
+  if (block_done(sc)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  T gam = 0, del = 0;
+  for (int64_t s = warp; s < nslices; s += nwarps) {
+    const int64_t i = 32 * s + lane;
+    // own-row operands first, so their loads overlap the row's gathers
+    T ui = 0, ri = 0;
+    if (i < rows) {
+      ui = __ldg(u + i);
+      ri = __ldg(r + i);
+    }
+    const T t = sell_row_dot<T, VEM_CG_KB, VEM_CG_PRED>(off, col, val, u, s, lane);
+    if (i < rows) {
+      w[i] = t;
+      gam += ri * ui;
+      del += t * ui;
+    }
+  }
+  cg_spmv_finish((double)gam, (double)del, part, sc, ctr, tol2, nb_rr);
+}
+
+// The stacked systems of a batch (values of system b at val + b * stored,
+// vectors at b * rows), each warp task a tile of one 32-row slice times kR
+// consecutive systems: the column ids are read once per tile and serve kR
+// value streams and gathers (independent FMA chains).  timing != 0 runs the
+// products only (no partials, no scalars), for the autotuner.
+template <class T, int kR>
+__global__ void __launch_bounds__(256) k_cg_spmv_tiles(int64_t rows, int64_t nslices, int nbatch, int64_t stored,
+                                                      const int64_t *__restrict__ off,
+                                                      const int32_t *__restrict__ col,
+                                                      const T *__restrict__ val, const T *__restrict__ u,
+                                                      const T *__restrict__ r, T *__restrict__ w, double *part,
+                                                      double *sc, unsigned int *ctr, double tol2, int nb_rr,
+                                                      int timing) {
+  if (!timing && block_done(sc)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t groups = (nbatch + kR - 1) / kR;
+  T gam = 0, del = 0;
+  for (int64_t tk = warp; tk < nslices * groups; tk += nwarps) {
+    const int64_t g = tk / nslices, s = tk - g * nslices, b0 = g * kR;
+    const int64_t o = off[s];
+    const int wdt = (int)((off[s + 1] - o) >> 5);
+    const int64_t i = 32 * s + lane;
+    T acc[kR];
+#pragma unroll
+    for (int q = 0; q < kR; ++q) acc[q] = 0;
+    // kB entries per step (predicated on the slice width): all their column
+    // ids, then the kR x kB values and gathers, then the FMAs
+    constexpr int kB = kR >= 8 ? 1 : 8 / kR;
+    for (int j = 0; j < wdt; j += kB) {
+      int32_t c[kB];
+#pragma unroll
+      for (int t = 0; t < kB; ++t) c[t] = (j + t < wdt) ? __ldcs(col + o + 32 * (int64_t)(j + t) + lane) : 0;
+      T v[kR][kB], x[kR][kB];
+#pragma unroll
+      for (int q = 0; q < kR; ++q)
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+          const bool ok = (j + t < wdt) && (b0 + q < nbatch);
+          v[q][t] = ok ? __ldcs(val + (b0 + q) * stored + o + 32 * (int64_t)(j + t) + lane) : T(0);
+          x[q][t] = ok ? __ldg(u + (b0 + q) * rows + c[t]) : T(0);
+        }
+#pragma unroll
+      for (int q = 0; q < kR; ++q)
+#pragma unroll
+        for (int t = 0; t < kB; ++t)
+          if ((j + t < wdt) && (b0 + q < nbatch)) acc[q] += v[q][t] * x[q][t];
+    }
+    if (i < rows) {
+#pragma unroll
+      for (int q = 0; q < kR; ++q) {
+        if (b0 + q < nbatch) {
+          const int64_t gi = (b0 + q) * rows + i;
+          w[gi] = acc[q];
+          const T ui = u[gi];
+          gam += r[gi] * ui;
+          del += acc[q] * ui;
+        }
+      }
+    }
+  }
+  if (timing) return;
+  cg_spmv_finish((double)gam, (double)del, part, sc, ctr, tol2, nb_rr);
 }
 
 // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, and with the
@@ -229,6 +306,107 @@ __global__ void k_f32_to_f64(int64_t n, const float *__restrict__ a, double *b) 
 
 // Solve S x = b (length n_p) to relative residual inner_rtol with vectors,
 // matrix values and arithmetic in T; returns the iterations.
+// Capture the launches of body() on a private stream into the handle's CUDA
+// graph (kernels counted once per replay, not at capture).  Returns false,
+// with no graph, when capture or instantiation fails.
+template <class F>
+static bool capture_pcg_graph(vem_handle *h, const std::vector<uintptr_t> &key, F body) {
+  if (h->pcg_graph) {
+    cudaGraphExecDestroy(h->pcg_graph);
+    h->pcg_graph = nullptr;
+  }
+  h->pcg_graph_key.clear();
+  if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaStream_t saved = h->stream;
+  const int64_t l0 = launch_count();
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    h->stream = h->cap_stream;
+    body();
+    h->stream = saved;
+    ok = cudaStreamEndCapture(h->cap_stream, &g) == cudaSuccess && g != nullptr;
+  }
+  const int64_t kernels = launch_count() - l0;
+  count_launches(-kernels);
+  if (ok) ok = cudaGraphInstantiate(&h->pcg_graph, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    h->pcg_graph = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  h->pcg_graph_key = key;
+  h->pcg_graph_kernels = kernels;
+  return true;
+}
+
+// One launch of the tiled batched Schur SpMV with kR systems per tile.
+template <class T, int kR>
+static void launch_tiles_r(vem_handle *h, const VemOp &op, const T *sval, const T *u, const T *r, T *w,
+                           double tol2, int nb_rr, int timing) {
+  static int cap = 0;
+  if (cap == 0) cap = one_wave_blocks((const void *)k_cg_spmv_tiles<T, kR>);
+  const int64_t tasks = op.S.nslices * ((op.nbatch + kR - 1) / kR);
+  int64_t g = (tasks + 7) / 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  count_launch();
+  k_cg_spmv_tiles<T, kR><<<(int)g, 256, 0, h->stream>>>(op.S.rows, op.S.nslices, op.nbatch, op.S.stored, op.S.off,
+                                                        op.S.col, sval, u, r, w, h->part, h->scal, h->ctr + 1, tol2,
+                                                        nb_rr, timing);
+}
+
+template <class T>
+static void launch_tiles(vem_handle *h, const VemOp &op, const T *sval, const T *u, const T *r, T *w, double tol2,
+                         int nb_rr, int tile, int timing) {
+  switch (tile) {
+    case 1: launch_tiles_r<T, 1>(h, op, sval, u, r, w, tol2, nb_rr, timing); break;
+    case 2: launch_tiles_r<T, 2>(h, op, sval, u, r, w, tol2, nb_rr, timing); break;
+    case 4: launch_tiles_r<T, 4>(h, op, sval, u, r, w, tol2, nb_rr, timing); break;
+    default: launch_tiles_r<T, 8>(h, op, sval, u, r, w, tol2, nb_rr, timing); break;
+  }
+}
+
+// Autotuner of the tile shape of the batched Schur SpMV: on the first solve
+// of a shape (rows, slices, systems, value type) every candidate (1, 2, 4, 8
+// systems per 32-row tile) runs on the live vectors in timing mode (products
+// only), three launches each after one warm-up, timed with CUDA events on the
+// stream; the fastest is kept for the process.
+template <class T>
+static int tune_tiles(vem_handle *h, const VemOp &op, const T *sval, const T *u, const T *r, T *w, int nb_rr) {
+  static std::map<std::tuple<int64_t, int64_t, int>, int> best;
+  const auto key = std::make_tuple(op.S.rows, op.S.nslices, op.nbatch);
+  auto it = best.find(key);
+  if (it != best.end()) {
+    h->schur_tile = it->second;
+    return it->second;
+  }
+  int pick = 1;
+  float pick_ms = 1e30f;
+  for (int tile : {1, 2, 4, 8}) {
+    if (tile > 1 && tile > op.nbatch) break;
+    launch_tiles<T>(h, op, sval, u, r, w, 0.0, nb_rr, tile, 1);
+    cudaEventRecord(h->ev2, h->stream);
+    for (int k = 0; k < 3; ++k) launch_tiles<T>(h, op, sval, u, r, w, 0.0, nb_rr, tile, 1);
+    cudaEventRecord(h->ev3, h->stream);
+    cudaEventSynchronize(h->ev3);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev2, h->ev3) == cudaSuccess && ms < pick_ms) {
+      pick_ms = ms;
+      pick = tile;
+    }
+  }
+  cudaGetLastError();
+  best[key] = pick;
+  h->schur_tile = pick;
+  if (debug_on()) fprintf(stderr, "[vem] batched Schur SpMV tile: %d systems (%.3f ms / 3)\n", pick, pick_ms);
+  return pick;
+}
+
 template <class T>
 static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, const T *dinv, const double *b,
                               T *x, T *wk, int *iters) {
@@ -238,7 +416,7 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   const int nb = nblocks_vec(n);
   static int cap_s = 0;
   if (cap_s == 0) cap_s = one_wave_blocks((const void *)k_cg_spmv<T>);
-  int nbs = (int)((op.S.nslices * op.nbatch + 7) / 8);
+  int nbs = (int)((op.S.nslices + 7) / 8);
   if (nbs > cap_s) nbs = cap_s;
   if (nbs < 1) nbs = 1;
   double *sc = h->scal;
@@ -254,11 +432,17 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   if (amg) precondition();
   // every launch of the Schur SpMV is timed with a pair of events
   int ntimed = 0;
-  auto spmv_it = [&](int it) {
+  // stacked systems: the tile shape (systems per tile) chosen by the autotuner
+  const int tile = op.nbatch > 1 ? tune_tiles<T>(h, op, sval, u, r, w, nb) : 1;
+  auto spmv_it = [&](int) {
     if (ntimed < vem_handle::kTimed) cudaEventRecord(h->tev[2 * ntimed], s);
-    count_launch();
-    k_cg_spmv<T><<<nbs, 256, 0, s>>>(op.S.rows, op.S.nslices, op.nbatch, op.S.stored, op.S.off, op.S.col,
-                                     sval, u, r, w, h->part, sc, h->ctr + 1, tol2, it, nb);
+    if (op.nbatch == 1) {
+      count_launch();
+      k_cg_spmv<T><<<nbs, 256, 0, s>>>(op.S.rows, op.S.nslices, op.S.stored, op.S.off, op.S.col, sval, u, r, w,
+                                       h->part, sc, h->ctr + 1, tol2, nb);
+    } else {
+      launch_tiles<T>(h, op, sval, u, r, w, tol2, nb, tile, 0);
+    }
     if (ntimed < vem_handle::kTimed) cudaEventRecord(h->tev[2 * ntimed + 1], s);
     ++ntimed;
   };
@@ -280,19 +464,52 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   // the previous inner solve took (consecutive solves need similar counts),
   // then every 4; launches past convergence return at once
   int chunk = h->last_pcg_iters > 0 ? h->last_pcg_iters : 8;
+  // one iteration (update, preconditioner, SpMV) on the handle's current
+  // stream; every launch argument is the same in every iteration
+  auto iteration = [&]() {
+    cudaStream_t cs = h->stream;
+    count_launch();
+    if (amg) {
+      k_cg_update<T, false><<<nb, kRedThreads, 0, cs>>>(n, x, r, u, p, sv, w, dinv, sc, h->part);
+      precondition();
+    } else {
+      k_cg_update<T><<<nb, kRedThreads, 0, cs>>>(n, x, r, u, p, sv, w, dinv, sc, h->part);
+    }
+    if (op.nbatch == 1) {
+      count_launch();
+      k_cg_spmv<T><<<nbs, 256, 0, cs>>>(op.S.rows, op.S.nslices, op.S.stored, op.S.off, op.S.col, sval, u, r, w,
+                                        h->part, sc, h->ctr + 1, tol2, nb);
+    } else {
+      launch_tiles<T>(h, op, sval, u, r, w, tol2, nb, tile, 0);
+    }
+  };
+  // the iterations run as a CUDA graph of kGraphIters iterations, captured
+  // once per set of launch arguments (eager launches if capture fails)
+  constexpr int kGraphIters = 4;
+  uint64_t tol_bits = 0;
+  std::memcpy(&tol_bits, &tol2, sizeof(double));
+  const std::vector<uintptr_t> key = {
+      (uintptr_t)op.S.off, (uintptr_t)op.S.col, (uintptr_t)sval, (uintptr_t)u, (uintptr_t)r, (uintptr_t)w,
+      (uintptr_t)x, (uintptr_t)p, (uintptr_t)sv, (uintptr_t)dinv, (uintptr_t)h->part, (uintptr_t)sc,
+      (uintptr_t)h->ctr, (uintptr_t)n, (uintptr_t)nb, (uintptr_t)nbs, (uintptr_t)tile,
+      (uintptr_t)tol_bits,
+      (uintptr_t)amg, (uintptr_t)(amg ? amg_generation(h) : 0), sizeof(T), (uintptr_t)op.nbatch,
+      (uintptr_t)op.S.rows, (uintptr_t)op.S.stored};
+  bool graph = h->pcg_graph != nullptr && h->pcg_graph_key == key;
+  if (!graph) graph = capture_pcg_graph(h, key, [&]() {
+    for (int k = 0; k < kGraphIters; ++k) iteration();
+  });
   int it = 0;
   while (it < maxit) {
     const int end = it + chunk < maxit ? it + chunk : maxit;
     chunk = 4;
-    for (; it < end; ++it) {
-      count_launch();
-      if (amg) {
-        k_cg_update<T, false><<<nb, kRedThreads, 0, s>>>(n, x, r, u, p, sv, w, dinv, sc, h->part);
-        precondition();
-      } else {
-        k_cg_update<T><<<nb, kRedThreads, 0, s>>>(n, x, r, u, p, sv, w, dinv, sc, h->part);
+    if (graph) {
+      for (; it < end; it += kGraphIters) {
+        VEM_CUDA(h, cudaGraphLaunch(h->pcg_graph, s));
+        count_launches(h->pcg_graph_kernels);
       }
-      spmv_it(it + 1);
+    } else {
+      for (; it < end; ++it) iteration();
     }
     VEM_CUDA(h, cudaGetLastError());
     VEM_CUDA(h, cudaMemcpyAsync(h->h_scal, sc, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
