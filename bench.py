@@ -690,6 +690,10 @@ def run_workload(a):
                       "precond": "block upper-triangular, FP32 Jacobi-PCG 1e-5"},
                      iterations=st["iterations"], inner_iterations=st["inner_iterations"],
                      worst_relres=float(np.max(rel)),
+                     schur_tile_systems=st["schur_tile"],
+                     schur_tile_note="systems per 32-row tile of the batched Schur SpMV, picked by the autotuner "
+                                     "from 1, 2, 4, 8 (timed on the live vectors at the first solve)",
+                     cuda_graphs="inner CG iterations replayed as a CUDA graph of 4 iterations",
                      sequential_fp64={"systems_timed": m8, "ms_per_system": ms_seq / m8,
                                       "ms_for_all": ms_seq / m8 * nb},
                      speedup_vs_sequential_fp64=(ms_seq / m8 * nb) / ms,

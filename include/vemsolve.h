@@ -150,6 +150,8 @@ typedef struct {
   int64_t n_saddle_spmv;     /* its timed launches (at most 16 per solve)   */
   double multiplier;         /* the mean-zero Lagrange multiplier (flux     */
                              /* data on the whole boundary; 0 otherwise)    */
+  int32_t schur_tile;        /* batched solves: systems per tile of the     */
+                             /* Schur SpMV chosen by the autotuner          */
 } vem_stats;
 
 /* Fill *opt with the defaults: E0, FGMRES(30), block-diagonal, Jacobi-PCG

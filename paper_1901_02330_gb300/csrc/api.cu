@@ -707,6 +707,7 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   st.t_solve_ms = ms;
+  st.schur_tile = h->schur_tile;
   if (r != VEM_OK && r != VEM_ERR_NOT_CONVERGED) {
     if (stats) *stats = st;
     return r;

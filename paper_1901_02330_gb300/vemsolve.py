@@ -48,7 +48,7 @@ class vem_stats(C.Structure):
                 ("t_schur_spmv_ms", C.c_double), ("n_schur_spmv", C.c_int64),
                 ("t_amg_setup_ms", C.c_double), ("amg_levels", C.c_int32),
                 ("t_saddle_spmv_ms", C.c_double), ("n_saddle_spmv", C.c_int64),
-                ("multiplier", C.c_double)]
+                ("multiplier", C.c_double), ("schur_tile", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
