@@ -1,6 +1,6 @@
 """Full-size parity: the 128^3 paper-k=1 workload (2,097,152 cells,
 27,410,432 unknowns) in the launch configuration the benchmark times:
-FGMRES(30), block upper-triangular preconditioner, inner Jacobi-PCG 1e-8,
+FGMRES(30), block upper-triangular preconditioner, inner AMG-PCG 1e-8,
 rtol 1e-8, device-resident inputs and outputs.
 
 The oracle cannot assemble 27 M unknowns, so it builds sampled rows of
@@ -100,7 +100,7 @@ def test_hex128_k1_sampled_rows(vs):
     stream = torch.cuda.current_stream().cuda_stream
     s = vs.Solver(mesh, stream=stream, device_io=1, element=vs.VEM_ELEMENT_K1, krylov=vs.VEM_KRYLOV_FGMRES,
                   restart=30, precond=vs.VEM_PREC_BLOCK_TRI, rtol=1e-8, inner_rtol=1e-8, inner_maxit=2000,
-                  maxit=1000)
+                  maxit=1000, inner=vs.VEM_INNER_AMG)
     try:
         s.set_coefficient(K)
         s.set_data(prob.f, prob.gD)
