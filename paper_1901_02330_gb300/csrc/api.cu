@@ -206,7 +206,8 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
   VEM_CUDA(h, cudaEventCreate(&h->ev3));
   for (auto &e : h->tev) VEM_CUDA(h, cudaEventCreate(&e));
   for (auto &e : h->aev) VEM_CUDA(h, cudaEventCreate(&e));
-  return geometry_build(h);
+  VEM_TRY(geometry_build(h));
+  return classify_cells(h);   // congruence classes: a property of the mesh
 }
 
 static vem_status ensure_rhs(vem_handle *h) {
@@ -505,6 +506,7 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
       x0d = x0;
     }
     count_launch(); k_import_x<<<grid_for(h->n, 256), 256, 0, s>>>(h->n_u, h->n, x0d, x);
+    h->x_zero = x0d == nullptr;
     h->t_schur_spmv_ms = 0.0;
     h->n_schur_spmv = 0;
     h->t_saddle_spmv_ms = 0.0;

@@ -632,6 +632,11 @@ __global__ void k_class_assign(int64_t nc, int nfd, int nid, const int32_t *__re
 }
 
 vem_status classify_cells(vem_handle *h) {
+  // the classes are a property of the mesh (and of the element's local sizes
+  // and the reuse option): computed once per handle, with the geometry
+  if (h->cls_valid && h->cls_nfd == h->nfd && h->cls_nid == h->nid && h->cls_reuse == h->opt.reuse)
+    return VEM_OK;
+  h->cls_valid = false;
   cudaStream_t s = h->stream;
   const int T = 256;
   const int64_t nc = h->nc;
@@ -706,6 +711,10 @@ vem_status classify_cells(vem_handle *h) {
     VEM_TRY(dalloc_n(h, &h->Bloc, (size_t)bt));
     h->b_total = bt;
   }
+  h->cls_valid = true;
+  h->cls_nfd = h->nfd;
+  h->cls_nid = h->nid;
+  h->cls_reuse = h->opt.reuse;
   return VEM_OK;
 }
 

@@ -73,6 +73,8 @@ struct vem_handle {
   int32_t *cls_of = nullptr;                     // [nc] class of every cell
   int32_t *cls_rep = nullptr;                    // [nc] representative cell of every class
   int64_t ncls = 0;
+  bool cls_valid = false;                        // classes of the current layout and reuse option
+  int cls_nfd = 0, cls_nid = 0, cls_reuse = -1;
   double lref = 1.0;                             // mesh bounding-box diagonal
   void *cls_scratch = nullptr;                   // classification scratch
   size_t cls_scratch_bytes = 0;
@@ -138,6 +140,7 @@ struct vem_handle {
   double *npart = nullptr;                       // partial sums of the projections
   double *bproj = nullptr;                       // [n_p] mean-free inner right-hand side
   int last_pcg_iters = 0;                        // iterations of the last inner solve
+  bool x_zero = false;                           // the solve starts from x = 0
   int schur_tile = 1;                            // systems per tile of the batched Schur SpMV
   // CUDA graph of a chunk of inner CG iterations (captured on cap_stream,
   // launched on stream; rebuilt when any launch argument changes)

@@ -560,7 +560,7 @@ __global__ void k_residual(int64_t n, const double *__restrict__ b, const double
   double rr = 0.0, bb = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double ri = b[i] - Ax[i];
+    const double ri = Ax ? b[i] - Ax[i] : b[i];   // Ax == NULL: x = 0
     r[i] = ri;
     rr += ri * ri;
     bb += b[i] * b[i];
@@ -835,12 +835,16 @@ static vem_status precond(vem_handle *h, const VemOp &op, const double *v, doubl
 }
 
 // true relative residual ||b - A x|| / ||b|| (synchronises)
-static vem_status true_relres(vem_handle *h, const VemOp &op, const double *rhs, const double *x, double *tmp, double *rel) {
+// ||b - A x|| / ||b||, leaving b - A x in tmp and its partial sums in the
+// P_R2 / P_B2 slots.  x_zero: x is known to be 0 (no SpMV).
+static vem_status true_relres(vem_handle *h, const VemOp &op, const double *rhs, const double *x, double *tmp,
+                              double *rel, bool x_zero = false) {
   cudaStream_t s = h->stream;
   const int64_t n = op.n;
-  op_apply_timed(h, op, x, tmp);
+  if (!x_zero) op_apply_timed(h, op, x, tmp);
   const int nb = nblocks_vec(n);
-  count_launch(); k_residual<<<nb, kRedThreads, 0, s>>>(n, rhs, tmp, tmp, slot(h->part, P_R2), slot(h->part, P_B2));
+  count_launch(); k_residual<<<nb, kRedThreads, 0, s>>>(n, rhs, x_zero ? nullptr : tmp, tmp, slot(h->part, P_R2),
+                                                         slot(h->part, P_B2));
   count_launch(); k_read_sum<<<1, kRedThreads, 0, s>>>(slot(h->part, P_R2), nb, h->scal + S_R2);
   count_launch(); k_read_sum<<<1, kRedThreads, 0, s>>>(slot(h->part, P_B2), nb, h->scal + S_B2);
   VEM_CUDA(h, cudaGetLastError());
@@ -939,14 +943,15 @@ static vem_status run_fgmres(vem_handle *h, const VemOp &op, const double *rhs, 
   int inner = 0, it = 0;
   const int nbn = nblocks_vec(n);
   double rel = 1.0;
-  VEM_TRY(true_relres(h, op, rhs, x, tmp, &rel));
+  VEM_TRY(true_relres(h, op, rhs, x, tmp, &rel, h->x_zero));
+  h->x_zero = false;
   vem_status result = rel <= h->opt.rtol ? VEM_OK : VEM_ERR_NOT_CONVERGED;
   double bnorm = std::sqrt(h->h_scal[S_B2]);
   if (bnorm == 0.0) bnorm = 1.0;
   while (result != VEM_OK && it < h->opt.maxit) {
-    // V_0 = (b - A x) / beta
-    op_apply_timed(h, op, x, tmp);
-    count_launch(); k_residual<<<nbn, kRedThreads, 0, s>>>(n, rhs, tmp, V, slot(h->part, P_R2), slot(h->part, P_B2));
+    // V_0 = (b - A x) / beta: the residual and its partial sums are those of
+    // the last true_relres (x has not changed since)
+    VEM_CUDA(h, cudaMemcpyAsync(V, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     count_launch(); k_gm_start<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbn, L);
     count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, V, h->scal + GM_IBETA);
     int jd = 0;
@@ -1022,6 +1027,7 @@ vem_status krylov_solve(vem_handle *h, const VemOp &op, const double *rhs, doubl
   }
   if (cudaStreamSynchronize(h->stream) == cudaSuccess) collect_saddle(h);
   cudaGetLastError();
+  h->x_zero = false;
   return r;
 }
 
