@@ -652,8 +652,11 @@ def run_workload(a):
         mesh = hex_mesh(64)
         nb = 64
         Ks = np.stack([fields.K_lognormal(mesh.n_cells, seed=100 + b, sigma=2.0) for b in range(nb)])
+        # the outer count stays ~25 for any inner tolerance (27 at 1e-1, 25 at
+        # 1e-5), so the Schur blocks are solved to 1e-1, here and in the
+        # sequential FP64 comparison
         s = vs.Solver(mesh, stream=sid, element=0, krylov=1, precond=1, precision=1, rtol=1e-8,
-                      inner_rtol=1e-5, inner_maxit=5000, maxit=3000)
+                      inner_rtol=1e-1, inner_maxit=5000, maxit=3000)
         xc = s.quadrature_points(vs.VEM_QP_CELL)
         F = np.stack([fields.fourier_source(200 + b)(xc) for b in range(nb)])
         Kd = torch.from_numpy(Ks).cuda()
@@ -668,7 +671,7 @@ def run_workload(a):
         ms, (_, _, rel, st) = _timed(step, a.steps, a.warmup, stream)
         # the same 64 problems one at a time in plain FP64 (first 8, scaled)
         s64 = vs.Solver(mesh, stream=sid, device_io=1, element=0, krylov=1, precond=1, rtol=1e-8,
-                        inner_rtol=1e-8, inner_maxit=5000, maxit=3000)
+                        inner_rtol=1e-1, inner_maxit=5000, maxit=3000)
         u1 = torch.empty(n_u, dtype=torch.float64, device="cuda")
         p1 = torch.empty(n_p, dtype=torch.float64, device="cuda")
         m8 = 8
@@ -687,7 +690,7 @@ def run_workload(a):
                      {"workload": w, "systems": nb, "cells": mesh.n_cells, "n_per_system": n_u + n_p, "element": "E0",
                       "K": "exp(2 xi) per cell and system", "f": "8 Fourier modes per system",
                       "krylov": "FGMRES(30) on the stacked block-diagonal system",
-                      "precond": "block upper-triangular, FP32 Jacobi-PCG 1e-5"},
+                      "precond": "block upper-triangular, FP32 Jacobi-PCG 1e-1"},
                      iterations=st["iterations"], inner_iterations=st["inner_iterations"],
                      worst_relres=float(np.max(rel)),
                      schur_tile_systems=st["schur_tile"],
