@@ -45,6 +45,7 @@ class System:
     local: list = field(repr=False, default=None)
     dofmap: list = field(repr=False, default=None)
     vol: np.ndarray = field(repr=False, default=None)          # cell volumes
+    diam: np.ndarray = field(repr=False, default=None)         # cell diameters h_P
     fixed: np.ndarray = field(repr=False, default=None)        # prescribed flux DOFs
     fixed_val: np.ndarray = field(repr=False, default=None)
     multiplier: bool = False                                    # mean-zero pressure
@@ -106,9 +107,11 @@ def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False
     F = np.zeros(n_p)
     cells, locs, maps = [], [], []
     vol = np.zeros(mesh.n_cells)
+    diam = np.zeros(mesh.n_cells)
     for c in range(mesh.n_cells):
         cell = cell_geometry(mesh, c, faces, nq)
         vol[c] = cell.volume
+        diam[c] = cell.diameter
         loc = local_system(cell, spec, float(nu_cell[c]), f=f, gD=gD)
         dm = cell_dofmap(mesh, c, spec)
         pm = spec.nq * c + np.arange(spec.nq)
@@ -133,7 +136,7 @@ def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False
                   cells=cells if keep_local else None,
                   local=locs if keep_local else None,
                   dofmap=maps if keep_local else None,
-                  vol=vol, fixed=fixed, fixed_val=fixed_val,
+                  vol=vol, diam=diam, fixed=fixed, fixed_val=fixed_val,
                   multiplier=bool(np.any(mesh.face_bc == 2)) and not bool(np.any(mesh.face_bc == 1)))
 
 

@@ -90,24 +90,54 @@ def pcg(S, b, rtol=1e-12, maxit=10000, x0=None):
     return Result(x, maxit, np.linalg.norm(b - S @ x) / nb, False)
 
 
+def mesh_size(sys) -> float:
+    """h = (1/N_P) sum_P h_P, the mean cell diameter (Sec. 6, eq. meshSize)."""
+    return float(np.mean(sys.diam))
+
+
+def regularized(sys, gamma: float) -> sp.csr_matrix:
+    """A + B^T W^{-1} B with W = gamma I (Block-Reg, Sec. 5) over the free
+    flux DOFs: the prescribed-flux DOFs keep a unit row and column, as in the
+    eliminated saddle-point matrix."""
+    keep = np.ones(sys.n_u)
+    if sys.fixed is not None and sys.fixed.size:
+        keep[sys.fixed] = 0.0
+    K = sp.diags(keep)
+    BK = sys.B @ K
+    return (K @ sys.M @ K + (1.0 / gamma) * (BK.T @ BK) + sp.diags(1.0 - keep)).tocsr()
+
+
 class BlockPreconditioner:
     """Block-diagonal (kind='diag') or block upper-triangular (kind='tri')
     preconditioner with diag(M) for the flux block and S = B diag(M)^{-1} B^T
     for the pressure block.  inner='exact' factorises S (the paper's choice,
     with MUMPS there and SuperLU here); inner='pcg' uses Jacobi-PCG to
     inner_rtol; inner='amg' uses CG preconditioned by one V-cycle of the
-    smoothed-aggregation AMG of oracle/amg.py to inner_rtol."""
+    smoothed-aggregation AMG of oracle/amg.py to inner_rtol.
 
-    def __init__(self, sys, kind="diag", inner="exact", inner_rtol=1e-12, inner_maxit=10000):
+    kind='reg' is the paper's Block-Reg (Sec. 5): block-diagonal with one
+    V-cycle of the smoothed-aggregation AMG of A + B^T W^{-1} B (Chebyshev
+    smoothing, as in the GAMG preconditioner the paper names) for the flux
+    block and W^{-1} = I / gamma for the pressure block; gamma defaults to
+    h^2, h the mean cell diameter (the paper's choice)."""
+
+    def __init__(self, sys, kind="diag", inner="exact", inner_rtol=1e-12, inner_maxit=10000, gamma=None):
         self.n_u = sys.n_u
+        self.kind = kind
+        self.inner_iters = 0
+        if kind == "reg":
+            from . import amg
+            self.amg = amg
+            self.gamma = mesh_size(sys) ** 2 if gamma is None else float(gamma)
+            self.A_reg = regularized(sys, self.gamma)
+            self.H_reg = amg.setup(self.A_reg, smoother="chebyshev")
+            return
         self.B = sys.B
         self.dM = sys.M.diagonal().copy()
         self.S = schur(sys)
-        self.kind = kind
         self.inner = inner
         self.inner_rtol = inner_rtol
         self.inner_maxit = inner_maxit
-        self.inner_iters = 0
         self.fixed = sys.fixed if sys.fixed is not None else np.zeros(0, dtype=np.int64)
         if self.fixed.size:
             self.B = (self.B @ sp.diags(np.where(np.isin(np.arange(sys.n_u), self.fixed), 0.0, 1.0))).tocsr()
@@ -141,6 +171,8 @@ class BlockPreconditioner:
 
     def __call__(self, r):
         ru, rp = r[:self.n_u], r[self.n_u:]
+        if self.kind == "reg":
+            return np.concatenate([self.amg.vcycle(self.H_reg, ru), rp / self.gamma])
         if self.kind == "diag":
             return np.concatenate([ru / self.dM, self.solve_S(rp)])
         zp = -self.solve_S(rp)
@@ -249,7 +281,7 @@ def fgmres(A, b, Pinv, restart=30, rtol=1e-12, maxit=5000):
 
 
 def solve_krylov(sys, method="minres", kind="diag", inner="exact", rtol=1e-12,
-                 inner_rtol=1e-12, restart=30, maxit=5000):
+                 inner_rtol=1e-12, restart=30, maxit=5000, gamma=None):
     """Preconditioned Krylov solve; returns (u, p, Result) with physical p.
     With the mean-zero multiplier the pressure equations are made consistent
     first (F - c lambda with lambda = sum F / sum c, the multiplier's value),
@@ -259,10 +291,10 @@ def solve_krylov(sys, method="minres", kind="diag", inner="exact", rtol=1e-12,
     if sys.multiplier:
         lam = b[sys.n_u:].sum() / sys.vol.sum()
         b[sys.n_u:] -= sys.vol * lam
-    P = BlockPreconditioner(sys, kind=kind, inner=inner, inner_rtol=inner_rtol)
+    P = BlockPreconditioner(sys, kind=kind, inner=inner, inner_rtol=inner_rtol, gamma=gamma)
     if method == "minres":
-        if kind != "diag":
-            raise ValueError("MINRES needs the SPD block-diagonal preconditioner")
+        if kind not in ("diag", "reg"):
+            raise ValueError("MINRES needs an SPD block-diagonal preconditioner")
         res = minres(A, b, P, rtol=rtol, maxit=maxit)
     elif method == "fgmres":
         res = fgmres(A, b, P, restart=restart, rtol=rtol, maxit=maxit)
