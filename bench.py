@@ -56,7 +56,7 @@ def parse():
                     help="inner Schur solver: Jacobi-PCG or AMG-preconditioned CG")
     ap.add_argument("--workload", default="hex128-k1",
                     choices=["hex128-k1", "hex8-e0-minres", "cvt200k-e0-mixed", "hex64-e0-batch64",
-                             "cvt100k-adjoint", "cube32-k1-neumann", "optimality-k1"],
+                             "cvt100k-adjoint", "cube32-k1-neumann", "cube32-k1-blockreg", "optimality-k1"],
                     help="hex128-k1 is the headline; the others are the remaining configurations")
     ap.add_argument("--profile", action="store_true",
                     help="one step only (for an ncu launch list); prints a short JSON line")
@@ -561,6 +561,36 @@ def run_workload(a):
                      paper_note="paper: 66 GMRES iterations (PETSc GMRES, tolerance not stated), T_sol 50 s on 1 "
                                 "core / 9 s on 32 cores of 2x Xeon E5-2683 v4 (MUMPS for S); context only",
                      pressure_max_err_vs_exact=float(np.abs(p.cpu().numpy() - pe).max()))
+    elif w == "cube32-k1-blockreg":
+        # The same problem as cube32-k1-neumann with the paper's second
+        # preconditioner, Block-Reg (Sec. 5): one V-cycle of the smoothed-
+        # aggregation AMG (Chebyshev smoothing) of A + B^T B / gamma for the
+        # flux block, I / gamma for the pressure block, gamma = h^2.
+        mesh = hex_mesh(32, bc=2)
+        prob = fields.paper_polynomial_problem()
+        s = vs.Solver(mesh, stream=sid, device_io=1, element=1, krylov=1, precond=vs.VEM_PREC_BLOCK_REG,
+                      restart=30, rtol=1e-8, maxit=4000)
+        s.set_data(prob.f, prob.gD, flux=prob.u)
+        n_u, n_p = s.sizes()
+        u = torch.empty(n_u, dtype=torch.float64, device="cuda")
+        p = torch.empty(n_p, dtype=torch.float64, device="cuda")
+
+        def step():
+            s.assemble()
+            return s.solve(u_out=u, p_out=p)[2]
+        ms, st = _timed(step, a.steps, a.warmup, stream)
+        s.close()
+        n = n_u + n_p
+        line = _line(a, "time-to-solution (rel.res 1e-8) and DOFs/s", n / (ms * 1e-3), "DOFs/s", ms, "f64",
+                     {"workload": w, "cells": mesh.n_cells, "dofs_with_multiplier": n + 1,
+                      "paper_dofs": 435201, "element": "paper k=1", "bc": "flux on the whole boundary, mean-zero p",
+                      "krylov": "FGMRES(30), right preconditioning",
+                      "precond": "Block-Reg (AMG V-cycle of A + B^T B/gamma, Chebyshev(2) smoothing; I/gamma)"},
+                     iterations=st["iterations"], relres=st["relres"], reg_gamma=st["reg_gamma"],
+                     nnz_reg=st["nnz_reg"], amg_levels=st["amg_levels"], t_amg_setup_ms=st["t_amg_setup_ms"],
+                     paper_block_reg_iterations=84,
+                     paper_note="paper: 84 GMRES iterations with PETSc GAMG (1 core), T_sol 53 s on 1 core of "
+                                "2x Xeon E5-2683 v4; context only")
     elif w == "optimality-k1":
         # Optimality under refinement (the paper's optimality test, at k = 1
         # here): flux data on the whole boundary, mean-zero pressure, the

@@ -94,7 +94,20 @@ typedef struct {
 
 enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1 };
 enum { VEM_KRYLOV_MINRES = 0, VEM_KRYLOV_FGMRES = 1 };
-enum { VEM_PREC_BLOCK_DIAG = 0, VEM_PREC_BLOCK_TRI = 1 };
+/* Block preconditioners of the saddle-point system [M B^T; B 0] (Sec. 5):
+ *   BLOCK_DIAG  diag(diag(M), S) with S = B diag(M)^-1 B^T (Block-Schur,
+ *               eq. block_schur; the S block solved by the inner solver);
+ *   BLOCK_TRI   the block upper-triangular form with the same blocks;
+ *   BLOCK_REG   Block-Reg (eq. block_diag): diag(A_reg, W) with W = gamma I,
+ *               A_reg = M + B^T W^-1 B applied through one V-cycle of a
+ *               smoothed-aggregation AMG of A_reg (two Chebyshev steps of the
+ *               Jacobi iteration before and after the coarse correction) and
+ *               W^-1 = I / gamma; gamma = vem_options.reg_gamma, or h^2 with
+ *               h the mean cell diameter (eq. meshSize, the paper's choice)
+ *               when that is 0.  The V-cycle is symmetric positive definite,
+ *               so MINRES accepts it; no inner solve (inner, inner_rtol are
+ *               unused).  Not supported by vem_solve_batched. */
+enum { VEM_PREC_BLOCK_DIAG = 0, VEM_PREC_BLOCK_TRI = 1, VEM_PREC_BLOCK_REG = 2 };
 /* Inner solver for S: Jacobi-preconditioned CG, or CG preconditioned by one
  * V(1,1) cycle of a smoothed-aggregation AMG built from S (Vanek, Mandel &
  * Brezina 1996; aggregates from a distance-2 maximal independent set, Bell,
@@ -107,7 +120,7 @@ enum { VEM_PRECISION_FP64 = 0, VEM_PRECISION_MIXED = 1 };
 
 typedef struct {
   int element;        /* VEM_ELEMENT_*                                      */
-  int krylov;         /* VEM_KRYLOV_*; MINRES needs VEM_PREC_BLOCK_DIAG     */
+  int krylov;         /* VEM_KRYLOV_*; MINRES needs BLOCK_DIAG or BLOCK_REG */
   int restart;        /* FGMRES restart length m (1..256)                   */
   double rtol;        /* stop when ||b - A x||_2 <= rtol ||b||_2 (true residual) */
   int maxit;          /* outer iteration cap                                */
@@ -120,6 +133,7 @@ typedef struct {
                       /* arithmetic); the outer Krylov method, its A-apply, */
                       /* orthogonalisation and restart residuals stay FP64. */
                       /* Needs FGMRES; inner_rtol >= 1e-6 is meaningful.    */
+                      /* With BLOCK_REG: the V-cycle of A_reg in FP32.      */
   int device_io;      /* 0: vem_solve's x0/u_out/p_out are host pointers;   */
                       /* 1: device pointers (e.g. torch tensors' data_ptr)  */
   int reuse;          /* 1: cells that are translates of one another (same  */
@@ -127,6 +141,7 @@ typedef struct {
                       /* the mesh diagonal, and same face/vertex order)     */
                       /* share one evaluation of their geometry-only local  */
                       /* matrices, scaled by nu_P; 0: every cell evaluated. */
+  double reg_gamma;   /* BLOCK_REG: gamma > 0, or 0 for h^2 (default 0)     */
 } vem_options;
 
 typedef struct {
@@ -152,6 +167,8 @@ typedef struct {
                              /* data on the whole boundary; 0 otherwise)    */
   int32_t schur_tile;        /* batched solves: systems per tile of the     */
                              /* Schur SpMV chosen by the autotuner          */
+  double reg_gamma;          /* BLOCK_REG: the gamma used (0 otherwise)     */
+  int64_t nnz_reg;           /* BLOCK_REG: nonzeros of A_reg (0 otherwise)  */
 } vem_stats;
 
 /* Fill *opt with the defaults: E0, FGMRES(30), block-diagonal, Jacobi-PCG
@@ -304,9 +321,12 @@ vem_status vem_residual_norm_noalloc(int64_t rows, const int64_t *row_ptr, const
                                      const double *val, const double *x, const double *b,
                                      double *out, void *cuda_stream);
 
-/* ---- AMG inspection (VEM_INNER_AMG) ----
- * vem_amg_setup builds the hierarchy from the assembled S (vem_solve does
- * this on demand after every vem_assemble).  Level 0 is S itself.
+/* ---- AMG inspection ----
+ * which = VEM_AMG_SCHUR: the hierarchy of S (VEM_INNER_AMG); level 0 is S.
+ * which = VEM_AMG_REG: the hierarchy of A_reg (VEM_PREC_BLOCK_REG); level 0
+ * is A_reg (n_u rows).  vem_amg_setup builds the hierarchy from the current
+ * assembly (vem_solve does this on demand after every vem_assemble), with
+ * the handle's precision and, for A_reg, its reg_gamma.
  * vem_amg_levels: *nlev levels (at most 12); rows[l], nnz[l] of each
  * level's operator and nnz_p[l] of its prolongator (0 on the coarsest);
  * arrays of at least 12 entries, any may be NULL.
@@ -315,13 +335,16 @@ vem_status vem_residual_norm_noalloc(int64_t rows, const int64_t *row_ptr, const
  * outside the coarse space) and its prolongator P (rows x rows of level
  * l + 1; prow_ptr[rows + 1], pcol/pval[nnz_p]); any pointer may be NULL,
  * agg and P are left untouched on the coarsest level.
- * vem_amg_vcycle_device: x = V(b), one cycle, device vectors of n_p.
+ * vem_amg_vcycle_device: x = V(b), one cycle, device vectors of the
+ * level-0 size (n_p for S, n_u for A_reg).
  * All return VEM_ERR_BAD_INPUT before vem_amg_setup / after vem_assemble. */
-vem_status vem_amg_setup(vem_handle *h);
-vem_status vem_amg_levels(vem_handle *h, int32_t *nlev, int64_t *rows, int64_t *nnz, int64_t *nnz_p);
-vem_status vem_amg_get_level(vem_handle *h, int32_t level, int64_t *row_ptr, int32_t *col, double *val,
-                             int32_t *agg, int64_t *prow_ptr, int32_t *pcol, double *pval);
-vem_status vem_amg_vcycle_device(vem_handle *h, const double *b_dev, double *x_dev);
+enum { VEM_AMG_SCHUR = 0, VEM_AMG_REG = 1 };
+vem_status vem_amg_setup(vem_handle *h, int32_t which);
+vem_status vem_amg_levels(vem_handle *h, int32_t which, int32_t *nlev, int64_t *rows, int64_t *nnz,
+                          int64_t *nnz_p);
+vem_status vem_amg_get_level(vem_handle *h, int32_t which, int32_t level, int64_t *row_ptr, int32_t *col,
+                             double *val, int32_t *agg, int64_t *prow_ptr, int32_t *pcol, double *pval);
+vem_status vem_amg_vcycle_device(vem_handle *h, int32_t which, const double *b_dev, double *x_dev);
 
 /* Number of CUDA kernel launches the library has issued in this process
  * (all handles), for accounting the work of a timed region. */

@@ -1,11 +1,13 @@
-// Smoothed-aggregation algebraic multigrid for the Schur block S: the setup
-// (strength of connection, distance-2 independent set, aggregates, smoothed
-// prolongator, Galerkin coarse operators) and the symmetric V(1,1) cycle that
-// preconditions the inner CG.
+// Smoothed-aggregation algebraic multigrid: the setup (strength of
+// connection, distance-2 independent set, aggregates, smoothed prolongator,
+// Galerkin coarse operators) and the symmetric V-cycle.  Two hierarchies use
+// it: one of the Schur block S (the cycle preconditions the inner CG) and one
+// of the regularised flux block A + B^T B / gamma of Block-Reg.
 //
 // The paper solves S exactly inside Block-Schur and uses a smoothed-
 // aggregation AMG (PETSc GAMG) for the velocity block of Block-Reg (Sec. 5);
-// this AMG is the library's inner solver option for S.  Method: Vanek,
+// this AMG is the library's inner solver option for S and its Block-Reg
+// flux-block preconditioner.  Method: Vanek,
 // Mandel & Brezina, Computing 56 (1996) (smoothed aggregation); Bell, Dalton &
 // Olson, SIAM J. Sci. Comput. 34 (2012) (aggregates from a distance-2 maximal
 // independent set found in parallel rounds).  Rules, whose integer decisions
@@ -28,6 +30,11 @@
 //   coarsening stops at <= 64 rows, when a level would keep more than 4/5 of
 //     its rows or none, or at 12 levels; the coarsest level is inverted
 //     (dense Gauss-Jordan) up to 512 rows, else gets 4 Jacobi sweeps.
+// Smoothers: one damped-Jacobi step before and after the coarse correction
+// (the S hierarchy), or two steps of Chebyshev acceleration of the Jacobi
+// iteration (Saad, Iterative Methods for Sparse Linear Systems, 2nd ed.,
+// Alg. 12.1, on [rho/10, rho] with rho the Gershgorin bound above), the
+// default smoother of GAMG (the Block-Reg hierarchy).
 // The products P, A P and P^T (A P) are formed row by row, one thread per
 // row holding the row's distinct columns in a small sorted list and summing
 // contributions in a fixed order, so the hierarchy is bitwise reproducible.
@@ -45,8 +52,9 @@ constexpr int kDenseMax = 512;
 constexpr int kCoarseSweeps = 4;
 constexpr double kTheta0 = 0.08;
 constexpr int kCapP = 128;       // distinct columns of a row of P
-constexpr int kHashSlots = 512;  // per-warp hash table of a product row
-constexpr int kHashMax = 384;    // distinct columns of a product row
+constexpr int kHashBits = 9;     // per-warp hash table of a product row: 512 slots
+constexpr int kBigBits = 13;     // rows that overflow it: one warp, 8192 slots
+constexpr int kBigMax = 6144;    // distinct columns of a product row
 constexpr int kSortMax = 512;    // entries of a row sorted by one warp
 constexpr int kProdWarps = 4;    // warps per block of the product kernels
 constexpr int kCapThreadRow = 64;  // distinct columns of a thread-per-row product row
@@ -86,9 +94,15 @@ struct AmgLevel {
   float *wd32 = nullptr, *vec32 = nullptr;   // FP32 cycle: wd and x, x2, b, r
   size_t c_wd32 = 0, c_vec32 = 0;
   int32_t *agg = nullptr;
-  double *vec = nullptr;    // x, x2, b, r: four vectors of n
+  double *vec = nullptr;    // x, x2, b, r (and xc for Chebyshev): vectors of n
   size_t c_dinv = 0, c_agg = 0, c_vec = 0;
+  double *wdc = nullptr;    // Chebyshev: (2 rho_1 / delta) D^-1 (the second step)
+  size_t c_wdc = 0;
+  float *wdc32 = nullptr;
+  size_t c_wdc32 = 0;
   double omega = 0.0;
+  double rho = 0.0;         // Gershgorin bound of rho(D^-1 A)
+  double cheb_c = 0.0;      // Chebyshev: rho_1 rho_0 (the second step)
   int64_t n = 0, nc = 0;
   double *x() const { return vec; }
   double *x2() const { return vec + n; }
@@ -101,7 +115,9 @@ template <> float *AmgLevel::vx<float>(int k) const { return vec32 + k * n; }
 
 struct AmgState {
   AmgLevel lv[kMaxLevels];
-  SellMat S0;               // level 0 operator (a view of the handle's S)
+  int smoother = kSmoothJacobi;
+  bool pin_last = false;    // singular level-0 operator (constants): pin the coarsest
+  SellMat S0;               // level 0 operator (a view of the handle's S or A_reg)
   const float *S0_val32 = nullptr;   // its FP32 values (the handle's copy)
   bool fp32 = false;                 // cycle in FP32
   int64_t generation = 0;            // counts setups (graphs of the cycle key on it)
@@ -123,6 +139,7 @@ struct AmgState {
   unsigned long long *ctr = nullptr;              // [kMaxRounds + 4] counters / maxima
   CsrBuf AP;
   int64_t *cur = nullptr;   size_t c_cur = 0;     // transpose cursors
+  uint8_t *big = nullptr;   size_t c_big = 0;     // product rows for the large table
   double t_setup_ms = 0.0;
 };
 
@@ -138,10 +155,6 @@ static vem_status grow(vem_handle *h, T *&p, size_t &cap, size_t n) {
   return VEM_OK;
 }
 
-static AmgState *state(vem_handle *h) {
-  if (!h->amg) h->amg = new AmgState();
-  return h->amg;
-}
 
 // Device view of a SELL-32 (off != nullptr) or CSR matrix: entry k of row i
 // sits at position base + stride * k.
@@ -517,20 +530,31 @@ __global__ void __launch_bounds__(32 * kProdWarps) k_sort_rows(int64_t n, const 
 // in shared memory; every column's sum therefore runs in a fixed order.  The
 // count pass stores the number of distinct columns; the fill pass sorts the
 // table by column and writes the row.
-template <bool kFill>
-__global__ void __launch_bounds__(32 * kProdWarps) k_prod_rows(DMat X, const int64_t *__restrict__ yrp,
-                                                              const int32_t *__restrict__ ycol,
-                                                              const double *__restrict__ yval, int64_t *cnt,
-                                                              const int64_t *__restrict__ rp, int32_t *ocol,
-                                                              double *oval, int *err) {
-  __shared__ int32_t tk[kProdWarps][kHashSlots];
-  __shared__ double tv[kProdWarps][kHashSlots];
-  __shared__ int tn[kProdWarps];
+//
+// Two sizes: kW warps with 2^kBits slots each (dynamic shared memory), and
+// one warp with 2^kBigBits slots for the rows that overflow the small table
+// (the dense-ish coarse operators of wide stencils).  A row overflows when it
+// has more than 3/4 of its table's slots of distinct columns.  The small
+// count pass marks such rows (big[r] = 1, cnt[r] = 0) when big is given,
+// else it raises DEVERR_AMG_ROW; the small fill pass skips marked rows; the
+// large passes (only_big) take the marked rows alone.
+template <bool kFill, int kBits, int kW>
+__global__ void __launch_bounds__(32 * kW) k_prod_rows(DMat X, const int64_t *__restrict__ yrp,
+                                                      const int32_t *__restrict__ ycol,
+                                                      const double *__restrict__ yval, int64_t *cnt,
+                                                      const int64_t *__restrict__ rp, int32_t *ocol,
+                                                      double *oval, int *err, uint8_t *big, bool only_big) {
+  constexpr int kSlots = 1 << kBits, kMax = 3 * kSlots / 4;
+  extern __shared__ __align__(16) unsigned char prod_smem[];
+  double *tv = reinterpret_cast<double *>(prod_smem);
+  int32_t *tk = reinterpret_cast<int32_t *>(tv + (size_t)kW * kSlots);
+  int *tn = reinterpret_cast<int *>(tk + (size_t)kW * kSlots);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * kProdWarps + w, nw = (int64_t)gridDim.x * kProdWarps;
-  int32_t *K = tk[w];
-  double *V = tv[w];
+  const int64_t gw = (int64_t)blockIdx.x * kW + w, nw = (int64_t)gridDim.x * kW;
+  int32_t *K = tk + (size_t)w * kSlots;
+  double *V = tv + (size_t)w * kSlots;
   for (int64_t r = gw; r < X.rows; r += nw) {
+    if (big && (big[r] != 0) != only_big) continue;
     int64_t base;
     int st, L;
     X.row(r, base, st, L);
@@ -543,7 +567,7 @@ __global__ void __launch_bounds__(32 * kProdWarps) k_prod_rows(DMat X, const int
     }
     for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
     int bits = 5;
-    while (bits < 9 && (1ll << bits) < 2 * cand) ++bits;
+    while (bits < kBits && (1ll << bits) < 2 * cand) ++bits;
     const int slots = 1 << bits;
     for (int t = lane; t < slots; t += 32) {
       K[t] = -1;
@@ -572,14 +596,15 @@ __global__ void __launch_bounds__(32 * kProdWarps) k_prod_rows(DMat X, const int
         }
       }
       __syncwarp();
-      if (tn[w] > kHashMax) over = true;
+      if (tn[w] > kMax) over = true;
       if (over) break;
     }
     __syncwarp();
     const int m = tn[w];
     if (over) {
       if (lane == 0) {
-        atomicOr(err, DEVERR_AMG_ROW);
+        if (!kFill && big && !only_big) big[r] = 1;
+        else atomicOr(err, DEVERR_AMG_ROW);
         if (!kFill) cnt[r] = 0;
       }
       __syncwarp();
@@ -718,14 +743,17 @@ __device__ __forceinline__ bool cycle_done(const double *sc) {
 //   kPost   y = x + wd (b - A x)
 //   kAdd    y += A x
 //   kApply  y = A x
-enum { kResid = 0, kPost = 1, kAdd = 2, kApply = 3 };
+//   kCheb   y = x + c (x - xp) + wd (b - A x)   (xp == nullptr: xp = 0)
+// kCheb is the second Chebyshev step: x - xp is the first step's update.
+enum { kResid = 0, kPost = 1, kAdd = 2, kApply = 3, kCheb = 4 };
 
 template <int kMode, class T, class Ty>
 __device__ __forceinline__ void cycle_out(int64_t r, T t, const T *__restrict__ x, const T *__restrict__ b,
-                                          const T *__restrict__ wd, Ty *y) {
+                                          const T *__restrict__ wd, Ty *y, const T *__restrict__ xp, T c) {
   if (kMode == kResid) y[r] = (Ty)(b[r] - t);
   else if (kMode == kPost) y[r] = (Ty)(x[r] + wd[r] * (b[r] - t));
   else if (kMode == kAdd) y[r] += (Ty)t;
+  else if (kMode == kCheb) y[r] = (Ty)(x[r] + c * (x[r] - (xp ? xp[r] : (T)0)) + wd[r] * (b[r] - t));
   else y[r] = (Ty)t;
 }
 
@@ -748,7 +776,8 @@ template <class T, class Ty, int kMode>
 __global__ void __launch_bounds__(256) k_vc_sell(int64_t rows, int64_t nslices, const int64_t *__restrict__ off,
                                                  const int32_t *__restrict__ col, const T *__restrict__ val,
                                                  const T *__restrict__ x, const T *__restrict__ b,
-                                                 const T *__restrict__ wd, Ty *y, const double *sc) {
+                                                 const T *__restrict__ wd, Ty *y, const double *sc,
+                                                 const T *__restrict__ xp, T c) {
   if (cycle_done(sc)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -756,7 +785,7 @@ __global__ void __launch_bounds__(256) k_vc_sell(int64_t rows, int64_t nslices, 
   for (int64_t s = warp; s < nslices; s += nwarps) {
     const T acc = sell_row_dot<T, 8, true>(off, col, val, x, s, lane);
     const int64_t r = 32 * s + lane;
-    if (r < rows) cycle_out<kMode>(r, acc, x, b, wd, y);
+    if (r < rows) cycle_out<kMode>(r, acc, x, b, wd, y, xp, c);
   }
 }
 
@@ -767,7 +796,8 @@ template <int G, class T, class Ty, int kMode>
 __global__ void __launch_bounds__(256) k_vc_csr(int64_t rows, const int64_t *__restrict__ rp,
                                                 const int32_t *__restrict__ col, const T *__restrict__ val,
                                                 const T *__restrict__ x, const T *__restrict__ b,
-                                                const T *__restrict__ wd, Ty *y, const double *sc) {
+                                                const T *__restrict__ wd, Ty *y, const double *sc,
+                                                const T *__restrict__ xp, T c) {
   if (cycle_done(sc)) return;
   constexpr int R = 32 / G;   // rows per warp
   const int lane = threadIdx.x & 31, sub = lane & (G - 1), grp = lane / G;
@@ -782,7 +812,7 @@ __global__ void __launch_bounds__(256) k_vc_csr(int64_t rows, const int64_t *__r
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (r < rows && sub == 0) cycle_out<kMode>(r, acc, x, b, wd, y);
+    if (r < rows && sub == 0) cycle_out<kMode>(r, acc, x, b, wd, y, xp, c);
   }
 }
 
@@ -837,26 +867,26 @@ template <> const float *vals<float>(const SellBuf &M) { return M.val32; }
 
 template <int kMode, class T, class Ty>
 static void csr_launch(cudaStream_t s, const CsrBuf &M, const T *x, const T *b, const T *wd, Ty *y,
-                       const double *sc) {
+                       const double *sc, const T *xp = nullptr, T c = 0) {
   const int64_t warps = (M.rows * M.lanes + 31) / 32;
   const int g = warps_grid(warps);
   const T *v = vals<T>(M);
   count_launch();
   switch (M.lanes) {
-    case 2: k_vc_csr<2, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc); break;
-    case 4: k_vc_csr<4, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc); break;
-    case 8: k_vc_csr<8, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc); break;
-    case 16: k_vc_csr<16, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc); break;
-    default: k_vc_csr<32, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc); break;
+    case 2: k_vc_csr<2, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
+    case 4: k_vc_csr<4, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
+    case 8: k_vc_csr<8, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
+    case 16: k_vc_csr<16, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
+    default: k_vc_csr<32, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
   }
 }
 
 template <int kMode, class T, class Ty>
 static void sell_launch(cudaStream_t s, const SellMat &A, const T *val, const T *x, const T *b, const T *wd, Ty *y,
-                        const double *sc) {
+                        const double *sc, const T *xp = nullptr, T c = 0) {
   count_launch();
   k_vc_sell<T, Ty, kMode><<<warps_grid(A.nslices), 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, val, x, b, wd, y,
-                                                                sc);
+                                                                sc, xp, c);
 }
 
 __global__ void k_rp_counts(int64_t n, const int64_t *__restrict__ rp, int64_t *cnt) {
@@ -963,6 +993,18 @@ static double bits_to_double(unsigned long long b) {
 
 static DMat level_op(AmgState *S, int l) { return l == 0 ? dview(S->S0) : dview(S->lv[l].A); }
 
+// dynamic shared memory of k_prod_rows: values, keys, counts
+static size_t prod_smem_bytes(int bits, int warps) {
+  return (size_t)warps * ((size_t)(1 << bits) * (sizeof(double) + sizeof(int32_t)) + sizeof(int));
+}
+
+__global__ void k_count_flags(int64_t n, const uint8_t *__restrict__ f, unsigned long long *out) {
+  unsigned long long c = 0;
+  ROWS_LOOP(i, n) c += f[i] != 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 // C = X Y (two passes: count, fill).  With short_rows one thread per row
 // (at most 64 distinct columns, else the product is redone a warp per row).
 static vem_status product(vem_handle *h, AmgState *S, const DMat &X, const CsrBuf &Y, CsrBuf &C,
@@ -985,12 +1027,39 @@ static vem_status product(vem_handle *h, AmgState *S, const DMat &X, const CsrBu
                                                                ovf);
   } else {
     const int g = prod_grid(X.rows);
+    const size_t sm = prod_smem_bytes(kHashBits, kProdWarps), smb = prod_smem_bytes(kBigBits, 1);
+    VEM_CUDA(h, cudaFuncSetAttribute(k_prod_rows<false, kBigBits, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smb));
+    VEM_CUDA(h, cudaFuncSetAttribute(k_prod_rows<true, kBigBits, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smb));
+    VEM_TRY(grow(h, S->big, S->c_big, (size_t)X.rows));
+    VEM_CUDA(h, cudaMemsetAsync(S->big, 0, (size_t)X.rows, s));
     count_launch();
-    k_prod_rows<false><<<g, 32 * kProdWarps, 0, s>>>(X, Y.rp, Y.col, Y.val, S->cnt, nullptr, nullptr, nullptr,
-                                                      h->d_err);
+    k_prod_rows<false, kHashBits, kProdWarps><<<g, 32 * kProdWarps, sm, s>>>(
+        X, Y.rp, Y.col, Y.val, S->cnt, nullptr, nullptr, nullptr, h->d_err, S->big, false);
+    // rows that overflowed the small tables: count them again with a large one
+    unsigned long long *nbig = S->ctr + kMaxRounds + 2;
+    VEM_CUDA(h, cudaMemsetAsync(nbig, 0, sizeof(*nbig), s));
+    count_launch();
+    k_count_flags<<<rows_grid(X.rows), 256, 0, s>>>(X.rows, S->big, nbig);
+    unsigned long long nb = 0;
+    VEM_CUDA(h, cudaMemcpyAsync(&nb, nbig, sizeof(nb), cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nb, (int64_t)num_sms() * 2));
+    if (nb) {
+      count_launch();
+      k_prod_rows<false, kBigBits, 1><<<gb, 32, smb, s>>>(X, Y.rp, Y.col, Y.val, S->cnt, nullptr, nullptr, nullptr,
+                                                           h->d_err, S->big, true);
+    }
     VEM_TRY(csr_layout(h, C, X.rows, Y.cols, S->cnt));
     count_launch();
-    k_prod_rows<true><<<g, 32 * kProdWarps, 0, s>>>(X, Y.rp, Y.col, Y.val, nullptr, C.rp, C.col, C.val, h->d_err);
+    k_prod_rows<true, kHashBits, kProdWarps><<<g, 32 * kProdWarps, sm, s>>>(
+        X, Y.rp, Y.col, Y.val, nullptr, C.rp, C.col, C.val, h->d_err, S->big, false);
+    if (nb) {
+      count_launch();
+      k_prod_rows<true, kBigBits, 1><<<gb, 32, smb, s>>>(X, Y.rp, Y.col, Y.val, nullptr, C.rp, C.col, C.val,
+                                                          h->d_err, S->big, true);
+    }
   }
   VEM_CUDA(h, cudaGetLastError());
   return VEM_OK;
@@ -1054,6 +1123,7 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   const int64_t nc = nroot + nfree;
   if (nc == 0 || 5 * nc > 4 * n) return VEM_OK;
   const double rho = bits_to_double(mx[0]), rhof = bits_to_double(mx[1]);
+  L.rho = rho;
   L.omega = 4.0 / (3.0 * rho);
   const double omega_f = 4.0 / (3.0 * rhof);
 
@@ -1094,12 +1164,15 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   return VEM_OK;
 }
 
+// cycle vectors per level: x, x2, b, r, and xc for the Chebyshev smoother
+static int nvec(const AmgState *S) { return S->smoother == kSmoothChebyshev ? 5 : 4; }
+
 static vem_status level_vectors(vem_handle *h, AmgState *S, int l) {
   AmgLevel &L = S->lv[l];
   const DMat A = level_op(S, l);
   L.n = A.rows;
   VEM_TRY(grow(h, L.dinv, L.c_dinv, (size_t)L.n));
-  VEM_TRY(grow(h, L.vec, L.c_vec, 4 * (size_t)L.n));
+  VEM_TRY(grow(h, L.vec, L.c_vec, nvec(S) * (size_t)L.n));
   VEM_TRY(grow(h, S->dg, S->c_dg, (size_t)L.n));
   count_launch();
   k_amg_diag<<<rows_grid(L.n), 256, 0, h->stream>>>(A, S->dg, L.dinv, h->d_err);
@@ -1122,7 +1195,9 @@ static vem_status make_fp32(vem_handle *h, AmgState *S) {
   for (int l = 0; l < S->nlev; ++l) {
     AmgLevel &L = S->lv[l];
     VEM_TRY(to_f32(h, L.wd32, L.c_wd32, L.wd, L.n));
-    VEM_TRY(grow(h, L.vec32, L.c_vec32, 4 * (size_t)L.n));
+    // the Chebyshev second-step weights exist on the levels above the coarsest
+    if (S->smoother == kSmoothChebyshev && l + 1 < S->nlev) VEM_TRY(to_f32(h, L.wdc32, L.c_wdc32, L.wdc, L.n));
+    VEM_TRY(grow(h, L.vec32, L.c_vec32, nvec(S) * (size_t)L.n));
     if (l > 0) {
       if (L.As.m.rows) VEM_TRY(to_f32(h, L.As.val32, L.As.c_v32, L.As.m.val, L.As.m.stored));
       else VEM_TRY(to_f32(h, L.A.val32, L.A.c_v32, L.A.val, L.A.nnz));
@@ -1142,12 +1217,16 @@ static vem_status make_fp32(vem_handle *h, AmgState *S) {
   return VEM_OK;
 }
 
-vem_status amg_setup(vem_handle *h, const SellMat &Sm, const float *S_val32, bool fp32) {
-  AmgState *S = state(h);
+vem_status amg_setup(vem_handle *h, AmgState *&slot, const SellMat &Sm, const float *S_val32, bool fp32,
+                     bool pin_last, int smoother) {
+  if (!slot) slot = new AmgState();
+  AmgState *S = slot;
   S->valid = false;
   S->fp32 = fp32;
   S->S0_val32 = S_val32;
-  if (fp32 && !S_val32) return fail(h, VEM_ERR_BAD_INPUT, "FP32 AMG cycle without FP32 values of S");
+  S->pin_last = pin_last;
+  S->smoother = smoother;
+  if (fp32 && !S_val32) return fail(h, VEM_ERR_BAD_INPUT, "FP32 AMG cycle without FP32 values of the operator");
   cudaStream_t s = h->stream;
   VEM_CUDA(h, cudaEventRecord(h->ev2, s));
   if (!S->ctr) VEM_TRY(dalloc_n(h, &S->ctr, kMaxRounds + 4));
@@ -1176,19 +1255,34 @@ vem_status amg_setup(vem_handle *h, const SellMat &Sm, const float *S_val32, boo
     unsigned long long mx[2] = {0, 0};
     VEM_CUDA(h, cudaMemcpyAsync(mx, S->ctr, sizeof(mx), cudaMemcpyDeviceToHost, s));
     VEM_CUDA(h, cudaStreamSynchronize(s));
-    C.omega = 4.0 / (3.0 * bits_to_double(mx[0]));
+    C.rho = bits_to_double(mx[0]);
+    C.omega = 4.0 / (3.0 * C.rho);
   }
   for (int l = 0; l < S->nlev; ++l) {
     AmgLevel &L = S->lv[l];
     VEM_TRY(grow(h, L.wd, L.c_wd, (size_t)L.n));
-    count_launch();
-    k_scale_into<<<rows_grid(L.n), 256, 0, s>>>(L.n, L.dinv, L.omega, L.wd);
+    if (S->smoother == kSmoothChebyshev && l + 1 < S->nlev) {
+      // two steps on [lo, hi] = [rho/10, rho]: x1 = x0 + D^-1 r0 / theta,
+      // x2 = x1 + rho1 rho0 (x1 - x0) + (2 rho1 / delta) D^-1 r1
+      const double hi = L.rho, lo = hi / 10.0;
+      const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+      const double rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
+      L.cheb_c = rho1 * rho0;
+      VEM_TRY(grow(h, L.wdc, L.c_wdc, (size_t)L.n));
+      count_launch();
+      k_scale_into<<<rows_grid(L.n), 256, 0, s>>>(L.n, L.dinv, 1.0 / theta, L.wd);
+      count_launch();
+      k_scale_into<<<rows_grid(L.n), 256, 0, s>>>(L.n, L.dinv, 2.0 * rho1 / delta, L.wdc);
+    } else {
+      count_launch();
+      k_scale_into<<<rows_grid(L.n), 256, 0, s>>>(L.n, L.dinv, L.omega, L.wd);
+    }
   }
   if (C.n <= kDenseMax) {
     VEM_TRY(grow(h, S->cinv, S->c_cinv, (size_t)C.n * C.n));
     count_launch();
     k_dense_from<<<rows_grid(C.n), 256, 0, s>>>(CA, S->cinv);
-    if (h->multiplier) {
+    if (S->pin_last) {
       // S is singular (constants): keep the diagonal of the last coarse row
       // and column, drop their other entries
       count_launch();
@@ -1213,38 +1307,41 @@ vem_status amg_setup(vem_handle *h, const SellMat &Sm, const float *S_val32, boo
   return VEM_OK;
 }
 
-bool amg_valid(const vem_handle *h) { return h->amg && h->amg->valid; }
-bool amg_is_fp32(const vem_handle *h) { return h->amg && h->amg->fp32; }
-int64_t amg_generation(const vem_handle *h) { return h->amg ? h->amg->generation : 0; }
-void amg_invalidate(vem_handle *h) {
-  if (h->amg) h->amg->valid = false;
+bool amg_valid(const AmgState *S) { return S && S->valid; }
+bool amg_is_fp32(const AmgState *S) { return S && S->fp32; }
+int64_t amg_generation(const AmgState *S) { return S ? S->generation : 0; }
+void amg_invalidate(AmgState *S) {
+  if (S) S->valid = false;
 }
-double amg_setup_ms(const vem_handle *h) { return h->amg ? h->amg->t_setup_ms : 0.0; }
-int amg_levels(const vem_handle *h) { return amg_valid(h) ? h->amg->nlev : 0; }
-void amg_free(vem_handle *h) {
-  delete h->amg;   // device buffers are in h->allocations
-  h->amg = nullptr;
+double amg_setup_ms(const AmgState *S) { return S ? S->t_setup_ms : 0.0; }
+int amg_levels(const AmgState *S) { return amg_valid(S) ? S->nlev : 0; }
+void amg_free(AmgState *&S) {
+  delete S;   // device buffers are in the handle's allocation list
+  S = nullptr;
 }
 
 // One operator application of a level (SELL-32: S on level 0, copies above).
 template <int kMode, class T, class Ty>
 static void op_launch(cudaStream_t s, AmgState *S, int l, const T *x, const T *b, const T *wd, Ty *y,
-                      const double *sc) {
+                      const double *sc, const T *xp = nullptr, T c = 0) {
   if (l == 0) {
     const T *v;
     if constexpr (sizeof(T) == sizeof(double)) v = S->S0.val;
     else v = S->S0_val32;
-    sell_launch<kMode>(s, S->S0, v, x, b, wd, y, sc);
+    sell_launch<kMode>(s, S->S0, v, x, b, wd, y, sc, xp, c);
   } else if (S->lv[l].As.m.rows) {
-    sell_launch<kMode>(s, S->lv[l].As.m, vals<T>(S->lv[l].As), x, b, wd, y, sc);
+    sell_launch<kMode>(s, S->lv[l].As.m, vals<T>(S->lv[l].As), x, b, wd, y, sc, xp, c);
   } else {
-    csr_launch<kMode>(s, S->lv[l].A, x, b, wd, y, sc);
+    csr_launch<kMode>(s, S->lv[l].A, x, b, wd, y, sc, xp, c);
   }
 }
 
 template <class T> static const T *wdv(const AmgLevel &L);
 template <> const double *wdv<double>(const AmgLevel &L) { return L.wd; }
 template <> const float *wdv<float>(const AmgLevel &L) { return L.wd32; }
+template <class T> static const T *wdcv(const AmgLevel &L);
+template <> const double *wdcv<double>(const AmgLevel &L) { return L.wdc; }
+template <> const float *wdcv<float>(const AmgLevel &L) { return L.wdc32; }
 
 // x = V(b) on level l, values and vectors in T; the level's output is Ty
 // (FP64 on level 0 of an FP32 cycle, so u needs no conversion pass).
@@ -1284,8 +1381,27 @@ static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const do
   AmgLevel &C = S->lv[l + 1];
   T *xa = L.vx<T>(0), *r = L.vx<T>(3);
   T *cb = C.vx<T>(2), *cx = C.vx<T>(1);
+  const bool cheb = S->smoother == kSmoothChebyshev;
+  const T cc = (T)L.cheb_c;
+  const T *wdc = cheb ? wdcv<T>(L) : nullptr;
   count_launch();
   k_vc_pre<T><<<rows_grid(L.n), 256, 0, s>>>(L.n, b, wd, xa, sc);               // xa = w D^-1 b
+  if (cheb) {
+    // second Chebyshev step from x0 = 0: xc = xa + c xa + wdc (b - A xa)
+    T *xc = L.vx<T>(4);
+    op_launch<kCheb>(s, S, l, (const T *)xa, b, wdc, xc, sc, (const T *)nullptr, cc);
+    op_launch<kResid>(s, S, l, (const T *)xc, b, (const T *)nullptr, r, sc);    // r = b - A xc
+    if (L.Rs.m.rows) sell_launch<kApply>(s, L.Rs.m, vals<T>(L.Rs), (const T *)r, (const T *)nullptr,
+                                         (const T *)nullptr, cb, sc);
+    else csr_launch<kApply>(s, L.R, (const T *)r, (const T *)nullptr, (const T *)nullptr, cb, sc);
+    cycle<T, T>(h, S, l + 1, (const T *)cb, cx, sc);
+    if (L.Ps.m.rows) sell_launch<kAdd>(s, L.Ps.m, vals<T>(L.Ps), (const T *)cx, (const T *)nullptr,
+                                       (const T *)nullptr, xc, sc);              // xc += P x_c
+    else csr_launch<kAdd>(s, L.P, (const T *)cx, (const T *)nullptr, (const T *)nullptr, xc, sc);
+    op_launch<kPost>(s, S, l, (const T *)xc, b, wd, xa, sc);                     // xa = xc + wd (b - A xc)
+    op_launch<kCheb>(s, S, l, (const T *)xa, b, wdc, x, sc, (const T *)xc, cc);  // x = xa + c (xa - xc) + ...
+    return;
+  }
   op_launch<kResid>(s, S, l, (const T *)xa, b, (const T *)nullptr, r, sc);      // r = b - A xa
   if (L.Rs.m.rows) sell_launch<kApply>(s, L.Rs.m, vals<T>(L.Rs), (const T *)r, (const T *)nullptr,
                                        (const T *)nullptr, cb, sc);
@@ -1297,8 +1413,7 @@ static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const do
   op_launch<kPost>(s, S, l, (const T *)xa, b, wd, x, sc);                        // x = xa + wd (b - A xa)
 }
 
-void amg_vcycle(vem_handle *h, const double *b, double *x, const double *sc) {
-  AmgState *S = h->amg;
+void amg_vcycle(vem_handle *h, AmgState *S, const double *b, double *x, const double *sc) {
   if (!S->fp32) {
     cycle<double, double>(h, S, 0, b, x, sc);
     return;
@@ -1318,9 +1433,9 @@ static vem_status csr_to_host(vem_handle *h, const CsrBuf &C, int64_t *rp, int32
   return VEM_OK;
 }
 
-vem_status amg_level_info(vem_handle *h, int *nlev, int64_t *rows, int64_t *nnz, int64_t *nnz_p) {
-  if (!amg_valid(h)) return fail(h, VEM_ERR_BAD_INPUT, "no AMG hierarchy: call vem_amg_setup first");
-  AmgState *S = h->amg;
+vem_status amg_level_info(vem_handle *h, const AmgState *S, int *nlev, int64_t *rows, int64_t *nnz,
+                          int64_t *nnz_p) {
+  if (!amg_valid(S)) return fail(h, VEM_ERR_BAD_INPUT, "no AMG hierarchy: call vem_amg_setup first");
   *nlev = S->nlev;
   for (int l = 0; l < S->nlev; ++l) {
     if (rows) rows[l] = S->lv[l].n;
@@ -1330,10 +1445,9 @@ vem_status amg_level_info(vem_handle *h, int *nlev, int64_t *rows, int64_t *nnz,
   return VEM_OK;
 }
 
-vem_status amg_level_copy(vem_handle *h, int l, int64_t *rp, int32_t *col, double *val, int32_t *agg,
-                          int64_t *prp, int32_t *pcol, double *pval) {
-  if (!amg_valid(h)) return fail(h, VEM_ERR_BAD_INPUT, "no AMG hierarchy: call vem_amg_setup first");
-  AmgState *S = h->amg;
+vem_status amg_level_copy(vem_handle *h, AmgState *S, int l, int64_t *rp, int32_t *col, double *val,
+                          int32_t *agg, int64_t *prp, int32_t *pcol, double *pval) {
+  if (!amg_valid(S)) return fail(h, VEM_ERR_BAD_INPUT, "no AMG hierarchy: call vem_amg_setup first");
   if (l < 0 || l >= S->nlev) return fail(h, VEM_ERR_BAD_INPUT, "AMG level %d of %d", l, S->nlev);
   AmgLevel &L = S->lv[l];
   VEM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1348,6 +1462,6 @@ vem_status amg_level_copy(vem_handle *h, int l, int64_t *rp, int32_t *col, doubl
   return VEM_OK;
 }
 
-double amg_omega(const vem_handle *h, int l) { return amg_valid(h) && l < h->amg->nlev ? h->amg->lv[l].omega : 0.0; }
+double amg_omega(const AmgState *S, int l) { return amg_valid(S) && l < S->nlev ? S->lv[l].omega : 0.0; }
 
 }  // namespace vem

@@ -73,10 +73,12 @@ static vem_status check_options(vem_handle *h, const vem_options *o) {
     return fail(h, VEM_ERR_BAD_INPUT, "unknown element %d", o->element);
   if (o->krylov != VEM_KRYLOV_MINRES && o->krylov != VEM_KRYLOV_FGMRES)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown Krylov method %d", o->krylov);
-  if (o->precond != VEM_PREC_BLOCK_DIAG && o->precond != VEM_PREC_BLOCK_TRI)
+  if (o->precond != VEM_PREC_BLOCK_DIAG && o->precond != VEM_PREC_BLOCK_TRI && o->precond != VEM_PREC_BLOCK_REG)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown preconditioner %d", o->precond);
-  if (o->krylov == VEM_KRYLOV_MINRES && o->precond != VEM_PREC_BLOCK_DIAG)
-    return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs the SPD block-diagonal preconditioner");
+  if (o->krylov == VEM_KRYLOV_MINRES && o->precond == VEM_PREC_BLOCK_TRI)
+    return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs an SPD block-diagonal preconditioner");
+  if (!(o->reg_gamma >= 0.0) || !std::isfinite(o->reg_gamma))
+    return fail(h, VEM_ERR_BAD_INPUT, "reg_gamma %g", o->reg_gamma);
   if (o->inner != VEM_INNER_PCG && o->inner != VEM_INNER_AMG)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown inner solver %d", o->inner);
   if (o->precision != VEM_PRECISION_FP64 && o->precision != VEM_PRECISION_MIXED)
@@ -217,7 +219,9 @@ static vem_status ensure_rhs(vem_handle *h) {
 }
 
 static vem_status assemble_impl(vem_handle *h) {
-  amg_invalidate(h);
+  amg_invalidate(h->amg);
+  amg_invalidate(h->amg_reg);
+  h->areg_valid = false;
   VEM_CUDA(h, cudaEventRecord(h->ev0, h->stream));
   VEM_TRY(classify_cells(h));
   VEM_CUDA(h, cudaEventRecord(h->ev2, h->stream));
@@ -346,6 +350,7 @@ vem_status vem_set_options(vem_handle *h, const vem_options *opt) {
   if (!h || !opt) return VEM_ERR_BAD_INPUT;
   VEM_TRY(check_options(h, opt));
   const bool elem_changed = opt->element != h->opt.element;
+  if (elem_changed || opt->reg_gamma != h->opt.reg_gamma) h->areg_valid = false;
   h->opt = *opt;
   if (elem_changed) {
     set_layout(h);
@@ -511,7 +516,7 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     h->n_schur_spmv = 0;
     h->t_saddle_spmv_ms = 0.0;
     h->n_saddle_spmv = 0;
-    const bool had_amg = amg_valid(h);
+    const bool had_amg = amg_valid(h->amg), had_reg = amg_valid(h->amg_reg);
     cudaEventRecord(h->ev0, s);
     r = krylov_solve(h, single_op(h), h->rhs, x, &st);
     cudaEventRecord(h->ev1, s);
@@ -521,8 +526,12 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     st.t_solve_ms = ms;
     st.t_schur_spmv_ms = h->t_schur_spmv_ms;
     st.n_schur_spmv = h->n_schur_spmv;
-    st.t_amg_setup_ms = (!had_amg && amg_valid(h)) ? amg_setup_ms(h) : 0.0;
-    st.amg_levels = amg_levels(h);
+    const bool reg = h->opt.precond == VEM_PREC_BLOCK_REG;
+    st.t_amg_setup_ms = ((!had_amg && amg_valid(h->amg)) ? amg_setup_ms(h->amg) : 0.0) +
+                        ((!had_reg && amg_valid(h->amg_reg)) ? amg_setup_ms(h->amg_reg) : 0.0);
+    st.amg_levels = reg ? amg_levels(h->amg_reg) : amg_levels(h->amg);
+    st.reg_gamma = reg ? h->reg_gamma : 0.0;
+    st.nnz_reg = reg && h->areg_valid ? h->Areg.nnz : 0;
     st.t_saddle_spmv_ms = h->t_saddle_spmv_ms;
     st.n_saddle_spmv = h->n_saddle_spmv;
     if (tmp) dfree(h, tmp);
@@ -616,6 +625,8 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   if (!K || !u_out || !p_out) return fail(h, VEM_ERR_BAD_INPUT, "K / u_out / p_out: NULL");
   if (h->opt.inner == VEM_INNER_AMG)
     return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver is single-system (no batched solves)");
+  if (h->opt.precond == VEM_PREC_BLOCK_REG)
+    return fail(h, VEM_ERR_UNSUPPORTED, "Block-Reg is single-system (no batched solves)");
   if (h->n_flux_faces > 0)
     return fail(h, VEM_ERR_UNSUPPORTED, "prescribed-flux faces in batched solves");
   cudaStream_t s = h->stream;
@@ -863,30 +874,48 @@ vem_status vem_bface_info(vem_handle *h, double *normals_out, int8_t *flags_out)
   return r;
 }
 
-vem_status vem_amg_setup(vem_handle *h) {
-  if (!h) return VEM_ERR_BAD_INPUT;
-  if (!h->assembled) VEM_TRY(assemble_impl(h));
-  return amg_setup(h, h->S, h->S_val32, h->opt.precision == VEM_PRECISION_MIXED);
+static AmgState **amg_slot(vem_handle *h, int32_t which) {
+  if (which == VEM_AMG_SCHUR) return &h->amg;
+  if (which == VEM_AMG_REG) return &h->amg_reg;
+  return nullptr;
 }
 
-vem_status vem_amg_levels(vem_handle *h, int32_t *nlev, int64_t *rows, int64_t *nnz, int64_t *nnz_p) {
+vem_status vem_amg_setup(vem_handle *h, int32_t which) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  AmgState **slot = amg_slot(h, which);
+  if (!slot) return fail(h, VEM_ERR_BAD_INPUT, "unknown AMG hierarchy %d", which);
+  if (!h->assembled) VEM_TRY(assemble_impl(h));
+  const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
+  if (which == VEM_AMG_SCHUR) return amg_setup(h, h->amg, h->S, h->S_val32, fp32, h->multiplier, kSmoothJacobi);
+  if (!h->areg_valid || (fp32 && !h->areg_has32)) VEM_TRY(assemble_reg(h, fp32));
+  return amg_setup(h, h->amg_reg, h->Areg, h->Areg_val32, fp32, false, kSmoothChebyshev);
+}
+
+vem_status vem_amg_levels(vem_handle *h, int32_t which, int32_t *nlev, int64_t *rows, int64_t *nnz,
+                          int64_t *nnz_p) {
   if (!h || !nlev) return VEM_ERR_BAD_INPUT;
+  AmgState **slot = amg_slot(h, which);
+  if (!slot) return fail(h, VEM_ERR_BAD_INPUT, "unknown AMG hierarchy %d", which);
   int nl = 0;
-  VEM_TRY(amg_level_info(h, &nl, rows, nnz, nnz_p));
+  VEM_TRY(amg_level_info(h, *slot, &nl, rows, nnz, nnz_p));
   *nlev = nl;
   return VEM_OK;
 }
 
-vem_status vem_amg_get_level(vem_handle *h, int32_t level, int64_t *row_ptr, int32_t *col, double *val,
-                             int32_t *agg, int64_t *prow_ptr, int32_t *pcol, double *pval) {
+vem_status vem_amg_get_level(vem_handle *h, int32_t which, int32_t level, int64_t *row_ptr, int32_t *col,
+                             double *val, int32_t *agg, int64_t *prow_ptr, int32_t *pcol, double *pval) {
   if (!h) return VEM_ERR_BAD_INPUT;
-  return amg_level_copy(h, level, row_ptr, col, val, agg, prow_ptr, pcol, pval);
+  AmgState **slot = amg_slot(h, which);
+  if (!slot) return fail(h, VEM_ERR_BAD_INPUT, "unknown AMG hierarchy %d", which);
+  return amg_level_copy(h, *slot, level, row_ptr, col, val, agg, prow_ptr, pcol, pval);
 }
 
-vem_status vem_amg_vcycle_device(vem_handle *h, const double *b_dev, double *x_dev) {
+vem_status vem_amg_vcycle_device(vem_handle *h, int32_t which, const double *b_dev, double *x_dev) {
   if (!h || !b_dev || !x_dev) return VEM_ERR_BAD_INPUT;
-  if (!amg_valid(h)) return fail(h, VEM_ERR_BAD_INPUT, "no AMG hierarchy: call vem_amg_setup first");
-  amg_vcycle(h, b_dev, x_dev, nullptr);
+  AmgState **slot = amg_slot(h, which);
+  if (!slot) return fail(h, VEM_ERR_BAD_INPUT, "unknown AMG hierarchy %d", which);
+  if (!amg_valid(*slot)) return fail(h, VEM_ERR_BAD_INPUT, "no AMG hierarchy: call vem_amg_setup first");
+  amg_vcycle(h, *slot, b_dev, x_dev, nullptr);
   VEM_CUDA(h, cudaGetLastError());
   VEM_CUDA(h, cudaStreamSynchronize(h->stream));
   return VEM_OK;
@@ -895,7 +924,8 @@ vem_status vem_amg_vcycle_device(vem_handle *h, const double *b_dev, double *x_d
 void vem_destroy(vem_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  vem::amg_free(h);
+  vem::amg_free(h->amg);
+  vem::amg_free(h->amg_reg);
   if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void *p : h->allocations) cudaFree(p);

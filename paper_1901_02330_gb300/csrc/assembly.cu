@@ -10,6 +10,8 @@
 // shared face, then the pressure columns.  No atomics: every entry is a
 // fixed-order sum of at most two local values, so the result is
 // deterministic.
+#include <cmath>
+
 #include "handle.cuh"
 
 namespace vem {
@@ -204,7 +206,8 @@ __global__ void k_schur_fill(Layout L, const double *__restrict__ diagM, const i
 }
 
 // Eliminate the prescribed flux DOFs (faces with flag 2): their rows become
-// unit rows, their columns are zeroed elsewhere, diag(M) there is 1.
+// unit rows, their columns are zeroed elsewhere, diag(M) there is 1 (when
+// diagM is given).
 __global__ void k_eliminate(int64_t rows, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
                             const int32_t *__restrict__ col, double *val, int nfd, int64_t nf,
                             const int8_t *__restrict__ fbc, double *diagM) {
@@ -220,7 +223,99 @@ __global__ void k_eliminate(int64_t rows, const int64_t *__restrict__ off, const
       if (fixed_row) val[p] = (c == r) ? 1.0 : 0.0;
       else if (fixed_col) val[p] = 0.0;
     }
-    if (fixed_row) diagM[r] = 1.0;
+    if (fixed_row && diagM) diagM[r] = 1.0;
+  }
+}
+
+// ---- Block-Reg: A_reg = M + B^T W^-1 B, W = gamma I (paper Sec. 5) ----
+// B^T B = sum_P B_P^T B_P couples only DOFs of one cell (the pressure DOF of
+// P belongs to P alone), so A_reg has the pattern of M: row r of a face DOF
+// gathers the rows of the (at most two) cells of its face, an interior row
+// that of its cell, in the column order of the saddle matrix's flux part.
+// Entry (r, j) of cell P adds B_P(r) B_P(j) / gamma to nu_P M_P(r, j), with
+// B_P(j) = Bloc[b_off + j] (one pressure DOF per cell, k <= 1).
+__global__ void k_reg_count(Layout L, int64_t *cnt) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_u;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v;
+    if (r < L.nfd * L.nf) {
+      const int64_t f = r / L.nfd;
+      const int32_t c0 = L.f_cell[2 * f], c1 = L.f_cell[2 * f + 1];
+      v = nloc(L, c0) + (c1 >= 0 ? nloc(L, c1) - L.nfd : 0);
+    } else {
+      v = nloc(L, (r - L.nfd * L.nf) / L.nid);
+    }
+    cnt[r] = v;
+  }
+}
+
+__global__ void k_reg_fill(Layout L, const int64_t *__restrict__ off, int64_t nrows_pad, int32_t *col, double *val,
+                           const double *__restrict__ nu_scale, double ig) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows_pad;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s0 = off[r >> 5];
+    const int width = (int)((off[(r >> 5) + 1] - s0) >> 5);
+    const int64_t lane = r & 31;
+    int j = 0;
+#define PUT(c_, v_)                                   \
+  do {                                                \
+    const int64_t q_ = s0 + ((int64_t)j << 5) + lane; \
+    col[q_] = (int32_t)(c_);                          \
+    val[q_] = (v_);                                   \
+    ++j;                                              \
+  } while (0)
+    if (r >= L.n_u) {
+      // ghost row
+    } else if (r < L.nfd * L.nf) {
+      const int64_t f = r / L.nfd;
+      const int beta = (int)(r % L.nfd);
+      const int32_t c0 = L.f_cell[2 * f], c1 = L.f_cell[2 * f + 1];
+      const int l0 = L.f_loc[2 * f], l1 = L.f_loc[2 * f + 1];
+      const int n0 = nloc(L, c0);
+      const int jr0 = l0 * L.nfd + beta;
+      const double *M0 = mloc(L, c0) + (int64_t)jr0 * n0;
+      const double *B0 = L.Bloc + boff(L, c0);
+      const double w0 = nu_scale[c0], g0 = ig * B0[jr0];
+      const double *M1 = nullptr, *B1 = nullptr;
+      int n1 = 0;
+      double w1 = 0.0, g1 = 0.0;
+      if (c1 >= 0) {
+        n1 = nloc(L, c1);
+        const int jr1 = l1 * L.nfd + beta;
+        M1 = mloc(L, c1) + (int64_t)jr1 * n1;
+        B1 = L.Bloc + boff(L, c1);
+        w1 = nu_scale[c1];
+        g1 = ig * B1[jr1];
+      }
+      for (int jl = 0; jl < n0; ++jl) {
+        double v = w0 * M0[jl] + g0 * B0[jl];
+        const bool shared = (jl < n0 - L.nid) && (jl / L.nfd == l0);
+        if (c1 >= 0 && shared) {
+          const int j1 = l1 * L.nfd + jl % L.nfd;
+          v += w1 * M1[j1] + g1 * B1[j1];
+        }
+        PUT(gcol(L, c0, jl), v);
+      }
+      if (c1 >= 0) {
+        const int k1 = (n1 - L.nid) / L.nfd;
+        for (int jl = 0; jl < n1; ++jl) {
+          if (jl < L.nfd * k1 && jl / L.nfd == l1) continue;
+          PUT(gcol(L, c1, jl), w1 * M1[jl] + g1 * B1[jl]);
+        }
+      }
+    } else {
+      const int64_t q = r - L.nfd * L.nf;
+      const int64_t c = q / L.nid;
+      const int l = (int)(q % L.nid);
+      const int nl = nloc(L, c);
+      const int jr = nl - L.nid + l;
+      const double *Mr = mloc(L, c) + (int64_t)jr * nl;
+      const double *Bc = L.Bloc + boff(L, c);
+      const double wc = nu_scale[c], gc = ig * Bc[jr];
+      for (int jl = 0; jl < nl; ++jl) PUT(gcol(L, c, jl), wc * Mr[jl] + gc * Bc[jl]);
+    }
+    while (j < width) PUT(0, 0.0);
+#undef PUT
   }
 }
 
@@ -507,6 +602,55 @@ vem_status assemble_global(vem_handle *h) {
   // true nonzero counts (for statistics)
   VEM_TRY(sell_nnz(h, h->A));
   VEM_TRY(sell_nnz(h, h->S));
+  return VEM_OK;
+}
+
+vem_status assemble_reg(vem_handle *h, bool fp32) {
+  cudaStream_t s = h->stream;
+  Layout L{h->nfd, h->nid, h->nf, h->nc, h->n_u, h->cf_ptr, h->cf, h->f_cell, h->f_loc,
+           h->m_off, h->b_off, h->cls_of, h->Mloc, h->Bloc, h->fbc};
+  const int T = 256;
+  amg_invalidate(h->amg_reg);   // its level 0 is a view of the matrix rebuilt here
+  h->areg_valid = false;
+  // gamma = h^2 with h the mean cell diameter (eq. meshSize), unless given
+  double gamma = h->opt.reg_gamma;
+  if (!(gamma > 0.0)) {
+    double sum = 0.0;
+    VEM_TRY(device_sum(h, h->nc, h->c_diam, &sum));
+    const double hm = sum / (double)h->nc;
+    gamma = hm * hm;
+  }
+  if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(h, VEM_ERR_BAD_INPUT, "Block-Reg: gamma %g", gamma);
+  h->reg_gamma = gamma;
+  if (!h->cnt_buf) VEM_TRY(dalloc_n(h, &h->cnt_buf, (size_t)h->n + 1));
+  int64_t *cnt = h->cnt_buf;
+  count_launch(); k_reg_count<<<grid_for(h->n_u, T), T, 0, s>>>(L, cnt);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_TRY(sell_layout(h, h->Areg, h->n_u, cnt));
+  const int64_t npad = h->Areg.nslices * 32;
+  count_launch(); k_reg_fill<<<grid_for(npad, T), T, 0, s>>>(L, h->Areg.off, npad, h->Areg.col, h->Areg.val, h->nu,
+                                                          1.0 / gamma);
+  VEM_CUDA(h, cudaGetLastError());
+  if (h->n_flux_faces > 0) {
+    count_launch();
+    k_eliminate<<<grid_for(h->n_u, T), T, 0, s>>>(h->n_u, h->Areg.off, h->Areg.len, h->Areg.col, h->Areg.val,
+                                                 h->nfd, h->nf, h->fbc, nullptr);
+    VEM_CUDA(h, cudaGetLastError());
+  }
+  if (fp32) {
+    if (h->areg32_stored != h->Areg.stored) {
+      dfree(h, h->Areg_val32);
+      h->Areg_val32 = nullptr;
+      VEM_TRY(dalloc_n(h, &h->Areg_val32, (size_t)h->Areg.stored));
+      h->areg32_stored = h->Areg.stored;
+    }
+    count_launch();
+    k_f64_to_f32<<<grid_for(h->Areg.stored, T), T, 0, s>>>(h->Areg.stored, h->Areg.val, h->Areg_val32);
+    VEM_CUDA(h, cudaGetLastError());
+  }
+  VEM_TRY(sell_nnz(h, h->Areg));
+  h->areg_has32 = fp32;
+  h->areg_valid = true;
   return VEM_OK;
 }
 

@@ -10,7 +10,7 @@
 #include "common.cuh"
 
 namespace vem {
-struct AmgState;   // smoothed-aggregation hierarchy of S (amg.cu)
+struct AmgState;   // smoothed-aggregation hierarchy (amg.cu)
 }
 
 // The operator a Krylov solve works on: the saddle matrix A, the Schur
@@ -132,6 +132,15 @@ struct vem_handle {
   // ---- AMG for the inner Schur solve ----
   vem::AmgState *amg = nullptr;
 
+  // ---- Block-Reg: A_reg = M + B^T B / gamma and its AMG ----
+  vem::SellMat Areg;                             // n_u rows, the flux pattern of the saddle matrix
+  float *Areg_val32 = nullptr;                   // FP32 values (FP32 cycle)
+  int64_t areg32_stored = 0;
+  bool areg_valid = false;                       // A_reg matches the current assembly
+  bool areg_has32 = false;                       // Areg_val32 matches A_reg
+  double reg_gamma = 0.0;                        // gamma of the current A_reg
+  vem::AmgState *amg_reg = nullptr;
+
   // ---- prescribed-flux faces and the mean-zero pressure ----
   int64_t n_flux_faces = 0, n_dir_faces = 0;
   bool multiplier = false;                       // flux data on the whole boundary
@@ -215,23 +224,37 @@ vem_status neumann_shift(vem_handle *h, double *xp);
 // (synchronises the stream).
 vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *out, int64_t *total);
 
-// Smoothed-aggregation AMG for S (amg.cu)
-// S_val32: FP32 values of S in its SELL layout, used by an FP32 cycle (fp32)
-vem_status amg_setup(vem_handle *h, const SellMat &S, const float *S_val32, bool fp32);
-bool amg_valid(const vem_handle *h);
-bool amg_is_fp32(const vem_handle *h);
-int64_t amg_generation(const vem_handle *h);
-void amg_invalidate(vem_handle *h);
-double amg_setup_ms(const vem_handle *h);
-int amg_levels(const vem_handle *h);
-void amg_free(vem_handle *h);
-// x = V(b) on the finest level (device vectors of n_p); sc: the PCG scalars
-// whose first entry, when non-zero, turns the launches into no-ops (NULL: run)
-void amg_vcycle(vem_handle *h, const double *b, double *x, const double *sc);
-vem_status amg_level_info(vem_handle *h, int *nlev, int64_t *rows, int64_t *nnz, int64_t *nnz_p);
-vem_status amg_level_copy(vem_handle *h, int l, int64_t *rp, int32_t *col, double *val, int32_t *agg,
-                          int64_t *prp, int32_t *pcol, double *pval);
-double amg_omega(const vem_handle *h, int l);
+// Smoothed-aggregation AMG (amg.cu): h->amg of S, h->amg_reg of A_reg.
+// setup builds (or rebuilds) the hierarchy in *slot from the level-0
+// operator A0 (kept as a view); A0_val32: its FP32 values in the same SELL
+// layout, used by an FP32 cycle (fp32); pin_last: A0 is singular with the
+// constants as null space; smoother: kSmooth*.
+enum { kSmoothJacobi = 0, kSmoothChebyshev = 1 };
+vem_status amg_setup(vem_handle *h, AmgState *&slot, const SellMat &A0, const float *A0_val32, bool fp32,
+                     bool pin_last, int smoother);
+bool amg_valid(const AmgState *S);
+bool amg_is_fp32(const AmgState *S);
+int64_t amg_generation(const AmgState *S);
+void amg_invalidate(AmgState *S);
+double amg_setup_ms(const AmgState *S);
+int amg_levels(const AmgState *S);
+void amg_free(AmgState *&S);
+// x = V(b) on the finest level (device vectors of the level-0 size); sc: the
+// PCG scalars whose first entry, when non-zero, turns the launches into
+// no-ops (NULL: run)
+void amg_vcycle(vem_handle *h, AmgState *S, const double *b, double *x, const double *sc);
+vem_status amg_level_info(vem_handle *h, const AmgState *S, int *nlev, int64_t *rows, int64_t *nnz,
+                          int64_t *nnz_p);
+vem_status amg_level_copy(vem_handle *h, AmgState *S, int l, int64_t *rp, int32_t *col, double *val,
+                          int32_t *agg, int64_t *prp, int32_t *pcol, double *pval);
+double amg_omega(const AmgState *S, int l);
+
+// Block-Reg (assembly.cu): A_reg = M + B^T B / gamma over the flux DOFs with
+// the prescribed-flux DOFs eliminated, gamma from the options or h^2 (the
+// mean cell diameter squared); FP32 copy when fp32.
+vem_status assemble_reg(vem_handle *h, bool fp32);
+// sum of a device vector (fixed-order partial sums; synchronises)
+vem_status device_sum(vem_handle *h, int64_t n, const double *a, double *out);
 
 }  // namespace vem
 

@@ -427,7 +427,7 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   count_launch();
   k_cg_init<T><<<nb, kRedThreads, 0, s>>>(n, b, dinv, x, r, u, p, sv, h->part, sc, h->ctr);
   auto precondition = [&]() {
-    if constexpr (sizeof(T) == sizeof(double)) amg_vcycle(h, r, u, sc);
+    if constexpr (sizeof(T) == sizeof(double)) amg_vcycle(h, h->amg, r, u, sc);
   };
   if (amg) precondition();
   // every launch of the Schur SpMV is timed with a pair of events
@@ -493,7 +493,7 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
       (uintptr_t)x, (uintptr_t)p, (uintptr_t)sv, (uintptr_t)dinv, (uintptr_t)h->part, (uintptr_t)sc,
       (uintptr_t)h->ctr, (uintptr_t)n, (uintptr_t)nb, (uintptr_t)nbs, (uintptr_t)tile,
       (uintptr_t)tol_bits,
-      (uintptr_t)amg, (uintptr_t)(amg ? amg_generation(h) : 0), sizeof(T), (uintptr_t)op.nbatch,
+      (uintptr_t)amg, (uintptr_t)(amg ? amg_generation(h->amg) : 0), sizeof(T), (uintptr_t)op.nbatch,
       (uintptr_t)op.S.rows, (uintptr_t)op.S.stored};
   bool graph = h->pcg_graph != nullptr && h->pcg_graph_key == key;
   if (!graph) graph = capture_pcg_graph(h, key, [&]() {
@@ -539,7 +539,8 @@ static vem_status pcg_solve(vem_handle *h, const VemOp &op, const double *b, dou
   if (h->opt.inner == VEM_INNER_AMG) {
     // FP64 CG; with the mixed option the V-cycle runs in FP32
     const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
-    if (!amg_valid(h) || amg_is_fp32(h) != fp32) VEM_TRY(amg_setup(h, op.S, op.S_val32, fp32));
+    if (!amg_valid(h->amg) || amg_is_fp32(h->amg) != fp32)
+      VEM_TRY(amg_setup(h, h->amg, op.S, op.S_val32, fp32, h->multiplier, kSmoothJacobi));
     return pcg_solve_t<double>(h, op, op.S.val, op.s_dinv, b, x, wk, iters);
   }
   if (h->opt.precision == VEM_PRECISION_MIXED) {
@@ -608,6 +609,19 @@ __global__ void k_tri_flux(int64_t nf, int nfd, int64_t n_u, int64_t n_u1, int64
     }
     z[R] = t / dM[R];
   }
+}
+
+// z = w v and the partial of v . z (the pressure block W^-1 = I / gamma of
+// Block-Reg)
+__global__ void k_scale_dot(int64_t n, const double *__restrict__ v, double w, double *z, double *part) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = w * v[i];
+    z[i] = zi;
+    s += v[i] * zi;
+  }
+  if (part) block_partial(s, part);
 }
 
 __global__ void k_negate(int64_t n, double *x) {
@@ -808,18 +822,39 @@ __global__ void k_gm_solve(double *sc, int k, GmLayout L) {
 }
 
 // ------------------------------------------------------- preconditioner ---
-// z = P^{-1} v for the block preconditioner (diag or upper triangular).
-// wk: 5 n_p PCG work vectors (FP64 units; the FP32 solve uses 6 n_p floats of it).  If part_g2 != nullptr (MINRES) also leaves
-// the partials of v.z in slots P_G2U (flux part) and P_G2P (pressure part).
+// Block-Reg: A_reg and its AMG hierarchy for the current assembly, gamma and
+// precision.
+static vem_status ensure_reg(vem_handle *h) {
+  const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
+  if (!h->areg_valid || (fp32 && !h->areg_has32)) VEM_TRY(assemble_reg(h, fp32));
+  if (!amg_valid(h->amg_reg) || amg_is_fp32(h->amg_reg) != fp32)
+    VEM_TRY(amg_setup(h, h->amg_reg, h->Areg, h->Areg_val32, fp32, false, kSmoothChebyshev));
+  return VEM_OK;
+}
+
+// z = P^{-1} v for the block preconditioner (diag, upper triangular or
+// Block-Reg).  wk: 5 n_p PCG work vectors (FP64 units; the FP32 solve uses
+// 6 n_p floats of it).  minres_partials (MINRES) also leaves the partials of
+// v.z in slots P_G2U (flux part) and P_G2P (pressure part).
 static vem_status precond(vem_handle *h, const VemOp &op, const double *v, double *z, double *wk, int *inner,
                           bool minres_partials) {
   cudaStream_t s = h->stream;
   const int64_t nu = op.n_u, np = op.n_p;
   int it = 0;
+  if (h->opt.precond == VEM_PREC_BLOCK_REG) {
+    // z_u = V(v_u), one V-cycle of the AMG of A_reg; z_p = v_p / gamma
+    amg_vcycle(h, h->amg_reg, v, z, nullptr);
+    if (minres_partials) dot_partials(s, nu, v, z, slot(h->part, P_G2U));
+    count_launch();
+    k_scale_dot<<<nblocks_vec(np), kRedThreads, 0, s>>>(np, v + nu, 1.0 / h->reg_gamma, z + nu,
+                                                        minres_partials ? slot(h->part, P_G2P) : nullptr);
+    VEM_CUDA(h, cudaGetLastError());
+    return VEM_OK;
+  }
   if (h->opt.precond == VEM_PREC_BLOCK_DIAG) {
-    if (!minres_partials) {
-      count_launch(); k_diag_scale<<<nblocks_vec(nu), kRedThreads, 0, s>>>(nu, v, op.diagM, z, nullptr);
-    }
+    count_launch();
+    k_diag_scale<<<nblocks_vec(nu), kRedThreads, 0, s>>>(nu, v, op.diagM, z,
+                                                         minres_partials ? slot(h->part, P_G2U) : nullptr);
     VEM_TRY(pcg_solve(h, op, v + nu, z + nu, wk, &it));
   } else {
     VEM_TRY(pcg_solve(h, op, v + nu, z + nu, wk, &it));
@@ -882,7 +917,6 @@ static vem_status run_minres(vem_handle *h, const VemOp &op, const double *rhs, 
   VEM_CUDA(h, cudaMemsetAsync(vold, 0, sizeof(double) * n, s));
   VEM_CUDA(h, cudaMemsetAsync(wold, 0, sizeof(double) * n, s));
   VEM_CUDA(h, cudaMemsetAsync(w, 0, sizeof(double) * n, s));
-  count_launch(); k_diag_scale<<<nbu, kRedThreads, 0, s>>>(nu, v, op.diagM, z, slot(h->part, P_G2U));
   VEM_TRY(precond(h, op, v, z, pw, &inner, true));
   count_launch(); k_mr_init<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbu, nbp);
   VEM_CUDA(h, cudaGetLastError());
@@ -900,7 +934,6 @@ static vem_status run_minres(vem_handle *h, const VemOp &op, const double *rhs, 
     count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, z, h->scal + S_MR + MR_IG);
     op_apply_timed(h, op, z, Az, slot(h->part, P_DELTA));
     count_launch(); k_mr_lanczos<<<nbn, kRedThreads, 0, s>>>(n, Az, v, vold, h->part, nbd, h->scal);
-    count_launch(); k_diag_scale<<<nbu, kRedThreads, 0, s>>>(nu, vold, op.diagM, zn, slot(h->part, P_G2U));
     VEM_TRY(precond(h, op, vold, zn, pw, &inner, true));
     count_launch(); k_mr_scalars<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbd, nbu, nbp);
     count_launch(); k_mr_update<<<grid_for(n, 256), 256, 0, s>>>(n, z, wold, w, x, h->scal);
@@ -1016,9 +1049,13 @@ VemOp single_op(vem_handle *h) {
 vem_status krylov_solve(vem_handle *h, const VemOp &op, const double *rhs, double *x, vem_stats *st) {
   h->n_saddle_pending = 0;
   vem_status r;
+  if (h->opt.precond == VEM_PREC_BLOCK_REG) {
+    if (op.nbatch != 1) return fail(h, VEM_ERR_UNSUPPORTED, "Block-Reg is single-system");
+    VEM_TRY(ensure_reg(h));
+  }
   if (h->opt.krylov == VEM_KRYLOV_MINRES) {
-    if (h->opt.precond != VEM_PREC_BLOCK_DIAG)
-      return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs the block-diagonal preconditioner");
+    if (h->opt.precond == VEM_PREC_BLOCK_TRI)
+      return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs a block-diagonal preconditioner");
     r = run_minres(h, op, rhs, x, st);
   } else if (h->opt.krylov == VEM_KRYLOV_FGMRES) {
     r = run_fgmres(h, op, rhs, x, st);

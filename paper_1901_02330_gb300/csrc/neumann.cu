@@ -10,6 +10,8 @@
 // consistent right-hand side F - c lambda, every inner Schur solve works on
 // the consistent (mean-free) part of its right-hand side, and the pressure is
 // shifted to sum |P| p_P = 0 at the end.
+#include <vector>
+
 #include "handle.cuh"
 
 namespace vem {
@@ -85,6 +87,21 @@ vem_status neumann_mean_free(vem_handle *h, int64_t n, const double *b, double *
   count_launch();
   k_sub_scaled<<<nb, kRedThreads, 0, h->stream>>>(n, h->npart, nullptr, nb, nullptr, b, out, nullptr);
   VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
+vem_status device_sum(vem_handle *h, int64_t n, const double *a, double *out) {
+  VEM_TRY(ensure_npart(h));
+  const int nb = nblocks_vec(n);
+  count_launch();
+  k_sums<<<nb, kRedThreads, 0, h->stream>>>(n, a, nullptr, h->npart);
+  VEM_CUDA(h, cudaGetLastError());
+  std::vector<double> part(nb);
+  VEM_CUDA(h, cudaMemcpyAsync(part.data(), h->npart, sizeof(double) * nb, cudaMemcpyDeviceToHost, h->stream));
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  double t = 0.0;
+  for (int i = 0; i < nb; ++i) t += part[i];
+  *out = t;
   return VEM_OK;
 }
 

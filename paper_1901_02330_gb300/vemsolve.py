@@ -21,7 +21,8 @@ STATUS = {0: "VEM_OK", 1: "VEM_ERR_BAD_INPUT", 2: "VEM_ERR_DEGENERATE_MESH", 3: 
           8: "VEM_ERR_UNSUPPORTED"}
 VEM_ELEMENT_E0, VEM_ELEMENT_K1 = 0, 1
 VEM_KRYLOV_MINRES, VEM_KRYLOV_FGMRES = 0, 1
-VEM_PREC_BLOCK_DIAG, VEM_PREC_BLOCK_TRI = 0, 1
+VEM_PREC_BLOCK_DIAG, VEM_PREC_BLOCK_TRI, VEM_PREC_BLOCK_REG = 0, 1, 2
+VEM_AMG_SCHUR, VEM_AMG_REG = 0, 1
 VEM_INNER_PCG, VEM_INNER_AMG = 0, 1
 VEM_PRECISION_FP64, VEM_PRECISION_MIXED = 0, 1
 VEM_QP_CELL, VEM_QP_BFACE = 0, 1
@@ -37,7 +38,8 @@ class vem_mesh(C.Structure):
 class vem_options(C.Structure):
     _fields_ = [("element", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("rtol", C.c_double),
                 ("maxit", C.c_int), ("precond", C.c_int), ("inner", C.c_int), ("inner_rtol", C.c_double),
-                ("inner_maxit", C.c_int), ("precision", C.c_int), ("device_io", C.c_int), ("reuse", C.c_int)]
+                ("inner_maxit", C.c_int), ("precision", C.c_int), ("device_io", C.c_int), ("reuse", C.c_int),
+                ("reg_gamma", C.c_double)]
 
 
 class vem_stats(C.Structure):
@@ -48,7 +50,8 @@ class vem_stats(C.Structure):
                 ("t_schur_spmv_ms", C.c_double), ("n_schur_spmv", C.c_int64),
                 ("t_amg_setup_ms", C.c_double), ("amg_levels", C.c_int32),
                 ("t_saddle_spmv_ms", C.c_double), ("n_saddle_spmv", C.c_int64),
-                ("multiplier", C.c_double), ("schur_tile", C.c_int32)]
+                ("multiplier", C.c_double), ("schur_tile", C.c_int32),
+                ("reg_gamma", C.c_double), ("nnz_reg", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -88,10 +91,11 @@ _SIGS = {
     "vem_residual_norm_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_bface_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
-    "vem_amg_setup": (C.c_int, [C.c_void_p]),
-    "vem_amg_levels": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p]),
-    "vem_amg_get_level": (C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 7),
-    "vem_amg_vcycle_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vem_amg_setup": (C.c_int, [C.c_void_p, C.c_int32]),
+    "vem_amg_levels": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
+    "vem_amg_get_level": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32] + [C.c_void_p] * 7),
+    "vem_amg_vcycle_device": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "vem_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
     "vem_last_error": (C.c_char_p, [C.c_void_p]),
     "vem_destroy": (None, [C.c_void_p]),
@@ -373,24 +377,24 @@ class Solver:
         self._check(lib().vem_get_schur(self._h, _ptr(rp), _ptr(col), _ptr(val), _ptr(dM)))
         return sp.csr_matrix((val, col, rp), shape=(np_, np_)), dM
 
-    # -- AMG hierarchy of S (VEM_INNER_AMG)
-    def amg_setup(self):
-        self._check(lib().vem_amg_setup(self._h))
+    # -- AMG hierarchies: of S (VEM_INNER_AMG) or of A_reg (Block-Reg)
+    def amg_setup(self, which=VEM_AMG_SCHUR):
+        self._check(lib().vem_amg_setup(self._h, which))
 
-    def amg_levels(self):
+    def amg_levels(self, which=VEM_AMG_SCHUR):
         """(rows, nnz, nnz of P) per level."""
         nl = C.c_int32()
         rows = np.zeros(16, dtype=np.int64)
         nnz = np.zeros(16, dtype=np.int64)
         nnzp = np.zeros(16, dtype=np.int64)
-        self._check(lib().vem_amg_levels(self._h, C.byref(nl), _ptr(rows), _ptr(nnz), _ptr(nnzp)))
+        self._check(lib().vem_amg_levels(self._h, which, C.byref(nl), _ptr(rows), _ptr(nnz), _ptr(nnzp)))
         k = nl.value
         return rows[:k].copy(), nnz[:k].copy(), nnzp[:k].copy()
 
-    def amg_level(self, level: int):
+    def amg_level(self, level: int, which=VEM_AMG_SCHUR):
         """(A_l as scipy CSR, agg or None, P_l as scipy CSR or None)."""
         import scipy.sparse as sp
-        rows, nnz, nnzp = self.amg_levels()
+        rows, nnz, nnzp = self.amg_levels(which)
         n = int(rows[level])
         rp = np.zeros(n + 1, dtype=np.int64)
         col = np.zeros(max(int(nnz[level]), 1), dtype=np.int32)
@@ -400,7 +404,7 @@ class Solver:
         prp = np.zeros(n + 1, dtype=np.int64) if coarse else None
         pcol = np.zeros(max(int(nnzp[level]), 1), dtype=np.int32) if coarse else None
         pval = np.zeros(max(int(nnzp[level]), 1)) if coarse else None
-        self._check(lib().vem_amg_get_level(self._h, level, _ptr(rp), _ptr(col), _ptr(val), _ptr(agg),
+        self._check(lib().vem_amg_get_level(self._h, which, level, _ptr(rp), _ptr(col), _ptr(val), _ptr(agg),
                                             _ptr(prp), _ptr(pcol), _ptr(pval)))
         A = sp.csr_matrix((val[:rp[-1]], col[:rp[-1]], rp), shape=(n, n))
         P = None
@@ -408,8 +412,8 @@ class Solver:
             P = sp.csr_matrix((pval[:prp[-1]], pcol[:prp[-1]], prp), shape=(n, int(rows[level + 1])))
         return A, agg, P
 
-    def amg_vcycle_device(self, b, x):
-        self._check(lib().vem_amg_vcycle_device(self._h, _ptr(b), _ptr(x)))
+    def amg_vcycle_device(self, b, x, which=VEM_AMG_SCHUR):
+        self._check(lib().vem_amg_vcycle_device(self._h, which, _ptr(b), _ptr(x)))
 
     def apply_device(self, x, y):
         self._check(lib().vem_apply_device(self._h, _ptr(x), _ptr(y)))
