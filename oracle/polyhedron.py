@@ -57,13 +57,16 @@ def face_geometry(mesh, f: int, nq: int = 5) -> Face:
     vid = mesh.face_vertices(f)
     V = mesh.xyz[vid]
     m = V.shape[0]
-    # Newell: area vector = 1/2 sum v_i x v_{i+1}
-    av = 0.5 * np.sum(np.cross(V, np.roll(V, -1, axis=0)), axis=0)
+    # Newell: area vector = 1/2 sum v_i x v_{i+1}, the same for any origin
+    # of the v_i (the loop is closed); taken about the vertex mean so that a
+    # small face far from the origin loses no digits to cancellation
+    xbar = V.mean(axis=0)
+    W = V - xbar
+    av = 0.5 * np.sum(np.cross(W, np.roll(W, -1, axis=0)), axis=0)
     a = np.linalg.norm(av)
     if not a > 0:
         raise ValueError(f"degenerate face {f}")
     n = av / a
-    xbar = V.mean(axis=0)
     # area barycentre from the fan around the vertex mean
     num = np.zeros(3)
     den = 0.0

@@ -102,3 +102,26 @@ def test_tet_mesh_volumes_sum_to_one():
     vols = [cell_geometry(t, c).volume for c in range(t.n_cells)]
     assert sum(vols) == pytest.approx(1.0, rel=1e-13)
     np.testing.assert_allclose(vols, 1 / 48, rtol=1e-13)
+
+
+def test_small_face_far_from_origin():
+    """A triangle of side 1e-5 around (0.5, 0.7, 0.3), in a plane with a
+    known unit normal: normal, area and centroid to rounding of the offsets
+    (the area vector does not depend on the origin; computed about the
+    vertex mean it keeps its digits)."""
+    from synth.meshes import from_cell_loops
+    nrm = np.array([1.0, 2.0, 2.0]) / 3.0
+    t1 = np.array([2.0, -1.0, 0.0]) / np.sqrt(5.0)
+    t2 = np.cross(nrm, t1)
+    c0 = np.array([0.5, 0.7, 0.3])
+    h = 1e-5
+    tri = [c0 + h * t1, c0 + h * (-0.5 * t1 + 0.8 * t2), c0 + h * (-0.5 * t1 - 0.8 * t2)]
+    apex = c0 - 0.1 * nrm
+    xyz = np.array(tri + [apex])
+    m = from_cell_loops(xyz, [[[0, 1, 2], [0, 1, 3], [1, 2, 3], [2, 0, 3]]])
+    f = [i for i in range(m.n_faces) if sorted(m.face_vertices(i).tolist()) == [0, 1, 2]][0]
+    F = face_geometry(m, f)
+    np.testing.assert_allclose(F.normal, nrm, atol=1e-10)
+    area = 0.5 * np.linalg.norm(np.cross(xyz[1] - xyz[0], xyz[2] - xyz[0]))
+    assert F.area == pytest.approx(area, rel=1e-10)
+    np.testing.assert_allclose(F.centroid, xyz[:3].mean(axis=0), atol=1e-15)
