@@ -7,5 +7,5 @@ element arithmetic (no geometry moments, projections, matrices or solvers);
 each side computes those itself.
 """
 
-from .meshes import Mesh, hex_mesh, tet_mesh, prism_mesh, affine, from_cell_loops, cell_vertex_ids  # noqa: F401
+from .meshes import Mesh, hex_mesh, tet_mesh, prism_mesh, octa_mesh, affine, from_cell_loops, cell_vertex_ids  # noqa: F401
 from . import fields  # noqa: F401

@@ -228,6 +228,45 @@ def prism_mesh(n: int, bc: int = 1) -> Mesh:
     return from_cell_loops(xyz, cells, bc, name=f"prism{n}")
 
 
+def octa_mesh(n: int, bc: int = 1) -> Mesh:
+    """Every cube of an n^3 grid split into 9 convex cells: the octahedron
+    whose vertices are the 6 face centres of the cube (8 triangular faces),
+    and the 8 corner pieces {cube octant} minus that octahedron, each with 7
+    faces (the quarter squares of the 3 cube faces at its corner, a triangle
+    on each of the 3 mid-planes, a triangle on the octahedron).  Cells have
+    seven or eight faces; 9 n^3 cells, 20 n^3 + 12 n^2 (n + 1) faces and the
+    (2n+1)^3 points of the half-step grid as vertices."""
+    m = 2 * n + 1
+    g = np.linspace(0.0, 1.0, m)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+    def vid(p):
+        return (p[0] * m + p[1]) * m + p[2]
+    e = np.eye(3, dtype=np.int64)
+    cells = []
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                C = np.array([2 * i + 1, 2 * j + 1, 2 * k + 1])
+                cells.append([[vid(C + sx * e[0]), vid(C + sy * e[1]), vid(C + sz * e[2])]
+                              for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)])
+                for sx in (-1, 1):
+                    for sy in (-1, 1):
+                        for sz in (-1, 1):
+                            Fx, Fy, Fz = C + sx * e[0], C + sy * e[1], C + sz * e[2]
+                            Exy, Exz, Eyz = Fx + sy * e[1], Fx + sz * e[2], Fy + sz * e[2]
+                            V = Exy + sz * e[2]
+                            cells.append([[vid(Fx), vid(Exy), vid(V), vid(Exz)],
+                                          [vid(Fy), vid(Exy), vid(V), vid(Eyz)],
+                                          [vid(Fz), vid(Exz), vid(V), vid(Eyz)],
+                                          [vid(Fy), vid(Fz), vid(Eyz)],
+                                          [vid(Fx), vid(Fz), vid(Exz)],
+                                          [vid(Fx), vid(Fy), vid(Exy)],
+                                          [vid(Fx), vid(Fy), vid(Fz)]])
+    return from_cell_loops(xyz, cells, bc, name=f"octa{n}")
+
+
 def affine(mesh: Mesh, A, b=(0.0, 0.0, 0.0)) -> Mesh:
     """Image of a mesh under x -> A x + b (faces stay planar)."""
     A = np.asarray(A, dtype=np.float64)

@@ -1,12 +1,13 @@
 """Optimality of the Block-Schur preconditioner under refinement (the
 paper's optimality test, Sec. 5, here at k = 1 and with the paper's flux
 boundary data and mean-zero pressure): with S solved to 1e-12 the FGMRES
-iteration count stays bounded as the Cube and CVT meshes are refined."""
+iteration count stays bounded as the Cube, Octa and CVT meshes are
+refined."""
 
 import numpy as np
 import pytest
 
-from synth import fields, hex_mesh
+from synth import fields, hex_mesh, octa_mesh
 from synth.voronoi import voronoi_mesh
 
 pytestmark = pytest.mark.gpu
@@ -37,11 +38,20 @@ def _neumann(m):
     return m
 
 
-@pytest.mark.parametrize("family,sizes", [("cube", (8, 16, 24)), ("cvt", (1000, 4000, 8000))])
+def _mesh(family, n):
+    if family == "cube":
+        return hex_mesh(n, bc=2)
+    if family == "octa":
+        return octa_mesh(n, bc=2)
+    return _neumann(voronoi_mesh(n, seed=7, lloyd=10))
+
+
+@pytest.mark.parametrize("family,sizes", [("cube", (8, 16, 24)), ("octa", (2, 4, 8)),
+                                          ("cvt", (1000, 4000, 8000))])
 def test_block_schur_iterations_bounded(vs, family, sizes):
     its = []
     for n in sizes:
-        m = hex_mesh(n, bc=2) if family == "cube" else _neumann(voronoi_mesh(n, seed=7, lloyd=10))
+        m = _mesh(family, n)
         its.append(_iters(vs, m))
     for a, b in zip(its, its[1:]):
         assert b <= 1.1 * a + 2, its

@@ -9,7 +9,7 @@ import pytest
 from oracle import E0, assemble, paper_element, solvers
 from oracle.assemble import mesh_cells
 from oracle.element import local_system
-from synth import affine, fields, hex_mesh, prism_mesh, tet_mesh
+from synth import affine, fields, hex_mesh, octa_mesh, prism_mesh, tet_mesh
 from synth.voronoi import voronoi_mesh
 
 pytestmark = pytest.mark.gpu
@@ -20,6 +20,7 @@ MESHES = {
     "tet2": lambda: tet_mesh(2),
     "prism2": lambda: prism_mesh(2),
     "sheared": lambda: affine(hex_mesh(2), A_SHEAR, (0.1, 0.0, -0.3)),
+    "octa2": lambda: octa_mesh(2),
     "cvt": lambda: voronoi_mesh(40, seed=3, lloyd=5),
 }
 ELEMENTS = {"E0": (E0, 0), "K1": (paper_element(1), 1)}

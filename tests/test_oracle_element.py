@@ -8,7 +8,7 @@ import pytest
 from oracle.element import E0, interpolate, local_system, paper_element
 from oracle.monomials import mono3
 from oracle.polyhedron import cell_geometry
-from synth import affine, hex_mesh, prism_mesh, tet_mesh
+from synth import affine, hex_mesh, octa_mesh, prism_mesh, tet_mesh
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table_dofs.txt")
 A_SHEAR = np.array([[1.0, 0.3, 0.1], [0.0, 0.8, -0.2], [0.1, 0.0, 1.2]])
@@ -21,18 +21,54 @@ def _cells():
     yield "prism", cell_geometry(prism_mesh(1), 1)
 
 
+def _mesh_counts(kind, n):
+    """(faces, cells): Cube n^3 has 3n^2(n+1) faces; Octa (9 cells per cube)
+    has 20 n^3 + 12 n^2 (n+1) (8 octahedron faces and 12 mid-plane triangles
+    inside each cube, 4 quarter squares on each cube face)."""
+    if kind == "cube":
+        return 3 * n * n * (n + 1), n ** 3
+    return 20 * n ** 3 + 12 * n * n * (n + 1), 9 * n ** 3
+
+
 def test_dof_counts_match_paper_tables():
-    """Cube n^3: faces 3n^2(n+1), cells n^3; total = face DOFs + interior DOFs
-    + pressure DOFs, and the paper's tables print that total + 1 (the
-    mean-zero pressure multiplier of its Neumann problem, Sec. 3)."""
+    """Total = face DOFs + interior DOFs + pressure DOFs, and the paper's
+    tables print that total + 1 (the mean-zero pressure multiplier of its
+    Neumann problem, Sec. 3).  The Octa rows fix the Octa family's cell and
+    face counts, from which synth.octa_mesh was built."""
     rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
-    assert len(rows) == 8
+    assert len(rows) == 16
     for r in rows:
         n, k, dofs = int(r[1]), int(r[2]), int(r[3])
         spec = paper_element(k)
-        F, Nc = 3 * n * n * (n + 1), n ** 3
+        F, Nc = _mesh_counts(r[0], n)
         total = spec.nfd * F + (spec.nid + spec.nq) * Nc
         assert total + 1 == dofs, r
+
+
+@pytest.mark.parametrize("n", [1, 2, 4])
+def test_octa_mesh_counts_and_cells(n):
+    """The generated Octa mesh has the counts above, cells of seven or eight
+    faces, and cell volumes h^3/6 (octahedron on the face centres of a cube
+    of side h) and (h^3 - h^3/6)/8 = 5h^3/48 (corner pieces), summing to 1."""
+    m = octa_mesh(n)
+    F, Nc = _mesh_counts("octa", n)
+    assert (m.n_faces, m.n_cells) == (F, Nc)
+    nfc = np.diff(m.cell_face_ptr)
+    assert np.array_equal(np.bincount(nfc, minlength=9)[7:], [8 * n ** 3, n ** 3])
+    h = 1.0 / n
+    vols = np.array([cell_geometry(m, c).volume for c in range(m.n_cells)])
+    np.testing.assert_allclose(vols[nfc == 8], h ** 3 / 6, rtol=1e-13)
+    np.testing.assert_allclose(vols[nfc == 7], 5 * h ** 3 / 48, rtol=1e-13)
+    assert vols.sum() == pytest.approx(1.0, rel=1e-13)
+
+
+def test_octa_table_dofs_from_generated_mesh():
+    """Table 5's N_P = 576 row (k = 2: 23809 DOFs) counted on the generated
+    mesh itself."""
+    m = octa_mesh(4)
+    spec = paper_element(2)
+    assert m.n_cells == 576
+    assert spec.nfd * m.n_faces + (spec.nid + spec.nq) * m.n_cells + 1 == 23809
 
 
 @pytest.mark.parametrize("spec", [E0, paper_element(1), paper_element(2)], ids=lambda s: s.name)

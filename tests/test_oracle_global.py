@@ -8,7 +8,7 @@ import scipy.sparse.linalg as spla
 
 from oracle import E0, assemble, errors, paper_element, solvers
 from oracle.element import interpolate
-from synth import affine, fields, hex_mesh, prism_mesh, tet_mesh
+from synth import affine, fields, hex_mesh, octa_mesh, prism_mesh, tet_mesh
 from synth.voronoi import voronoi_mesh
 
 A_SHEAR = np.array([[1.0, 0.3, 0.1], [0.0, 0.8, -0.2], [0.1, 0.0, 1.2]])
@@ -17,6 +17,7 @@ MESHES = {
     "tet": lambda: tet_mesh(2),
     "prism": lambda: prism_mesh(2),
     "sheared": lambda: affine(hex_mesh(2), A_SHEAR, (0.1, 0.0, -0.3)),
+    "octa": lambda: octa_mesh(2),
     "voronoi": lambda: voronoi_mesh(30, seed=3, lloyd=0),
     "cvt": lambda: voronoi_mesh(40, seed=3, lloyd=5),
 }

@@ -8,7 +8,7 @@ import pytest
 from oracle import E0, assemble, paper_element, solvers
 from oracle.assemble import mesh_cells
 from oracle.element import interpolate
-from synth import affine, fields, hex_mesh, prism_mesh, tet_mesh
+from synth import affine, fields, hex_mesh, octa_mesh, prism_mesh, tet_mesh
 from synth.voronoi import voronoi_mesh
 
 A_SHEAR = np.array([[1.0, 0.3, 0.1], [0.0, 0.8, -0.2], [0.1, 0.0, 1.2]])
@@ -16,6 +16,7 @@ MESHES = {
     "hex": lambda bc: hex_mesh(3, bc=bc),
     "tet": lambda bc: tet_mesh(2, bc=bc),
     "prism": lambda bc: prism_mesh(2, bc=bc),
+    "octa": lambda bc: octa_mesh(1, bc=bc),
     "voronoi": lambda bc: _with_bc(voronoi_mesh(30, seed=3, lloyd=2), bc),
 }
 
