@@ -495,29 +495,40 @@ __device__ void warp_sort(int32_t *key, double *val, int m) {
 }
 
 // Sort every row of a CSR matrix by column (distinct columns), one warp per
-// row, rows of at most kSortMax entries.
-__global__ void __launch_bounds__(32 * kProdWarps) k_sort_rows(int64_t n, const int64_t *__restrict__ rp, int32_t *col,
-                                                              double *val, int *err) {
-  __shared__ int32_t sk[kProdWarps][kSortMax];
-  __shared__ double sv[kProdWarps][kSortMax];
+// row with kCap entries of shared memory (dynamic: values, then keys).  Rows
+// longer than kCap are marked (big[i] = 1) for the one-warp pass with the
+// large buffer when big is given, else they raise DEVERR_AMG_ROW; only_big
+// takes the marked rows alone.
+template <int kCap, int kW>
+__global__ void __launch_bounds__(32 * kW) k_sort_rows(int64_t n, const int64_t *__restrict__ rp, int32_t *col,
+                                                      double *val, int *err, uint8_t *big, bool only_big) {
+  extern __shared__ __align__(16) unsigned char sort_smem[];
+  double *svb = reinterpret_cast<double *>(sort_smem);
+  int32_t *skb = reinterpret_cast<int32_t *>(svb + (size_t)kW * kCap);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * kProdWarps + w, nw = (int64_t)gridDim.x * kProdWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kW + w, nw = (int64_t)gridDim.x * kW;
+  double *sv = svb + (size_t)w * kCap;
+  int32_t *sk = skb + (size_t)w * kCap;
   for (int64_t i = gw; i < n; i += nw) {
+    if (only_big && !big[i]) continue;
     const int64_t lo = rp[i];
     const int m = (int)(rp[i + 1] - lo);
-    if (m > kSortMax) {
-      if (lane == 0) atomicOr(err, DEVERR_AMG_ROW);
+    if (m > kCap) {
+      if (lane == 0) {
+        if (big && !only_big) big[i] = 1;
+        else atomicOr(err, DEVERR_AMG_ROW);
+      }
       continue;
     }
     for (int t = lane; t < m; t += 32) {
-      sk[w][t] = col[lo + t];
-      sv[w][t] = val[lo + t];
+      sk[t] = col[lo + t];
+      sv[t] = val[lo + t];
     }
     __syncwarp();
-    warp_sort(sk[w], sv[w], m);
+    warp_sort(sk, sv, m);
     for (int t = lane; t < m; t += 32) {
-      col[lo + t] = sk[w][t];
-      val[lo + t] = sv[w][t];
+      col[lo + t] = sk[t];
+      val[lo + t] = sv[t];
     }
     __syncwarp();
   }
@@ -1005,6 +1016,36 @@ __global__ void k_count_flags(int64_t n, const uint8_t *__restrict__ f, unsigned
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// Sort the rows of a CSR matrix by column: rows of up to kSortMax entries a
+// warp each in blocks of kProdWarps, longer ones (up to 2^kBigBits) one warp
+// per block with a large shared buffer.
+static vem_status sort_rows(vem_handle *h, AmgState *S, int64_t n, const int64_t *rp, int32_t *col, double *val) {
+  cudaStream_t s = h->stream;
+  constexpr int kBigCap = 1 << kBigBits;
+  const size_t sm = (size_t)kProdWarps * kSortMax * (sizeof(double) + sizeof(int32_t));
+  const size_t smb = (size_t)kBigCap * (sizeof(double) + sizeof(int32_t));
+  VEM_CUDA(h, cudaFuncSetAttribute(k_sort_rows<kBigCap, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+  VEM_TRY(grow(h, S->big, S->c_big, (size_t)std::max<int64_t>(n, 1)));
+  VEM_CUDA(h, cudaMemsetAsync(S->big, 0, (size_t)n, s));
+  count_launch();
+  k_sort_rows<kSortMax, kProdWarps><<<prod_grid(n), 32 * kProdWarps, sm, s>>>(n, rp, col, val, h->d_err, S->big,
+                                                                              false);
+  unsigned long long *nbig = S->ctr + kMaxRounds + 2;
+  VEM_CUDA(h, cudaMemsetAsync(nbig, 0, sizeof(*nbig), s));
+  count_launch();
+  k_count_flags<<<rows_grid(n), 256, 0, s>>>(n, S->big, nbig);
+  unsigned long long nb = 0;
+  VEM_CUDA(h, cudaMemcpyAsync(&nb, nbig, sizeof(nb), cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  if (nb) {
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nb, (int64_t)num_sms() * 2));
+    count_launch();
+    k_sort_rows<kBigCap, 1><<<gb, 32, smb, s>>>(n, rp, col, val, h->d_err, S->big, true);
+  }
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
 // C = X Y (two passes: count, fill).  With short_rows one thread per row
 // (at most 64 distinct columns, else the product is redone a warp per row).
 static vem_status product(vem_handle *h, AmgState *S, const DMat &X, const CsrBuf &Y, CsrBuf &C,
@@ -1146,7 +1187,7 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   k_t_fill<<<g, 256, 0, s>>>(n, L.P.rp, L.P.col, L.P.val, reinterpret_cast<unsigned long long *>(S->cur), L.R.col,
                              L.R.val);
   count_launch();
-  k_sort_rows<<<prod_grid(nc), 32 * kProdWarps, 0, s>>>(nc, L.R.rp, L.R.col, L.R.val, h->d_err);
+  VEM_TRY(sort_rows(h, S, nc, L.R.rp, L.R.col, L.R.val));
   VEM_CUDA(h, cudaGetLastError());
   // A P, then R (A P)
   // the finest level's A P has short rows: try one thread per row first

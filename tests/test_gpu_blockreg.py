@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import E0, amg, assemble, paper_element, solvers
-from synth import fields, hex_mesh, prism_mesh
+from synth import fields, hex_mesh, octa_mesh, prism_mesh
 from synth.voronoi import voronoi_mesh
 
 pytestmark = pytest.mark.gpu
@@ -29,23 +29,34 @@ CASES = {
     "cvt150-E0-lognormal": lambda: _cvt(150, "lognormal"),
     "prism3-K1-uniform": lambda: (prism_mesh(3), paper_element(1), 1, np.ones(54)),
     "hex5-K1-flux": lambda: (_neumann(hex_mesh(5)), paper_element(1), 1, np.ones(125)),
+    "octa2-K1-flux": lambda: (octa_mesh(2, bc=2), paper_element(1), 1, np.ones(72)),
     "cvt150-E0-contrast": lambda: _cvt(150, "contrast"),
     "prism3-K1-contrast": lambda: (prism_mesh(3), paper_element(1), 1,
                                    fields.K_high_contrast(54, seed=2, decades=3.0)),
+    "cvt1000-K1-flux": lambda: _cvt_flux(1000),
 }
 # gamma = h^2 does not depend on K: with two or three decades of contrast
 # restarted FGMRES stagnates and MINRES needs ~1000 iterations on these small
 # meshes, in the oracle as here, so the contrast cases check the matrix, the
 # hierarchy and the cycle only.
-SOLVE_CASES = [k for k in CASES if "contrast" not in k]
+SOLVE_CASES = [k for k in CASES if "contrast" not in k and k != "cvt1000-K1-flux"]
+# cvt1000-K1-flux: rows of R with more than 512 entries and Galerkin product
+# rows with more than 384 distinct columns, so its hierarchy takes the
+# large-buffer sort and product kernels.
 
 # Relative tolerance of prolongator entries and cycle outputs: as for the S
 # hierarchy, small entries of the independently assembled matrices agree to
 # ~1e-10 relative on the high-contrast polyhedral meshes, to rounding on the
 # structured ones.
 TOL = {"hex6-E0-uniform": 1e-12, "hex5-K1-lognormal": 1e-12, "cvt150-E0-lognormal": 1e-10,
-       "prism3-K1-uniform": 1e-12, "hex5-K1-flux": 1e-12, "cvt150-E0-contrast": 1e-9,
-       "prism3-K1-contrast": 1e-9}
+       "prism3-K1-uniform": 1e-12, "hex5-K1-flux": 1e-12, "octa2-K1-flux": 1e-12, "cvt150-E0-contrast": 1e-9,
+       "prism3-K1-contrast": 1e-9, "cvt1000-K1-flux": 1e-9}
+
+
+def _cvt_flux(n):
+    m = voronoi_mesh(n, seed=7, lloyd=10)
+    m.face_bc = np.where(m.face_bc != 0, 2, 0).astype(np.int8)
+    return m, paper_element(1), 1, np.ones(m.n_cells)
 
 
 def _cvt(n, kind):
