@@ -101,6 +101,7 @@ struct AmgLevel {
   float *wdc32 = nullptr;
   size_t c_wdc32 = 0;
   double omega = 0.0;
+  int mis_rounds = 0;       // MIS-2 rounds this level needed in the last setup
   double rho = 0.0;         // Gershgorin bound of rho(D^-1 A)
   double cheb_c = 0.0;      // Chebyshev: rho_1 rho_0 (the second step)
   int64_t n = 0, nc = 0;
@@ -140,6 +141,9 @@ struct AmgState {
   CsrBuf AP;
   int64_t *cur = nullptr;   size_t c_cur = 0;     // transpose cursors
   uint8_t *big = nullptr;   size_t c_big = 0;     // product rows for the large table
+  int64_t *coff = nullptr;  size_t c_coff = 0;    // one-pass product: scratch row offsets
+  int32_t *tcol = nullptr;  size_t c_tcol = 0;    //   and the scratch rows
+  double *tval = nullptr;   size_t c_tval = 0;
   double t_setup_ms = 0.0;
 };
 
@@ -614,9 +618,9 @@ __global__ void __launch_bounds__(32 * kW) k_prod_rows(DMat X, const int64_t *__
     const int m = tn[w];
     if (over) {
       if (lane == 0) {
-        if (!kFill && big && !only_big) big[r] = 1;
+        if (big && !only_big) big[r] = 1;
         else atomicOr(err, DEVERR_AMG_ROW);
-        if (!kFill) cnt[r] = 0;
+        if (cnt) cnt[r] = 0;
       }
       __syncwarp();
       continue;
@@ -651,7 +655,41 @@ __global__ void __launch_bounds__(32 * kW) k_prod_rows(DMat X, const int64_t *__
       ocol[o + t] = K[t];
       oval[o + t] = V[t];
     }
+    if (cnt && lane == 0) cnt[r] = m;
     __syncwarp();
+  }
+}
+
+// Upper bound of the distinct columns of row r of X Y: the number of
+// candidate products sum_{k in row r of X} |row k of Y|.
+__global__ void k_prod_cand(DMat X, const int64_t *__restrict__ yrp, int64_t *cand) {
+  ROWS_LOOP(r, X.rows) {
+    int64_t base;
+    int st, L;
+    X.row(r, base, st, L);
+    int64_t c = 0;
+    for (int e = 0; e < L; ++e) {
+      const int32_t k = X.col[base + (int64_t)st * e];
+      c += yrp[k + 1] - yrp[k];
+    }
+    cand[r] = c;
+  }
+}
+
+// Row r's entries from the scratch (at off[r]) to their final place (rp[r]),
+// one warp per row.
+__global__ void k_compact_rows(int64_t rows, const int64_t *__restrict__ off, const int64_t *__restrict__ rp,
+                               const int32_t *__restrict__ tcol, const double *__restrict__ tval, int32_t *col,
+                               double *val) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < rows; r += nwarps) {
+    const int64_t src = off[r], dst = rp[r], m = rp[r + 1] - dst;
+    for (int64_t t = lane; t < m; t += 32) {
+      col[dst + t] = tcol[src + t];
+      val[dst + t] = tval[src + t];
+    }
   }
 }
 
@@ -678,6 +716,7 @@ __global__ void k_prod_rows_thread(DMat X, const int64_t *__restrict__ yrp, cons
     if (!kFill) {
       cnt[r] = ok ? m.n : 0;
     } else if (ok) {
+      if (cnt) cnt[r] = m.n;
       const int64_t o = rp[r];
       for (int t = 0; t < m.n; ++t) {
         ocol[o + t] = m.key[t];
@@ -1046,14 +1085,74 @@ static vem_status sort_rows(vem_handle *h, AmgState *S, int64_t n, const int64_t
   return VEM_OK;
 }
 
-// C = X Y (two passes: count, fill).  With short_rows one thread per row
-// (at most 64 distinct columns, else the product is redone a warp per row).
+// C = X Y.  One pass when the candidate products fit the scratch budget:
+// every row is formed once into a scratch buffer at an upper-bound offset
+// (its candidate count), then the rows are compacted; otherwise two passes
+// (count, fill).  With short_rows one thread per row (at most 64 distinct
+// columns, else the product is redone a warp per row); warp rows that
+// overflow the small hash table are redone with the large one.  Both ways
+// form each row with the same kernels in the same order, so C is the same
+// bit for bit.
+constexpr size_t kProdScratchMax = size_t(6) << 30;   // bytes of scratch for the one-pass form
+
 static vem_status product(vem_handle *h, AmgState *S, const DMat &X, const CsrBuf &Y, CsrBuf &C,
                           bool short_rows) {
   cudaStream_t s = h->stream;
   VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)X.rows + 1));
   unsigned long long *ovf = S->ctr + kMaxRounds + 3;
   unsigned long long over = 0;
+  const size_t sm = prod_smem_bytes(kHashBits, kProdWarps), smb = prod_smem_bytes(kBigBits, 1);
+  VEM_CUDA(h, cudaFuncSetAttribute(k_prod_rows<false, kBigBits, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smb));
+  VEM_CUDA(h, cudaFuncSetAttribute(k_prod_rows<true, kBigBits, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smb));
+  // ---- one pass through the scratch ----
+  VEM_TRY(grow(h, S->coff, S->c_coff, (size_t)X.rows + 1));
+  count_launch();
+  k_prod_cand<<<rows_grid(X.rows), 256, 0, s>>>(X, Y.rp, S->cnt);
+  int64_t ncand = 0;
+  VEM_TRY(scan_counts(h, X.rows, S->cnt, S->coff, &ncand));   // synchronises
+  if ((size_t)ncand * (sizeof(double) + sizeof(int32_t)) <= kProdScratchMax) {
+    VEM_TRY(grow(h, S->tcol, S->c_tcol, (size_t)std::max<int64_t>(ncand, 1)));
+    VEM_TRY(grow(h, S->tval, S->c_tval, (size_t)std::max<int64_t>(ncand, 1)));
+    bool warp_rows = !short_rows;
+    if (short_rows) {
+      VEM_CUDA(h, cudaMemsetAsync(ovf, 0, sizeof(*ovf), s));
+      count_launch();
+      k_prod_rows_thread<true><<<rows_grid(X.rows), 256, 0, s>>>(X, Y.rp, Y.col, Y.val, S->cnt, S->coff, S->tcol,
+                                                                 S->tval, ovf);
+      VEM_CUDA(h, cudaMemcpyAsync(&over, ovf, sizeof(over), cudaMemcpyDeviceToHost, s));
+      VEM_CUDA(h, cudaStreamSynchronize(s));
+      warp_rows = over != 0;
+    }
+    if (warp_rows) {
+      const int g = prod_grid(X.rows);
+      VEM_TRY(grow(h, S->big, S->c_big, (size_t)X.rows));
+      VEM_CUDA(h, cudaMemsetAsync(S->big, 0, (size_t)X.rows, s));
+      count_launch();
+      k_prod_rows<true, kHashBits, kProdWarps><<<g, 32 * kProdWarps, sm, s>>>(
+          X, Y.rp, Y.col, Y.val, S->cnt, S->coff, S->tcol, S->tval, h->d_err, S->big, false);
+      unsigned long long *nbig = S->ctr + kMaxRounds + 2;
+      VEM_CUDA(h, cudaMemsetAsync(nbig, 0, sizeof(*nbig), s));
+      count_launch();
+      k_count_flags<<<rows_grid(X.rows), 256, 0, s>>>(X.rows, S->big, nbig);
+      unsigned long long nb = 0;
+      VEM_CUDA(h, cudaMemcpyAsync(&nb, nbig, sizeof(nb), cudaMemcpyDeviceToHost, s));
+      VEM_CUDA(h, cudaStreamSynchronize(s));
+      if (nb) {
+        const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nb, (int64_t)num_sms() * 2));
+        count_launch();
+        k_prod_rows<true, kBigBits, 1><<<gb, 32, smb, s>>>(X, Y.rp, Y.col, Y.val, S->cnt, S->coff, S->tcol,
+                                                            S->tval, h->d_err, S->big, true);
+      }
+    }
+    VEM_TRY(csr_layout(h, C, X.rows, Y.cols, S->cnt));
+    count_launch();
+    k_compact_rows<<<warps_grid(X.rows), 256, 0, s>>>(X.rows, S->coff, C.rp, S->tcol, S->tval, C.col, C.val);
+    VEM_CUDA(h, cudaGetLastError());
+    return VEM_OK;
+  }
+  // ---- two passes ----
   if (short_rows) {
     const int g = rows_grid(X.rows);
     VEM_CUDA(h, cudaMemsetAsync(ovf, 0, sizeof(*ovf), s));
@@ -1068,11 +1167,6 @@ static vem_status product(vem_handle *h, AmgState *S, const DMat &X, const CsrBu
                                                                ovf);
   } else {
     const int g = prod_grid(X.rows);
-    const size_t sm = prod_smem_bytes(kHashBits, kProdWarps), smb = prod_smem_bytes(kBigBits, 1);
-    VEM_CUDA(h, cudaFuncSetAttribute(k_prod_rows<false, kBigBits, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smb));
-    VEM_CUDA(h, cudaFuncSetAttribute(k_prod_rows<true, kBigBits, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smb));
     VEM_TRY(grow(h, S->big, S->c_big, (size_t)X.rows));
     VEM_CUDA(h, cudaMemsetAsync(S->big, 0, (size_t)X.rows, s));
     count_launch();
@@ -1127,24 +1221,32 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   VEM_CUDA(h, cudaMemsetAsync(S->ctr, 0, sizeof(unsigned long long) * (kMaxRounds + 4), s));
   count_launch();
   k_amg_strength<<<g, 256, 0, s>>>(A, S->dg, theta, S->flag, S->nstr, S->ctr);
-  // MIS-2 rounds; the host reads the undecided count every second round
+  // MIS-2 rounds.  The host reads the undecided counts after a batch of
+  // rounds: first as many as this level needed in the last setup (rounds
+  // after the set is complete change nothing), then two at a time.
   count_launch();
   k_mis_init<<<g, 256, 0, s>>>(n, S->tup);
   uint64_t *t1 = S->tup + n;
   int round = 0;
-  unsigned long long und = 1;
-  while (und != 0) {
-    if (round + 2 > kMaxRounds) return fail(h, VEM_ERR_CUDA, "AMG aggregation did not finish in %d rounds", kMaxRounds);
-    for (int k = 0; k < 2; ++k, ++round) {
+  int batch = std::max(2, L.mis_rounds);
+  int needed = 0;
+  while (needed == 0) {
+    if (round + batch > kMaxRounds) return fail(h, VEM_ERR_CUDA, "AMG aggregation did not finish in %d rounds", kMaxRounds);
+    for (int k = 0; k < batch; ++k, ++round) {
       count_launch();
       k_mis_max1<<<g, 256, 0, s>>>(A, S->flag, S->tup, t1);
       count_launch();
       k_mis_max2<<<g, 256, 0, s>>>(A, S->flag, t1, S->tup, S->ctr + 2 + round);
     }
     VEM_CUDA(h, cudaGetLastError());
-    VEM_CUDA(h, cudaMemcpyAsync(&und, S->ctr + 2 + round - 1, sizeof(und), cudaMemcpyDeviceToHost, s));
+    unsigned long long und[kMaxRounds];
+    VEM_CUDA(h, cudaMemcpyAsync(und, S->ctr + 2 + round - batch, sizeof(und[0]) * batch, cudaMemcpyDeviceToHost, s));
     VEM_CUDA(h, cudaStreamSynchronize(s));
+    for (int k = 0; k < batch && needed == 0; ++k)
+      if (und[k] == 0) needed = round - batch + k + 1;
+    batch = 2;
   }
+  L.mis_rounds = needed;
   unsigned long long mx[2] = {0, 0};
   VEM_CUDA(h, cudaMemcpyAsync(mx, S->ctr, sizeof(mx), cudaMemcpyDeviceToHost, s));
   // aggregates
