@@ -69,11 +69,14 @@ __global__ void k_rowcount(Layout L, int64_t *cnt) {
 // Batched use (gridDim.y systems): values of system b at val + b * stored,
 // diag(M) at diagM + b * n_u, local matrices scaled by nu_scale[b * nc + c]
 // (the local matrices then hold nu = 1); col == nullptr skips the (shared)
-// column ids.
+// column ids.  NFD / NID: face and interior DOFs per face / cell (E0: 1 / 0,
+// K1: 3 / 3), so the local-to-global map runs without divisions.
+template <int NFD, int NID>
 __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
                        int64_t nrows_pad, int32_t *col, double *val, double *diagM,
                        const double *__restrict__ nu_scale, int64_t stored) {
   const int64_t n = L.n_u + L.nc;
+  const int64_t nfr = (int64_t)NFD * L.nf;
   const int64_t bb = blockIdx.y;
   val += bb * stored;
   diagM += bb * L.n_u;
@@ -93,58 +96,91 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t 
   } while (0)
     if (r >= n) {
       // ghost row
-    } else if (r < L.nfd * L.nf) {
-      const int64_t f = r / L.nfd;
-      const int beta = (int)(r % L.nfd);
+    } else if (r < nfr) {
+      const int64_t f = r / NFD;
+      const int beta = (int)(r - f * NFD);
       const int32_t c0 = L.f_cell[2 * f], c1 = L.f_cell[2 * f + 1];
       const int l0 = L.f_loc[2 * f], l1 = L.f_loc[2 * f + 1];
-      const int n0 = nloc(L, c0);
-      const double *M0 = mloc(L, c0) + (int64_t)(l0 * L.nfd + beta) * n0;
+      const int64_t b0 = L.cfp[c0];
+      const int k0 = (int)(L.cfp[c0 + 1] - b0);
+      const int n0 = NFD * k0 + NID;
+      const double *M0 = mloc(L, c0) + (int64_t)(l0 * NFD + beta) * n0;
       const double *M1 = nullptr;
-      int n1 = 0;
+      int64_t b1 = 0;
+      int k1 = 0, n1 = 0;
       if (c1 >= 0) {
-        n1 = nloc(L, c1);
-        M1 = mloc(L, c1) + (int64_t)(l1 * L.nfd + beta) * n1;
+        b1 = L.cfp[c1];
+        k1 = (int)(L.cfp[c1 + 1] - b1);
+        n1 = NFD * k1 + NID;
+        M1 = mloc(L, c1) + (int64_t)(l1 * NFD + beta) * n1;
       }
       const double w0 = nsc ? nsc[c0] : 1.0, w1 = (nsc && c1 >= 0) ? nsc[c1] : 1.0;
       double dg = 0.0;
-      for (int jl = 0; jl < n0; ++jl) {
-        double v = w0 * M0[jl];
-        const bool shared = (jl < n0 - L.nid) && (jl / L.nfd == l0);
-        if (c1 >= 0 && shared) v += w1 * M1[l1 * L.nfd + jl % L.nfd];
-        if (shared && jl % L.nfd == beta) dg = v;
-        PUT(gcol(L, c0, jl), v);
-      }
-      if (c1 >= 0) {
-        const int k1 = (n1 - L.nid) / L.nfd;
-        for (int jl = 0; jl < n1; ++jl) {
-          if (jl < L.nfd * k1 && jl / L.nfd == l1) continue;
-          PUT(gcol(L, c1, jl), w1 * M1[jl]);
+      for (int i = 0; i < k0; ++i) {
+        const int64_t gc = (int64_t)NFD * L.cf[b0 + i];
+#pragma unroll
+        for (int bt = 0; bt < NFD; ++bt) {
+          double v = w0 * M0[i * NFD + bt];
+          if (i == l0) {
+            if (c1 >= 0) v += w1 * M1[l1 * NFD + bt];
+            if (bt == beta) dg = v;
+          }
+          PUT(gc + bt, v);
         }
       }
+#pragma unroll
+      for (int l = 0; l < NID; ++l) PUT(nfr + (int64_t)NID * c0 + l, w0 * M0[NFD * k0 + l]);
+      if (c1 >= 0) {
+        for (int i = 0; i < k1; ++i) {
+          if (i == l1) continue;
+          const int64_t gc = (int64_t)NFD * L.cf[b1 + i];
+#pragma unroll
+          for (int bt = 0; bt < NFD; ++bt) PUT(gc + bt, w1 * M1[i * NFD + bt]);
+        }
+#pragma unroll
+        for (int l = 0; l < NID; ++l) PUT(nfr + (int64_t)NID * c1 + l, w1 * M1[NFD * k1 + l]);
+      }
       if (beta == 0) {
-        PUT(L.n_u + c0, L.Bloc[boff(L, c0) + l0 * L.nfd]);
-        if (c1 >= 0) PUT(L.n_u + c1, L.Bloc[boff(L, c1) + l1 * L.nfd]);
+        PUT(L.n_u + c0, L.Bloc[boff(L, c0) + l0 * NFD]);
+        if (c1 >= 0) PUT(L.n_u + c1, L.Bloc[boff(L, c1) + l1 * NFD]);
       }
       diagM[r] = dg;
     } else if (r < L.n_u) {
-      const int64_t q = r - L.nfd * L.nf;
-      const int64_t c = q / L.nid;
-      const int l = (int)(q % L.nid);
-      const int nl = nloc(L, c);
-      const int jr = nl - L.nid + l;
-      const double *Mr = mloc(L, c) + (int64_t)jr * nl;
-      const double wc = nsc ? nsc[c] : 1.0;
-      for (int jl = 0; jl < nl; ++jl) PUT(gcol(L, c, jl), wc * Mr[jl]);
-      diagM[r] = wc * Mr[jr];
+      if constexpr (NID > 0) {
+        const int64_t q = r - nfr;
+        const int64_t c = q / NID;
+        const int l = (int)(q - c * NID);
+        const int64_t b0 = L.cfp[c];
+        const int k = (int)(L.cfp[c + 1] - b0);
+        const int nl = NFD * k + NID;
+        const int jr = nl - NID + l;
+        const double *Mr = mloc(L, c) + (int64_t)jr * nl;
+        const double wc = nsc ? nsc[c] : 1.0;
+        for (int i = 0; i < k; ++i) {
+          const int64_t gc = (int64_t)NFD * L.cf[b0 + i];
+#pragma unroll
+          for (int bt = 0; bt < NFD; ++bt) PUT(gc + bt, wc * Mr[i * NFD + bt]);
+        }
+#pragma unroll
+        for (int l2 = 0; l2 < NID; ++l2) PUT(nfr + (int64_t)NID * c + l2, wc * Mr[NFD * k + l2]);
+        diagM[r] = wc * Mr[jr];
+      }
     } else {
       const int64_t c = r - L.n_u;
       const int k = (int)(L.cfp[c + 1] - L.cfp[c]);
-      for (int i = 0; i < k; ++i) PUT((int64_t)L.nfd * L.cf[L.cfp[c] + i], L.Bloc[boff(L, c) + i * L.nfd]);
+      for (int i = 0; i < k; ++i) PUT((int64_t)NFD * L.cf[L.cfp[c] + i], L.Bloc[boff(L, c) + i * NFD]);
     }
     while (j < width) PUT(0, 0.0);
 #undef PUT
   }
+}
+
+static void launch_fill(cudaStream_t s, int nfd, dim3 grid, const Layout &L, const int64_t *off, const int32_t *len,
+                        int64_t npad, int32_t *col, double *val, double *diagM, const double *nu_scale,
+                        int64_t stored) {
+  count_launch();
+  if (nfd == 3) k_fill<3, 3><<<grid, 256, 0, s>>>(L, off, len, npad, col, val, diagM, nu_scale, stored);
+  else k_fill<1, 0><<<grid, 256, 0, s>>>(L, off, len, npad, col, val, diagM, nu_scale, stored);
 }
 
 // S = B diag(M)^{-1} B^T: row P holds sum_f B_Pf^2 / M_ff on the diagonal and
@@ -559,8 +595,8 @@ vem_status assemble_global(vem_handle *h) {
   VEM_TRY(sell_layout(h, h->A, n, cnt));
   if (!h->diagM) VEM_TRY(dalloc_n(h, &h->diagM, (size_t)h->n_u));
   const int64_t npad = h->A.nslices * 32;
-  count_launch(); k_fill<<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, h->A.len, npad, h->A.col, h->A.val, h->diagM,
-                                                      h->nu, h->A.stored);
+  launch_fill(s, h->nfd, dim3(grid_for(npad, T)), L, h->A.off, h->A.len, npad, h->A.col, h->A.val, h->diagM, h->nu,
+              h->A.stored);
   VEM_CUDA(h, cudaGetLastError());
   if (h->n_flux_faces > 0) {
     // prescribed flux DOFs: values, A x_fix with the full matrix (moved to the
@@ -872,8 +908,7 @@ vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, Ve
   const int T = 256;
   const int64_t npad = h->A.nslices * 32, spad = h->S.nslices * 32;
   dim3 ga(grid_for(npad, T, 2), nb), gs(grid_for(spad, T, 2), nb);
-  count_launch();
-  k_fill<<<ga, T, 0, s>>>(L, h->A.off, h->A.len, npad, nullptr, op.A.val, op.diagM, nu_b, h->A.stored);
+  launch_fill(s, h->nfd, ga, L, h->A.off, h->A.len, npad, nullptr, op.A.val, op.diagM, nu_b, h->A.stored);
   count_launch();
   k_schur_fill<<<gs, T, 0, s>>>(L, op.diagM, h->S.off, spad, nullptr, op.S.val, op.s_dinv, h->d_err, h->S.stored);
   count_launch();

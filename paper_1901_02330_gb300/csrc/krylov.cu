@@ -591,24 +591,54 @@ __global__ void k_diag_scale(int64_t nu, const double *__restrict__ v, const dou
 // Block upper-triangular flux part: z_u = (v_u - B^T z_p) / diag(M), with
 // B^T z_p gathered per face from its (at most two) cells.
 // (stacked rows R = b * n_u1 + r; pressure of cell c of system b at b * n_p1 + c)
-__global__ void k_tri_flux(int64_t nf, int nfd, int64_t n_u, int64_t n_u1, int64_t n_p1,
+// NFD: face DOFs per face (1 for E0, 3 for K1), a constant so the face of a
+// row is found without a division by a run-time value; kBatch: stacked
+// systems (the single system needs no division by n_u1 at all).
+template <int NFD, bool kBatch>
+__global__ void k_tri_flux(int64_t nf, int64_t n_u, int64_t n_u1, int64_t n_p1,
                            const double *__restrict__ v, const double *__restrict__ dM,
                            const int32_t *__restrict__ f_cell, const double *__restrict__ bt,
                            const double *__restrict__ zp, double *z) {
   for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < n_u;
        R += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = R / n_u1, r = R - b * n_u1;
+    int64_t b = 0, r = R;
+    if (kBatch) {
+      b = R / n_u1;
+      r = R - b * n_u1;
+    }
     double t = v[R];
-    if (r < nfd * nf && r % nfd == 0) {
-      const int64_t f = r / nfd;
-      const int32_t c0 = f_cell[2 * f], c1 = f_cell[2 * f + 1];
-      const double *zb = zp + b * n_p1;
-      double g = bt[2 * f] * zb[c0];
-      if (c1 >= 0) g += bt[2 * f + 1] * zb[c1];
-      t -= g;
+    if (r < NFD * nf) {
+      const int64_t f = r / NFD;
+      if (r == f * NFD) {
+        const int32_t c0 = f_cell[2 * f], c1 = f_cell[2 * f + 1];
+        const double *zb = zp + b * n_p1;
+        double g = bt[2 * f] * zb[c0];
+        if (c1 >= 0) g += bt[2 * f + 1] * zb[c1];
+        t -= g;
+      }
     }
     z[R] = t / dM[R];
   }
+}
+
+static void launch_tri_flux(cudaStream_t s, int nfd, bool batch, int64_t nf, int64_t n_u, int64_t n_u1,
+                            int64_t n_p1, const double *v, const double *dM, const int32_t *f_cell,
+                            const double *bt, const double *zp, double *z) {
+  const int g = grid_for(n_u, 256);
+  count_launch();
+  if (nfd == 3) {
+    if (batch) k_tri_flux<3, true><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dM, f_cell, bt, zp, z);
+    else k_tri_flux<3, false><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dM, f_cell, bt, zp, z);
+  } else {
+    if (batch) k_tri_flux<1, true><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dM, f_cell, bt, zp, z);
+    else k_tri_flux<1, false><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dM, f_cell, bt, zp, z);
+  }
+}
+
+__global__ void k_negate(int64_t n, double *x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = -x[i];
 }
 
 // z = w v and the partial of v . z (the pressure block W^-1 = I / gamma of
@@ -622,12 +652,6 @@ __global__ void k_scale_dot(int64_t n, const double *__restrict__ v, double w, d
     s += v[i] * zi;
   }
   if (part) block_partial(s, part);
-}
-
-__global__ void k_negate(int64_t n, double *x) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = -x[i];
 }
 
 // ------------------------------------------------------------ MINRES -----
@@ -859,8 +883,8 @@ static vem_status precond(vem_handle *h, const VemOp &op, const double *v, doubl
   } else {
     VEM_TRY(pcg_solve(h, op, v + nu, z + nu, wk, &it));
     count_launch(); k_negate<<<grid_for(np, 256), 256, 0, s>>>(np, z + nu);
-    count_launch(); k_tri_flux<<<grid_for(nu, 256), 256, 0, s>>>(h->nf, h->nfd, nu, op.n_u1, op.n_p1, v, op.diagM,
-                                                  h->f_cell, h->bt_face, z + nu, z);
+    launch_tri_flux(s, h->nfd, op.nbatch > 1, h->nf, nu, op.n_u1, op.n_p1, v, op.diagM, h->f_cell, h->bt_face,
+                    z + nu, z);
   }
   VEM_CUDA(h, cudaGetLastError());
   if (minres_partials)
