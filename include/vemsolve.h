@@ -353,8 +353,16 @@ vem_status vem_launch_count(int64_t *n);
 /* Message for the last failing call on this handle ("" if none). */
 const char *vem_last_error(const vem_handle *h);
 
-/* Free every device and host resource of the handle (NULL is a no-op). */
+/* Free every device and host resource of the handle (NULL is a no-op).
+ * Device memory goes back to the library's stream-ordered pool of the
+ * current device (freed in the handle's stream order), which keeps it
+ * reserved for the next handle; small pinned host buffers are kept too. */
 void vem_destroy(vem_handle *h);
+
+/* Return the unused memory of the current device's pool and the cached
+ * pinned host buffers to the system (synchronises the device).  Memory of
+ * live handles is unaffected. */
+vem_status vem_release_memory(void);
 
 #ifdef __cplusplus
 }

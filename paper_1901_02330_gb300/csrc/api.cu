@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "handle.cuh"
@@ -29,14 +31,73 @@ vem_status cuda_check(vem_handle *h, cudaError_t e, const char *what) {
   return fail(h, VEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Device memory comes from one stream-ordered pool per device that keeps
+// freed memory reserved (release threshold: unlimited), so a handle created
+// after another one was destroyed reuses its memory without cudaMalloc or
+// cudaFree (which synchronise the device).  vem_release_memory returns the
+// unused part to the system.
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static cudaError_t device_pool(cudaMemPool_t *out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool;
+  e = cudaMemPoolCreate(&pool, &props);
+  if (e != cudaSuccess) return e;
+  uint64_t thr = ~0ull;
+  e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  if (e != cudaSuccess) return e;
+  g_pools[dev] = pool;
+  *out = pool;
+  return cudaSuccess;
+}
+
+// Small pinned host buffers (scalar read-backs) are kept for the next handle
+// too: cudaMallocHost / cudaFreeHost are slow and may synchronise.
+static std::mutex g_pinned_mu;
+static std::vector<std::pair<void *, size_t>> g_pinned_free;
+
+static cudaError_t pinned_alloc(void **p, size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    for (size_t i = 0; i < g_pinned_free.size(); ++i)
+      if (g_pinned_free[i].second >= bytes) {
+        *p = g_pinned_free[i].first;
+        g_pinned_free.erase(g_pinned_free.begin() + (std::ptrdiff_t)i);
+        return cudaSuccess;
+      }
+  }
+  return cudaMallocHost(p, bytes);
+}
+
+static void pinned_free(void *p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.emplace_back(p, bytes);
+}
+
 vem_status dalloc(vem_handle *h, void **p, size_t bytes) {
   *p = nullptr;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaMemPool_t pool;
+  cudaError_t e = device_pool(&pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, h->stream);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
     return fail(h, e == cudaErrorMemoryAllocation ? VEM_ERR_OOM : VEM_ERR_CUDA,
-                "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+                "device allocation (%zu bytes): %s", bytes, cudaGetErrorString(e));
   }
   h->allocations.push_back(*p);
   return VEM_OK;
@@ -46,7 +107,7 @@ void dfree(vem_handle *h, void *p) {
   if (!p) return;
   auto it = std::find(h->allocations.begin(), h->allocations.end(), p);
   if (it != h->allocations.end()) h->allocations.erase(it);
-  cudaFree(p);
+  cudaFreeAsync(p, h->stream);
 }
 
 vem_status check_device_errors(vem_handle *h, const char *what) {
@@ -112,6 +173,117 @@ static vem_status upload(vem_handle *h, T **dst, const T *src, size_t n) {
   return VEM_OK;
 }
 
+// ---- mesh checks on the device (the arrays are uploaded first; these
+// kernels read them sequentially, no index is followed before it passed) ----
+enum {
+  MS_ERR = 0,        // error bits MSE_*
+  MS_BAD_FACE, MS_BAD_CELL, MS_BAD_FV, MS_BAD_CF, MS_BAD_X,   // smallest offending index
+  MS_MAXNV, MS_MAXNF, MS_NFLUX, MS_NDIR,
+  MS_LO, MS_HI = MS_LO + 3,                                      // ordered bits of min / max coordinates
+  MS_COUNT = MS_HI + 3
+};
+enum { MSE_FACE_NV = 1, MSE_FLAG = 2, MSE_CELL_NF = 4, MSE_VTX = 8, MSE_FACE = 16, MSE_COORD = 32 };
+
+// order-preserving map of a double to an unsigned integer
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+static double from_ordered(unsigned long long k) {
+  const unsigned long long u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  double d;
+  std::memcpy(&d, &u, sizeof(d));
+  return d;
+}
+
+__device__ __forceinline__ void warp_add(unsigned long long v, unsigned long long *out) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
+__global__ void k_check_faces(int64_t nf, const int64_t *__restrict__ fvp, const int8_t *__restrict__ fbc,
+                              unsigned long long *ms, int64_t *bq_cnt) {
+  unsigned long long nflux = 0, ndir = 0, mx = 0;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = fvp[f + 1] - fvp[f];
+    const int fl = fbc[f];
+    if (k < 3 || k > 4096) {
+      atomicOr(&ms[MS_ERR], (unsigned long long)MSE_FACE_NV);
+      atomicMin(&ms[MS_BAD_FACE], (unsigned long long)f);
+    }
+    if (fl < 0 || fl > 2) {
+      atomicOr(&ms[MS_ERR], (unsigned long long)MSE_FLAG);
+      atomicMin(&ms[MS_BAD_FACE], (unsigned long long)f);
+    }
+    nflux += fl == 2;
+    ndir += fl == 1;
+    if (k > 0 && (unsigned long long)k > mx) mx = (unsigned long long)k;
+    bq_cnt[f] = (fl != 0 && k > 0) ? 6 * k : 0;   // boundary-face load points: 6 per fan triangle
+  }
+  warp_add(nflux, &ms[MS_NFLUX]);
+  warp_add(ndir, &ms[MS_NDIR]);
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&ms[MS_MAXNV], mx);
+}
+
+__global__ void k_check_cells(int64_t nc, const int64_t *__restrict__ cfp, unsigned long long *ms) {
+  unsigned long long mx = 0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = cfp[c + 1] - cfp[c];
+    if (k < 4 || k > 256) {
+      atomicOr(&ms[MS_ERR], (unsigned long long)MSE_CELL_NF);
+      atomicMin(&ms[MS_BAD_CELL], (unsigned long long)c);
+    }
+    if (k > 0 && (unsigned long long)k > mx) mx = (unsigned long long)k;
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&ms[MS_MAXNF], mx);
+}
+
+__global__ void k_check_ids(int64_t n, const int32_t *__restrict__ ids, int64_t lim, int bit, int slot,
+                            unsigned long long *ms) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = ids[i];
+    if (v < 0 || v >= lim) {
+      atomicOr(&ms[MS_ERR], (unsigned long long)bit);
+      atomicMin(&ms[slot], (unsigned long long)i);
+    }
+  }
+}
+
+__global__ void k_check_coords(int64_t nv, const double *__restrict__ xyz, unsigned long long *ms) {
+  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int d = 0; d < 3; ++d) {
+      const double v = xyz[3 * i + d];
+      if (!isfinite(v)) {
+        atomicOr(&ms[MS_ERR], (unsigned long long)MSE_COORD);
+        atomicMin(&ms[MS_BAD_X], (unsigned long long)i);
+        continue;
+      }
+      const unsigned long long b = ordered_bits(v);
+      lo[d] = min(lo[d], b);
+      hi[d] = max(hi[d], b);
+    }
+  }
+  for (int d = 0; d < 3; ++d) {
+    unsigned long long a = lo[d], b = hi[d];
+    for (int o = 16; o > 0; o >>= 1) {
+      a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&ms[MS_LO + d], a);
+      atomicMax(&ms[MS_HI + d], b);
+    }
+  }
+}
+
+__global__ void k_fill_value(int64_t n, double v, double *a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
 static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
   if (!m || !m->xyz || !m->face_vtx_ptr || !m->face_vtx || !m->cell_face_ptr || !m->cell_face || !m->face_bc)
     return fail(h, VEM_ERR_BAD_INPUT, "mesh: NULL array");
@@ -122,49 +294,68 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
   h->nv = m->n_vertices;
   h->nf = m->n_faces;
   h->nc = m->n_cells;
-  h->h_fv_ptr.assign(m->face_vtx_ptr, m->face_vtx_ptr + h->nf + 1);
-  h->h_cf_ptr.assign(m->cell_face_ptr, m->cell_face_ptr + h->nc + 1);
-  h->h_fbc.assign(m->face_bc, m->face_bc + h->nf);
-  if (h->h_fv_ptr[0] != 0 || h->h_cf_ptr[0] != 0) return fail(h, VEM_ERR_BAD_INPUT, "mesh: pointers must start at 0");
-  for (int64_t f = 0; f < h->nf; ++f) {
-    const int64_t k = h->h_fv_ptr[f + 1] - h->h_fv_ptr[f];
-    if (k < 3 || k > 4096) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face %lld has %lld vertices", (long long)f, (long long)k);
-    h->max_nv_face = std::max<int>(h->max_nv_face, (int)k);
-    if (h->h_fbc[f] < 0 || h->h_fbc[f] > 2) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face flag %d", (int)h->h_fbc[f]);
-    h->n_flux_faces += h->h_fbc[f] == 2;
-    h->n_dir_faces += h->h_fbc[f] == 1;
-  }
-  for (int64_t c = 0; c < h->nc; ++c) {
-    const int64_t k = h->h_cf_ptr[c + 1] - h->h_cf_ptr[c];
-    if (k < 4 || k > 256) return fail(h, VEM_ERR_BAD_INPUT, "mesh: cell %lld has %lld faces", (long long)c, (long long)k);
-    h->max_nf_cell = std::max<int>(h->max_nf_cell, (int)k);
-  }
-  h->multiplier = h->n_flux_faces > 0 && h->n_dir_faces == 0;
-  h->n_fv = h->h_fv_ptr[h->nf];
-  h->n_cf = h->h_cf_ptr[h->nc];
-  for (int64_t i = 0; i < h->n_fv; ++i)
-    if (m->face_vtx[i] < 0 || m->face_vtx[i] >= h->nv) return fail(h, VEM_ERR_BAD_INPUT, "mesh: vertex index out of range");
-  for (int64_t i = 0; i < h->n_cf; ++i)
-    if (m->cell_face[i] < 0 || m->cell_face[i] >= h->nf) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face index out of range");
-  double lo[3] = {m->xyz[0], m->xyz[1], m->xyz[2]}, hi[3] = {lo[0], lo[1], lo[2]};
-  for (int64_t i = 0; i < 3 * h->nv; ++i) {
-    if (!std::isfinite(m->xyz[i])) return fail(h, VEM_ERR_NONFINITE, "mesh: non-finite coordinate");
-    lo[i % 3] = std::min(lo[i % 3], m->xyz[i]);
-    hi[i % 3] = std::max(hi[i % 3], m->xyz[i]);
-  }
-  h->lref = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
-                      (hi[2] - lo[2]) * (hi[2] - lo[2]));
-  if (!(h->lref > 0.0)) return fail(h, VEM_ERR_DEGENERATE_MESH, "mesh: zero extent");
+  if (m->face_vtx_ptr[0] != 0 || m->cell_face_ptr[0] != 0)
+    return fail(h, VEM_ERR_BAD_INPUT, "mesh: pointers must start at 0");
+  h->n_fv = m->face_vtx_ptr[h->nf];
+  h->n_cf = m->cell_face_ptr[h->nc];
+  if (h->n_fv < 3 * h->nf || h->n_fv > 4096 * h->nf || h->n_cf < 4 * h->nc || h->n_cf > 256 * h->nc)
+    return fail(h, VEM_ERR_BAD_INPUT, "mesh: face_vtx_ptr / cell_face_ptr totals out of range");
   set_layout(h);
 
-  VEM_CUDA(h, cudaMallocHost(&h->h_err, sizeof(int)));
-  VEM_CUDA(h, cudaMallocHost(&h->h_scal, 8192 * sizeof(double)));
+  VEM_CUDA(h, pinned_alloc(reinterpret_cast<void **>(&h->h_err), 64));
+  VEM_CUDA(h, pinned_alloc(reinterpret_cast<void **>(&h->h_scal), 8192 * sizeof(double)));
   VEM_TRY(upload(h, &h->xyz, m->xyz, 3 * (size_t)h->nv));
   VEM_TRY(upload(h, &h->fv_ptr, m->face_vtx_ptr, (size_t)h->nf + 1));
   VEM_TRY(upload(h, &h->fv, m->face_vtx, (size_t)h->n_fv));
   VEM_TRY(upload(h, &h->cf_ptr, m->cell_face_ptr, (size_t)h->nc + 1));
   VEM_TRY(upload(h, &h->cf, m->cell_face, (size_t)h->n_cf));
   VEM_TRY(upload(h, &h->fbc, m->face_bc, (size_t)h->nf));
+  // checks and summaries of the mesh, one read-back
+  {
+    cudaStream_t s = h->stream;
+    unsigned long long *ms = nullptr;
+    VEM_TRY(dalloc_n(h, &ms, (size_t)MS_COUNT));
+    unsigned long long init[MS_COUNT];
+    for (int i = 0; i < MS_COUNT; ++i) init[i] = 0;
+    for (int i = MS_BAD_FACE; i <= MS_BAD_X; ++i) init[i] = ~0ull;
+    for (int d = 0; d < 3; ++d) init[MS_LO + d] = ~0ull;
+    VEM_CUDA(h, cudaMemcpyAsync(ms, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    int64_t *bq_cnt = nullptr;
+    VEM_TRY(dalloc_n(h, &bq_cnt, (size_t)h->nf + 1));
+    count_launch(); k_check_faces<<<grid_for(h->nf, 256), 256, 0, s>>>(h->nf, h->fv_ptr, h->fbc, ms, bq_cnt);
+    count_launch(); k_check_cells<<<grid_for(h->nc, 256), 256, 0, s>>>(h->nc, h->cf_ptr, ms);
+    count_launch(); k_check_ids<<<grid_for(h->n_fv, 256), 256, 0, s>>>(h->n_fv, h->fv, h->nv, MSE_VTX, MS_BAD_FV, ms);
+    count_launch(); k_check_ids<<<grid_for(h->n_cf, 256), 256, 0, s>>>(h->n_cf, h->cf, h->nf, MSE_FACE, MS_BAD_CF, ms);
+    count_launch(); k_check_coords<<<grid_for(h->nv, 256), 256, 0, s>>>(h->nv, h->xyz, ms);
+    VEM_CUDA(h, cudaGetLastError());
+    unsigned long long r[MS_COUNT];
+    VEM_CUDA(h, cudaMemcpyAsync(r, ms, sizeof(r), cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+    dfree(h, ms);
+    const unsigned long long e = r[MS_ERR];
+    if (e & MSE_FACE_NV) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face %llu needs 3..4096 vertices", r[MS_BAD_FACE]);
+    if (e & MSE_FLAG) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face %llu has a flag outside 0..2", r[MS_BAD_FACE]);
+    if (e & MSE_CELL_NF) return fail(h, VEM_ERR_BAD_INPUT, "mesh: cell %llu needs 4..256 faces", r[MS_BAD_CELL]);
+    if (e & MSE_VTX) return fail(h, VEM_ERR_BAD_INPUT, "mesh: vertex index out of range (face_vtx[%llu])", r[MS_BAD_FV]);
+    if (e & MSE_FACE) return fail(h, VEM_ERR_BAD_INPUT, "mesh: face index out of range (cell_face[%llu])", r[MS_BAD_CF]);
+    if (e & MSE_COORD) return fail(h, VEM_ERR_NONFINITE, "mesh: non-finite coordinate (vertex %llu)", r[MS_BAD_X]);
+    h->max_nv_face = (int)r[MS_MAXNV];
+    h->max_nf_cell = (int)r[MS_MAXNF];
+    h->n_flux_faces = (int64_t)r[MS_NFLUX];
+    h->n_dir_faces = (int64_t)r[MS_NDIR];
+    double ext2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double w = from_ordered(r[MS_HI + d]) - from_ordered(r[MS_LO + d]);
+      ext2 += w * w;
+    }
+    h->lref = std::sqrt(ext2);
+    if (!(h->lref > 0.0)) return fail(h, VEM_ERR_DEGENERATE_MESH, "mesh: zero extent");
+    // boundary-face quadrature offsets from the per-face counts
+    VEM_TRY(dalloc_n(h, &h->bqp_off, (size_t)h->nf + 1));
+    VEM_TRY(scan_counts(h, h->nf, bq_cnt, h->bqp_off, &h->n_bqp));
+    dfree(h, bq_cnt);
+  }
+  h->multiplier = h->n_flux_faces > 0 && h->n_dir_faces == 0;
   VEM_TRY(dalloc_n(h, &h->f_area, h->nf));
   VEM_TRY(dalloc_n(h, &h->f_cent, 3 * h->nf));
   VEM_TRY(dalloc_n(h, &h->f_norm, 3 * h->nf));
@@ -183,20 +374,11 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
   VEM_TRY(dalloc_n(h, &h->ctr, 64));
   VEM_CUDA(h, cudaMemsetAsync(h->ctr, 0, 64 * sizeof(unsigned int), h->stream));
   VEM_CUDA(h, cudaMemsetAsync(h->scal, 0, 8192 * sizeof(double), h->stream));
-  // boundary-face quadrature offsets (6 points per fan triangle)
-  h->h_bqp_off.assign(h->nf + 1, 0);
-  for (int64_t f = 0; f < h->nf; ++f)
-    h->h_bqp_off[f + 1] = h->h_bqp_off[f] + (h->h_fbc[f] != 0 ? 6 * (h->h_fv_ptr[f + 1] - h->h_fv_ptr[f]) : 0);
-  h->n_bqp = h->h_bqp_off[h->nf];
-  VEM_TRY(upload(h, &h->bqp_off, h->h_bqp_off.data(), (size_t)h->nf + 1));
   VEM_TRY(dalloc_n(h, &h->bqp_xyz, 3 * (size_t)std::max<int64_t>(h->n_bqp, 1)));
   // coefficient nu = 1/K, default K = 1
   VEM_TRY(dalloc_n(h, &h->nu, h->nc));
-  {
-    std::vector<double> ones(h->nc, 1.0);
-    VEM_CUDA(h, cudaMemcpyAsync(h->nu, ones.data(), sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->stream));
-    VEM_CUDA(h, cudaStreamSynchronize(h->stream));
-  }
+  count_launch(); k_fill_value<<<grid_for(h->nc, 256), 256, 0, h->stream>>>(h->nc, 1.0, h->nu);
+  VEM_CUDA(h, cudaGetLastError());
   h->have_coef = true;
   VEM_TRY(dalloc_n(h, &h->f_qp, h->nc));
   VEM_TRY(dalloc_n(h, &h->gD_qp, std::max<int64_t>(h->n_bqp, 1)));
@@ -775,11 +957,22 @@ vem_status vem_get_geometry(vem_handle *h, double *fa, double *fc, double *fn, d
   return VEM_OK;
 }
 
+static std::vector<int64_t> host_cell_face_ptr(const vem_handle *h) {
+  std::vector<int64_t> p(h->nc + 1);
+  if (cudaMemcpy(p.data(), h->cf_ptr, sizeof(int64_t) * (h->nc + 1), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    p.assign(h->nc + 1, 0);
+  }
+  return p;
+}
+
 vem_status vem_local_size(const vem_handle *h, int64_t *m_total, int64_t *b_total) {
   if (!h || !m_total || !b_total) return VEM_ERR_BAD_INPUT;
+  cudaStreamSynchronize(h->stream);
+  const std::vector<int64_t> cfp = host_cell_face_ptr(h);
   int64_t mt = 0;
   for (int64_t c = 0; c < h->nc; ++c) {
-    const int64_t nl = h->nfd * (h->h_cf_ptr[c + 1] - h->h_cf_ptr[c]) + h->nid;
+    const int64_t nl = h->nfd * (cfp[c + 1] - cfp[c]) + h->nid;
     mt += nl * nl;
   }
   *m_total = mt;
@@ -802,9 +995,10 @@ vem_status vem_get_local(vem_handle *h, double *M_out, int64_t *M_offsets, doubl
   VEM_CUDA(h, cudaMemcpyAsync(bo.data(), h->b_off, sizeof(int64_t) * (h->ncls + 1), cudaMemcpyDeviceToHost, s));
   VEM_CUDA(h, cudaMemcpyAsync(cls.data(), h->cls_of, sizeof(int32_t) * h->nc, cudaMemcpyDeviceToHost, s));
   VEM_CUDA(h, cudaStreamSynchronize(s));
+  const std::vector<int64_t> cfp = host_cell_face_ptr(h);
   int64_t om = 0, ob = 0;
   for (int64_t c = 0; c < h->nc; ++c) {
-    const int64_t nl = h->nfd * (h->h_cf_ptr[c + 1] - h->h_cf_ptr[c]) + h->nid;
+    const int64_t nl = h->nfd * (cfp[c + 1] - cfp[c]) + h->nid;
     const int k = cls[c];
     if (M_offsets) M_offsets[c] = om;
     if (M_out)
@@ -921,6 +1115,22 @@ vem_status vem_amg_vcycle_device(vem_handle *h, int32_t which, const double *b_d
   return VEM_OK;
 }
 
+vem_status vem_release_memory(void) {
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return VEM_ERR_CUDA;
+  }
+  cudaMemPool_t pool;
+  if (device_pool(&pool) != cudaSuccess || cudaMemPoolTrimTo(pool, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return VEM_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  for (auto &b : g_pinned_free) cudaFreeHost(b.first);
+  g_pinned_free.clear();
+  return VEM_OK;
+}
+
 void vem_destroy(vem_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -928,10 +1138,11 @@ void vem_destroy(vem_handle *h) {
   vem::amg_free(h->amg_reg);
   if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-  for (void *p : h->allocations) cudaFree(p);
+  for (void *p : h->allocations) cudaFreeAsync(p, h->stream);
+  if (!h->allocations.empty()) cudaStreamSynchronize(h->stream);
   h->allocations.clear();
-  if (h->h_err) cudaFreeHost(h->h_err);
-  if (h->h_scal) cudaFreeHost(h->h_scal);
+  pinned_free(h->h_err, 64);
+  pinned_free(h->h_scal, 8192 * sizeof(double));
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ev2) cudaEventDestroy(h->ev2);

@@ -40,8 +40,6 @@ struct vem_handle {
   int64_t n_u = 0, n_p = 0, n = 0;
 
   // ---- host copies of small topology arrays ----
-  std::vector<int8_t> h_fbc;
-  std::vector<int64_t> h_fv_ptr, h_cf_ptr, h_bqp_off;
 
   // ---- device mesh ----
   double *xyz = nullptr;

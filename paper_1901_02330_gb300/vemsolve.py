@@ -99,6 +99,7 @@ _SIGS = {
     "vem_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
     "vem_last_error": (C.c_char_p, [C.c_void_p]),
     "vem_destroy": (None, [C.c_void_p]),
+    "vem_release_memory": (C.c_int, []),
 }
 
 
@@ -122,6 +123,14 @@ def launch_count() -> int:
     n = C.c_int64()
     lib().vem_launch_count(C.byref(n))
     return n.value
+
+
+def release_memory() -> None:
+    """Return the unused part of the library's device memory pool (and its
+    cached pinned host buffers) to the system."""
+    st = lib().vem_release_memory()
+    if st != VEM_OK:
+        raise VemError(st, "vem_release_memory")
 
 
 def residual_norm_noalloc(row_ptr, col, val, x, b, out, stream: int = 0) -> None:

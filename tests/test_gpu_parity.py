@@ -274,3 +274,70 @@ def test_reuse_of_congruent_cells(vs, mname, expect_few, ename):
         assert st1["n_classes"] == mesh.n_cells
     assert np.linalg.norm(u1 - u0) <= 1e-11 * np.linalg.norm(u0)
     assert np.linalg.norm(p1 - p0) <= 1e-11 * np.linalg.norm(p0)
+
+
+def test_bad_mesh_inputs(vs):
+    """The mesh is checked on the device before any kernel follows its
+    indices: out-of-range vertex and face ids, short faces and cells, face
+    flags and coordinates are refused with a status, and the device stays
+    usable (a valid mesh solves afterwards)."""
+    mesh = hex_mesh(2)
+
+    def variant(**kw):
+        a = dict(xyz=mesh.xyz.copy(), fvp=mesh.face_vtx_ptr.copy(), fv=mesh.face_vtx.copy(),
+                 cfp=mesh.cell_face_ptr.copy(), cf=mesh.cell_face.copy(), bc=mesh.face_bc.copy())
+        a.update(kw)
+        return type(mesh)(a["xyz"], a["fvp"], a["fv"], a["cfp"], a["cf"], a["bc"])
+
+    fv = mesh.face_vtx.copy()
+    fv[5] = mesh.n_vertices + 3
+    cf = mesh.cell_face.copy()
+    cf[2] = -1
+    bc = mesh.face_bc.copy()
+    bc[0] = 7
+    xyz = mesh.xyz.copy()
+    xyz[4, 1] = np.nan
+    # first face with two vertices: move one vertex id to the next face
+    fvp = mesh.face_vtx_ptr.copy()
+    fvp[1] = 2
+    cfp = mesh.cell_face_ptr.copy()
+    cfp[1] = 3
+    cases = [(variant(fv=fv), 1), (variant(cf=cf), 1), (variant(bc=bc), 1), (variant(xyz=xyz), 5),
+             (variant(fvp=fvp), 1), (variant(cfp=cfp), 1)]
+    for bad, code in cases:
+        with pytest.raises(vs.VemError) as e:
+            vs.Solver(bad)
+        assert e.value.code == code, (e.value, code)
+    prob = fields.sine_problem()
+    s = _solver(vs, mesh, 0, krylov=1, precond=1, rtol=1e-10, inner_rtol=1e-12)
+    try:
+        s.set_data(prob.f, prob.gD)
+        _, _, st = s.solve()
+    finally:
+        s.close()
+    assert st["relres"] <= 1e-10
+
+
+def test_memory_pool_reuse_and_release(vs):
+    """Handles created after others were destroyed reuse the pool's memory
+    and give the same solution bit for bit; releasing the pool's unused
+    memory leaves live handles working."""
+    mesh = hex_mesh(4)
+    prob = fields.sine_problem()
+    outs = []
+    for _ in range(2):
+        s = _solver(vs, mesh, 1, krylov=1, precond=1, rtol=1e-10, inner_rtol=1e-12)
+        s.set_data(prob.f, prob.gD)
+        outs.append(s.solve()[:2])
+        s.close()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    s = _solver(vs, mesh, 1, krylov=1, precond=1, rtol=1e-10, inner_rtol=1e-12)
+    try:
+        s.set_data(prob.f, prob.gD)
+        vs.release_memory()
+        u, p, st = s.solve()
+    finally:
+        s.close()
+    vs.release_memory()
+    np.testing.assert_array_equal(u, outs[0][0])
