@@ -123,6 +123,7 @@ vem_status check_device_errors(vem_handle *h, const char *what) {
   if (e & DEVERR_NONCONVEX) return fail(h, VEM_ERR_DEGENERATE_MESH, "%s: non-convex cell", what);
   if (e & DEVERR_SINGULAR_LOCAL) return fail(h, VEM_ERR_DEGENERATE_MESH, "%s: singular local Gram matrix", what);
   if (e & DEVERR_NONFINITE) return fail(h, VEM_ERR_NONFINITE, "%s: NaN or Inf in data", what);
+  if (e & DEVERR_NONPOSITIVE) return fail(h, VEM_ERR_BAD_INPUT, "%s: K <= 0", what);
   if (e & DEVERR_AMG_DIAG) return fail(h, VEM_ERR_BREAKDOWN, "%s: non-positive diagonal or pivot", what);
   if (e & DEVERR_AMG_ROW)
     return fail(h, VEM_ERR_UNSUPPORTED, "%s: a row of an AMG product has too many distinct columns", what);
@@ -425,13 +426,23 @@ static vem_status assemble_impl(vem_handle *h) {
   return VEM_OK;
 }
 
+// nu = 1/K (K may alias nu); non-finite K raise DEVERR_NONFINITE, K <= 0
+// DEVERR_NONPOSITIVE.
 __global__ void k_invert_check(int64_t n, const double *K, double *nu, int *err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double k = K[i];
-    if (!(k > 0.0) || !isfinite(k)) atomicOr(err, DEVERR_NONFINITE);
+    if (!isfinite(k)) atomicOr(err, DEVERR_NONFINITE);
+    else if (!(k > 0.0)) atomicOr(err, DEVERR_NONPOSITIVE);
     nu[i] = 1.0 / k;
   }
+}
+
+// Non-finite entries of a vector raise DEVERR_NONFINITE.
+__global__ void k_check_finite(int64_t n, const double *__restrict__ a, int *err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(a[i])) atomicOr(err, DEVERR_NONFINITE);
 }
 
 __global__ void k_export_x(int64_t nu, int64_t np, const double *x, double *u, double *p) {
@@ -589,54 +600,82 @@ vem_status vem_quadrature_points(vem_handle *h, int which, double *xyz_out) {
   return VEM_OK;
 }
 
+// K (device) -> nu = 1/K with the checks on the device; on a bad K the old
+// nu is kept (the new values go to a scratch first).
+static vem_status set_nu_from_device(vem_handle *h, const double *K) {
+  double *tmp = nullptr;
+  VEM_TRY(dalloc_n(h, &tmp, (size_t)h->nc));
+  count_launch(); k_invert_check<<<grid_for(h->nc, 256), 256, 0, h->stream>>>(h->nc, K, tmp, h->d_err);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int e = *h->h_err;
+  if (e & (DEVERR_NONFINITE | DEVERR_NONPOSITIVE)) {
+    VEM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+    dfree(h, tmp);
+    if (e & DEVERR_NONFINITE) return fail(h, VEM_ERR_NONFINITE, "K is not finite");
+    return fail(h, VEM_ERR_BAD_INPUT, "K <= 0");
+  }
+  VEM_CUDA(h, cudaMemcpyAsync(h->nu, tmp, sizeof(double) * h->nc, cudaMemcpyDeviceToDevice, h->stream));
+  dfree(h, tmp);
+  h->assembled = false;
+  h->have_solution = false;
+  return check_device_errors(h, "coefficient");
+}
+
 vem_status vem_set_coefficient(vem_handle *h, const double *K) {
   if (!h) return VEM_ERR_BAD_INPUT;
   if (!K) return fail(h, VEM_ERR_BAD_INPUT, "K: NULL");
-  std::vector<double> nu(h->nc);
-  for (int64_t c = 0; c < h->nc; ++c) {
-    if (!std::isfinite(K[c])) return fail(h, VEM_ERR_NONFINITE, "K[%lld] is not finite", (long long)c);
-    if (!(K[c] > 0.0)) return fail(h, VEM_ERR_BAD_INPUT, "K[%lld] <= 0", (long long)c);
-    nu[c] = 1.0 / K[c];
-  }
-  VEM_CUDA(h, cudaMemcpyAsync(h->nu, nu.data(), sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->stream));
-  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
-  h->assembled = false;
-  h->have_solution = false;
-  return VEM_OK;
+  double *Kd = nullptr;
+  VEM_TRY(dalloc_n(h, &Kd, (size_t)h->nc));
+  vem_status st = cuda_check(h, cudaMemcpyAsync(Kd, K, sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->stream),
+                             "K upload");
+  if (st == VEM_OK) st = set_nu_from_device(h, Kd);
+  dfree(h, Kd);
+  return st;
 }
 
 vem_status vem_set_coefficient_device(vem_handle *h, const double *K) {
   if (!h) return VEM_ERR_BAD_INPUT;
   if (!K) return fail(h, VEM_ERR_BAD_INPUT, "K: NULL");
-  count_launch(); k_invert_check<<<grid_for(h->nc, 256), 256, 0, h->stream>>>(h->nc, K, h->nu, h->d_err);
-  VEM_CUDA(h, cudaGetLastError());
-  h->assembled = false;
-  h->have_solution = false;
-  vem_status st = check_device_errors(h, "coefficient");
-  if (st == VEM_ERR_NONFINITE) return fail(h, VEM_ERR_BAD_INPUT, "K must be finite and > 0");
-  return st;
+  return set_nu_from_device(h, K);
 }
 
 vem_status vem_set_source(vem_handle *h, const double *f_qp, const double *gD_qp) {
   if (!h) return VEM_ERR_BAD_INPUT;
+  cudaStream_t s = h->stream;
+  // the new data go to scratch buffers and are checked on the device; the
+  // handle's data change only when they are finite
+  double *fs = nullptr, *gs = nullptr;
   if (f_qp) {
-    for (int64_t i = 0; i < h->nc; ++i)
-      if (!std::isfinite(f_qp[i])) return fail(h, VEM_ERR_NONFINITE, "f is not finite at point %lld", (long long)i);
-    VEM_CUDA(h, cudaMemcpyAsync(h->f_qp, f_qp, sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->stream));
-  } else {
-    VEM_CUDA(h, cudaMemsetAsync(h->f_qp, 0, sizeof(double) * h->nc, h->stream));
+    VEM_TRY(dalloc_n(h, &fs, (size_t)h->nc));
+    VEM_CUDA(h, cudaMemcpyAsync(fs, f_qp, sizeof(double) * h->nc, cudaMemcpyHostToDevice, s));
+    count_launch(); k_check_finite<<<grid_for(h->nc, 256), 256, 0, s>>>(h->nc, fs, h->d_err);
   }
+  if (h->n_bqp > 0 && gD_qp) {
+    VEM_TRY(dalloc_n(h, &gs, (size_t)h->n_bqp));
+    VEM_CUDA(h, cudaMemcpyAsync(gs, gD_qp, sizeof(double) * h->n_bqp, cudaMemcpyHostToDevice, s));
+    count_launch(); k_check_finite<<<grid_for(h->n_bqp, 256), 256, 0, s>>>(h->n_bqp, gs, h->d_err);
+  }
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  if (*h->h_err & DEVERR_NONFINITE) {
+    VEM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+    dfree(h, fs);
+    dfree(h, gs);
+    return fail(h, VEM_ERR_NONFINITE, "f or g_D is not finite at a quadrature point");
+  }
+  if (fs) VEM_CUDA(h, cudaMemcpyAsync(h->f_qp, fs, sizeof(double) * h->nc, cudaMemcpyDeviceToDevice, s));
+  else VEM_CUDA(h, cudaMemsetAsync(h->f_qp, 0, sizeof(double) * h->nc, s));
   if (h->n_bqp > 0) {
-    if (gD_qp) {
-      for (int64_t i = 0; i < h->n_bqp; ++i)
-        if (!std::isfinite(gD_qp[i])) return fail(h, VEM_ERR_NONFINITE, "g_D is not finite at point %lld", (long long)i);
-      VEM_CUDA(h, cudaMemcpyAsync(h->gD_qp, gD_qp, sizeof(double) * h->n_bqp, cudaMemcpyHostToDevice, h->stream));
-    } else {
-      VEM_CUDA(h, cudaMemsetAsync(h->gD_qp, 0, sizeof(double) * h->n_bqp, h->stream));
-    }
+    if (gs) VEM_CUDA(h, cudaMemcpyAsync(h->gD_qp, gs, sizeof(double) * h->n_bqp, cudaMemcpyDeviceToDevice, s));
+    else VEM_CUDA(h, cudaMemsetAsync(h->gD_qp, 0, sizeof(double) * h->n_bqp, s));
   }
-  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  dfree(h, fs);
+  dfree(h, gs);
   h->rhs_ready = false;
+  if (h->n_flux_faces > 0) h->assembled = false;   // the flux data is eliminated at assembly
   return VEM_OK;
 }
 

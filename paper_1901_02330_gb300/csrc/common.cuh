@@ -21,6 +21,7 @@ enum : int {
   DEVERR_SINGULAR_LOCAL = 32,
   DEVERR_AMG_DIAG = 64,        // AMG: non-positive diagonal or pivot
   DEVERR_AMG_ROW = 128,        // AMG: a product row exceeds its column list
+  DEVERR_NONPOSITIVE = 256,    // a coefficient K <= 0
 };
 
 struct Status {

@@ -89,16 +89,49 @@ __global__ void k_cell_geom(int64_t nc, const int64_t *__restrict__ cfp,
       int8_t s = hc > 0.0 ? 1 : -1;
       if (s != cf_sigma[b + i] || hc == 0.0) bad = 1;
     }
-    double dm2 = 0;   // squared diameter (one square root at the end)
-    for (int i = 0; i < k; ++i) {
+    // squared diameter (one square root at the end): the largest distance
+    // between two vertices, over the cell's distinct vertices (a vertex is
+    // listed by every face that has it); cells with more than kCapV distinct
+    // vertices take all pairs of face-vertex references instead (the same
+    // maximum)
+    constexpr int kCapV = 64;
+    int32_t vu[kCapV];
+    int nvu = 0;
+    bool many = false;
+    for (int i = 0; i < k && !many; ++i) {
       const int f = cf[b + i];
       for (int64_t p = fvp[f]; p < fvp[f + 1]; ++p) {
-        double3 A = load3(xyz, fv[p]);
-        for (int j = i; j < k; ++j) {
-          const int g = cf[b + j];
-          for (int64_t q = fvp[g]; q < fvp[g + 1]; ++q) {
-            const double3 d = sub3(A, load3(xyz, fv[q]));
-            dm2 = fmax(dm2, dot3(d, d));
+        const int32_t v = fv[p];
+        bool seen = false;
+        for (int t = 0; t < nvu && !seen; ++t) seen = vu[t] == v;
+        if (seen) continue;
+        if (nvu == kCapV) {
+          many = true;
+          break;
+        }
+        vu[nvu++] = v;
+      }
+    }
+    double dm2 = 0;
+    if (!many) {
+      for (int a = 0; a < nvu; ++a) {
+        const double3 A = load3(xyz, vu[a]);
+        for (int t = a + 1; t < nvu; ++t) {
+          const double3 d = sub3(A, load3(xyz, vu[t]));
+          dm2 = fmax(dm2, dot3(d, d));
+        }
+      }
+    } else {
+      for (int i = 0; i < k; ++i) {
+        const int f = cf[b + i];
+        for (int64_t p = fvp[f]; p < fvp[f + 1]; ++p) {
+          double3 A = load3(xyz, fv[p]);
+          for (int j = i; j < k; ++j) {
+            const int g = cf[b + j];
+            for (int64_t q = fvp[g]; q < fvp[g + 1]; ++q) {
+              const double3 d = sub3(A, load3(xyz, fv[q]));
+              dm2 = fmax(dm2, dot3(d, d));
+            }
           }
         }
       }
