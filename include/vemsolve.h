@@ -92,7 +92,13 @@ typedef struct {
   const int8_t *face_bc;          /* [n_faces] */
 } vem_mesh;
 
-enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1 };
+/* Elements: E0 (face moments against M_0(f), P0 pressure), K1 (the paper's
+ * k = 1: 3 face moments, 3 cross moments, P0 pressure), K2 (the paper's
+ * k = 2, Sec. 4.1-4.3: 6 face moments against M_2(f), 3 gradient and 11
+ * cross moments, P1 pressure moments).  K2 provides the element matrices
+ * only (vem_assemble_local, vem_get_local); vem_assemble and vem_solve give
+ * VEM_ERR_UNSUPPORTED for it. */
+enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1, VEM_ELEMENT_K2 = 2 };
 enum { VEM_KRYLOV_MINRES = 0, VEM_KRYLOV_FGMRES = 1 };
 /* Block preconditioners of the saddle-point system [M B^T; B 0] (Sec. 5):
  *   BLOCK_DIAG  diag(diag(M), S) with S = B diag(M)^-1 B^T (Block-Schur,
@@ -271,13 +277,21 @@ vem_status vem_get_geometry(vem_handle *h, double *face_area, double *face_centr
                             double *face_normal, double *face_diam, double *cell_volume,
                             double *cell_centroid, double *cell_diam);
 
-/* Local matrices after vem_assemble: for each cell, M_P (n_loc x n_loc,
- * row-major) and B_P (n_loc) in the cell's local DOF order (its faces in
- * cell_face order, nfd moments each, then nid interior DOFs), with
- * n_loc = nfd * n_faces(cell) + nid.  vem_local_size gives the total
- * lengths; M_offsets[n_cells + 1] receives the start of each cell's M_P in
- * M_out (in doubles); B_P of cell c starts at nfd * cell_face_ptr[c] + nid * c
- * in B_out.  Host buffers; any may be NULL. */
+/* Element matrices only (every element; the only assembly step of K2):
+ * the geometry-only local matrices of every congruence class of cells, on
+ * the device; vem_local_time reports the element kernel's time (ms, CUDA
+ * events) and the number of classes evaluated. */
+vem_status vem_assemble_local(vem_handle *h);
+vem_status vem_local_time(const vem_handle *h, double *element_ms, int64_t *n_classes);
+
+/* Local matrices after vem_assemble or vem_assemble_local: for each cell,
+ * M_P (n_loc x n_loc, row-major) and B_P (nq x n_loc, row-major; nq = 1, or
+ * 4 for K2) in the cell's local DOF order (its faces in cell_face order, nfd
+ * moments each, then nid interior DOFs), with n_loc = nfd * n_faces(cell) +
+ * nid.  vem_local_size gives the total lengths; M_offsets[n_cells + 1]
+ * receives the start of each cell's M_P in M_out (in doubles); B_P of cell
+ * c starts at nq * (nfd * cell_face_ptr[c] + nid * c) in B_out.  Host
+ * buffers; any may be NULL. */
 vem_status vem_local_size(const vem_handle *h, int64_t *m_total, int64_t *b_total);
 vem_status vem_get_local(vem_handle *h, double *M_out, int64_t *M_offsets, double *B_out);
 

@@ -131,7 +131,7 @@ vem_status check_device_errors(vem_handle *h, const char *what) {
 }
 
 static vem_status check_options(vem_handle *h, const vem_options *o) {
-  if (o->element != VEM_ELEMENT_E0 && o->element != VEM_ELEMENT_K1)
+  if (o->element != VEM_ELEMENT_E0 && o->element != VEM_ELEMENT_K1 && o->element != VEM_ELEMENT_K2)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown element %d", o->element);
   if (o->krylov != VEM_KRYLOV_MINRES && o->krylov != VEM_KRYLOV_FGMRES)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown Krylov method %d", o->krylov);
@@ -155,7 +155,12 @@ static vem_status check_options(vem_handle *h, const vem_options *o) {
 }
 
 static void set_layout(vem_handle *h) {
-  if (h->opt.element == VEM_ELEMENT_K1) {
+  h->nq = 1;
+  if (h->opt.element == VEM_ELEMENT_K2) {
+    h->nfd = 6;
+    h->nid = 14;
+    h->nq = 4;
+  } else if (h->opt.element == VEM_ELEMENT_K1) {
     h->nfd = 3;
     h->nid = 3;
   } else {
@@ -163,7 +168,7 @@ static void set_layout(vem_handle *h) {
     h->nid = 0;
   }
   h->n_u = h->nfd * h->nf + h->nid * h->nc;
-  h->n_p = h->nc;
+  h->n_p = (int64_t)h->nq * h->nc;
   h->n = h->n_u + h->n_p;
 }
 
@@ -402,6 +407,10 @@ static vem_status ensure_rhs(vem_handle *h) {
 }
 
 static vem_status assemble_impl(vem_handle *h) {
+  if (h->opt.element == VEM_ELEMENT_K2)
+    return fail(h, VEM_ERR_UNSUPPORTED,
+                "paper k = 2: global assembly and solves are not built (vem_assemble_local gives the element "
+                "matrices)");
   amg_invalidate(h->amg);
   amg_invalidate(h->amg_reg);
   h->areg_valid = false;
@@ -548,6 +557,7 @@ vem_status vem_set_options(vem_handle *h, const vem_options *opt) {
   if (elem_changed) {
     set_layout(h);
     h->assembled = false;
+    h->local_ready = false;
     h->rhs_ready = false;
     h->have_solution = false;
     dfree(h, h->rhs);
@@ -699,6 +709,27 @@ vem_status vem_set_source_device(vem_handle *h, const double *f_qp, const double
 vem_status vem_assemble(vem_handle *h) {
   if (!h) return VEM_ERR_BAD_INPUT;
   return assemble_impl(h);
+}
+
+vem_status vem_assemble_local(vem_handle *h) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  VEM_CUDA(h, cudaEventRecord(h->ev2, h->stream));
+  VEM_TRY(classify_cells(h));
+  VEM_TRY(assemble_local(h));
+  VEM_CUDA(h, cudaEventRecord(h->ev3, h->stream));
+  VEM_CUDA(h, cudaEventSynchronize(h->ev3));
+  float me = 0.f;
+  VEM_CUDA(h, cudaEventElapsedTime(&me, h->ev2, h->ev3));
+  h->t_element_ms = me;
+  h->local_ready = true;
+  return VEM_OK;
+}
+
+vem_status vem_local_time(const vem_handle *h, double *element_ms, int64_t *n_classes) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (element_ms) *element_ms = h->t_element_ms;
+  if (n_classes) *n_classes = h->ncls;
+  return VEM_OK;
 }
 
 vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_out, vem_stats *stats) {
@@ -1015,13 +1046,14 @@ vem_status vem_local_size(const vem_handle *h, int64_t *m_total, int64_t *b_tota
     mt += nl * nl;
   }
   *m_total = mt;
-  *b_total = h->nfd * h->n_cf + h->nid * h->nc;
+  *b_total = (int64_t)h->nq * (h->nfd * h->n_cf + h->nid * h->nc);
   return VEM_OK;
 }
 
 vem_status vem_get_local(vem_handle *h, double *M_out, int64_t *M_offsets, double *B_out) {
   if (!h) return VEM_ERR_BAD_INPUT;
-  if (!h->assembled) return fail(h, VEM_ERR_BAD_INPUT, "vem_get_local before vem_assemble");
+  if (!h->assembled && !h->local_ready)
+    return fail(h, VEM_ERR_BAD_INPUT, "vem_get_local before vem_assemble / vem_assemble_local");
   cudaStream_t s = h->stream;
   // stored per congruence class with nu = 1: expand to M_P = nu_P Mhat, B_P = Bhat
   std::vector<double> Mc(h->m_total), Bc(h->b_total), nu(h->nc);
@@ -1043,9 +1075,9 @@ vem_status vem_get_local(vem_handle *h, double *M_out, int64_t *M_offsets, doubl
     if (M_out)
       for (int64_t e = 0; e < nl * nl; ++e) M_out[om + e] = nu[c] * Mc[mo[k] + e];
     if (B_out)
-      for (int64_t e = 0; e < nl; ++e) B_out[ob + e] = Bc[bo[k] + e];
+      for (int64_t e = 0; e < h->nq * nl; ++e) B_out[ob + e] = Bc[bo[k] + e];
     om += nl * nl;
-    ob += nl;
+    ob += h->nq * nl;
   }
   if (M_offsets) M_offsets[h->nc] = om;
   return VEM_OK;

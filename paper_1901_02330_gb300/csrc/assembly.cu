@@ -795,7 +795,7 @@ __global__ void k_class_flags(int64_t nc, const int32_t *__restrict__ rep, int64
 }
 
 // idx = exclusive scan of the flags: class of c = idx[rep[c]]; class sizes
-__global__ void k_class_assign(int64_t nc, int nfd, int nid, const int32_t *__restrict__ rep,
+__global__ void k_class_assign(int64_t nc, int nfd, int nid, int nq, const int32_t *__restrict__ rep,
                                const int64_t *__restrict__ idx, const int64_t *__restrict__ cfp,
                                int32_t *cls_of, int32_t *cls_rep, int64_t *msz, int64_t *bsz) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
@@ -806,7 +806,7 @@ __global__ void k_class_assign(int64_t nc, int nfd, int nid, const int32_t *__re
       cls_rep[k] = (int32_t)c;
       const int64_t nl = nfd * (cfp[c + 1] - cfp[c]) + nid;
       msz[k] = nl * nl;
-      bsz[k] = nl;
+      bsz[k] = nq * nl;
     }
   }
 }
@@ -872,7 +872,7 @@ vem_status classify_cells(vem_handle *h) {
   int64_t ncls = 0;
   VEM_TRY(scan_counts(h, nc, flag, idx, &ncls));
   count_launch();
-  k_class_assign<<<grid_for(nc, T), T, 0, s>>>(nc, h->nfd, h->nid, rep, idx, h->cf_ptr, h->cls_of, h->cls_rep,
+  k_class_assign<<<grid_for(nc, T), T, 0, s>>>(nc, h->nfd, h->nid, h->nq, rep, idx, h->cf_ptr, h->cls_of, h->cls_rep,
                                                 msz, bsz);
   VEM_CUDA(h, cudaGetLastError());
   int64_t mt = 0, bt = 0;

@@ -530,6 +530,8 @@ vem_status assemble_local(vem_handle *h) {
         ncls, mx, h->cf_ptr, h->cf, h->cf_sigma, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm,
         h->f_t1, h->f_diam, h->c_cent, h->c_diam, h->cls_rep, h->m_off, h->b_off, h->Mloc, h->Bloc, h->d_err);
     VEM_CUDA(h, cudaGetLastError());
+  } else if (h->opt.element == VEM_ELEMENT_K2) {
+    VEM_TRY(element_k2(h));
   } else {
     return fail(h, VEM_ERR_UNSUPPORTED, "element %d", h->opt.element);
   }

@@ -34,6 +34,8 @@ struct vem_handle {
   // ---- mesh sizes ----
   int64_t nv = 0, nf = 0, nc = 0, n_fv = 0, n_cf = 0;
   int max_nf_cell = 0, max_nv_face = 0;
+  int nq = 1;                                    // pressure DOFs per cell (4 for paper k = 2)
+  bool local_ready = false;                      // element matrices of the current coefficients
 
   // ---- DOF layout (depends on the element) ----
   int nfd = 1, nid = 0;
@@ -214,6 +216,7 @@ vem_status adjoint_contract(vem_handle *h, const double *lam, const double *x, d
 // geometry.cu)
 vem_status flux_fixed(vem_handle *h, double *xfix);
 vem_status bface_info(vem_handle *h, double *nout, int8_t *flag);
+vem_status element_k2(vem_handle *h);       // paper k = 2 local matrices (element_k2.cu)
 vem_status neumann_rhs(vem_handle *h, double *rhs);
 vem_status neumann_mean_free(vem_handle *h, int64_t n, const double *b, double *out);
 vem_status neumann_shift(vem_handle *h, double *xp);

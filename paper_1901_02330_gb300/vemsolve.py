@@ -19,7 +19,7 @@ VEM_OK = 0
 STATUS = {0: "VEM_OK", 1: "VEM_ERR_BAD_INPUT", 2: "VEM_ERR_DEGENERATE_MESH", 3: "VEM_ERR_NOT_CONVERGED",
           4: "VEM_ERR_BREAKDOWN", 5: "VEM_ERR_NONFINITE", 6: "VEM_ERR_OOM", 7: "VEM_ERR_CUDA",
           8: "VEM_ERR_UNSUPPORTED"}
-VEM_ELEMENT_E0, VEM_ELEMENT_K1 = 0, 1
+VEM_ELEMENT_E0, VEM_ELEMENT_K1, VEM_ELEMENT_K2 = 0, 1, 2
 VEM_KRYLOV_MINRES, VEM_KRYLOV_FGMRES = 0, 1
 VEM_PREC_BLOCK_DIAG, VEM_PREC_BLOCK_TRI, VEM_PREC_BLOCK_REG = 0, 1, 2
 VEM_AMG_SCHUR, VEM_AMG_REG = 0, 1
@@ -85,6 +85,8 @@ _SIGS = {
     "vem_get_geometry": (C.c_int, [C.c_void_p] + [C.c_void_p] * 7),
     "vem_local_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "vem_get_local": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vem_assemble_local": (C.c_int, [C.c_void_p]),
+    "vem_local_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "vem_get_system": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_get_schur": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_apply_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -352,15 +354,24 @@ class Solver:
         off = np.zeros(self.n_cells + 1, dtype=np.int64)
         B = np.zeros(bt.value)
         self._check(lib().vem_get_local(self._h, _ptr(M), _ptr(off), _ptr(B)))
-        nfd = 3 if self.options.element == VEM_ELEMENT_K1 else 1
-        nid = 3 if self.options.element == VEM_ELEMENT_K1 else 0
+        nfd, nid, nq = {VEM_ELEMENT_E0: (1, 0, 1), VEM_ELEMENT_K1: (3, 3, 1),
+                        VEM_ELEMENT_K2: (6, 14, 4)}[self.options.element]
         out = []
         for c in range(self.n_cells):
             k = int(self.cell_face_ptr[c + 1] - self.cell_face_ptr[c])
             nl = nfd * k + nid
-            b0 = nfd * int(self.cell_face_ptr[c]) + nid * c
-            out.append((M[off[c]:off[c] + nl * nl].reshape(nl, nl), B[b0:b0 + nl]))
+            b0 = nq * (nfd * int(self.cell_face_ptr[c]) + nid * c)
+            Bc = B[b0:b0 + nq * nl]
+            out.append((M[off[c]:off[c] + nl * nl].reshape(nl, nl), Bc if nq == 1 else Bc.reshape(nq, nl)))
         return out
+
+    def assemble_local(self):
+        """Element matrices only (vem_assemble_local); returns (element kernel
+        ms, classes evaluated)."""
+        self._check(lib().vem_assemble_local(self._h))
+        ms, nc = C.c_double(), C.c_int64()
+        self._check(lib().vem_local_time(self._h, C.byref(ms), C.byref(nc)))
+        return ms.value, nc.value
 
     def system(self):
         """(A as scipy CSR [M B^T; B 0], rhs [g; F])."""
