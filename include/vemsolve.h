@@ -95,9 +95,13 @@ typedef struct {
 /* Elements: E0 (face moments against M_0(f), P0 pressure), K1 (the paper's
  * k = 1: 3 face moments, 3 cross moments, P0 pressure), K2 (the paper's
  * k = 2, Sec. 4.1-4.3: 6 face moments against M_2(f), 3 gradient and 11
- * cross moments, P1 pressure moments).  K2 provides the element matrices
- * only (vem_assemble_local, vem_get_local); vem_assemble and vem_solve give
- * VEM_ERR_UNSUPPORTED for it. */
+ * cross moments, P1 pressure moments: 4 pressure unknowns per cell, cell c's
+ * at n_u + 4c .. n_u + 4c + 3).  K2 solves Dirichlet problems with the
+ * block-diagonal and block-triangular preconditioners (Jacobi-PCG or AMG for
+ * S); prescribed-flux faces, Block-Reg, vem_solve_batched and vem_adjoint
+ * give VEM_ERR_UNSUPPORTED with it.  Its cell quadrature points
+ * (VEM_QP_CELL) are those of a degree-3 rule on the fan tetrahedra of every
+ * cell (27 per tetrahedron), built on first use. */
 enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1, VEM_ELEMENT_K2 = 2 };
 enum { VEM_KRYLOV_MINRES = 0, VEM_KRYLOV_FGMRES = 1 };
 /* Block preconditioners of the saddle-point system [M B^T; B 0] (Sec. 5):

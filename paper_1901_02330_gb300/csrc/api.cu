@@ -407,10 +407,8 @@ static vem_status ensure_rhs(vem_handle *h) {
 }
 
 static vem_status assemble_impl(vem_handle *h) {
-  if (h->opt.element == VEM_ELEMENT_K2)
-    return fail(h, VEM_ERR_UNSUPPORTED,
-                "paper k = 2: global assembly and solves are not built (vem_assemble_local gives the element "
-                "matrices)");
+  if (h->nq > 1 && h->n_flux_faces > 0)
+    return fail(h, VEM_ERR_UNSUPPORTED, "paper k = 2 with prescribed-flux faces");
   amg_invalidate(h->amg);
   amg_invalidate(h->amg_reg);
   h->areg_valid = false;
@@ -583,21 +581,43 @@ vem_status vem_sizes(const vem_handle *h, int64_t *n_u, int64_t *n_p) {
   return VEM_OK;
 }
 
-vem_status vem_quadrature_count(const vem_handle *h, int which, int64_t *n) {
-  if (!h || !n) return VEM_ERR_BAD_INPUT;
-  if (which == VEM_QP_CELL) *n = h->nc;
-  else if (which == VEM_QP_BFACE) *n = h->n_bqp;
-  else return VEM_ERR_BAD_INPUT;
+// cell points: one per cell (its barycentre) for E0 / K1, the fan-tetrahedron
+// rule of the k = 2 loads otherwise
+static int64_t n_cell_points(const vem_handle *h) { return h->nq > 1 ? h->n_cqp : h->nc; }
+
+static vem_status ensure_cell_points(vem_handle *h) {
+  if (h->nq == 1) return VEM_OK;
+  const bool had = h->cqp_valid;
+  VEM_TRY(cell_points_k2(h));
+  if (!had) {
+    // the source buffer holds one value per cell point
+    dfree(h, h->f_qp);
+    h->f_qp = nullptr;
+    VEM_TRY(dalloc_n(h, &h->f_qp, (size_t)std::max<int64_t>(h->n_cqp, 1)));
+    VEM_CUDA(h, cudaMemsetAsync(h->f_qp, 0, sizeof(double) * std::max<int64_t>(h->n_cqp, 1), h->stream));
+    h->rhs_ready = false;
+  }
   return VEM_OK;
 }
 
+vem_status vem_quadrature_count(const vem_handle *hc, int which, int64_t *n) {
+  if (!hc || !n) return VEM_ERR_BAD_INPUT;
+  vem_handle *h = const_cast<vem_handle *>(hc);   // the k = 2 points are built on first use
+  if (which == VEM_QP_CELL) {
+    VEM_TRY(ensure_cell_points(h));
+    *n = n_cell_points(h);
+  } else if (which == VEM_QP_BFACE) *n = h->n_bqp;
+  else return VEM_ERR_BAD_INPUT;
+  return VEM_OK;
+}
 vem_status vem_quadrature_points(vem_handle *h, int which, double *xyz_out) {
   if (!h || !xyz_out) return h ? fail(h, VEM_ERR_BAD_INPUT, "NULL output") : VEM_ERR_BAD_INPUT;
   const double *src = nullptr;
   int64_t n = 0;
   if (which == VEM_QP_CELL) {
-    src = h->c_cent;
-    n = h->nc;
+    VEM_TRY(ensure_cell_points(h));
+    src = h->nq > 1 ? h->cqp_x : h->c_cent;
+    n = n_cell_points(h);
   } else if (which == VEM_QP_BFACE) {
     src = h->bqp_xyz;
     n = h->n_bqp;
@@ -657,10 +677,12 @@ vem_status vem_set_source(vem_handle *h, const double *f_qp, const double *gD_qp
   // the new data go to scratch buffers and are checked on the device; the
   // handle's data change only when they are finite
   double *fs = nullptr, *gs = nullptr;
+  VEM_TRY(ensure_cell_points(h));
+  const int64_t ncp = n_cell_points(h);
   if (f_qp) {
-    VEM_TRY(dalloc_n(h, &fs, (size_t)h->nc));
-    VEM_CUDA(h, cudaMemcpyAsync(fs, f_qp, sizeof(double) * h->nc, cudaMemcpyHostToDevice, s));
-    count_launch(); k_check_finite<<<grid_for(h->nc, 256), 256, 0, s>>>(h->nc, fs, h->d_err);
+    VEM_TRY(dalloc_n(h, &fs, (size_t)ncp));
+    VEM_CUDA(h, cudaMemcpyAsync(fs, f_qp, sizeof(double) * ncp, cudaMemcpyHostToDevice, s));
+    count_launch(); k_check_finite<<<grid_for(ncp, 256), 256, 0, s>>>(ncp, fs, h->d_err);
   }
   if (h->n_bqp > 0 && gD_qp) {
     VEM_TRY(dalloc_n(h, &gs, (size_t)h->n_bqp));
@@ -676,8 +698,8 @@ vem_status vem_set_source(vem_handle *h, const double *f_qp, const double *gD_qp
     dfree(h, gs);
     return fail(h, VEM_ERR_NONFINITE, "f or g_D is not finite at a quadrature point");
   }
-  if (fs) VEM_CUDA(h, cudaMemcpyAsync(h->f_qp, fs, sizeof(double) * h->nc, cudaMemcpyDeviceToDevice, s));
-  else VEM_CUDA(h, cudaMemsetAsync(h->f_qp, 0, sizeof(double) * h->nc, s));
+  if (fs) VEM_CUDA(h, cudaMemcpyAsync(h->f_qp, fs, sizeof(double) * ncp, cudaMemcpyDeviceToDevice, s));
+  else VEM_CUDA(h, cudaMemsetAsync(h->f_qp, 0, sizeof(double) * ncp, s));
   if (h->n_bqp > 0) {
     if (gs) VEM_CUDA(h, cudaMemcpyAsync(h->gD_qp, gs, sizeof(double) * h->n_bqp, cudaMemcpyDeviceToDevice, s));
     else VEM_CUDA(h, cudaMemsetAsync(h->gD_qp, 0, sizeof(double) * h->n_bqp, s));
@@ -691,10 +713,12 @@ vem_status vem_set_source(vem_handle *h, const double *f_qp, const double *gD_qp
 
 vem_status vem_set_source_device(vem_handle *h, const double *f_qp, const double *gD_qp) {
   if (!h) return VEM_ERR_BAD_INPUT;
+  VEM_TRY(ensure_cell_points(h));
+  const int64_t ncp = n_cell_points(h);
   if (f_qp)
-    VEM_CUDA(h, cudaMemcpyAsync(h->f_qp, f_qp, sizeof(double) * h->nc, cudaMemcpyDeviceToDevice, h->stream));
+    VEM_CUDA(h, cudaMemcpyAsync(h->f_qp, f_qp, sizeof(double) * ncp, cudaMemcpyDeviceToDevice, h->stream));
   else
-    VEM_CUDA(h, cudaMemsetAsync(h->f_qp, 0, sizeof(double) * h->nc, h->stream));
+    VEM_CUDA(h, cudaMemsetAsync(h->f_qp, 0, sizeof(double) * ncp, h->stream));
   if (h->n_bqp > 0) {
     if (gD_qp)
       VEM_CUDA(h, cudaMemcpyAsync(h->gD_qp, gD_qp, sizeof(double) * h->n_bqp, cudaMemcpyDeviceToDevice, h->stream));
@@ -826,6 +850,7 @@ vem_status vem_adjoint(vem_handle *h, const double *dL_du, const double *dL_dp, 
   if (!h->have_solution || !h->assembled)
     return fail(h, VEM_ERR_BAD_INPUT, "vem_adjoint needs a preceding vem_solve with the same K");
   if (h->n_flux_faces > 0) return fail(h, VEM_ERR_UNSUPPORTED, "adjoint with prescribed-flux faces");
+  if (h->nq > 1) return fail(h, VEM_ERR_UNSUPPORTED, "adjoint of the paper k = 2 element");
   cudaStream_t s = h->stream;
   if (!h->lam) VEM_TRY(dalloc_n(h, &h->lam, (size_t)h->n));
   if (!h->arhs) VEM_TRY(dalloc_n(h, &h->arhs, (size_t)h->n));
@@ -879,6 +904,7 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
     return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver is single-system (no batched solves)");
   if (h->opt.precond == VEM_PREC_BLOCK_REG)
     return fail(h, VEM_ERR_UNSUPPORTED, "Block-Reg is single-system (no batched solves)");
+  if (h->nq > 1) return fail(h, VEM_ERR_UNSUPPORTED, "paper k = 2 in batched solves");
   if (h->n_flux_faces > 0)
     return fail(h, VEM_ERR_UNSUPPORTED, "prescribed-flux faces in batched solves");
   cudaStream_t s = h->stream;

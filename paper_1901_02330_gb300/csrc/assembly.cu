@@ -581,7 +581,258 @@ vem_status sell_to_host_csr(vem_handle *h, const SellMat &M, int64_t *rp, int32_
   return VEM_OK;
 }
 
+// ---- several pressure DOFs per cell (paper k = 2: NQ = 4) ----
+// B_P is NQ x n_loc (row-major at Bloc + b_off): every local DOF couples to
+// every pressure DOF of its cell.  Pressure unknown q of cell c sits at
+// n_u + NQ c + q.
+template <int NFD, int NID, int NQ>
+__global__ void k_rowcount_q(Layout L, int64_t *cnt) {
+  const int64_t nfr = (int64_t)NFD * L.nf;
+  const int64_t n = L.n_u + (int64_t)NQ * L.nc;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v;
+    if (r < nfr) {
+      const int64_t f = r / NFD;
+      const int32_t c0 = L.f_cell[2 * f], c1 = L.f_cell[2 * f + 1];
+      const int64_t k0 = L.cfp[c0 + 1] - L.cfp[c0];
+      v = NFD * k0 + NID + NQ;
+      if (c1 >= 0) v += NFD * (L.cfp[c1 + 1] - L.cfp[c1]) + NID - NFD + NQ;
+    } else if (r < L.n_u) {
+      const int64_t c = (r - nfr) / NID;
+      v = NFD * (L.cfp[c + 1] - L.cfp[c]) + NID + NQ;
+    } else {
+      const int64_t c = (r - L.n_u) / NQ;
+      v = NFD * (L.cfp[c + 1] - L.cfp[c]) + NID;
+    }
+    cnt[r] = v;
+  }
+}
+
+template <int NFD, int NID, int NQ>
+__global__ void k_fill_q(Layout L, const int64_t *__restrict__ off, int64_t nrows_pad, int32_t *col, double *val,
+                         double *diagM, const double *__restrict__ nsc) {
+  const int64_t nfr = (int64_t)NFD * L.nf;
+  const int64_t n = L.n_u + (int64_t)NQ * L.nc;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows_pad;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s0 = off[r >> 5];
+    const int width = (int)((off[(r >> 5) + 1] - s0) >> 5);
+    const int64_t lane = r & 31;
+    int j = 0;
+#define PUT(c_, v_)                                   \
+  do {                                                \
+    const int64_t q_ = s0 + ((int64_t)j << 5) + lane; \
+    col[q_] = (int32_t)(c_);                          \
+    val[q_] = (v_);                                   \
+    ++j;                                              \
+  } while (0)
+    if (r >= n) {
+      // ghost row
+    } else if (r < nfr) {
+      const int64_t f = r / NFD;
+      const int beta = (int)(r - f * NFD);
+      const int32_t c0 = L.f_cell[2 * f], c1 = L.f_cell[2 * f + 1];
+      const int l0 = L.f_loc[2 * f], l1 = L.f_loc[2 * f + 1];
+      const int64_t b0 = L.cfp[c0];
+      const int k0 = (int)(L.cfp[c0 + 1] - b0);
+      const int n0 = NFD * k0 + NID;
+      const double *M0 = mloc(L, c0) + (int64_t)(l0 * NFD + beta) * n0;
+      const double *B0 = L.Bloc + boff(L, c0);
+      const double *M1 = nullptr, *B1 = nullptr;
+      int64_t b1 = 0;
+      int k1 = 0, n1 = 0;
+      if (c1 >= 0) {
+        b1 = L.cfp[c1];
+        k1 = (int)(L.cfp[c1 + 1] - b1);
+        n1 = NFD * k1 + NID;
+        M1 = mloc(L, c1) + (int64_t)(l1 * NFD + beta) * n1;
+        B1 = L.Bloc + boff(L, c1);
+      }
+      const double w0 = nsc[c0], w1 = c1 >= 0 ? nsc[c1] : 1.0;
+      double dg = 0.0;
+      for (int i = 0; i < k0; ++i) {
+        const int64_t gc = (int64_t)NFD * L.cf[b0 + i];
+        for (int bt = 0; bt < NFD; ++bt) {
+          double v = w0 * M0[i * NFD + bt];
+          if (i == l0) {
+            if (c1 >= 0) v += w1 * M1[l1 * NFD + bt];
+            if (bt == beta) dg = v;
+          }
+          PUT(gc + bt, v);
+        }
+      }
+      for (int l = 0; l < NID; ++l) PUT(nfr + (int64_t)NID * c0 + l, w0 * M0[NFD * k0 + l]);
+      if (c1 >= 0) {
+        for (int i = 0; i < k1; ++i) {
+          if (i == l1) continue;
+          const int64_t gc = (int64_t)NFD * L.cf[b1 + i];
+          for (int bt = 0; bt < NFD; ++bt) PUT(gc + bt, w1 * M1[i * NFD + bt]);
+        }
+        for (int l = 0; l < NID; ++l) PUT(nfr + (int64_t)NID * c1 + l, w1 * M1[NFD * k1 + l]);
+      }
+      for (int q = 0; q < NQ; ++q) PUT(L.n_u + (int64_t)NQ * c0 + q, B0[q * n0 + l0 * NFD + beta]);
+      if (c1 >= 0)
+        for (int q = 0; q < NQ; ++q) PUT(L.n_u + (int64_t)NQ * c1 + q, B1[q * n1 + l1 * NFD + beta]);
+      diagM[r] = dg;
+    } else if (r < L.n_u) {
+      const int64_t c = (r - nfr) / NID;
+      const int l = (int)(r - nfr - c * NID);
+      const int64_t b0 = L.cfp[c];
+      const int k = (int)(L.cfp[c + 1] - b0);
+      const int nl = NFD * k + NID;
+      const int jr = nl - NID + l;
+      const double *Mr = mloc(L, c) + (int64_t)jr * nl;
+      const double *Bc = L.Bloc + boff(L, c);
+      const double wc = nsc[c];
+      for (int i = 0; i < k; ++i) {
+        const int64_t gc = (int64_t)NFD * L.cf[b0 + i];
+        for (int bt = 0; bt < NFD; ++bt) PUT(gc + bt, wc * Mr[i * NFD + bt]);
+      }
+      for (int l2 = 0; l2 < NID; ++l2) PUT(nfr + (int64_t)NID * c + l2, wc * Mr[NFD * k + l2]);
+      for (int q = 0; q < NQ; ++q) PUT(L.n_u + (int64_t)NQ * c + q, Bc[q * nl + jr]);
+      diagM[r] = wc * Mr[jr];
+    } else {
+      const int64_t c = (r - L.n_u) / NQ;
+      const int q = (int)(r - L.n_u - c * NQ);
+      const int64_t b0 = L.cfp[c];
+      const int k = (int)(L.cfp[c + 1] - b0);
+      const int nl = NFD * k + NID;
+      const double *Bq = L.Bloc + boff(L, c) + (int64_t)q * nl;
+      for (int i = 0; i < k; ++i) {
+        const int64_t gc = (int64_t)NFD * L.cf[b0 + i];
+        for (int bt = 0; bt < NFD; ++bt) PUT(gc + bt, Bq[i * NFD + bt]);
+      }
+      for (int l = 0; l < NID; ++l) PUT(nfr + (int64_t)NID * c + l, Bq[NFD * k + l]);
+    }
+    while (j < width) PUT(0, 0.0);
+#undef PUT
+  }
+}
+
+// S = B diag(M)^-1 B^T with NQ pressure DOFs per cell: row (P, q) holds the
+// NQ x NQ block of P (all its local DOFs) and one NQ block per neighbour Q
+// across an interior face (that face's NFD DOFs).
+template <int NFD, int NID, int NQ>
+__global__ void k_schur_count_q(Layout L, int64_t *cnt) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < (int64_t)NQ * L.nc;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = r / NQ;
+    int64_t v = NQ;
+    for (int64_t p = L.cfp[c]; p < L.cfp[c + 1]; ++p) v += (L.f_cell[2 * L.cf[p] + 1] >= 0) ? NQ : 0;
+    cnt[r] = v;
+  }
+}
+
+template <int NFD, int NID, int NQ>
+__global__ void k_schur_fill_q(Layout L, const double *__restrict__ diagM, const int64_t *__restrict__ off,
+                               int64_t nrows_pad, int32_t *col, double *val, double *dinv, int *err) {
+  const int64_t nfr = (int64_t)NFD * L.nf;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows_pad;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s0 = off[r >> 5];
+    const int width = (int)((off[(r >> 5) + 1] - s0) >> 5);
+    const int64_t lane = r & 31;
+    int j = 0;
+    if (r < (int64_t)NQ * L.nc) {
+      const int64_t c = r / NQ;
+      const int q = (int)(r - c * NQ);
+      const int64_t b0 = L.cfp[c];
+      const int k = (int)(L.cfp[c + 1] - b0);
+      const int nl = NFD * k + NID;
+      const double *Bc = L.Bloc + boff(L, c);
+      // own block: all local DOFs
+      for (int q2 = 0; q2 < NQ; ++q2) {
+        double v = 0.0;
+        for (int i = 0; i < k; ++i) {
+          const int64_t gc = (int64_t)NFD * L.cf[b0 + i];
+          for (int bt = 0; bt < NFD; ++bt)
+            v += Bc[q * nl + i * NFD + bt] * Bc[q2 * nl + i * NFD + bt] / diagM[gc + bt];
+        }
+        for (int l = 0; l < NID; ++l)
+          v += Bc[q * nl + NFD * k + l] * Bc[q2 * nl + NFD * k + l] / diagM[nfr + (int64_t)NID * c + l];
+        const int64_t p = s0 + ((int64_t)j << 5) + lane;
+        col[p] = (int32_t)(NQ * c + q2);
+        val[p] = v;
+        ++j;
+        if (q2 == q) {
+          if (!(v > 0.0) || !isfinite(v)) atomicOr(err, DEVERR_NONFINITE);
+          dinv[r] = 1.0 / v;
+        }
+      }
+      // neighbours across interior faces
+      for (int i = 0; i < k; ++i) {
+        const int f = L.cf[b0 + i];
+        const int32_t f0 = L.f_cell[2 * f], f1 = L.f_cell[2 * f + 1];
+        if (f1 < 0) continue;
+        const int32_t nb = (f0 == c) ? f1 : f0;
+        const int lq = (f0 == c) ? L.f_loc[2 * f + 1] : L.f_loc[2 * f];
+        const int kq = (int)(L.cfp[nb + 1] - L.cfp[nb]);
+        const int nlq = NFD * kq + NID;
+        const double *Bq = L.Bloc + boff(L, nb);
+        for (int q2 = 0; q2 < NQ; ++q2) {
+          double v = 0.0;
+          for (int bt = 0; bt < NFD; ++bt)
+            v += Bc[q * nl + i * NFD + bt] * Bq[q2 * nlq + lq * NFD + bt] / diagM[(int64_t)NFD * f + bt];
+          const int64_t p = s0 + ((int64_t)j << 5) + lane;
+          col[p] = (int32_t)(NQ * nb + q2);
+          val[p] = v;
+          ++j;
+        }
+      }
+    }
+    for (; j < width; ++j) {
+      const int64_t p = s0 + ((int64_t)j << 5) + lane;
+      col[p] = 0;
+      val[p] = 0.0;
+    }
+  }
+}
+
+static vem_status assemble_global_q(vem_handle *h) {
+  cudaStream_t s = h->stream;
+  Layout L{h->nfd, h->nid, h->nf, h->nc, h->n_u, h->cf_ptr, h->cf, h->f_cell, h->f_loc,
+           h->m_off, h->b_off, h->cls_of, h->Mloc, h->Bloc, h->fbc};
+  const int T = 256;
+  const int64_t n = h->n;
+  if (h->nfd != 6 || h->nid != 14 || h->nq != 4) return fail(h, VEM_ERR_UNSUPPORTED, "element layout");
+  if (!h->cnt_buf) VEM_TRY(dalloc_n(h, &h->cnt_buf, (size_t)n + 1));
+  int64_t *cnt = h->cnt_buf;
+  count_launch(); k_rowcount_q<6, 14, 4><<<grid_for(n, T), T, 0, s>>>(L, cnt);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_TRY(sell_layout(h, h->A, n, cnt));
+  if (!h->diagM) VEM_TRY(dalloc_n(h, &h->diagM, (size_t)h->n_u));
+  const int64_t npad = h->A.nslices * 32;
+  count_launch();
+  k_fill_q<6, 14, 4><<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, npad, h->A.col, h->A.val, h->diagM, h->nu);
+  VEM_CUDA(h, cudaGetLastError());
+  count_launch(); k_schur_count_q<6, 14, 4><<<grid_for(h->n_p, T), T, 0, s>>>(L, cnt);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_TRY(sell_layout(h, h->S, h->n_p, cnt));
+  if (!h->s_dinv) VEM_TRY(dalloc_n(h, &h->s_dinv, (size_t)h->n_p));
+  const int64_t spad = h->S.nslices * 32;
+  count_launch();
+  k_schur_fill_q<6, 14, 4><<<grid_for(spad, T), T, 0, s>>>(L, h->diagM, h->S.off, spad, h->S.col, h->S.val,
+                                                           h->s_dinv, h->d_err);
+  VEM_CUDA(h, cudaGetLastError());
+  if (h->s32_stored != h->S.stored) {
+    dfree(h, h->S_val32);
+    h->S_val32 = nullptr;
+    VEM_TRY(dalloc_n(h, &h->S_val32, (size_t)h->S.stored));
+    h->s32_stored = h->S.stored;
+  }
+  if (!h->s_dinv32) VEM_TRY(dalloc_n(h, &h->s_dinv32, (size_t)h->n_p));
+  count_launch(); k_f64_to_f32<<<grid_for(h->S.stored, T), T, 0, s>>>(h->S.stored, h->S.val, h->S_val32);
+  count_launch(); k_f64_to_f32<<<grid_for(h->n_p, T), T, 0, s>>>(h->n_p, h->s_dinv, h->s_dinv32);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_TRY(check_device_errors(h, "global assembly"));
+  VEM_TRY(sell_nnz(h, h->A));
+  VEM_TRY(sell_nnz(h, h->S));
+  return VEM_OK;
+}
+
 vem_status assemble_global(vem_handle *h) {
+  if (h->nq > 1) return assemble_global_q(h);
   cudaStream_t s = h->stream;
   Layout L{h->nfd, h->nid, h->nf, h->nc, h->n_u, h->cf_ptr, h->cf, h->f_cell, h->f_loc,
            h->m_off, h->b_off, h->cls_of, h->Mloc, h->Bloc, h->fbc};

@@ -595,6 +595,7 @@ vem_status flux_fixed(vem_handle *h, double *xfix) {
 }
 
 vem_status assemble_rhs_into(vem_handle *h, const double *f_qp, const double *gD_qp, double *g, double *F) {
+  if (h->nq > 1) return assemble_rhs_k2(h, f_qp, gD_qp, g, F);
   cudaStream_t s = h->stream;
   const int T = 128;
   count_launch(); k_rhs_faces<<<grid_for(h->nf, T), T, 0, s>>>(

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_k2(
     const double *__restrict__ f_norm, const double *__restrict__ f_t1, const double *__restrict__ f_diam,
     const double *__restrict__ c_vol, const double *__restrict__ c_cent, const double *__restrict__ c_diam,
     const int32_t *__restrict__ cls_rep, const int64_t *__restrict__ m_off, const int64_t *__restrict__ b_off,
-    double *Mloc, double *Bloc, int *err) {
+    double *Mloc, double *Bloc, double *hq_inv, int *err) {
   extern __shared__ double sm[];
   const int NUmax = kNfd * max_nf + kNid;
   const int NQmax = 7 * max_nv;
@@ -352,6 +352,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_k2(
     if (tid == 0) gj_inverse(Hp, 10);
     if (tid == 32) gj_inverse(Hq, 4);
     __syncthreads();
+    if (hq_inv && tid < 16) hq_inv[16 * k + tid] = vol * Hq[tid];   // load map F = |P| H_1^-1 int f m
     const int gcol0 = kNfd * nfc, ccol0 = gcol0 + 3;
     // divergence coefficients d = H_1^-1 r, r_0 = bnd_0, r_a = bnd_a - (|P|/h_P) e_{grad a}
     for (int e = tid; e < kNq * NU; e += blockDim.x) {
@@ -475,6 +476,12 @@ vem_status element_k2(vem_handle *h) {
   }
   const int mx = h->max_nf_cell, mv = h->max_nv_face;
   const size_t bytes = sizeof(double) * k2_smem_doubles(mx, mv);
+  if (h->hq_inv_n < h->ncls) {
+    dfree(h, h->hq_inv);
+    h->hq_inv = nullptr;
+    VEM_TRY(dalloc_n(h, &h->hq_inv, 16 * (size_t)h->ncls));
+    h->hq_inv_n = h->ncls;
+  }
   if (mv > 64 || bytes > 220 * 1024)
     return fail(h, VEM_ERR_UNSUPPORTED, "k = 2 element: cell with %d faces / face with %d vertices", mx, mv);
   VEM_CUDA(h, cudaFuncSetAttribute(k_elem_k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -486,7 +493,179 @@ vem_status element_k2(vem_handle *h) {
   k_elem_k2<<<(int)blocks, kThreads, bytes, h->stream>>>(
       h->ncls, mx, mv, h->cf_ptr, h->cf, h->cf_sigma, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm,
       h->f_t1, h->f_diam, h->c_vol, h->c_cent, h->c_diam, h->cls_rep, h->m_off, h->b_off, h->Mloc, h->Bloc,
-      h->d_err);
+      h->hq_inv, h->d_err);
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
+// ---- loads of the k = 2 element ----
+// Cell points: every fan tetrahedron (x_P, x_f, v_j, v_j+1) with the
+// collapsed (Duffy) product of 3-point Gauss-Legendre rules in each
+// direction (27 points, exact to degree 3: P1 moments of a quadratic f);
+// weights signed by the face orientation, so they sum to |P|.
+__global__ void k_cell_qp_count(int64_t nc, const int64_t *__restrict__ cfp, const int32_t *__restrict__ cf,
+                                const int64_t *__restrict__ fvp, int64_t *cnt) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v = 0;
+    for (int64_t p = cfp[c]; p < cfp[c + 1]; ++p) v += 27 * (fvp[cf[p] + 1] - fvp[cf[p]]);
+    cnt[c] = v;
+  }
+}
+
+__global__ void k_cell_qp(int64_t nc, const int64_t *__restrict__ off, const int64_t *__restrict__ cfp,
+                          const int32_t *__restrict__ cf, const int8_t *__restrict__ sig,
+                          const int64_t *__restrict__ fvp, const int32_t *__restrict__ fv,
+                          const double *__restrict__ xyz, const double *__restrict__ f_cent,
+                          const double *__restrict__ c_cent, double *qx, double *qw) {
+  const double g = 0.5 * 0.774596669241483377;   // sqrt(3/5) / 2
+  const double s3[3] = {0.5 - g, 0.5, 0.5 + g};
+  const double w3[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = off[c];
+    const double3 A = load3(c_cent, c);
+    for (int64_t p = cfp[c]; p < cfp[c + 1]; ++p) {
+      const int f = cf[p];
+      const double sg = (double)sig[p];
+      const double3 B = load3(f_cent, f);
+      const int64_t vb = fvp[f];
+      const int m = (int)(fvp[f + 1] - vb);
+      for (int j = 0; j < m; ++j) {
+        const double3 C = load3(xyz, fv[vb + j]), D = load3(xyz, fv[vb + (j + 1) % m]);
+        const double3 e1 = sub3(B, A), e2 = sub3(C, A), e3 = sub3(D, A);
+        const double det = dot3(e1, cross3(e2, e3));
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            for (int cc = 0; cc < 3; ++cc, ++o) {
+              const double xi = s3[a], eta = s3[b] * (1.0 - s3[a]), zeta = s3[cc] * (1.0 - s3[a]) * (1.0 - s3[b]);
+              const double3 x = add3(A, add3(add3(scale3(e1, xi), scale3(e2, eta)), scale3(e3, zeta)));
+              store3(qx, o, x);
+              qw[o] = sg * det * w3[a] * w3[b] * w3[cc] * (1.0 - s3[a]) * (1.0 - s3[a]) * (1.0 - s3[b]);
+            }
+      }
+    }
+  }
+}
+
+// F_P = |P| H_1^-1 (int_P f m_r)_r, r in P_1, from f at the cell points.
+__global__ void k_rhs_cells_k2(int64_t nc, const int64_t *__restrict__ off, const double *__restrict__ qx,
+                               const double *__restrict__ qw, const double *__restrict__ f_qp,
+                               const double *__restrict__ c_cent, const double *__restrict__ c_diam,
+                               const int32_t *__restrict__ cls_of, const double *__restrict__ hq_inv, double *F,
+                               int *err) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+    const double3 xP = load3(c_cent, c);
+    const double ih = 1.0 / c_diam[c];
+    double fm[4] = {0, 0, 0, 0};
+    for (int64_t o = off[c]; o < off[c + 1]; ++o) {
+      const double fv = f_qp ? f_qp[o] : 0.0;
+      if (!isfinite(fv)) atomicOr(err, DEVERR_NONFINITE);
+      const double3 y = scale3(sub3(load3(qx, o), xP), ih);
+      const double wf = qw[o] * fv;
+      fm[0] += wf;
+      fm[1] += wf * y.x;
+      fm[2] += wf * y.y;
+      fm[3] += wf * y.z;
+    }
+    const double *Hi = hq_inv + 16 * (int64_t)cls_of[c];
+    for (int q = 0; q < 4; ++q)
+      F[4 * c + q] = Hi[4 * q] * fm[0] + Hi[4 * q + 1] * fm[1] + Hi[4 * q + 2] * fm[2] + Hi[4 * q + 3] * fm[3];
+  }
+}
+
+// g_(f,beta) = -sigma |f| sum_g Ginv[g][beta] int_f g_D m^f_g on Dirichlet
+// faces (zero elsewhere) for the six face moments; the face Gram matrix and
+// the load by the Dunavant degree-4 fan rule of the boundary-face points
+// (exact for products of M_2(f) monomials).
+__global__ void k_rhs_faces_k2(int64_t nf, const int8_t *__restrict__ fbc, const int64_t *__restrict__ off,
+                               const int64_t *__restrict__ fvp, const int32_t *__restrict__ fv,
+                               const double *__restrict__ xyz, const double *__restrict__ f_area,
+                               const double *__restrict__ f_cent, const double *__restrict__ f_norm,
+                               const double *__restrict__ f_t1, const double *__restrict__ f_diam,
+                               const int32_t *__restrict__ f_cell, const int32_t *__restrict__ f_loc,
+                               const int64_t *__restrict__ cfp, const int8_t *__restrict__ sig,
+                               const double *__restrict__ gD, double *g, int *err) {
+  const int fb[6][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    for (int bt = 0; bt < 6; ++bt) g[6 * f + bt] = 0.0;
+    if (fbc[f] != 1 || gD == nullptr) continue;
+    const int64_t vb = fvp[f];
+    const int m = (int)(fvp[f + 1] - vb);
+    const double3 xf = load3(f_cent, f), n = load3(f_norm, f), t1 = load3(f_t1, f);
+    const double3 t2 = cross3(n, t1);
+    const double ihf = 1.0 / f_diam[f];
+    const double sg = (double)sig[cfp[f_cell[2 * f]] + f_loc[2 * f]];
+    double G[36], mom[6];
+    for (int e = 0; e < 36; ++e) G[e] = 0.0;
+    for (int e = 0; e < 6; ++e) mom[e] = 0.0;
+    int64_t o = off[f];
+    for (int i = 0; i < m; ++i) {
+      const double3 A = load3(xyz, fv[vb + i]);
+      const double3 B = load3(xyz, fv[vb + (i + 1) % m]);
+      const double areaT = 0.5 * dot3(cross3(sub3(A, xf), sub3(B, xf)), n);
+      for (int q = 0; q < 6; ++q, ++o) {
+        double l0, l1, l2, wq;
+        dunavant4_point(q, l0, l1, l2, wq);
+        const double3 x = add3(add3(scale3(xf, l0), scale3(A, l1)), scale3(B, l2));
+        const double w = wq * areaT;
+        const double3 dx = sub3(x, xf);
+        const double s = dot3(dx, t1) * ihf, t = dot3(dx, t2) * ihf;
+        double mf[6];
+        for (int bt = 0; bt < 6; ++bt) mf[bt] = ipow(s, fb[bt][0]) * ipow(t, fb[bt][1]);
+        const double gv = gD[o];
+        if (!isfinite(gv)) atomicOr(err, DEVERR_NONFINITE);
+        for (int a = 0; a < 6; ++a) {
+          mom[a] += w * gv * mf[a];
+          for (int b = 0; b < 6; ++b) G[6 * a + b] += w * mf[a] * mf[b];
+        }
+      }
+    }
+    gj_inverse(G, 6);
+    const double ar = f_area[f];
+    for (int bt = 0; bt < 6; ++bt) {
+      double v = 0.0;
+      for (int a = 0; a < 6; ++a) v += G[6 * a + bt] * mom[a];
+      g[6 * f + bt] = -sg * ar * v;
+    }
+  }
+}
+
+vem_status cell_points_k2(vem_handle *h) {
+  if (h->cqp_valid) return VEM_OK;
+  cudaStream_t s = h->stream;
+  if (!h->cqp_off) VEM_TRY(dalloc_n(h, &h->cqp_off, (size_t)h->nc + 1));
+  int64_t *cnt = nullptr;
+  VEM_TRY(dalloc_n(h, &cnt, (size_t)h->nc + 1));
+  count_launch();
+  k_cell_qp_count<<<grid_for(h->nc, 256), 256, 0, s>>>(h->nc, h->cf_ptr, h->cf, h->fv_ptr, cnt);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_TRY(scan_counts(h, h->nc, cnt, h->cqp_off, &h->n_cqp));
+  dfree(h, cnt);
+  dfree(h, h->cqp_x);
+  dfree(h, h->cqp_w);
+  h->cqp_x = h->cqp_w = nullptr;
+  VEM_TRY(dalloc_n(h, &h->cqp_x, 3 * (size_t)std::max<int64_t>(h->n_cqp, 1)));
+  VEM_TRY(dalloc_n(h, &h->cqp_w, (size_t)std::max<int64_t>(h->n_cqp, 1)));
+  count_launch();
+  k_cell_qp<<<grid_for(h->nc, 128), 128, 0, s>>>(h->nc, h->cqp_off, h->cf_ptr, h->cf, h->cf_sigma, h->fv_ptr, h->fv,
+                                                  h->xyz, h->f_cent, h->c_cent, h->cqp_x, h->cqp_w);
+  VEM_CUDA(h, cudaGetLastError());
+  h->cqp_valid = true;
+  return VEM_OK;
+}
+
+vem_status assemble_rhs_k2(vem_handle *h, const double *f_qp, const double *gD_qp, double *g, double *F) {
+  cudaStream_t s = h->stream;
+  VEM_TRY(cell_points_k2(h));
+  count_launch();
+  k_rhs_faces_k2<<<grid_for(h->nf, 128), 128, 0, s>>>(h->nf, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz,
+                                                        h->f_area, h->f_cent, h->f_norm, h->f_t1, h->f_diam,
+                                                        h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, gD_qp, g,
+                                                        h->d_err);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_CUDA(h, cudaMemsetAsync(g + 6 * h->nf, 0, sizeof(double) * 14 * h->nc, s));
+  count_launch();
+  k_rhs_cells_k2<<<grid_for(h->nc, 128), 128, 0, s>>>(h->nc, h->cqp_off, h->cqp_x, h->cqp_w, f_qp, h->c_cent,
+                                                        h->c_diam, h->cls_of, h->hq_inv, F, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   return VEM_OK;
 }

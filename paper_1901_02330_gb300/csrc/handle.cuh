@@ -36,6 +36,13 @@ struct vem_handle {
   int max_nf_cell = 0, max_nv_face = 0;
   int nq = 1;                                    // pressure DOFs per cell (4 for paper k = 2)
   bool local_ready = false;                      // element matrices of the current coefficients
+  // paper k = 2: |P| H_1^-1 per class (the load map) and the cell points
+  double *hq_inv = nullptr;
+  int64_t hq_inv_n = 0;
+  int64_t *cqp_off = nullptr;                    // [nc + 1] first point of each cell
+  double *cqp_x = nullptr, *cqp_w = nullptr;     // [n_cqp][3], [n_cqp]
+  int64_t n_cqp = 0;
+  bool cqp_valid = false;
 
   // ---- DOF layout (depends on the element) ----
   int nfd = 1, nid = 0;
@@ -217,6 +224,8 @@ vem_status adjoint_contract(vem_handle *h, const double *lam, const double *x, d
 vem_status flux_fixed(vem_handle *h, double *xfix);
 vem_status bface_info(vem_handle *h, double *nout, int8_t *flag);
 vem_status element_k2(vem_handle *h);       // paper k = 2 local matrices (element_k2.cu)
+vem_status cell_points_k2(vem_handle *h);   // paper k = 2 cell quadrature points (lazily)
+vem_status assemble_rhs_k2(vem_handle *h, const double *f_qp, const double *gD_qp, double *g, double *F);
 vem_status neumann_rhs(vem_handle *h, double *rhs);
 vem_status neumann_mean_free(vem_handle *h, int64_t n, const double *b, double *out);
 vem_status neumann_shift(vem_handle *h, double *xp);

@@ -635,6 +635,26 @@ static void launch_tri_flux(cudaStream_t s, int nfd, bool batch, int64_t nf, int
   }
 }
 
+// The same for any element, from the saddle matrix itself: B^T z_p of flux
+// row R is the part of row R of [M B^T; B 0] in the pressure columns.
+__global__ void k_tri_flux_rows(int64_t n_u, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
+                                const int32_t *__restrict__ col, const double *__restrict__ val,
+                                const double *__restrict__ v, const double *__restrict__ dM,
+                                const double *__restrict__ zp, double *z) {
+  for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < n_u;
+       R += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t base = off[R >> 5] + (R & 31);
+    const int L = len[R];
+    double t = v[R];
+    for (int k = 0; k < L; ++k) {
+      const int64_t p = base + 32 * (int64_t)k;
+      const int64_t cidx = col[p];
+      if (cidx >= n_u) t -= val[p] * zp[cidx - n_u];
+    }
+    z[R] = t / dM[R];
+  }
+}
+
 __global__ void k_negate(int64_t n, double *x) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -883,8 +903,14 @@ static vem_status precond(vem_handle *h, const VemOp &op, const double *v, doubl
   } else {
     VEM_TRY(pcg_solve(h, op, v + nu, z + nu, wk, &it));
     count_launch(); k_negate<<<grid_for(np, 256), 256, 0, s>>>(np, z + nu);
-    launch_tri_flux(s, h->nfd, op.nbatch > 1, h->nf, nu, op.n_u1, op.n_p1, v, op.diagM, h->f_cell, h->bt_face,
-                    z + nu, z);
+    if (h->nq > 1) {
+      count_launch();
+      k_tri_flux_rows<<<grid_for(nu, 256), 256, 0, s>>>(nu, op.A.off, op.A.len, op.A.col, op.A.val, v, op.diagM,
+                                                         z + nu, z);
+    } else {
+      launch_tri_flux(s, h->nfd, op.nbatch > 1, h->nf, nu, op.n_u1, op.n_p1, v, op.diagM, h->f_cell, h->bt_face,
+                      z + nu, z);
+    }
   }
   VEM_CUDA(h, cudaGetLastError());
   if (minres_partials)
@@ -1075,6 +1101,7 @@ vem_status krylov_solve(vem_handle *h, const VemOp &op, const double *rhs, doubl
   vem_status r;
   if (h->opt.precond == VEM_PREC_BLOCK_REG) {
     if (op.nbatch != 1) return fail(h, VEM_ERR_UNSUPPORTED, "Block-Reg is single-system");
+    if (h->nq > 1) return fail(h, VEM_ERR_UNSUPPORTED, "Block-Reg with the paper k = 2 element");
     VEM_TRY(ensure_reg(h));
   }
   if (h->opt.krylov == VEM_KRYLOV_MINRES) {
