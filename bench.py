@@ -56,7 +56,8 @@ def parse():
                     help="inner Schur solver: Jacobi-PCG or AMG-preconditioned CG")
     ap.add_argument("--workload", default="hex128-k1",
                     choices=["hex128-k1", "hex8-e0-minres", "cvt200k-e0-mixed", "hex64-e0-batch64",
-                             "cvt100k-adjoint", "cube32-k1-neumann", "cube32-k1-blockreg", "optimality-k1"],
+                             "cvt100k-adjoint", "cube32-k1-neumann", "cube32-k1-blockreg", "optimality-k1",
+                             "cube24-k2", "cvt27k-k2-element"],
                     help="hex128-k1 is the headline; the others are the remaining configurations")
     ap.add_argument("--profile", action="store_true",
                     help="one step only (for an ncu launch list); prints a short JSON line")
@@ -591,6 +592,57 @@ def run_workload(a):
                      paper_block_reg_iterations=84,
                      paper_note="paper: 84 GMRES iterations with PETSc GAMG (1 core), T_sol 53 s on 1 core of "
                                 "2x Xeon E5-2683 v4; context only")
+    elif w == "cube24-k2":
+        # The paper's k = 2 element on its 24^3 Cube mesh (first strong-scaling
+        # table, k = 2 row: 13,824 cells), with Dirichlet data of the paper's
+        # polynomial solution (prescribed-flux faces are not built for k = 2),
+        # K = 1, FGMRES(30) with the block upper-triangular preconditioner, S
+        # by AMG-PCG to 1e-8.
+        mesh = hex_mesh(24)
+        prob = fields.paper_polynomial_problem()
+        s = vs.Solver(mesh, stream=sid, device_io=1, element=vs.VEM_ELEMENT_K2, krylov=1, precond=1, restart=30,
+                      rtol=1e-8, inner=vs.VEM_INNER_AMG, inner_rtol=1e-8, inner_maxit=2000, maxit=3000)
+        s.set_data(prob.f, prob.gD)
+        n_u, n_p = s.sizes()
+        u = torch.empty(n_u, dtype=torch.float64, device="cuda")
+        p = torch.empty(n_p, dtype=torch.float64, device="cuda")
+
+        def step():
+            s.assemble()
+            return s.solve(u_out=u, p_out=p)[2]
+        ms, st = _timed(step, a.steps, a.warmup, stream)
+        s.close()
+        n = n_u + n_p
+        line = _line(a, "time-to-solution (rel.res 1e-8) and DOFs/s", n / (ms * 1e-3), "DOFs/s", ms, "f64",
+                     {"workload": w, "cells": mesh.n_cells, "dofs": n, "paper_dofs_with_multiplier": 508033,
+                      "element": "paper k=2 (6 face moments, 3 gradient + 11 cross moments, P1 pressure)",
+                      "bc": "Dirichlet (the paper's polynomial solution)", "krylov": "FGMRES(30)",
+                      "precond": "block upper-triangular, S by AMG-PCG 1e-8"},
+                     iterations=st["iterations"], inner_iterations=st["inner_iterations"], relres=st["relres"],
+                     t_assemble_ms=st["t_assemble_ms"], t_element_ms=st["t_element_ms"],
+                     t_solve_ms=st["t_solve_ms"], nnz_A=st["nnz_A"], nnz_S=st["nnz_S"],
+                     t_amg_setup_ms=st["t_amg_setup_ms"],
+                     paper_note="paper (flux data, mean-zero pressure, Block-Schur with MUMPS on S): 72 GMRES "
+                                "iterations, T_ass 271 s, T_sol 347 s on 1 core of 2x Xeon E5-2683 v4; context only")
+    elif w == "cvt27k-k2-element":
+        # The element kernel of the paper's k = 2 element on a 27,000-cell
+        # CVT mesh (every cell its own class): the assembly stage that the
+        # paper finds as costly as the solve on CVT meshes at k = 2.
+        mesh = voronoi_mesh(27000, seed=7, lloyd=10)
+        s = vs.Solver(mesh, stream=sid, element=vs.VEM_ELEMENT_K2)
+        times = []
+        for i in range(a.warmup + a.steps):
+            ms_e, ncls = s.assemble_local()
+            if i >= a.warmup:
+                times.append(ms_e)
+        s.close()
+        ms = float(np.median(times))
+        line = _line(a, "element matrices per second (paper k = 2)", mesh.n_cells / (ms * 1e-3), "cells/s", ms,
+                     "f64", {"workload": w, "cells": mesh.n_cells, "classes": ncls,
+                             "faces_per_cell": float(np.diff(mesh.cell_face_ptr).mean()),
+                             "element": "paper k=2"},
+                     note="the element kernel alone (vem_assemble_local), CUDA events; one block of 256 threads "
+                          "per cell; FP64 dense algebra in shared memory")
     elif w == "optimality-k1":
         # Optimality under refinement (the paper's optimality test, Tables
         # 4-6, at k = 1 here): flux data on the whole boundary, mean-zero
