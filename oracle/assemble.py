@@ -17,8 +17,12 @@ coupling moved to the right-hand side).  With no Dirichlet face the pressure
 lives in Q = {int q = 0} (Sec. 3): the mean-zero constraint enters through
 one Lagrange multiplier, the "+1" of the paper's DOF counts,
     [M  B^T 0] [u ]   [g]
-    [B  0   c] [p~] = [F],   c_P = int_P q_P = |P|  (P0 pressure).
+    [B  0   c] [p~] = [F],   c = (int_P psi_q)_(P,q),
     [0  c^T 0] [l ]   [0]
+with psi_q the pressure basis dual to the moment DOFs (1/|P|) int_P p m_q
+(eq. presMom): int_P psi_q = |P| for the constant moment, 0 for the others
+(m_q has zero mean about the barycentre).  The constants have the moments
+(1, 0, ..., 0) in every cell: that vector spans the kernel of B^T.
 """
 
 from __future__ import annotations
@@ -78,9 +82,26 @@ class System:
         b[self.fixed] = self.fixed_val
         return b
 
+    @property
+    def cvec(self) -> np.ndarray:
+        """c_(P,q) = int_P psi_q: |P| on each cell's constant moment, 0 else."""
+        nq = self.n_p // self.vol.size
+        c = np.zeros(self.n_p)
+        c[::nq] = self.vol
+        return c
+
+    @property
+    def null_vec(self) -> np.ndarray:
+        """The pressure moments of the constant 1 (kernel of B^T with the
+        flux prescribed on the whole boundary)."""
+        nq = self.n_p // self.vol.size
+        e = np.zeros(self.n_p)
+        e[::nq] = 1.0
+        return e
+
     def augmented(self):
         """The system with the mean-zero multiplier row and column."""
-        e = np.concatenate([np.zeros(self.n_u), self.vol])[:, None]
+        e = np.concatenate([np.zeros(self.n_u), self.cvec])[:, None]
         A = sp.bmat([[self.saddle(), sp.csr_matrix(e)], [sp.csr_matrix(e.T), None]], format="csr")
         return A, np.concatenate([self.rhs(), [0.0]])
 

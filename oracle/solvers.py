@@ -143,21 +143,26 @@ class BlockPreconditioner:
             self.B = (self.B @ sp.diags(np.where(np.isin(np.arange(sys.n_u), self.fixed), 0.0, 1.0))).tocsr()
             self.dM[self.fixed] = 1.0
         self.multiplier = sys.multiplier
+        if sys.multiplier:
+            self.e = sys.null_vec
         if inner == "exact":
             if sys.multiplier:
                 # singular S (constants): factorise [[S, c], [c^T, 0]]
-                c = sp.csr_matrix(sys.vol[:, None])
+                c = sp.csr_matrix(sys.cvec[:, None])
                 self.lu = spla.splu(sp.bmat([[self.S, c], [c.T, None]], format="csc"))
             else:
                 self.lu = spla.splu(self.S.tocsc())
         elif inner == "amg":
             from . import amg
             self.amg = amg
+            if sys.multiplier and sys.n_p != sys.vol.size:
+                raise NotImplementedError("AMG with the multiplier needs one pressure DOF per cell")
             self.H = amg.setup(self.S, pin_last=sys.multiplier)
 
     def solve_S(self, r):
         if self.multiplier:
-            r = r - r.mean()               # the consistent part (range of S)
+            # the consistent part (range of S = orthogonal complement of e)
+            r = r - (self.e @ r) / (self.e @ self.e) * self.e
         if self.inner == "exact":
             if self.multiplier:
                 return self.lu.solve(np.concatenate([r, [0.0]]))[:-1]
@@ -289,8 +294,10 @@ def solve_krylov(sys, method="minres", kind="diag", inner="exact", rtol=1e-12,
     A = sys.saddle()
     b = sys.rhs()
     if sys.multiplier:
-        lam = b[sys.n_u:].sum() / sys.vol.sum()
-        b[sys.n_u:] -= sys.vol * lam
+        # e^T (B u + c lambda) = e^T F with B^T e = 0
+        e, c = sys.null_vec, sys.cvec
+        lam = (e @ b[sys.n_u:]) / (e @ c)
+        b[sys.n_u:] -= c * lam
     P = BlockPreconditioner(sys, kind=kind, inner=inner, inner_rtol=inner_rtol, gamma=gamma)
     if method == "minres":
         if kind not in ("diag", "reg"):
@@ -303,5 +310,6 @@ def solve_krylov(sys, method="minres", kind="diag", inner="exact", rtol=1e-12,
     res.inner_iters = P.inner_iters
     u, pt = res.x[:sys.n_u], res.x[sys.n_u:]
     if sys.multiplier:
-        pt = pt - (sys.vol @ pt) / sys.vol.sum()
+        e, c = sys.null_vec, sys.cvec
+        pt = pt - (c @ pt) / (c @ e) * e
     return u, -pt, res

@@ -3,6 +3,7 @@ the paper's model problem (Sec. 3: u.n = u_N on the boundary, pressure in
 Q = {int q = 0}, one Lagrange multiplier)."""
 
 import numpy as np
+import scipy.sparse as sp
 import pytest
 
 from oracle import E0, assemble, paper_element, solvers
@@ -111,6 +112,73 @@ def test_neumann_conservation_and_krylov(spec):
     np.testing.assert_allclose(sys.B @ (u * keep), r, atol=1e-10 * np.abs(r).max())
     for method, kind, inner in [("fgmres", "diag", "exact"), ("fgmres", "tri", "amg"), ("minres", "diag", "exact")]:
         uk, pk, res = solvers.solve_krylov(sys, method, kind, inner, rtol=1e-11, inner_rtol=1e-13)
+        assert res.converged
+        np.testing.assert_allclose(uk, u, atol=1e-8 * np.abs(u).max())
+        np.testing.assert_allclose(pk, p, atol=1e-8 * np.abs(p).max())
+
+
+def _cubic_problem(K):
+    """p in P_3, constant K: u = -K grad p in [P_2]^3, f = div u in P_1."""
+    def p(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        return X ** 3 - 2 * X * Y * Y + 0.5 * Z ** 3 + X * Y * Z + Y * Y - 0.4 * Z
+
+    def u(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        return -K * np.stack([3 * X * X - 2 * Y * Y + Y * Z, -4 * X * Y + X * Z + 2 * Y,
+                              1.5 * Z * Z + X * Y - 0.4], 1)
+
+    def f(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        return -K * (6 * X - 4 * X + 2 + 3 * Z)
+
+    return p, u, f
+
+
+@pytest.mark.parametrize("mesh", ["hex", "prism", "octa", "voronoi"])
+def test_neumann_patch_k2(mesh):
+    """The k = 2 element with flux data on the whole boundary, constant K and
+    p in P_3: u_h is the interpolant of the exact flux, the pressure DOFs
+    are the P_1 moments (1/|P|) int_P p m_q shifted along the constants to
+    int p_h = 0, and the multiplier vanishes (compatible data)."""
+    from oracle.monomials import eval_mono3, mono3
+    spec = paper_element(2)
+    m = MESHES[mesh](2)
+    K = 1.7
+    p_ex, u_ex, f_ex = _cubic_problem(K)
+    sys = assemble(m, spec, np.full(m.n_cells, 1.0 / K), f=f_ex, flux=u_ex)
+    assert sys.multiplier and sys.n_p == 4 * m.n_cells
+    u, p, lam = solvers.solve_direct(sys, return_multiplier=True)
+    cells = mesh_cells(m)
+    uI = _interp(sys, spec, cells, m, u_ex)
+    pI = np.concatenate([(cell.qw * p_ex(cell.qp)) @ eval_mono3(mono3(1), cell.qp, cell.centroid, cell.diameter)
+                         / cell.volume for cell in cells])
+    e, c = sys.null_vec, sys.cvec
+    pI -= (c @ pI) / (c @ e) * e
+    np.testing.assert_allclose(u, uI, atol=1e-9 * max(1, np.abs(uI).max()))
+    np.testing.assert_allclose(p, pI, atol=1e-9 * max(1, np.abs(pI).max()))
+    assert abs(c @ p) <= 1e-12 * np.abs(p).max()
+    assert abs(lam) <= 1e-9
+
+
+def test_neumann_k2_multiplier_and_krylov():
+    """k = 2, the paper's polynomial solution with flux data: local
+    conservation up to the multiplier (B u_h = F - c lambda), the kernel of
+    B^T is the constant moments, and Block-Schur Krylov solves with the exact
+    bordered Schur block reach the direct solution."""
+    spec = paper_element(2)
+    m = hex_mesh(2, bc=2)
+    prob = fields.paper_polynomial_problem()
+    sys = assemble(m, spec, 1.0 / fields.K_lognormal(m.n_cells, seed=4, sigma=0.5), f=prob.f, flux=prob.u)
+    u, p, lam = solvers.solve_direct(sys, return_multiplier=True)
+    keep = np.ones(sys.n_u)
+    keep[sys.fixed] = 0.0
+    Bk = sys.B @ sp.diags(keep)
+    np.testing.assert_allclose(Bk.T @ sys.null_vec, 0.0, atol=1e-12 * abs(sys.B).max())
+    r = sys.rhs()[sys.n_u:] - sys.cvec * lam
+    np.testing.assert_allclose(Bk @ u, r, atol=1e-10 * np.abs(r).max())
+    for method, kind in [("fgmres", "diag"), ("fgmres", "tri"), ("minres", "diag")]:
+        uk, pk, res = solvers.solve_krylov(sys, method, kind, "exact", rtol=1e-11)
         assert res.converged
         np.testing.assert_allclose(uk, u, atol=1e-8 * np.abs(u).max())
         np.testing.assert_allclose(pk, p, atol=1e-8 * np.abs(p).max())
