@@ -96,10 +96,12 @@ typedef struct {
  * k = 1: 3 face moments, 3 cross moments, P0 pressure), K2 (the paper's
  * k = 2, Sec. 4.1-4.3: 6 face moments against M_2(f), 3 gradient and 11
  * cross moments, P1 pressure moments: 4 pressure unknowns per cell, cell c's
- * at n_u + 4c .. n_u + 4c + 3).  K2 solves Dirichlet problems with the
- * block-diagonal and block-triangular preconditioners (Jacobi-PCG or AMG for
- * S); prescribed-flux faces, Block-Reg, vem_solve_batched and vem_adjoint
- * give VEM_ERR_UNSUPPORTED with it.  Its cell quadrature points
+ * at n_u + 4c .. n_u + 4c + 3).  K2 solves with Dirichlet and prescribed-
+ * flux faces (the mean-zero pressure then constrains the constant moments,
+ * c = |P| on them) and the block-diagonal and block-triangular
+ * preconditioners (Jacobi-PCG or AMG for S; the AMG not with the
+ * multiplier); Block-Reg, vem_solve_batched and vem_adjoint give
+ * VEM_ERR_UNSUPPORTED with it.  Its cell quadrature points
  * (VEM_QP_CELL) are those of a degree-3 rule on the fan tetrahedra of every
  * cell (27 per tetrahedron), built on first use. */
 enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1, VEM_ELEMENT_K2 = 2 };

@@ -407,8 +407,6 @@ static vem_status ensure_rhs(vem_handle *h) {
 }
 
 static vem_status assemble_impl(vem_handle *h) {
-  if (h->nq > 1 && h->n_flux_faces > 0)
-    return fail(h, VEM_ERR_UNSUPPORTED, "paper k = 2 with prescribed-flux faces");
   amg_invalidate(h->amg);
   amg_invalidate(h->amg_reg);
   h->areg_valid = false;

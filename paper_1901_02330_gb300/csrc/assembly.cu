@@ -745,7 +745,9 @@ __global__ void k_schur_fill_q(Layout L, const double *__restrict__ diagM, const
       for (int q2 = 0; q2 < NQ; ++q2) {
         double v = 0.0;
         for (int i = 0; i < k; ++i) {
-          const int64_t gc = (int64_t)NFD * L.cf[b0 + i];
+          const int fi = L.cf[b0 + i];
+          if (L.fbc[fi] == 2) continue;   // eliminated flux DOFs: no column of B
+          const int64_t gc = (int64_t)NFD * fi;
           for (int bt = 0; bt < NFD; ++bt)
             v += Bc[q * nl + i * NFD + bt] * Bc[q2 * nl + i * NFD + bt] / diagM[gc + bt];
         }
@@ -806,6 +808,19 @@ static vem_status assemble_global_q(vem_handle *h) {
   count_launch();
   k_fill_q<6, 14, 4><<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, npad, h->A.col, h->A.val, h->diagM, h->nu);
   VEM_CUDA(h, cudaGetLastError());
+  if (h->n_flux_faces > 0) {
+    // prescribed flux DOFs: values, A x_fix moved to the right-hand side,
+    // symmetric elimination (as for one pressure DOF per cell)
+    if (!h->xfix) VEM_TRY(dalloc_n(h, &h->xfix, (size_t)n));
+    if (!h->rhs_corr) VEM_TRY(dalloc_n(h, &h->rhs_corr, (size_t)n));
+    VEM_CUDA(h, cudaMemsetAsync(h->xfix, 0, sizeof(double) * n, s));
+    VEM_TRY(flux_fixed(h, h->xfix));
+    spmv(s, h->A, h->xfix, h->rhs_corr);
+    count_launch();
+    k_eliminate<<<grid_for(n, T), T, 0, s>>>(n, h->A.off, h->A.len, h->A.col, h->A.val, h->nfd, h->nf, h->fbc,
+                                            h->diagM);
+    VEM_CUDA(h, cudaGetLastError());
+  }
   count_launch(); k_schur_count_q<6, 14, 4><<<grid_for(h->n_p, T), T, 0, s>>>(L, cnt);
   VEM_CUDA(h, cudaGetLastError());
   VEM_TRY(sell_layout(h, h->S, h->n_p, cnt));

@@ -562,7 +562,7 @@ __global__ void k_flux_fixed(int64_t nf, int nfd, const int8_t *__restrict__ fbc
     const double3 t2 = cross3(n, t1);
     const double ihf = 1.0 / f_diam[f];
     const double sg = (double)sig[cfp[f_cell[2 * f]] + f_loc[2 * f]];
-    double mom[3] = {0, 0, 0};
+    double mom[6] = {0, 0, 0, 0, 0, 0};
     int64_t o = off[f];
     for (int i = 0; i < m; ++i) {
       const double3 A = load3(xyz, fv[vb + i]);
@@ -574,7 +574,9 @@ __global__ void k_flux_fixed(int64_t nf, int nfd, const int8_t *__restrict__ fbc
         const double3 x = add3(add3(scale3(xf, l0), scale3(A, l1)), scale3(B, l2));
         const double w = wq * areaT;
         const double3 dx = sub3(x, xf);
-        const double mf[3] = {1.0, dot3(dx, t1) * ihf, dot3(dx, t2) * ihf};
+        const double fs = dot3(dx, t1) * ihf, ft = dot3(dx, t2) * ihf;
+        // face monomials of M_2(f): 1, s, t, s^2, s t, t^2 (the first nfd)
+        const double mf[6] = {1.0, fs, ft, fs * fs, fs * ft, ft * ft};
         const double un = uN[o];
         if (!isfinite(un)) atomicOr(err, DEVERR_NONFINITE);
         for (int bta = 0; bta < nfd; ++bta) mom[bta] += w * un * mf[bta];

@@ -539,6 +539,8 @@ static vem_status pcg_solve(vem_handle *h, const VemOp &op, const double *b, dou
   if (h->opt.inner == VEM_INNER_AMG) {
     // FP64 CG; with the mixed option the V-cycle runs in FP32
     const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
+    if (h->multiplier && h->nq > 1)
+      return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver with the multiplier needs one pressure DOF per cell");
     if (!amg_valid(h->amg) || amg_is_fp32(h->amg) != fp32)
       VEM_TRY(amg_setup(h, h->amg, op.S, op.S_val32, fp32, h->multiplier, kSmoothJacobi));
     return pcg_solve_t<double>(h, op, op.S.val, op.s_dinv, b, x, wk, iters);

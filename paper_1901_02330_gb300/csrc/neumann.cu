@@ -26,27 +26,32 @@ __global__ void k_apply_fixed(int64_t n, int nfd, int64_t nf, const int8_t *__re
   }
 }
 
-// Block partials of sum a_i, or of sum w_i a_i when w is given.
-__global__ void k_sums(int64_t n, const double *__restrict__ a, const double *__restrict__ w, double *pa) {
+// Block partials of sum a_(i stride), or of sum w_i a_(i stride) when w is
+// given (stride: pressure DOFs per cell; entry i stride is cell i's constant
+// moment).
+__global__ void k_sums(int64_t n, const double *__restrict__ a, const double *__restrict__ w, double *pa,
+                       int stride = 1) {
   double sa = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    sa += w ? w[i] * a[i] : a[i];
+    sa += w ? w[i] * a[i * stride] : a[i * stride];
   block_partial(sa, pa);
 }
 
-// y = x - s c with s = (sum of the pa partials) / (sum of the pw partials, or
-// n when pw is NULL); c = NULL stands for the vector of ones.  Every block
-// recomputes s from the partials in the same order.  Optionally stores s.
+// y_(i stride) = x_(i stride) - s c_i with s = (sum of the pa partials) /
+// (sum of the pw partials, or n when pw is NULL); c = NULL stands for the
+// vector of ones.  Every block recomputes s from the partials in the same
+// order.  Optionally stores s.  Entries off the stride are not touched.
 __global__ void k_sub_scaled(int64_t n, const double *__restrict__ pa, const double *__restrict__ pw, int nb,
-                             const double *__restrict__ c, const double *x, double *y, double *s_out) {
+                             const double *__restrict__ c, const double *x, double *y, double *s_out,
+                             int stride = 1) {
   const double sa = sum_partials(pa, nb);
   const double sw = pw ? sum_partials(pw, nb) : (double)n;
   const double s = sa / sw;
   if (s_out && blockIdx.x == 0 && threadIdx.x == 0) *s_out = s;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = x[i] - s * (c ? c[i] : 1.0);
+    y[i * stride] = x[i * stride] - s * (c ? c[i] : 1.0);
 }
 
 static vem_status ensure_npart(vem_handle *h) {
@@ -62,30 +67,38 @@ vem_status neumann_rhs(vem_handle *h, double *rhs) {
   k_apply_fixed<<<grid_for(n, 256), 256, 0, s>>>(n, h->nfd, h->nf, h->fbc, h->rhs_corr, h->xfix, rhs);
   VEM_CUDA(h, cudaGetLastError());
   if (!h->multiplier) return VEM_OK;
-  // lambda = sum F / sum |P|;  F <- F - |P| lambda
+  // lambda = e^T F / e^T c (e: the constant moments, c: |P| on them);
+  // F <- F - c lambda
   VEM_TRY(ensure_npart(h));
   double *F = rhs + h->n_u;
-  const int nb = nblocks_vec(h->n_p);
+  const int nb = nblocks_vec(h->nc);
+  const int q = h->nq;
   double *pa = h->npart, *pw = h->npart + kMaxBlocks, *lam = h->npart + 2 * kMaxBlocks;
   count_launch();
-  k_sums<<<nb, kRedThreads, 0, s>>>(h->n_p, F, nullptr, pa);
+  k_sums<<<nb, kRedThreads, 0, s>>>(h->nc, F, nullptr, pa, q);
   count_launch();
-  k_sums<<<nb, kRedThreads, 0, s>>>(h->n_p, h->c_vol, nullptr, pw);
+  k_sums<<<nb, kRedThreads, 0, s>>>(h->nc, h->c_vol, nullptr, pw);
   count_launch();
-  k_sub_scaled<<<nb, kRedThreads, 0, s>>>(h->n_p, pa, pw, nb, h->c_vol, F, F, lam);
+  k_sub_scaled<<<nb, kRedThreads, 0, s>>>(h->nc, pa, pw, nb, h->c_vol, F, F, lam, q);
   VEM_CUDA(h, cudaGetLastError());
   VEM_CUDA(h, cudaMemcpyAsync(&h->lambda, lam, sizeof(double), cudaMemcpyDeviceToHost, s));
   VEM_CUDA(h, cudaStreamSynchronize(s));
   return VEM_OK;
 }
 
+// out = b minus its component along the constant moments (the consistent
+// part: the range of S is orthogonal to them).
 vem_status neumann_mean_free(vem_handle *h, int64_t n, const double *b, double *out) {
   VEM_TRY(ensure_npart(h));
-  const int nb = nblocks_vec(n);
+  const int q = h->nq;
+  const int64_t nc = n / q;
+  const int nb = nblocks_vec(nc);
+  if (q > 1 && out != b) VEM_CUDA(h, cudaMemcpyAsync(out, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
   count_launch();
-  k_sums<<<nb, kRedThreads, 0, h->stream>>>(n, b, nullptr, h->npart);
+  k_sums<<<nb, kRedThreads, 0, h->stream>>>(nc, b, nullptr, h->npart, q);
   count_launch();
-  k_sub_scaled<<<nb, kRedThreads, 0, h->stream>>>(n, h->npart, nullptr, nb, nullptr, b, out, nullptr);
+  k_sub_scaled<<<nb, kRedThreads, 0, h->stream>>>(nc, h->npart, nullptr, nb, nullptr, q > 1 ? out : b, out, nullptr,
+                                                  q);
   VEM_CUDA(h, cudaGetLastError());
   return VEM_OK;
 }
@@ -107,15 +120,17 @@ vem_status device_sum(vem_handle *h, int64_t n, const double *a, double *out) {
 
 vem_status neumann_shift(vem_handle *h, double *xp) {
   if (!h->multiplier) return VEM_OK;
+  // shift along the constant moments to c^T p = 0
   VEM_TRY(ensure_npart(h));
-  const int nb = nblocks_vec(h->n_p);
+  const int nb = nblocks_vec(h->nc);
+  const int q = h->nq;
   count_launch();
-  k_sums<<<nb, kRedThreads, 0, h->stream>>>(h->n_p, xp, h->c_vol, h->npart);
+  k_sums<<<nb, kRedThreads, 0, h->stream>>>(h->nc, xp, h->c_vol, h->npart, q);
   count_launch();
-  k_sums<<<nb, kRedThreads, 0, h->stream>>>(h->n_p, h->c_vol, nullptr, h->npart + kMaxBlocks);
+  k_sums<<<nb, kRedThreads, 0, h->stream>>>(h->nc, h->c_vol, nullptr, h->npart + kMaxBlocks);
   count_launch();
-  k_sub_scaled<<<nb, kRedThreads, 0, h->stream>>>(h->n_p, h->npart, h->npart + kMaxBlocks, nb, nullptr, xp, xp,
-                                                  nullptr);
+  k_sub_scaled<<<nb, kRedThreads, 0, h->stream>>>(h->nc, h->npart, h->npart + kMaxBlocks, nb, nullptr, xp, xp,
+                                                  nullptr, q);
   VEM_CUDA(h, cudaGetLastError());
   return VEM_OK;
 }

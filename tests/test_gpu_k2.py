@@ -157,6 +157,82 @@ def test_k2_solve_matches_direct(vs, mname, krylov, prec, inner):
     assert np.linalg.norm(p - pd) <= 1e-9 * np.linalg.norm(pd)
 
 
+def _cubic(K=1.0):
+    """p in P_3, u = -K grad p in [P_2]^3, f = div u in P_1: every load and
+    flux datum is integrated exactly by both sides' rules."""
+    def p(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        return X ** 3 - 2 * X * Y * Y + 0.5 * Z ** 3 + X * Y * Z + Y * Y - 0.4 * Z
+
+    def u(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        return -K * np.stack([3 * X * X - 2 * Y * Y + Y * Z, -4 * X * Y + X * Z + 2 * Y,
+                              1.5 * Z * Z + X * Y - 0.4], 1)
+
+    def f(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        return -K * (2 * X + 2 + 3 * Z)
+
+    return p, u, f
+
+
+def _flux_mesh(name):
+    if name == "cvt30":
+        m = voronoi_mesh(30, seed=4, lloyd=5)
+        m.face_bc = np.where(m.face_bc != 0, 2, 0).astype(np.int8)
+        return m
+    return {"hex3": lambda: hex_mesh(3, bc=2), "prism2": lambda: prism_mesh(2, bc=2),
+            "octa2": lambda: octa_mesh(2, bc=2)}[name]()
+
+
+@pytest.mark.parametrize("mname", ["hex3", "prism2", "octa2", "cvt30"])
+def test_k2_flux_system_and_solves(vs, mname):
+    """k = 2 with flux data on the whole boundary and the mean-zero pressure:
+    the eliminated saddle matrix, the right-hand side with the multiplier's
+    projection and S against the oracle; MINRES and FGMRES solves against
+    the oracle's direct solve of the bordered system, the multiplier value
+    and int p_h = 0."""
+    from oracle import assemble, solvers
+    m = _flux_mesh(mname)
+    K = fields.K_lognormal(m.n_cells, seed=6, sigma=0.5)
+    _, u_ex, f_ex = _cubic()
+    sys_ = assemble(m, paper_element(2), 1.0 / K, f=f_ex, flux=u_ex)
+    assert sys_.multiplier
+    tol = SYS_TOL[mname]
+    s = vs.Solver(m, element=vs.VEM_ELEMENT_K2)
+    try:
+        s.set_coefficient(K)
+        s.set_data(f_ex, None, flux=u_ex)
+        A, rhs = s.system()
+        S, _ = s.schur()
+    finally:
+        s.close()
+    Ar = sys_.saddle()
+    assert abs(A - Ar).max() <= tol * abs(Ar).max()
+    ref = sys_.rhs()
+    e, c = sys_.null_vec, sys_.cvec
+    lam = (e @ ref[sys_.n_u:]) / (e @ c)
+    ref[sys_.n_u:] -= c * lam
+    np.testing.assert_allclose(rhs, ref, rtol=0, atol=tol * np.abs(ref).max())
+    Sr = solvers.schur(sys_)
+    assert abs(S - Sr).max() <= tol * abs(Sr).max()
+    ud, pd, lamd = solvers.solve_direct(sys_, return_multiplier=True)
+    for krylov, prec in [(0, 0), (1, 1)]:
+        s = vs.Solver(m, element=vs.VEM_ELEMENT_K2, krylov=krylov, precond=prec, rtol=1e-12, inner_rtol=1e-13,
+                      maxit=4000)
+        try:
+            s.set_coefficient(K)
+            s.set_data(f_ex, None, flux=u_ex)
+            u, p, st = s.solve()
+        finally:
+            s.close()
+        assert st["relres"] <= 1e-12
+        assert np.linalg.norm(u - ud) <= 1e-9 * np.linalg.norm(ud)
+        assert np.linalg.norm(p - pd) <= 1e-9 * np.linalg.norm(pd)
+        assert abs(c @ p) <= 1e-11 * np.abs(p).max() * c.sum()
+        assert st["multiplier"] == pytest.approx(lamd, rel=1e-9, abs=1e-12)
+
+
 def test_k2_unsupported_combinations(vs):
     mesh = hex_mesh(2)
     s = vs.Solver(mesh, element=vs.VEM_ELEMENT_K2, krylov=1, precond=vs.VEM_PREC_BLOCK_REG)
@@ -170,9 +246,12 @@ def test_k2_unsupported_combinations(vs):
         assert e.value.code == 8
     finally:
         s.close()
+    # the AMG inner solver with the multiplier pins one DOF per cell
     m = hex_mesh(2, bc=2)
-    s = vs.Solver(m, element=vs.VEM_ELEMENT_K2)
+    _, u_ex, f_ex = _cubic()
+    s = vs.Solver(m, element=vs.VEM_ELEMENT_K2, krylov=1, precond=1, inner=vs.VEM_INNER_AMG)
     try:
+        s.set_data(f_ex, None, flux=u_ex)
         with pytest.raises(vs.VemError) as e:
             s.solve()
         assert e.value.code == 8
