@@ -593,18 +593,19 @@ def run_workload(a):
                      paper_note="paper: 84 GMRES iterations with PETSc GAMG (1 core), T_sol 53 s on 1 core of "
                                 "2x Xeon E5-2683 v4; context only")
     elif w == "cube24-k2":
-        # The paper's k = 2 element on its 24^3 Cube mesh (first strong-scaling
-        # table, k = 2 row: 13,824 cells), with Dirichlet data of the paper's
-        # polynomial solution (prescribed-flux faces are not built for k = 2),
-        # K = 1, FGMRES(30) with the block upper-triangular preconditioner, S
-        # by Jacobi-PCG to 1e-2: the outer count (~260) does not depend on
-        # the inner tolerance (diag(M) limits it), and the scalar AMG gains
-        # nothing on the 4 x 4 blocks of this S.
-        mesh = hex_mesh(24)
+        # The paper's k = 2 element on its 24^3 Cube mesh in the paper's own
+        # setting (first strong-scaling table, k = 2 row: 13,824 cells,
+        # 508,033 DOFs with the multiplier): flux data of its polynomial
+        # solution on the whole boundary, mean-zero pressure, K = 1,
+        # FGMRES(30) with the block upper-triangular preconditioner, S by
+        # Jacobi-PCG to 1e-2 (the outer count hardly depends on the inner
+        # tolerance: diag(M) limits it; the scalar AMG gains nothing on the
+        # 4 x 4 blocks of this S).
+        mesh = hex_mesh(24, bc=2)
         prob = fields.paper_polynomial_problem()
         s = vs.Solver(mesh, stream=sid, device_io=1, element=vs.VEM_ELEMENT_K2, krylov=1, precond=1, restart=30,
                       rtol=1e-8, inner=vs.VEM_INNER_PCG, inner_rtol=1e-2, inner_maxit=2000, maxit=3000)
-        s.set_data(prob.f, prob.gD)
+        s.set_data(prob.f, prob.gD, flux=prob.u)
         n_u, n_p = s.sizes()
         u = torch.empty(n_u, dtype=torch.float64, device="cuda")
         p = torch.empty(n_p, dtype=torch.float64, device="cuda")
@@ -616,16 +617,17 @@ def run_workload(a):
         s.close()
         n = n_u + n_p
         line = _line(a, "time-to-solution (rel.res 1e-8) and DOFs/s", n / (ms * 1e-3), "DOFs/s", ms, "f64",
-                     {"workload": w, "cells": mesh.n_cells, "dofs": n, "paper_dofs_with_multiplier": 508033,
+                     {"workload": w, "cells": mesh.n_cells, "dofs_with_multiplier": n + 1, "paper_dofs": 508033,
                       "element": "paper k=2 (6 face moments, 3 gradient + 11 cross moments, P1 pressure)",
-                      "bc": "Dirichlet (the paper's polynomial solution)", "krylov": "FGMRES(30)",
+                      "bc": "flux on the whole boundary, mean-zero p", "krylov": "FGMRES(30)",
                       "precond": "block upper-triangular, S by Jacobi-PCG 1e-2"},
                      iterations=st["iterations"], inner_iterations=st["inner_iterations"], relres=st["relres"],
                      t_assemble_ms=st["t_assemble_ms"], t_element_ms=st["t_element_ms"],
                      t_solve_ms=st["t_solve_ms"], nnz_A=st["nnz_A"], nnz_S=st["nnz_S"],
                      t_amg_setup_ms=st["t_amg_setup_ms"],
-                     paper_note="paper (flux data, mean-zero pressure, Block-Schur with MUMPS on S): 72 GMRES "
-                                "iterations, T_ass 271 s, T_sol 347 s on 1 core of 2x Xeon E5-2683 v4; context only")
+                     multiplier=st["multiplier"],
+                     paper_note="paper (Block-Schur, block-diagonal with MUMPS on S): 72 GMRES iterations, T_ass "
+                                "271 s, T_sol 347 s on 1 core of 2x Xeon E5-2683 v4; context only")
     elif w == "cvt27k-k2-element":
         # The element kernel of the paper's k = 2 element on a 27,000-cell
         # CVT mesh (every cell its own class): the assembly stage that the
@@ -647,10 +649,10 @@ def run_workload(a):
                           "per cell; FP64 dense algebra in shared memory")
     elif w == "optimality-k2":
         # Iterations under refinement at the paper's k = 2 (its optimality
-        # tables are at k = 2) on Cube, Octa and CVT meshes, with Dirichlet
-        # data of the paper's polynomial solution (prescribed-flux faces are
-        # not built for k = 2), Block-Schur (block-diagonal, S by Jacobi-PCG
-        # to 1e-8), FGMRES(30) to 1e-8.
+        # tables, Tables 4-6) on Cube, Octa and CVT meshes in the paper's
+        # setting: flux data of its polynomial solution on the whole
+        # boundary, mean-zero pressure, Block-Schur (block-diagonal, S by
+        # Jacobi-PCG to 1e-8), FGMRES(30) to 1e-8.
         prob = fields.paper_polynomial_problem()
         rows = []
         total_ms = 0.0
@@ -659,15 +661,16 @@ def run_workload(a):
                  + [("cvt", n) for n in (125, 1000, 4000)])
         for kind, n in cases:
             if kind == "cube":
-                mesh = hex_mesh(n)
+                mesh = hex_mesh(n, bc=2)
             elif kind == "octa":
-                mesh = octa_mesh(n)
+                mesh = octa_mesh(n, bc=2)
             else:
                 mesh = voronoi_mesh(n, seed=7, lloyd=10)
+                mesh.face_bc = np.where(mesh.face_bc != 0, 2, 0).astype(np.int8)
             s = vs.Solver(mesh, stream=sid, device_io=1, element=vs.VEM_ELEMENT_K2, krylov=1, precond=0,
                           restart=30, rtol=1e-8, inner=vs.VEM_INNER_PCG, inner_rtol=1e-8, inner_maxit=4000,
                           maxit=5000)
-            s.set_data(prob.f, prob.gD)
+            s.set_data(prob.f, prob.gD, flux=prob.u)
             n_u, n_p = s.sizes()
             u = torch.empty(n_u, dtype=torch.float64, device="cuda")
             p = torch.empty(n_p, dtype=torch.float64, device="cuda")
@@ -678,19 +681,19 @@ def run_workload(a):
             ms, st = _timed(step, max(1, a.steps), 1, stream)
             s.close()
             total_ms += ms
-            n_all += n_u + n_p
-            rows.append({"mesh": f"{kind}{n}", "cells": mesh.n_cells, "dofs": n_u + n_p,
+            n_all += n_u + n_p + 1
+            rows.append({"mesh": f"{kind}{n}", "cells": mesh.n_cells, "dofs_with_multiplier": n_u + n_p + 1,
                          "outer_iterations": st["iterations"], "inner_iterations": st["inner_iterations"],
                          "relres": st["relres"], "ms": ms})
         line = _line(a, "GMRES iterations under refinement at k = 2 (Block-Schur) and DOFs/s",
                      n_all / (total_ms * 1e-3), "DOFs/s", total_ms, "f64",
-                     {"workload": w, "element": "paper k=2", "bc": "Dirichlet (the paper's polynomial solution)",
+                     {"workload": w, "element": "paper k=2", "bc": "flux on the whole boundary, mean-zero p",
                       "precond": "Block-Schur (block-diagonal, S by Jacobi-PCG 1e-8)", "krylov": "FGMRES(30)"},
                      runs=rows,
                      paper_block_schur_iterations={"cube": [113, 78, 76, 72, 69], "octa": [367, 498, 598, 559, 631],
                                                    "cvt": [727, 535, 652, 736, 607]},
-                     paper_note="the paper's Tables 4-6 (flux data, mean-zero pressure, MUMPS on S, 8 processes); "
-                                "context only")
+                     paper_note="the paper's Tables 4-6 (same setting with MUMPS on S, 8 processes, PETSc GMRES "
+                                "tolerance not stated); context only")
     elif w == "optimality-k1":
         # Optimality under refinement (the paper's optimality test, Tables
         # 4-6, at k = 1 here): flux data on the whole boundary, mean-zero
