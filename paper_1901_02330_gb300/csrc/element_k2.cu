@@ -179,7 +179,7 @@ __device__ void gj_inverse(double *A, int n) {
 size_t k2_smem_doubles(int max_nf, int max_nv) {
   const size_t nu = (size_t)kNfd * max_nf + kNid;
   const size_t nq = 7 * (size_t)max_nv;
-  return 133 * nu + 6 * nq + 120 + 35 + 36 + 36 + kMom + 100 + 100 + 16 + 16 + 4 * kGr + 900 + 8;
+  return 133 * nu + 6 * nq + 120 + 35 + 36 + kMom + 100 + 16 + 4 * kGr + 900 + 8;
 }
 
 __global__ void __launch_bounds__(kThreads) k_elem_k2(
@@ -204,13 +204,10 @@ __global__ void __launch_bounds__(kThreads) k_elem_k2(
   double *Jf = qp + 6 * NQmax;            // kNfd x kT
   double *Fm = Jf + 120;                  // kMom face integrals of the cell monomials
   double *Gf = Fm + 35;                   // 6 x 6 face Gram, then its inverse
-  double *Gs = Gf + 36;                   // spare
-  double *mu = Gs + 36;                   // kMom cell moments
+  double *mu = Gf + 36;                   // kMom cell moments
   double *Hp = mu + kMom;                 // 10 x 10, inverted in place
-  double *Hw = Hp + 100;                  // W = H + |P| D^T D, then scratch
-  double *Hq = Hw + 100;                  // 4 x 4, inverted in place
-  double *Hq2 = Hq + 16;
-  double *Hqt = Hq2 + 16;                 // kNq x kGr: int m_g m_b
+  double *Hq = Hp + 100;                  // 4 x 4, inverted in place
+  double *Hqt = Hq + 16;                  // kNq x kGr: int m_g m_b
   double *W = Hqt + 4 * kGr;              // kV x kV
   const int tid = threadIdx.x;
 
@@ -468,12 +465,10 @@ __global__ void __launch_bounds__(kThreads) k_elem_k2(
 }
 
 vem_status element_k2(vem_handle *h) {
-  static bool tables = false;
-  if (!tables) {
-    const K2Tables t = make_tables();
-    VEM_CUDA(h, cudaMemcpyToSymbol(c_k2, &t, sizeof(t)));
-    tables = true;
-  }
+  // the decomposition and index tables (a few KB) go to the current device's
+  // constant memory before every launch
+  const K2Tables t = make_tables();
+  VEM_CUDA(h, cudaMemcpyToSymbolAsync(c_k2, &t, sizeof(t), 0, cudaMemcpyHostToDevice, h->stream));
   const int mx = h->max_nf_cell, mv = h->max_nv_face;
   const size_t bytes = sizeof(double) * k2_smem_doubles(mx, mv);
   if (h->hq_inv_n < h->ncls) {
