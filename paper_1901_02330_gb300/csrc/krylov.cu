@@ -17,6 +17,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <tuple>
 
 #include "handle.cuh"
@@ -375,15 +376,22 @@ static void launch_tiles(vem_handle *h, const VemOp &op, const T *sval, const T 
 // of a shape (rows, slices, systems, value type) every candidate (1, 2, 4, 8
 // systems per 32-row tile) runs on the live vectors in timing mode (products
 // only), three launches each after one warm-up, timed with CUDA events on the
-// stream; the fastest is kept for the process.
+// stream; the fastest is kept for the process (per device, shape and value
+// type; the cache is shared by all handles and guarded by a mutex).
 template <class T>
 static int tune_tiles(vem_handle *h, const VemOp &op, const T *sval, const T *u, const T *r, T *w, int nb_rr) {
-  static std::map<std::tuple<int64_t, int64_t, int>, int> best;
-  const auto key = std::make_tuple(op.S.rows, op.S.nslices, op.nbatch);
-  auto it = best.find(key);
-  if (it != best.end()) {
-    h->schur_tile = it->second;
-    return it->second;
+  static std::mutex mu;
+  static std::map<std::tuple<int, int64_t, int64_t, int>, int> best;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, op.S.rows, op.S.nslices, op.nbatch);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = best.find(key);
+    if (it != best.end()) {
+      h->schur_tile = it->second;
+      return it->second;
+    }
   }
   int pick = 1;
   float pick_ms = 1e30f;
@@ -401,7 +409,10 @@ static int tune_tiles(vem_handle *h, const VemOp &op, const T *sval, const T *u,
     }
   }
   cudaGetLastError();
-  best[key] = pick;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    best[key] = pick;
+  }
   h->schur_tile = pick;
   if (debug_on()) fprintf(stderr, "[vem] batched Schur SpMV tile: %d systems (%.3f ms / 3)\n", pick, pick_ms);
   return pick;
