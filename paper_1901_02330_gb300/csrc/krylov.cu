@@ -10,7 +10,9 @@
 //
 //   MINRES: Paige & Saunders (1975), preconditioned Lanczos form.
 //   FGMRES(m): Saad (1993), right preconditioning, classical Gram-Schmidt
-//   applied twice (CGS2) for the Arnoldi step, Givens rotations.
+//   for the Arnoldi step with a second pass when the first lost more than
+//   1/sqrt(2) of the vector's norm (Daniel, Gragg, Kaufman & Stewart 1976),
+//   Givens rotations.
 //   PCG: Hestenes & Stiefel (1952) with the Jacobi preconditioner or one
 //   V-cycle of the smoothed-aggregation AMG of amg.cu.
 #include <cmath>
@@ -772,9 +774,12 @@ __global__ void k_mr_update(int64_t n, const double *__restrict__ z, double *wol
 constexpr int kMD = 8;   // vectors per multi-dot pass
 
 // partials of V_i . w for i in [i0, i0 + cnt), cnt <= kMD
+// skip (optional): a device flag; the launch does nothing when it is 0.
 __global__ void __launch_bounds__(kRedThreads) k_multidot(int64_t n, const double *__restrict__ V,
                                                           int i0, int cnt,
-                                                          const double *__restrict__ w, double *part) {
+                                                          const double *__restrict__ w, double *part,
+                                                          const double *skip = nullptr) {
+  if (skip && *skip == 0.0) return;
   double acc[kMD];
 #pragma unroll
   for (int t = 0; t < kMD; ++t) acc[t] = 0.0;
@@ -791,7 +796,8 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(int64_t n, const doubl
 }
 
 // out[i] = sum of the partials of slot P_H0 + i, one block per i
-__global__ void k_multidot_fin(const double *part, int nb, double *out) {
+__global__ void k_multidot_fin(const double *part, int nb, double *out, const double *skip = nullptr) {
+  if (skip && *skip == 0.0) return;
   const double v = sum_partials(slot((double *)part, P_H0 + blockIdx.x), nb);
   if (threadIdx.x == 0) out[blockIdx.x] = v;
 }
@@ -799,7 +805,9 @@ __global__ void k_multidot_fin(const double *part, int nb, double *out) {
 // w += sgn * sum_i c[i] V_i  (i < cnt), optional partial of ||w||^2
 __global__ void __launch_bounds__(kRedThreads) k_multiaxpy(int64_t n, const double *__restrict__ V, int cnt,
                                                            const double *__restrict__ c, double sgn,
-                                                           double *w, double *part_nrm) {
+                                                           double *w, double *part_nrm,
+                                                           const double *skip = nullptr) {
+  if (skip && *skip == 0.0) return;
   __shared__ double cs[260];
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) cs[i] = sgn * c[i];
   __syncthreads();
@@ -825,7 +833,7 @@ struct GmLayout {
   __host__ __device__ int H2(int i) const { return H1(m + 1) + i; }
   __host__ __device__ int end() const { return H2(m + 1); }
 };
-enum { GM_BETA = S_GM, GM_IBETA, GM_EST, GM_IHN, GM_BAD };
+enum { GM_BETA = S_GM, GM_IBETA, GM_EST, GM_IHN, GM_BAD, GM_REORTH };
 
 __global__ void k_gm_start(double *sc, const double *part, int nb, GmLayout L) {
   const double r2 = sum_partials(slot((double *)part, P_R2), nb);
@@ -840,6 +848,22 @@ __global__ void k_gm_start(double *sc, const double *part, int nb, GmLayout L) {
 }
 
 // H[:, j] = h1 + h2, H[j+1, j] = ||w||, apply the rotations, new rotation
+// Second Gram-Schmidt pass only when the first lost too much: with w1 the
+// vector after the first pass and h its coefficients, reorthogonalise iff
+// ||w1|| < ||w0|| / sqrt(2), i.e. ||w1||^2 < ||h||^2 (||w0||^2 = ||w1||^2 +
+// ||h||^2); the criterion of Daniel, Gragg, Kaufman & Stewart, Math. Comp. 30
+// (1976).  Without it the second-pass coefficients are zero.
+__global__ void k_gm_reorth_flag(double *sc, const double *part, int nb, int j, GmLayout L) {
+  const double w2 = sum_partials(slot((double *)part, P_NRM), nb);
+  if (threadIdx.x != 0) return;
+  double h2 = 0.0;
+  for (int i = 0; i <= j; ++i) h2 += sc[L.H1(i)] * sc[L.H1(i)];
+  const bool again = !(w2 >= h2);   // also on NaN: the second pass then reports it
+  sc[GM_REORTH] = again ? 1.0 : 0.0;
+  if (!again)
+    for (int i = 0; i <= j; ++i) sc[L.H2(i)] = 0.0;
+}
+
 __global__ void k_gm_givens(double *sc, const double *part, int nb, int j, GmLayout L) {
   const double w2 = sum_partials(slot((double *)part, P_NRM), nb);
   if (threadIdx.x != 0) return;
@@ -1056,15 +1080,20 @@ static vem_status run_fgmres(vem_handle *h, const VemOp &op, const double *rhs, 
       double *Vj = V + (size_t)j * n, *Zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
       VEM_TRY(precond(h, op, Vj, Zj, pw, &inner, false));
       op_apply_timed(h, op, Zj, w);
+      // classical Gram-Schmidt, the second pass on the device's decision
       for (int pass = 0; pass < 2; ++pass) {
+        const double *skip = pass == 1 ? h->scal + GM_REORTH : nullptr;
         for (int i0 = 0; i0 <= j; i0 += kMD) {
           const int cnt = (j + 1 - i0) < kMD ? (j + 1 - i0) : kMD;
-          count_launch(); k_multidot<<<nbn, kRedThreads, 0, s>>>(n, V, i0, cnt, w, h->part);
+          count_launch(); k_multidot<<<nbn, kRedThreads, 0, s>>>(n, V, i0, cnt, w, h->part, skip);
         }
         double *hc = h->scal + (pass == 0 ? L.H1(0) : L.H2(0));
-        count_launch(); k_multidot_fin<<<j + 1, kRedThreads, 0, s>>>(h->part, nbn, hc);
-        count_launch(); k_multiaxpy<<<nbn, kRedThreads, 0, s>>>(n, V, j + 1, hc, -1.0, w,
-                                                pass == 1 ? slot(h->part, P_NRM) : nullptr);
+        count_launch(); k_multidot_fin<<<j + 1, kRedThreads, 0, s>>>(h->part, nbn, hc, skip);
+        count_launch(); k_multiaxpy<<<nbn, kRedThreads, 0, s>>>(n, V, j + 1, hc, -1.0, w, slot(h->part, P_NRM),
+                                                                 skip);
+        if (pass == 0) {
+          count_launch(); k_gm_reorth_flag<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbn, j, L);
+        }
       }
       count_launch(); k_gm_givens<<<1, kRedThreads, 0, s>>>(h->scal, h->part, nbn, j, L);
       count_launch(); k_scale_by<<<grid_for(n, 256), 256, 0, s>>>(n, w, h->scal + GM_IHN);

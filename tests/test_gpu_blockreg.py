@@ -191,8 +191,8 @@ def test_solve_matches_direct(vs, name, krylov):
 @pytest.mark.parametrize("method", ["minres", "fgmres"])
 def test_iterations_match_oracle(vs, name, method):
     """Same preconditioner, same Krylov method: the outer counts agree to a
-    few iterations (rounding differs: classical Gram-Schmidt twice here,
-    modified Gram-Schmidt in the oracle, restarts every 30)."""
+    few iterations (rounding differs: classical Gram-Schmidt with a conditional second
+    pass here, modified Gram-Schmidt in the oracle, restarts every 30)."""
     s, sys_ = _pair(vs, name, krylov=0 if method == "minres" else 1, restart=30, rtol=1e-10, maxit=4000)
     try:
         _, _, st = s.solve()

@@ -122,8 +122,8 @@ def test_block_schur_iterations_match_oracle(vs, ename):
     preconditioner: FGMRES(30), block-diagonal, the Schur block solved to
     1e-13 (exact in effect).  The outer iteration count matches the oracle's
     FGMRES with a direct Schur solve to within 10%: the two orthogonalise
-    differently (classical Gram-Schmidt twice here, modified Gram-Schmidt in
-    the oracle) and restart every 30 iterations, so rounding moves the count
+    differently (classical Gram-Schmidt with a conditional second pass here,
+    modified Gram-Schmidt in the oracle) and restart every 30 iterations, so rounding moves the count
     by a few iterations."""
     spec, elem = ELEMENTS[ename]
     m = _bc(hex_mesh(6), "neumann")
