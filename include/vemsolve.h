@@ -203,8 +203,14 @@ vem_status vem_sizes(const vem_handle *h, int64_t *n_u, int64_t *n_p);
 
 /* Quadrature points at which the caller evaluates the data (the paper leaves
  * the quadrature of b_h and f_h open, Sec. 4.3 remark):
- *   which = VEM_QP_CELL : one point per cell, its barycentre x_P; the load is
- *                         F_P = |P| f(x_P)  (n = n_cells);
+ *   which = VEM_QP_CELL : E0 / K1: one point per cell, its barycentre x_P;
+ *                         the load is F_P = |P| f(x_P)  (n = n_cells).
+ *                         K2: for every cell, in cell order, its fan
+ *                         tetrahedra (x_P, x_f, v_i, v_{i+1}) face by face,
+ *                         each with the 27 points of the collapsed 3-point
+ *                         Gauss product rule (degree 3); the load is
+ *                         F_P = |P| H_1^-1 (int_P f m_q)_q  (n = 27 * sum
+ *                         over cells of their faces' vertex counts);
  *   which = VEM_QP_BFACE: for every face with face_bc 1 or 2, in face
  *                         order, its fan triangles (x_f, v_i, v_{i+1}) each
  *                         with the 6-point degree-4 rule of Dunavant (1985)
