@@ -6,8 +6,9 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from oracle import E0, assemble, errors, paper_element, solvers
+from oracle import E0, assemble, element, errors, paper_element, solvers
 from oracle.element import interpolate
+from oracle.monomials import eval_mono3, mono3
 from synth import affine, fields, hex_mesh, octa_mesh, prism_mesh, tet_mesh
 from synth.voronoi import voronoi_mesh
 
@@ -48,7 +49,95 @@ def test_patch(mesh, spec, probname):
     np.testing.assert_allclose(p, pI, atol=1e-11)
 
 
-@pytest.mark.parametrize("spec", [E0, paper_element(1)], ids=lambda s: s.name)
+def _quadratic_and_cubic(K):
+    """p in P_2 and p in P_3 with constant K: u = -K grad p, f = div u."""
+    def p2(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        return 0.7 * X * X - X * Y + 0.3 * Z * Z + 0.5 * Y * Z - 0.2 * X + Y
+
+    def u2(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        return -K * np.stack([1.4 * X - Y - 0.2, -X + 0.5 * Z + 1.0, 0.6 * Z + 0.5 * Y], 1)
+
+    def f2(x):
+        return np.full(x.shape[0], -K * 2.0)
+
+    def p3(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        return X ** 3 - 2 * X * Y * Y + 0.5 * Z ** 3 + X * Y * Z + Y * Y - 0.4 * Z
+
+    def u3(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        return -K * np.stack([3 * X * X - 2 * Y * Y + Y * Z, -4 * X * Y + X * Z + 2 * Y,
+                              1.5 * Z * Z + X * Y - 0.4], 1)
+
+    def f3(x):
+        X, Z = x[:, 0], x[:, 2]
+        return -K * (2 * X + 2 + 3 * Z)
+
+    return {"quadratic": (p2, u2, f2), "cubic": (p3, u3, f3)}
+
+
+def _p1_moments(cells, q):
+    """Pressure DOFs of the k = 2 element: (1/|P|) int_P q m_a, m_a the scaled
+    P_1 monomials of the cell (eq. presMom)."""
+    return np.concatenate([(cell.qw * q(cell.qp)) @ eval_mono3(mono3(1), cell.qp, cell.centroid, cell.diameter)
+                           / cell.volume for cell in cells])
+
+
+def _exact_face_rule(F):
+    """The face's own integration rule (exact to degree 8) in place of the
+    degree-4 boundary data rule."""
+    return F.qp, F.qw
+
+
+@pytest.mark.parametrize("mesh", list(MESHES))
+@pytest.mark.parametrize("probname", ["quadratic", "cubic"])
+def test_patch_k2_dirichlet(mesh, probname, monkeypatch):
+    """k = 2 with pressure data on the whole boundary, constant K: for p in
+    P_3 (flux in [P_2]^3) u_h is the interpolant of the exact flux and p_h the
+    P_1 moments of p.  The boundary term -int_f g_D m^f needs degree
+    deg(p) + 2, which the degree-4 boundary data rule covers for p in P_2
+    only; the cubic case therefore swaps in an exact face rule, so that
+    what it checks is the element alone."""
+    if probname == "cubic":
+        monkeypatch.setattr(element, "load_face_points", _exact_face_rule)
+    spec = paper_element(2)
+    m = MESHES[mesh]()
+    K = 1.7
+    p_ex, u_ex, f_ex = _quadratic_and_cubic(K)[probname]
+    sys = assemble(m, spec, np.full(m.n_cells, 1.0 / K), f=f_ex, gD=p_ex, keep_local=True)
+    assert sys.n_p == 4 * m.n_cells and not sys.multiplier
+    u, p = solvers.solve_direct(sys)
+    uI = _interp_all(sys, spec, u_ex)
+    pI = _p1_moments(sys.cells, p_ex)
+    np.testing.assert_allclose(u, uI, atol=1e-10 * max(1, np.abs(uI).max()))
+    np.testing.assert_allclose(p, pI, atol=1e-10 * max(1, np.abs(pI).max()))
+
+
+def test_k2_cubic_patch_needs_an_exact_boundary_rule(monkeypatch):
+    """The degree-4 boundary data rule misses the degree-5 part of g_D m^f
+    for a cubic g_D on triangular faces, so the cubic k = 2 patch is not
+    reproduced there; the exact face rule changes g alone (M, B and F are
+    the same matrices) and restores it."""
+    spec = paper_element(2)
+    m = tet_mesh(2)
+    K = 1.7
+    p_ex, u_ex, f_ex = _quadratic_and_cubic(K)["cubic"]
+    sys = assemble(m, spec, np.full(m.n_cells, 1.0 / K), f=f_ex, gD=p_ex, keep_local=True)
+    u, _ = solvers.solve_direct(sys)
+    uI = _interp_all(sys, spec, u_ex)
+    assert np.abs(u - uI).max() > 1e-6 * np.abs(uI).max()
+    monkeypatch.setattr(element, "load_face_points", _exact_face_rule)
+    ex = assemble(m, spec, np.full(m.n_cells, 1.0 / K), f=f_ex, gD=p_ex)
+    assert abs(ex.M - sys.M).max() == 0.0 and abs(ex.B - sys.B).max() == 0.0
+    np.testing.assert_array_equal(ex.F, sys.F)
+    assert np.abs(ex.g - sys.g).max() > 1e-6 * np.abs(ex.g).max()
+    ue, _ = solvers.solve_direct(ex)
+    np.testing.assert_allclose(ue, uI, atol=1e-10 * np.abs(uI).max())
+
+
+@pytest.mark.parametrize("spec", [E0, paper_element(1), paper_element(2)], ids=lambda s: s.name)
 def test_local_conservation(spec):
     """B u_h = F: div u_h equals the projection of f on every cell."""
     m = prism_mesh(2)
@@ -59,13 +148,14 @@ def test_local_conservation(spec):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("spec,rv,rq", [(E0, 1.0, 1.0), (paper_element(1), 2.0, 1.0)], ids=["E0", "E1"])
+@pytest.mark.parametrize("spec,rv,rq", [(E0, 1.0, 1.0), (paper_element(1), 2.0, 1.0),
+                                        (paper_element(2), 3.0, 2.0)], ids=["E0", "E1", "E2"])
 def test_convergence_rates(spec, rv, rq):
     """Sine solution on 4^3 -> 8^3 cubes: observed slopes of e_v, e_q against
     h (eq. meshSize) at least the expected rates - 0.2.  Expected: pressure
-    O(h^k) (P0 pressure), flux O(h^{k+1}) for the paper's k = 1 and O(h)
-    for E0 -- Remark 4.1 prints the two rates the other way round; a P_{k-1}
-    pressure cannot converge faster than O(h^k) in L2."""
+    O(h^k) (P_{k-1} pressure), flux O(h^{k+1}) for the paper's k = 1, 2 and
+    O(h) for E0 -- Remark 4.1 prints the two rates the other way round; a
+    P_{k-1} pressure cannot converge faster than O(h^k) in L2."""
     prob = fields.sine_problem()
     hs, ev, eq = [], [], []
     for n in (4, 8):
