@@ -95,6 +95,34 @@ def test_mixed_boundary_patch(spec):
     np.testing.assert_allclose(p, pI, atol=1e-10)
 
 
+@pytest.mark.parametrize("mesh", ["sheared", "prism"])
+def test_mixed_boundary_patch_k2(mesh):
+    """k = 2, pressure data on x = 0 and flux data elsewhere, constant K and
+    p in P_3 (flux in [P_2]^3): no multiplier, u_h is the interpolant and
+    p_h the P_1 moments of p.  The Dirichlet faces at x = 0 are rectangles
+    and parallelograms: centrally symmetric, so on their fans the odd part
+    of g_D m^f about the face centroid integrates to zero and the rest has
+    degree <= 4, which the degree-4 face rule integrates exactly."""
+    from oracle.monomials import eval_mono3, mono3
+    spec = paper_element(2)
+    base = hex_mesh(2) if mesh == "sheared" else prism_mesh(2)
+    m = _mixed_bc(base)
+    if mesh == "sheared":
+        A = np.array([[1.0, 0.0, 0.0], [0.3, 0.8, -0.2], [0.1, 0.0, 1.2]])
+        m = affine(m, A, (0.0, 0.0, 0.0))
+    K = 1.3
+    p_ex, u_ex, f_ex = _cubic_problem(K)
+    sys = assemble(m, spec, np.full(m.n_cells, 1.0 / K), f=f_ex, gD=p_ex, flux=u_ex)
+    assert not sys.multiplier and sys.fixed.size > 0
+    u, p = solvers.solve_direct(sys)
+    cells = mesh_cells(m)
+    uI = _interp(sys, spec, cells, m, u_ex)
+    pI = np.concatenate([(cell.qw * p_ex(cell.qp)) @ eval_mono3(mono3(1), cell.qp, cell.centroid, cell.diameter)
+                         / cell.volume for cell in cells])
+    np.testing.assert_allclose(u, uI, atol=1e-10 * max(1, np.abs(uI).max()))
+    np.testing.assert_allclose(p, pI, atol=1e-10 * max(1, np.abs(pI).max()))
+
+
 @pytest.mark.parametrize("spec", [E0, paper_element(1)], ids=lambda s: s.name)
 def test_neumann_conservation_and_krylov(spec):
     """Paper's polynomial solution with flux data: B u_h = F - c lambda per
