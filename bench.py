@@ -136,14 +136,16 @@ class Clocks:
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="vem_clocks_", suffix=".csv")
+        self.f = os.fdopen(fd, "w")
         try:
-            import tempfile
-            fd, self.path = tempfile.mkstemp(prefix="vem_clocks_", suffix=".csv")
-            self.f = os.fdopen(fd, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
                                        "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            self.f.close()
+            os.remove(self.path)
 
     def stop(self):
         if self.p is None:
