@@ -115,7 +115,10 @@ def run_reference(a):
         times.append(dt)
     tot = sum(times)
     value = n * a.steps / tot
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": a.steps,
+    # n_gpus is the launch's N, as in the other arm's line; the oracle itself
+    # runs on rank 0's host cores and uses none of them (gpus_used)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": max(world, a.gpus), "gpus_used": 0,
+            "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
