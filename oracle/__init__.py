@@ -20,8 +20,11 @@ steps in its order and notation:
 * Sec. 4.2   pressure moments                                -> element.py
 * Sec. 4.3   local forms a_{h,P}, b_{h,P}, f_{h,P}, the dofi-dofi
              stabilisation, global assembly                  -> element.py, assemble.py
-* Sec. 5     block preconditioners (Block-Schur / block-triangular),
-             MINRES, FGMRES, Jacobi-PCG                      -> solvers.py
+* Sec. 5     block preconditioners (Block-Schur / block-triangular,
+             Block-Reg), MINRES, FGMRES, Jacobi-PCG          -> solvers.py
+             smoothed-aggregation AMG for S and A_reg        -> amg.py
+             point-block AMG for S with several pressure
+             moments per cell (k >= 2)                       -> block_amg.py
 * Sec. 4.4   error indicators e_v, e_q                       -> errors.py
 
 Every function is pinned by a ``-m "not gpu"`` test against something the

@@ -113,7 +113,10 @@ class BlockPreconditioner:
     for the pressure block.  inner='exact' factorises S (the paper's choice,
     with MUMPS there and SuperLU here); inner='pcg' uses Jacobi-PCG to
     inner_rtol; inner='amg' uses CG preconditioned by one V-cycle of the
-    smoothed-aggregation AMG of oracle/amg.py to inner_rtol.
+    smoothed-aggregation AMG of oracle/amg.py to inner_rtol; inner='block-amg'
+    the same with the point-block AMG of oracle/block_amg.py (a cell's
+    pressure moments kept together, near-null space the moments of 1, x, y,
+    z; needs assemble(..., keep_local=True)).
 
     kind='reg' is the paper's Block-Reg (Sec. 5): block-diagonal with one
     V-cycle of the smoothed-aggregation AMG of A + B^T W^{-1} B (Chebyshev
@@ -158,6 +161,10 @@ class BlockPreconditioner:
             if sys.multiplier and sys.n_p != sys.vol.size:
                 raise NotImplementedError("AMG with the multiplier needs one pressure DOF per cell")
             self.H = amg.setup(self.S, pin_last=sys.multiplier)
+        elif inner == "block-amg":
+            from . import block_amg
+            self.bamg = block_amg
+            self.H = block_amg.setup(self.S, sys.spec.nq, block_amg.pressure_modes(sys), pin_last=sys.multiplier)
 
     def solve_S(self, r):
         if self.multiplier:
@@ -169,6 +176,8 @@ class BlockPreconditioner:
             return self.lu.solve(r)
         if self.inner == "amg":
             res = self.amg.amg_pcg(self.S, r, self.H, self.inner_rtol, self.inner_maxit)
+        elif self.inner == "block-amg":
+            res = self.bamg.pcg(self.S, r, self.H, self.inner_rtol, self.inner_maxit)
         else:
             res = pcg(self.S, r, self.inner_rtol, self.inner_maxit)
         self.inner_iters += res.iters
