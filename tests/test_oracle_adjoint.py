@@ -9,17 +9,25 @@ from synth import fields, prism_mesh
 from synth.voronoi import voronoi_mesh
 
 
-def _check(mesh, spec, seed):
+def _check(mesh, spec, seed, flux_term=False):
+    """flux_term: the misfit also weighs the flux DOFs (w . u, w random),
+    which exercises the flux part of the adjoint right-hand side and its
+    sign relative to the pressure part (the system is solved for -p)."""
     rng = np.random.default_rng(seed)
     theta = rng.standard_normal(mesh.n_cells)
     prob = fields.sine_problem()
     ptarget = rng.standard_normal(mesh.n_cells) * 0.1
+    w = None
 
     def loss(u, p):
-        return 0.5 * np.sum((p - ptarget) ** 2)
+        val = 0.5 * np.sum((p - ptarget) ** 2)
+        return val + (w @ u if flux_term else 0.0)
 
     def dL(u, p):
-        return np.zeros_like(u), p - ptarget
+        return (w.copy() if flux_term else np.zeros_like(u)), p - ptarget
+
+    n_u = solve_u_p(mesh, spec, theta, prob.f, prob.gD)[0].size
+    w = rng.standard_normal(n_u) * 0.05
 
     u, p, g = gradient_logK(mesh, spec, theta, prob.f, prob.gD, dL)
     eps = 1e-6
@@ -38,3 +46,8 @@ def test_adjoint_E0_voronoi():
 
 def test_adjoint_K1_prism():
     _check(prism_mesh(2), paper_element(1), 2)
+
+
+def test_adjoint_flux_and_pressure_misfit():
+    _check(prism_mesh(2), paper_element(1), 3, flux_term=True)
+    _check(voronoi_mesh(25, seed=6, lloyd=2), E0, 4, flux_term=True)
