@@ -24,8 +24,11 @@ CASES = {"E0-cvt": (lambda: voronoi_mesh(60, seed=5, lloyd=3), E0, 0),
          "K1-prism": (lambda: prism_mesh(3), paper_element(1), 1)}
 
 
+@pytest.mark.parametrize("flux_term", [False, True], ids=["p-misfit", "u-and-p-misfit"])
 @pytest.mark.parametrize("case", list(CASES))
-def test_adjoint_matches_oracle(vs, case):
+def test_adjoint_matches_oracle(vs, case, flux_term):
+    """flux_term: the loss also has a term w . u on the flux DOFs, so dL/du
+    enters the adjoint right-hand side next to dL/dp."""
     mk, spec, elem = CASES[case]
     mesh = mk()
     rng = np.random.default_rng(7)
@@ -36,9 +39,10 @@ def test_adjoint_matches_oracle(vs, case):
     s.set_coefficient(np.exp(theta))
     s.set_data(prob.f, prob.gD)
     u, p, st = s.solve()
-    g, ast = s.adjoint(None, p - ptarget)
+    w = 0.05 * rng.standard_normal(u.size) if flux_term else np.zeros(u.size)
+    g, ast = s.adjoint(w if flux_term else None, p - ptarget)
     u_o, p_o, g_o = gradient_logK(mesh, spec, theta, prob.f, prob.gD,
-                                  lambda u_, p_: (np.zeros_like(u_), p_ - ptarget))
+                                  lambda u_, p_: (w.copy(), p_ - ptarget))
     assert np.linalg.norm(g - g_o) <= 1e-8 * np.linalg.norm(g_o)
     s.close()
 
