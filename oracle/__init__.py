@@ -25,6 +25,7 @@ steps in its order and notation:
              smoothed-aggregation AMG for S and A_reg        -> amg.py
              point-block AMG for S with several pressure
              moments per cell (k >= 2)                       -> block_amg.py
+             edge-patch Schwarz smoothing for A_reg          -> schwarz.py
 * Sec. 4.4   error indicators e_v, e_q                       -> errors.py
 
 Every function is pinned by a ``-m "not gpu"`` test against something the

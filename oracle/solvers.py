@@ -120,11 +120,14 @@ class BlockPreconditioner:
 
     kind='reg' is the paper's Block-Reg (Sec. 5): block-diagonal with one
     V-cycle of the smoothed-aggregation AMG of A + B^T W^{-1} B (Chebyshev
-    smoothing, as in the GAMG preconditioner the paper names) for the flux
+    smoothing, as in the GAMG preconditioner the paper names, or with
+    reg_smoother='edge-schwarz' the edge-patch Schwarz smoothing of
+    oracle/schwarz.py on the finest level, which needs the mesh) for the flux
     block and W^{-1} = I / gamma for the pressure block; gamma defaults to
     h^2, h the mean cell diameter (the paper's choice)."""
 
-    def __init__(self, sys, kind="diag", inner="exact", inner_rtol=1e-12, inner_maxit=10000, gamma=None):
+    def __init__(self, sys, kind="diag", inner="exact", inner_rtol=1e-12, inner_maxit=10000, gamma=None,
+                 reg_smoother="chebyshev", mesh=None):
         self.n_u = sys.n_u
         self.kind = kind
         self.inner_iters = 0
@@ -133,7 +136,17 @@ class BlockPreconditioner:
             self.amg = amg
             self.gamma = mesh_size(sys) ** 2 if gamma is None else float(gamma)
             self.A_reg = regularized(sys, self.gamma)
-            self.H_reg = amg.setup(self.A_reg, smoother="chebyshev")
+            if reg_smoother == "chebyshev":
+                H = amg.setup(self.A_reg, smoother="chebyshev")
+                self.cycle_reg = lambda r: amg.vcycle(H, r)
+                self.H_reg = H
+            elif reg_smoother == "edge-schwarz":
+                from . import schwarz
+                if mesh is None:
+                    raise ValueError("the edge-patch smoother needs the mesh")
+                self.cycle_reg = schwarz.setup(self.A_reg, schwarz.edge_patches(mesh, sys.spec))
+            else:
+                raise ValueError(reg_smoother)
             return
         self.B = sys.B
         self.dM = sys.M.diagonal().copy()
@@ -186,7 +199,7 @@ class BlockPreconditioner:
     def __call__(self, r):
         ru, rp = r[:self.n_u], r[self.n_u:]
         if self.kind == "reg":
-            return np.concatenate([self.amg.vcycle(self.H_reg, ru), rp / self.gamma])
+            return np.concatenate([self.cycle_reg(ru), rp / self.gamma])
         if self.kind == "diag":
             return np.concatenate([ru / self.dM, self.solve_S(rp)])
         zp = -self.solve_S(rp)
@@ -295,7 +308,7 @@ def fgmres(A, b, Pinv, restart=30, rtol=1e-12, maxit=5000):
 
 
 def solve_krylov(sys, method="minres", kind="diag", inner="exact", rtol=1e-12,
-                 inner_rtol=1e-12, restart=30, maxit=5000, gamma=None):
+                 inner_rtol=1e-12, restart=30, maxit=5000, gamma=None, reg_smoother="chebyshev", mesh=None):
     """Preconditioned Krylov solve; returns (u, p, Result) with physical p.
     With the mean-zero multiplier the pressure equations are made consistent
     first (F - c lambda with lambda = sum F / sum c, the multiplier's value),
@@ -307,7 +320,8 @@ def solve_krylov(sys, method="minres", kind="diag", inner="exact", rtol=1e-12,
         e, c = sys.null_vec, sys.cvec
         lam = (e @ b[sys.n_u:]) / (e @ c)
         b[sys.n_u:] -= c * lam
-    P = BlockPreconditioner(sys, kind=kind, inner=inner, inner_rtol=inner_rtol, gamma=gamma)
+    P = BlockPreconditioner(sys, kind=kind, inner=inner, inner_rtol=inner_rtol, gamma=gamma,
+                            reg_smoother=reg_smoother, mesh=mesh)
     if method == "minres":
         if kind not in ("diag", "reg"):
             raise ValueError("MINRES needs an SPD block-diagonal preconditioner")
