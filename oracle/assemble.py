@@ -114,10 +114,12 @@ def cell_dofmap(mesh, c: int, spec: ElementSpec):
     return np.array(idx, dtype=np.int64)
 
 
-def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False, nq=5, flux=None) -> System:
+def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False, nq=5, flux=None,
+             bface_rule="dunavant4") -> System:
     """Assemble M, B, g, F.  nu_cell = 1/K per cell (eq. bilin_form, nu = K^-1).
     flux: the vector field u (callable (N,3) -> (N,3)) whose normal component
-    is prescribed on faces with flag 2."""
+    is prescribed on faces with flag 2.  bface_rule: the fan rule of the
+    Dirichlet term ('dunavant4', the library's, or 'radon5')."""
     nu_cell = np.asarray(nu_cell, dtype=np.float64)
     faces = all_faces(mesh, nq)
     n_u = spec.nfd * mesh.n_faces + spec.nid * mesh.n_cells
@@ -133,7 +135,7 @@ def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False
         cell = cell_geometry(mesh, c, faces, nq)
         vol[c] = cell.volume
         diam[c] = cell.diameter
-        loc = local_system(cell, spec, float(nu_cell[c]), f=f, gD=gD)
+        loc = local_system(cell, spec, float(nu_cell[c]), f=f, gD=gD, bface_rule=bface_rule)
         dm = cell_dofmap(mesh, c, spec)
         pm = spec.nq * c + np.arange(spec.nq)
         rows.append(np.repeat(dm, dm.size))

@@ -41,7 +41,7 @@ import numpy as np
 
 from .monomials import (mono2, mono3, dim_P2, MG_plus, decompose, eval_mono2,
                         eval_mono3, eval_grad_mono3, mI_cross)
-from .quadrature import dunavant4
+from .quadrature import dunavant4, radon5
 
 
 @dataclass(frozen=True)
@@ -89,7 +89,7 @@ def _cell_gram(alphas_a, alphas_b, cell):
     return (cell.qw[:, None] * Ma).T @ Mb
 
 
-def local_system(cell, spec: ElementSpec, nu: float, f=None, gD=None, details=False):
+def local_system(cell, spec: ElementSpec, nu: float, f=None, gD=None, details=False, bface_rule="dunavant4"):
     """Local matrices of cell P.  Returns dict(M, B, F, g[, details...]).
 
     Local DOF order: for each face of the cell (in the cell's face order) its
@@ -201,7 +201,7 @@ def local_system(cell, spec: ElementSpec, nu: float, f=None, gD=None, details=Fa
         for i, F in enumerate(faces):
             if F.bc != 1:
                 continue
-            pts, wts = load_face_points(F)
+            pts, wts = load_face_points(F, bface_rule)
             Mf = eval_mono2(betas, pts, F)
             gm = (wts[:, None] * Mf).T @ gD(pts)     # int_f g_D m^f_gamma
             g[i * nfd:(i + 1) * nfd] = -F.sigma * F.area * (face_ginv[i].T @ gm)
@@ -212,14 +212,16 @@ def local_system(cell, spec: ElementSpec, nu: float, f=None, gD=None, details=Fa
     return out
 
 
-def load_face_points(F):
-    """Boundary-face load rule: Dunavant degree-4 on the fan (x_f, v_i, v_{i+1})."""
+def load_face_points(F, rule="dunavant4"):
+    """Boundary-face load rule on the fan (x_f, v_i, v_{i+1}): Dunavant's
+    degree-4 rule (the library's), or rule='radon5', Radon's degree-5 rule."""
+    tri = {"dunavant4": dunavant4, "radon5": radon5}[rule]
     V = F.verts
     m = V.shape[0]
     pts, wts = [], []
     for i in range(m):
         A, B = V[i], V[(i + 1) % m]
-        p, w = dunavant4(F.centroid, A, B)
+        p, w = tri(F.centroid, A, B)
         s = np.sign(np.dot(np.cross(A - F.centroid, B - F.centroid), F.normal))
         pts.append(p)
         wts.append(w * s)

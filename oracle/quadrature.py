@@ -15,7 +15,9 @@ definitions and independently in the CUDA library:
 * boundary-face rule: the face is fanned into triangles (x_f, v_i, v_{i+1})
   and each triangle gets the 6-point degree-4 rule of D.A. Dunavant,
   "High degree efficient symmetrical Gaussian quadrature rules for the
-  triangle", IJNME 21 (1985), Table for p = 4.
+  triangle", IJNME 21 (1985), Table for p = 4 (the library's rule), or on
+  request Radon's 7-point degree-5 rule, which makes the Dirichlet term of
+  the k = 2 element exact for cubic g_D.
 """
 
 from __future__ import annotations
@@ -76,6 +78,28 @@ def dunavant4(A, B, C):
     bary = []
     wts = []
     for a, w in zip(_DUN4_A, _DUN4_W):
+        b = 1.0 - 2.0 * a
+        for l in ((a, a, b), (a, b, a), (b, a, a)):
+            bary.append(l)
+            wts.append(w)
+    bary = np.array(bary)
+    pts = bary[:, 0:1] * A + bary[:, 1:2] * B + bary[:, 2:3] * C
+    return pts, np.array(wts) * area
+
+
+def radon5(A, B, C):
+    """Radon's degree-5 7-point rule on triangle ABC (J. Radon, "Zur
+    mechanischen Kubatur", Monatsh. Math. 52 (1948)): the centroid with
+    weight 9/40 and the orbits (a, a, 1 - 2a), a = (6 -+ sqrt 15)/21, with
+    weights (155 -+ sqrt 15)/1200, as fractions of the area."""
+    A = np.asarray(A, float)
+    B = np.asarray(B, float)
+    C = np.asarray(C, float)
+    area = 0.5 * np.linalg.norm(np.cross(B - A, C - A))
+    r15 = np.sqrt(15.0)
+    bary = [(1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0)]
+    wts = [9.0 / 40.0]
+    for a, w in (((6.0 - r15) / 21.0, (155.0 - r15) / 1200.0), ((6.0 + r15) / 21.0, (155.0 + r15) / 1200.0)):
         b = 1.0 - 2.0 * a
         for l in ((a, a, b), (a, b, a), (b, a, a)):
             bary.append(l)

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from oracle.polyhedron import cell_geometry, face_geometry
-from oracle.quadrature import dunavant4, tet_rule, triangle_rule
+from oracle.quadrature import dunavant4, radon5, tet_rule, triangle_rule
 from synth import affine, hex_mesh, tet_mesh
 
 
@@ -15,7 +15,7 @@ def _bary_integral(a, b, c, area):
     return 2 * area * factorial(a) * factorial(b) * factorial(c) / factorial(a + b + c + 2)
 
 
-@pytest.mark.parametrize("rule", ["gauss", "dunavant"])
+@pytest.mark.parametrize("rule", ["gauss", "dunavant", "radon"])
 def test_triangle_rules_exact(rule):
     rng = np.random.default_rng(0)
     A, B, C = rng.uniform(-1, 1, (3, 3))
@@ -23,9 +23,12 @@ def test_triangle_rules_exact(rule):
     if rule == "gauss":
         pts, w = triangle_rule(A, B, C, 5)
         maxdeg, tol = 8, 1e-13
-    else:
+    elif rule == "dunavant":
         pts, w = dunavant4(A, B, C)
         maxdeg, tol = 4, 1e-13
+    else:
+        pts, w = radon5(A, B, C)
+        maxdeg, tol = 5, 1e-13
     # barycentric coordinates of the points
     T = np.stack([B - A, C - A], 1)
     lam = np.linalg.lstsq(T, (pts - A).T, rcond=None)[0].T
@@ -36,6 +39,22 @@ def test_triangle_rules_exact(rule):
             for c in range(maxdeg + 1 - a - b):
                 val = np.sum(w * l1 ** a * l2 ** b * l3 ** c)
                 assert val == pytest.approx(_bary_integral(a, b, c, area), rel=tol, abs=tol)
+
+
+@pytest.mark.parametrize("rule", ["dunavant", "radon"])
+def test_triangle_rules_degree_is_sharp(rule):
+    """The stated degree is the largest: some monomial one degree higher is
+    integrated with an error well above rounding."""
+    A, B, C = np.array([0.0, 0, 0]), np.array([1.0, 0, 0]), np.array([0.0, 1, 0])
+    pts, w = (dunavant4 if rule == "dunavant" else radon5)(A, B, C)
+    d = 5 if rule == "dunavant" else 6
+    T = np.stack([B - A, C - A], 1)
+    lam = np.linalg.lstsq(T, (pts - A).T, rcond=None)[0].T
+    l2, l3 = lam[:, 0], lam[:, 1]
+    l1 = 1 - l2 - l3
+    errs = [abs(np.sum(w * l1 ** a * l2 ** b * l3 ** (d - a - b)) - _bary_integral(a, b, d - a - b, 0.5))
+            / _bary_integral(a, b, d - a - b, 0.5) for a in range(d + 1) for b in range(d + 1 - a)]
+    assert max(errs) > 1e-6
 
 
 def test_tet_rule_second_moments():

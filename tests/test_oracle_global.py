@@ -85,10 +85,25 @@ def _p1_moments(cells, q):
                            / cell.volume for cell in cells])
 
 
-def _exact_face_rule(F):
+def _exact_face_rule(F, rule=None):
     """The face's own integration rule (exact to degree 8) in place of the
     degree-4 boundary data rule."""
     return F.qp, F.qw
+
+
+@pytest.mark.parametrize("mesh", ["tet", "prism", "voronoi"])
+def test_patch_k2_dirichlet_radon_rule(mesh):
+    """With Radon's degree-5 fan rule for the Dirichlet term the cubic k = 2
+    patch holds on triangular and Voronoi faces as well."""
+    spec = paper_element(2)
+    m = MESHES[mesh]()
+    K = 1.7
+    p_ex, u_ex, f_ex = _quadratic_and_cubic(K)["cubic"]
+    sys = assemble(m, spec, np.full(m.n_cells, 1.0 / K), f=f_ex, gD=p_ex, keep_local=True, bface_rule="radon5")
+    u, p = solvers.solve_direct(sys)
+    uI = _interp_all(sys, spec, u_ex)
+    np.testing.assert_allclose(u, uI, atol=1e-10 * np.abs(uI).max())
+    np.testing.assert_allclose(p, _p1_moments(sys.cells, p_ex), atol=1e-10 * np.abs(p).max())
 
 
 @pytest.mark.parametrize("mesh", list(MESHES))
