@@ -49,6 +49,13 @@ Exact rules:
 * cycle: V(1,1) with damped block Jacobi, x = omega D^-1 b;
   x += P V(P^T (b - A x)); x += omega D^-1 (b - A x); symmetric, and
   positive definite when the smoother converges (rho > 2/3 lambda_max).
+  Or (smoother='chebyshev') two Chebyshev steps of block Jacobi on
+  [rho/10, rho] before and after the coarse correction.
+
+The same construction serves the regularised flux block A_reg of Block-Reg
+at the paper's k = 1, whose face moments (3 per face) and interior moments
+(3 per cell) form 3 x 3 blocks: near-null space the DOFs of the three
+constant vector fields (``flux_modes``), Chebyshev smoothing.
 """
 
 from __future__ import annotations
@@ -187,6 +194,8 @@ class Level:
 class Hierarchy:
     levels: list = field(default_factory=list)
     coarse_inv: np.ndarray = None
+    smoother: str = "jacobi"           # 'jacobi' (one damped step) or 'chebyshev'
+    degree: int = 2                    # Chebyshev steps per smoothing
 
     @property
     def sizes(self):
@@ -194,16 +203,22 @@ class Hierarchy:
 
 
 def setup(A: sp.csr_matrix, bs: int, B: np.ndarray, theta: float = 0.08, coarse_max: int = 64,
-          max_levels: int = 12, dense_max: int = 1024, pin_last: bool = False) -> Hierarchy:
+          max_levels: int = 12, dense_max: int = 1024, pin_last: bool = False,
+          smoother: str = "jacobi", degree: int = 2) -> Hierarchy:
     """A: SPD with bs x bs point blocks, or SPSD with the constant pressure
     as null space (pin_last: flux data on the whole boundary; its first
     column of B must be that null vector); B: near-null space, one row per
-    DOF of A."""
+    DOF of A.  smoother: damped block Jacobi, or 'chebyshev': ``degree``
+    steps of Chebyshev acceleration of block Jacobi on [rho/10, rho] (Saad
+    2003, Algorithm 12.1, as in ``amg.chebyshev`` with D the block
+    diagonal); the hierarchy does not depend on it."""
+    if smoother not in ("jacobi", "chebyshev"):
+        raise ValueError(smoother)
     A = A.tocsr()
     B = np.asarray(B, dtype=np.float64)
     if A.shape[0] % bs or B.shape[0] != A.shape[0]:
         raise ValueError("A and B must consist of whole blocks")
-    H = Hierarchy()
+    H = Hierarchy(smoother=smoother, degree=degree)
     th = theta
     while True:
         Dinv = block_diag_inv(A, bs)
@@ -240,13 +255,41 @@ def setup(A: sp.csr_matrix, bs: int, B: np.ndarray, theta: float = 0.08, coarse_
     return H
 
 
+def chebyshev(lv: Level, b: np.ndarray, x: np.ndarray, degree: int) -> np.ndarray:
+    """``degree`` Chebyshev steps for A x = b from x with the block-Jacobi
+    residual D^-1 (b - A x) on [lo, hi] = [rho/10, rho]."""
+    hi = lv.rho
+    lo = hi / 10.0
+    theta = 0.5 * (hi + lo)
+    delta = 0.5 * (hi - lo)
+    sigma = theta / delta
+    rho_k = 1.0 / sigma
+    d = (lv.Dinv @ (b - lv.A @ x)) / theta
+    x = x + d
+    for _ in range(degree - 1):
+        rho_n = 1.0 / (2.0 * sigma - rho_k)
+        d = rho_n * rho_k * d + (2.0 * rho_n / delta) * (lv.Dinv @ (b - lv.A @ x))
+        x = x + d
+        rho_k = rho_n
+    return x
+
+
+def smooth(H: Hierarchy, lv: Level, b: np.ndarray, x) -> np.ndarray:
+    """One smoothing of the cycle; x = None starts from zero."""
+    if H.smoother == "chebyshev":
+        return chebyshev(lv, b, np.zeros_like(b) if x is None else x, H.degree)
+    if x is None:
+        return lv.omega * (lv.Dinv @ b)
+    return x + lv.omega * (lv.Dinv @ (b - lv.A @ x))
+
+
 def vcycle(H: Hierarchy, b: np.ndarray, level: int = 0) -> np.ndarray:
     lv = H.levels[level]
     if level == len(H.levels) - 1:
         return H.coarse_inv @ b
-    x = lv.omega * (lv.Dinv @ b)
+    x = smooth(H, lv, b, None)
     x = x + lv.P @ vcycle(H, lv.P.T @ (b - lv.A @ x), level + 1)
-    return x + lv.omega * (lv.Dinv @ (b - lv.A @ x))
+    return smooth(H, lv, b, x)
 
 
 def pcg(S, b, H: Hierarchy, rtol=1e-12, maxit=1000):
@@ -292,4 +335,21 @@ def pressure_modes(sys) -> np.ndarray:
         Mq = eval_mono3(mono3(1), cell.qp, cell.centroid, cell.diameter)
         Q = np.column_stack([np.ones(cell.qp.shape[0]), cell.qp])
         out[4 * c:4 * c + 4] = (Mq.T * cell.qw) @ Q / cell.volume
+    return out
+
+
+def flux_modes(sys) -> np.ndarray:
+    """Near-null space of A_reg = A + B^T B / gamma for the flux DOFs: the
+    DOFs (face moments in the global orientation, interior moments) of the
+    three constant vector fields, which are divergence-free.  Needs the cells
+    of the system (assemble(..., keep_local=True))."""
+    from .element import interpolate
+    if sys.cells is None:
+        raise ValueError("flux_modes needs assemble(..., keep_local=True)")
+    out = np.zeros((sys.n_u, 3))
+    for c, cell in enumerate(sys.cells):
+        for j in range(3):
+            e = np.zeros(3)
+            e[j] = 1.0
+            out[sys.dofmap[c], j] = interpolate(cell, sys.spec, lambda X, e=e: np.tile(e, (X.shape[0], 1)))
     return out

@@ -120,9 +120,12 @@ class BlockPreconditioner:
 
     kind='reg' is the paper's Block-Reg (Sec. 5): block-diagonal with one
     V-cycle of the smoothed-aggregation AMG of A + B^T W^{-1} B (Chebyshev
-    smoothing, as in the GAMG preconditioner the paper names, or with
+    smoothing, as in the GAMG preconditioner the paper names; with
     reg_smoother='edge-schwarz' the edge-patch Schwarz smoothing of
-    oracle/schwarz.py on the finest level, which needs the mesh) for the flux
+    oracle/schwarz.py on the finest level, which needs the mesh; with
+    reg_smoother='block-chebyshev' (k = 1) the point-block AMG of
+    oracle/block_amg.py on 3 x 3 blocks with the constant fields as
+    near-null space) for the flux
     block and W^{-1} = I / gamma for the pressure block; gamma defaults to
     h^2, h the mean cell diameter (the paper's choice)."""
 
@@ -140,6 +143,13 @@ class BlockPreconditioner:
                 H = amg.setup(self.A_reg, smoother="chebyshev")
                 self.cycle_reg = lambda r: amg.vcycle(H, r)
                 self.H_reg = H
+            elif reg_smoother == "block-chebyshev":
+                from . import block_amg
+                if not (sys.spec.nfd == sys.spec.nid == 3):
+                    raise NotImplementedError("3 x 3 flux blocks need the paper's k = 1 element")
+                Hb = block_amg.setup(self.A_reg, 3, block_amg.flux_modes(sys), smoother="chebyshev")
+                self.cycle_reg = lambda r: block_amg.vcycle(Hb, r)
+                self.H_reg = Hb
             elif reg_smoother == "edge-schwarz":
                 from . import schwarz
                 if mesh is None:

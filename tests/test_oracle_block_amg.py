@@ -203,3 +203,89 @@ def test_block_amg_with_p0_pressure():
     u, p, res = solvers.solve_krylov(sys_, "fgmres", "tri", "block-amg", rtol=1e-11, inner_rtol=1e-13)
     assert res.converged
     np.testing.assert_allclose(p, pd, atol=1e-8 * np.abs(pd).max())
+
+
+# ---- the same construction on the regularised flux block of Block-Reg (k = 1)
+
+def test_flux_modes_on_cubes():
+    """The constant field e_x has face moments (1, 0, 0) on x-normal faces
+    (global normal +x, centred face monomials) and 0 on the others, and zero
+    cross moments (int_P (x - x_P) = 0); likewise for e_y, e_z."""
+    n = 2
+    m = hex_mesh(n)
+    sys_ = assemble(m, paper_element(1), np.ones(m.n_cells), keep_local=True)
+    B = block_amg.flux_modes(sys_)
+    nfx = n * n * (n + 1)                     # faces per normal direction, x first
+    ref = np.zeros_like(B)
+    for d in range(3):
+        for f in range(d * nfx, (d + 1) * nfx):
+            ref[3 * f, d] = 1.0
+    np.testing.assert_allclose(B, ref, atol=1e-13)
+
+
+def test_block_chebyshev_error_factors():
+    """Block-Chebyshev smoothing from zero leaves the error p(lambda) v on
+    every generalised eigenvector A v = lambda D v of the block diagonal D,
+    p(l) = T_2((theta - l)/delta) / T_2(theta/delta) on [rho/10, rho]."""
+    m = hex_mesh(2)
+    sys_ = assemble(m, paper_element(1), np.ones(m.n_cells), keep_local=True)
+    A = solvers.regularized(sys_, 0.3)
+    H = block_amg.setup(A, 3, block_amg.flux_modes(sys_), coarse_max=1000, smoother="chebyshev")
+    lv = H.levels[0]
+    D = np.linalg.inv(lv.Dinv.toarray())
+    import scipy.linalg as sla
+    lam, V = sla.eigh(A.toarray(), D)
+    hi, lo = lv.rho, lv.rho / 10.0
+    th, de = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    assert lam.max() < 1.5 * hi
+    for i in range(0, lam.size, 7):
+        v = V[:, i]
+        x = block_amg.chebyshev(lv, A @ v, np.zeros(v.size), 2)
+        t = (th - lam[i]) / de
+        p = (2 * t * t - 1) / (2 * (th / de) ** 2 - 1)
+        np.testing.assert_allclose(v - x, p * v, atol=1e-11 * np.abs(v).max())
+
+
+def test_block_chebyshev_cycle_spd_on_areg():
+    m = voronoi_mesh(30, seed=4, lloyd=3)
+    sys_ = assemble(m, paper_element(1), np.ones(m.n_cells), keep_local=True)
+    A = solvers.regularized(sys_, solvers.mesh_size(sys_) ** 2)
+    H = block_amg.setup(A, 3, block_amg.flux_modes(sys_), coarse_max=8, smoother="chebyshev")
+    assert len(H.levels) >= 2 and H.levels[1].bs == 3
+    n = A.shape[0]
+    C = np.column_stack([block_amg.vcycle(H, e) for e in np.eye(n)])
+    np.testing.assert_allclose(C, C.T, atol=1e-12 * np.abs(C).max())
+    assert np.linalg.eigvalsh(0.5 * (C + C.T)).min() > 0.0
+
+
+@pytest.mark.parametrize("case", ["hex-flux", "voronoi-dirichlet"])
+def test_block_reg_with_block_amg_reaches_direct_solution(case):
+    prob = fields.paper_polynomial_problem()
+    if case == "hex-flux":
+        m = hex_mesh(3, bc=2)
+        kw = dict(f=prob.f, flux=prob.u)
+    else:
+        m = voronoi_mesh(40, seed=3, lloyd=3)
+        kw = dict(f=prob.f, gD=prob.gD)
+    sys_ = assemble(m, paper_element(1), np.ones(m.n_cells), keep_local=True, **kw)
+    ud, pd = solvers.solve_direct(sys_)
+    u, p, res = solvers.solve_krylov(sys_, "fgmres", "reg", rtol=1e-11, restart=30, maxit=3000,
+                                     reg_smoother="block-chebyshev")
+    assert res.converged
+    np.testing.assert_allclose(u, ud, atol=1e-8 * np.abs(ud).max())
+    np.testing.assert_allclose(p, pd, atol=1e-8 * np.abs(pd).max())
+
+
+@pytest.mark.slow
+def test_block_amg_on_areg_cuts_block_reg_counts_on_cvt():
+    """k = 1 on 125 CVT cells: Block-Reg FGMRES(30) to 1e-6 with the point-
+    block AMG of A_reg takes under half the iterations of the scalar
+    Chebyshev cycle (41 against 162 when written)."""
+    m = voronoi_mesh(125, seed=7, lloyd=10)
+    prob = fields.paper_polynomial_problem()
+    sys_ = assemble(m, paper_element(1), np.ones(m.n_cells), f=prob.f, gD=prob.gD, keep_local=True)
+    _, _, rs = solvers.solve_krylov(sys_, "fgmres", "reg", rtol=1e-6, restart=30, maxit=2000)
+    _, _, rb = solvers.solve_krylov(sys_, "fgmres", "reg", rtol=1e-6, restart=30, maxit=2000,
+                                    reg_smoother="block-chebyshev")
+    assert rb.converged and rb.iters <= 50
+    assert 2 * rb.iters < rs.iters, (rb.iters, rs.iters)
