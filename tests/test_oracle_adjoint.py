@@ -5,7 +5,7 @@ import numpy as np
 
 from oracle import E0, paper_element
 from oracle.adjoint import gradient_logK, solve_u_p
-from synth import fields, prism_mesh
+from synth import fields, hex_mesh, prism_mesh
 from synth.voronoi import voronoi_mesh
 
 
@@ -16,7 +16,8 @@ def _check(mesh, spec, seed, flux_term=False):
     rng = np.random.default_rng(seed)
     theta = rng.standard_normal(mesh.n_cells)
     prob = fields.sine_problem()
-    ptarget = rng.standard_normal(mesh.n_cells) * 0.1
+    u0, p0 = solve_u_p(mesh, spec, theta, prob.f, prob.gD)
+    ptarget = rng.standard_normal(p0.size) * 0.1
     w = None
 
     def loss(u, p):
@@ -26,8 +27,7 @@ def _check(mesh, spec, seed, flux_term=False):
     def dL(u, p):
         return (w.copy() if flux_term else np.zeros_like(u)), p - ptarget
 
-    n_u = solve_u_p(mesh, spec, theta, prob.f, prob.gD)[0].size
-    w = rng.standard_normal(n_u) * 0.05
+    w = rng.standard_normal(u0.size) * 0.05
 
     u, p, g = gradient_logK(mesh, spec, theta, prob.f, prob.gD, dL)
     eps = 1e-6
@@ -51,3 +51,9 @@ def test_adjoint_K1_prism():
 def test_adjoint_flux_and_pressure_misfit():
     _check(prism_mesh(2), paper_element(1), 3, flux_term=True)
     _check(voronoi_mesh(25, seed=6, lloyd=2), E0, 4, flux_term=True)
+
+
+def test_adjoint_K2_hex():
+    """The paper's k = 2 element (four pressure moments per cell): the same
+    contraction with the cell's k = 2 mass matrix."""
+    _check(hex_mesh(2), paper_element(2), 5, flux_term=True)
