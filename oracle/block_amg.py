@@ -52,10 +52,12 @@ Exact rules:
   Or (smoother='chebyshev') two Chebyshev steps of block Jacobi on
   [rho/10, rho] before and after the coarse correction.
 
-The same construction serves the regularised flux block A_reg of Block-Reg
-at the paper's k = 1, whose face moments (3 per face) and interior moments
-(3 per cell) form 3 x 3 blocks: near-null space the DOFs of the three
-constant vector fields (``flux_modes``), Chebyshev smoothing.
+The same construction serves the regularised flux block A_reg of Block-Reg:
+at the paper's k = 1 directly, whose face moments (3 per face) and interior
+moments (3 per cell) form 3 x 3 blocks, and at any k >= 1 on the face system
+left after eliminating the interior DOFs cell by cell (``CondensedCycle``),
+with the DOFs of the three constant vector fields as near-null space
+(``flux_modes``) and Chebyshev smoothing.
 """
 
 from __future__ import annotations
@@ -353,3 +355,49 @@ def flux_modes(sys) -> np.ndarray:
             e[j] = 1.0
             out[sys.dofmap[c], j] = interpolate(cell, sys.spec, lambda X, e=e: np.tile(e, (X.shape[0], 1)))
     return out
+
+
+class CondensedCycle:
+    """Approximate inverse of the regularised flux block A_reg by exact
+    elimination of the interior DOFs cell by cell (their block of A_reg is
+    block diagonal over the cells: an interior DOF couples only to its own
+    cell) and one V-cycle of this module's point-block AMG on the remaining
+    face system S_f = A_ff - A_fi A_ii^-1 A_if, whose bs x bs blocks are the
+    nfd face moments of a face:
+
+        r_f' = r_f - A_fi A_ii^-1 r_i,  x_f = V(S_f) r_f',
+        x_i  = A_ii^-1 (r_i - A_if x_f).
+
+    Near-null space of S_f: the face DOFs of the three constant fields
+    (``flux_modes``); smoothing: block Chebyshev.  Symmetric positive
+    definite whenever the V-cycle is (a block LDL^T form with the exact
+    interior blocks)."""
+
+    def __init__(self, sys, A_reg: sp.csr_matrix):
+        spec = sys.spec
+        if spec.nfd < 3:
+            raise NotImplementedError("the face blocks must hold the three constant-field modes (nfd >= 3)")
+        nf = sys.n_u - spec.nid * sys.vol.size          # face DOFs come first
+        A = A_reg.tocsr()
+        F = np.arange(nf)
+        I = np.arange(nf, sys.n_u)
+        self.nf = nf
+        self.Afi = A[F][:, I].tocsr()
+        if I.size:
+            nid = spec.nid
+            Aii = A[I][:, I].tocsr()
+            blocks = [sp.csr_matrix(np.linalg.inv(Aii[nid * c:nid * (c + 1), nid * c:nid * (c + 1)].toarray()))
+                      for c in range(I.size // nid)]
+            self.Aii_inv = sp.block_diag(blocks, format="csr")
+            self.Sf = (A[F][:, F] - self.Afi @ self.Aii_inv @ self.Afi.T).tocsr()
+        else:
+            self.Aii_inv = None
+            self.Sf = A
+        self.H = setup(self.Sf, spec.nfd, flux_modes(sys)[:nf], smoother="chebyshev")
+
+    def __call__(self, r: np.ndarray) -> np.ndarray:
+        rf, ri = r[:self.nf], r[self.nf:]
+        if self.Aii_inv is None:
+            return vcycle(self.H, rf)
+        xf = vcycle(self.H, rf - self.Afi @ (self.Aii_inv @ ri))
+        return np.concatenate([xf, self.Aii_inv @ (ri - self.Afi.T @ xf)])

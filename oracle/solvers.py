@@ -125,7 +125,9 @@ class BlockPreconditioner:
     oracle/schwarz.py on the finest level, which needs the mesh; with
     reg_smoother='block-chebyshev' (k = 1) the point-block AMG of
     oracle/block_amg.py on 3 x 3 blocks with the constant fields as
-    near-null space) for the flux
+    near-null space; with reg_smoother='condensed-block' the interior DOFs
+    eliminated cell by cell and that AMG on the face system,
+    block_amg.CondensedCycle) for the flux
     block and W^{-1} = I / gamma for the pressure block; gamma defaults to
     h^2, h the mean cell diameter (the paper's choice)."""
 
@@ -150,6 +152,9 @@ class BlockPreconditioner:
                 Hb = block_amg.setup(self.A_reg, 3, block_amg.flux_modes(sys), smoother="chebyshev")
                 self.cycle_reg = lambda r: block_amg.vcycle(Hb, r)
                 self.H_reg = Hb
+            elif reg_smoother == "condensed-block":
+                from . import block_amg
+                self.cycle_reg = block_amg.CondensedCycle(sys, self.A_reg)
             elif reg_smoother == "edge-schwarz":
                 from . import schwarz
                 if mesh is None:
