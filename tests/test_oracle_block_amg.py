@@ -1,6 +1,9 @@
-"""Pins for oracle/block_amg.py: smoothed aggregation on the cell blocks of
-the k = 2 Schur block (four P1 pressure moments per cell, eq. presMom),
-with the moments of 1, x, y, z as near-null space."""
+"""Pins for oracle/block_amg.py: smoothed aggregation on point blocks --
+the cell blocks of the k = 2 Schur block (four P1 pressure moments per
+cell, eq. presMom, near-null space the moments of 1, x, y, z), and the face
+and cell blocks of Block-Reg's regularised flux block A_reg (near-null
+space the DOFs of the constant fields), directly at k = 1 and behind the
+cell-wise condensation of the interior DOFs at k = 1 and 2."""
 
 import numpy as np
 import pytest
