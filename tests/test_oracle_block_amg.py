@@ -356,3 +356,22 @@ def test_condensed_block_reg_on_cvt_k2():
                                     reg_smoother="edge-schwarz", mesh=m)
     assert rc.converged and rc.iters < 100, rc.iters
     assert 2 * rc.iters < re.iters, (rc.iters, re.iters)
+
+
+def test_cholesky_qr_gives_the_same_factor():
+    """The thin QR with R_jj > 0 is unique, so R = chol(B^T B)^T and
+    Q = B R^-1 (Cholesky-QR, the form a thread per aggregate computes)
+    agree with the Householder factors on every aggregate of a k = 2
+    Schur block."""
+    m = voronoi_mesh(60, seed=4, lloyd=3)
+    sys_, S = _k2_schur(m, seed=2)
+    B = block_amg.pressure_modes(sys_)
+    ptr, idx = block_amg.block_strength(S, 4, 0.08)
+    agg, nc = amg.aggregate(m.n_cells, ptr, idx)
+    for a in range(nc):
+        members = np.nonzero(agg == a)[0]
+        X = B[(members[:, None] * 4 + np.arange(4)[None, :]).ravel()]
+        Q, R = block_amg.qr_positive(X)
+        Rc = np.linalg.cholesky(X.T @ X).T
+        np.testing.assert_allclose(Rc, R, rtol=0, atol=1e-9 * np.abs(R).max())
+        np.testing.assert_allclose(X @ np.linalg.inv(Rc), Q, rtol=0, atol=1e-8)
