@@ -289,10 +289,10 @@ vem_status vem_get_geometry(vem_handle *h, double *face_area, double *face_centr
                             double *face_normal, double *face_diam, double *cell_volume,
                             double *cell_centroid, double *cell_diam);
 
-/* Element matrices only (every element; the only assembly step of K2):
- * the geometry-only local matrices of every congruence class of cells, on
- * the device; vem_local_time reports the element kernel's time (ms, CUDA
- * events) and the number of classes evaluated. */
+/* Element matrices only (every element), without the scatter into the
+ * global matrices: the geometry-only local matrices of every congruence
+ * class of cells, on the device; vem_local_time reports the element
+ * kernel's time (ms, CUDA events) and the number of classes evaluated. */
 vem_status vem_assemble_local(vem_handle *h);
 vem_status vem_local_time(const vem_handle *h, double *element_ms, int64_t *n_classes);
 
