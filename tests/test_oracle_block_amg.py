@@ -375,3 +375,16 @@ def test_cholesky_qr_gives_the_same_factor():
         Rc = np.linalg.cholesky(X.T @ X).T
         np.testing.assert_allclose(Rc, R, rtol=0, atol=1e-9 * np.abs(R).max())
         np.testing.assert_allclose(X @ np.linalg.inv(Rc), Q, rtol=0, atol=1e-8)
+
+
+def test_block_reg_condensed_with_minres():
+    """The condensed cycle is symmetric positive definite, so Block-Reg with
+    it also preconditions MINRES (k = 2, pressure data)."""
+    prob = fields.paper_polynomial_problem()
+    m = hex_mesh(3)
+    sys_ = assemble(m, K2, np.ones(m.n_cells), f=prob.f, gD=prob.gD, keep_local=True)
+    ud, pd = solvers.solve_direct(sys_)
+    u, p, res = solvers.solve_krylov(sys_, "minres", "reg", rtol=1e-11, maxit=3000, reg_smoother="condensed-block")
+    assert res.converged
+    np.testing.assert_allclose(u, ud, atol=1e-8 * np.abs(ud).max())
+    np.testing.assert_allclose(p, pd, atol=1e-8 * np.abs(pd).max())
