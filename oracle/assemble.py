@@ -33,7 +33,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from .element import ElementSpec, local_system
-from .polyhedron import all_faces, cell_geometry
+from .polyhedron import all_faces, cell_geometry, face_geometry
 
 
 @dataclass
@@ -114,14 +114,51 @@ def cell_dofmap(mesh, c: int, spec: ElementSpec):
     return np.array(idx, dtype=np.int64)
 
 
+def _cell_items(mesh, spec, nu, c, faces, f, gD, nq, bface_rule):
+    """Geometry, local system and DOF map of cell c."""
+    cell = cell_geometry(mesh, c, faces, nq)
+    loc = local_system(cell, spec, float(nu), f=f, gD=gD, bface_rule=bface_rule)
+    return cell, loc, cell_dofmap(mesh, c, spec)
+
+
+def _cell_chunk(mesh, spec, nu_chunk, c0, c1, f, gD, nq, bface_rule):
+    """_cell_items for the cells c0 .. c1 - 1 (in a worker process): the
+    geometry of the faces these cells use is computed here, face by face as
+    in all_faces, so every value is the one the sequential loop computes."""
+    faces = {}
+    for c in range(c0, c1):
+        for fid in mesh.cell_faces(c):
+            if int(fid) not in faces:
+                faces[int(fid)] = face_geometry(mesh, int(fid), nq)
+    return [_cell_items(mesh, spec, nu_chunk[c - c0], c, faces, f, gD, nq, bface_rule) for c in range(c0, c1)]
+
+
+def _parallel_items(mesh, spec, nu_cell, f, gD, nq, bface_rule, processes):
+    """Per-cell items in cell order from a pool of spawned processes (spawned,
+    not forked, so a process that already uses a GPU can start it)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    nc = mesh.n_cells
+    nchunk = min(nc, 8 * processes)
+    bounds = [nc * i // nchunk for i in range(nchunk + 1)]
+    with ProcessPoolExecutor(max_workers=processes, mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(_cell_chunk, mesh, spec, nu_cell[a:b], a, b, f, gD, nq, bface_rule)
+                for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+        for fu in futs:
+            yield from fu.result()
+
+
 def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False, nq=5, flux=None,
-             bface_rule="dunavant4") -> System:
+             bface_rule="dunavant4", processes: int = 1) -> System:
     """Assemble M, B, g, F.  nu_cell = 1/K per cell (eq. bilin_form, nu = K^-1).
     flux: the vector field u (callable (N,3) -> (N,3)) whose normal component
     is prescribed on faces with flag 2.  bface_rule: the fan rule of the
-    Dirichlet term ('dunavant4', the library's, or 'radon5')."""
+    Dirichlet term ('dunavant4', the library's, or 'radon5').
+    processes > 1 computes the per-cell local systems in that many spawned
+    worker processes (f, gD must then be picklable, e.g. module-level
+    functions); the global sums run in cell order either way, so the result
+    is the same bit for bit."""
     nu_cell = np.asarray(nu_cell, dtype=np.float64)
-    faces = all_faces(mesh, nq)
     n_u = spec.nfd * mesh.n_faces + spec.nid * mesh.n_cells
     n_p = spec.nq * mesh.n_cells
     rows, cols, vals = [], [], []
@@ -131,12 +168,16 @@ def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False
     cells, locs, maps = [], [], []
     vol = np.zeros(mesh.n_cells)
     diam = np.zeros(mesh.n_cells)
-    for c in range(mesh.n_cells):
-        cell = cell_geometry(mesh, c, faces, nq)
+    if processes > 1 and mesh.n_cells > 1:
+        items = _parallel_items(mesh, spec, nu_cell, f, gD, nq, bface_rule, processes)
+        fl = np.nonzero(mesh.face_bc == 2)[0]
+        faces = {int(fid): face_geometry(mesh, int(fid), nq) for fid in fl}
+    else:
+        faces = all_faces(mesh, nq)
+        items = (_cell_items(mesh, spec, nu_cell[c], c, faces, f, gD, nq, bface_rule) for c in range(mesh.n_cells))
+    for c, (cell, loc, dm) in enumerate(items):
         vol[c] = cell.volume
         diam[c] = cell.diameter
-        loc = local_system(cell, spec, float(nu_cell[c]), f=f, gD=gD, bface_rule=bface_rule)
-        dm = cell_dofmap(mesh, c, spec)
         pm = spec.nq * c + np.arange(spec.nq)
         rows.append(np.repeat(dm, dm.size))
         cols.append(np.tile(dm, dm.size))

@@ -41,7 +41,7 @@ import numpy as np
 
 from .monomials import (mono2, mono3, dim_P2, MG_plus, decompose, eval_mono2,
                         eval_mono3, eval_grad_mono3, mI_cross)
-from .quadrature import dunavant4, radon5
+from .quadrature import cross3, dunavant4, radon5
 
 
 @dataclass(frozen=True)
@@ -222,7 +222,7 @@ def load_face_points(F, rule="dunavant4"):
     for i in range(m):
         A, B = V[i], V[(i + 1) % m]
         p, w = tri(F.centroid, A, B)
-        s = np.sign(np.dot(np.cross(A - F.centroid, B - F.centroid), F.normal))
+        s = np.sign(np.dot(cross3(A - F.centroid, B - F.centroid), F.normal))
         pts.append(p)
         wts.append(w * s)
     return np.concatenate(pts), np.concatenate(wts)

@@ -23,7 +23,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .quadrature import triangle_rule, tet_rule
+from .quadrature import cross3, triangle_rule, tet_rule
 
 
 @dataclass
@@ -72,19 +72,19 @@ def face_geometry(mesh, f: int, nq: int = 5) -> Face:
     den = 0.0
     for i in range(m):
         A, B = V[i], V[(i + 1) % m]
-        sa = 0.5 * np.dot(np.cross(A - xbar, B - xbar), n)
+        sa = 0.5 * np.dot(cross3(A - xbar, B - xbar), n)
         num += sa * (xbar + A + B) / 3.0
         den += sa
     xf = num / den
     diam = max(np.linalg.norm(V[i] - V[j]) for i in range(m) for j in range(i + 1, m))
     t1 = (V[1] - V[0]) / np.linalg.norm(V[1] - V[0])
-    t2 = np.cross(n, t1)
+    t2 = cross3(n, t1)
     # exact-integration points: fan (x_f, v_i, v_{i+1})
     pts, wts = [], []
     for i in range(m):
         A, B = V[i], V[(i + 1) % m]
         p, w = triangle_rule(xf, A, B, nq)
-        s = np.sign(np.dot(np.cross(A - xf, B - xf), n))
+        s = np.sign(np.dot(cross3(A - xf, B - xf), n))
         pts.append(p)
         wts.append(w * s)
     return Face(gid=f, verts=V, normal=n, area=den, centroid=xf, diameter=diam,

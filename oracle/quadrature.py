@@ -22,33 +22,47 @@ definitions and independently in the CUDA library:
 
 from __future__ import annotations
 
+from functools import lru_cache
+
 import numpy as np
 from numpy.polynomial.legendre import leggauss
 
 
+def cross3(a, b):
+    """Cross product of two 3-vectors (the componentwise products and
+    differences of numpy.cross, without its general-shape overhead)."""
+    return np.array([a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]])
+
+
+@lru_cache(maxsize=None)
 def gauss01(n: int):
+    """n-point Gauss-Legendre rule mapped to [0, 1] (memoised; read-only)."""
     x, w = leggauss(n)
-    return 0.5 * (x + 1.0), 0.5 * w
+    x, w = 0.5 * (x + 1.0), 0.5 * w
+    x.flags.writeable = False
+    w.flags.writeable = False
+    return x, w
 
 
-def triangle_rule(A, B, C, n: int = 5):
-    """Points (N,3) and weights (N,) on triangle ABC, |weights| summing to the area."""
+@lru_cache(maxsize=None)
+def _ref_triangle(n: int):
+    """Collapsed Gauss points (xi, eta) and weights on the unit right
+    triangle {xi, eta >= 0, xi + eta <= 1}, weights summing to 1/2."""
     s, ws = gauss01(n)
     S, T = np.meshgrid(s, s, indexing="ij")
     WS, WT = np.meshgrid(ws, ws, indexing="ij")
     xi = S.ravel()
     eta = (T * (1.0 - S)).ravel()
     w = (WS * WT * (1.0 - S)).ravel()
-    A = np.asarray(A, float)
-    B = np.asarray(B, float)
-    C = np.asarray(C, float)
-    area2 = np.linalg.norm(np.cross(B - A, C - A))
-    pts = A[None, :] + xi[:, None] * (B - A)[None, :] + eta[:, None] * (C - A)[None, :]
-    return pts, w * area2
+    for a in (xi, eta, w):
+        a.flags.writeable = False
+    return xi, eta, w
 
 
-def tet_rule(A, B, C, D, n: int = 5):
-    """Points and *signed* weights on tetrahedron ABCD (sign of det[B-A, C-A, D-A])."""
+@lru_cache(maxsize=None)
+def _ref_tet(n: int):
+    """Collapsed Gauss points (xi, eta, zeta) as an (N, 3) array and weights
+    on the unit tetrahedron, weights summing to 1/6."""
     s, ws = gauss01(n)
     S, T, R = np.meshgrid(s, s, s, indexing="ij")
     WS, WT, WR = np.meshgrid(ws, ws, ws, indexing="ij")
@@ -56,10 +70,30 @@ def tet_rule(A, B, C, D, n: int = 5):
     eta = (T * (1.0 - S)).ravel()
     zeta = (R * (1.0 - S) * (1.0 - T)).ravel()
     w = (WS * WT * WR * (1.0 - S) ** 2 * (1.0 - T)).ravel()
+    X = np.stack([xi, eta, zeta], 1)
+    X.flags.writeable = False
+    w.flags.writeable = False
+    return X, w
+
+
+def triangle_rule(A, B, C, n: int = 5):
+    """Points (N,3) and weights (N,) on triangle ABC, |weights| summing to the area."""
+    xi, eta, w = _ref_triangle(n)
+    A = np.asarray(A, float)
+    B = np.asarray(B, float)
+    C = np.asarray(C, float)
+    area2 = np.linalg.norm(cross3(B - A, C - A))
+    pts = A[None, :] + xi[:, None] * (B - A)[None, :] + eta[:, None] * (C - A)[None, :]
+    return pts, w * area2
+
+
+def tet_rule(A, B, C, D, n: int = 5):
+    """Points and *signed* weights on tetrahedron ABCD (sign of det[B-A, C-A, D-A])."""
+    X, w = _ref_tet(n)
     A = np.asarray(A, float)
     J = np.stack([np.asarray(B, float) - A, np.asarray(C, float) - A, np.asarray(D, float) - A], 1)
     det = np.linalg.det(J)
-    pts = A[None, :] + np.stack([xi, eta, zeta], 1) @ J.T
+    pts = A[None, :] + X @ J.T
     return pts, w * det
 
 
@@ -74,7 +108,7 @@ def dunavant4(A, B, C):
     A = np.asarray(A, float)
     B = np.asarray(B, float)
     C = np.asarray(C, float)
-    area = 0.5 * np.linalg.norm(np.cross(B - A, C - A))
+    area = 0.5 * np.linalg.norm(cross3(B - A, C - A))
     bary = []
     wts = []
     for a, w in zip(_DUN4_A, _DUN4_W):
@@ -95,7 +129,7 @@ def radon5(A, B, C):
     A = np.asarray(A, float)
     B = np.asarray(B, float)
     C = np.asarray(C, float)
-    area = 0.5 * np.linalg.norm(np.cross(B - A, C - A))
+    area = 0.5 * np.linalg.norm(cross3(B - A, C - A))
     r15 = np.sqrt(15.0)
     bary = [(1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0)]
     wts = [9.0 / 40.0]
