@@ -341,8 +341,13 @@ vem_status vem_apply_device(vem_handle *h, const double *x_dev, double *y_dev);
  * stream capture.  Each call overwrites every partial it reads, so nothing
  * needs clearing, but all calls share the one array: calls that overlap on
  * the GPU (other streams, other host threads) race and must be ordered by
- * the caller.  No cudaMalloc, cudaFree or allocating library routine is
- * called. */
+ * the caller.  The array's address is kept per device for the life of the
+ * process: do not call this entry point again on a device after
+ * cudaDeviceReset (or any other destruction of its primary context).  A CUDA
+ * error already pending when the call starts (from earlier, unrelated work)
+ * gives VEM_ERR_CUDA before any launch and is left pending for its owner.
+ * The matrix is read one warp per row.  No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
 vem_status vem_residual_norm_noalloc(int64_t rows, const int64_t *row_ptr, const int32_t *col,
                                      const double *val, const double *x, const double *b,
                                      double *out, void *cuda_stream);

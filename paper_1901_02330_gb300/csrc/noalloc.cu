@@ -30,8 +30,10 @@ static __device__ __align__(256) double g_scratch[2 * kMaxTiles];
 double *g_addr[kMaxDevices] = {};
 std::mutex g_mutex;
 
-// One block per tile; each thread forms whole rows of A x in column order,
-// so the partial sums do not depend on the GPU or the launch.
+// One block per tile, one warp per row: the lanes take the row's entries in
+// strides of 32 (coalesced loads of col and val) and combine them with the
+// fixed-pattern warp_sum, so the partial sums do not depend on the GPU or the
+// launch.
 __global__ void __launch_bounds__(kTileThreads) k_tiles(int64_t rows, const int64_t *__restrict__ rp,
                                                         const int32_t *__restrict__ col,
                                                         const double *__restrict__ val,
@@ -39,18 +41,18 @@ __global__ void __launch_bounds__(kTileThreads) k_tiles(int64_t rows, const int6
                                                         const double *__restrict__ b, double *part) {
   const int64_t lo = (int64_t)blockIdx.x * kTileRows;
   const int64_t hi = lo + kTileRows < rows ? lo + kTileRows : rows;
-  double r2 = 0.0, b2 = 0.0;
-  for (int64_t r = lo + threadIdx.x; r < hi; r += kTileThreads) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  double r2 = 0.0, b2 = 0.0;   // meaningful in lane 0
+  for (int64_t r = lo + w; r < hi; r += kTileThreads / 32) {
     double ax = 0.0;
-    for (int64_t p = rp[r]; p < rp[r + 1]; ++p) ax += val[p] * x[col[p]];
+    const int64_t p1 = rp[r + 1];
+    for (int64_t p = rp[r] + l; p < p1; p += 32) ax += val[p] * x[col[p]];
+    ax = warp_sum(ax);
     const double ri = b[r] - ax;
     r2 += ri * ri;
     b2 += b[r] * b[r];
   }
   __shared__ double s_r[kTileThreads / 32], s_b[kTileThreads / 32];
-  r2 = warp_sum(r2);
-  b2 = warp_sum(b2);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) {
     s_r[w] = r2;
     s_b[w] = b2;
@@ -103,6 +105,10 @@ extern "C" vem_status vem_residual_norm_noalloc(int64_t rows, const int64_t *row
     }
     scratch = g_addr[dev];
   }
+  // an error left pending by earlier, unrelated work is reported here and
+  // left in place for its owner (not cleared), so the launch check below
+  // sees only this call's launches
+  if (cudaPeekAtLastError() != cudaSuccess) return VEM_ERR_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   const int ntiles = (int)((rows + kTileRows - 1) / kTileRows);
   count_launch();

@@ -139,8 +139,41 @@ def residual_norm_noalloc(row_ptr, col, val, x, b, out, stream: int = 0) -> None
     """vem_residual_norm_noalloc on device tensors: out[0] = ||b - A x||,
     out[1] = ||b||, out[2] = their ratio.  Allocates nothing on the device
     (for callers whose device memory is owned by another allocator); the
-    result is ready when the stream reaches it."""
-    rows = int(row_ptr.shape[0]) - 1
+    result is ready when the stream reaches it.
+
+    The library reads the buffers through raw device pointers, so every
+    argument is checked here first: contiguous CUDA tensors on the current
+    device, row_ptr int64 with rows + 1 entries, col int32, val / x / b / out
+    float64, val and col holding row_ptr[-1] entries, x and b rows entries
+    (the matrix is square) and out at least 3.  Column ids must lie in
+    [0, rows); they are not scanned here (that would need device memory)."""
+    import torch
+    args = dict(row_ptr=row_ptr, col=col, val=val, x=x, b=b, out=out)
+    want = dict(row_ptr=torch.int64, col=torch.int32, val=torch.float64, x=torch.float64, b=torch.float64,
+                out=torch.float64)
+    for k, t in args.items():
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{k}: a torch CUDA tensor is required, got {type(t).__name__}")
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else -1
+    for k, t in args.items():
+        if t.device.type != "cuda" or t.device.index != dev:
+            raise ValueError(f"{k}: must be on the current CUDA device cuda:{dev}, is on {t.device}")
+        if t.dtype != want[k]:
+            raise TypeError(f"{k}: dtype {want[k]} required, got {t.dtype}")
+        if not t.is_contiguous() or t.dim() != 1:
+            raise ValueError(f"{k}: a contiguous 1-D tensor is required")
+    rows = int(row_ptr.numel()) - 1
+    if rows < 1:
+        raise ValueError("row_ptr: needs at least 2 entries")
+    nnz = int(row_ptr[-1].item())
+    if int(row_ptr[0].item()) != 0 or nnz < 0:
+        raise ValueError("row_ptr: must start at 0 and end at the entry count")
+    if col.numel() < nnz or val.numel() < nnz:
+        raise ValueError(f"col / val: {nnz} entries required, have {col.numel()} / {val.numel()}")
+    if x.numel() != rows or b.numel() != rows:
+        raise ValueError(f"x / b: {rows} entries required, have {x.numel()} / {b.numel()}")
+    if out.numel() < 3:
+        raise ValueError("out: at least 3 entries required")
     st = lib().vem_residual_norm_noalloc(rows, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(x), _ptr(b),
                                          _ptr(out), C.c_void_p(stream or None))
     if st != VEM_OK:
