@@ -129,6 +129,7 @@ enum { VEM_PREC_BLOCK_DIAG = 0, VEM_PREC_BLOCK_TRI = 1, VEM_PREC_BLOCK_REG = 2 }
  * vem_solve_batched gives VEM_ERR_UNSUPPORTED with it. */
 enum { VEM_INNER_PCG = 0, VEM_INNER_AMG = 1 };
 enum { VEM_PRECISION_FP64 = 0, VEM_PRECISION_MIXED = 1 };
+enum { VEM_SMOOTH_JACOBI = 0, VEM_SMOOTH_CHEBYSHEV = 1 };
 
 typedef struct {
   int element;        /* VEM_ELEMENT_*                                      */
@@ -154,6 +155,12 @@ typedef struct {
                       /* share one evaluation of their geometry-only local  */
                       /* matrices, scaled by nu_P; 0: every cell evaluated. */
   double reg_gamma;   /* BLOCK_REG: gamma > 0, or 0 for h^2 (default 0)     */
+  int inner_smoother; /* VEM_SMOOTH_*: smoother of the AMG V-cycle of S     */
+                      /* (inner = AMG): one damped-Jacobi step before and   */
+                      /* after the coarse correction (default), or two      */
+                      /* Chebyshev steps of the Jacobi iteration on         */
+                      /* [rho/10, rho] (rho the Gershgorin bound of         */
+                      /* rho(D^-1 S); the Block-Reg cycle's smoother)       */
 } vem_options;
 
 typedef struct {
@@ -181,11 +188,16 @@ typedef struct {
                              /* Schur SpMV chosen by the autotuner          */
   double reg_gamma;          /* BLOCK_REG: the gamma used (0 otherwise)     */
   int64_t nnz_reg;           /* BLOCK_REG: nonzeros of A_reg (0 otherwise)  */
+  double t_vc_resid_ms;      /* inner AMG: the finest-level residual launch */
+  int64_t n_vc_resid;        /* (r = b - S x) of the first, eagerly launched */
+  double t_vc_post_ms;       /* V-cycle of every inner solve, and its post-  */
+  int64_t n_vc_post;         /* smoothing launch: summed times (CUDA events) */
+                             /* and counts                                  */
 } vem_stats;
 
 /* Fill *opt with the defaults: E0, FGMRES(30), block-diagonal, Jacobi-PCG
  * inner solve to 1e-12 (at most 2000 iterations), rtol 1e-12, maxit 2000,
- * FP64, host I/O, reuse on. */
+ * FP64, host I/O, reuse on, damped-Jacobi smoothing in the AMG of S. */
 vem_status vem_default_options(vem_options *opt);
 
 /* Create a solver for a mesh: copies the mesh to the device, computes the
@@ -236,6 +248,13 @@ vem_status vem_set_source(vem_handle *h, const double *f_qp, const double *gD_qp
 
 /* Same as vem_set_coefficient / vem_set_source with DEVICE arrays. */
 vem_status vem_set_coefficient_device(vem_handle *h, const double *K_cell_dev);
+
+/* The coefficient as theta_P = log K_P per cell (DEVICE array [n_cells]):
+ * the parameter of the adjoint gradient (vem_adjoint returns dL/dtheta_P).
+ * The library forms nu_P = exp(-theta_P) = 1/K_P (Sec. 3, nu = K^-1) on the
+ * device.  VEM_ERR_NONFINITE (the previous coefficient kept) if a theta is
+ * not finite or exp(-theta) over- or underflows.  Invalidates the assembly. */
+vem_status vem_set_log_coefficient_device(vem_handle *h, const double *logK_cell_dev);
 vem_status vem_set_source_device(vem_handle *h, const double *f_qp_dev, const double *gD_qp_dev);
 
 /* Assemble: element-batched local matrices M_P, B_P and loads (Sec. 4.3),

@@ -1,6 +1,6 @@
 """torch.autograd binding: (u, p) = solve(log K) with a hand-written backward.
 
-The forward calls vem_set_coefficient_device + vem_solve; the backward calls
+The forward calls vem_set_log_coefficient_device + vem_solve; the backward calls
 vem_adjoint, which solves the adjoint saddle-point system and contracts it
 with dM/dlog K per cell on the GPU.  Argument marshalling only.
 """
@@ -20,7 +20,9 @@ class VemSolve(torch.autograd.Function):
     def forward(ctx, logK, solver):
         if not solver.options.device_io:
             raise ValueError("the solver must be created with device_io=1")
-        solver.set_coefficient(torch.exp(logK).contiguous())
+        if logK.dtype != torch.float64 or not logK.is_cuda:
+            raise TypeError("logK must be a CUDA float64 tensor")
+        solver.set_log_coefficient(logK.detach().contiguous())
         n_u, n_p = solver.sizes()
         u = torch.empty(n_u, dtype=torch.float64, device=logK.device)
         p = torch.empty(n_p, dtype=torch.float64, device=logK.device)

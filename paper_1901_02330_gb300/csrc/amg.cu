@@ -145,6 +145,12 @@ struct AmgState {
   int32_t *tcol = nullptr;  size_t c_tcol = 0;    //   and the scratch rows
   double *tval = nullptr;   size_t c_tval = 0;
   double t_setup_ms = 0.0;
+  cudaEvent_t tev[4] = {};  // level-0 residual and post-smoothing launches of a timed cycle
+  bool timing = false, timed = false;
+  ~AmgState() {
+    for (cudaEvent_t &e : tev)
+      if (e) cudaEventDestroy(e);
+  }
 };
 
 template <class T>
@@ -1458,6 +1464,32 @@ void amg_invalidate(AmgState *S) {
 }
 double amg_setup_ms(const AmgState *S) { return S ? S->t_setup_ms : 0.0; }
 int amg_levels(const AmgState *S) { return amg_valid(S) ? S->nlev : 0; }
+int amg_smoother(const AmgState *S) { return S ? S->smoother : -1; }
+
+void amg_time_next_cycle(AmgState *S) {
+  if (!S) return;
+  for (cudaEvent_t &e : S->tev)
+    if (!e && cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      e = nullptr;
+      return;
+    }
+  S->timing = true;
+}
+
+void amg_collect_timing(vem_handle *h, AmgState *S) {
+  if (!S || !S->timed) return;
+  S->timed = false;
+  float a = 0.f, b = 0.f;
+  if (cudaEventElapsedTime(&a, S->tev[0], S->tev[1]) == cudaSuccess &&
+      cudaEventElapsedTime(&b, S->tev[2], S->tev[3]) == cudaSuccess) {
+    h->t_vc_resid_ms += a;
+    h->n_vc_resid += 1;
+    h->t_vc_post_ms += b;
+    h->n_vc_post += 1;
+  }
+  cudaGetLastError();
+}
 void amg_free(AmgState *&S) {
   delete S;   // device buffers are in the handle's allocation list
   S = nullptr;
@@ -1525,6 +1557,11 @@ static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const do
   T *xa = L.vx<T>(0), *r = L.vx<T>(3);
   T *cb = C.vx<T>(2), *cx = C.vx<T>(1);
   const bool cheb = S->smoother == kSmoothChebyshev;
+  // events around the level-0 residual and post-smoothing launches of a timed cycle
+  const bool tm = l == 0 && S->timing;
+  auto mark = [&](int k) {
+    if (tm) cudaEventRecord(S->tev[k], s);
+  };
   const T cc = (T)L.cheb_c;
   const T *wdc = cheb ? wdcv<T>(L) : nullptr;
   count_launch();
@@ -1533,7 +1570,9 @@ static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const do
     // second Chebyshev step from x0 = 0: xc = xa + c xa + wdc (b - A xa)
     T *xc = L.vx<T>(4);
     op_launch<kCheb>(s, S, l, (const T *)xa, b, wdc, xc, sc, (const T *)nullptr, cc);
+    mark(0);
     op_launch<kResid>(s, S, l, (const T *)xc, b, (const T *)nullptr, r, sc);    // r = b - A xc
+    mark(1);
     if (L.Rs.m.rows) sell_launch<kApply>(s, L.Rs.m, vals<T>(L.Rs), (const T *)r, (const T *)nullptr,
                                          (const T *)nullptr, cb, sc);
     else csr_launch<kApply>(s, L.R, (const T *)r, (const T *)nullptr, (const T *)nullptr, cb, sc);
@@ -1541,11 +1580,19 @@ static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const do
     if (L.Ps.m.rows) sell_launch<kAdd>(s, L.Ps.m, vals<T>(L.Ps), (const T *)cx, (const T *)nullptr,
                                        (const T *)nullptr, xc, sc);              // xc += P x_c
     else csr_launch<kAdd>(s, L.P, (const T *)cx, (const T *)nullptr, (const T *)nullptr, xc, sc);
+    mark(2);
     op_launch<kPost>(s, S, l, (const T *)xc, b, wd, xa, sc);                     // xa = xc + wd (b - A xc)
+    mark(3);
     op_launch<kCheb>(s, S, l, (const T *)xa, b, wdc, x, sc, (const T *)xc, cc);  // x = xa + c (xa - xc) + ...
+    if (tm) {
+      S->timing = false;
+      S->timed = true;
+    }
     return;
   }
+  mark(0);
   op_launch<kResid>(s, S, l, (const T *)xa, b, (const T *)nullptr, r, sc);      // r = b - A xa
+  mark(1);
   if (L.Rs.m.rows) sell_launch<kApply>(s, L.Rs.m, vals<T>(L.Rs), (const T *)r, (const T *)nullptr,
                                        (const T *)nullptr, cb, sc);
   else csr_launch<kApply>(s, L.R, (const T *)r, (const T *)nullptr, (const T *)nullptr, cb, sc);
@@ -1553,7 +1600,13 @@ static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const do
   if (L.Ps.m.rows) sell_launch<kAdd>(s, L.Ps.m, vals<T>(L.Ps), (const T *)cx, (const T *)nullptr,
                                      (const T *)nullptr, xa, sc);                // xa += P x_c
   else csr_launch<kAdd>(s, L.P, (const T *)cx, (const T *)nullptr, (const T *)nullptr, xa, sc);
+  mark(2);
   op_launch<kPost>(s, S, l, (const T *)xa, b, wd, x, sc);                        // x = xa + wd (b - A xa)
+  mark(3);
+  if (tm) {
+    S->timing = false;
+    S->timed = true;
+  }
 }
 
 void amg_vcycle(vem_handle *h, AmgState *S, const double *b, double *x, const double *sc) {

@@ -143,6 +143,8 @@ static vem_status check_options(vem_handle *h, const vem_options *o) {
     return fail(h, VEM_ERR_BAD_INPUT, "reg_gamma %g", o->reg_gamma);
   if (o->inner != VEM_INNER_PCG && o->inner != VEM_INNER_AMG)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown inner solver %d", o->inner);
+  if (o->inner_smoother != VEM_SMOOTH_JACOBI && o->inner_smoother != VEM_SMOOTH_CHEBYSHEV)
+    return fail(h, VEM_ERR_BAD_INPUT, "unknown inner smoother %d", o->inner_smoother);
   if (o->precision != VEM_PRECISION_FP64 && o->precision != VEM_PRECISION_MIXED)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown precision %d", o->precision);
   if (o->precision == VEM_PRECISION_MIXED && o->krylov != VEM_KRYLOV_FGMRES)
@@ -443,6 +445,17 @@ __global__ void k_invert_check(int64_t n, const double *K, double *nu, int *err)
   }
 }
 
+// nu = exp(-theta) = 1/K from theta = log K; a theta whose K or nu is not a
+// finite positive double raises DEVERR_NONFINITE.
+__global__ void k_nu_from_log(int64_t n, const double *theta, double *nu, int *err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = exp(-theta[i]);
+    if (!isfinite(theta[i]) || !isfinite(v) || !(v > 0.0)) atomicOr(err, DEVERR_NONFINITE);
+    nu[i] = v;
+  }
+}
+
 // Non-finite entries of a vector raise DEVERR_NONFINITE.
 __global__ void k_check_finite(int64_t n, const double *__restrict__ a, int *err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -630,10 +643,12 @@ vem_status vem_quadrature_points(vem_handle *h, int which, double *xyz_out) {
 
 // K (device) -> nu = 1/K with the checks on the device; on a bad K the old
 // nu is kept (the new values go to a scratch first).
-static vem_status set_nu_from_device(vem_handle *h, const double *K) {
+static vem_status set_nu_from_device(vem_handle *h, const double *K, bool log_k = false) {
   double *tmp = nullptr;
   VEM_TRY(dalloc_n(h, &tmp, (size_t)h->nc));
-  count_launch(); k_invert_check<<<grid_for(h->nc, 256), 256, 0, h->stream>>>(h->nc, K, tmp, h->d_err);
+  count_launch();
+  if (log_k) k_nu_from_log<<<grid_for(h->nc, 256), 256, 0, h->stream>>>(h->nc, K, tmp, h->d_err);
+  else k_invert_check<<<grid_for(h->nc, 256), 256, 0, h->stream>>>(h->nc, K, tmp, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   VEM_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   VEM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -667,6 +682,12 @@ vem_status vem_set_coefficient_device(vem_handle *h, const double *K) {
   if (!h) return VEM_ERR_BAD_INPUT;
   if (!K) return fail(h, VEM_ERR_BAD_INPUT, "K: NULL");
   return set_nu_from_device(h, K);
+}
+
+vem_status vem_set_log_coefficient_device(vem_handle *h, const double *logK) {
+  if (!h) return VEM_ERR_BAD_INPUT;
+  if (!logK) return fail(h, VEM_ERR_BAD_INPUT, "log K: NULL");
+  return set_nu_from_device(h, logK, true);
 }
 
 vem_status vem_set_source(vem_handle *h, const double *f_qp, const double *gD_qp) {
@@ -788,6 +809,8 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     h->x_zero = x0d == nullptr;
     h->t_schur_spmv_ms = 0.0;
     h->n_schur_spmv = 0;
+    h->t_vc_resid_ms = h->t_vc_post_ms = 0.0;
+    h->n_vc_resid = h->n_vc_post = 0;
     h->t_saddle_spmv_ms = 0.0;
     h->n_saddle_spmv = 0;
     const bool had_amg = amg_valid(h->amg), had_reg = amg_valid(h->amg_reg);
@@ -808,6 +831,10 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
     st.nnz_reg = reg && h->areg_valid ? h->Areg.nnz : 0;
     st.t_saddle_spmv_ms = h->t_saddle_spmv_ms;
     st.n_saddle_spmv = h->n_saddle_spmv;
+    st.t_vc_resid_ms = h->t_vc_resid_ms;
+    st.n_vc_resid = h->n_vc_resid;
+    st.t_vc_post_ms = h->t_vc_post_ms;
+    st.n_vc_post = h->n_vc_post;
     if (tmp) dfree(h, tmp);
     if (r != VEM_OK && r != VEM_ERR_NOT_CONVERGED) break;
     {
@@ -1175,7 +1202,8 @@ vem_status vem_amg_setup(vem_handle *h, int32_t which) {
   if (!slot) return fail(h, VEM_ERR_BAD_INPUT, "unknown AMG hierarchy %d", which);
   if (!h->assembled) VEM_TRY(assemble_impl(h));
   const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
-  if (which == VEM_AMG_SCHUR) return amg_setup(h, h->amg, h->S, h->S_val32, fp32, h->multiplier, kSmoothJacobi);
+  if (which == VEM_AMG_SCHUR)
+    return amg_setup(h, h->amg, h->S, h->S_val32, fp32, h->multiplier, schur_smoother(h));
   if (!h->areg_valid || (fp32 && !h->areg_has32)) VEM_TRY(assemble_reg(h, fp32));
   return amg_setup(h, h->amg_reg, h->Areg, h->Areg_val32, fp32, false, kSmoothChebyshev);
 }

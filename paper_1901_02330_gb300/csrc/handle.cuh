@@ -124,6 +124,8 @@ struct vem_handle {
   cudaEvent_t tev[2 * kTimed] = {};
   double t_schur_spmv_ms = 0.0;                  // accumulated over a solve
   int64_t n_schur_spmv = 0;
+  double t_vc_resid_ms = 0.0, t_vc_post_ms = 0.0;  // timed finest-level cycle launches of a solve
+  int64_t n_vc_resid = 0, n_vc_post = 0;
   static constexpr int kTimedA = 16;             // timed saddle SpMV launches per solve
   cudaEvent_t aev[2 * kTimedA] = {};
   int n_saddle_pending = 0;
@@ -240,6 +242,10 @@ vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *ou
 // layout, used by an FP32 cycle (fp32); pin_last: A0 is singular with the
 // constants as null space; smoother: kSmooth*.
 enum { kSmoothJacobi = 0, kSmoothChebyshev = 1 };
+// the smoother of the S hierarchy chosen by the options
+inline int schur_smoother(const vem_handle *h) {
+  return h->opt.inner_smoother == VEM_SMOOTH_CHEBYSHEV ? kSmoothChebyshev : kSmoothJacobi;
+}
 vem_status amg_setup(vem_handle *h, AmgState *&slot, const SellMat &A0, const float *A0_val32, bool fp32,
                      bool pin_last, int smoother);
 bool amg_valid(const AmgState *S);
@@ -248,6 +254,12 @@ int64_t amg_generation(const AmgState *S);
 void amg_invalidate(AmgState *S);
 double amg_setup_ms(const AmgState *S);
 int amg_levels(const AmgState *S);
+int amg_smoother(const AmgState *S);
+// Time the level-0 residual and post-smoothing launches of the next cycle
+// with CUDA events (an eager cycle: not one captured into a graph); collect
+// adds their durations to h->t_vc_resid_ms / t_vc_post_ms after a sync.
+void amg_time_next_cycle(AmgState *S);
+void amg_collect_timing(vem_handle *h, AmgState *S);
 void amg_free(AmgState *&S);
 // x = V(b) on the finest level (device vectors of the level-0 size); sc: the
 // PCG scalars whose first entry, when non-zero, turns the launches into

@@ -442,7 +442,10 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   auto precondition = [&]() {
     if constexpr (sizeof(T) == sizeof(double)) amg_vcycle(h, h->amg, r, u, sc);
   };
-  if (amg) precondition();
+  if (amg) {
+    amg_time_next_cycle(h->amg);   // the finest-level cycle launches of this eager cycle
+    precondition();
+  }
   // every launch of the Schur SpMV is timed with a pair of events
   int ntimed = 0;
   // stacked systems: the tile shape (systems per tile) chosen by the autotuner
@@ -470,6 +473,7 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
     }
     cudaGetLastError();
     ntimed = 0;
+    if (amg) amg_collect_timing(h, h->amg);
   };
   spmv_it(0);
   const int maxit = h->opt.inner_maxit;
@@ -554,8 +558,8 @@ static vem_status pcg_solve(vem_handle *h, const VemOp &op, const double *b, dou
     const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
     if (h->multiplier && h->nq > 1)
       return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver with the multiplier needs one pressure DOF per cell");
-    if (!amg_valid(h->amg) || amg_is_fp32(h->amg) != fp32)
-      VEM_TRY(amg_setup(h, h->amg, op.S, op.S_val32, fp32, h->multiplier, kSmoothJacobi));
+    if (!amg_valid(h->amg) || amg_is_fp32(h->amg) != fp32 || amg_smoother(h->amg) != schur_smoother(h))
+      VEM_TRY(amg_setup(h, h->amg, op.S, op.S_val32, fp32, h->multiplier, schur_smoother(h)));
     return pcg_solve_t<double>(h, op, op.S.val, op.s_dinv, b, x, wk, iters);
   }
   if (h->opt.precision == VEM_PRECISION_MIXED) {

@@ -25,6 +25,7 @@ VEM_PREC_BLOCK_DIAG, VEM_PREC_BLOCK_TRI, VEM_PREC_BLOCK_REG = 0, 1, 2
 VEM_AMG_SCHUR, VEM_AMG_REG = 0, 1
 VEM_INNER_PCG, VEM_INNER_AMG = 0, 1
 VEM_PRECISION_FP64, VEM_PRECISION_MIXED = 0, 1
+VEM_SMOOTH_JACOBI, VEM_SMOOTH_CHEBYSHEV = 0, 1
 VEM_QP_CELL, VEM_QP_BFACE = 0, 1
 
 
@@ -39,7 +40,7 @@ class vem_options(C.Structure):
     _fields_ = [("element", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("rtol", C.c_double),
                 ("maxit", C.c_int), ("precond", C.c_int), ("inner", C.c_int), ("inner_rtol", C.c_double),
                 ("inner_maxit", C.c_int), ("precision", C.c_int), ("device_io", C.c_int), ("reuse", C.c_int),
-                ("reg_gamma", C.c_double)]
+                ("reg_gamma", C.c_double), ("inner_smoother", C.c_int)]
 
 
 class vem_stats(C.Structure):
@@ -51,7 +52,9 @@ class vem_stats(C.Structure):
                 ("t_amg_setup_ms", C.c_double), ("amg_levels", C.c_int32),
                 ("t_saddle_spmv_ms", C.c_double), ("n_saddle_spmv", C.c_int64),
                 ("multiplier", C.c_double), ("schur_tile", C.c_int32),
-                ("reg_gamma", C.c_double), ("nnz_reg", C.c_int64)]
+                ("reg_gamma", C.c_double), ("nnz_reg", C.c_int64),
+                ("t_vc_resid_ms", C.c_double), ("n_vc_resid", C.c_int64),
+                ("t_vc_post_ms", C.c_double), ("n_vc_post", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,6 +79,7 @@ _SIGS = {
     "vem_set_coefficient": (C.c_int, [C.c_void_p, C.c_void_p]),
     "vem_set_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_set_coefficient_device": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "vem_set_log_coefficient_device": (C.c_int, [C.c_void_p, C.c_void_p]),
     "vem_set_source_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vem_assemble": (C.c_int, [C.c_void_p]),
     "vem_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(vem_stats)]),
@@ -279,6 +283,14 @@ class Solver:
             K = np.ascontiguousarray(K, dtype=np.float64)
             assert K.shape == (self.n_cells,)
             self._check(lib().vem_set_coefficient(self._h, _ptr(K)))
+
+    def set_log_coefficient(self, logK):
+        """theta = log K per cell as a CUDA float64 tensor (vem_set_log_coefficient_device)."""
+        if not hasattr(logK, "data_ptr") or logK.device.type != "cuda" or logK.dtype.itemsize != 8:
+            raise TypeError("log K: a CUDA float64 tensor is required")
+        if logK.numel() != self.n_cells:
+            raise ValueError(f"log K: {self.n_cells} entries required, have {logK.numel()}")
+        self._check(lib().vem_set_log_coefficient_device(self._h, _ptr(logK)))
 
     def set_source(self, f_qp=None, gD_qp=None):
         dev = any(hasattr(a, "data_ptr") for a in (f_qp, gD_qp) if a is not None)

@@ -197,3 +197,59 @@ def test_unsupported_combinations(vs):
             s.amg_levels()
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("name", ["hex10-E0-lognormal", "cvt400-E0-contrast", "prism4-K1-contrast"])
+def test_chebyshev_option_vcycle_matches_oracle(vs, name):
+    """inner_smoother = Chebyshev: the same hierarchy with two Chebyshev steps
+    of the Jacobi iteration before and after the coarse correction; one cycle
+    against the oracle's Chebyshev cycle."""
+    import torch
+    s, sys_ = _pair(vs, name, inner_smoother=vs.VEM_SMOOTH_CHEBYSHEV)
+    try:
+        s.amg_setup()
+        H = amg.setup(solvers.schur(sys_), smoother="chebyshev")
+        assert list(s.amg_levels()[0]) == H.sizes
+        b = np.random.default_rng(13).standard_normal(sys_.n_p)
+        xb = torch.from_numpy(b).cuda()
+        x = torch.empty_like(xb)
+        s.amg_vcycle_device(xb, x)
+        ref = amg.vcycle(H, b)
+        err = np.abs(x.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err <= 10 * TOL[name], err
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("name", ["hex10-E0-lognormal", "cvt400-E0-contrast", "hex12-K1-uniform"])
+@pytest.mark.parametrize("krylov,prec", [(0, 0), (1, 1)], ids=["minres-diag", "fgmres-tri"])
+def test_chebyshev_option_solve_matches_direct(vs, name, krylov, prec):
+    s, sys_ = _pair(vs, name, krylov=krylov, precond=prec, rtol=1e-12, inner_rtol=1e-13,
+                    inner_smoother=vs.VEM_SMOOTH_CHEBYSHEV)
+    try:
+        u, p, st = s.solve()
+    finally:
+        s.close()
+    ud, pd = solvers.solve_direct(sys_)
+    assert st["relres"] <= 1e-12
+    assert np.linalg.norm(u - ud) <= 1e-10 * np.linalg.norm(ud)
+    assert np.linalg.norm(p - pd) <= 1e-10 * np.linalg.norm(pd)
+
+
+def test_chebyshev_option_cuts_inner_iterations(vs):
+    """The oracle's AMG-PCG needs about 0.6 of the Jacobi-smoothed iterations
+    with the Chebyshev smoother on these operators; the library likewise."""
+    mesh = hex_mesh(24)
+    K = fields.K_lognormal(mesh.n_cells, seed=4, sigma=1.5)
+    prob = fields.sine_problem()
+    its = {}
+    for sm in (vs.VEM_SMOOTH_JACOBI, vs.VEM_SMOOTH_CHEBYSHEV):
+        s = vs.Solver(mesh, element=0, krylov=1, precond=1, rtol=1e-10, inner_rtol=1e-10, inner=vs.VEM_INNER_AMG,
+                      inner_smoother=sm)
+        s.set_coefficient(K)
+        s.set_data(prob.f, prob.gD)
+        _, _, st = s.solve()
+        s.close()
+        its[sm] = st["inner_iterations"]
+        assert st["relres"] <= 1e-10
+    assert its[vs.VEM_SMOOTH_CHEBYSHEV] < 0.8 * its[vs.VEM_SMOOTH_JACOBI], its

@@ -93,6 +93,8 @@ BAD_OPTIONS = {
     "reg_gamma-inf": dict(reg_gamma=math.inf),
     "inner": dict(inner=2),
     "precision": dict(precision=2),
+    "inner_smoother": dict(inner_smoother=2),
+    "inner_smoother<0": dict(inner_smoother=-1),
     "mixed-minres": dict(precision=1, krylov=0, precond=0),
     "restart0": dict(restart=0),
     "restart257": dict(restart=257),
