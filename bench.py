@@ -48,8 +48,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_CELLS, help="cells per side (default 128)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-procs", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-data", default="sine", help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
+    ap.add_argument("--no-general", action="store_true", help="skip the polynomial-data (non-eigenvector) run")
     ap.add_argument("--inner-rtol", type=float, default=INNER_RTOL, help="inner Schur solve tolerance")
     ap.add_argument("--element", default="k1", choices=["k1", "e0"])
     ap.add_argument("--inner", default="amg", choices=["pcg", "amg"],
@@ -57,7 +60,7 @@ def parse():
     ap.add_argument("--workload", default="hex128-k1",
                     choices=["hex128-k1", "hex8-e0-minres", "cvt200k-e0-mixed", "hex64-e0-batch64",
                              "cvt100k-adjoint", "cube32-k1-neumann", "cube32-k1-blockreg", "optimality-k1",
-                             "cube24-k2", "cvt27k-k2-element", "optimality-k2"],
+                             "cube24-k2", "cvt27k-k2-element", "optimality-k2", "cvt200k-k1-element"],
                     help="hex128-k1 is the headline; the others are the remaining configurations")
     ap.add_argument("--profile", action="store_true",
                     help="one step only (for an ncu launch list); prints a short JSON line")
@@ -72,33 +75,51 @@ def dist_env():
 
 
 # ----------------------------------------------------------------- oracle ---
-def oracle_sample(n: int = SAMPLE_N, inner: str = "amg"):
+def oracle_sample(n: int = SAMPLE_N, inner: str = "amg", data: str = "sine", processes: int = 1):
     """Run the CPU oracle on one n^3 sample of the workload (same element,
     preconditioner, inner solver and tolerances); returns (unknowns,
-    seconds, iterations)."""
+    seconds, iterations).  processes > 1 assembles in that many spawned
+    worker processes."""
     from oracle import assemble, paper_element, solvers
     from synth import fields, hex_mesh
     m = hex_mesh(n)
-    prob = fields.sine_problem()
+    prob = fields.sine_problem() if data == "sine" else fields.paper_polynomial_problem()
     t0 = time.perf_counter()
-    sys_ = assemble(m, paper_element(1), np.ones(m.n_cells), f=prob.f, gD=prob.gD)
+    sys_ = assemble(m, paper_element(1), np.ones(m.n_cells), f=prob.f, gD=prob.gD, processes=processes)
     u, p, res = solvers.solve_krylov(sys_, "fgmres", "tri", inner, rtol=RTOL, inner_rtol=INNER_RTOL, restart=30)
     dt = time.perf_counter() - t0
     return sys_.n, dt, res.iters
 
 
 def cpu_baseline_subprocess(inner: str):
-    """The oracle timed single-threaded in a fresh process (spawned, never forked
-    from the CUDA process)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--inner", inner], env=env,
-                       capture_output=True, text=True, timeout=600)
-    if r.returncode != 0:
-        return {"error": r.stderr[-300:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["n"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"hex{SAMPLE_N}^3 k=1 ({d['n']} unknowns, same element/solver/tolerance), "
-                      f"assembly + FGMRES(30)/block-tri solve in {d['seconds']:.1f}s, {d['iters']} iterations"}
+    """The oracle timed in fresh processes (spawned, never forked from the
+    CUDA process): single-threaded, and on all the host's cores (assembly in
+    one worker process per core, BLAS on all cores; SciPy's sparse products
+    stay on one thread), the latter also with the paper's polynomial data."""
+    ncpu = os.cpu_count() or 1
+    runs = {}
+    for key, threads, data in (("single_thread", 1, "sine"), ("all_cores", ncpu, "sine"),
+                               ("all_cores_polynomial", ncpu, "poly")):
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+                   MKL_NUM_THREADS=str(threads))
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--inner", inner,
+                            "--cpu-procs", str(threads), "--cpu-data", data], env=env,
+                           capture_output=True, text=True, timeout=900)
+        if r.returncode != 0:
+            runs[key] = {"error": r.stderr[-300:]}
+            continue
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        runs[key] = {"value": d["n"] / d["seconds"], "unit": UNIT, "cores": threads, "seconds": d["seconds"],
+                     "iterations": d["iters"], "data": data}
+    best = runs.get("all_cores", {})
+    if "value" not in best:
+        best = runs.get("single_thread", {})
+    if "value" not in best:
+        return {"error": "oracle runs failed", "runs": runs}
+    return {"value": best["value"], "unit": UNIT, "cores": best["cores"], "kind": "oracle", "nproc": ncpu,
+            "sample": f"hex{SAMPLE_N}^3 k=1 (same element/solver/tolerance, sine data), assembly + FGMRES(30)/"
+                      f"block-tri solve: {best['seconds']:.1f} s, {best['iterations']} iterations, on "
+                      f"{best['cores']} of {ncpu} host cores", "runs": runs}
 
 
 def run_reference(a):
@@ -220,6 +241,35 @@ def spmv_bytes(nnz, rows):
     return 12 * nnz + 16 * rows
 
 
+def vcycle_roofline(stats, nnz, rows, fp32, hbm_peak):
+    """Roofline of the finest-level V-cycle launches (k_vc_sell on S: the
+    residual r = b - S x and the post-smoothing y = x + w D^-1 (b - S x)),
+    timed live by the library with CUDA events in the first, eagerly
+    launched cycle of every inner solve.  Algorithmic bytes: values and
+    int32 column ids once per nonzero, each vector once per row (residual:
+    x, b read, r written; post-smoothing: x, b, w D^-1 read, y written)."""
+    sv = 4 if fp32 else 8
+    out = {}
+    for key, tk, nk, nvec, flops_row in (("residual", "t_vc_resid_ms", "n_vc_resid", 3, 1),
+                                         ("post_smoothing", "t_vc_post_ms", "n_vc_post", 4, 3)):
+        cnt = sum(x_[nk] for x_ in stats)
+        if not cnt:
+            continue
+        ms_ = sum(x_[tk] for x_ in stats) / cnt
+        by = (sv + 4) * nnz + nvec * sv * rows
+        gbs = by / (ms_ * 1e-3) / 1e9
+        d = {"kernel": "k_vc_sell<%s> level 0 %s" % ("float" if fp32 else "double", key), "bound": "hbm",
+             "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+             "algorithmic_bytes": by, "launch_ms": ms_, "launches_timed": cnt}
+        if not fp32:
+            # FP64 operations per launch (an FMA counts 2) against the nominal FP64 rate
+            fl = 2 * nnz + flops_row * rows
+            d["fp64_gflops"] = fl / (ms_ * 1e-3) / 1e9
+            d["fp64_frac_of_nominal"] = d["fp64_gflops"] / FP64_PEAK_GFLOPS
+        out[key] = d
+    return out
+
+
 def k1_cell_flops(m):
     """FP64 operations of the paper-k=1 element kernel for one cell whose faces
     have m[i] vertices (hand count of the kernel's formulas, FMA = 2):
@@ -315,6 +365,46 @@ def run_ours(a):
     value = n * world / (ms * 1e-3)
     st = stats[-1]
 
+    # ---------------- a right-hand side that is not an eigenvector of S ----------------
+    # The sine data of the headline are an exact eigenvector of S on uniform
+    # cubes (3 outer iterations).  The paper's polynomial solution (its
+    # convergence test) with K = 1 and Dirichlet data is not: same mesh,
+    # element, preconditioner, inner and outer tolerances.
+    general = None
+    if not a.no_general:
+        prob2 = fields.paper_polynomial_problem()
+        s.set_data(prob2.f, prob2.gD)
+        ug = torch.empty_like(u)
+        pg = torch.empty_like(p)
+        general = {"data": "the paper's polynomial solution x^5 + 6y^4 + 9z^3 + x y^2 z^3 (Sec. 4.4), K = 1, "
+                           "Dirichlet data; same mesh, element, preconditioner and outer tolerance"}
+        for key, irt in (("same_config", a.inner_rtol), ("inner_rtol_1e-1", 1e-1)):
+            s.set_options(inner_rtol=irt)
+            gstats = []
+
+            def gstep():
+                s.assemble()
+                return s.solve(u_out=ug, p_out=pg)[2]
+
+            gstep()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(a.steps):
+                gstats.append(gstep())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            gms = max_over_ranks(e0.elapsed_time(e1) / a.steps)
+            g = gstats[-1]
+            general[key] = {"inner_rtol": irt, "value": n * world / (gms * 1e-3), "unit": UNIT, "ms_per_step": gms,
+                            "iterations": g["iterations"], "inner_iterations": g["inner_iterations"],
+                            "relres": g["relres"], "t_assemble_ms": g["t_assemble_ms"],
+                            "t_solve_ms": g["t_solve_ms"], "t_amg_setup_ms": g["t_amg_setup_ms"],
+                            "ms_per_outer_iteration": (g["t_solve_ms"] - g["t_amg_setup_ms"]) / max(1, g["iterations"]),
+                            "inner_iterations_per_outer": g["inner_iterations"] / max(1, g["iterations"])}
+        s.set_options(inner_rtol=a.inner_rtol)
+        s.set_data(prob.f, prob.gD)
+        del ug, pg
+
     # ---------------- roofline of the saddle-matrix SpMV ----------------
     # live: every saddle SpMV launch of the timed steps (up to 16 per solve)
     # timed by the library with CUDA events on its stream
@@ -338,6 +428,16 @@ def run_ours(a):
     spmv_gbs = sb / (spmv_ms * 1e-3) / 1e9
     s.close()
     del x, y
+    # the element kernel on every cell (no congruence classes): the K1 local
+    # matrices of all 2,097,152 cells, timed by the library with CUDA events
+    sr = vs.Solver(mesh, stream=sid, device_io=1, **dict(opts, reuse=0))
+    el_all = []
+    for i in range(4):
+        ms_e, ncls_all = sr.assemble_local()
+        if i > 0:
+            el_all.append(ms_e)
+    sr.close()
+    el_all_ms = statistics.median(el_all)
     # element kernel: timed by the library with events on its stream, every step
     el_ms = statistics.median([x_["t_element_ms"] for x_ in stats])
     if a.element == "k1":
@@ -351,6 +451,7 @@ def run_ours(a):
     cg_ms = sum(x_["t_schur_spmv_ms"] for x_ in stats) / max(1, sum(x_["n_schur_spmv"] for x_ in stats))
     cg_bytes = 12 * st["nnz_S"] + 24 * st["n_p"]
     cg_gbs = cg_bytes / (cg_ms * 1e-3) / 1e9
+    vc_roof = vcycle_roofline(stats, st["nnz_S"], st["n_p"], False, hbm_peak) if a.inner == "amg" else None
 
     # ---------------- mixed precision at equal accuracy ----------------
     mixed = None
@@ -374,8 +475,10 @@ def run_ours(a):
             mst = mstep()
         torch.cuda.synchronize()
         e0.record(stream)
+        mstats = []
         for _ in range(a.steps):
             mst = mstep()
+            mstats.append(mst)
         e1.record(stream)
         torch.cuda.synchronize()
         mms = e0.elapsed_time(e1) / a.steps
@@ -386,7 +489,9 @@ def run_ours(a):
                  "inner": ("FP64 CG with FP32 AMG V-cycle rtol %g" % mixed_inner_rtol if a.inner == "amg"
                            else "FP32 Jacobi-PCG rtol %g" % mixed_inner_rtol),
                  "rel_diff_vs_fp64_u": float(torch.linalg.norm(um - u) / torch.linalg.norm(u)),
-                 "rel_diff_vs_fp64_p": float(torch.linalg.norm(pm_ - p) / torch.linalg.norm(p))}
+                 "rel_diff_vs_fp64_p": float(torch.linalg.norm(pm_ - p) / torch.linalg.norm(p)),
+                 "roofline_vcycle_fp32": (vcycle_roofline(mstats, st["nnz_S"], st["n_p"], True, hbm_peak)
+                                          if a.inner == "amg" else None)}
         del um, pm_
 
     # ---------------- end-to-end through the public API (e2e) ----------------
@@ -458,11 +563,22 @@ def run_ours(a):
                                 "traffic": NCU_TRAFFIC.get(("k_cg_spmv", n_p, st["nnz_S"])),
                                 "algorithmic_bytes": cg_bytes, "launch_ms": cg_ms,
                                 "launches_per_step": st["n_schur_spmv"]},
+        "roofline_vcycle": vc_roof,
         "element_kernel": {"kernel": "k_elem_%s" % a.element, "bound": "alu", "classes_evaluated": st["n_classes"],
                            "cells": mesh.n_cells, "flops_per_class": cell_flops, "launch_ms": el_ms,
                            "achieved_gflops": el_gflops, "peak_gflops": FP64_PEAK_GFLOPS,
+                           "peak_source": "nominal FP64: 152 SMs x 2070 MHz x 2 DFMA/clock x 2 (not measured)",
                            "note": "congruent cells share one evaluation (translation invariance)"},
+        "element_kernel_every_cell": {"kernel": "k_elem_%s" % a.element, "bound": "alu", "reuse": 0,
+                                      "classes_evaluated": ncls_all, "launch_ms": el_all_ms,
+                                      "cells_per_s": ncls_all / (el_all_ms * 1e-3),
+                                      "achieved_gflops": cell_flops * ncls_all / (el_all_ms * 1e-3) / 1e9,
+                                      "peak_gflops": FP64_PEAK_GFLOPS,
+                                      "frac_of_nominal": cell_flops * ncls_all / (el_all_ms * 1e-3) / 1e9
+                                      / FP64_PEAK_GFLOPS,
+                                      "peak_source": "nominal FP64 (not measured)"},
         "mixed_precision": mixed,
+        "general_rhs": general,
         "phases_ms": {"element": el_ms, "scatter": st["t_scatter_ms"], "assemble": st["t_assemble_ms"],
                       "solve": st["t_solve_ms"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -656,6 +772,31 @@ def run_workload(a):
                              "element": "paper k=2"},
                      note="the element kernel alone (vem_assemble_local), CUDA events; one block of 256 threads "
                           "per cell; FP64 dense algebra in shared memory")
+    elif w == "cvt200k-k1-element":
+        # The paper's k = 1 element kernel on the 200k-seed CVT mesh of the
+        # high-contrast configuration, every cell evaluated (no classes)
+        mesh = voronoi_mesh(200000, seed=0, lloyd=10)
+        s = vs.Solver(mesh, stream=sid, element=vs.VEM_ELEMENT_K1, reuse=0)
+        times = []
+        for i in range(a.warmup + a.steps):
+            ms_e, ncls = s.assemble_local()
+            if i >= a.warmup:
+                times.append(ms_e)
+        s.close()
+        ms = float(np.median(times))
+        nv = np.diff(mesh.face_vtx_ptr)
+        flops = sum(k1_cell_flops(nv[mesh.cell_face[mesh.cell_face_ptr[c]:mesh.cell_face_ptr[c + 1]]].tolist())
+                    for c in range(mesh.n_cells))
+        gfl = flops / (ms * 1e-3) / 1e9
+        line = _line(a, "element matrices per second (paper k = 1)", mesh.n_cells / (ms * 1e-3), "cells/s", ms, "f64",
+                     {"workload": w, "cells": mesh.n_cells, "classes": ncls, "reuse": 0,
+                      "faces_per_cell": float(np.diff(mesh.cell_face_ptr).mean()), "element": "paper k=1"},
+                     roofline={"kernel": "k_elem_k1", "bound": "alu", "achieved": gfl, "peak": FP64_PEAK_GFLOPS,
+                               "unit": "GFLOP/s", "frac": gfl / FP64_PEAK_GFLOPS, "traffic": None,
+                               "flops_per_launch": flops,
+                               "peak_source": "nominal FP64: 152 SMs x 2070 MHz x 2 DFMA/clock x 2 (not measured)"},
+                     note="the element kernel alone (vem_assemble_local), CUDA events; FP64 operations from the "
+                          "hand count of the kernel's formulas per cell (face vertex counts)")
     elif w == "optimality-k2":
         # Iterations under refinement at the paper's k = 2 (its optimality
         # tables, Tables 4-6) on Cube, Octa and CVT meshes in the paper's
@@ -789,6 +930,26 @@ def run_workload(a):
                      "rel_diff_vs_fp64_jacobi_u": float(torch.linalg.norm(v[2] - u64) / torch.linalg.norm(u64)),
                      "rel_diff_vs_fp64_jacobi_p": float(torch.linalg.norm(v[3] - p64) / torch.linalg.norm(p64))}
                  for k, v in res.items()}
+        # Error of every variant against the oracle on the largest mesh of this
+        # recipe the oracle solves quickly: 20,000 seeds (seed 0, 10 Lloyd
+        # iterations), K = 10^U (seed 1), the oracle's FGMRES with an exact S
+        # to relres 1e-14 (within 2e-14 of its 1e-12 solve)
+        from oracle import E0 as E0o, assemble as oassemble, solvers as osolvers
+        m20 = voronoi_mesh(20000, seed=0, lloyd=10)
+        K20 = fields.K_high_contrast(m20.n_cells, seed=1, decades=4.0)
+        sys20 = oassemble(m20, E0o, 1.0 / K20, f=prob.f, gD=prob.gD, processes=max(1, os.cpu_count() or 1))
+        uo, po, reso = osolvers.solve_krylov(sys20, "fgmres", "tri", "exact", rtol=1e-14, restart=30, maxit=5000)
+        vs_oracle = {"mesh": f"{m20.n_cells} cells (20,000 seeds, same recipe)", "oracle_relres": reso.relres}
+        for name, (prec, inner, irt) in variants.items():
+            s20 = vs.Solver(m20, stream=sid, element=0, krylov=1, precond=1, precision=prec, inner=inner,
+                            rtol=1e-8, inner_rtol=irt, inner_maxit=5000, maxit=2000)
+            s20.set_coefficient(K20)
+            s20.set_data(prob.f, prob.gD)
+            u20, p20, st20 = s20.solve()
+            s20.close()
+            vs_oracle[name] = {"relres": st20["relres"], "iterations": st20["iterations"],
+                               "rel_err_u": float(np.linalg.norm(u20 - uo) / np.linalg.norm(uo)),
+                               "rel_err_p": float(np.linalg.norm(p20 - po) / np.linalg.norm(po))}
         line = _line(a, "time-to-solution (rel.res 1e-8) and DOFs/s", n / (ms * 1e-3), "DOFs/s", ms,
                      "f64 outer and inner CG / f32 AMG V-cycle",
                      {"workload": w, "cells": mesh.n_cells, "faces": mesh.n_faces, "n_u": st["n_u"], "n_p": st["n_p"],
@@ -799,7 +960,8 @@ def run_workload(a):
                      variants=table,
                      speedup_vs_fp64_jacobi=res["fp64-jacobi"][0] / ms,
                      speedup_vs_fp64_amg=res["fp64-amg"][0] / ms,
-                     speedup_mixed_vs_fp64_jacobi_solver=res["fp64-jacobi"][0] / res["mixed-jacobi"][0])
+                     speedup_mixed_vs_fp64_jacobi_solver=res["fp64-jacobi"][0] / res["mixed-jacobi"][0],
+                     error_vs_oracle=vs_oracle)
     elif w == "hex64-e0-batch64":
         # 64 systems on 64^3 cubes, E0, K_b = exp(2 xi) (seed 100 + b), f_b = 8 Fourier modes (seed 200 + b)
         mesh = hex_mesh(64)
@@ -886,25 +1048,53 @@ def run_workload(a):
         ms, g = _timed(step, a.steps, a.warmup, stream)
         g = g.detach().cpu().numpy()
         cells = np.random.default_rng(5).choice(mesh.n_cells, size=20, replace=False)
-        eps = 1e-6
-        errs = []
+        # solver noise of the loss: the same system solved from three initial
+        # guesses (FGMRES stops at relres 1e-12, so L carries an error dL);
+        # a central difference with step eps then carries up to 2 dL / (2 eps)
+        n_u, n_p = s.sizes()
+        Ls = []
+        with torch.no_grad():
+            L0 = loss_of(theta).item()
+            for k in range(3):
+                x0 = torch.tensor(1e-3 * np.random.default_rng(60 + k).standard_normal(n_u + n_p), device="cuda")
+                uu = torch.empty(n_u, dtype=torch.float64, device="cuda")
+                pp = torch.empty(n_p, dtype=torch.float64, device="cuda")
+                s.set_log_coefficient(theta)
+                s.solve(x0=x0, u_out=uu, p_out=pp)
+                Ls.append(0.5 * torch.sum((pp - ptarget) ** 2).item())
+        dL = max(Ls + [L0]) - min(Ls + [L0])
+        rows_fd = []
         with torch.no_grad():
             for P in cells:
-                tp = theta.clone()
-                tm = theta.clone()
-                tp[P] += eps
-                tm[P] -= eps
-                fd = (loss_of(tp).item() - loss_of(tm).item()) / (2 * eps)
-                errs.append((abs(fd - g[P]) / max(abs(fd), 1e-300), abs(fd - g[P]) / np.abs(g).max()))
+                fds = {}
+                for eps in (1e-6, 1e-4):
+                    tp = theta.clone()
+                    tm = theta.clone()
+                    tp[P] += eps
+                    tm[P] -= eps
+                    fds[eps] = (loss_of(tp).item() - loss_of(tm).item()) / (2 * eps)
+                bound = 10 * 2 * dL / (2 * 1e-6)
+                err6 = abs(fds[1e-6] - g[P])
+                rows_fd.append({"cell": int(P), "grad": float(g[P]), "fd_1e-6": fds[1e-6], "fd_1e-4": fds[1e-4],
+                                "rel_err_1e-6": err6 / abs(fds[1e-6]),
+                                "rel_err_1e-4": abs(fds[1e-4] - g[P]) / abs(fds[1e-4]),
+                                "fd_noise_bound_1e-6": bound,
+                                "within_1e-6_or_bound": bool(err6 <= 1e-6 * abs(fds[1e-6]) + bound)})
         n = mesh.n_cells
         line = _line(a, "forward + adjoint gradient time and cells/s", n / (ms * 1e-3), "cells/s", ms, "f64",
                      {"workload": w, "cells": mesh.n_cells, "faces": mesh.n_faces, "element": "E0",
                       "loss": "0.5 ||p_h - p_target||^2", "krylov": "FGMRES(30)", "precond": "block upper-triangular",
                       "inner": "AMG-PCG 1e-2", "rtol": 1e-12},
-                     fd_check={"cells": 20, "step": eps,
-                               "max_rel_err": float(max(e[0] for e in errs)),
-                               "median_rel_err": float(np.median([e[0] for e in errs])),
-                               "max_err_rel_to_max_grad": float(max(e[1] for e in errs))})
+                     fd_check={"cells": 20, "step": 1e-6,
+                               "max_rel_err": float(max(r_["rel_err_1e-6"] for r_ in rows_fd)),
+                               "median_rel_err": float(np.median([r_["rel_err_1e-6"] for r_ in rows_fd])),
+                               "max_rel_err_step_1e-4": float(max(r_["rel_err_1e-4"] for r_ in rows_fd)),
+                               "loss": L0, "loss_solver_noise": dL,
+                               "all_within_1e-6_or_noise_bound": all(r_["within_1e-6_or_bound"] for r_ in rows_fd),
+                               "note": "noise bound = 10 x 2 dL / (2 x 1e-6), dL the spread of L over solves of "
+                                       "one system from different initial guesses; FD truncation at step 1e-4 is "
+                                       "~1e-8 relative",
+                               "per_cell": rows_fd})
         s.close()
     print(json.dumps(line))
     return 0
@@ -915,7 +1105,7 @@ def main():
     if a.workload != "hex128-k1" and not a.cpu_sample and a.impl == "ours":
         return run_workload(a)
     if a.cpu_sample:
-        n, dt, it = oracle_sample(SAMPLE_N, "amg" if a.inner == "amg" else "pcg")
+        n, dt, it = oracle_sample(SAMPLE_N, "amg" if a.inner == "amg" else "pcg", a.cpu_data, a.cpu_procs)
         print(json.dumps({"n": n, "seconds": dt, "iters": it}))
         return 0
     if a.impl == "reference":
