@@ -99,8 +99,9 @@ typedef struct {
  * at n_u + 4c .. n_u + 4c + 3).  K2 solves with Dirichlet and prescribed-
  * flux faces (the mean-zero pressure then constrains the constant moments,
  * c = |P| on them) and the block-diagonal and block-triangular
- * preconditioners (Jacobi-PCG or AMG for S; the AMG not with the
- * multiplier); Block-Reg, vem_solve_batched and vem_adjoint give
+ * preconditioners (Jacobi-PCG, the scalar AMG without the multiplier, or
+ * the point-block AMG VEM_INNER_BLOCK_AMG for S); Block-Reg,
+ * vem_solve_batched and vem_adjoint give
  * VEM_ERR_UNSUPPORTED with it.  Its cell quadrature points
  * (VEM_QP_CELL) are those of a degree-3 rule on the fan tetrahedra of every
  * cell (27 per tetrahedron), built on first use. */
@@ -127,7 +128,16 @@ enum { VEM_PREC_BLOCK_DIAG = 0, VEM_PREC_BLOCK_TRI = 1, VEM_PREC_BLOCK_REG = 2 }
  * VEM_PRECISION_MIXED runs the V-cycle (matrix values, vectors and
  * arithmetic of every level) in FP32.  The AMG is single-system:
  * vem_solve_batched gives VEM_ERR_UNSUPPORTED with it. */
-enum { VEM_INNER_PCG = 0, VEM_INNER_AMG = 1 };
+/* VEM_INNER_BLOCK_AMG (the paper's k = 2 element only): CG preconditioned
+ * by one V-cycle of a point-block smoothed-aggregation AMG of S that keeps
+ * the four pressure moments of a cell together: aggregates of the graph of
+ * 4 x 4 blocks (strength by Frobenius norms), a tentative prolongator from
+ * the pressure DOFs of 1, x, y, z orthonormalised per aggregate (Vanek,
+ * Mandel & Brezina 1996), damped block-Jacobi smoothing with the weight
+ * from a Lanczos estimate of rho(D^-1 S) (or two block-Chebyshev steps with
+ * inner_smoother), FP64 only.  The scalar AMG treats every moment as its own
+ * node and loses to plain Jacobi-PCG on this S. */
+enum { VEM_INNER_PCG = 0, VEM_INNER_AMG = 1, VEM_INNER_BLOCK_AMG = 2 };
 enum { VEM_PRECISION_FP64 = 0, VEM_PRECISION_MIXED = 1 };
 enum { VEM_SMOOTH_JACOBI = 0, VEM_SMOOTH_CHEBYSHEV = 1 };
 
@@ -382,7 +392,8 @@ vem_status vem_residual_norm_noalloc(int64_t rows, const int64_t *row_ptr, const
  * arrays of at least 12 entries, any may be NULL.
  * vem_amg_get_level: host CSR of level l's operator (row_ptr[rows + 1],
  * col[nnz], val[nnz]), its aggregate of every row (agg[rows], -1 for rows
- * outside the coarse space) and its prolongator P (rows x rows of level
+ * outside the coarse space; with VEM_INNER_BLOCK_AMG one entry per point
+ * block, agg[rows / block size]) and its prolongator P (rows x rows of level
  * l + 1; prow_ptr[rows + 1], pcol/pval[nnz_p]); any pointer may be NULL,
  * agg and P are left untouched on the coarsest level.
  * vem_amg_vcycle_device: x = V(b), one cycle, device vectors of the

@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "handle.cuh"
 
@@ -102,8 +103,16 @@ struct AmgLevel {
   size_t c_wdc32 = 0;
   double omega = 0.0;
   int mis_rounds = 0;       // MIS-2 rounds this level needed in the last setup
-  double rho = 0.0;         // Gershgorin bound of rho(D^-1 A)
+  double rho = 0.0;         // Gershgorin bound of rho(D^-1 A) (point blocks: the estimate below)
   double cheb_c = 0.0;      // Chebyshev: rho_1 rho_0 (the second step)
+  // point blocks (block hierarchies): bs x bs diagonal blocks D_I, row-major
+  int bs = 1;
+  double *dblk = nullptr;   // D_I^-1
+  double *lblk = nullptr;   // L_I^-1 with D_I = L_I L_I^T
+  size_t c_dblk = 0, c_lblk = 0;
+  double *bns = nullptr;    // near-null space of this level (levels >= 1; rows x m)
+  size_t c_bns = 0;
+  double cheb_theta = 0.0, cheb_w2 = 0.0;   // block Chebyshev: 1 / theta and 2 rho_1 / delta
   int64_t n = 0, nc = 0;
   double *x() const { return vec; }
   double *x2() const { return vec + n; }
@@ -145,6 +154,16 @@ struct AmgState {
   int32_t *tcol = nullptr;  size_t c_tcol = 0;    //   and the scratch rows
   double *tval = nullptr;   size_t c_tval = 0;
   double t_setup_ms = 0.0;
+  // point-block hierarchy: level-0 block size and near-null space (m columns)
+  bool block = false;
+  int m = 0;
+  const double *B0 = nullptr;
+  CsrBuf bQ, bQT, bAQ, bN, bT, bZ, bAgg, bAggT, bLm, bLmT, bY, bC;   // block setup scratch
+  double *sq = nullptr;     size_t c_sq = 0;      // squared values of the level operator
+  double *dgb = nullptr;    size_t c_dgb = 0;     // diagonal of the block graph
+  double *dgbi = nullptr;   size_t c_dgbi = 0;
+  double *lz = nullptr;     size_t c_lz = 0;      // Lanczos basis (n x 11) and w
+  double *lpart = nullptr;  size_t c_lpart = 0;   // partial sums of the Lanczos dots
   cudaEvent_t tev[4] = {};  // level-0 residual and post-smoothing launches of a timed cycle
   bool timing = false, timed = false;
   ~AmgState() {
@@ -982,6 +1001,325 @@ __global__ void k_scale_into(int64_t n, const double *__restrict__ a, double w, 
   ROWS_LOOP(i, n) y[i] = w * a[i];
 }
 
+// ------------------------------------------------------ point blocks ------
+// Smoothed aggregation on point blocks (several unknowns per node, e.g. the
+// four P1 pressure moments of a cell of the paper's k = 2 element): Vanek,
+// Mandel & Brezina (1996), the tentative prolongator built from a near-null
+// space B orthonormalised per aggregate.  Rules:
+//   block graph: N_IJ = Frobenius norm of the bs x bs block (I, J) of A,
+//     formed as sqrt(Q^T (A o A) Q) with Q the n x nb block-membership
+//     matrix; strong(I, J): N_IJ >= theta sqrt(N_II N_JJ); aggregates from
+//     that graph by the scalar rules above;
+//   T: for aggregate a with member blocks I_1 < I_2 < ..., the rows of its
+//     DOFs (block by block) of B = Q_a R_a with R_a upper triangular,
+//     R_jj > 0 (Cholesky of B_a^T B_a, then Q_a = B_a R_a^-1); T holds Q_a in
+//     columns a m .. a m + m - 1, the coarse near-null space R_a;
+//   D = block diagonal of A = L L^T blockwise; rho = min(Gershgorin bound
+//     of C = L^-1 A L^-T, 1.1 x the largest Ritz value of C after 10 Lanczos
+//     steps with full reorthogonalisation from v_i = 2 (splitmix64(i) >> 11)
+//     2^-53 - 1); omega = 4 / (3 rho);
+//   P = T - omega D^-1 (A T); coarse operator P^T A P with block size m;
+//   cycle: damped block Jacobi (x = omega D^-1 b; ...) or two Chebyshev
+//     steps of block Jacobi on [rho/10, rho].
+constexpr int kMaxBs = 8;   // largest block size
+constexpr int kMaxM = 6;    // largest near-null space width
+
+// D_I^-1 and L_I^-1 (D_I = L_I L_I^T) of every diagonal block, a thread per block.
+__global__ void k_blk_diag(int64_t nb, int bs, DMat A, double *dinvb, double *linvb, int *err) {
+  ROWS_LOOP(I, nb) {
+    double D[kMaxBs][kMaxBs], Lc[kMaxBs][kMaxBs], Li[kMaxBs][kMaxBs];
+    for (int r = 0; r < bs; ++r)
+      for (int c = 0; c < bs; ++c) D[r][c] = 0.0, Lc[r][c] = 0.0, Li[r][c] = 0.0;
+    const int64_t i0 = I * bs;
+    for (int r = 0; r < bs; ++r) {
+      int64_t base;
+      int st, L;
+      A.row(i0 + r, base, st, L);
+      for (int k = 0; k < L; ++k) {
+        const int64_t p = base + (int64_t)st * k;
+        const int64_t j = A.col[p];
+        if (j >= i0 && j < i0 + bs) D[r][j - i0] = A.val[p];
+      }
+    }
+    bool ok = true;
+    for (int j = 0; j < bs; ++j) {          // Cholesky, column by column
+      double d = D[j][j];
+      for (int k = 0; k < j; ++k) d -= Lc[j][k] * Lc[j][k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        ok = false;
+        d = 1.0;
+      }
+      Lc[j][j] = sqrt(d);
+      for (int i = j + 1; i < bs; ++i) {
+        double v = D[i][j];
+        for (int k = 0; k < j; ++k) v -= Lc[i][k] * Lc[j][k];
+        Lc[i][j] = v / Lc[j][j];
+      }
+    }
+    if (!ok) atomicOr(err, DEVERR_AMG_DIAG);
+    for (int c = 0; c < bs; ++c) {          // L^-1 by forward substitution, column by column
+      for (int i = 0; i < bs; ++i) {
+        double v = (i == c) ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) v -= Lc[i][k] * Li[k][c];
+        Li[i][c] = (i >= c) ? v / Lc[i][i] : 0.0;
+      }
+    }
+    double *dv = dinvb + I * bs * bs, *lv = linvb + I * bs * bs;
+    for (int r = 0; r < bs; ++r)
+      for (int c = 0; c < bs; ++c) {
+        double v = 0.0;                     // (L^-T L^-1)_rc = sum_k Li_kr Li_kc
+        for (int k = 0; k < bs; ++k) v += Li[k][r] * Li[k][c];
+        dv[r * bs + c] = v;
+        lv[r * bs + c] = Li[r][c];
+      }
+  }
+}
+
+__global__ void k_square(int64_t n, const double *__restrict__ a, double *b) {
+  ROWS_LOOP(i, n) b[i] = a[i] * a[i];
+}
+
+__global__ void k_sqrt_inplace(int64_t n, double *a) {
+  ROWS_LOOP(i, n) a[i] = sqrt(a[i]);
+}
+
+// Q (n x nb, Q_{i, i / bs} = 1) and Q^T.
+__global__ void k_member_rows(int64_t n, int bs, int64_t *rp, int32_t *col, double *val) {
+  ROWS_LOOP(i, n) {
+    rp[i] = i;
+    col[i] = (int32_t)(i / bs);
+    val[i] = 1.0;
+    if (i == n - 1) rp[n] = n;
+  }
+}
+
+__global__ void k_member_cols(int64_t nb, int bs, int64_t *rp, int32_t *col, double *val) {
+  ROWS_LOOP(I, nb) {
+    rp[I] = I * bs;
+    for (int k = 0; k < bs; ++k) {
+      col[I * bs + k] = (int32_t)(I * bs + k);
+      val[I * bs + k] = 1.0;
+    }
+    if (I == nb - 1) rp[nb] = nb * bs;
+  }
+}
+
+// The block-diagonal matrix of the blocks blk (row-major bs x bs per block)
+// as CSR with full blocks; trans: the transposed blocks.
+__global__ void k_blkdiag_rows(int64_t n, int bs, const double *__restrict__ blk, int trans, int64_t *rp,
+                               int32_t *col, double *val) {
+  ROWS_LOOP(i, n) {
+    const int64_t I = i / bs;
+    const int r = (int)(i - I * bs);
+    rp[i] = i * bs;
+    for (int k = 0; k < bs; ++k) {
+      col[i * bs + k] = (int32_t)(I * bs + k);
+      val[i * bs + k] = trans ? blk[I * bs * bs + k * bs + r] : blk[I * bs * bs + r * bs + k];
+    }
+    if (i == n - 1) rp[n] = n * bs;
+  }
+}
+
+// Aggregate membership as a CSR matrix (nb x nc): one entry per aggregated block.
+__global__ void k_agg_count(int64_t nb, const int32_t *__restrict__ agg, int64_t *cnt) {
+  ROWS_LOOP(I, nb) cnt[I] = agg[I] >= 0 ? 1 : 0;
+}
+
+__global__ void k_agg_fill(int64_t nb, const int32_t *__restrict__ agg, const int64_t *__restrict__ rp, int32_t *col,
+                           double *val) {
+  ROWS_LOOP(I, nb) {
+    if (agg[I] >= 0) {
+      col[rp[I]] = agg[I];
+      val[rp[I]] = 1.0;
+    }
+  }
+}
+
+__global__ void k_tent_count(int64_t n, int bs, int m, const int32_t *__restrict__ agg, int64_t *cnt) {
+  ROWS_LOOP(i, n) cnt[i] = agg[i / bs] >= 0 ? m : 0;
+}
+
+// Tentative prolongator, a thread per aggregate: members from the sorted row
+// of A^T (agg membership transposed), B_a = Q_a R_a by Cholesky of the Gram
+// matrix (R_a = chol(B_a^T B_a)^T, R_jj > 0) and Q_a = B_a R_a^-1.
+__global__ void k_tent(int64_t nc, int bs, int m, const int64_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                       const double *__restrict__ B, const int64_t *__restrict__ trp, int32_t *tcol, double *tval,
+                       double *Bc, int *err) {
+  ROWS_LOOP(a, nc) {
+    double G[kMaxM][kMaxM], R[kMaxM][kMaxM];
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k < m; ++k) G[j][k] = 0.0, R[j][k] = 0.0;
+    for (int64_t p = arp[a]; p < arp[a + 1]; ++p)
+      for (int c = 0; c < bs; ++c) {
+        const double *x = B + ((int64_t)acol[p] * bs + c) * m;
+        for (int j = 0; j < m; ++j)
+          for (int k = 0; k < m; ++k) G[j][k] += x[j] * x[k];
+      }
+    bool ok = true;
+    for (int j = 0; j < m; ++j) {          // G = R^T R, R upper triangular
+      double d = G[j][j];
+      for (int k = 0; k < j; ++k) d -= R[k][j] * R[k][j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        ok = false;
+        d = 1.0;
+      }
+      R[j][j] = sqrt(d);
+      for (int i = j + 1; i < m; ++i) {
+        double v = G[j][i];
+        for (int k = 0; k < j; ++k) v -= R[k][j] * R[k][i];
+        R[j][i] = v / R[j][j];
+      }
+    }
+    if (!ok) atomicOr(err, DEVERR_AMG_DIAG);
+    for (int64_t p = arp[a]; p < arp[a + 1]; ++p)
+      for (int c = 0; c < bs; ++c) {
+        const int64_t i = (int64_t)acol[p] * bs + c;
+        const double *x = B + i * m;
+        double q[kMaxM];
+        for (int j = 0; j < m; ++j) {      // q R = x
+          double v = x[j];
+          for (int k = 0; k < j; ++k) v -= q[k] * R[k][j];
+          q[j] = v / R[j][j];
+        }
+        const int64_t o = trp[i];
+        for (int j = 0; j < m; ++j) {
+          tcol[o + j] = (int32_t)(a * m + j);
+          tval[o + j] = q[j];
+        }
+      }
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k < m; ++k) Bc[(a * m + j) * m + k] = k >= j ? R[j][k] : 0.0;
+  }
+}
+
+// C = X - w Y for CSR matrices with sorted rows (union pattern).
+template <bool kFill>
+__global__ void k_sub_rows(int64_t rows, const int64_t *__restrict__ xrp, const int32_t *__restrict__ xc,
+                           const double *__restrict__ xv, const int64_t *__restrict__ yrp,
+                           const int32_t *__restrict__ yc, const double *__restrict__ yv, double w, int64_t *cnt,
+                           const int64_t *__restrict__ crp, int32_t *cc, double *cv) {
+  ROWS_LOOP(i, rows) {
+    int64_t p = xrp[i], q = yrp[i];
+    const int64_t p1 = xrp[i + 1], q1 = yrp[i + 1];
+    int64_t o = kFill ? crp[i] : 0;
+    int64_t t = 0;
+    while (p < p1 || q < q1) {
+      const int32_t a = p < p1 ? xc[p] : INT32_MAX, b = q < q1 ? yc[q] : INT32_MAX;
+      const int32_t c = a < b ? a : b;
+      double v = 0.0;
+      if (a == c) v += xv[p++];
+      if (b == c) v -= w * yv[q++];
+      if (kFill) {
+        cc[o + t] = c;
+        cv[o + t] = v;
+      }
+      ++t;
+    }
+    if (!kFill) cnt[i] = t;
+  }
+}
+
+// max_i sum_j |a_ij| (as the bit pattern of a non-negative double)
+__global__ void k_abs_rowsum_max(int64_t rows, const int64_t *__restrict__ rp, const double *__restrict__ val,
+                                 unsigned long long *mx) {
+  double m = 0.0;
+  ROWS_LOOP(i, rows) {
+    double s = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s += fabs(val[p]);
+    m = fmax(m, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
+}
+
+// ---- Lanczos ----
+__global__ void k_start_vec(int64_t n, double *v) {
+  ROWS_LOOP(i, n) v[i] = 2.0 * ((double)(splitmix64((uint64_t)i) >> 11) * 0x1p-53) - 1.0;
+}
+
+__global__ void k_csr_spmv(int64_t rows, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ x, double *y) {
+  ROWS_LOOP(i, rows) {
+    double s = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s += val[p] * x[col[p]];
+    y[i] = s;
+  }
+}
+
+constexpr int kDotBlocks = 256;
+// part[j * kDotBlocks + block] = partial sum of V_j . w (V column-major, n rows)
+__global__ void __launch_bounds__(256) k_dots_part(int64_t n, int K, const double *__restrict__ V,
+                                                   const double *__restrict__ w, double *part) {
+  __shared__ double sh[8];
+  for (int j = 0; j < K; ++j) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      s += V[(int64_t)j * n + i] * w[i];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+      part[j * kDotBlocks + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_dots_fin(int K, const double *__restrict__ part, double *out) {
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int b = 0; b < kDotBlocks; ++b) t += part[threadIdx.x * kDotBlocks + b];
+    out[threadIdx.x] = t;
+  }
+}
+
+// w -= sum_j h_j V_j (j in order)
+__global__ void k_sub_proj(int64_t n, int K, const double *__restrict__ V, const double *__restrict__ hcoef,
+                           double *w) {
+  ROWS_LOOP(i, n) {
+    double v = w[i];
+    for (int j = 0; j < K; ++j) v -= hcoef[j] * V[(int64_t)j * n + i];
+    w[i] = v;
+  }
+}
+
+__global__ void k_scale_copy(int64_t n, const double *__restrict__ a, const double *__restrict__ s, double *b) {
+  const double f = 1.0 / sqrt(s[0]);
+  ROWS_LOOP(i, n) b[i] = a[i] * f;
+}
+
+// Block-Jacobi steps of the cycle (y indexes rows; I = i / bs):
+//   mode 0: y = s D r;  mode 1: y = x + s D r;  mode 2: y = x + c (x - xp) + s D r (xp == nullptr: 0)
+__global__ void __launch_bounds__(256) k_blk_apply(int64_t n, int bs, const double *__restrict__ D, double s,
+                                                   const double *__restrict__ r, const double *__restrict__ x,
+                                                   const double *__restrict__ xp, double c, double *y, int mode,
+                                                   const double *sc) {
+  if (cycle_done(sc)) return;
+  ROWS_LOOP(i, n) {
+    const int64_t I = i / bs;
+    const int q = (int)(i - I * bs);
+    const double *Dr = D + I * bs * bs + q * bs;
+    const double *rr = r + I * bs;
+    double t = 0.0;
+    for (int k = 0; k < bs; ++k) t += Dr[k] * rr[k];
+    t *= s;
+    if (mode == 0) y[i] = t;
+    else if (mode == 1) y[i] = x[i] + t;
+    else y[i] = x[i] + c * (x[i] - (xp ? xp[i] : 0.0)) + t;
+  }
+}
+
+__global__ void k_pin_row(int n, int k, double *M) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (i != k) {
+      M[(int64_t)k * n + i] = 0.0;
+      M[(int64_t)i * n + k] = 0.0;
+    }
+  }
+}
+
 // ------------------------------------------------------------ host --------
 // Row counts cnt[rows] -> CSR with that pattern (row pointers from the scan).
 static vem_status csr_layout(vem_handle *h, CsrBuf &C, int64_t rows, int64_t cols, const int64_t *cnt) {
@@ -1206,12 +1544,15 @@ static vem_status product(vem_handle *h, AmgState *S, const DMat &X, const CsrBu
   return VEM_OK;
 }
 
-// One level: strength, MIS-2, aggregates, P, R and the coarse operator.
-// Returns nc = 0 when the level is not coarsened.
-static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64_t *nc_out) {
+// Strength of connection on the graph of A (|a_ij| >= theta sqrt(a_ii a_jj)
+// with dg the diagonal), the distance-2 maximal independent set in rounds and
+// the three aggregation passes: agg[i] (-1 outside the coarse space), the
+// number of aggregates nc and the two Gershgorin maxima (mx[0]: of D^-1 A,
+// mx[1]: of the filtered D^-1 A^F) as double bit patterns.  mis_rounds: the
+// rounds this graph needed in the last setup (updated).
+static vem_status aggregate_graph(vem_handle *h, AmgState *S, const DMat &A, const double *dg, double theta,
+                                  int32_t *agg, int &mis_rounds, int64_t *nc_out, unsigned long long mx[2]) {
   cudaStream_t s = h->stream;
-  AmgLevel &L = S->lv[l];
-  const DMat A = level_op(S, l);
   const int64_t n = A.rows;
   *nc_out = 0;
   VEM_TRY(grow(h, S->flag, S->c_flag, (size_t)A.stored));
@@ -1220,13 +1561,12 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)n + 1));
   VEM_TRY(grow(h, S->scn, S->c_scn, (size_t)n + 1));
   VEM_TRY(grow(h, S->agg1, S->c_agg1, (size_t)n));
-  VEM_TRY(grow(h, L.agg, L.c_agg, (size_t)n));
   const int g = rows_grid(n);
 
   // strength and the Gershgorin maxima (diagonal and dinv already computed)
   VEM_CUDA(h, cudaMemsetAsync(S->ctr, 0, sizeof(unsigned long long) * (kMaxRounds + 4), s));
   count_launch();
-  k_amg_strength<<<g, 256, 0, s>>>(A, S->dg, theta, S->flag, S->nstr, S->ctr);
+  k_amg_strength<<<g, 256, 0, s>>>(A, dg, theta, S->flag, S->nstr, S->ctr);
   // MIS-2 rounds.  The host reads the undecided counts after a batch of
   // rounds: first as many as this level needed in the last setup (rounds
   // after the set is complete change nothing), then two at a time.
@@ -1234,7 +1574,7 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   k_mis_init<<<g, 256, 0, s>>>(n, S->tup);
   uint64_t *t1 = S->tup + n;
   int round = 0;
-  int batch = std::max(2, L.mis_rounds);
+  int batch = std::max(2, mis_rounds);
   int needed = 0;
   while (needed == 0) {
     if (round + batch > kMaxRounds) return fail(h, VEM_ERR_CUDA, "AMG aggregation did not finish in %d rounds", kMaxRounds);
@@ -1252,9 +1592,8 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
       if (und[k] == 0) needed = round - batch + k + 1;
     batch = 2;
   }
-  L.mis_rounds = needed;
-  unsigned long long mx[2] = {0, 0};
-  VEM_CUDA(h, cudaMemcpyAsync(mx, S->ctr, sizeof(mx), cudaMemcpyDeviceToHost, s));
+  mis_rounds = needed;
+  VEM_CUDA(h, cudaMemcpyAsync(mx, S->ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   // aggregates
   count_launch();
   k_agg_root<<<g, 256, 0, s>>>(n, S->tup, S->nstr, S->cnt);
@@ -1263,13 +1602,29 @@ static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64
   count_launch();
   k_agg_pass1<<<g, 256, 0, s>>>(A, S->flag, S->tup, S->nstr, S->scn, S->agg1);
   count_launch();
-  k_agg_pass2<<<g, 256, 0, s>>>(A, S->flag, S->nstr, S->agg1, L.agg, S->cnt);
+  k_agg_pass2<<<g, 256, 0, s>>>(A, S->flag, S->nstr, S->agg1, agg, S->cnt);
   int64_t nfree = 0;
   VEM_TRY(scan_counts(h, n, S->cnt, S->scn, &nfree));
   count_launch();
-  k_agg_pass3<<<g, 256, 0, s>>>(n, nroot, S->nstr, S->scn, L.agg);
+  k_agg_pass3<<<g, 256, 0, s>>>(n, nroot, S->nstr, S->scn, agg);
   VEM_CUDA(h, cudaGetLastError());
-  const int64_t nc = nroot + nfree;
+  *nc_out = nroot + nfree;
+  return VEM_OK;
+}
+
+// One level: strength, MIS-2, aggregates, P, R and the coarse operator.
+// Returns nc = 0 when the level is not coarsened.
+static vem_status coarsen(vem_handle *h, AmgState *S, int l, double theta, int64_t *nc_out) {
+  cudaStream_t s = h->stream;
+  AmgLevel &L = S->lv[l];
+  const DMat A = level_op(S, l);
+  const int64_t n = A.rows;
+  *nc_out = 0;
+  VEM_TRY(grow(h, L.agg, L.c_agg, (size_t)n));
+  const int g = rows_grid(n);
+  unsigned long long mx[2] = {0, 0};
+  int64_t nc = 0;
+  VEM_TRY(aggregate_graph(h, S, A, S->dg, theta, L.agg, L.mis_rounds, &nc, mx));
   if (nc == 0 || 5 * nc > 4 * n) return VEM_OK;
   const double rho = bits_to_double(mx[0]), rhof = bits_to_double(mx[1]);
   L.rho = rho;
@@ -1375,6 +1730,7 @@ vem_status amg_setup(vem_handle *h, AmgState *&slot, const SellMat &Sm, const fl
   S->S0_val32 = S_val32;
   S->pin_last = pin_last;
   S->smoother = smoother;
+  S->block = false;
   if (fp32 && !S_val32) return fail(h, VEM_ERR_BAD_INPUT, "FP32 AMG cycle without FP32 values of the operator");
   cudaStream_t s = h->stream;
   VEM_CUDA(h, cudaEventRecord(h->ev2, s));
@@ -1456,7 +1812,338 @@ vem_status amg_setup(vem_handle *h, AmgState *&slot, const SellMat &Sm, const fl
   return VEM_OK;
 }
 
+// ------------------------------------------------- point-block setup ------
+// X^T of a CSR matrix with cols columns, rows sorted by column.
+static vem_status transpose_csr(vem_handle *h, AmgState *S, const CsrBuf &X, int64_t cols, CsrBuf &XT) {
+  cudaStream_t s = h->stream;
+  const int g = rows_grid(X.rows);
+  VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)cols + 1));
+  VEM_CUDA(h, cudaMemsetAsync(S->cnt, 0, sizeof(int64_t) * cols, s));
+  count_launch();
+  k_t_count<<<g, 256, 0, s>>>(X.rows, X.rp, X.col, reinterpret_cast<unsigned long long *>(S->cnt));
+  VEM_TRY(csr_layout(h, XT, cols, X.rows, S->cnt));
+  VEM_TRY(grow(h, S->cur, S->c_cur, (size_t)cols + 1));
+  VEM_CUDA(h, cudaMemcpyAsync(S->cur, XT.rp, sizeof(int64_t) * cols, cudaMemcpyDeviceToDevice, s));
+  count_launch();
+  k_t_fill<<<g, 256, 0, s>>>(X.rows, X.rp, X.col, X.val, reinterpret_cast<unsigned long long *>(S->cur), XT.col,
+                             XT.val);
+  VEM_TRY(sort_rows(h, S, cols, XT.rp, XT.col, XT.val));
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
+// A CSR buffer with exactly rows x (entries per row) stored entries, for
+// matrices whose layout a kernel writes directly.
+static vem_status csr_fixed(vem_handle *h, CsrBuf &C, int64_t rows, int64_t cols, int64_t nnz) {
+  VEM_TRY(grow(h, C.rp, C.c_rp, (size_t)rows + 1));
+  if (!C.col || (size_t)nnz + 1 > C.c_nz) {
+    dfree(h, C.col);
+    dfree(h, C.val);
+    C.col = nullptr;
+    C.val = nullptr;
+    C.c_nz = 0;
+    const size_t c = (size_t)nnz + (size_t)nnz / 4 + 64;
+    VEM_TRY(dalloc_n(h, &C.col, c));
+    VEM_TRY(dalloc_n(h, &C.val, c));
+    C.c_nz = c;
+  }
+  C.rows = rows;
+  C.cols = cols;
+  C.nnz = nnz;
+  C.lanes = lanes_for(rows, nnz);
+  return VEM_OK;
+}
+
+// Largest eigenvalue of the symmetric tridiagonal matrix (alpha, beta) by
+// cyclic Jacobi rotations on its dense form (k <= 11).
+static double tridiag_max_eig(const std::vector<double> &al, const std::vector<double> &be) {
+  const int k = (int)al.size();
+  double M[12][12] = {};
+  for (int i = 0; i < k; ++i) M[i][i] = al[i];
+  for (int i = 0; i + 1 < k; ++i) M[i][i + 1] = M[i + 1][i] = be[i];
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        tot += M[i][j] * M[i][j];
+        if (i != j) off += M[i][j] * M[i][j];
+      }
+    if (off <= 1e-32 * tot) break;
+    for (int p = 0; p < k; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        if (M[p][q] == 0.0) continue;
+        const double th = (M[q][q] - M[p][p]) / (2.0 * M[p][q]);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int r = 0; r < k; ++r) {   // columns p, q
+          const double a = M[r][p], b = M[r][q];
+          M[r][p] = c * a - sn * b;
+          M[r][q] = sn * a + c * b;
+        }
+        for (int r = 0; r < k; ++r) {   // rows p, q
+          const double a = M[p][r], b = M[q][r];
+          M[p][r] = c * a - sn * b;
+          M[q][r] = sn * a + c * b;
+        }
+      }
+  }
+  double mx = M[0][0];
+  for (int i = 1; i < k; ++i) mx = std::max(mx, M[i][i]);
+  return mx;
+}
+
+// Largest Ritz value of C after `steps` Lanczos steps (full
+// reorthogonalisation by one classical Gram-Schmidt pass, as stated above).
+static vem_status lanczos_max(vem_handle *h, AmgState *S, const CsrBuf &C, int steps, double *ritz) {
+  cudaStream_t s = h->stream;
+  const int64_t n = C.rows;
+  if (steps > n) steps = (int)n;
+  VEM_TRY(grow(h, S->lz, S->c_lz, (size_t)n * (steps + 2)));
+  VEM_TRY(grow(h, S->lpart, S->c_lpart, (size_t)kDotBlocks * (steps + 1) + 16));
+  double *V = S->lz, *w = S->lz + (size_t)n * (steps + 1);
+  double *hd = S->lpart + (size_t)kDotBlocks * (steps + 1);
+  const int g = rows_grid(n);
+  count_launch();
+  k_start_vec<<<g, 256, 0, s>>>(n, w);
+  count_launch();
+  k_dots_part<<<kDotBlocks, 256, 0, s>>>(n, 1, w, w, S->lpart);
+  count_launch();
+  k_dots_fin<<<1, 32, 0, s>>>(1, S->lpart, hd);
+  count_launch();
+  k_scale_copy<<<g, 256, 0, s>>>(n, w, hd, V);
+  std::vector<double> al, be;
+  double hh[16];
+  for (int k = 0; k < steps; ++k) {
+    count_launch();
+    k_csr_spmv<<<g, 256, 0, s>>>(n, C.rp, C.col, C.val, V + (size_t)k * n, w);
+    count_launch();
+    k_dots_part<<<kDotBlocks, 256, 0, s>>>(n, k + 1, V, w, S->lpart);
+    count_launch();
+    k_dots_fin<<<1, 32, 0, s>>>(k + 1, S->lpart, hd);
+    count_launch();
+    k_sub_proj<<<g, 256, 0, s>>>(n, k + 1, V, hd, w);
+    count_launch();
+    k_dots_part<<<kDotBlocks, 256, 0, s>>>(n, 1, w, w, S->lpart);
+    count_launch();
+    k_dots_fin<<<1, 32, 0, s>>>(1, S->lpart, hd + k + 1);
+    VEM_CUDA(h, cudaMemcpyAsync(hh, hd, sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+    const double a = hh[k], b = std::sqrt(hh[k + 1]);
+    al.push_back(a);
+    if (b <= 1e-12 * std::fabs(a) || k == steps - 1) break;
+    be.push_back(b);
+    count_launch();
+    k_scale_copy<<<g, 256, 0, s>>>(n, w, hd + k + 1, V + (size_t)(k + 1) * n);
+  }
+  VEM_CUDA(h, cudaGetLastError());
+  *ritz = tridiag_max_eig(al, be);
+  return VEM_OK;
+}
+
+// Diagonal blocks, their inverses and the spectral estimate of D^-1 A for
+// level l (block size L.bs).
+static vem_status block_level_setup(vem_handle *h, AmgState *S, int l) {
+  cudaStream_t s = h->stream;
+  AmgLevel &L = S->lv[l];
+  const DMat A = level_op(S, l);
+  const int bs = L.bs;
+  const int64_t n = L.n, nb = n / bs;
+  VEM_TRY(grow(h, L.dblk, L.c_dblk, (size_t)nb * bs * bs));
+  VEM_TRY(grow(h, L.lblk, L.c_lblk, (size_t)nb * bs * bs));
+  count_launch();
+  k_blk_diag<<<rows_grid(nb), 256, 0, s>>>(nb, bs, A, L.dblk, L.lblk, h->d_err);
+  VEM_TRY(check_device_errors(h, "point-block AMG diagonal blocks"));
+  // C = L^-1 (A L^-T)
+  VEM_TRY(csr_fixed(h, S->bLm, n, n, n * bs));
+  VEM_TRY(csr_fixed(h, S->bLmT, n, n, n * bs));
+  count_launch();
+  k_blkdiag_rows<<<rows_grid(n), 256, 0, s>>>(n, bs, L.lblk, 0, S->bLm.rp, S->bLm.col, S->bLm.val);
+  count_launch();
+  k_blkdiag_rows<<<rows_grid(n), 256, 0, s>>>(n, bs, L.lblk, 1, S->bLmT.rp, S->bLmT.col, S->bLmT.val);
+  VEM_TRY(product(h, S, A, S->bLmT, S->bY, false));
+  VEM_TRY(product(h, S, dview(S->bLm), S->bY, S->bC, false));
+  unsigned long long *mx = S->ctr + kMaxRounds + 1;
+  VEM_CUDA(h, cudaMemsetAsync(mx, 0, sizeof(*mx), s));
+  count_launch();
+  k_abs_rowsum_max<<<rows_grid(n), 256, 0, s>>>(n, S->bC.rp, S->bC.val, mx);
+  unsigned long long gb = 0;
+  VEM_CUDA(h, cudaMemcpyAsync(&gb, mx, sizeof(gb), cudaMemcpyDeviceToHost, s));
+  double ritz = 0.0;
+  VEM_TRY(lanczos_max(h, S, S->bC, 10, &ritz));   // synchronises
+  const double gersh = bits_to_double(gb);
+  L.rho = std::min(gersh, 1.1 * ritz);
+  L.omega = 4.0 / (3.0 * L.rho);
+  VEM_TRY(check_device_errors(h, "point-block AMG spectral estimate"));
+  return VEM_OK;
+}
+
+// One point-block level: block graph, aggregates, tentative and smoothed
+// prolongators, restriction and the coarse operator.  nc = 0: not coarsened.
+static vem_status block_coarsen(vem_handle *h, AmgState *S, int l, double theta, const double *Bl, int64_t *nc_out) {
+  cudaStream_t s = h->stream;
+  AmgLevel &L = S->lv[l];
+  const DMat A = level_op(S, l);
+  const int bs = L.bs, m = S->m;
+  const int64_t n = L.n, nb = n / bs;
+  *nc_out = 0;
+  // N = sqrt(Q^T (A o A) Q)
+  VEM_TRY(grow(h, S->sq, S->c_sq, (size_t)std::max<int64_t>(A.stored, 1)));
+  count_launch();
+  k_square<<<rows_grid(A.stored), 256, 0, s>>>(A.stored, A.val, S->sq);
+  DMat A2 = A;
+  A2.val = S->sq;
+  VEM_TRY(csr_fixed(h, S->bQ, n, nb, n));
+  VEM_TRY(csr_fixed(h, S->bQT, nb, n, n));
+  count_launch();
+  k_member_rows<<<rows_grid(n), 256, 0, s>>>(n, bs, S->bQ.rp, S->bQ.col, S->bQ.val);
+  count_launch();
+  k_member_cols<<<rows_grid(nb), 256, 0, s>>>(nb, bs, S->bQT.rp, S->bQT.col, S->bQT.val);
+  VEM_TRY(product(h, S, A2, S->bQ, S->bAQ, l == 0));
+  VEM_TRY(product(h, S, dview(S->bQT), S->bAQ, S->bN, false));
+  count_launch();
+  k_sqrt_inplace<<<rows_grid(S->bN.nnz), 256, 0, s>>>(S->bN.nnz, S->bN.val);
+  // aggregates of the block graph
+  const DMat Nv = dview(S->bN);
+  VEM_TRY(grow(h, S->dgb, S->c_dgb, (size_t)nb));
+  VEM_TRY(grow(h, S->dgbi, S->c_dgbi, (size_t)nb));
+  count_launch();
+  k_amg_diag<<<rows_grid(nb), 256, 0, s>>>(Nv, S->dgb, S->dgbi, h->d_err);
+  VEM_TRY(grow(h, L.agg, L.c_agg, (size_t)nb));
+  unsigned long long mx[2] = {0, 0};
+  int64_t nc = 0;
+  VEM_TRY(aggregate_graph(h, S, Nv, S->dgb, theta, L.agg, L.mis_rounds, &nc, mx));
+  if (nc == 0 || 5 * nc > 4 * nb) return VEM_OK;
+  // members of every aggregate in increasing block order
+  VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)nb + 1));
+  count_launch();
+  k_agg_count<<<rows_grid(nb), 256, 0, s>>>(nb, L.agg, S->cnt);
+  VEM_TRY(csr_layout(h, S->bAgg, nb, nc, S->cnt));
+  count_launch();
+  k_agg_fill<<<rows_grid(nb), 256, 0, s>>>(nb, L.agg, S->bAgg.rp, S->bAgg.col, S->bAgg.val);
+  VEM_TRY(transpose_csr(h, S, S->bAgg, nc, S->bAggT));
+  // T and the coarse near-null space
+  AmgLevel &Cl = S->lv[l + 1];
+  VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)n + 1));
+  count_launch();
+  k_tent_count<<<rows_grid(n), 256, 0, s>>>(n, bs, m, L.agg, S->cnt);
+  VEM_TRY(csr_layout(h, S->bT, n, nc * m, S->cnt));
+  VEM_TRY(grow(h, Cl.bns, Cl.c_bns, (size_t)nc * m * m));
+  count_launch();
+  k_tent<<<rows_grid(nc), 256, 0, s>>>(nc, bs, m, S->bAggT.rp, S->bAggT.col, Bl, S->bT.rp, S->bT.col, S->bT.val,
+                                       Cl.bns, h->d_err);
+  VEM_TRY(check_device_errors(h, "point-block AMG tentative prolongator"));
+  // P = T - omega D^-1 (A T)
+  VEM_TRY(product(h, S, A, S->bT, S->bY, l == 0));
+  VEM_TRY(csr_fixed(h, S->bLm, n, n, n * bs));
+  count_launch();
+  k_blkdiag_rows<<<rows_grid(n), 256, 0, s>>>(n, bs, L.dblk, 0, S->bLm.rp, S->bLm.col, S->bLm.val);
+  VEM_TRY(product(h, S, dview(S->bLm), S->bY, S->bZ, false));
+  count_launch();
+  k_sub_rows<false><<<rows_grid(n), 256, 0, s>>>(n, S->bT.rp, S->bT.col, S->bT.val, S->bZ.rp, S->bZ.col, S->bZ.val,
+                                                 L.omega, S->cnt, nullptr, nullptr, nullptr);
+  VEM_TRY(csr_layout(h, L.P, n, nc * m, S->cnt));
+  count_launch();
+  k_sub_rows<true><<<rows_grid(n), 256, 0, s>>>(n, S->bT.rp, S->bT.col, S->bT.val, S->bZ.rp, S->bZ.col, S->bZ.val,
+                                                L.omega, nullptr, L.P.rp, L.P.col, L.P.val);
+  // R = P^T, A P, R (A P)
+  VEM_TRY(transpose_csr(h, S, L.P, nc * m, L.R));
+  VEM_TRY(product(h, S, A, L.P, S->AP, l == 0));
+  VEM_TRY(product(h, S, dview(L.R), S->AP, Cl.A, false));
+  VEM_TRY(check_device_errors(h, "point-block AMG Galerkin product"));
+  L.Rs.m.rows = 0;
+  L.Ps.m.rows = 0;
+  Cl.As.m.rows = 0;
+  if (L.R.rows >= kSellMinRows) VEM_TRY(csr_to_sell(h, S, L.R, L.Rs));
+  if (L.P.rows >= kSellMinRows) VEM_TRY(csr_to_sell(h, S, L.P, L.Ps));
+  if (nc * m >= kSellMinRows) VEM_TRY(csr_to_sell(h, S, Cl.A, Cl.As));
+  L.nc = nc * m;
+  *nc_out = nc;
+  return VEM_OK;
+}
+
+vem_status amg_setup_block(vem_handle *h, AmgState *&slot, const SellMat &A0, int bs0, const double *B0, int m,
+                           bool pin_last, int smoother) {
+  if (!slot) slot = new AmgState();
+  AmgState *S = slot;
+  S->valid = false;
+  S->fp32 = false;
+  S->S0_val32 = nullptr;
+  S->pin_last = pin_last;
+  S->smoother = smoother;
+  S->block = true;
+  S->m = m;
+  S->B0 = B0;
+  if (bs0 < 1 || bs0 > kMaxBs || m < 1 || m > kMaxM || A0.rows % bs0)
+    return fail(h, VEM_ERR_UNSUPPORTED, "point-block AMG: block size %d, near-null space of %d vectors", bs0, m);
+  cudaStream_t s = h->stream;
+  VEM_CUDA(h, cudaEventRecord(h->ev2, s));
+  if (!S->ctr) VEM_TRY(dalloc_n(h, &S->ctr, kMaxRounds + 4));
+  S->S0 = A0;
+  S->nlev = 1;
+  double theta = kTheta0;
+  int bs = bs0;
+  const double *Bl = B0;
+  for (int l = 0;; ++l) {
+    VEM_TRY(level_vectors(h, S, l));
+    AmgLevel &L = S->lv[l];
+    L.bs = bs;
+    VEM_TRY(block_level_setup(h, S, l));
+    if (L.n / bs <= kCoarseMax || l + 1 == kMaxLevels) break;
+    int64_t nc = 0;
+    VEM_TRY(block_coarsen(h, S, l, theta, Bl, &nc));
+    if (nc == 0) break;
+    S->nlev = l + 2;
+    theta *= 0.5;
+    bs = m;
+    Bl = S->lv[l + 1].bns;
+  }
+  AmgLevel &C = S->lv[S->nlev - 1];
+  const DMat CA = level_op(S, S->nlev - 1);
+  for (int l = 0; l < S->nlev; ++l) {
+    AmgLevel &L = S->lv[l];
+    if (S->smoother == kSmoothChebyshev && l + 1 < S->nlev) {
+      const double hi = L.rho, lo = hi / 10.0;
+      const double th = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = th / delta;
+      const double rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
+      L.cheb_c = rho1 * rho0;
+      L.cheb_theta = 1.0 / th;
+      L.cheb_w2 = 2.0 * rho1 / delta;
+    }
+    // scalar omega D^-1 for coarsest-level sweeps (coarsest above the dense size)
+    VEM_TRY(grow(h, L.wd, L.c_wd, (size_t)L.n));
+    count_launch();
+    k_scale_into<<<rows_grid(L.n), 256, 0, s>>>(L.n, L.dinv, L.omega, L.wd);
+  }
+  if (C.n <= kDenseMax) {
+    VEM_TRY(grow(h, S->cinv, S->c_cinv, (size_t)C.n * C.n));
+    count_launch();
+    k_dense_from<<<rows_grid(C.n), 256, 0, s>>>(CA, S->cinv);
+    if (S->pin_last) {
+      // the constant pressure is carried by the first component of every
+      // block on every level: pin that component of the last block
+      count_launch();
+      k_pin_row<<<1, 256, 0, s>>>((int)C.n, (int)(C.n - C.bs), S->cinv);
+    }
+    count_launch();
+    k_gauss_jordan<<<1, 256, 0, s>>>((int)C.n, S->cinv, h->d_err);
+    S->csweeps = 0;
+  } else {
+    S->csweeps = kCoarseSweeps;
+  }
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_TRY(check_device_errors(h, "point-block AMG setup"));
+  VEM_CUDA(h, cudaEventRecord(h->ev3, s));
+  VEM_CUDA(h, cudaEventSynchronize(h->ev3));
+  float ms = 0.f;
+  VEM_CUDA(h, cudaEventElapsedTime(&ms, h->ev2, h->ev3));
+  S->t_setup_ms = ms;
+  S->valid = true;
+  ++S->generation;
+  return VEM_OK;
+}
+
 bool amg_valid(const AmgState *S) { return S && S->valid; }
+bool amg_is_block(const AmgState *S) { return S && S->block; }
 bool amg_is_fp32(const AmgState *S) { return S && S->fp32; }
 int64_t amg_generation(const AmgState *S) { return S ? S->generation : 0; }
 void amg_invalidate(AmgState *S) {
@@ -1518,12 +2205,89 @@ template <class T> static const T *wdcv(const AmgLevel &L);
 template <> const double *wdcv<double>(const AmgLevel &L) { return L.wdc; }
 template <> const float *wdcv<float>(const AmgLevel &L) { return L.wdc32; }
 
+// One block-Jacobi step of the point-block cycle (k_blk_apply modes).
+static void blk_launch(cudaStream_t s, const AmgLevel &L, double scale, const double *r, const double *x,
+                       const double *xp, double c, double *y, int mode, const double *sc) {
+  count_launch();
+  k_blk_apply<<<rows_grid(L.n), 256, 0, s>>>(L.n, L.bs, L.dblk, scale, r, x, xp, c, y, mode, sc);
+}
+
+static void coarsest_solve(vem_handle *h, AmgState *S, int l, const double *b, double *x, const double *sc);
+
+// x = V(b) on level l of a point-block hierarchy (FP64): the cycle of the
+// scalar hierarchy with the diagonal replaced by the bs x bs blocks.
+static void bcycle(vem_handle *h, AmgState *S, int l, const double *b, double *x, const double *sc) {
+  cudaStream_t s = h->stream;
+  AmgLevel &L = S->lv[l];
+  if (l == S->nlev - 1) {
+    coarsest_solve(h, S, l, b, x, sc);
+    return;
+  }
+  AmgLevel &C = S->lv[l + 1];
+  double *xa = L.vx<double>(0), *r = L.vx<double>(3);
+  double *cb = C.vx<double>(2), *cx = C.vx<double>(1);
+  const bool tm = l == 0 && S->timing;
+  auto mark = [&](int k) {
+    if (tm) cudaEventRecord(S->tev[k], s);
+  };
+  auto restrict_and_recurse = [&](const double *res) {
+    if (L.Rs.m.rows) sell_launch<kApply>(s, L.Rs.m, vals<double>(L.Rs), res, (const double *)nullptr,
+                                         (const double *)nullptr, cb, sc);
+    else csr_launch<kApply>(s, L.R, res, (const double *)nullptr, (const double *)nullptr, cb, sc);
+    bcycle(h, S, l + 1, cb, cx, sc);
+  };
+  auto prolong_add = [&](double *y) {
+    if (L.Ps.m.rows) sell_launch<kAdd>(s, L.Ps.m, vals<double>(L.Ps), (const double *)cx, (const double *)nullptr,
+                                       (const double *)nullptr, y, sc);
+    else csr_launch<kAdd>(s, L.P, (const double *)cx, (const double *)nullptr, (const double *)nullptr, y, sc);
+  };
+  if (S->smoother == kSmoothChebyshev) {
+    double *xc = L.vx<double>(4);
+    const double c = L.cheb_c, t = L.cheb_theta, w2 = L.cheb_w2;
+    blk_launch(s, L, t, b, nullptr, nullptr, 0.0, xa, 0, sc);                       // xa = D^-1 b / theta
+    op_launch<kResid>(s, S, l, (const double *)xa, b, (const double *)nullptr, r, sc);
+    blk_launch(s, L, w2, r, xa, nullptr, c, xc, 2, sc);                             // xc = xa + c xa + w2 D^-1 r
+    mark(0);
+    op_launch<kResid>(s, S, l, (const double *)xc, b, (const double *)nullptr, r, sc);
+    mark(1);
+    restrict_and_recurse(r);
+    prolong_add(xc);
+    mark(2);
+    op_launch<kResid>(s, S, l, (const double *)xc, b, (const double *)nullptr, r, sc);
+    mark(3);
+    blk_launch(s, L, t, r, xc, nullptr, 0.0, xa, 1, sc);                            // xa = xc + D^-1 r / theta
+    op_launch<kResid>(s, S, l, (const double *)xa, b, (const double *)nullptr, r, sc);
+    blk_launch(s, L, w2, r, xa, xc, c, x, 2, sc);                                   // x = xa + c (xa - xc) + ...
+  } else {
+    blk_launch(s, L, L.omega, b, nullptr, nullptr, 0.0, xa, 0, sc);                 // xa = omega D^-1 b
+    mark(0);
+    op_launch<kResid>(s, S, l, (const double *)xa, b, (const double *)nullptr, r, sc);
+    mark(1);
+    restrict_and_recurse(r);
+    prolong_add(xa);
+    mark(2);
+    op_launch<kResid>(s, S, l, (const double *)xa, b, (const double *)nullptr, r, sc);
+    mark(3);
+    blk_launch(s, L, L.omega, r, xa, nullptr, 0.0, x, 1, sc);                       // x = xa + omega D^-1 r
+  }
+  if (tm) {
+    S->timing = false;
+    S->timed = true;
+  }
+}
+
 // x = V(b) on level l, values and vectors in T; the level's output is Ty
 // (FP64 on level 0 of an FP32 cycle, so u needs no conversion pass).
 template <class T, class Ty>
 static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const double *sc) {
   cudaStream_t s = h->stream;
   AmgLevel &L = S->lv[l];
+  if constexpr (sizeof(T) == sizeof(double) && sizeof(Ty) == sizeof(double)) {
+    if (S->block) {
+      bcycle(h, S, l, (const double *)b, (double *)x, sc);
+      return;
+    }
+  }
   const T *wd = wdv<T>(L);
   if (l == S->nlev - 1) {
     if (S->csweeps == 0) {
@@ -1609,6 +2373,27 @@ static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const do
   }
 }
 
+// The coarsest level of an FP64 cycle: the dense inverse, or damped-Jacobi
+// sweeps from zero.
+static void coarsest_solve(vem_handle *h, AmgState *S, int l, const double *b, double *x, const double *sc) {
+  cudaStream_t s = h->stream;
+  AmgLevel &L = S->lv[l];
+  if (S->csweeps == 0) {
+    const int g = (int)std::min<int64_t>((L.n + 7) / 8, 1024);
+    count_launch();
+    k_vc_dense<double><<<g, 256, 0, s>>>((int)L.n, S->cinv, b, x, sc);
+    return;
+  }
+  double *xa = L.vx<double>(0), *xb = L.vx<double>(3);
+  count_launch();
+  k_vc_pre<double><<<rows_grid(L.n), 256, 0, s>>>(L.n, b, L.wd, xa, sc);
+  for (int k = 1; k < S->csweeps; ++k) {
+    if (k == S->csweeps - 1) op_launch<kPost>(s, S, l, (const double *)xa, b, (const double *)L.wd, x, sc);
+    else op_launch<kPost>(s, S, l, (const double *)xa, b, (const double *)L.wd, xb, sc);
+    std::swap(xa, xb);
+  }
+}
+
 void amg_vcycle(vem_handle *h, AmgState *S, const double *b, double *x, const double *sc) {
   if (!S->fp32) {
     cycle<double, double>(h, S, 0, b, x, sc);
@@ -1652,8 +2437,8 @@ vem_status amg_level_copy(vem_handle *h, AmgState *S, int l, int64_t *rp, int32_
     else VEM_TRY(csr_to_host(h, L.A, rp, col, val));
   }
   const bool coarse = l + 1 < S->nlev;
-  if (agg && coarse)
-    VEM_CUDA(h, cudaMemcpy(agg, L.agg, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost));
+  if (agg && coarse)   // one aggregate per point block
+    VEM_CUDA(h, cudaMemcpy(agg, L.agg, sizeof(int32_t) * (S->block ? L.n / L.bs : L.n), cudaMemcpyDeviceToHost));
   if ((prp || pcol || pval) && coarse) VEM_TRY(csr_to_host(h, L.P, prp, pcol, pval));
   return VEM_OK;
 }

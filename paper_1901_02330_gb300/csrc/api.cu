@@ -141,7 +141,7 @@ static vem_status check_options(vem_handle *h, const vem_options *o) {
     return fail(h, VEM_ERR_BAD_INPUT, "MINRES needs an SPD block-diagonal preconditioner");
   if (!(o->reg_gamma >= 0.0) || !std::isfinite(o->reg_gamma))
     return fail(h, VEM_ERR_BAD_INPUT, "reg_gamma %g", o->reg_gamma);
-  if (o->inner != VEM_INNER_PCG && o->inner != VEM_INNER_AMG)
+  if (o->inner != VEM_INNER_PCG && o->inner != VEM_INNER_AMG && o->inner != VEM_INNER_BLOCK_AMG)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown inner solver %d", o->inner);
   if (o->inner_smoother != VEM_SMOOTH_JACOBI && o->inner_smoother != VEM_SMOOTH_CHEBYSHEV)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown inner smoother %d", o->inner_smoother);
@@ -925,8 +925,8 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   if (!h) return VEM_ERR_BAD_INPUT;
   if (nbatch < 1 || nbatch > 65535) return fail(h, VEM_ERR_BAD_INPUT, "nbatch %lld", (long long)nbatch);
   if (!K || !u_out || !p_out) return fail(h, VEM_ERR_BAD_INPUT, "K / u_out / p_out: NULL");
-  if (h->opt.inner == VEM_INNER_AMG)
-    return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver is single-system (no batched solves)");
+  if (h->opt.inner != VEM_INNER_PCG)
+    return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solvers are single-system (no batched solves)");
   if (h->opt.precond == VEM_PREC_BLOCK_REG)
     return fail(h, VEM_ERR_UNSUPPORTED, "Block-Reg is single-system (no batched solves)");
   if (h->nq > 1) return fail(h, VEM_ERR_UNSUPPORTED, "paper k = 2 in batched solves");
@@ -1202,8 +1202,7 @@ vem_status vem_amg_setup(vem_handle *h, int32_t which) {
   if (!slot) return fail(h, VEM_ERR_BAD_INPUT, "unknown AMG hierarchy %d", which);
   if (!h->assembled) VEM_TRY(assemble_impl(h));
   const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
-  if (which == VEM_AMG_SCHUR)
-    return amg_setup(h, h->amg, h->S, h->S_val32, fp32, h->multiplier, schur_smoother(h));
+  if (which == VEM_AMG_SCHUR) return schur_amg_setup(h, h->S, h->S_val32);
   if (!h->areg_valid || (fp32 && !h->areg_has32)) VEM_TRY(assemble_reg(h, fp32));
   return amg_setup(h, h->amg_reg, h->Areg, h->Areg_val32, fp32, false, kSmoothChebyshev);
 }

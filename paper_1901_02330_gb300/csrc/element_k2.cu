@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_k2(
     const double *__restrict__ f_norm, const double *__restrict__ f_t1, const double *__restrict__ f_diam,
     const double *__restrict__ c_vol, const double *__restrict__ c_cent, const double *__restrict__ c_diam,
     const int32_t *__restrict__ cls_rep, const int64_t *__restrict__ m_off, const int64_t *__restrict__ b_off,
-    double *Mloc, double *Bloc, double *hq_inv, int *err) {
+    double *Mloc, double *Bloc, double *hq_inv, double *pm_hat, int *err) {
   extern __shared__ double sm[];
   const int NUmax = kNfd * max_nf + kNid;
   const int NQmax = 7 * max_nv;
@@ -346,6 +346,13 @@ __global__ void __launch_bounds__(kThreads) k_elem_k2(
     // interior columns of bnd are zero (the interior DOFs have no trace)
     for (int e = tid; e < kT * kNid; e += blockDim.x) bnd[(e / kNid) * NUmax + kNfd * nfc + e % kNid] = 0.0;
     __syncthreads();
+    // pressure DOFs (1/|P|) int q m_a of the fields q = 1 and q = x_j - x_P,j
+    // (translation invariant; the near-null space of S for the point-block AMG)
+    if (pm_hat && tid < 16) {
+      const int a = tid / 4, j = tid % 4;
+      pm_hat[16 * k + tid] = (j == 0 ? Hq[a] : hP * Hq[j * 4 + a]) / vol;
+    }
+    __syncthreads();
     if (tid == 0) gj_inverse(Hp, 10);
     if (tid == 32) gj_inverse(Hq, 4);
     __syncthreads();
@@ -473,8 +480,11 @@ vem_status element_k2(vem_handle *h) {
   const size_t bytes = sizeof(double) * k2_smem_doubles(mx, mv);
   if (h->hq_inv_n < h->ncls) {
     dfree(h, h->hq_inv);
+    dfree(h, h->pm_hat);
     h->hq_inv = nullptr;
+    h->pm_hat = nullptr;
     VEM_TRY(dalloc_n(h, &h->hq_inv, 16 * (size_t)h->ncls));
+    VEM_TRY(dalloc_n(h, &h->pm_hat, 16 * (size_t)h->ncls));
     h->hq_inv_n = h->ncls;
   }
   if (mv > 64 || bytes > 220 * 1024)
@@ -488,7 +498,7 @@ vem_status element_k2(vem_handle *h) {
   k_elem_k2<<<(int)blocks, kThreads, bytes, h->stream>>>(
       h->ncls, mx, mv, h->cf_ptr, h->cf, h->cf_sigma, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm,
       h->f_t1, h->f_diam, h->c_vol, h->c_cent, h->c_diam, h->cls_rep, h->m_off, h->b_off, h->Mloc, h->Bloc,
-      h->hq_inv, h->d_err);
+      h->hq_inv, h->pm_hat, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   return VEM_OK;
 }

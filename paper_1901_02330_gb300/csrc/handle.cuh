@@ -38,6 +38,8 @@ struct vem_handle {
   bool local_ready = false;                      // element matrices of the current coefficients
   // paper k = 2: |P| H_1^-1 per class (the load map) and the cell points
   double *hq_inv = nullptr;
+  double *pm_hat = nullptr;   // K2: per class, the pressure DOFs of 1 and x_j - x_P,j (4 x 4)
+  double *pmodes = nullptr;   // K2: near-null space of S (n_p x 4) for the point-block AMG
   int64_t hq_inv_n = 0;
   int64_t *cqp_off = nullptr;                    // [nc + 1] first point of each cell
   double *cqp_x = nullptr, *cqp_w = nullptr;     // [n_cqp][3], [n_cqp]
@@ -248,6 +250,13 @@ inline int schur_smoother(const vem_handle *h) {
 }
 vem_status amg_setup(vem_handle *h, AmgState *&slot, const SellMat &A0, const float *A0_val32, bool fp32,
                      bool pin_last, int smoother);
+// The point-block hierarchy (FP64) of A0 with bs0 x bs0 blocks and the
+// near-null space B0 (device, rows x m, row-major; kept by reference).
+vem_status amg_setup_block(vem_handle *h, AmgState *&slot, const SellMat &A0, int bs0, const double *B0, int m,
+                           bool pin_last, int smoother);
+bool amg_is_block(const AmgState *S);
+// the hierarchy of S for the options' inner solver (krylov.cu)
+vem_status schur_amg_setup(vem_handle *h, const SellMat &S, const float *S_val32);
 bool amg_valid(const AmgState *S);
 bool amg_is_fp32(const AmgState *S);
 int64_t amg_generation(const AmgState *S);

@@ -22,6 +22,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "geom_device.cuh"
 #include "handle.cuh"
 
 namespace vem {
@@ -436,7 +437,7 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   const double tol2 = h->opt.inner_rtol * h->opt.inner_rtol;
   // the AMG-preconditioned form replaces u = D^-1 r by one V-cycle u = V(r)
   bool amg = false;
-  if constexpr (sizeof(T) == sizeof(double)) amg = h->opt.inner == VEM_INNER_AMG;
+  if constexpr (sizeof(T) == sizeof(double)) amg = h->opt.inner != VEM_INNER_PCG;
   count_launch();
   k_cg_init<T><<<nb, kRedThreads, 0, s>>>(n, b, dinv, x, r, u, p, sv, h->part, sc, h->ctr);
   auto precondition = [&]() {
@@ -544,6 +545,42 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   return VEM_OK;
 }
 
+// The near-null space of S for the paper's k = 2 element: per cell P, the
+// pressure DOFs (1/|P|) int q m_a (eq. presMom) of q = 1, x, y, z, from the
+// class's moments of 1 and x_j - x_P,j (translation invariant) and the cell's
+// barycentre: B[(4P + a) 4 + j].
+__global__ void k_pressure_modes(int64_t nc, const int32_t *__restrict__ cls_of, const double *__restrict__ pm_hat,
+                                 const double *__restrict__ c_cent, double *B) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+    const double *ph = pm_hat + 16 * (int64_t)cls_of[c];
+    const double3 xP = load3(c_cent, c);
+    const double xs[3] = {xP.x, xP.y, xP.z};
+    for (int a = 0; a < 4; ++a)
+      for (int j = 0; j < 4; ++j)
+        B[(4 * c + a) * 4 + j] = j == 0 ? ph[4 * a] : xs[j - 1] * ph[4 * a] + ph[4 * a + j];
+  }
+}
+
+// Build the hierarchy of S for the configured inner solver: the scalar AMG,
+// or the point-block AMG on the 4 x 4 pressure blocks of the k = 2 element.
+vem_status schur_amg_setup(vem_handle *h, const SellMat &S, const float *S_val32) {
+  const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
+  if (h->opt.inner == VEM_INNER_BLOCK_AMG) {
+    if (h->nq != 4)
+      return fail(h, VEM_ERR_UNSUPPORTED, "the point-block AMG inner solver needs the paper's k = 2 element");
+    if (fp32) return fail(h, VEM_ERR_UNSUPPORTED, "the point-block AMG cycle runs in FP64 only");
+    if (!h->pmodes) VEM_TRY(dalloc_n(h, &h->pmodes, 16 * (size_t)h->nc));
+    count_launch();
+    k_pressure_modes<<<grid_for(h->nc, 256), 256, 0, h->stream>>>(h->nc, h->cls_of, h->pm_hat, h->c_cent,
+                                                                   h->pmodes);
+    VEM_CUDA(h, cudaGetLastError());
+    return amg_setup_block(h, h->amg, S, 4, h->pmodes, 4, h->multiplier, schur_smoother(h));
+  }
+  if (h->multiplier && h->nq > 1)
+    return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver with the multiplier needs one pressure DOF per cell");
+  return amg_setup(h, h->amg, S, S_val32, fp32, h->multiplier, schur_smoother(h));
+}
+
 // S x = b with x, b FP64; the solve runs in FP64 or, with the mixed
 // precision option, entirely in FP32 (values, vectors, arithmetic).
 static vem_status pcg_solve(vem_handle *h, const VemOp &op, const double *b, double *x, double *wk, int *iters) {
@@ -553,13 +590,13 @@ static vem_status pcg_solve(vem_handle *h, const VemOp &op, const double *b, dou
     VEM_TRY(neumann_mean_free(h, op.n_p, b, h->bproj));
     b = h->bproj;
   }
-  if (h->opt.inner == VEM_INNER_AMG) {
-    // FP64 CG; with the mixed option the V-cycle runs in FP32
+  if (h->opt.inner == VEM_INNER_AMG || h->opt.inner == VEM_INNER_BLOCK_AMG) {
+    // FP64 CG; with the mixed option the scalar V-cycle runs in FP32
     const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
-    if (h->multiplier && h->nq > 1)
-      return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solver with the multiplier needs one pressure DOF per cell");
-    if (!amg_valid(h->amg) || amg_is_fp32(h->amg) != fp32 || amg_smoother(h->amg) != schur_smoother(h))
-      VEM_TRY(amg_setup(h, h->amg, op.S, op.S_val32, fp32, h->multiplier, schur_smoother(h)));
+    const bool block = h->opt.inner == VEM_INNER_BLOCK_AMG;
+    if (!amg_valid(h->amg) || amg_is_fp32(h->amg) != fp32 || amg_smoother(h->amg) != schur_smoother(h) ||
+        amg_is_block(h->amg) != block)
+      VEM_TRY(schur_amg_setup(h, op.S, op.S_val32));
     return pcg_solve_t<double>(h, op, op.S.val, op.s_dinv, b, x, wk, iters);
   }
   if (h->opt.precision == VEM_PRECISION_MIXED) {

@@ -23,7 +23,7 @@ VEM_ELEMENT_E0, VEM_ELEMENT_K1, VEM_ELEMENT_K2 = 0, 1, 2
 VEM_KRYLOV_MINRES, VEM_KRYLOV_FGMRES = 0, 1
 VEM_PREC_BLOCK_DIAG, VEM_PREC_BLOCK_TRI, VEM_PREC_BLOCK_REG = 0, 1, 2
 VEM_AMG_SCHUR, VEM_AMG_REG = 0, 1
-VEM_INNER_PCG, VEM_INNER_AMG = 0, 1
+VEM_INNER_PCG, VEM_INNER_AMG, VEM_INNER_BLOCK_AMG = 0, 1, 2
 VEM_PRECISION_FP64, VEM_PRECISION_MIXED = 0, 1
 VEM_SMOOTH_JACOBI, VEM_SMOOTH_CHEBYSHEV = 0, 1
 VEM_QP_CELL, VEM_QP_BFACE = 0, 1

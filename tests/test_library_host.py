@@ -91,7 +91,7 @@ BAD_OPTIONS = {
     "reg_gamma<0": dict(reg_gamma=-1.0),
     "reg_gamma-nan": dict(reg_gamma=math.nan),
     "reg_gamma-inf": dict(reg_gamma=math.inf),
-    "inner": dict(inner=2),
+    "inner": dict(inner=3),
     "precision": dict(precision=2),
     "inner_smoother": dict(inner_smoother=2),
     "inner_smoother<0": dict(inner_smoother=-1),
