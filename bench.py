@@ -694,26 +694,37 @@ def run_workload(a):
         # flux block, I / gamma for the pressure block, gamma = h^2.
         mesh = hex_mesh(32, bc=2)
         prob = fields.paper_polynomial_problem()
-        s = vs.Solver(mesh, stream=sid, device_io=1, element=1, krylov=1, precond=vs.VEM_PREC_BLOCK_REG,
-                      restart=30, rtol=1e-8, maxit=4000)
-        s.set_data(prob.f, prob.gD, flux=prob.u)
-        n_u, n_p = s.sizes()
-        u = torch.empty(n_u, dtype=torch.float64, device="cuda")
-        p = torch.empty(n_p, dtype=torch.float64, device="cuda")
+        res = {}
+        for cname, cyc in (("condensed", vs.VEM_REG_CONDENSED), ("scalar_amg", vs.VEM_REG_SCALAR_AMG)):
+            s = vs.Solver(mesh, stream=sid, device_io=1, element=1, krylov=1, precond=vs.VEM_PREC_BLOCK_REG,
+                          restart=30, rtol=1e-8, maxit=4000, reg_cycle=cyc)
+            s.set_data(prob.f, prob.gD, flux=prob.u)
+            n_u, n_p = s.sizes()
+            u = torch.empty(n_u, dtype=torch.float64, device="cuda")
+            p = torch.empty(n_p, dtype=torch.float64, device="cuda")
 
-        def step():
-            s.assemble()
-            return s.solve(u_out=u, p_out=p)[2]
-        ms, st = _timed(step, a.steps, a.warmup, stream)
-        s.close()
+            def step():
+                s.assemble()
+                return s.solve(u_out=u, p_out=p)[2]
+            ms_c, st_c = _timed(step, a.steps, a.warmup, stream)
+            s.close()
+            res[cname] = {"ms_per_step": ms_c, "iterations": st_c["iterations"], "relres": st_c["relres"],
+                          "amg_levels": st_c["amg_levels"], "t_amg_setup_ms": st_c["t_amg_setup_ms"],
+                          "t_solve_ms": st_c["t_solve_ms"], "nnz_reg": st_c["nnz_reg"]}
+            if cname == "condensed":
+                st, ms = st_c, ms_c
         n = n_u + n_p
         line = _line(a, "time-to-solution (rel.res 1e-8) and DOFs/s", n / (ms * 1e-3), "DOFs/s", ms, "f64",
                      {"workload": w, "cells": mesh.n_cells, "dofs_with_multiplier": n + 1,
                       "paper_dofs": 435201, "element": "paper k=1", "bc": "flux on the whole boundary, mean-zero p",
                       "krylov": "FGMRES(30), right preconditioning",
-                      "precond": "Block-Reg (AMG V-cycle of A + B^T B/gamma, Chebyshev(2) smoothing; I/gamma)"},
+                      "precond": "Block-Reg (A + B^T B/gamma by the condensed cycle: interior DOFs eliminated per "
+                                 "cell, point-block AMG V-cycle of the face system with block-Chebyshev smoothing; "
+                                 "I/gamma)"},
                      iterations=st["iterations"], relres=st["relres"], reg_gamma=st["reg_gamma"],
                      nnz_reg=st["nnz_reg"], amg_levels=st["amg_levels"], t_amg_setup_ms=st["t_amg_setup_ms"],
+                     cycles=res,
+                     speedup_condensed_vs_scalar=res["scalar_amg"]["ms_per_step"] / res["condensed"]["ms_per_step"],
                      paper_block_reg_iterations=84,
                      paper_note="paper: 84 GMRES iterations with PETSc GAMG (1 core), T_sol 53 s on 1 core of "
                                 "2x Xeon E5-2683 v4; context only")
@@ -875,7 +886,8 @@ def run_workload(a):
         cases = ([("cube", n) for n in (8, 16, 24, 32, 48)] + [("octa", n) for n in (4, 8, 12, 16)]
                  + [("cvt", n) for n in (1000, 8000, 27000, 64000)])
         precs = {"block_schur": dict(precond=0, inner=vs.VEM_INNER_AMG, inner_rtol=1e-12, inner_maxit=2000),
-                 "block_reg": dict(precond=vs.VEM_PREC_BLOCK_REG)}
+                 "block_reg": dict(precond=vs.VEM_PREC_BLOCK_REG),
+                 "block_reg_condensed": dict(precond=vs.VEM_PREC_BLOCK_REG, reg_cycle=vs.VEM_REG_CONDENSED)}
         for kind, n in cases:
             if kind == "cube":
                 mesh = hex_mesh(n, bc=2)
@@ -907,8 +919,9 @@ def run_workload(a):
         line = _line(a, "GMRES iterations under refinement (Block-Schur, Block-Reg) and DOFs/s",
                      n_all / (total_ms * 1e-3), "DOFs/s", total_ms, "f64",
                      {"workload": w, "element": "paper k=1", "bc": "flux on the whole boundary, mean-zero p",
-                      "precond": "Block-Schur (diag(A), S to 1e-12 by AMG-PCG) and Block-Reg (AMG V-cycle of "
-                                 "A + B^T B/gamma, gamma = h^2)", "krylov": "FGMRES(30), rtol 1e-8"},
+                      "precond": "Block-Schur (diag(A), S to 1e-12 by AMG-PCG) and Block-Reg (A + B^T B/gamma, "
+                                 "gamma = h^2, by the scalar AMG V-cycle and by the condensed point-block cycle)",
+                      "krylov": "FGMRES(30), rtol 1e-8"},
                      runs=rows)
     elif w == "cvt200k-e0-mixed":
         # 200k seeds U[0,1]^3 (seed 0), 10 Lloyd iterations, E0, K = 10^U, U ~ U[-4,4] (seed 1)

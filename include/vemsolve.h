@@ -140,6 +140,18 @@ enum { VEM_PREC_BLOCK_DIAG = 0, VEM_PREC_BLOCK_TRI = 1, VEM_PREC_BLOCK_REG = 2 }
 enum { VEM_INNER_PCG = 0, VEM_INNER_AMG = 1, VEM_INNER_BLOCK_AMG = 2 };
 enum { VEM_PRECISION_FP64 = 0, VEM_PRECISION_MIXED = 1 };
 enum { VEM_SMOOTH_JACOBI = 0, VEM_SMOOTH_CHEBYSHEV = 1 };
+/* Block-Reg's approximate inverse of A_reg (vem_options.reg_cycle):
+ *   SCALAR_AMG  one V-cycle of the scalar smoothed-aggregation AMG of A_reg
+ *               (two Chebyshev steps of Jacobi); FP64 or FP32 (MIXED);
+ *   CONDENSED   the paper's k = 1 element only, FP64: the interior DOFs of
+ *               A_reg, which couple only within their cell, are eliminated
+ *               exactly (3 x 3 blocks A_ii), and the face system
+ *               S_f = A_ff - A_fi A_ii^-1 A_if gets one V-cycle of the
+ *               point-block AMG with the 3 face moments of a face as a
+ *               block, the face DOFs of the three constant fields as
+ *               near-null space and two block-Chebyshev steps; the interior
+ *               DOFs are then recovered.  Symmetric positive definite. */
+enum { VEM_REG_SCALAR_AMG = 0, VEM_REG_CONDENSED = 1 };
 
 typedef struct {
   int element;        /* VEM_ELEMENT_*                                      */
@@ -171,6 +183,7 @@ typedef struct {
                       /* Chebyshev steps of the Jacobi iteration on         */
                       /* [rho/10, rho] (rho the Gershgorin bound of         */
                       /* rho(D^-1 S); the Block-Reg cycle's smoother)       */
+  int reg_cycle;      /* BLOCK_REG: VEM_REG_* (default SCALAR_AMG)          */
 } vem_options;
 
 typedef struct {
@@ -390,6 +403,10 @@ vem_status vem_residual_norm_noalloc(int64_t rows, const int64_t *row_ptr, const
  * vem_amg_levels: *nlev levels (at most 12); rows[l], nnz[l] of each
  * level's operator and nnz_p[l] of its prolongator (0 on the coarsest);
  * arrays of at least 12 entries, any may be NULL.
+ * With reg_cycle = VEM_REG_CONDENSED the VEM_AMG_REG hierarchy is that of
+ * the face system S_f (level 0 has the 3 n_f face rows; one aggregate per
+ * face block) and vem_amg_vcycle_device applies the whole condensed cycle
+ * to vectors of n_u entries.
  * vem_amg_get_level: host CSR of level l's operator (row_ptr[rows + 1],
  * col[nnz], val[nnz]), its aggregate of every row (agg[rows], -1 for rows
  * outside the coarse space; with VEM_INNER_BLOCK_AMG one entry per point

@@ -164,10 +164,21 @@ struct AmgState {
   double *dgbi = nullptr;   size_t c_dgbi = 0;
   double *lz = nullptr;     size_t c_lz = 0;      // Lanczos basis (n x 11) and w
   double *lpart = nullptr;  size_t c_lpart = 0;   // partial sums of the Lanczos dots
+  // condensed Block-Reg: A_reg's parts, A_ii^-1 and the face system in SELL-32
+  bool condensed = false;
+  int64_t nfr = 0, nint = 0;
+  int nid = 0;
+  CsrBuf cAff, cAfi, cAif, cAii, cSf;
+  SellBuf cSell;
+  double *aii_inv = nullptr; size_t c_aii = 0;
+  double *cvec = nullptr;    size_t c_cvec = 0;   // nint + nfr scratch of the apply
   cudaEvent_t tev[4] = {};  // level-0 residual and post-smoothing launches of a timed cycle
   bool timing = false, timed = false;
+  cudaEvent_t sev[2] = {};  // the condensed setup's time
   ~AmgState() {
     for (cudaEvent_t &e : tev)
+      if (e) cudaEventDestroy(e);
+    for (cudaEvent_t &e : sev)
       if (e) cudaEventDestroy(e);
   }
 };
@@ -1320,6 +1331,59 @@ __global__ void k_pin_row(int n, int k, double *M) {
   }
 }
 
+// ------------------------------------------------ condensed Block-Reg -----
+// A_reg = [A_ff A_fi; A_if A_ii] with the face DOFs (rows < nfr) first; an
+// interior DOF couples only to its own cell, so A_ii is block diagonal with
+// nid x nid blocks.  The split writes the four parts as CSR (columns of the
+// interior parts shifted by -nfr), a count pass then a fill pass.
+// Rows r0 .. r0 + nrows - 1; the count pass writes c0/c1 at the global row,
+// the fill pass uses rp0/rp1 at the row within the range.
+template <bool kFill>
+__global__ void k_split(DMat A, int64_t r0, int64_t nrows, int64_t nfr, int64_t *c0, int64_t *c1,
+                        const int64_t *__restrict__ rp0, const int64_t *__restrict__ rp1, int32_t *col0,
+                        double *val0, int32_t *col1, double *val1) {
+  ROWS_LOOP(t, nrows) {
+    const int64_t i = r0 + t;
+    int64_t base;
+    int st, L;
+    A.row(i, base, st, L);
+    int64_t n0 = 0, n1 = 0;
+    const int64_t o0 = kFill ? rp0[t] : 0, o1 = kFill ? rp1[t] : 0;
+    for (int k = 0; k < L; ++k) {
+      const int64_t p = base + (int64_t)st * k;
+      const int64_t j = A.col[p];
+      if (j < nfr) {
+        if (kFill) {
+          col0[o0 + n0] = (int32_t)j;
+          val0[o0 + n0] = A.val[p];
+        }
+        ++n0;
+      } else {
+        if (kFill) {
+          col1[o1 + n1] = (int32_t)(j - nfr);
+          val1[o1 + n1] = A.val[p];
+        }
+        ++n1;
+      }
+    }
+    if (!kFill) {
+      c0[i] = n0;
+      c1[i] = n1;
+    }
+  }
+}
+
+// Near-null space of the condensed face system of the paper's k = 1 element:
+// the face DOFs (1/|f|) int_f (e_j . n_f) m_beta of the constant fields e_j,
+// n_f the global normal: n_f[j] for beta = (0, 0), 0 for the two linear face
+// monomials (their mean over the face vanishes about its barycentre).
+__global__ void k_flux_modes_k1(int64_t nf, const double *__restrict__ f_norm, double *B) {
+  ROWS_LOOP(f, nf) {
+    for (int b = 0; b < 3; ++b)
+      for (int j = 0; j < 3; ++j) B[(3 * f + b) * 3 + j] = b == 0 ? f_norm[3 * f + j] : 0.0;
+  }
+}
+
 // ------------------------------------------------------------ host --------
 // Row counts cnt[rows] -> CSR with that pattern (row pointers from the scan).
 static vem_status csr_layout(vem_handle *h, CsrBuf &C, int64_t rows, int64_t cols, const int64_t *cnt) {
@@ -1731,6 +1795,7 @@ vem_status amg_setup(vem_handle *h, AmgState *&slot, const SellMat &Sm, const fl
   S->pin_last = pin_last;
   S->smoother = smoother;
   S->block = false;
+  S->condensed = false;
   if (fp32 && !S_val32) return fail(h, VEM_ERR_BAD_INPUT, "FP32 AMG cycle without FP32 values of the operator");
   cudaStream_t s = h->stream;
   VEM_CUDA(h, cudaEventRecord(h->ev2, s));
@@ -2394,7 +2459,114 @@ static void coarsest_solve(vem_handle *h, AmgState *S, int l, const double *b, d
   }
 }
 
+// ------------------------------------------------ condensed Block-Reg -----
+// The face system S_f = A_ff - A_fi A_ii^-1 A_if of A_reg (interior DOFs
+// eliminated cell by cell, exactly) and the point-block hierarchy of S_f
+// with nfd x nfd face blocks and the near-null space Bf (nfr x m).
+vem_status amg_setup_condensed(vem_handle *h, AmgState *&slot, const SellMat &Areg, int64_t nfr, int nid, int nfd,
+                               const double *Bf, int m, int smoother) {
+  if (!slot) slot = new AmgState();
+  AmgState *S = slot;
+  S->valid = false;
+  S->condensed = false;
+  if (nid < 1 || nid > kMaxBs || nfd < 1 || nfd > kMaxBs || (Areg.rows - nfr) % nid)
+    return fail(h, VEM_ERR_UNSUPPORTED, "condensed Block-Reg cycle: %d interior DOFs per cell", nid);
+  cudaStream_t s = h->stream;
+  for (cudaEvent_t &e : S->sev)
+    if (!e) VEM_CUDA(h, cudaEventCreate(&e));
+  VEM_CUDA(h, cudaEventRecord(S->sev[0], s));
+  if (!S->ctr) VEM_TRY(dalloc_n(h, &S->ctr, kMaxRounds + 4));
+  const int64_t nu = Areg.rows, nint = nu - nfr, nc = nint / nid;
+  const DMat A = dview(Areg);
+  // split the rows: face rows into A_ff | A_fi, interior rows into A_if | A_ii
+  VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)nu + 1));
+  VEM_TRY(grow(h, S->scn, S->c_scn, (size_t)nu + 1));
+  count_launch();
+  k_split<false><<<rows_grid(nu), 256, 0, s>>>(A, 0, nu, nfr, S->cnt, S->scn, nullptr, nullptr, nullptr, nullptr,
+                                               nullptr, nullptr);
+  // face rows: counts at cnt[0..nfr), scn[0..nfr); interior rows after them
+  VEM_TRY(csr_layout(h, S->cAff, nfr, nfr, S->cnt));
+  VEM_TRY(csr_layout(h, S->cAfi, nfr, nint, S->scn));
+  VEM_TRY(csr_layout(h, S->cAif, nint, nfr, S->cnt + nfr));
+  VEM_TRY(csr_layout(h, S->cAii, nint, nint, S->scn + nfr));
+  count_launch();
+  k_split<true><<<rows_grid(nfr), 256, 0, s>>>(A, 0, nfr, nfr, nullptr, nullptr, S->cAff.rp, S->cAfi.rp,
+                                               S->cAff.col, S->cAff.val, S->cAfi.col, S->cAfi.val);
+  count_launch();
+  k_split<true><<<rows_grid(nint), 256, 0, s>>>(A, nfr, nint, nfr, nullptr, nullptr, S->cAif.rp, S->cAii.rp,
+                                                S->cAif.col, S->cAif.val, S->cAii.col, S->cAii.val);
+  VEM_TRY(sort_rows(h, S, nfr, S->cAff.rp, S->cAff.col, S->cAff.val));
+  VEM_TRY(sort_rows(h, S, nfr, S->cAfi.rp, S->cAfi.col, S->cAfi.val));
+  VEM_TRY(sort_rows(h, S, nint, S->cAif.rp, S->cAif.col, S->cAif.val));
+  // A_ii^-1 blockwise, then S_f = A_ff - A_fi (A_ii^-1 A_if)
+  VEM_TRY(grow(h, S->aii_inv, S->c_aii, (size_t)nint * nid));
+  VEM_TRY(grow(h, S->cvec, S->c_cvec, (size_t)nint + nfr));
+  double *lscr = nullptr;
+  VEM_TRY(dalloc_n(h, &lscr, (size_t)nint * nid));
+  count_launch();
+  k_blk_diag<<<rows_grid(nc), 256, 0, s>>>(nc, nid, dview(S->cAii), S->aii_inv, lscr, h->d_err);
+  VEM_TRY(check_device_errors(h, "condensed Block-Reg: interior blocks of A_reg"));
+  VEM_TRY(csr_fixed(h, S->bLm, nint, nint, nint * nid));
+  count_launch();
+  k_blkdiag_rows<<<rows_grid(nint), 256, 0, s>>>(nint, nid, S->aii_inv, 0, S->bLm.rp, S->bLm.col, S->bLm.val);
+  VEM_TRY(product(h, S, dview(S->bLm), S->cAif, S->bY, false));
+  VEM_TRY(product(h, S, dview(S->cAfi), S->bY, S->bZ, false));
+  count_launch();
+  k_sub_rows<false><<<rows_grid(nfr), 256, 0, s>>>(nfr, S->cAff.rp, S->cAff.col, S->cAff.val, S->bZ.rp, S->bZ.col,
+                                                   S->bZ.val, 1.0, S->cnt, nullptr, nullptr, nullptr);
+  VEM_TRY(csr_layout(h, S->cSf, nfr, nfr, S->cnt));
+  count_launch();
+  k_sub_rows<true><<<rows_grid(nfr), 256, 0, s>>>(nfr, S->cAff.rp, S->cAff.col, S->cAff.val, S->bZ.rp, S->bZ.col,
+                                                  S->bZ.val, 1.0, nullptr, S->cSf.rp, S->cSf.col, S->cSf.val);
+  VEM_TRY(csr_to_sell(h, S, S->cSf, S->cSell));
+  dfree(h, lscr);
+  VEM_TRY(check_device_errors(h, "condensed Block-Reg: face system"));
+  // the point-block hierarchy of S_f; the setup time covers the condensation too
+  VEM_TRY(amg_setup_block(h, slot, S->cSell.m, nfd, Bf, m, false, smoother));
+  VEM_CUDA(h, cudaEventRecord(S->sev[1], s));
+  VEM_CUDA(h, cudaEventSynchronize(S->sev[1]));
+  float ms = 0.f;
+  VEM_CUDA(h, cudaEventElapsedTime(&ms, S->sev[0], S->sev[1]));
+  S->t_setup_ms = ms;
+  S->condensed = true;
+  S->nfr = nfr;
+  S->nint = nint;
+  S->nid = nid;
+  return VEM_OK;
+}
+
+// z = (condensed cycle) r for vectors of n_u = nfr + nint entries.
+static void condensed_apply(vem_handle *h, AmgState *S, const double *r, double *z) {
+  cudaStream_t s = h->stream;
+  const int64_t nfr = S->nfr, nint = S->nint;
+  double *t = S->cvec, *rf = S->cvec + nint;
+  const double *ri = r + nfr;
+  double *zi = z + nfr;
+  count_launch();
+  k_blk_apply<<<rows_grid(nint), 256, 0, s>>>(nint, S->nid, S->aii_inv, 1.0, ri, nullptr, nullptr, 0.0, t, 0,
+                                             nullptr);                                    // t = A_ii^-1 r_i
+  csr_launch<kResid>(s, S->cAfi, (const double *)t, r, (const double *)nullptr, rf, nullptr);  // r_f - A_fi t
+  bcycle(h, S, 0, rf, z, nullptr);                                                         // z_f = V(S_f) rf
+  csr_launch<kResid>(s, S->cAif, (const double *)z, ri, (const double *)nullptr, t, nullptr);  // r_i - A_if z_f
+  count_launch();
+  k_blk_apply<<<rows_grid(nint), 256, 0, s>>>(nint, S->nid, S->aii_inv, 1.0, t, nullptr, nullptr, 0.0, zi, 0,
+                                             nullptr);                                    // z_i = A_ii^-1 t
+}
+
+bool amg_is_condensed(const AmgState *S) { return S && S->condensed; }
+
+vem_status flux_modes_k1(vem_handle *h, int64_t nf, const double *f_norm, double *B) {
+  count_launch();
+  k_flux_modes_k1<<<rows_grid(nf), 256, 0, h->stream>>>(nf, f_norm, B);
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
 void amg_vcycle(vem_handle *h, AmgState *S, const double *b, double *x, const double *sc) {
+  if (S->condensed) {
+    condensed_apply(h, S, b, x);
+    return;
+  }
   if (!S->fp32) {
     cycle<double, double>(h, S, 0, b, x, sc);
     return;

@@ -145,6 +145,8 @@ static vem_status check_options(vem_handle *h, const vem_options *o) {
     return fail(h, VEM_ERR_BAD_INPUT, "unknown inner solver %d", o->inner);
   if (o->inner_smoother != VEM_SMOOTH_JACOBI && o->inner_smoother != VEM_SMOOTH_CHEBYSHEV)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown inner smoother %d", o->inner_smoother);
+  if (o->reg_cycle != VEM_REG_SCALAR_AMG && o->reg_cycle != VEM_REG_CONDENSED)
+    return fail(h, VEM_ERR_BAD_INPUT, "unknown Block-Reg cycle %d", o->reg_cycle);
   if (o->precision != VEM_PRECISION_FP64 && o->precision != VEM_PRECISION_MIXED)
     return fail(h, VEM_ERR_BAD_INPUT, "unknown precision %d", o->precision);
   if (o->precision == VEM_PRECISION_MIXED && o->krylov != VEM_KRYLOV_FGMRES)
@@ -1203,8 +1205,9 @@ vem_status vem_amg_setup(vem_handle *h, int32_t which) {
   if (!h->assembled) VEM_TRY(assemble_impl(h));
   const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
   if (which == VEM_AMG_SCHUR) return schur_amg_setup(h, h->S, h->S_val32);
-  if (!h->areg_valid || (fp32 && !h->areg_has32)) VEM_TRY(assemble_reg(h, fp32));
-  return amg_setup(h, h->amg_reg, h->Areg, h->Areg_val32, fp32, false, kSmoothChebyshev);
+  (void)fp32;
+  amg_invalidate(h->amg_reg);   // rebuilt for the current options
+  return ensure_reg(h);
 }
 
 vem_status vem_amg_levels(vem_handle *h, int32_t which, int32_t *nlev, int64_t *rows, int64_t *nnz,

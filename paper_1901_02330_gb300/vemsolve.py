@@ -26,6 +26,7 @@ VEM_AMG_SCHUR, VEM_AMG_REG = 0, 1
 VEM_INNER_PCG, VEM_INNER_AMG, VEM_INNER_BLOCK_AMG = 0, 1, 2
 VEM_PRECISION_FP64, VEM_PRECISION_MIXED = 0, 1
 VEM_SMOOTH_JACOBI, VEM_SMOOTH_CHEBYSHEV = 0, 1
+VEM_REG_SCALAR_AMG, VEM_REG_CONDENSED = 0, 1
 VEM_QP_CELL, VEM_QP_BFACE = 0, 1
 
 
@@ -40,7 +41,7 @@ class vem_options(C.Structure):
     _fields_ = [("element", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("rtol", C.c_double),
                 ("maxit", C.c_int), ("precond", C.c_int), ("inner", C.c_int), ("inner_rtol", C.c_double),
                 ("inner_maxit", C.c_int), ("precision", C.c_int), ("device_io", C.c_int), ("reuse", C.c_int),
-                ("reg_gamma", C.c_double), ("inner_smoother", C.c_int)]
+                ("reg_gamma", C.c_double), ("inner_smoother", C.c_int), ("reg_cycle", C.c_int)]
 
 
 class vem_stats(C.Structure):

@@ -95,6 +95,7 @@ BAD_OPTIONS = {
     "precision": dict(precision=2),
     "inner_smoother": dict(inner_smoother=2),
     "inner_smoother<0": dict(inner_smoother=-1),
+    "reg_cycle": dict(reg_cycle=2),
     "mixed-minres": dict(precision=1, krylov=0, precond=0),
     "restart0": dict(restart=0),
     "restart257": dict(restart=257),
