@@ -100,9 +100,9 @@ typedef struct {
  * flux faces (the mean-zero pressure then constrains the constant moments,
  * c = |P| on them) and the block-diagonal and block-triangular
  * preconditioners (Jacobi-PCG, the scalar AMG without the multiplier, or
- * the point-block AMG VEM_INNER_BLOCK_AMG for S); Block-Reg,
- * vem_solve_batched and vem_adjoint give
- * VEM_ERR_UNSUPPORTED with it.  Its cell quadrature points
+ * the point-block AMG VEM_INNER_BLOCK_AMG for S) and vem_adjoint (Dirichlet
+ * boundaries); Block-Reg and vem_solve_batched give VEM_ERR_UNSUPPORTED with
+ * it.  Its cell quadrature points
  * (VEM_QP_CELL) are those of a degree-3 rule on the fan tetrahedra of every
  * cell (27 per tetrahedron), built on first use. */
 enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1, VEM_ELEMENT_K2 = 2 };

@@ -877,7 +877,6 @@ vem_status vem_adjoint(vem_handle *h, const double *dL_du, const double *dL_dp, 
   if (!h->have_solution || !h->assembled)
     return fail(h, VEM_ERR_BAD_INPUT, "vem_adjoint needs a preceding vem_solve with the same K");
   if (h->n_flux_faces > 0) return fail(h, VEM_ERR_UNSUPPORTED, "adjoint with prescribed-flux faces");
-  if (h->nq > 1) return fail(h, VEM_ERR_UNSUPPORTED, "adjoint of the paper k = 2 element");
   cudaStream_t s = h->stream;
   if (!h->lam) VEM_TRY(dalloc_n(h, &h->lam, (size_t)h->n));
   if (!h->arhs) VEM_TRY(dalloc_n(h, &h->arhs, (size_t)h->n));
@@ -1262,6 +1261,7 @@ void vem_destroy(vem_handle *h) {
   vem::amg_free(h->amg);
   vem::amg_free(h->amg_reg);
   if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
+  if (h->pcg_graph16) cudaGraphExecDestroy(h->pcg_graph16);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void *p : h->allocations) cudaFreeAsync(p, h->stream);
   if (!h->allocations.empty()) cudaStreamSynchronize(h->stream);

@@ -166,9 +166,10 @@ struct vem_handle {
   // CUDA graph of a chunk of inner CG iterations (captured on cap_stream,
   // launched on stream; rebuilt when any launch argument changes)
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t pcg_graph = nullptr;
+  cudaGraphExec_t pcg_graph = nullptr;          // 4 inner PCG iterations
+  cudaGraphExec_t pcg_graph16 = nullptr;        // 16 inner PCG iterations
   std::vector<uintptr_t> pcg_graph_key;
-  int64_t pcg_graph_kernels = 0;
+  int64_t pcg_graph_kernels = 0, pcg_graph16_kernels = 0;
   double lambda = 0.0;                           // the mean-zero multiplier
 };
 

@@ -310,16 +310,15 @@ __global__ void k_f32_to_f64(int64_t n, const float *__restrict__ a, double *b) 
 
 // Solve S x = b (length n_p) to relative residual inner_rtol with vectors,
 // matrix values and arithmetic in T; returns the iterations.
-// Capture the launches of body() on a private stream into the handle's CUDA
-// graph (kernels counted once per replay, not at capture).  Returns false,
-// with no graph, when capture or instantiation fails.
+// Capture the launches of body() on a private stream into the executable
+// graph slot (kernels counted once per replay, not at capture).  Returns
+// false, with no graph, when capture or instantiation fails.
 template <class F>
-static bool capture_pcg_graph(vem_handle *h, const std::vector<uintptr_t> &key, F body) {
-  if (h->pcg_graph) {
-    cudaGraphExecDestroy(h->pcg_graph);
-    h->pcg_graph = nullptr;
+static bool capture_graph(vem_handle *h, cudaGraphExec_t &slot, int64_t &kernels, F body) {
+  if (slot) {
+    cudaGraphExecDestroy(slot);
+    slot = nullptr;
   }
-  h->pcg_graph_key.clear();
   if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -334,18 +333,32 @@ static bool capture_pcg_graph(vem_handle *h, const std::vector<uintptr_t> &key, 
     h->stream = saved;
     ok = cudaStreamEndCapture(h->cap_stream, &g) == cudaSuccess && g != nullptr;
   }
-  const int64_t kernels = launch_count() - l0;
-  count_launches(-kernels);
-  if (ok) ok = cudaGraphInstantiate(&h->pcg_graph, g, 0) == cudaSuccess;
+  const int64_t nk = launch_count() - l0;
+  count_launches(-nk);
+  if (ok) ok = cudaGraphInstantiate(&slot, g, 0) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
   if (!ok) {
-    h->pcg_graph = nullptr;
+    slot = nullptr;
     cudaGetLastError();
     return false;
   }
-  h->pcg_graph_key = key;
-  h->pcg_graph_kernels = kernels;
+  kernels = nk;
   return true;
+}
+
+// The inner PCG's graphs of 4 and of 16 iterations for one set of launch
+// arguments (key).
+template <class F>
+static bool capture_pcg_graphs(vem_handle *h, const std::vector<uintptr_t> &key, F iteration) {
+  h->pcg_graph_key.clear();
+  const bool ok = capture_graph(h, h->pcg_graph, h->pcg_graph_kernels, [&]() {
+                    for (int k = 0; k < 4; ++k) iteration();
+                  }) &&
+                  capture_graph(h, h->pcg_graph16, h->pcg_graph16_kernels, [&]() {
+                    for (int k = 0; k < 16; ++k) iteration();
+                  });
+  if (ok) h->pcg_graph_key = key;
+  return ok;
 }
 
 // One launch of the tiled batched Schur SpMV with kR systems per tile.
@@ -501,9 +514,11 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
       launch_tiles<T>(h, op, sval, u, r, w, tol2, nb, tile, 0);
     }
   };
-  // the iterations run as a CUDA graph of kGraphIters iterations, captured
-  // once per set of launch arguments (eager launches if capture fails)
-  constexpr int kGraphIters = 4;
+  // the iterations run from CUDA graphs of 16 and of 4 iterations, captured
+  // once per set of launch arguments (eager launches if capture fails): the
+  // expected count first (the previous inner solve's), as 16-iteration graphs
+  // and the rest in 4s, then 4 at a time between polls of the device flag
+  constexpr int kGraphIters = 4, kLongIters = 16;
   uint64_t tol_bits = 0;
   std::memcpy(&tol_bits, &tol2, sizeof(double));
   const std::vector<uintptr_t> key = {
@@ -513,15 +528,17 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
       (uintptr_t)tol_bits,
       (uintptr_t)amg, (uintptr_t)(amg ? amg_generation(h->amg) : 0), sizeof(T), (uintptr_t)op.nbatch,
       (uintptr_t)op.S.rows, (uintptr_t)op.S.stored};
-  bool graph = h->pcg_graph != nullptr && h->pcg_graph_key == key;
-  if (!graph) graph = capture_pcg_graph(h, key, [&]() {
-    for (int k = 0; k < kGraphIters; ++k) iteration();
-  });
+  bool graph = h->pcg_graph != nullptr && h->pcg_graph16 != nullptr && h->pcg_graph_key == key;
+  if (!graph) graph = capture_pcg_graphs(h, key, iteration);
   int it = 0;
   while (it < maxit) {
     const int end = it + chunk < maxit ? it + chunk : maxit;
     chunk = 4;
     if (graph) {
+      for (; it + kLongIters <= end; it += kLongIters) {
+        VEM_CUDA(h, cudaGraphLaunch(h->pcg_graph16, s));
+        count_launches(h->pcg_graph16_kernels);
+      }
       for (; it < end; it += kGraphIters) {
         VEM_CUDA(h, cudaGraphLaunch(h->pcg_graph, s));
         count_launches(h->pcg_graph_kernels);

@@ -264,3 +264,35 @@ def test_pcg_matches_direct(small_system):
     res = solvers.pcg(S, b, rtol=1e-13)
     assert res.converged
     np.testing.assert_allclose(res.x, spla.spsolve(S.tocsc(), b), rtol=1e-10, atol=1e-12)
+
+
+def _unit_cube_l2_sq(a0, a):
+    """int over [0,1]^3 of (a0 + a.x)^2, expanded by hand."""
+    a = np.asarray(a, float)
+    cross = sum(a[i] * a[j] for i in range(3) for j in range(i + 1, 3))
+    return a0 * a0 + a0 * a.sum() + (a * a).sum() / 3.0 + cross / 2.0
+
+
+def test_indicators_on_the_linear_patch():
+    """Linear p = a0 + a.x, K = 1, on 3^3 cubes.  The paper's k = 1 element
+    reproduces the constant flux, so e_v vanishes; its P0 pressure is the
+    cell mean p(x_P), so e_q^2 ||p||^2 = sum_P int_P (a.(x - x_P))^2 =
+    n^3 h^5 |a|^2 / 12 with h = 1/n.  The k = 2 element has P1 pressure and
+    reproduces p, so both indicators vanish.  A mis-scaled or mis-signed term
+    in either indicator fails one of these."""
+    a0, a = 0.3, (1.0, -2.0, 0.5)
+    prob = fields.linear_problem(a0, a)
+    n = 3
+    m = hex_mesh(n)
+    nu = np.ones(m.n_cells)
+    sys = assemble(m, paper_element(1), nu, f=prob.f, gD=prob.gD, keep_local=True)
+    u, p = solvers.solve_direct(sys)
+    ev, eq = errors.indicators(sys, sys.cells, sys.dofmap, u, p, prob.u, prob.p, nu)
+    h = 1.0 / n
+    eq_exact = np.sqrt(n ** 3 * h ** 5 * np.dot(a, a) / 12.0 / _unit_cube_l2_sq(a0, a))
+    assert ev <= 1e-12
+    assert eq == pytest.approx(eq_exact, rel=1e-10)
+    sys2 = assemble(m, paper_element(2), nu, f=prob.f, gD=prob.gD, keep_local=True)
+    u2, p2 = solvers.solve_direct(sys2)
+    ev2, eq2 = errors.indicators(sys2, sys2.cells, sys2.dofmap, u2, p2, prob.u, prob.p, nu)
+    assert ev2 <= 1e-11 and eq2 <= 1e-11
