@@ -298,11 +298,15 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
  * K [nbatch][n_cells] (> 0), f_qp [nbatch][n_cells] and gD_qp
  * [nbatch][n_bqp] at the VEM_QP_CELL / VEM_QP_BFACE points (NULL = zero).
  * The systems share the sparsity structure: their saddle matrices and Schur
- * approximations are stored as one structure with per-system values, every
- * A-apply is one launch over all systems, and the Krylov method and
- * preconditioner of the options run on the block-diagonal stacked system
- * (one Krylov process for all systems, stopped when every system's true
- * relative residual is <= rtol).  Writes u_out [nbatch][n_u], p_out
+ * approximations are stored as one structure with per-system values, and
+ * every A-apply, Schur product and vector operation is one launch over all
+ * systems.  With FGMRES every system runs its own Krylov process: its own
+ * Arnoldi coefficients, Givens rotations, restarts and stopping test
+ * (||b_b - A_b x_b|| <= rtol ||b_b||), and its own inner Jacobi-PCG on its
+ * Schur block (own alpha, beta and convergence test); converged systems are
+ * skipped, and a system's result does not depend on the other systems.
+ * With MINRES one Krylov process runs on the block-diagonal stacked system,
+ * stopped when every system's true relative residual is <= rtol.  Writes u_out [nbatch][n_u], p_out
  * [nbatch][n_p] (host or device per options.device_io) and, if not NULL,
  * relres_out [nbatch] (host).  stats->relres is the worst system's. */
 vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, const double *f_qp,

@@ -992,8 +992,10 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   cudaEventSynchronize(h->ev1);
   float tas = 0.f;
   cudaEventElapsedTime(&tas, h->ev0, h->ev1);
-  // per-system right-hand-side norms: the shared Krylov process stops when
-  // ||r|| <= rtol min_b ||b_b||, so that every system meets rtol
+  // per-system right-hand-side norms.  FGMRES: every system runs its own
+  // Krylov process and stops on its own test.  MINRES: one process on the
+  // stacked system, stopped when ||r|| <= rtol min_b ||b_b||, so that every
+  // system meets rtol.
   std::vector<double> bn(nb), rn(nb);
   double *dn = h->part;   // nb <= 65535 norms fit in the partial-sum buffer
   count_launch();
@@ -1007,7 +1009,8 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   }
   btot = std::sqrt(btot);
   const double rtol = h->opt.rtol;
-  if (btot > 0.0 && bmin > 0.0) h->opt.rtol = rtol * bmin / btot;
+  const bool per_system = h->opt.krylov == VEM_KRYLOV_FGMRES;
+  if (!per_system && btot > 0.0 && bmin > 0.0) h->opt.rtol = rtol * bmin / btot;
   count_launch();
   k_import_x<<<grid_for(op.n, 256), 256, 0, s>>>(op.n_u, op.n, nullptr, h->b_x);
   vem_stats st{};
@@ -1017,7 +1020,8 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   st.nnz_S = h->S.nnz;
   st.t_assemble_ms = tas;
   cudaEventRecord(h->ev0, s);
-  vem_status r = krylov_solve(h, op, h->b_rhs, h->b_x, &st);
+  vem_status r = per_system ? run_fgmres_systems(h, op, h->b_rhs, h->b_x, &st, nullptr)
+                            : krylov_solve(h, op, h->b_rhs, h->b_x, &st);
   cudaEventRecord(h->ev1, s);
   cudaEventSynchronize(h->ev1);
   h->opt.rtol = rtol;
@@ -1262,6 +1266,8 @@ void vem_destroy(vem_handle *h) {
   vem::amg_free(h->amg_reg);
   if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
   if (h->pcg_graph16) cudaGraphExecDestroy(h->pcg_graph16);
+  if (h->bpcg_graph) cudaGraphExecDestroy(h->bpcg_graph);
+  if (h->bpcg_graph16) cudaGraphExecDestroy(h->bpcg_graph16);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void *p : h->allocations) cudaFreeAsync(p, h->stream);
   if (!h->allocations.empty()) cudaStreamSynchronize(h->stream);

@@ -168,6 +168,13 @@ struct vem_handle {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t pcg_graph = nullptr;          // 4 inner PCG iterations
   cudaGraphExec_t pcg_graph16 = nullptr;        // 16 inner PCG iterations
+  // per-system batched solve: scalars, partial sums, the inner PCG's graphs
+  double *sys_gs = nullptr, *sys_dd = nullptr, *sys_part = nullptr, *bc_part = nullptr, *bc_sc = nullptr;
+  size_t sys_n = 0, sys_dd_n = 0, sys_part_n = 0, bc_part_n = 0, bc_sc_n = 0;
+  cudaGraphExec_t bpcg_graph = nullptr, bpcg_graph16 = nullptr;
+  std::vector<uintptr_t> bpcg_key;
+  int64_t bpcg_kernels = 0, bpcg16_kernels = 0;
+  int last_bpcg_iters = 0;
   std::vector<uintptr_t> pcg_graph_key;
   int64_t pcg_graph_kernels = 0, pcg_graph16_kernels = 0;
   double lambda = 0.0;                           // the mean-zero multiplier
@@ -216,6 +223,9 @@ vem_status sell_to_host_csr(vem_handle *h, const SellMat &A, int64_t *rp, int32_
 
 // Krylov solve (krylov.cu)
 vem_status krylov_solve(vem_handle *h, const VemOp &op, const double *rhs, double *x, vem_stats *st);
+// the batched systems each with its own FGMRES and inner PCG (krylov.cu)
+vem_status run_fgmres_systems(vem_handle *h, const VemOp &op, const double *rhs, double *x, vem_stats *st,
+                              double *relres);
 // The single-system operator view of the handle.
 VemOp single_op(vem_handle *h);
 

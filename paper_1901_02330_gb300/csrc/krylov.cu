@@ -1190,6 +1190,754 @@ static vem_status run_fgmres(vem_handle *h, const VemOp &op, const double *rhs, 
   return VEM_OK;
 }
 
+// ----------------------------------------------- per-system batched solve --
+// nb systems stacked as [u_0 .. u_{nb-1} | p_0 .. p_{nb-1}] (n_u1 flux and
+// n_p1 pressure unknowns each).  Every system runs its own FGMRES(m) (its
+// own Arnoldi basis coefficients, Givens rotations, stopping test and
+// iteration count) and its own inner Jacobi-PCG on its Schur block (its own
+// alpha, beta and convergence test); the launches serve all systems at once
+// and converged systems are skipped.  Reductions are per system in a fixed
+// order: a grid of P x nb blocks writes partial sums, a second pass adds them.
+
+// global row of the t-th unknown (u part, then p part) of system b
+__device__ __forceinline__ int64_t sys_row(int64_t t, int b, int nb, int64_t n_u1, int64_t n_p1) {
+  return t < n_u1 ? (int64_t)b * n_u1 + t : (int64_t)nb * n_u1 + (int64_t)b * n_p1 + (t - n_u1);
+}
+
+// part[(b P + p) K + k] = partial sums of V_{i0+k} . w over system b (K <= 8)
+__global__ void __launch_bounds__(256) k_sys_dots(int nb, int64_t n_u1, int64_t n_p1, int64_t N, const double *V,
+                                                  int i0, int K, const double *__restrict__ w, double *part,
+                                                  const double *skip) {
+  __shared__ double sh[8][8];
+  if (skip && skip[0] == 0.0) return;
+  const int b = blockIdx.y, P = gridDim.x, pb = blockIdx.x;
+  const int64_t n1 = n_u1 + n_p1;
+  double acc[8];
+  for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+  for (int64_t t = (int64_t)pb * blockDim.x + threadIdx.x; t < n1; t += (int64_t)P * blockDim.x) {
+    const int64_t g = sys_row(t, b, nb, n_u1, n_p1);
+    const double wv = w[g];
+    for (int k = 0; k < K; ++k) acc[k] += V[(int64_t)(i0 + k) * N + g] * wv;
+  }
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int k = 0; k < K; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (l == 0) sh[k][wi] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[threadIdx.x][q];
+    part[((int64_t)b * P + pb) * K + threadIdx.x] = t;
+  }
+}
+
+// out[b ld + o + k] = sum_p part[(b P + p) K + k]
+__global__ void k_sys_dots_fin(int nb, int P, int K, const double *__restrict__ part, double *out, int ld, int o,
+                               const double *skip) {
+  if (skip && skip[0] == 0.0) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nb * K) return;
+  const int b = (int)(t / K), k = (int)(t % K);
+  double s = 0.0;
+  for (int p = 0; p < P; ++p) s += part[((int64_t)b * P + p) * K + k];
+  out[(int64_t)b * ld + o + k] = s;
+}
+
+// w[g] += sgn sum_{j < J} coef[b ld + j] V_j[g] for the rows g of every system b
+__global__ void k_sys_axpy(int nb, int64_t n_u1, int64_t n_p1, int64_t N, int J, const double *__restrict__ V,
+                           const double *__restrict__ coef, int ld, double sgn, double *w, const double *skip) {
+  if (skip && skip[0] == 0.0) return;
+  const int64_t nu = (int64_t)nb * n_u1;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N; g += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(g < nu ? g / n_u1 : (g - nu) / n_p1);
+    const double *c = coef + (int64_t)b * ld;
+    double s = 0.0;
+    for (int j = 0; j < J; ++j) s += c[j] * V[(int64_t)j * N + g];
+    w[g] += sgn * s;
+  }
+}
+
+// y[g] = fac[b] x[g]
+__global__ void k_sys_scale(int nb, int64_t n_u1, int64_t n_p1, int64_t N, const double *__restrict__ x,
+                            const double *__restrict__ fac, int ld, double *y) {
+  const int64_t nu = (int64_t)nb * n_u1;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N; g += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(g < nu ? g / n_u1 : (g - nu) / n_p1);
+    y[g] = fac[(int64_t)b * ld] * x[g];
+  }
+}
+
+// ---- the per-system inner Jacobi-PCG on the stacked Schur blocks ----
+// Per-system scalars at bsc[k nb + b]: the slots below; flag[0] = all done.
+enum { BC_ALPHA = 0, BC_BETA, BC_GPREV, BC_APREV, BC_BB, BC_IT, BC_DONE, BC_BAD, BC_N };
+
+__device__ __forceinline__ bool all_done(const double *flag) {
+  __shared__ int f;
+  if (threadIdx.x == 0) f = flag[0] != 0.0;
+  __syncthreads();
+  const bool r = f != 0;
+  __syncthreads();
+  return r;
+}
+
+// x = 0, r = b, u = D^-1 r, p = s = 0; partials of (b, b) per system (grid P x nb)
+template <class T>
+__global__ void __launch_bounds__(256) k_bcg_init(int nb, int64_t n1, const double *__restrict__ b,
+                                                  const T *__restrict__ dinv, T *x, T *r, T *u, T *p, T *s,
+                                                  double *part, double *bsc, const double *__restrict__ active,
+                                                  int lda, double *flag) {
+  __shared__ double sh[8];
+  const int sb = blockIdx.y, P = gridDim.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // this solve's state: systems whose outer iteration is inactive are done
+    bsc[BC_DONE * nb + sb] = active[(int64_t)sb * lda] != 0.0 ? 0.0 : 1.0;
+    bsc[BC_IT * nb + sb] = 0.0;
+    bsc[BC_BAD * nb + sb] = 0.0;
+    if (sb == 0) flag[0] = 0.0;
+  }
+  double acc = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n1; t += (int64_t)P * blockDim.x) {
+    const int64_t i = (int64_t)sb * n1 + t;
+    const T bt = (T)b[i];
+    x[i] = 0;
+    r[i] = bt;
+    u[i] = dinv[i] * bt;
+    p[i] = 0;
+    s[i] = 0;
+    acc += (double)bt * (double)bt;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    part[(int64_t)sb * P + blockIdx.x] = t;
+  }
+}
+
+// w = S u for every system not done, with per-(system, slice) partials of
+// (r, u) and (w, u): part_ru[b nsl + s], part_wu[b nsl + s].  A warp task is
+// one 32-row slice of kR consecutive systems, so each column id is read once
+// for kR value streams and gathers; tasks whose systems are all done are
+// skipped.
+template <class T, int kR>
+__global__ void __launch_bounds__(256) k_bcg_spmv(int nb, int64_t rows, int64_t nsl, int64_t stored,
+                                                  const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                                  const T *__restrict__ val, const T *__restrict__ u,
+                                                  const T *__restrict__ r, T *w, double *part_ru, double *part_wu,
+                                                  const double *bsc, const double *flag) {
+  if (all_done(flag)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t groups = (nb + kR - 1) / kR;
+  for (int64_t tk = warp; tk < nsl * groups; tk += nwarps) {
+    const int64_t g = tk / nsl, sl = tk - g * nsl;
+    const int b0 = (int)(g * kR);
+    bool live[kR];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < kR; ++q) {
+      live[q] = (b0 + q < nb) && bsc[BC_DONE * nb + b0 + q] == 0.0;
+      any = any || live[q];
+    }
+    if (!any) continue;   // uniform over the warp
+    const int64_t o = off[sl];
+    const int wdt = (int)((off[sl + 1] - o) >> 5);
+    T acc[kR];
+#pragma unroll
+    for (int q = 0; q < kR; ++q) acc[q] = 0;
+#pragma unroll 2
+    for (int j = 0; j < wdt; ++j) {
+      const int64_t pos = o + 32 * (int64_t)j + lane;
+      const int32_t c = __ldcs(col + pos);
+#pragma unroll
+      for (int q = 0; q < kR; ++q)
+        if (live[q]) acc[q] += __ldcs(val + (int64_t)(b0 + q) * stored + pos) * __ldg(u + (int64_t)(b0 + q) * rows + c);
+    }
+    const int64_t i = 32 * sl + lane;
+#pragma unroll
+    for (int q = 0; q < kR; ++q) {
+      if (!live[q]) continue;
+      double gam = 0.0, del = 0.0;
+      if (i < rows) {
+        const int64_t gi = (int64_t)(b0 + q) * rows + i;
+        w[gi] = acc[q];
+        gam = (double)r[gi] * (double)u[gi];
+        del = (double)acc[q] * (double)u[gi];
+      }
+      gam = warp_sum(gam);
+      del = warp_sum(del);
+      if (lane == 0) {
+        part_ru[(int64_t)(b0 + q) * nsl + sl] = gam;
+        part_wu[(int64_t)(b0 + q) * nsl + sl] = del;
+      }
+    }
+  }
+}
+
+// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r for
+// every system not done; partials of (r, r) per system (grid P x nb)
+template <class T>
+__global__ void __launch_bounds__(256) k_bcg_update(int nb, int64_t n1, T *x, T *r, T *u, T *p, T *s,
+                                                    const T *__restrict__ w, const T *__restrict__ dinv,
+                                                    const double *bsc, double *part, const double *flag) {
+  __shared__ double sh[8];
+  if (all_done(flag)) return;
+  const int sb = blockIdx.y, P = gridDim.x;
+  if (bsc[BC_DONE * nb + sb] != 0.0) return;   // uniform over the block
+  const T alpha = (T)bsc[BC_ALPHA * nb + sb], beta = (T)bsc[BC_BETA * nb + sb];
+  double acc = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n1; t += (int64_t)P * blockDim.x) {
+    const int64_t i = (int64_t)sb * n1 + t;
+    const T pi = u[i] + beta * p[i];
+    const T si = w[i] + beta * s[i];
+    x[i] += alpha * pi;
+    const T ri = r[i] - alpha * si;
+    p[i] = pi;
+    s[i] = si;
+    r[i] = ri;
+    u[i] = dinv[i] * ri;
+    acc += (double)ri * (double)ri;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    part[(int64_t)sb * P + blockIdx.x] = t;
+  }
+}
+
+// One block per system: (r,u), (w,u) over its slices and (r,r) over its
+// update partials, in a fixed order; then the convergence test, alpha and
+// beta (the recurrences of the single-system form).  init != 0: the first
+// call after k_bcg_init ((r, r) = (b, b) is also stored as BC_BB).  The last
+// block to finish sets flag[0] = 1 when every system is done and flag[1] to
+// the largest iteration count (ctr: a zeroed counter, reset by that block).
+__global__ void __launch_bounds__(256) k_bcg_scalars(int nb, int64_t nsl, int P, const double *__restrict__ part_ru,
+                                                     const double *__restrict__ part_wu,
+                                                     const double *__restrict__ part_rr, double tol2, double *bsc,
+                                                     int init, double *flag, unsigned int *ctr) {
+  __shared__ double sh[3][8];
+  __shared__ int open;
+  __shared__ unsigned long long mx;
+  if (all_done(flag)) return;   // uniform over the grid
+  const int b = blockIdx.x;
+  const bool skip = !init && bsc[BC_DONE * nb + b] != 0.0;
+  double g = 0.0, d = 0.0, rr = 0.0;
+  if (!skip) {
+    for (int64_t s2 = threadIdx.x; s2 < nsl; s2 += blockDim.x) {
+      g += part_ru[(int64_t)b * nsl + s2];
+      d += part_wu[(int64_t)b * nsl + s2];
+    }
+    for (int p = threadIdx.x; p < P; p += blockDim.x) rr += part_rr[(int64_t)b * P + p];
+  }
+  g = warp_sum(g);
+  d = warp_sum(d);
+  rr = warp_sum(rr);
+  const int wi = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][wi] = g;
+    sh[1][wi] = d;
+    sh[2][wi] = rr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !skip) {
+    double G = 0.0, D = 0.0, R = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      G += sh[0][q];
+      D += sh[1][q];
+      R += sh[2][q];
+    }
+    bool go = true;
+    if (init) {
+      bsc[BC_BB * nb + b] = R;
+      if (R == 0.0) bsc[BC_DONE * nb + b] = 1.0;
+      go = bsc[BC_DONE * nb + b] == 0.0;
+    }
+    if (go) {
+      const int it = (int)bsc[BC_IT * nb + b];
+      if (!isfinite(R) || !isfinite(G) || !isfinite(D)) {
+        bsc[BC_BAD * nb + b] = 2.0;
+        bsc[BC_DONE * nb + b] = 1.0;
+      } else if (R <= tol2 * bsc[BC_BB * nb + b]) {
+        bsc[BC_DONE * nb + b] = 1.0;
+      } else {
+        double beta = 0.0, den = D;
+        if (it > 0) {
+          beta = G / bsc[BC_GPREV * nb + b];
+          den = D - beta * G / bsc[BC_APREV * nb + b];
+        }
+        if (!(den > 0.0) || !(G > 0.0)) {
+          bsc[BC_BAD * nb + b] = 1.0;
+          bsc[BC_DONE * nb + b] = 1.0;
+        } else {
+          const double alpha = G / den;
+          bsc[BC_ALPHA * nb + b] = alpha;
+          bsc[BC_BETA * nb + b] = beta;
+          bsc[BC_GPREV * nb + b] = G;
+          bsc[BC_APREV * nb + b] = alpha;
+          bsc[BC_IT * nb + b] = (double)(it + 1);
+        }
+      }
+    }
+  }
+  if (!last_block(ctr)) return;
+  if (threadIdx.x == 0) {
+    open = 0;
+    mx = 0ull;
+  }
+  __syncthreads();
+  int c = 0;
+  double m = 0.0;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+    c += bsc[BC_DONE * nb + q] == 0.0;
+    m = fmax(m, bsc[BC_IT * nb + q]);
+  }
+  atomicAdd(&open, c);
+  atomicMax(&mx, (unsigned long long)__double_as_longlong(m));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    flag[0] = open == 0 ? 1.0 : 0.0;
+    flag[1] = __longlong_as_double((long long)mx);
+  }
+}
+
+// ---- the per-system FGMRES scalars ----
+// Per system b at gs + b L: H ((m+1) x m, row-major), cs[m], sn[m], g[m+1],
+// y[m], then the slots below.
+enum { GS_BETA = 0, GS_BNORM, GS_EST, GS_ACTIVE, GS_JD, GS_DONE, GS_IT, GS_FAC, GS_REL, GS_N };
+struct SysLayout {
+  int m;
+  __host__ __device__ int H(int i, int j) const { return i * m + j; }
+  __host__ __device__ int CS(int i) const { return (m + 1) * m + i; }
+  __host__ __device__ int SN(int i) const { return (m + 1) * m + m + i; }
+  __host__ __device__ int G(int i) const { return (m + 1) * m + 2 * m + i; }
+  __host__ __device__ int Y(int i) const { return (m + 1) * m + 3 * m + 1 + i; }
+  __host__ __device__ int S(int k) const { return (m + 1) * m + 4 * m + 1 + k; }
+  __host__ __device__ int size() const { return (m + 1) * m + 4 * m + 1 + GS_N; }
+};
+
+// Restart: beta = ||r_b||, ||b_b||, the relative residual, the stopping test;
+// g = beta e_1 and the scale 1 / beta of the new basis vector.  first: the
+// first cycle of the solve (sets the iteration count to 0).
+__global__ void k_sys_start(int nb, SysLayout L, double rtol, const double *__restrict__ dd, int ldd, int orr,
+                            int obb, double *gs, int first) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double *q = gs + (int64_t)b * L.size();
+  const double rr = dd[(int64_t)b * ldd + orr], bb = dd[(int64_t)b * ldd + obb];
+  const double beta = sqrt(fmax(rr, 0.0)), bn = sqrt(fmax(bb, 0.0));
+  const double rel = bn > 0.0 ? beta / bn : beta;
+  q[L.S(GS_BETA)] = beta;
+  q[L.S(GS_BNORM)] = bn;
+  q[L.S(GS_REL)] = rel;
+  if (first) q[L.S(GS_IT)] = 0.0;
+  const bool done = !(rel > rtol) || beta == 0.0;
+  q[L.S(GS_DONE)] = done ? 1.0 : 0.0;
+  q[L.S(GS_ACTIVE)] = done ? 0.0 : 1.0;
+  q[L.S(GS_JD)] = 0.0;
+  q[L.S(GS_FAC)] = done ? 0.0 : 1.0 / beta;
+  for (int i = 0; i <= L.m; ++i) q[L.G(i)] = 0.0;
+  q[L.G(0)] = beta;
+}
+
+// The second Gram-Schmidt pass where the first lost too much (the DGKS test
+// of Daniel, Gragg, Kaufman & Stewart, 1976): system b repeats the pass when
+// ||w|| after the first is below 0.7 of ||w|| before it (dd at ob and on);
+// ro[b] = 1 then; flag[0] = 1 when any system needs it.  Systems without the
+// second pass get zero second-pass coefficients.
+__global__ void k_sys_reorth(int nb, const double *__restrict__ active, int lda, double *dd, int ldd, int ob, int on,
+                             int o2, int jp1, double *ro, double *flag) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int a = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const double *h = dd + (int64_t)b * ldd;
+    const bool need = active[(int64_t)b * lda] != 0.0 && h[on] < 0.49 * h[ob];
+    ro[b] = need ? 1.0 : 0.0;
+    a |= need;
+  }
+  if (a) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) flag[0] = any ? 1.0 : 0.0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    if (ro[b] == 0.0)
+      for (int i = 0; i < jp1; ++i) dd[(int64_t)b * ldd + o2 + i] = 0.0;
+}
+
+// Column j of H from the two Gram-Schmidt passes (hh: pass 1 at o1, pass 2
+// at o2, ||w||^2 at on, row b at dd + b ldd), the Givens rotations and the
+// stopping test of every active system; the scale of V_{j+1}.
+__global__ void k_sys_arnoldi(int nb, int j, SysLayout L, double rtol, const double *__restrict__ dd, int ldd, int o1,
+                              int o2, int on, double *gs) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double *q = gs + (int64_t)b * L.size();
+  if (q[L.S(GS_ACTIVE)] == 0.0) {
+    q[L.S(GS_FAC)] = 0.0;
+    return;
+  }
+  const double *h = dd + (int64_t)b * ldd;
+  for (int i = 0; i <= j; ++i) q[L.H(i, j)] = h[o1 + i] + h[o2 + i];
+  const double hn = sqrt(fmax(h[on], 0.0));
+  for (int i = 0; i < j; ++i) {
+    const double t = q[L.CS(i)] * q[L.H(i, j)] + q[L.SN(i)] * q[L.H(i + 1, j)];
+    q[L.H(i + 1, j)] = -q[L.SN(i)] * q[L.H(i, j)] + q[L.CS(i)] * q[L.H(i + 1, j)];
+    q[L.H(i, j)] = t;
+  }
+  const double hjj = q[L.H(j, j)];
+  const double den = sqrt(hjj * hjj + hn * hn);
+  const double c = den > 0.0 ? hjj / den : 1.0, sn = den > 0.0 ? hn / den : 0.0;
+  q[L.CS(j)] = c;
+  q[L.SN(j)] = sn;
+  q[L.H(j, j)] = den;
+  q[L.G(j + 1)] = -sn * q[L.G(j)];
+  q[L.G(j)] = c * q[L.G(j)];
+  const double est = fabs(q[L.G(j + 1)]);
+  q[L.S(GS_EST)] = est;
+  q[L.S(GS_IT)] += 1.0;
+  q[L.S(GS_JD)] = (double)(j + 1);
+  const bool stop = est <= 0.5 * rtol * q[L.S(GS_BNORM)] || hn == 0.0 || den == 0.0;
+  if (stop) q[L.S(GS_ACTIVE)] = 0.0;
+  q[L.S(GS_FAC)] = (!stop && hn > 0.0) ? 1.0 / hn : 0.0;
+}
+
+// y = H^-1 g on the first jd columns (upper triangular), 0 beyond
+__global__ void k_sys_solve(int nb, SysLayout L, double *gs) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double *q = gs + (int64_t)b * L.size();
+  const int jd = (int)q[L.S(GS_JD)];
+  for (int i = L.m - 1; i >= 0; --i) {
+    if (i >= jd) {
+      q[L.Y(i)] = 0.0;
+      continue;
+    }
+    double v = q[L.G(i)];
+    for (int k = i + 1; k < jd; ++k) v -= q[L.H(i, k)] * q[L.Y(k)];
+    q[L.Y(i)] = q[L.H(i, i)] != 0.0 ? v / q[L.H(i, i)] : 0.0;
+  }
+}
+
+// out[0] = systems still active in the cycle, out[1] = systems not done,
+// out[2] = the largest iteration count
+__global__ void k_sys_flags(int nb, SysLayout L, const double *__restrict__ gs, double *out) {
+  __shared__ int na, nn;
+  __shared__ unsigned long long mx;
+  if (threadIdx.x == 0) {
+    na = 0;
+    nn = 0;
+    mx = 0ull;
+  }
+  __syncthreads();
+  int a = 0, d = 0;
+  double m = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const double *q = gs + (int64_t)b * L.size();
+    a += q[L.S(GS_ACTIVE)] != 0.0;
+    d += q[L.S(GS_DONE)] == 0.0;
+    m = fmax(m, q[L.S(GS_IT)]);
+  }
+  atomicAdd(&na, a);
+  atomicAdd(&nn, d);
+  atomicMax(&mx, (unsigned long long)__double_as_longlong(m));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out[0] = na;
+    out[1] = nn;
+    out[2] = __longlong_as_double((long long)mx);
+  }
+}
+
+// r = b - A x
+__global__ void k_sub_vec(int64_t n, const double *__restrict__ b, const double *__restrict__ ax, double *r) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - ax[i];
+}
+
+// ---- host side of the per-system batched solve ----
+static int sys_blocks(int nb, int64_t n1) {
+  int64_t P = (4LL * num_sms() + nb - 1) / nb;
+  P = std::min<int64_t>(P, (n1 + 255) / 256);
+  P = std::max<int64_t>(P, 1);
+  return (int)std::min<int64_t>(P, 64);
+}
+
+// dd[b ldd + o + k] = V_{i0+k} . w over system b, k < K
+static vem_status sys_dots(vem_handle *h, const VemOp &op, const double *V, int i0, int K, const double *w,
+                           double *dd, int ldd, int o, const double *skip = nullptr) {
+  cudaStream_t s = h->stream;
+  const int nb = op.nbatch;
+  const int P = sys_blocks(nb, op.n_u1 + op.n_p1);
+  for (int c = 0; c < K; c += 8) {
+    const int k = std::min(8, K - c);
+    count_launch();
+    k_sys_dots<<<dim3(P, nb), 256, 0, s>>>(nb, op.n_u1, op.n_p1, op.n, V, i0 + c, k, w, h->sys_part, skip);
+    count_launch();
+    k_sys_dots_fin<<<grid_for((int64_t)nb * k, 256), 256, 0, s>>>(nb, P, k, h->sys_part, dd, ldd, o + c, skip);
+  }
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
+// x = S^-1 b for every system whose outer iteration is active (active[b lda]
+// != 0), each by its own Jacobi-PCG to inner_rtol; vectors and values in T.
+template <class T>
+static vem_status bpcg_solve(vem_handle *h, const VemOp &op, const T *sval, const T *dinv, const double *b, T *x,
+                             T *wk, const double *active, int lda, int *iters) {
+  cudaStream_t s = h->stream;
+  const int nb = op.nbatch;
+  const int64_t n1 = op.n_p1, nsl = op.S.nslices, N = (int64_t)nb * n1;
+  T *r = wk, *u = wk + N, *p = wk + 2 * N, *sv = wk + 3 * N, *w = wk + 4 * N;
+  const int P = sys_blocks(nb, n1);
+  double *ru = h->bc_part, *wu = ru + (size_t)nb * nsl, *rr = wu + (size_t)nb * nsl;
+  double *bsc = h->bc_sc, *flag = h->bc_sc + BC_N * nb;
+  unsigned int *tick = reinterpret_cast<unsigned int *>(flag + 2);
+  const double tol2 = h->opt.inner_rtol * h->opt.inner_rtol;
+  constexpr int kR = 4;
+  static int cap = 0;
+  if (cap == 0) cap = one_wave_blocks((const void *)k_bcg_spmv<T, kR>);
+  int64_t gsp = (nsl * ((nb + kR - 1) / kR) + 7) / 8;
+  if (gsp > cap) gsp = cap;
+  if (gsp < 1) gsp = 1;
+  count_launch();
+  k_bcg_init<T><<<dim3(P, nb), 256, 0, s>>>(nb, n1, b, dinv, x, r, u, p, sv, rr, bsc, active, lda, flag);
+  count_launch();
+  k_bcg_spmv<T, kR><<<(int)gsp, 256, 0, s>>>(nb, n1, nsl, op.S.stored, op.S.off, op.S.col, sval, u, r, w, ru, wu,
+                                             bsc, flag);
+  count_launch();
+  k_bcg_scalars<<<nb, 256, 0, s>>>(nb, nsl, P, ru, wu, rr, tol2, bsc, 1, flag, tick);
+  auto iteration = [&]() {
+    cudaStream_t cs = h->stream;
+    count_launch();
+    k_bcg_update<T><<<dim3(P, nb), 256, 0, cs>>>(nb, n1, x, r, u, p, sv, w, dinv, bsc, rr, flag);
+    count_launch();
+    k_bcg_spmv<T, kR><<<(int)gsp, 256, 0, cs>>>(nb, n1, nsl, op.S.stored, op.S.off, op.S.col, sval, u, r, w, ru,
+                                                wu, bsc, flag);
+    count_launch();
+    k_bcg_scalars<<<nb, 256, 0, cs>>>(nb, nsl, P, ru, wu, rr, tol2, bsc, 0, flag, tick);
+  };
+  uint64_t tol_bits = 0;
+  std::memcpy(&tol_bits, &tol2, sizeof(double));
+  const std::vector<uintptr_t> key = {(uintptr_t)op.S.off, (uintptr_t)op.S.col, (uintptr_t)sval, (uintptr_t)dinv,
+                                      (uintptr_t)x, (uintptr_t)wk, (uintptr_t)bsc, (uintptr_t)ru, (uintptr_t)nb,
+                                      (uintptr_t)n1, (uintptr_t)P, (uintptr_t)gsp, (uintptr_t)tol_bits,
+                                      sizeof(T), (uintptr_t)op.S.stored};
+  bool graph = h->bpcg_graph && h->bpcg_graph16 && h->bpcg_key == key;
+  if (!graph) {
+    h->bpcg_key.clear();
+    graph = capture_graph(h, h->bpcg_graph, h->bpcg_kernels, [&]() {
+              for (int k = 0; k < 4; ++k) iteration();
+            }) &&
+            capture_graph(h, h->bpcg_graph16, h->bpcg16_kernels, [&]() {
+              for (int k = 0; k < 16; ++k) iteration();
+            });
+    if (graph) h->bpcg_key = key;
+  }
+  const int maxit = h->opt.inner_maxit;
+  int chunk = h->last_bpcg_iters > 0 ? h->last_bpcg_iters : 8;
+  int it = 0;
+  while (it < maxit) {
+    const int end = it + chunk < maxit ? it + chunk : maxit;
+    chunk = 4;
+    if (graph) {
+      for (; it + 16 <= end; it += 16) {
+        VEM_CUDA(h, cudaGraphLaunch(h->bpcg_graph16, s));
+        count_launches(h->bpcg16_kernels);
+      }
+      for (; it < end; it += 4) {
+        VEM_CUDA(h, cudaGraphLaunch(h->bpcg_graph, s));
+        count_launches(h->bpcg_kernels);
+      }
+    } else {
+      for (; it < end; ++it) iteration();
+    }
+    VEM_CUDA(h, cudaGetLastError());
+    VEM_CUDA(h, cudaMemcpyAsync(h->h_scal, flag, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+    if (h->h_scal[0] != 0.0) break;
+  }
+  std::vector<double> bad(nb);
+  VEM_CUDA(h, cudaMemcpyAsync(bad.data(), bsc + BC_BAD * nb, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  for (int b2 = 0; b2 < nb; ++b2)
+    if (bad[b2] != 0.0)
+      return fail(h, bad[b2] == 2.0 ? VEM_ERR_NONFINITE : VEM_ERR_BREAKDOWN, "inner PCG breakdown in system %d", b2);
+  *iters = (int)h->h_scal[1];
+  h->last_bpcg_iters = *iters;
+  return VEM_OK;
+}
+
+// z = P^-1 v for every system (block-diagonal or block upper-triangular with
+// the systems' own inner solves); systems whose outer iteration is inactive
+// have v = 0 and get z = 0.
+static vem_status sys_precond(vem_handle *h, const VemOp &op, const double *v, double *z, double *pw,
+                              const double *active, int lda, int *inner) {
+  cudaStream_t s = h->stream;
+  const int64_t nu = op.n_u, np = op.n_p;
+  int it = 0;
+  if (h->opt.precision == VEM_PRECISION_MIXED) {
+    float *w32 = reinterpret_cast<float *>(pw);
+    float *x32 = w32 + 5 * np;
+    VEM_TRY(bpcg_solve<float>(h, op, op.S_val32, op.s_dinv32, v + nu, x32, w32, active, lda, &it));
+    count_launch();
+    k_f32_to_f64<<<grid_for(np, 256), 256, 0, s>>>(np, x32, z + nu);
+  } else {
+    VEM_TRY(bpcg_solve<double>(h, op, op.S.val, op.s_dinv, v + nu, z + nu, pw, active, lda, &it));
+  }
+  *inner += it;
+  if (h->opt.precond == VEM_PREC_BLOCK_DIAG) {
+    count_launch();
+    k_diag_scale<<<nblocks_vec(nu), kRedThreads, 0, s>>>(nu, v, op.diagM, z, nullptr);
+  } else {
+    count_launch();
+    k_negate<<<grid_for(np, 256), 256, 0, s>>>(np, z + nu);
+    launch_tri_flux(s, h->nfd, true, h->nf, nu, op.n_u1, op.n_p1, v, op.diagM, h->f_cell, h->bt_face, z + nu, z);
+  }
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
+// Per-system restarted FGMRES(m) with right preconditioning from x (usually
+// 0): system b stops when ||b_b - A_b x_b|| <= rtol ||b_b||.  relres (host,
+// nb entries, may be NULL) receives each system's last true relative residual.
+vem_status run_fgmres_systems(vem_handle *h, const VemOp &op, const double *rhs, double *x, vem_stats *st,
+                              double *relres) {
+  cudaStream_t s = h->stream;
+  h->n_saddle_pending = 0;
+  const int nb = op.nbatch;
+  const int64_t N = op.n, np = op.n_p;
+  const int m = h->opt.restart;
+  const SysLayout L{m};
+  // per-system dot rows: pass-1 and pass-2 coefficients, ||w||^2, ||r||^2, ||b||^2
+  const int ldd = 2 * (m + 2) + 4, o1 = 0, o2 = m + 2, on = 2 * (m + 2), orr = on + 1, obb = on + 2;
+  VEM_TRY(ensure_work(h, (size_t)(2 * m + 2) * N + 5 * (size_t)np));
+  double *V = h->work, *Z = V + (size_t)(m + 1) * N, *tmp = Z + (size_t)m * N, *pw = tmp + N;
+  const int P = sys_blocks(nb, op.n_u1 + op.n_p1);
+  if (h->sys_n < (size_t)nb * L.size()) {
+    dfree(h, h->sys_gs);
+    h->sys_gs = nullptr;
+    VEM_TRY(dalloc_n(h, &h->sys_gs, (size_t)nb * L.size() + 8));
+    h->sys_n = (size_t)nb * L.size();
+  }
+  const size_t ddn = (size_t)nb * ldd + 8 + (size_t)nb;   // dot rows, flags, reorthogonalisation marks
+  if (h->sys_dd_n < ddn) {
+    dfree(h, h->sys_dd);
+    h->sys_dd = nullptr;
+    VEM_TRY(dalloc_n(h, &h->sys_dd, ddn));
+    h->sys_dd_n = ddn;
+  }
+  if (h->sys_part_n < (size_t)nb * P * 8) {
+    dfree(h, h->sys_part);
+    VEM_TRY(dalloc_n(h, &h->sys_part, (size_t)nb * P * 8));
+    h->sys_part_n = (size_t)nb * P * 8;
+  }
+  const size_t bcn = 3 * (size_t)nb * op.S.nslices + (size_t)nb * sys_blocks(nb, op.n_p1) + 16;
+  if (h->bc_part_n < bcn) {
+    dfree(h, h->bc_part);
+    VEM_TRY(dalloc_n(h, &h->bc_part, bcn));
+    h->bc_part_n = bcn;
+  }
+  if (h->bc_sc_n < (size_t)BC_N * nb + 4) {
+    dfree(h, h->bc_sc);
+    VEM_TRY(dalloc_n(h, &h->bc_sc, (size_t)BC_N * nb + 4));
+    h->bc_sc_n = (size_t)BC_N * nb + 4;
+    // the scalars kernel's last-block counter (after the two flags) starts at 0
+    VEM_CUDA(h, cudaMemsetAsync(h->bc_sc + (size_t)BC_N * nb + 2, 0, sizeof(double), s));
+  }
+  double *gs = h->sys_gs, *dd = h->sys_dd, *fl = h->sys_dd + (size_t)nb * ldd, *ro = fl + 8;
+  const int gnb = grid_for(nb, 128);
+  const double rtol = h->opt.rtol;
+  // r = b - A x, the norms and the first cycle's start
+  op_apply_timed(h, op, x, tmp);
+  count_launch();
+  k_sub_vec<<<grid_for(N, 256), 256, 0, s>>>(N, rhs, tmp, tmp);
+  VEM_TRY(sys_dots(h, op, tmp, 0, 1, tmp, dd, ldd, orr));
+  VEM_TRY(sys_dots(h, op, rhs, 0, 1, rhs, dd, ldd, obb));
+  count_launch();
+  k_sys_start<<<gnb, 128, 0, s>>>(nb, L, rtol, dd, ldd, orr, obb, gs, 1);
+  int inner = 0, it = 0;
+  double hf[3] = {0, 0, 0};
+  auto flags = [&]() -> vem_status {
+    count_launch();
+    k_sys_flags<<<1, 256, 0, s>>>(nb, L, gs, fl);
+    VEM_CUDA(h, cudaMemcpyAsync(hf, fl, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+    return VEM_OK;
+  };
+  VEM_TRY(flags());
+  while (hf[1] > 0.0 && it < h->opt.maxit) {
+    count_launch();
+    k_sys_scale<<<grid_for(N, 256), 256, 0, s>>>(nb, op.n_u1, op.n_p1, N, tmp, gs + L.S(GS_FAC), L.size(), V);
+    for (int j = 0; j < m && it < h->opt.maxit; ++j) {
+      ++it;
+      double *Vj = V + (size_t)j * N, *Zj = Z + (size_t)j * N, *w = V + (size_t)(j + 1) * N;
+      VEM_TRY(sys_precond(h, op, Vj, Zj, pw, gs + L.S(GS_ACTIVE), L.size(), &inner));
+      op_apply_timed(h, op, Zj, w);
+      // classical Gram-Schmidt per system; the first pass's dots include
+      // w = V_{j+1} itself (||w||^2 before the pass, at o1 + j + 1); the
+      // second pass only where the DGKS test asks, decided on the device
+      VEM_TRY(sys_dots(h, op, V, 0, j + 2, w, dd, ldd, o1));
+      count_launch();
+      k_sys_axpy<<<grid_for(N, 256), 256, 0, s>>>(nb, op.n_u1, op.n_p1, N, j + 1, V, dd + o1, ldd, -1.0, w, nullptr);
+      VEM_TRY(sys_dots(h, op, w, 0, 1, w, dd, ldd, on));
+      count_launch();
+      k_sys_reorth<<<1, 256, 0, s>>>(nb, gs + L.S(GS_ACTIVE), L.size(), dd, ldd, o1 + j + 1, on, o2, j + 1, ro,
+                                     fl + 4);
+      VEM_TRY(sys_dots(h, op, V, 0, j + 1, w, dd, ldd, o2, fl + 4));
+      count_launch();
+      k_sys_axpy<<<grid_for(N, 256), 256, 0, s>>>(nb, op.n_u1, op.n_p1, N, j + 1, V, dd + o2, ldd, -1.0, w, fl + 4);
+      VEM_TRY(sys_dots(h, op, w, 0, 1, w, dd, ldd, on, fl + 4));
+      count_launch();
+      k_sys_arnoldi<<<gnb, 128, 0, s>>>(nb, j, L, rtol, dd, ldd, o1, o2, on, gs);
+      count_launch();
+      k_sys_scale<<<grid_for(N, 256), 256, 0, s>>>(nb, op.n_u1, op.n_p1, N, w, gs + L.S(GS_FAC), L.size(), w);
+      VEM_TRY(flags());
+      if (debug_on()) fprintf(stderr, "[vem] batched fgmres it=%d active=%g open=%g\n", it, hf[0], hf[1]);
+      if (hf[0] == 0.0) break;
+    }
+    // x += Z y per system, then the true residuals and the next start
+    count_launch();
+    k_sys_solve<<<gnb, 128, 0, s>>>(nb, L, gs);
+    count_launch();
+    k_sys_axpy<<<grid_for(N, 256), 256, 0, s>>>(nb, op.n_u1, op.n_p1, N, m, Z, gs + L.Y(0), L.size(), 1.0, x,
+                                                nullptr);
+    op_apply_timed(h, op, x, V);
+    count_launch();
+    k_sub_vec<<<grid_for(N, 256), 256, 0, s>>>(N, rhs, V, tmp);
+    VEM_TRY(sys_dots(h, op, tmp, 0, 1, tmp, dd, ldd, orr));
+    count_launch();
+    k_sys_start<<<gnb, 128, 0, s>>>(nb, L, rtol, dd, ldd, orr, obb, gs, 0);
+    VEM_TRY(flags());
+  }
+  std::vector<double> q((size_t)nb * L.size());
+  VEM_CUDA(h, cudaMemcpyAsync(q.data(), gs, sizeof(double) * q.size(), cudaMemcpyDeviceToHost, s));
+  VEM_CUDA(h, cudaStreamSynchronize(s));
+  double worst = 0.0;
+  int itmax = 0;
+  for (int b = 0; b < nb; ++b) {
+    const double rel = q[(size_t)b * L.size() + L.S(GS_REL)];
+    if (relres) relres[b] = rel;
+    worst = std::max(worst, rel);
+    itmax = std::max(itmax, (int)q[(size_t)b * L.size() + L.S(GS_IT)]);
+  }
+  st->iterations = itmax;
+  st->inner_iterations = inner;
+  st->relres = worst;
+  if (cudaStreamSynchronize(s) == cudaSuccess) collect_saddle(h);
+  cudaGetLastError();
+  if (hf[1] > 0.0)
+    return fail(h, VEM_ERR_NOT_CONVERGED, "batched FGMRES: %g systems above rtol after %d iterations", hf[1], it);
+  return VEM_OK;
+}
+
 VemOp single_op(vem_handle *h) {
   VemOp op;
   op.A = h->A;

@@ -55,3 +55,30 @@ def test_batched_rejects_bad_K(vs):
     with pytest.raises(vs.VemError) as e:
         s.solve_batched(K)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_batched_systems_are_independent(vs, precision):
+    """Every system of a batch runs its own FGMRES and its own inner PCG
+    (own scalars, own stopping test): with the batch size and position fixed,
+    a system's solution does not depend, bit for bit, on the other systems,
+    and a system with zero data stops at once while the others iterate."""
+    mesh = hex_mesh(5)
+    nc = mesh.n_cells
+    K = [fields.K_lognormal(nc, seed=300 + b, sigma=2.0) for b in range(3)]
+    s = vs.Solver(mesh, element=0, krylov=1, precond=1, precision=precision, rtol=1e-10,
+                  inner_rtol=1e-8 if precision == 0 else 1e-5, maxit=3000)
+    xc = s.quadrature_points(vs.VEM_QP_CELL)
+    F0 = fields.fourier_source(400)(xc)
+    F1 = fields.fourier_source(401)(xc)
+    try:
+        Ua, Pa, ra, _ = s.solve_batched(np.stack([K[0], K[1]]), np.stack([F0, F1]), None)
+        Ub, Pb, rb, _ = s.solve_batched(np.stack([K[0], K[2]]), np.stack([F0, 3.0 * F1]), None)
+        Uc, Pc, rc, _ = s.solve_batched(np.stack([K[0], K[1]]), np.stack([F0, np.zeros(nc)]), None)
+    finally:
+        s.close()
+    np.testing.assert_array_equal(Ua[0], Ub[0])
+    np.testing.assert_array_equal(Pa[0], Pb[0])
+    np.testing.assert_array_equal(Ua[0], Uc[0])
+    assert np.all(Uc[1] == 0.0) and np.all(Pc[1] == 0.0)
+    assert ra[0] <= 1e-10 and rb[1] <= 1e-10
