@@ -1055,14 +1055,15 @@ def run_workload(a):
                      "f64 outer / f32 Schur solve",
                      {"workload": w, "systems": nb, "cells": mesh.n_cells, "n_per_system": n_u + n_p, "element": "E0",
                       "K": "exp(2 xi) per cell and system", "f": "8 Fourier modes per system",
-                      "krylov": "FGMRES(30) on the stacked block-diagonal system",
-                      "precond": "block upper-triangular, FP32 Jacobi-PCG 1e-1"},
+                      "krylov": "FGMRES(30), one Krylov process per system (own scalars and stopping test)",
+                      "precond": "block upper-triangular, per-system FP32 Jacobi-PCG 1e-1"},
                      iterations=st["iterations"], inner_iterations=st["inner_iterations"],
                      worst_relres=float(np.max(rel)),
                      schur_tile_systems=st["schur_tile"],
-                     schur_tile_note="systems per 32-row tile of the batched Schur SpMV, picked by the autotuner "
-                                     "from 1, 2, 4, 8 (timed on the live vectors at the first solve)",
-                     cuda_graphs="inner CG iterations replayed as a CUDA graph of 4 iterations",
+                     schur_tile_note="tile of the per-system Schur SpMV, rows x systems (reported as "
+                                     "100 * slices + systems), picked by the autotuner from 32 or 64 rows x 1, 2, "
+                                     "4, 8 systems (timed on the live vectors at the first solve of a shape)",
+                     cuda_graphs="inner CG iterations replayed as CUDA graphs of 16 and 4 iterations",
                      timings=timings, speedups=effects,
                      speedup_vs_sequential_fp64=effects["total_vs_sequential_fp64"],
                      max_rel_diff_vs_fp64_u=max(diffs))

@@ -1319,63 +1319,162 @@ __global__ void __launch_bounds__(256) k_bcg_init(int nb, int64_t n1, const doub
 
 // w = S u for every system not done, with per-(system, slice) partials of
 // (r, u) and (w, u): part_ru[b nsl + s], part_wu[b nsl + s].  A warp task is
-// one 32-row slice of kR consecutive systems, so each column id is read once
-// for kR value streams and gathers; tasks whose systems are all done are
-// skipped.
-template <class T, int kR>
+// a tile of kS consecutive 32-row slices of kR consecutive systems: each
+// column id is read once for kR value streams and gathers, and a thread
+// carries kS x kR independent sums.  Tasks whose systems are all done are
+// skipped.  flag == nullptr: the autotuner's timing launches (every system
+// taken as live).
+template <class T, int kR, int kS>
 __global__ void __launch_bounds__(256) k_bcg_spmv(int nb, int64_t rows, int64_t nsl, int64_t stored,
                                                   const int64_t *__restrict__ off, const int32_t *__restrict__ col,
                                                   const T *__restrict__ val, const T *__restrict__ u,
                                                   const T *__restrict__ r, T *w, double *part_ru, double *part_wu,
                                                   const double *bsc, const double *flag) {
-  if (all_done(flag)) return;
+  if (flag && all_done(flag)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t groups = (nb + kR - 1) / kR;
-  for (int64_t tk = warp; tk < nsl * groups; tk += nwarps) {
-    const int64_t g = tk / nsl, sl = tk - g * nsl;
+  const int64_t groups = (nb + kR - 1) / kR, stiles = (nsl + kS - 1) / kS;
+  for (int64_t tk = warp; tk < stiles * groups; tk += nwarps) {
+    const int64_t g = tk / stiles, st0 = (tk - g * stiles) * kS;
     const int b0 = (int)(g * kR);
     bool live[kR];
     bool any = false;
 #pragma unroll
     for (int q = 0; q < kR; ++q) {
-      live[q] = (b0 + q < nb) && bsc[BC_DONE * nb + b0 + q] == 0.0;
+      live[q] = (b0 + q < nb) && (!flag || bsc[BC_DONE * nb + b0 + q] == 0.0);
       any = any || live[q];
     }
     if (!any) continue;   // uniform over the warp
-    const int64_t o = off[sl];
-    const int wdt = (int)((off[sl + 1] - o) >> 5);
-    T acc[kR];
 #pragma unroll
-    for (int q = 0; q < kR; ++q) acc[q] = 0;
-#pragma unroll 2
-    for (int j = 0; j < wdt; ++j) {
-      const int64_t pos = o + 32 * (int64_t)j + lane;
-      const int32_t c = __ldcs(col + pos);
+    for (int k = 0; k < kS; ++k) {
+      const int64_t sl = st0 + k;
+      if (sl >= nsl) break;
+      const int64_t o = off[sl];
+      const int wdt = (int)((off[sl + 1] - o) >> 5);
+      T acc[kR];
 #pragma unroll
-      for (int q = 0; q < kR; ++q)
-        if (live[q]) acc[q] += __ldcs(val + (int64_t)(b0 + q) * stored + pos) * __ldg(u + (int64_t)(b0 + q) * rows + c);
-    }
-    const int64_t i = 32 * sl + lane;
+      for (int q = 0; q < kR; ++q) acc[q] = 0;
+      // kB entries per step (predicated on the slice width): their column
+      // ids first, then the kR x kB values and gathers, then the FMAs
+      constexpr int kB = kR >= 8 ? 1 : 8 / kR;
+      for (int j = 0; j < wdt; j += kB) {
+        int32_t c[kB];
 #pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      if (!live[q]) continue;
-      double gam = 0.0, del = 0.0;
-      if (i < rows) {
-        const int64_t gi = (int64_t)(b0 + q) * rows + i;
-        w[gi] = acc[q];
-        gam = (double)r[gi] * (double)u[gi];
-        del = (double)acc[q] * (double)u[gi];
+        for (int t = 0; t < kB; ++t) c[t] = (j + t < wdt) ? __ldcs(col + o + 32 * (int64_t)(j + t) + lane) : 0;
+        T v[kR][kB], xg[kR][kB];
+#pragma unroll
+        for (int q = 0; q < kR; ++q)
+#pragma unroll
+          for (int t = 0; t < kB; ++t) {
+            const bool ok = live[q] && (j + t < wdt);
+            v[q][t] = ok ? __ldcs(val + (int64_t)(b0 + q) * stored + o + 32 * (int64_t)(j + t) + lane) : T(0);
+            xg[q][t] = ok ? __ldg(u + (int64_t)(b0 + q) * rows + c[t]) : T(0);
+          }
+#pragma unroll
+        for (int q = 0; q < kR; ++q)
+#pragma unroll
+          for (int t = 0; t < kB; ++t) acc[q] += v[q][t] * xg[q][t];
       }
-      gam = warp_sum(gam);
-      del = warp_sum(del);
-      if (lane == 0) {
-        part_ru[(int64_t)(b0 + q) * nsl + sl] = gam;
-        part_wu[(int64_t)(b0 + q) * nsl + sl] = del;
+      const int64_t i = 32 * sl + lane;
+#pragma unroll
+      for (int q = 0; q < kR; ++q) {
+        if (!live[q]) continue;
+        // products and the warp's sums in T (no FP64 work per row in the
+        // FP32 form); one conversion per slice
+        T gam = 0, del = 0;
+        if (i < rows) {
+          const int64_t gi = (int64_t)(b0 + q) * rows + i;
+          w[gi] = acc[q];
+          gam = r[gi] * u[gi];
+          del = acc[q] * u[gi];
+        }
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+          gam += __shfl_xor_sync(0xffffffffu, gam, o2);
+          del += __shfl_xor_sync(0xffffffffu, del, o2);
+        }
+        if (lane == 0) {
+          part_ru[(int64_t)(b0 + q) * nsl + sl] = (double)gam;
+          part_wu[(int64_t)(b0 + q) * nsl + sl] = (double)del;
+        }
       }
     }
   }
+}
+
+// One launch of the per-system Schur SpMV with the tile code 100 kS + kR.
+template <class T, int kR, int kS>
+static void bspmv_launch_t(cudaStream_t s, int nb, const VemOp &op, const T *sval, const T *u, const T *r, T *w,
+                           double *ru, double *wu, const double *bsc, const double *flag) {
+  static int cap = 0;
+  if (cap == 0) cap = one_wave_blocks((const void *)k_bcg_spmv<T, kR, kS>);
+  const int64_t nsl = op.S.nslices;
+  int64_t g = (((nsl + kS - 1) / kS) * ((nb + kR - 1) / kR) + 7) / 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  count_launch();
+  k_bcg_spmv<T, kR, kS><<<(int)g, 256, 0, s>>>(nb, op.n_p1, nsl, op.S.stored, op.S.off, op.S.col, sval, u, r, w, ru,
+                                               wu, bsc, flag);
+}
+
+template <class T>
+static void bspmv_launch(cudaStream_t s, int tile, int nb, const VemOp &op, const T *sval, const T *u, const T *r,
+                         T *w, double *ru, double *wu, const double *bsc, const double *flag) {
+  switch (tile) {
+    case 101: bspmv_launch_t<T, 1, 1>(s, nb, op, sval, u, r, w, ru, wu, bsc, flag); break;
+    case 102: bspmv_launch_t<T, 2, 1>(s, nb, op, sval, u, r, w, ru, wu, bsc, flag); break;
+    case 108: bspmv_launch_t<T, 8, 1>(s, nb, op, sval, u, r, w, ru, wu, bsc, flag); break;
+    case 201: bspmv_launch_t<T, 1, 2>(s, nb, op, sval, u, r, w, ru, wu, bsc, flag); break;
+    case 202: bspmv_launch_t<T, 2, 2>(s, nb, op, sval, u, r, w, ru, wu, bsc, flag); break;
+    case 204: bspmv_launch_t<T, 4, 2>(s, nb, op, sval, u, r, w, ru, wu, bsc, flag); break;
+    case 208: bspmv_launch_t<T, 8, 2>(s, nb, op, sval, u, r, w, ru, wu, bsc, flag); break;
+    default: bspmv_launch_t<T, 4, 1>(s, nb, op, sval, u, r, w, ru, wu, bsc, flag); break;
+  }
+}
+
+// Autotuner of the per-system Schur SpMV's tile (32 or 64 rows x 1, 2, 4 or 8
+// systems): on the first solve of a shape (rows, slices, systems, value
+// type) every tile runs three timed launches on the live vectors (after one
+// warm-up; every system taken as live), with CUDA events on the stream; the
+// fastest is kept for the process (per device and shape; a mutex guards the
+// shared cache).  The launches write only w and the partial sums, which the
+// solve recomputes before reading.
+template <class T>
+static int tune_bspmv(vem_handle *h, int nb, const VemOp &op, const T *sval, const T *u, const T *r, T *w,
+                      double *ru, double *wu) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int64_t, int64_t, int, int>, int> best;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, op.S.rows, op.S.nslices, nb, (int)sizeof(T));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = best.find(key);
+    if (it != best.end()) return it->second;
+  }
+  int pick = 104;
+  float pick_ms = 1e30f;
+  for (int tile : {101, 102, 104, 108, 201, 202, 204, 208}) {
+    if (tile % 100 > 1 && tile % 100 > nb) continue;
+    bspmv_launch<T>(h->stream, tile, nb, op, sval, u, r, w, ru, wu, nullptr, nullptr);
+    cudaEventRecord(h->ev2, h->stream);
+    for (int k = 0; k < 3; ++k) bspmv_launch<T>(h->stream, tile, nb, op, sval, u, r, w, ru, wu, nullptr, nullptr);
+    cudaEventRecord(h->ev3, h->stream);
+    cudaEventSynchronize(h->ev3);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev2, h->ev3) == cudaSuccess && ms < pick_ms) {
+      pick_ms = ms;
+      pick = tile;
+    }
+  }
+  cudaGetLastError();
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    best[key] = pick;
+  }
+  if (debug_on()) fprintf(stderr, "[vem] per-system Schur SpMV tile: %d (%.3f ms / 3)\n", pick, pick_ms);
+  return pick;
 }
 
 // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r for
@@ -1389,7 +1488,7 @@ __global__ void __launch_bounds__(256) k_bcg_update(int nb, int64_t n1, T *x, T 
   const int sb = blockIdx.y, P = gridDim.x;
   if (bsc[BC_DONE * nb + sb] != 0.0) return;   // uniform over the block
   const T alpha = (T)bsc[BC_ALPHA * nb + sb], beta = (T)bsc[BC_BETA * nb + sb];
-  double acc = 0.0;
+  T acct = 0;   // (r, r) of this thread's rows in T, as the single-system update
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n1; t += (int64_t)P * blockDim.x) {
     const int64_t i = (int64_t)sb * n1 + t;
     const T pi = u[i] + beta * p[i];
@@ -1400,9 +1499,9 @@ __global__ void __launch_bounds__(256) k_bcg_update(int nb, int64_t n1, T *x, T 
     s[i] = si;
     r[i] = ri;
     u[i] = dinv[i] * ri;
-    acc += (double)ri * (double)ri;
+    acct += ri * ri;
   }
-  acc = warp_sum(acc);
+  double acc = warp_sum((double)acct);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1701,26 +1800,19 @@ static vem_status bpcg_solve(vem_handle *h, const VemOp &op, const T *sval, cons
   double *bsc = h->bc_sc, *flag = h->bc_sc + BC_N * nb;
   unsigned int *tick = reinterpret_cast<unsigned int *>(flag + 2);
   const double tol2 = h->opt.inner_rtol * h->opt.inner_rtol;
-  constexpr int kR = 4;
-  static int cap = 0;
-  if (cap == 0) cap = one_wave_blocks((const void *)k_bcg_spmv<T, kR>);
-  int64_t gsp = (nsl * ((nb + kR - 1) / kR) + 7) / 8;
-  if (gsp > cap) gsp = cap;
-  if (gsp < 1) gsp = 1;
+  // the tile of the Schur SpMV: the autotuner's choice for this shape
+  const int tile = tune_bspmv<T>(h, nb, op, sval, u, r, w, ru, wu);
+  h->schur_tile = tile;
   count_launch();
   k_bcg_init<T><<<dim3(P, nb), 256, 0, s>>>(nb, n1, b, dinv, x, r, u, p, sv, rr, bsc, active, lda, flag);
-  count_launch();
-  k_bcg_spmv<T, kR><<<(int)gsp, 256, 0, s>>>(nb, n1, nsl, op.S.stored, op.S.off, op.S.col, sval, u, r, w, ru, wu,
-                                             bsc, flag);
+  bspmv_launch<T>(s, tile, nb, op, sval, u, r, w, ru, wu, bsc, flag);
   count_launch();
   k_bcg_scalars<<<nb, 256, 0, s>>>(nb, nsl, P, ru, wu, rr, tol2, bsc, 1, flag, tick);
   auto iteration = [&]() {
     cudaStream_t cs = h->stream;
     count_launch();
     k_bcg_update<T><<<dim3(P, nb), 256, 0, cs>>>(nb, n1, x, r, u, p, sv, w, dinv, bsc, rr, flag);
-    count_launch();
-    k_bcg_spmv<T, kR><<<(int)gsp, 256, 0, cs>>>(nb, n1, nsl, op.S.stored, op.S.off, op.S.col, sval, u, r, w, ru,
-                                                wu, bsc, flag);
+    bspmv_launch<T>(cs, tile, nb, op, sval, u, r, w, ru, wu, bsc, flag);
     count_launch();
     k_bcg_scalars<<<nb, 256, 0, cs>>>(nb, nsl, P, ru, wu, rr, tol2, bsc, 0, flag, tick);
   };
@@ -1728,7 +1820,7 @@ static vem_status bpcg_solve(vem_handle *h, const VemOp &op, const T *sval, cons
   std::memcpy(&tol_bits, &tol2, sizeof(double));
   const std::vector<uintptr_t> key = {(uintptr_t)op.S.off, (uintptr_t)op.S.col, (uintptr_t)sval, (uintptr_t)dinv,
                                       (uintptr_t)x, (uintptr_t)wk, (uintptr_t)bsc, (uintptr_t)ru, (uintptr_t)nb,
-                                      (uintptr_t)n1, (uintptr_t)P, (uintptr_t)gsp, (uintptr_t)tol_bits,
+                                      (uintptr_t)n1, (uintptr_t)P, (uintptr_t)tile, (uintptr_t)tol_bits,
                                       sizeof(T), (uintptr_t)op.S.stored};
   bool graph = h->bpcg_graph && h->bpcg_graph16 && h->bpcg_key == key;
   if (!graph) {
