@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--workload", default="hex128-k1",
                     choices=["hex128-k1", "hex8-e0-minres", "cvt200k-e0-mixed", "hex64-e0-batch64",
                              "cvt100k-adjoint", "cube32-k1-neumann", "cube32-k1-blockreg", "optimality-k1",
-                             "cube24-k2", "cvt27k-k2-element", "optimality-k2", "cvt200k-k1-element"],
+                             "cube24-k2", "cvt27k-k2-element", "optimality-k2", "cvt200k-k1-element",
+                             "hex128-k2"],
                     help="hex128-k1 is the headline; the others are the remaining configurations")
     ap.add_argument("--profile", action="store_true",
                     help="one step only (for an ncu launch list); prints a short JSON line")
@@ -777,6 +778,88 @@ def run_workload(a):
                          res["block-amg-1e-2"]["ms_per_step"], res["block-amg-1e-1"]["ms_per_step"]),
                      paper_note="paper (Block-Schur, block-diagonal with MUMPS on S): 72 GMRES iterations, T_ass "
                                 "271 s, T_sol 347 s on 1 core of 2x Xeon E5-2683 v4; context only")
+    elif w == "hex128-k2":
+        # The 128^3 unit cube with the paper's k = 2 element (the other
+        # reading of the 128^3 configuration: 6 face moments against M_2(f),
+        # 3 gradient + 11 cross moments, 4 P1 pressure moments per cell):
+        # 2,097,152 cells, 75.8 M unknowns, about 5.9e9 stored matrix entries.
+        # K = 1, Dirichlet data; FGMRES(30) to 1e-8 with the block
+        # upper-triangular preconditioner, S by CG with one V-cycle of the
+        # point-block AMG to 1e-2.  Two data sets: the configuration's
+        # p = sin(pi x) sin(pi y) sin(pi z), and the paper's polynomial
+        # solution (not an eigenvector of S).  f is evaluated on the device at
+        # the 1.36e9 cell quadrature points (648 per cell), checked against
+        # the host formula on a sample.
+        n_side = a.n
+        mesh = hex_mesh(n_side)
+        s = vs.Solver(mesh, stream=sid, device_io=1, element=vs.VEM_ELEMENT_K2, krylov=1, precond=1, restart=30,
+                      rtol=1e-8, inner=vs.VEM_INNER_BLOCK_AMG, inner_rtol=1e-2, inner_maxit=2000, maxit=3000)
+        n_u, n_p = s.sizes()
+        nq = s.quadrature_count(vs.VEM_QP_CELL)
+        pb = s.quadrature_points(vs.VEM_QP_BFACE)
+        pi = np.pi
+
+        def f_sine(X):
+            return 3 * pi ** 2 * torch.sin(pi * X[:, 0]) * torch.sin(pi * X[:, 1]) * torch.sin(pi * X[:, 2])
+
+        def f_poly(X):
+            x, y, z = X[:, 0], X[:, 1], X[:, 2]
+            return -(20 * x ** 3 + 72 * y ** 2 + 54 * z + 2 * x * z ** 3 + 6 * x * y ** 2 * z)
+
+        def cell_means_sine():
+            # exact cell means of p on the uniform grid: products of
+            # (cos(pi a) - cos(pi (a + h))) / (pi h) per direction
+            hh = 1.0 / n_side
+            a0 = torch.arange(n_side, dtype=torch.float64, device="cuda") * hh
+            m1 = (torch.cos(pi * a0) - torch.cos(pi * (a0 + hh))) / (pi * hh)
+            cz, cy, cx = torch.meshgrid(m1, m1, m1, indexing="ij")
+            return (cx * cy * cz).reshape(-1)
+
+        legs = {}
+        for dname, prob, fdev in (("sine", fields.sine_problem(), f_sine),
+                                  ("paper_polynomial", fields.paper_polynomial_problem(), f_poly)):
+            X = torch.empty((nq, 3), dtype=torch.float64, device="cuda")
+            s.quadrature_points(vs.VEM_QP_CELL, out=X)
+            fq = torch.empty(nq, dtype=torch.float64, device="cuda")
+            chunk = 1 << 26
+            for i0 in range(0, nq, chunk):
+                fq[i0:i0 + chunk] = fdev(X[i0:i0 + chunk])
+            sample = X[:: max(1, nq // 100000)].cpu().numpy()
+            ref = prob.f(sample)
+            got = fq[:: max(1, nq // 100000)].cpu().numpy()
+            assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max()), "device f disagrees"
+            del X
+            gq = torch.from_numpy(np.ascontiguousarray(prob.gD(pb))).cuda()
+            s.set_source(fq, gq)
+            del fq, gq
+            torch.cuda.empty_cache()
+            u = torch.empty(n_u, dtype=torch.float64, device="cuda")
+            p = torch.empty(n_p, dtype=torch.float64, device="cuda")
+
+            def step():
+                s.assemble()
+                return s.solve(u_out=u, p_out=p)[2]
+            ms_l, st_l = _timed(step, a.steps, a.warmup, stream)
+            leg = {"ms_per_step": ms_l, "dofs_per_s": (n_u + n_p) / (ms_l * 1e-3), "iterations": st_l["iterations"],
+                   "inner_iterations": st_l["inner_iterations"], "relres": st_l["relres"],
+                   "t_assemble_ms": st_l["t_assemble_ms"], "t_element_ms": st_l["t_element_ms"],
+                   "t_amg_setup_ms": st_l["t_amg_setup_ms"], "t_solve_ms": st_l["t_solve_ms"],
+                   "amg_levels": st_l["amg_levels"], "nnz_A": st_l["nnz_A"], "nnz_S": st_l["nnz_S"]}
+            if dname == "sine":
+                e = p[0::4] - cell_means_sine()
+                leg["pressure_mean_error_max"] = float(e.abs().max())
+            legs[dname] = leg
+            del u, p
+        s.close()
+        torch.cuda.empty_cache()
+        ms = legs["sine"]["ms_per_step"]
+        line = _line(a, "time-to-solution (rel.res 1e-8) and DOFs/s", (n_u + n_p) / (ms * 1e-3), "DOFs/s", ms,
+                     "f64", {"workload": w, "cells": mesh.n_cells, "n_u": n_u, "n_p": n_p,
+                             "element": "paper k=2 (6 face moments, 3 gradient + 11 cross moments, P1 pressure)",
+                             "bc": "Dirichlet", "krylov": "FGMRES(30), rtol 1e-8",
+                             "precond": "block upper-triangular, S by point-block AMG-PCG to 1e-2",
+                             "cell_quadrature_points": nq, "l2_flush": "inputs larger than L2"},
+                     legs=legs)
     elif w == "cvt27k-k2-element":
         # The element kernel of the paper's k = 2 element on a 27,000-cell
         # CVT mesh (every cell its own class): the assembly stage that the
@@ -826,13 +909,17 @@ def run_workload(a):
         # tables, Tables 4-6) on Cube, Octa and CVT meshes in the paper's
         # setting: flux data of its polynomial solution on the whole
         # boundary, mean-zero pressure, Block-Schur (block-diagonal, S by
-        # Jacobi-PCG to 1e-8), FGMRES(30) to 1e-8.
+        # Jacobi-PCG and by point-block AMG-PCG to 1e-8) and Block-Reg (the
+        # condensed cycle), FGMRES(30) to 1e-8; the paper's mesh sizes.
         prob = fields.paper_polynomial_problem()
         rows = []
         total_ms = 0.0
         n_all = 0
-        cases = ([("cube", n) for n in (8, 16, 20, 24)] + [("octa", n) for n in (2, 4, 8)]
-                 + [("cvt", n) for n in (125, 1000, 4000)])
+        cases = ([("cube", n) for n in (8, 16, 20, 24, 28)] + [("octa", n) for n in (2, 4, 8, 10, 12)]
+                 + [("cvt", n) for n in (27, 125, 1000, 4000, 8000)])
+        precs = {"jacobi_pcg": dict(precond=0, inner=vs.VEM_INNER_PCG, inner_rtol=1e-8, inner_maxit=4000),
+                 "block_amg": dict(precond=0, inner=vs.VEM_INNER_BLOCK_AMG, inner_rtol=1e-8, inner_maxit=4000),
+                 "block_reg_condensed": dict(precond=vs.VEM_PREC_BLOCK_REG, reg_cycle=vs.VEM_REG_CONDENSED)}
         for kind, n in cases:
             if kind == "cube":
                 mesh = hex_mesh(n, bc=2)
@@ -842,10 +929,9 @@ def run_workload(a):
                 mesh = voronoi_mesh(n, seed=7, lloyd=10)
                 mesh.face_bc = np.where(mesh.face_bc != 0, 2, 0).astype(np.int8)
             row = {"mesh": f"{kind}{n}", "cells": mesh.n_cells}
-            for iname, inner in (("jacobi_pcg", vs.VEM_INNER_PCG), ("block_amg", vs.VEM_INNER_BLOCK_AMG)):
-                s = vs.Solver(mesh, stream=sid, device_io=1, element=vs.VEM_ELEMENT_K2, krylov=1, precond=0,
-                              restart=30, rtol=1e-8, inner=inner, inner_rtol=1e-8, inner_maxit=4000,
-                              maxit=5000)
+            for iname, popt in precs.items():
+                s = vs.Solver(mesh, stream=sid, device_io=1, element=vs.VEM_ELEMENT_K2, krylov=1, restart=30,
+                              rtol=1e-8, maxit=5000, **popt)
                 s.set_data(prob.f, prob.gD, flux=prob.u)
                 n_u, n_p = s.sizes()
                 u = torch.empty(n_u, dtype=torch.float64, device="cuda")
@@ -863,14 +949,17 @@ def run_workload(a):
                               "inner_per_outer": st["inner_iterations"] / max(1, st["iterations"]),
                               "relres": st["relres"], "ms": ms}
             rows.append(row)
-        line = _line(a, "GMRES iterations under refinement at k = 2 (Block-Schur) and DOFs/s",
+        line = _line(a, "GMRES iterations under refinement at k = 2 (Block-Schur, Block-Reg) and DOFs/s",
                      n_all / (total_ms * 1e-3), "DOFs/s", total_ms, "f64",
                      {"workload": w, "element": "paper k=2", "bc": "flux on the whole boundary, mean-zero p",
-                      "precond": "Block-Schur (block-diagonal, S to 1e-8 by Jacobi-PCG and by point-block AMG-PCG)",
+                      "precond": "Block-Schur (block-diagonal, S to 1e-8 by Jacobi-PCG and by point-block AMG-PCG) "
+                                 "and Block-Reg (A + B^T B/gamma, gamma = h^2, by the condensed point-block cycle)",
                       "krylov": "FGMRES(30)"},
                      runs=rows,
                      paper_block_schur_iterations={"cube": [113, 78, 76, 72, 69], "octa": [367, 498, 598, 559, 631],
                                                    "cvt": [727, 535, 652, 736, 607]},
+                     paper_block_reg_iterations={"cube": [86, 123, 145, 168, 188], "octa": [88, 140, 230, 277, 310],
+                                                 "cvt": [151, 124, 142, 168, 201]},
                      paper_note="the paper's Tables 4-6 (same setting with MUMPS on S, 8 processes, PETSc GMRES "
                                 "tolerance not stated); context only")
     elif w == "optimality-k1":

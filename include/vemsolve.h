@@ -100,9 +100,10 @@ typedef struct {
  * flux faces (the mean-zero pressure then constrains the constant moments,
  * c = |P| on them) and the block-diagonal and block-triangular
  * preconditioners (Jacobi-PCG, the scalar AMG without the multiplier, or
- * the point-block AMG VEM_INNER_BLOCK_AMG for S) and vem_adjoint (Dirichlet
- * boundaries); Block-Reg and vem_solve_batched give VEM_ERR_UNSUPPORTED with
- * it.  Its cell quadrature points
+ * the point-block AMG VEM_INNER_BLOCK_AMG for S), Block-Reg (both reg_cycle
+ * forms; B^T W^-1 B sums over the four pressure rows of a cell) and
+ * vem_adjoint (Dirichlet boundaries); vem_solve_batched gives
+ * VEM_ERR_UNSUPPORTED with it.  Its cell quadrature points
  * (VEM_QP_CELL) are those of a degree-3 rule on the fan tetrahedra of every
  * cell (27 per tetrahedron), built on first use. */
 enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1, VEM_ELEMENT_K2 = 2 };
@@ -143,14 +144,17 @@ enum { VEM_SMOOTH_JACOBI = 0, VEM_SMOOTH_CHEBYSHEV = 1 };
 /* Block-Reg's approximate inverse of A_reg (vem_options.reg_cycle):
  *   SCALAR_AMG  one V-cycle of the scalar smoothed-aggregation AMG of A_reg
  *               (two Chebyshev steps of Jacobi); FP64 or FP32 (MIXED);
- *   CONDENSED   the paper's k = 1 element only, FP64: the interior DOFs of
- *               A_reg, which couple only within their cell, are eliminated
- *               exactly (3 x 3 blocks A_ii), and the face system
+ *   CONDENSED   the paper's k = 1 and k = 2 elements, FP64: the interior
+ *               DOFs of A_reg, which couple only within their cell, are
+ *               eliminated exactly (nid x nid blocks A_ii: 3 x 3 at k = 1,
+ *               14 x 14 at k = 2), and the face system
  *               S_f = A_ff - A_fi A_ii^-1 A_if gets one V-cycle of the
- *               point-block AMG with the 3 face moments of a face as a
- *               block, the face DOFs of the three constant fields as
- *               near-null space and two block-Chebyshev steps; the interior
- *               DOFs are then recovered.  Symmetric positive definite. */
+ *               point-block AMG with the face moments of a face (3 or 6) as
+ *               a block, the face DOFs of the three constant fields as
+ *               near-null space (n_f[j] times the face means of the face
+ *               monomials) and two block-Chebyshev steps; the interior DOFs
+ *               are then recovered.  Symmetric positive definite.  At k = 2
+ *               the scalar cycle barely reduces the residual; use this one. */
 enum { VEM_REG_SCALAR_AMG = 0, VEM_REG_CONDENSED = 1 };
 
 typedef struct {
@@ -251,7 +255,10 @@ vem_status vem_sizes(const vem_handle *h, int64_t *n_u, int64_t *n_p);
  *                         with the 6-point degree-4 rule of Dunavant (1985)
  *                         (n = 6 * sum of those faces' vertex counts).
  * vem_quadrature_count gives n; vem_quadrature_points writes [n][3]
- * coordinates to the host buffer xyz_out.  vem_bface_info writes, for every
+ * coordinates to xyz_out, a host buffer or a device buffer of the handle's
+ * device (the copy's direction follows the pointer; the k = 2 cell set of a
+ * 128^3 mesh holds 1.36e9 points, which are best evaluated where they
+ * are).  vem_bface_info writes, for every
  * VEM_QP_BFACE point, the outward unit normal of its face ([n][3]) and the
  * face flag ([n]); either pointer may be NULL. */
 enum { VEM_QP_CELL = 0, VEM_QP_BFACE = 1 };

@@ -25,7 +25,11 @@ Exact rules:
 * block norm N_IJ = Frobenius norm of the bs x bs block (I, J) of A;
   strong(I, J): J != I and N_IJ >= theta sqrt(N_II N_JJ);
 * aggregates: ``amg.aggregate`` on that graph (isolated blocks stay out of
-  the coarse space);
+  the coarse space); an aggregate on which B has numerical rank below m (a
+  Cholesky pivot of B_a^T B_a at most 1e-10 of its diagonal entry) is
+  dissolved, its blocks left out of the coarse space, and the others are
+  renumbered in order (``dissolve_rank_deficient``; the paper uses PETSc's
+  GAMG and does not describe its coarse spaces, so this rule is ours);
 * T: for aggregate a with member blocks I_1 < I_2 < ..., the rows of its
   DOFs (block by block, component by component) of B have the thin QR
   factorisation Q R with R upper triangular and R_jj > 0 (unique for full
@@ -164,6 +168,41 @@ def qr_positive(X: np.ndarray):
     return Q * s, s[:, None] * R
 
 
+RANK_TOL = 1e-10
+
+
+def dissolve_rank_deficient(agg: np.ndarray, nc: int, B: np.ndarray, bs: int, tol: float = RANK_TOL):
+    """Aggregates on which the near-null space has numerical rank below its
+    width m are dissolved: their blocks leave the coarse space (agg = -1,
+    like blocks without strong neighbours) and the remaining aggregates are
+    renumbered in their order.  Rank test: a pivot of the Cholesky
+    factorisation of the Gram matrix G = B_a^T B_a, d_j = G_jj - sum_{k<j}
+    R_kj^2, at most tol G_jj.  (A face aggregate of Block-Reg's condensed
+    system with fewer than three independent face normals has rank < 3 on
+    the constant fields; without this rule its QR gives a column of rounding
+    noise.)"""
+    m = B.shape[1]
+    keep = np.zeros(nc, dtype=bool)
+    for a in range(nc):
+        members = np.nonzero(agg == a)[0]
+        dofs = (members[:, None] * bs + np.arange(bs)[None, :]).ravel()
+        G = B[dofs].T @ B[dofs]
+        R = np.zeros((m, m))
+        ok = True
+        for j in range(m):
+            d = G[j, j] - R[:j, j] @ R[:j, j]
+            if not d > tol * G[j, j]:
+                ok = False
+                break
+            R[j, j] = np.sqrt(d)
+            for i in range(j + 1, m):
+                R[j, i] = (G[j, i] - R[:j, j] @ R[:j, i]) / R[j, j]
+        keep[a] = ok
+    new_id = np.cumsum(keep) - 1
+    out = np.where((agg >= 0) & keep[np.maximum(agg, 0)], new_id[np.maximum(agg, 0)], -1)
+    return out.astype(agg.dtype), int(keep.sum())
+
+
 def tentative(agg: np.ndarray, nc: int, B: np.ndarray, bs: int):
     """T (n x nc m) and the coarse near-null space (nc m x m)."""
     n, m = B.shape
@@ -233,6 +272,9 @@ def setup(A: sp.csr_matrix, bs: int, B: np.ndarray, theta: float = 0.08, coarse_
         ptr, idx = block_strength(A, bs, th)
         agg, nc = amg.aggregate(nb, ptr, idx)
         if nc == 0 or 5 * nc > 4 * nb:
+            break
+        agg, nc = dissolve_rank_deficient(agg, nc, B, bs)
+        if nc == 0:
             break
         T, Bc = tentative(agg, nc, B, bs)
         P = (T - lv.omega * (Dinv @ (A @ T))).tocsr()

@@ -1032,13 +1032,16 @@ __global__ void k_scale_into(int64_t n, const double *__restrict__ a, double w, 
 //   P = T - omega D^-1 (A T); coarse operator P^T A P with block size m;
 //   cycle: damped block Jacobi (x = omega D^-1 b; ...) or two Chebyshev
 //     steps of block Jacobi on [rho/10, rho].
-constexpr int kMaxBs = 8;   // largest block size
-constexpr int kMaxM = 6;    // largest near-null space width
+constexpr int kMaxBs = 8;    // largest block size
+constexpr int kMaxM = 6;     // largest near-null space width
+constexpr int kMaxInt = 16;  // largest interior block of the condensed cycle (14 at the paper's k = 2)
 
-// D_I^-1 and L_I^-1 (D_I = L_I L_I^T) of every diagonal block, a thread per block.
+// D_I^-1 and L_I^-1 (D_I = L_I L_I^T) of every diagonal block (bs <= kN), a
+// thread per block.
+template <int kN>
 __global__ void k_blk_diag(int64_t nb, int bs, DMat A, double *dinvb, double *linvb, int *err) {
   ROWS_LOOP(I, nb) {
-    double D[kMaxBs][kMaxBs], Lc[kMaxBs][kMaxBs], Li[kMaxBs][kMaxBs];
+    double D[kN][kN], Lc[kN][kN], Li[kN][kN];
     for (int r = 0; r < bs; ++r)
       for (int c = 0; c < bs; ++c) D[r][c] = 0.0, Lc[r][c] = 0.0, Li[r][c] = 0.0;
     const int64_t i0 = I * bs;
@@ -1143,6 +1146,56 @@ __global__ void k_agg_fill(int64_t nb, const int32_t *__restrict__ agg, const in
       col[rp[I]] = agg[I];
       val[rp[I]] = 1.0;
     }
+  }
+}
+
+// Rank test of the near-null space on every aggregate (a thread per
+// aggregate): keep[a] = 1 when every pivot of the Cholesky factorisation of
+// G = B_a^T B_a, d_j = G_jj - sum_{k<j} R_kj^2, exceeds kRankTol G_jj, else 0
+// (the aggregate is then dissolved: with fewer independent modes than m its
+// factorisation would give a column of rounding noise).
+constexpr double kRankTol = 1e-10;
+
+__global__ void k_tent_rank(int64_t nc, int bs, int m, const int64_t *__restrict__ arp,
+                            const int32_t *__restrict__ acol, const double *__restrict__ B, int64_t *keep,
+                            int *err) {
+  ROWS_LOOP(a, nc) {
+    double G[kMaxM][kMaxM], R[kMaxM][kMaxM];
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k < m; ++k) G[j][k] = 0.0, R[j][k] = 0.0;
+    for (int64_t p = arp[a]; p < arp[a + 1]; ++p)
+      for (int c = 0; c < bs; ++c) {
+        const double *x = B + ((int64_t)acol[p] * bs + c) * m;
+        for (int j = 0; j < m; ++j)
+          for (int k = 0; k < m; ++k) G[j][k] += x[j] * x[k];
+      }
+    int64_t ok = 1;
+    for (int j = 0; j < m && ok; ++j) {
+      double d = G[j][j];
+      for (int k = 0; k < j; ++k) d -= R[k][j] * R[k][j];
+      if (!isfinite(d)) atomicOr(err, DEVERR_NONFINITE);
+      if (!(d > kRankTol * G[j][j])) {
+        ok = 0;
+        break;
+      }
+      R[j][j] = sqrt(d);
+      for (int i = j + 1; i < m; ++i) {
+        double v = G[j][i];
+        for (int k = 0; k < j; ++k) v -= R[k][j] * R[k][i];
+        R[j][i] = v / R[j][j];
+      }
+    }
+    keep[a] = ok;
+  }
+}
+
+// agg[I] -> its aggregate's new number (pos: exclusive scan of keep), or -1
+// for a dissolved aggregate.
+__global__ void k_agg_renumber(int64_t nb, const int64_t *__restrict__ keep, const int64_t *__restrict__ pos,
+                               int32_t *agg) {
+  ROWS_LOOP(I, nb) {
+    const int32_t a = agg[I];
+    if (a >= 0) agg[I] = keep[a] ? (int32_t)pos[a] : -1;
   }
 }
 
@@ -2016,7 +2069,7 @@ static vem_status block_level_setup(vem_handle *h, AmgState *S, int l) {
   VEM_TRY(grow(h, L.dblk, L.c_dblk, (size_t)nb * bs * bs));
   VEM_TRY(grow(h, L.lblk, L.c_lblk, (size_t)nb * bs * bs));
   count_launch();
-  k_blk_diag<<<rows_grid(nb), 256, 0, s>>>(nb, bs, A, L.dblk, L.lblk, h->d_err);
+  k_blk_diag<kMaxBs><<<rows_grid(nb), 256, 0, s>>>(nb, bs, A, L.dblk, L.lblk, h->d_err);
   VEM_TRY(check_device_errors(h, "point-block AMG diagonal blocks"));
   // C = L^-1 (A L^-T)
   VEM_TRY(csr_fixed(h, S->bLm, n, n, n * bs));
@@ -2079,13 +2132,32 @@ static vem_status block_coarsen(vem_handle *h, AmgState *S, int l, double theta,
   VEM_TRY(aggregate_graph(h, S, Nv, S->dgb, theta, L.agg, L.mis_rounds, &nc, mx));
   if (nc == 0 || 5 * nc > 4 * nb) return VEM_OK;
   // members of every aggregate in increasing block order
-  VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)nb + 1));
-  count_launch();
-  k_agg_count<<<rows_grid(nb), 256, 0, s>>>(nb, L.agg, S->cnt);
-  VEM_TRY(csr_layout(h, S->bAgg, nb, nc, S->cnt));
-  count_launch();
-  k_agg_fill<<<rows_grid(nb), 256, 0, s>>>(nb, L.agg, S->bAgg.rp, S->bAgg.col, S->bAgg.val);
-  VEM_TRY(transpose_csr(h, S, S->bAgg, nc, S->bAggT));
+  auto members = [&]() -> vem_status {
+    VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)nb + 1));
+    count_launch();
+    k_agg_count<<<rows_grid(nb), 256, 0, s>>>(nb, L.agg, S->cnt);
+    VEM_TRY(csr_layout(h, S->bAgg, nb, nc, S->cnt));
+    count_launch();
+    k_agg_fill<<<rows_grid(nb), 256, 0, s>>>(nb, L.agg, S->bAgg.rp, S->bAgg.col, S->bAgg.val);
+    return transpose_csr(h, S, S->bAgg, nc, S->bAggT);
+  };
+  VEM_TRY(members());
+  // dissolve the aggregates on which the near-null space loses rank
+  {
+    int64_t *keep = S->cnt;   // nc + 1 <= nb + 1 entries, free after the layout above
+    VEM_TRY(grow(h, S->scn, S->c_scn, (size_t)nc + 1));
+    count_launch();
+    k_tent_rank<<<rows_grid(nc), 256, 0, s>>>(nc, bs, m, S->bAggT.rp, S->bAggT.col, Bl, keep, h->d_err);
+    int64_t nkeep = 0;
+    VEM_TRY(scan_counts(h, nc, keep, S->scn, &nkeep));
+    if (nkeep < nc) {
+      count_launch();
+      k_agg_renumber<<<rows_grid(nb), 256, 0, s>>>(nb, keep, S->scn, L.agg);
+      nc = nkeep;
+      if (nc == 0) return VEM_OK;
+      VEM_TRY(members());
+    }
+  }
   // T and the coarse near-null space
   AmgLevel &Cl = S->lv[l + 1];
   VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)n + 1));
@@ -2469,7 +2541,7 @@ vem_status amg_setup_condensed(vem_handle *h, AmgState *&slot, const SellMat &Ar
   AmgState *S = slot;
   S->valid = false;
   S->condensed = false;
-  if (nid < 1 || nid > kMaxBs || nfd < 1 || nfd > kMaxBs || (Areg.rows - nfr) % nid)
+  if (nid < 1 || nid > kMaxInt || nfd < 1 || nfd > kMaxBs || (Areg.rows - nfr) % nid)
     return fail(h, VEM_ERR_UNSUPPORTED, "condensed Block-Reg cycle: %d interior DOFs per cell", nid);
   cudaStream_t s = h->stream;
   for (cudaEvent_t &e : S->sev)
@@ -2504,7 +2576,7 @@ vem_status amg_setup_condensed(vem_handle *h, AmgState *&slot, const SellMat &Ar
   double *lscr = nullptr;
   VEM_TRY(dalloc_n(h, &lscr, (size_t)nint * nid));
   count_launch();
-  k_blk_diag<<<rows_grid(nc), 256, 0, s>>>(nc, nid, dview(S->cAii), S->aii_inv, lscr, h->d_err);
+  k_blk_diag<kMaxInt><<<rows_grid(nc), 256, 0, s>>>(nc, nid, dview(S->cAii), S->aii_inv, lscr, h->d_err);
   VEM_TRY(check_device_errors(h, "condensed Block-Reg: interior blocks of A_reg"));
   VEM_TRY(csr_fixed(h, S->bLm, nint, nint, nint * nid));
   count_launch();

@@ -638,7 +638,7 @@ vem_status vem_quadrature_points(vem_handle *h, int which, double *xyz_out) {
     return fail(h, VEM_ERR_BAD_INPUT, "unknown quadrature set %d", which);
   }
   if (n > 0)
-    VEM_CUDA(h, cudaMemcpyAsync(xyz_out, src, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    VEM_CUDA(h, cudaMemcpyAsync(xyz_out, src, 3 * n * sizeof(double), cudaMemcpyDefault, h->stream));
   VEM_CUDA(h, cudaStreamSynchronize(h->stream));
   return VEM_OK;
 }

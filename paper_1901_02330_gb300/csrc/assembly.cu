@@ -268,8 +268,9 @@ __global__ void k_eliminate(int64_t rows, const int64_t *__restrict__ off, const
 // P belongs to P alone), so A_reg has the pattern of M: row r of a face DOF
 // gathers the rows of the (at most two) cells of its face, an interior row
 // that of its cell, in the column order of the saddle matrix's flux part.
-// Entry (r, j) of cell P adds B_P(r) B_P(j) / gamma to nu_P M_P(r, j), with
-// B_P(j) = Bloc[b_off + j] (one pressure DOF per cell, k <= 1).
+// Entry (r, j) of cell P adds sum_q B_P(q, r) B_P(q, j) / gamma to
+// nu_P M_P(r, j), with B_P(q, j) = Bloc[b_off + q n_loc + j] (nq pressure
+// DOFs per cell: 1 for k <= 1, the 4 P1 moments for the paper's k = 2).
 __global__ void k_reg_count(Layout L, int64_t *cnt) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n_u;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -285,8 +286,8 @@ __global__ void k_reg_count(Layout L, int64_t *cnt) {
   }
 }
 
-__global__ void k_reg_fill(Layout L, const int64_t *__restrict__ off, int64_t nrows_pad, int32_t *col, double *val,
-                           const double *__restrict__ nu_scale, double ig) {
+__global__ void k_reg_fill(Layout L, int nq, const int64_t *__restrict__ off, int64_t nrows_pad, int32_t *col,
+                           double *val, const double *__restrict__ nu_scale, double ig) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows_pad;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s0 = off[r >> 5];
@@ -311,24 +312,29 @@ __global__ void k_reg_fill(Layout L, const int64_t *__restrict__ off, int64_t nr
       const int jr0 = l0 * L.nfd + beta;
       const double *M0 = mloc(L, c0) + (int64_t)jr0 * n0;
       const double *B0 = L.Bloc + boff(L, c0);
-      const double w0 = nu_scale[c0], g0 = ig * B0[jr0];
+      const double w0 = nu_scale[c0];
+      double g0[4], g1[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int q = 0; q < nq; ++q) g0[q] = ig * B0[q * n0 + jr0];
       const double *M1 = nullptr, *B1 = nullptr;
       int n1 = 0;
-      double w1 = 0.0, g1 = 0.0;
+      double w1 = 0.0;
       if (c1 >= 0) {
         n1 = nloc(L, c1);
         const int jr1 = l1 * L.nfd + beta;
         M1 = mloc(L, c1) + (int64_t)jr1 * n1;
         B1 = L.Bloc + boff(L, c1);
         w1 = nu_scale[c1];
-        g1 = ig * B1[jr1];
+        for (int q = 0; q < nq; ++q) g1[q] = ig * B1[q * n1 + jr1];
       }
       for (int jl = 0; jl < n0; ++jl) {
-        double v = w0 * M0[jl] + g0 * B0[jl];
+        double v = w0 * M0[jl];
+        for (int q = 0; q < nq; ++q) v += g0[q] * B0[q * n0 + jl];
         const bool shared = (jl < n0 - L.nid) && (jl / L.nfd == l0);
         if (c1 >= 0 && shared) {
           const int j1 = l1 * L.nfd + jl % L.nfd;
-          v += w1 * M1[j1] + g1 * B1[j1];
+          double v1 = w1 * M1[j1];
+          for (int q = 0; q < nq; ++q) v1 += g1[q] * B1[q * n1 + j1];
+          v += v1;
         }
         PUT(gcol(L, c0, jl), v);
       }
@@ -336,7 +342,9 @@ __global__ void k_reg_fill(Layout L, const int64_t *__restrict__ off, int64_t nr
         const int k1 = (n1 - L.nid) / L.nfd;
         for (int jl = 0; jl < n1; ++jl) {
           if (jl < L.nfd * k1 && jl / L.nfd == l1) continue;
-          PUT(gcol(L, c1, jl), w1 * M1[jl] + g1 * B1[jl]);
+          double v1 = w1 * M1[jl];
+          for (int q = 0; q < nq; ++q) v1 += g1[q] * B1[q * n1 + jl];
+          PUT(gcol(L, c1, jl), v1);
         }
       }
     } else {
@@ -347,8 +355,14 @@ __global__ void k_reg_fill(Layout L, const int64_t *__restrict__ off, int64_t nr
       const int jr = nl - L.nid + l;
       const double *Mr = mloc(L, c) + (int64_t)jr * nl;
       const double *Bc = L.Bloc + boff(L, c);
-      const double wc = nu_scale[c], gc = ig * Bc[jr];
-      for (int jl = 0; jl < nl; ++jl) PUT(gcol(L, c, jl), wc * Mr[jl] + gc * Bc[jl]);
+      const double wc = nu_scale[c];
+      double gc[4];
+      for (int q2 = 0; q2 < nq; ++q2) gc[q2] = ig * Bc[q2 * nl + jr];
+      for (int jl = 0; jl < nl; ++jl) {
+        double v = wc * Mr[jl];
+        for (int q2 = 0; q2 < nq; ++q2) v += gc[q2] * Bc[q2 * nl + jl];
+        PUT(gcol(L, c, jl), v);
+      }
     }
     while (j < width) PUT(0, 0.0);
 #undef PUT
@@ -930,8 +944,9 @@ vem_status assemble_reg(vem_handle *h, bool fp32) {
   VEM_CUDA(h, cudaGetLastError());
   VEM_TRY(sell_layout(h, h->Areg, h->n_u, cnt));
   const int64_t npad = h->Areg.nslices * 32;
-  count_launch(); k_reg_fill<<<grid_for(npad, T), T, 0, s>>>(L, h->Areg.off, npad, h->Areg.col, h->Areg.val, h->nu,
-                                                          1.0 / gamma);
+  count_launch();
+  k_reg_fill<<<grid_for(npad, T), T, 0, s>>>(L, h->nq, h->Areg.off, npad, h->Areg.col, h->Areg.val, h->nu,
+                                             1.0 / gamma);
   VEM_CUDA(h, cudaGetLastError());
   if (h->n_flux_faces > 0) {
     count_launch();

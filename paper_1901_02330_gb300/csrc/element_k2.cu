@@ -658,6 +658,51 @@ vem_status cell_points_k2(vem_handle *h) {
   return VEM_OK;
 }
 
+// Near-null space of the condensed Block-Reg face system at k = 2: the face
+// DOFs (1/|f|) int_f (e_j . n_f) m^f_beta of the three constant fields e_j,
+// i.e. n_f[j] times the face mean of m^f_beta.  The means come from the fan
+// triangles (x_f, v_i, v_i+1) with the edge-midpoint rule, exact for the
+// quadratic face monomials; the triangle areas are signed along n_f, so a
+// face centre outside a non-convex face still gives the right sums.
+// B: (6 nf) x 3, row (6 f + beta).
+__global__ void k_flux_modes_k2(int64_t nf, const int64_t *__restrict__ fvp, const int32_t *__restrict__ fv,
+                                const double *__restrict__ xyz, const double *__restrict__ f_area,
+                                const double *__restrict__ f_cent, const double *__restrict__ f_norm,
+                                const double *__restrict__ f_t1, const double *__restrict__ f_diam, double *B) {
+  const int fb[6][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t vb = fvp[f];
+    const int m = (int)(fvp[f + 1] - vb);
+    const double3 xf = load3(f_cent, f), n = load3(f_norm, f), t1 = load3(f_t1, f);
+    const double3 t2 = cross3(n, t1);
+    const double ihf = 1.0 / f_diam[f];
+    double mean[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < m; ++i) {
+      const double3 A = load3(xyz, fv[vb + i]);
+      const double3 Bv = load3(xyz, fv[vb + (i + 1) % m]);
+      const double w = dot3(cross3(sub3(A, xf), sub3(Bv, xf)), n) / 6.0;   // area / 3 per midpoint
+      const double3 mid[3] = {scale3(add3(xf, A), 0.5), scale3(add3(A, Bv), 0.5), scale3(add3(Bv, xf), 0.5)};
+      for (int q = 0; q < 3; ++q) {
+        const double3 dx = sub3(mid[q], xf);
+        const double u = dot3(dx, t1) * ihf, v = dot3(dx, t2) * ihf;
+        for (int bt = 0; bt < 6; ++bt) mean[bt] += w * ipow(u, fb[bt][0]) * ipow(v, fb[bt][1]);
+      }
+    }
+    const double ia = 1.0 / f_area[f];
+    const double nn[3] = {n.x, n.y, n.z};
+    for (int bt = 0; bt < 6; ++bt)
+      for (int j = 0; j < 3; ++j) B[(6 * f + bt) * 3 + j] = nn[j] * mean[bt] * ia;
+  }
+}
+
+vem_status flux_modes_k2(vem_handle *h, double *B) {
+  count_launch();
+  k_flux_modes_k2<<<grid_for(h->nf, 128), 128, 0, h->stream>>>(h->nf, h->fv_ptr, h->fv, h->xyz, h->f_area,
+                                                                h->f_cent, h->f_norm, h->f_t1, h->f_diam, B);
+  VEM_CUDA(h, cudaGetLastError());
+  return VEM_OK;
+}
+
 vem_status assemble_rhs_k2(vem_handle *h, const double *f_qp, const double *gD_qp, double *g, double *F) {
   cudaStream_t s = h->stream;
   VEM_TRY(cell_points_k2(h));

@@ -40,7 +40,7 @@ struct vem_handle {
   double *hq_inv = nullptr;
   double *pm_hat = nullptr;   // K2: per class, the pressure DOFs of 1 and x_j - x_P,j (4 x 4)
   double *pmodes = nullptr;   // K2: near-null space of S (n_p x 4) for the point-block AMG
-  double *fmodes = nullptr;   // K1: face DOFs of the constant fields (3 n_f x 3), condensed Block-Reg
+  double *fmodes = nullptr;   // face DOFs of the constant fields (nfd n_f x 3), condensed Block-Reg
   int64_t hq_inv_n = 0;
   int64_t *cqp_off = nullptr;                    // [nc + 1] first point of each cell
   double *cqp_x = nullptr, *cqp_w = nullptr;     // [n_cqp][3], [n_cqp]
@@ -276,6 +276,8 @@ vem_status amg_setup_condensed(vem_handle *h, AmgState *&slot, const SellMat &Ar
 bool amg_is_condensed(const AmgState *S);
 // the face DOFs of the three constant fields for the paper's k = 1 element
 vem_status flux_modes_k1(vem_handle *h, int64_t nf, const double *f_norm, double *B);
+// The same for the paper's k = 2 element (six face moments per face).
+vem_status flux_modes_k2(vem_handle *h, double *B);
 // A_reg and its hierarchy for the options (krylov.cu)
 vem_status ensure_reg(vem_handle *h);
 // the hierarchy of S for the options' inner solver (krylov.cu)

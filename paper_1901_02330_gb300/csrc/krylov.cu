@@ -966,16 +966,19 @@ __global__ void k_gm_solve(double *sc, int k, GmLayout L) {
 vem_status ensure_reg(vem_handle *h) {
   const bool fp32 = h->opt.precision == VEM_PRECISION_MIXED;
   const bool cond = h->opt.reg_cycle == VEM_REG_CONDENSED;
-  if (cond && h->opt.element != VEM_ELEMENT_K1)
-    return fail(h, VEM_ERR_UNSUPPORTED, "the condensed Block-Reg cycle needs the paper's k = 1 element");
+  if (cond && h->opt.element != VEM_ELEMENT_K1 && h->opt.element != VEM_ELEMENT_K2)
+    return fail(h, VEM_ERR_UNSUPPORTED, "the condensed Block-Reg cycle needs the paper's k = 1 or k = 2 element");
   if (cond && fp32) return fail(h, VEM_ERR_UNSUPPORTED, "the condensed Block-Reg cycle runs in FP64 only");
   if (!h->areg_valid || (fp32 && !h->areg_has32)) VEM_TRY(assemble_reg(h, fp32));
   if (amg_valid(h->amg_reg) && amg_is_fp32(h->amg_reg) == fp32 && amg_is_condensed(h->amg_reg) == cond)
     return VEM_OK;
   if (cond) {
-    if (!h->fmodes) VEM_TRY(dalloc_n(h, &h->fmodes, 9 * (size_t)h->nf));
-    VEM_TRY(flux_modes_k1(h, h->nf, h->f_norm, h->fmodes));
-    return amg_setup_condensed(h, h->amg_reg, h->Areg, 3 * (int64_t)h->nf, 3, 3, h->fmodes, 3, kSmoothChebyshev);
+    // face DOFs first (nfd per face), nid interior DOFs per cell after them
+    if (!h->fmodes) VEM_TRY(dalloc_n(h, &h->fmodes, 3 * (size_t)h->nfd * h->nf));
+    if (h->nq > 1) VEM_TRY(flux_modes_k2(h, h->fmodes));
+    else VEM_TRY(flux_modes_k1(h, h->nf, h->f_norm, h->fmodes));
+    return amg_setup_condensed(h, h->amg_reg, h->Areg, (int64_t)h->nfd * h->nf, h->nid, h->nfd, h->fmodes, 3,
+                               kSmoothChebyshev);
   }
   return amg_setup(h, h->amg_reg, h->Areg, h->Areg_val32, fp32, false, kSmoothChebyshev);
 }
@@ -2050,7 +2053,6 @@ vem_status krylov_solve(vem_handle *h, const VemOp &op, const double *rhs, doubl
   vem_status r;
   if (h->opt.precond == VEM_PREC_BLOCK_REG) {
     if (op.nbatch != 1) return fail(h, VEM_ERR_UNSUPPORTED, "Block-Reg is single-system");
-    if (h->nq > 1) return fail(h, VEM_ERR_UNSUPPORTED, "Block-Reg with the paper k = 2 element");
     VEM_TRY(ensure_reg(h));
   }
   if (h->opt.krylov == VEM_KRYLOV_MINRES) {

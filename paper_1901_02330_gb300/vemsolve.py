@@ -269,11 +269,26 @@ class Solver:
         self._check(lib().vem_sizes(self._h, C.byref(nu), C.byref(np_)))
         return nu.value, np_.value
 
-    def quadrature_points(self, which: int) -> np.ndarray:
+    def quadrature_count(self, which: int) -> int:
         n = C.c_int64()
         self._check(lib().vem_quadrature_count(self._h, which, C.byref(n)))
-        out = np.zeros((n.value, 3))
-        if n.value:
+        return n.value
+
+    def quadrature_points(self, which: int, out=None):
+        """[n, 3] coordinates; into out when given (numpy, or a contiguous
+        float64 CUDA tensor on the handle's device)."""
+        n = self.quadrature_count(which)
+        if out is None:
+            out = np.zeros((n, 3))
+        elif tuple(out.shape) != (n, 3):
+            raise ValueError(f"out must have shape ({n}, 3)")
+        elif hasattr(out, "data_ptr"):
+            import torch
+            if out.dtype != torch.float64 or not out.is_contiguous():
+                raise ValueError("out must be a contiguous float64 tensor")
+        elif out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array")
+        if n:
             self._check(lib().vem_quadrature_points(self._h, which, _ptr(out)))
         return out
 

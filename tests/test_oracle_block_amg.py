@@ -136,6 +136,37 @@ def test_tentative_prolongator():
         assert np.all(np.diag(R) > 0.0)
 
 
+def test_rank_deficient_aggregates_dissolved():
+    """Aggregates on which the near-null space loses rank (two blocks
+    spanning only two of three modes, a zero mode) leave the coarse space,
+    the others keep their order; the decision agrees with the SVD rank on
+    random full-rank and exactly rank-deficient blocks, including badly
+    scaled full-rank ones (singular value ratio 1e-3)."""
+    rng = np.random.default_rng(4)
+    bs, m = 3, 3
+    full = rng.standard_normal((2 * bs, m))
+    two = rng.standard_normal((2 * bs, 2)) @ np.array([[1.0, 0.0, 1.0], [0.0, 1.0, 1.0]])
+    zero = rng.standard_normal((2 * bs, m))
+    zero[:, 1] = 0.0
+    U, _, Vt = np.linalg.svd(rng.standard_normal((2 * bs, m)), full_matrices=False)
+    scaled = U @ np.diag([1.0, 1e-2, 1e-3]) @ Vt
+    B = np.vstack([full, two, zero, scaled, rng.standard_normal((bs, m))])
+    agg = np.array([0, 0, 1, 1, 2, 2, 3, 3, -1])
+    new, nc = block_amg.dissolve_rank_deficient(agg, 4, B, bs)
+    np.testing.assert_array_equal(new, [0, 0, -1, -1, -1, -1, 1, 1, -1])
+    assert nc == 2
+    for a, blk in enumerate((full, two, zero, scaled)):
+        assert (np.linalg.matrix_rank(blk) == m) == (a in (0, 3))
+    T, Bc = block_amg.tentative(new, nc, B, bs)
+    keep = np.repeat(new >= 0, bs)
+    np.testing.assert_allclose(T @ Bc, B * keep[:, None], atol=1e-13)
+    # nothing changes where every aggregate has full rank
+    same, nc2 = block_amg.dissolve_rank_deficient(np.array([0, 0, 1, 1, -1]), 2,
+                                                  np.vstack([full, scaled, B[-bs:]]), bs)
+    np.testing.assert_array_equal(same, [0, 0, 1, 1, -1])
+    assert nc2 == 2
+
+
 def test_cycle_symmetric_positive_definite():
     _, S = _k2_schur(hex_mesh(4), seed=6)
     H = block_amg.setup(S, 4, block_amg.pressure_modes(_k2_schur(hex_mesh(4), seed=6)[0]), coarse_max=4)
