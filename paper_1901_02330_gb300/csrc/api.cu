@@ -124,6 +124,7 @@ vem_status check_device_errors(vem_handle *h, const char *what) {
   if (e & DEVERR_SINGULAR_LOCAL) return fail(h, VEM_ERR_DEGENERATE_MESH, "%s: singular local Gram matrix", what);
   if (e & DEVERR_NONFINITE) return fail(h, VEM_ERR_NONFINITE, "%s: NaN or Inf in data", what);
   if (e & DEVERR_NONPOSITIVE) return fail(h, VEM_ERR_BAD_INPUT, "%s: K <= 0", what);
+  if (e & DEVERR_LAYOUT) return fail(h, VEM_ERR_BAD_INPUT, "%s: flux row with too many pressure couplings", what);
   if (e & DEVERR_AMG_DIAG) return fail(h, VEM_ERR_BREAKDOWN, "%s: non-positive diagonal or pivot", what);
   if (e & DEVERR_AMG_ROW)
     return fail(h, VEM_ERR_UNSUPPORTED, "%s: a row of an AMG product has too many distinct columns", what);

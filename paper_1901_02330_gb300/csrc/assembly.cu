@@ -805,6 +805,38 @@ __global__ void k_schur_fill_q(Layout L, const double *__restrict__ diagM, const
   }
 }
 
+// The B^T part of every flux row of A (its entries in pressure columns, in
+// the row's order) copied to kBtRow slots per row (zero-padded; slot k of
+// row R at k n_u + R, so a warp's loads of one slot are contiguous), so that
+// the block upper-triangular flux update reads 8 entries per row instead of
+// the whole row of A (about 100 entries per face row at k = 2).
+__global__ void k_bt_rows(int64_t n_u, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
+                          const int32_t *__restrict__ col, const double *__restrict__ val, int32_t *bcol,
+                          double *bval, int *err) {
+  for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < n_u;
+       R += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t base = off[R >> 5] + (R & 31);
+    const int L = len[R];
+    int k = 0;
+    for (int j = 0; j < L; ++j) {
+      const int64_t p = base + 32 * (int64_t)j;
+      const int64_t c = col[p];
+      if (c >= n_u) {
+        if (k < kBtRow) {
+          bcol[k * n_u + R] = (int32_t)(c - n_u);
+          bval[k * n_u + R] = val[p];
+        }
+        ++k;
+      }
+    }
+    if (k > kBtRow) atomicOr(err, DEVERR_LAYOUT);
+    for (; k < kBtRow; ++k) {
+      bcol[k * n_u + R] = 0;
+      bval[k * n_u + R] = 0.0;
+    }
+  }
+}
+
 static vem_status assemble_global_q(vem_handle *h) {
   cudaStream_t s = h->stream;
   Layout L{h->nfd, h->nid, h->nf, h->nc, h->n_u, h->cf_ptr, h->cf, h->f_cell, h->f_loc,
@@ -853,6 +885,20 @@ static vem_status assemble_global_q(vem_handle *h) {
   if (!h->s_dinv32) VEM_TRY(dalloc_n(h, &h->s_dinv32, (size_t)h->n_p));
   count_launch(); k_f64_to_f32<<<grid_for(h->S.stored, T), T, 0, s>>>(h->S.stored, h->S.val, h->S_val32);
   count_launch(); k_f64_to_f32<<<grid_for(h->n_p, T), T, 0, s>>>(h->n_p, h->s_dinv, h->s_dinv32);
+  VEM_CUDA(h, cudaGetLastError());
+  if (h->bt_rows_n != h->n_u) {
+    dfree(h, h->bt_col);
+    dfree(h, h->bt_val);
+    h->bt_col = nullptr;
+    h->bt_val = nullptr;
+    h->bt_rows_n = 0;
+    VEM_TRY(dalloc_n(h, &h->bt_col, (size_t)kBtRow * h->n_u));
+    VEM_TRY(dalloc_n(h, &h->bt_val, (size_t)kBtRow * h->n_u));
+    h->bt_rows_n = h->n_u;
+  }
+  count_launch();
+  k_bt_rows<<<grid_for(h->n_u, T), T, 0, s>>>(h->n_u, h->A.off, h->A.len, h->A.col, h->A.val, h->bt_col, h->bt_val,
+                                              h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   VEM_TRY(check_device_errors(h, "global assembly"));
   VEM_TRY(sell_nnz(h, h->A));

@@ -22,6 +22,7 @@ enum : int {
   DEVERR_AMG_DIAG = 64,        // AMG: non-positive diagonal or pivot
   DEVERR_AMG_ROW = 128,        // AMG: a product row exceeds its column list
   DEVERR_NONPOSITIVE = 256,    // a coefficient K <= 0
+  DEVERR_LAYOUT = 512,         // a flux row couples to more pressure DOFs than its cells hold
 };
 
 struct Status {
@@ -64,6 +65,7 @@ int64_t launch_count();
 constexpr int kRedThreads = 256;
 constexpr int kMaxBlocks = 1216;   // 8 x 152 SMs
 constexpr int kMaxSlots = 300;     // FGMRES(m <= 256) needs m + 2 slots
+constexpr int kBtRow = 8;          // B^T entries kept per flux row (two cells x 4 P1 moments)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

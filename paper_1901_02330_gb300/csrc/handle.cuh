@@ -98,6 +98,11 @@ struct vem_handle {
   vem::SellMat A, S;
   double *rhs = nullptr;                         // [n] = [g; F]
   double *bt_face = nullptr;                     // [2 nf] B entries of each face's cells
+  // several pressure DOFs per cell: the B^T entries of every flux row of A
+  // (pressure column, value), kBtRow per row in row order, zero-padded
+  int32_t *bt_col = nullptr;
+  double *bt_val = nullptr;
+  int64_t bt_rows_n = 0;
   double *diagM = nullptr;                       // [n_u]
   double *s_dinv = nullptr;                      // [n_p] 1 / diag(S)
   float *S_val32 = nullptr;                      // FP32 copy of S's values

@@ -302,6 +302,166 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, T *x, T *r
   block_partial((double)rr, slot(part, P_RR));
 }
 
+// The whole Jacobi-PCG inner solve of a small S in one thread block: the
+// recurrence, scalars and stopping rule of k_cg_init / k_cg_update /
+// k_cg_spmv, with every reduction a block reduction (fixed order), so no
+// launch boundary separates the iterations (a small solve is bound by the
+// latency of dependent launches, not by bytes).  u, which the SpMV
+// gathers, lives in shared memory; the other vectors are touched only by
+// the thread that owns their row (row 32 s + lane of slice s, slices dealt
+// to the warps in turn, as in the SpMV).  At most maxit updates; the host
+// reads S_PCG_DONE / S_PCG_IT / S_PCG_BAD as after the multi-launch form.
+constexpr int kSmallCgRows = 4096;      // n_p up to this runs in one block
+constexpr int kSmallCgThreads = 1024;
+
+// a, b, c summed over the block in a fixed order; the sums are valid in
+// thread 0 only.
+__device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double (*red)[32]) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = a;
+    red[1][warp] = b;
+    red[2][warp] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      s0 += red[0][k];
+      s1 += red[1][k];
+      s2 += red[2][k];
+    }
+    a = s0;
+    b = s1;
+    c = s2;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kSmallCgThreads) k_cg_block(int64_t n, int64_t nslices,
+                                                              const int64_t *__restrict__ off,
+                                                              const int32_t *__restrict__ col,
+                                                              const T *__restrict__ val, const T *__restrict__ dinv,
+                                                              const double *__restrict__ b, T *x, T *r, T *p, T *sv,
+                                                              T *w, double *sc, double tol2, int maxit) {
+  extern __shared__ unsigned char cg_smem[];
+  T *u = reinterpret_cast<T *>(cg_smem);
+  __shared__ double red[3][32];
+  __shared__ double bc[3];   // alpha, beta, stop
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double bb = 0.0;
+  for (int64_t sl = warp; sl < nslices; sl += nw) {
+    const int64_t i = 32 * sl + lane;
+    if (i < n) {
+      const T bt = (T)b[i];
+      x[i] = 0;
+      r[i] = bt;
+      u[i] = dinv[i] * bt;
+      p[i] = 0;
+      sv[i] = 0;
+      bb += (double)bt * (double)bt;
+    }
+  }
+  double t1 = 0.0, t2 = 0.0;
+  block_sum3(bb, t1, t2, red);
+  // thread 0's scalars: ||b||^2, the previous gamma and alpha, the state
+  double BB = bb, gprev = 0.0, aprev = 0.0, R = bb;
+  int it_done = 0, bad = 0, done = 0;
+  if (threadIdx.x == 0) {
+    done = (BB == 0.0) ? 1 : 0;
+    if (!isfinite(BB)) {
+      bad = 2;
+      done = 1;
+    }
+    bc[2] = done;
+  }
+  __syncthreads();
+  for (int it = 0; it <= maxit; ++it) {
+    if (bc[2] != 0.0) break;
+    double rr = 0.0;
+    if (it > 0) {
+      // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r
+      const T alpha = (T)bc[0], beta = (T)bc[1];
+      for (int64_t sl = warp; sl < nslices; sl += nw) {
+        const int64_t i = 32 * sl + lane;
+        if (i < n) {
+          const T pi = u[i] + beta * p[i];
+          const T si = w[i] + beta * sv[i];
+          x[i] += alpha * pi;
+          const T ri = r[i] - alpha * si;
+          p[i] = pi;
+          sv[i] = si;
+          r[i] = ri;
+          u[i] = dinv[i] * ri;
+          rr += (double)(ri * ri);
+        }
+      }
+      __syncthreads();   // u complete before the gathers
+    }
+    // w = S u with (r, u) and (w, u)
+    T gam = 0, del = 0;
+    for (int64_t sl = warp; sl < nslices; sl += nw) {
+      const int64_t i = 32 * sl + lane;
+      const int64_t o = off[sl];
+      const int wdt = (int)((off[sl + 1] - o) >> 5);
+      T t = 0;
+      for (int j = 0; j < wdt; ++j) {
+        const int64_t q = o + 32 * (int64_t)j + lane;
+        t += __ldg(val + q) * u[__ldg(col + q)];
+      }
+      if (i < n) {
+        w[i] = t;
+        gam += r[i] * u[i];
+        del += t * u[i];
+      }
+    }
+    double G = (double)gam, D = (double)del;
+    block_sum3(rr, G, D, red);
+    if (threadIdx.x == 0) {
+      if (it > 0) R = rr;
+      if (!isfinite(R) || !isfinite(G) || !isfinite(D)) {
+        bad = 2;
+        done = 1;
+      } else {
+        it_done = it;
+        if (R <= tol2 * BB) {
+          done = 1;
+        } else {
+          double beta = 0.0, den = D;
+          if (it > 0) {
+            beta = G / gprev;
+            den = D - beta * G / aprev;
+          }
+          if (!(den > 0.0) || !(G > 0.0)) {
+            bad = 1;
+            done = 1;
+          } else {
+            const double alpha = G / den;
+            bc[0] = alpha;
+            bc[1] = beta;
+            gprev = G;
+            aprev = alpha;
+          }
+        }
+      }
+      // the cap: maxit updates at most (the update of iteration maxit + 1
+      // never runs)
+      bc[2] = (done || it == maxit) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sc[S_PCG_DONE] = done ? 1.0 : 0.0;
+    sc[S_PCG_IT] = (double)it_done;
+    sc[S_PCG_BAD] = (double)bad;
+  }
+}
+
 __global__ void k_f32_to_f64(int64_t n, const float *__restrict__ a, double *b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -451,6 +611,20 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   // the AMG-preconditioned form replaces u = D^-1 r by one V-cycle u = V(r)
   bool amg = false;
   if constexpr (sizeof(T) == sizeof(double)) amg = h->opt.inner != VEM_INNER_PCG;
+  const int maxit = h->opt.inner_maxit;
+  if (!amg && op.nbatch == 1 && n <= kSmallCgRows) {
+    count_launch();
+    k_cg_block<T><<<1, kSmallCgThreads, (size_t)n * sizeof(T), s>>>(n, op.S.nslices, op.S.off, op.S.col, sval,
+                                                                     dinv, b, x, r, p, sv, w, sc, tol2, maxit);
+    VEM_CUDA(h, cudaGetLastError());
+    VEM_CUDA(h, cudaMemcpyAsync(h->h_scal, sc, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+    if (h->h_scal[S_PCG_BAD] != 0.0)
+      return fail(h, h->h_scal[S_PCG_BAD] == 2.0 ? VEM_ERR_NONFINITE : VEM_ERR_BREAKDOWN, "inner PCG breakdown");
+    *iters = h->h_scal[S_PCG_DONE] != 0.0 ? (int)h->h_scal[S_PCG_IT] : maxit;
+    h->last_pcg_iters = *iters;
+    return VEM_OK;
+  }
   count_launch();
   k_cg_init<T><<<nb, kRedThreads, 0, s>>>(n, b, dinv, x, r, u, p, sv, h->part, sc, h->ctr);
   auto precondition = [&]() {
@@ -490,7 +664,6 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
     if (amg) amg_collect_timing(h, h->amg);
   };
   spmv_it(0);
-  const int maxit = h->opt.inner_maxit;
   // the host polls the convergence flag first after as many iterations as
   // the previous inner solve took (consecutive solves need similar counts),
   // then every 4; launches past convergence return at once
@@ -708,22 +881,17 @@ static void launch_tri_flux(cudaStream_t s, int nfd, bool batch, int64_t nf, int
   }
 }
 
-// The same for any element, from the saddle matrix itself: B^T z_p of flux
-// row R is the part of row R of [M B^T; B 0] in the pressure columns.
-__global__ void k_tri_flux_rows(int64_t n_u, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                                const int32_t *__restrict__ col, const double *__restrict__ val,
+// The same for several pressure DOFs per cell: B^T z_p of flux row R from
+// the pressure-column entries of row R of [M B^T; B 0], which the assembly
+// copies to kBtRow slots per row (slot k at k n_u + R; k_bt_rows).
+__global__ void k_tri_flux_rows(int64_t n_u, const int32_t *__restrict__ bcol, const double *__restrict__ bval,
                                 const double *__restrict__ v, const double *__restrict__ dM,
                                 const double *__restrict__ zp, double *z) {
   for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < n_u;
        R += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t base = off[R >> 5] + (R & 31);
-    const int L = len[R];
     double t = v[R];
-    for (int k = 0; k < L; ++k) {
-      const int64_t p = base + 32 * (int64_t)k;
-      const int64_t cidx = col[p];
-      if (cidx >= n_u) t -= val[p] * zp[cidx - n_u];
-    }
+#pragma unroll
+    for (int k = 0; k < kBtRow; ++k) t -= bval[k * n_u + R] * zp[bcol[k * n_u + R]];
     z[R] = t / dM[R];
   }
 }
@@ -1012,8 +1180,7 @@ static vem_status precond(vem_handle *h, const VemOp &op, const double *v, doubl
     count_launch(); k_negate<<<grid_for(np, 256), 256, 0, s>>>(np, z + nu);
     if (h->nq > 1) {
       count_launch();
-      k_tri_flux_rows<<<grid_for(nu, 256), 256, 0, s>>>(nu, op.A.off, op.A.len, op.A.col, op.A.val, v, op.diagM,
-                                                         z + nu, z);
+      k_tri_flux_rows<<<grid_for(nu, 256), 256, 0, s>>>(nu, h->bt_col, h->bt_val, v, op.diagM, z + nu, z);
     } else {
       launch_tri_flux(s, h->nfd, op.nbatch > 1, h->nf, nu, op.n_u1, op.n_p1, v, op.diagM, h->f_cell, h->bt_face,
                       z + nu, z);

@@ -233,6 +233,27 @@ def test_k2_flux_system_and_solves(vs, mname):
         assert st["multiplier"] == pytest.approx(lamd, rel=1e-9, abs=1e-12)
 
 
+def test_quadrature_points_into_device_buffer(vs):
+    """The cell and boundary-face points copied into a CUDA tensor equal the
+    host copy (the k = 2 cell set of a large mesh is evaluated on the
+    device); a buffer of the wrong shape or type is refused."""
+    import torch
+    s = vs.Solver(prism_mesh(2), element=vs.VEM_ELEMENT_K2)
+    try:
+        for which in (vs.VEM_QP_CELL, vs.VEM_QP_BFACE):
+            host = s.quadrature_points(which)
+            dev = torch.full((host.shape[0], 3), np.nan, dtype=torch.float64, device="cuda")
+            s.quadrature_points(which, out=dev)
+            np.testing.assert_array_equal(dev.cpu().numpy(), host)
+        n = s.quadrature_count(vs.VEM_QP_CELL)
+        with pytest.raises(ValueError):
+            s.quadrature_points(vs.VEM_QP_CELL, out=torch.empty((n, 2), dtype=torch.float64, device="cuda"))
+        with pytest.raises(ValueError):
+            s.quadrature_points(vs.VEM_QP_CELL, out=torch.empty((n, 3), dtype=torch.float32, device="cuda"))
+    finally:
+        s.close()
+
+
 def test_k2_unsupported_combinations(vs):
     mesh = hex_mesh(2)
     s = vs.Solver(mesh, element=vs.VEM_ELEMENT_K2, krylov=1, precond=vs.VEM_PREC_BLOCK_TRI)

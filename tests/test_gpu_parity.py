@@ -129,6 +129,35 @@ def test_solve_matches_oracle_direct(vs, mname, ename, method, krylov, prec):
     s.close()
 
 
+@pytest.mark.parametrize("n_side", [16, 17], ids=["one-block-pcg", "multi-launch-pcg"])
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_inner_pcg_both_forms(vs, n_side, precision):
+    """The inner Jacobi-PCG runs in one thread block for S of up to 4,096
+    rows (16^3 cells: 4,096) and as launches of its multi-block kernels
+    above (17^3: 4,913): both forms reach the oracle's direct solution with
+    a general right-hand side (FP64: 1e-10; mixed: FP32 inner solve, FP64
+    refinement), in FGMRES with the block-triangular preconditioner."""
+    mesh = hex_mesh(n_side)
+    K = fields.K_lognormal(mesh.n_cells, seed=9, sigma=1.0)
+    f = np.random.default_rng(3).standard_normal(mesh.n_cells)
+    s = _solver(vs, mesh, 0, krylov=1, precond=1, rtol=1e-12, inner_rtol=1e-6, maxit=500,
+                precision=precision)
+    try:
+        s.set_coefficient(K)
+        s.set_source(f, None)
+        u, p, st = s.solve()
+    finally:
+        s.close()
+    sys = assemble(mesh, E0, 1.0 / K)
+    cells = mesh_cells(mesh)
+    sys.F[:] = [c.volume * f[i] for i, c in enumerate(cells)]
+    ud, pd = solvers.solve_direct(sys)
+    assert st["relres"] <= 1e-12
+    assert st["inner_iterations"] >= st["iterations"]
+    assert np.linalg.norm(u - ud) <= 1e-10 * np.linalg.norm(ud)
+    assert np.linalg.norm(p - pd) <= 1e-10 * np.linalg.norm(pd)
+
+
 def test_random_rhs_krylov(vs):
     """A right-hand side with no special structure (the manufactured sine data
     is an eigenvector on uniform cubes): FGMRES + block-triangular needs tens of
