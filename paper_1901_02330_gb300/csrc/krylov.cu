@@ -305,40 +305,45 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, T *x, T *r
 // The whole Jacobi-PCG inner solve of a small S in one thread block: the
 // recurrence, scalars and stopping rule of k_cg_init / k_cg_update /
 // k_cg_spmv, with every reduction a block reduction (fixed order), so no
-// launch boundary separates the iterations (a small solve is bound by the
-// latency of dependent launches, not by bytes).  u, which the SpMV
-// gathers, lives in shared memory; the other vectors are touched only by
-// the thread that owns their row (row 32 s + lane of slice s, slices dealt
-// to the warps in turn, as in the SpMV).  At most maxit updates; the host
-// reads S_PCG_DONE / S_PCG_IT / S_PCG_BAD as after the multi-launch form.
+// launch boundary separates the iterations (a small solve is bound by
+// latency, not by bytes).  The six vectors live in shared memory (6 n
+// entries; global round trips cost ~12 us per iteration on a 512-row S),
+// S and D^-1 are read through the read-only cache; x is written out at the
+// end.  Rows are dealt as in the SpMV (row 32 s + lane of slice s, slices to
+// the warps in turn).  At most maxit updates; the host reads S_PCG_DONE /
+// S_PCG_IT / S_PCG_BAD as after the multi-launch form.
 constexpr int kSmallCgRows = 4096;      // n_p up to this runs in one block
 constexpr int kSmallCgThreads = 1024;
 
-// a, b, c summed over the block in a fixed order; the sums are valid in
-// thread 0 only.
-__device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double (*red)[32]) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][warp] = a;
-    red[1][warp] = b;
-    red[2][warp] = c;
-  }
+// a, b, c summed over the block in a fixed order: a tree over the threads'
+// values in shared memory (red: 3 blockDim entries; blockDim a power of two
+// >= 32), then the last 32 by shuffles in warp 0.  The sums are valid in
+// thread 0 only.  GB300 issues an FP64 warp instruction about every 16
+// cycles per SM, so the tree (31 warp additions per value at 1,024 threads)
+// is used rather than per-warp shuffle trees (160).
+__device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double *red) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  red[t] = a;
+  red[nt + t] = b;
+  red[2 * nt + t] = c;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-      s0 += red[0][k];
-      s1 += red[1][k];
-      s2 += red[2][k];
+  for (int h = nt >> 1; h >= 32; h >>= 1) {
+    if (t < h) {
+      red[t] += red[t + h];
+      red[nt + t] += red[nt + t + h];
+      red[2 * nt + t] += red[2 * nt + t + h];
     }
-    a = s0;
-    b = s1;
-    c = s2;
+    __syncthreads();
+  }
+  if (t < 32) {
+    a = red[t];
+    b = red[nt + t];
+    c = red[2 * nt + t];
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
   }
 }
 
@@ -347,11 +352,12 @@ __global__ void __launch_bounds__(kSmallCgThreads) k_cg_block(int64_t n, int64_t
                                                               const int64_t *__restrict__ off,
                                                               const int32_t *__restrict__ col,
                                                               const T *__restrict__ val, const T *__restrict__ dinv,
-                                                              const double *__restrict__ b, T *x, T *r, T *p, T *sv,
-                                                              T *w, double *sc, double tol2, int maxit) {
+                                                              const double *__restrict__ b, T *x_out, double *sc,
+                                                              double tol2, int maxit) {
   extern __shared__ unsigned char cg_smem[];
   T *u = reinterpret_cast<T *>(cg_smem);
-  __shared__ double red[3][32];
+  T *x = u + n, *r = x + n, *p = r + n, *sv = p + n, *w = sv + n;
+  __shared__ double red[3 * kSmallCgThreads];
   __shared__ double bc[3];   // alpha, beta, stop
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double bb = 0.0;
@@ -361,9 +367,10 @@ __global__ void __launch_bounds__(kSmallCgThreads) k_cg_block(int64_t n, int64_t
       const T bt = (T)b[i];
       x[i] = 0;
       r[i] = bt;
-      u[i] = dinv[i] * bt;
+      u[i] = __ldg(dinv + i) * bt;
       p[i] = 0;
       sv[i] = 0;
+      w[i] = 0;
       bb += (double)bt * (double)bt;
     }
   }
@@ -397,7 +404,7 @@ __global__ void __launch_bounds__(kSmallCgThreads) k_cg_block(int64_t n, int64_t
           p[i] = pi;
           sv[i] = si;
           r[i] = ri;
-          u[i] = dinv[i] * ri;
+          u[i] = __ldg(dinv + i) * ri;
           rr += (double)(ri * ri);
         }
       }
@@ -407,8 +414,8 @@ __global__ void __launch_bounds__(kSmallCgThreads) k_cg_block(int64_t n, int64_t
     T gam = 0, del = 0;
     for (int64_t sl = warp; sl < nslices; sl += nw) {
       const int64_t i = 32 * sl + lane;
-      const int64_t o = off[sl];
-      const int wdt = (int)((off[sl + 1] - o) >> 5);
+      const int64_t o = __ldg(off + sl);
+      const int wdt = (int)((__ldg(off + sl + 1) - o) >> 5);
       T t = 0;
       for (int j = 0; j < wdt; ++j) {
         const int64_t q = o + 32 * (int64_t)j + lane;
@@ -449,11 +456,14 @@ __global__ void __launch_bounds__(kSmallCgThreads) k_cg_block(int64_t n, int64_t
           }
         }
       }
-      // the cap: maxit updates at most (the update of iteration maxit + 1
-      // never runs)
+      // the cap: maxit updates at most
       bc[2] = (done || it == maxit) ? 1.0 : 0.0;
     }
     __syncthreads();
+  }
+  for (int64_t sl = warp; sl < nslices; sl += nw) {
+    const int64_t i = 32 * sl + lane;
+    if (i < n) x_out[i] = x[i];
   }
   if (threadIdx.x == 0) {
     sc[S_PCG_DONE] = done ? 1.0 : 0.0;
@@ -613,9 +623,18 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   if constexpr (sizeof(T) == sizeof(double)) amg = h->opt.inner != VEM_INNER_PCG;
   const int maxit = h->opt.inner_maxit;
   if (!amg && op.nbatch == 1 && n <= kSmallCgRows) {
+    const size_t smem = 6 * (size_t)n * sizeof(T);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(T) == sizeof(double)]) {
+      VEM_CUDA(h, cudaFuncSetAttribute(k_cg_block<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       6 * kSmallCgRows * (int)sizeof(T)));
+      attr_set[sizeof(T) == sizeof(double)] = true;
+    }
+    // a warp per slice up to 32 warps (a power of two for the tree sums)
+    int nthr = 32;
+    while (nthr < kSmallCgThreads && nthr < 32 * op.S.nslices) nthr <<= 1;
     count_launch();
-    k_cg_block<T><<<1, kSmallCgThreads, (size_t)n * sizeof(T), s>>>(n, op.S.nslices, op.S.off, op.S.col, sval,
-                                                                     dinv, b, x, r, p, sv, w, sc, tol2, maxit);
+    k_cg_block<T><<<1, nthr, smem, s>>>(n, op.S.nslices, op.S.off, op.S.col, sval, dinv, b, x, sc, tol2, maxit);
     VEM_CUDA(h, cudaGetLastError());
     VEM_CUDA(h, cudaMemcpyAsync(h->h_scal, sc, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
     VEM_CUDA(h, cudaStreamSynchronize(s));
