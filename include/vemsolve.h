@@ -101,9 +101,9 @@ typedef struct {
  * c = |P| on them) and the block-diagonal and block-triangular
  * preconditioners (Jacobi-PCG, the scalar AMG without the multiplier, or
  * the point-block AMG VEM_INNER_BLOCK_AMG for S), Block-Reg (both reg_cycle
- * forms; B^T W^-1 B sums over the four pressure rows of a cell) and
- * vem_adjoint (Dirichlet boundaries); vem_solve_batched gives
- * VEM_ERR_UNSUPPORTED with it.  Its cell quadrature points
+ * forms; B^T W^-1 B sums over the four pressure rows of a cell),
+ * vem_solve_batched (Jacobi-PCG inner solver, as for every element) and
+ * vem_adjoint (Dirichlet boundaries).  Its cell quadrature points
  * (VEM_QP_CELL) are those of a degree-3 rule on the fan tetrahedra of every
  * cell (27 per tetrahedron), built on first use. */
 enum { VEM_ELEMENT_E0 = 0, VEM_ELEMENT_K1 = 1, VEM_ELEMENT_K2 = 2 };
@@ -302,8 +302,10 @@ vem_status vem_solve(vem_handle *h, const double *x0, double *u_out, double *p_o
 
 /* Batched solve of nbatch problems on the same mesh (the batched form of the
  * same discretisation: per-system coefficient and data, Sec. 4.3 forms):
- * K [nbatch][n_cells] (> 0), f_qp [nbatch][n_cells] and gD_qp
- * [nbatch][n_bqp] at the VEM_QP_CELL / VEM_QP_BFACE points (NULL = zero).
+ * K [nbatch][n_cells] (> 0), f_qp [nbatch][n_cqp] and gD_qp
+ * [nbatch][n_bqp] at the VEM_QP_CELL / VEM_QP_BFACE points (NULL = zero;
+ * n_cqp = vem_quadrature_count(VEM_QP_CELL): n_cells for E0 and K1, the
+ * fan-tetrahedron points for K2).
  * The systems share the sparsity structure: their saddle matrices and Schur
  * approximations are stored as one structure with per-system values, and
  * every A-apply, Schur product and vector operation is one launch over all

@@ -40,6 +40,8 @@
 // contributions in a fixed order, so the hierarchy is bitwise reproducible.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -1556,6 +1558,12 @@ static vem_status sort_rows(vem_handle *h, AmgState *S, int64_t n, const int64_t
 // bit for bit.
 constexpr size_t kProdScratchMax = size_t(6) << 30;   // bytes of scratch for the one-pass form
 
+static bool amg_debug() {
+  static int v = -1;
+  if (v < 0) v = std::getenv("VEM_DEBUG") ? 1 : 0;
+  return v == 1;
+}
+
 static vem_status product(vem_handle *h, AmgState *S, const DMat &X, const CsrBuf &Y, CsrBuf &C,
                           bool short_rows) {
   cudaStream_t s = h->stream;
@@ -1600,6 +1608,9 @@ static vem_status product(vem_handle *h, AmgState *S, const DMat &X, const CsrBu
       unsigned long long nb = 0;
       VEM_CUDA(h, cudaMemcpyAsync(&nb, nbig, sizeof(nb), cudaMemcpyDeviceToHost, s));
       VEM_CUDA(h, cudaStreamSynchronize(s));
+      if (amg_debug())
+        fprintf(stderr, "[vem] product rows=%lld cols=%lld candidates=%lld wide rows=%llu\n", (long long)X.rows,
+                (long long)Y.cols, (long long)ncand, nb);
       if (nb) {
         const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nb, (int64_t)num_sms() * 2));
         count_launch();

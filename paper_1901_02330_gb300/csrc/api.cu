@@ -931,7 +931,6 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
     return fail(h, VEM_ERR_UNSUPPORTED, "the AMG inner solvers are single-system (no batched solves)");
   if (h->opt.precond == VEM_PREC_BLOCK_REG)
     return fail(h, VEM_ERR_UNSUPPORTED, "Block-Reg is single-system (no batched solves)");
-  if (h->nq > 1) return fail(h, VEM_ERR_UNSUPPORTED, "paper k = 2 in batched solves");
   if (h->n_flux_faces > 0)
     return fail(h, VEM_ERR_UNSUPPORTED, "prescribed-flux faces in batched solves");
   cudaStream_t s = h->stream;
@@ -939,10 +938,12 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   const bool dev = h->opt.device_io != 0;
   // structure of A and S from a single-system assembly
   if (!h->assembled) VEM_TRY(assemble_impl(h));
-  const bool grow = nb > h->b_cap;
+  VEM_TRY(ensure_cell_points(h));
+  const int64_t ncp = n_cell_points(h);   // f_qp entries per system (n_cells below k = 2)
+  const bool grow = nb > h->b_cap || ncp != h->b_ncp;
   const int64_t nbq = std::max<int64_t>(h->n_bqp, 1);
   VEM_TRY(batch_buf(h, &h->b_nu, (size_t)nb * h->nc, grow));
-  VEM_TRY(batch_buf(h, &h->b_fqp, (size_t)nb * h->nc, grow));
+  VEM_TRY(batch_buf(h, &h->b_fqp, (size_t)nb * std::max(ncp, h->nc), grow));
   VEM_TRY(batch_buf(h, &h->b_gqp, (size_t)nb * nbq, grow));
   VEM_TRY(batch_buf(h, &h->b_rhs, (size_t)nb * h->n, grow));
   VEM_TRY(batch_buf(h, &h->b_x, (size_t)nb * h->n, grow));
@@ -951,10 +952,13 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   VEM_TRY(batch_buf(h, &op.A.val, (size_t)nb * h->A.stored, regrow));
   VEM_TRY(batch_buf(h, &op.diagM, (size_t)nb * h->n_u, regrow));
   VEM_TRY(batch_buf(h, &op.S.val, (size_t)nb * h->S.stored, regrow));
-  VEM_TRY(batch_buf(h, &op.s_dinv, (size_t)nb * h->nc, regrow));
+  VEM_TRY(batch_buf(h, &op.s_dinv, (size_t)nb * h->n_p, regrow));
   VEM_TRY(batch_buf(h, &op.S_val32, (size_t)nb * h->S.stored, regrow));
-  VEM_TRY(batch_buf(h, &op.s_dinv32, (size_t)nb * h->nc, regrow));
-  if (grow) h->b_cap = nb;
+  VEM_TRY(batch_buf(h, &op.s_dinv32, (size_t)nb * h->n_p, regrow));
+  if (grow) {
+    h->b_cap = nb;
+    h->b_ncp = ncp;
+  }
   op.A.rows = h->A.rows; op.A.nslices = h->A.nslices; op.A.stored = h->A.stored; op.A.nnz = h->A.nnz;
   op.A.off = h->A.off; op.A.len = h->A.len; op.A.col = h->A.col;
   op.S.rows = h->S.rows; op.S.nslices = h->S.nslices; op.S.stored = h->S.stored; op.S.nnz = h->S.nnz;
@@ -976,8 +980,8 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
     if (e == VEM_ERR_NONFINITE) return fail(h, VEM_ERR_BAD_INPUT, "K must be finite and > 0");
     if (e != VEM_OK) return e;
   }
-  if (f_qp) VEM_CUDA(h, cudaMemcpyAsync(h->b_fqp, f_qp, sizeof(double) * nb * h->nc, kind, s));
-  else VEM_CUDA(h, cudaMemsetAsync(h->b_fqp, 0, sizeof(double) * nb * h->nc, s));
+  if (f_qp) VEM_CUDA(h, cudaMemcpyAsync(h->b_fqp, f_qp, sizeof(double) * nb * ncp, kind, s));
+  else VEM_CUDA(h, cudaMemsetAsync(h->b_fqp, 0, sizeof(double) * nb * ncp, s));
   if (gD_qp && h->n_bqp > 0) VEM_CUDA(h, cudaMemcpyAsync(h->b_gqp, gD_qp, sizeof(double) * nb * h->n_bqp, kind, s));
   else VEM_CUDA(h, cudaMemsetAsync(h->b_gqp, 0, sizeof(double) * nb * nbq, s));
   // geometry-only local matrices (nu = 1), then the per-system values
@@ -986,7 +990,7 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   VEM_TRY(assemble_local(h));
   VEM_TRY(assemble_batched_values(h, nb, h->b_nu, op));
   for (int b = 0; b < nb; ++b)
-    VEM_TRY(assemble_rhs_into(h, h->b_fqp + (int64_t)b * h->nc, (gD_qp && h->n_bqp > 0) ? h->b_gqp + (int64_t)b * nbq : nullptr,
+    VEM_TRY(assemble_rhs_into(h, h->b_fqp + (int64_t)b * ncp, (gD_qp && h->n_bqp > 0) ? h->b_gqp + (int64_t)b * nbq : nullptr,
                               h->b_rhs + (int64_t)b * h->n_u, h->b_rhs + op.n_u + (int64_t)b * h->n_p));
   VEM_TRY(check_device_errors(h, "batched right-hand side"));
   cudaEventRecord(h->ev1, s);

@@ -624,10 +624,17 @@ __global__ void k_rowcount_q(Layout L, int64_t *cnt) {
 }
 
 template <int NFD, int NID, int NQ>
+// Batched (gridDim.y systems, as k_fill): values of system blockIdx.y at
+// val + y stored, diag(M) at diagM + y n_u, its nu at nsc + y n_c; col NULL
+// writes the values only (the structure is shared).
 __global__ void k_fill_q(Layout L, const int64_t *__restrict__ off, int64_t nrows_pad, int32_t *col, double *val,
-                         double *diagM, const double *__restrict__ nsc) {
+                         double *diagM, const double *__restrict__ nsc, int64_t stored) {
   const int64_t nfr = (int64_t)NFD * L.nf;
   const int64_t n = L.n_u + (int64_t)NQ * L.nc;
+  const int64_t bb = blockIdx.y;
+  val += bb * stored;
+  diagM += bb * L.n_u;
+  nsc += bb * L.nc;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows_pad;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s0 = off[r >> 5];
@@ -637,7 +644,7 @@ __global__ void k_fill_q(Layout L, const int64_t *__restrict__ off, int64_t nrow
 #define PUT(c_, v_)                                   \
   do {                                                \
     const int64_t q_ = s0 + ((int64_t)j << 5) + lane; \
-    col[q_] = (int32_t)(c_);                          \
+    if (col) col[q_] = (int32_t)(c_);                 \
     val[q_] = (v_);                                   \
     ++j;                                              \
   } while (0)
@@ -740,8 +747,13 @@ __global__ void k_schur_count_q(Layout L, int64_t *cnt) {
 
 template <int NFD, int NID, int NQ>
 __global__ void k_schur_fill_q(Layout L, const double *__restrict__ diagM, const int64_t *__restrict__ off,
-                               int64_t nrows_pad, int32_t *col, double *val, double *dinv, int *err) {
+                               int64_t nrows_pad, int32_t *col, double *val, double *dinv, int *err,
+                               int64_t stored) {
   const int64_t nfr = (int64_t)NFD * L.nf;
+  const int64_t bb = blockIdx.y;   // batched as k_schur_fill; col NULL: values only
+  diagM += bb * L.n_u;
+  val += bb * stored;
+  dinv += bb * (int64_t)NQ * L.nc;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows_pad;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s0 = off[r >> 5];
@@ -768,7 +780,7 @@ __global__ void k_schur_fill_q(Layout L, const double *__restrict__ diagM, const
         for (int l = 0; l < NID; ++l)
           v += Bc[q * nl + NFD * k + l] * Bc[q2 * nl + NFD * k + l] / diagM[nfr + (int64_t)NID * c + l];
         const int64_t p = s0 + ((int64_t)j << 5) + lane;
-        col[p] = (int32_t)(NQ * c + q2);
+        if (col) col[p] = (int32_t)(NQ * c + q2);
         val[p] = v;
         ++j;
         if (q2 == q) {
@@ -791,7 +803,7 @@ __global__ void k_schur_fill_q(Layout L, const double *__restrict__ diagM, const
           for (int bt = 0; bt < NFD; ++bt)
             v += Bc[q * nl + i * NFD + bt] * Bq[q2 * nlq + lq * NFD + bt] / diagM[(int64_t)NFD * f + bt];
           const int64_t p = s0 + ((int64_t)j << 5) + lane;
-          col[p] = (int32_t)(NQ * nb + q2);
+          if (col) col[p] = (int32_t)(NQ * nb + q2);
           val[p] = v;
           ++j;
         }
@@ -799,7 +811,7 @@ __global__ void k_schur_fill_q(Layout L, const double *__restrict__ diagM, const
     }
     for (; j < width; ++j) {
       const int64_t p = s0 + ((int64_t)j << 5) + lane;
-      col[p] = 0;
+      if (col) col[p] = 0;
       val[p] = 0.0;
     }
   }
@@ -852,7 +864,8 @@ static vem_status assemble_global_q(vem_handle *h) {
   if (!h->diagM) VEM_TRY(dalloc_n(h, &h->diagM, (size_t)h->n_u));
   const int64_t npad = h->A.nslices * 32;
   count_launch();
-  k_fill_q<6, 14, 4><<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, npad, h->A.col, h->A.val, h->diagM, h->nu);
+  k_fill_q<6, 14, 4><<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, npad, h->A.col, h->A.val, h->diagM, h->nu,
+                                                     h->A.stored);
   VEM_CUDA(h, cudaGetLastError());
   if (h->n_flux_faces > 0) {
     // prescribed flux DOFs: values, A x_fix moved to the right-hand side,
@@ -874,7 +887,7 @@ static vem_status assemble_global_q(vem_handle *h) {
   const int64_t spad = h->S.nslices * 32;
   count_launch();
   k_schur_fill_q<6, 14, 4><<<grid_for(spad, T), T, 0, s>>>(L, h->diagM, h->S.off, spad, h->S.col, h->S.val,
-                                                           h->s_dinv, h->d_err);
+                                                           h->s_dinv, h->d_err, h->S.stored);
   VEM_CUDA(h, cudaGetLastError());
   if (h->s32_stored != h->S.stored) {
     dfree(h, h->S_val32);
@@ -1235,13 +1248,23 @@ vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, Ve
   const int T = 256;
   const int64_t npad = h->A.nslices * 32, spad = h->S.nslices * 32;
   dim3 ga(grid_for(npad, T, 2), nb), gs(grid_for(spad, T, 2), nb);
-  launch_fill(s, h->nfd, ga, L, h->A.off, h->A.len, npad, nullptr, op.A.val, op.diagM, nu_b, h->A.stored);
-  count_launch();
-  k_schur_fill<<<gs, T, 0, s>>>(L, op.diagM, h->S.off, spad, nullptr, op.S.val, op.s_dinv, h->d_err, h->S.stored);
+  if (h->nq > 1) {
+    if (h->nfd != 6 || h->nid != 14 || h->nq != 4) return fail(h, VEM_ERR_UNSUPPORTED, "element layout");
+    count_launch();
+    k_fill_q<6, 14, 4><<<ga, T, 0, s>>>(L, h->A.off, npad, nullptr, op.A.val, op.diagM, nu_b, h->A.stored);
+    count_launch();
+    k_schur_fill_q<6, 14, 4><<<gs, T, 0, s>>>(L, op.diagM, h->S.off, spad, nullptr, op.S.val, op.s_dinv, h->d_err,
+                                              h->S.stored);
+  } else {
+    launch_fill(s, h->nfd, ga, L, h->A.off, h->A.len, npad, nullptr, op.A.val, op.diagM, nu_b, h->A.stored);
+    count_launch();
+    k_schur_fill<<<gs, T, 0, s>>>(L, op.diagM, h->S.off, spad, nullptr, op.S.val, op.s_dinv, h->d_err,
+                                  h->S.stored);
+  }
   count_launch();
   k_f64_to_f32<<<grid_for(nb * h->S.stored, T), T, 0, s>>>(nb * h->S.stored, op.S.val, op.S_val32);
   count_launch();
-  k_f64_to_f32<<<grid_for(nb * h->nc, T), T, 0, s>>>(nb * h->nc, op.s_dinv, op.s_dinv32);
+  k_f64_to_f32<<<grid_for(nb * h->n_p, T), T, 0, s>>>(nb * h->n_p, op.s_dinv, op.s_dinv32);
   VEM_CUDA(h, cudaGetLastError());
   return check_device_errors(h, "batched assembly");
 }

@@ -145,6 +145,7 @@ struct vem_handle {
   VemOp bop;                                     // stacked operator (values per batch)
   double *b_nu = nullptr, *b_rhs = nullptr, *b_x = nullptr, *b_fqp = nullptr, *b_gqp = nullptr;
   int b_cap = 0;                                 // batches the buffers hold
+  int64_t b_ncp = 0;                             // cell quadrature points per system they hold
 
   // ---- AMG for the inner Schur solve ----
   vem::AmgState *amg = nullptr;

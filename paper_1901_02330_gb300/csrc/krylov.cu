@@ -903,14 +903,23 @@ static void launch_tri_flux(cudaStream_t s, int nfd, bool batch, int64_t nf, int
 // The same for several pressure DOFs per cell: B^T z_p of flux row R from
 // the pressure-column entries of row R of [M B^T; B 0], which the assembly
 // copies to kBtRow slots per row (slot k at k n_u + R; k_bt_rows).
-__global__ void k_tri_flux_rows(int64_t n_u, const int32_t *__restrict__ bcol, const double *__restrict__ bval,
-                                const double *__restrict__ v, const double *__restrict__ dM,
-                                const double *__restrict__ zp, double *z) {
+// (stacked systems as in k_tri_flux: row R = b n_u1 + r, the copied B^T
+// entries are those of the shared structure, B being independent of K)
+template <bool kBatch>
+__global__ void k_tri_flux_rows(int64_t n_u, int64_t n_u1, int64_t n_p1, const int32_t *__restrict__ bcol,
+                                const double *__restrict__ bval, const double *__restrict__ v,
+                                const double *__restrict__ dM, const double *__restrict__ zp, double *z) {
   for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < n_u;
        R += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = 0, r = R;
+    if (kBatch) {
+      b = R / n_u1;
+      r = R - b * n_u1;
+    }
+    const double *zb = zp + b * n_p1;
     double t = v[R];
 #pragma unroll
-    for (int k = 0; k < kBtRow; ++k) t -= bval[k * n_u + R] * zp[bcol[k * n_u + R]];
+    for (int k = 0; k < kBtRow; ++k) t -= bval[k * n_u1 + r] * zb[bcol[k * n_u1 + r]];
     z[R] = t / dM[R];
   }
 }
@@ -1199,7 +1208,12 @@ static vem_status precond(vem_handle *h, const VemOp &op, const double *v, doubl
     count_launch(); k_negate<<<grid_for(np, 256), 256, 0, s>>>(np, z + nu);
     if (h->nq > 1) {
       count_launch();
-      k_tri_flux_rows<<<grid_for(nu, 256), 256, 0, s>>>(nu, h->bt_col, h->bt_val, v, op.diagM, z + nu, z);
+      if (op.nbatch > 1)
+        k_tri_flux_rows<true><<<grid_for(nu, 256), 256, 0, s>>>(nu, op.n_u1, op.n_p1, h->bt_col, h->bt_val, v,
+                                                                 op.diagM, z + nu, z);
+      else
+        k_tri_flux_rows<false><<<grid_for(nu, 256), 256, 0, s>>>(nu, nu, 0, h->bt_col, h->bt_val, v, op.diagM,
+                                                                  z + nu, z);
     } else {
       launch_tri_flux(s, h->nfd, op.nbatch > 1, h->nf, nu, op.n_u1, op.n_p1, v, op.diagM, h->f_cell, h->bt_face,
                       z + nu, z);
@@ -2080,7 +2094,13 @@ static vem_status sys_precond(vem_handle *h, const VemOp &op, const double *v, d
   } else {
     count_launch();
     k_negate<<<grid_for(np, 256), 256, 0, s>>>(np, z + nu);
-    launch_tri_flux(s, h->nfd, true, h->nf, nu, op.n_u1, op.n_p1, v, op.diagM, h->f_cell, h->bt_face, z + nu, z);
+    if (h->nq > 1) {
+      count_launch();
+      k_tri_flux_rows<true><<<grid_for(nu, 256), 256, 0, s>>>(nu, op.n_u1, op.n_p1, h->bt_col, h->bt_val, v,
+                                                               op.diagM, z + nu, z);
+    } else {
+      launch_tri_flux(s, h->nfd, true, h->nf, nu, op.n_u1, op.n_p1, v, op.diagM, h->f_cell, h->bt_face, z + nu, z);
+    }
   }
   VEM_CUDA(h, cudaGetLastError());
   return VEM_OK;

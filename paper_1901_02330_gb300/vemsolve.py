@@ -369,6 +369,12 @@ class Solver:
         nb = int(K.shape[0])
         nu, np_ = self.sizes()
         dev = bool(self.options.device_io)
+        # the library reads nb rows of these sizes: refuse anything shorter
+        want = {"K": (K, self.n_cells), "f_qp": (f_qp, self.quadrature_count(VEM_QP_CELL)),
+                "gD_qp": (gD_qp, self.quadrature_count(VEM_QP_BFACE))}
+        for name, (arr, m) in want.items():
+            if arr is not None and tuple(arr.shape) != (nb, m):
+                raise ValueError(f"{name} must have shape ({nb}, {m}), not {tuple(arr.shape)}")
         if not dev:
             K = np.ascontiguousarray(K, dtype=np.float64)
             f_qp = None if f_qp is None else np.ascontiguousarray(f_qp, dtype=np.float64)

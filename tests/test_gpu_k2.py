@@ -143,10 +143,12 @@ def test_k2_solve_matches_direct(vs, mname, krylov, prec, inner):
     """(FGMRES(30) with the block-diagonal preconditioner stalls near 1e-8 on
     the Voronoi mesh at k = 2 -- the paper reports 600-700 GMRES iterations
     for Block-Schur on CVT meshes at k = 2 -- so the block-diagonal cases run
-    MINRES, which is not restarted.)"""
+    MINRES, which is not restarted.  The block-triangular FGMRES(30) needs
+    about 3,100 iterations there to 1e-12, a count that moves by a restart
+    cycle with the rounding of the inner solves, so the cap is 6,000.)"""
     from oracle import solvers
     s, sys_ = _k2_pair(vs, mname, krylov=krylov, precond=prec, inner=inner, rtol=1e-12, inner_rtol=1e-13,
-                       maxit=3000)
+                       maxit=6000)
     try:
         u, p, st = s.solve()
     finally:
@@ -256,7 +258,9 @@ def test_quadrature_points_into_device_buffer(vs):
 
 def test_k2_unsupported_combinations(vs):
     mesh = hex_mesh(2)
-    s = vs.Solver(mesh, element=vs.VEM_ELEMENT_K2, krylov=1, precond=vs.VEM_PREC_BLOCK_TRI)
+    # batched solves take the Jacobi-PCG inner solver only, as for every element
+    s = vs.Solver(mesh, element=vs.VEM_ELEMENT_K2, krylov=1, precond=vs.VEM_PREC_BLOCK_TRI,
+                  inner=vs.VEM_INNER_AMG)
     try:
         s.set_data(_f2, _g2)
         with pytest.raises(vs.VemError) as e:
