@@ -181,7 +181,7 @@ struct vem_handle {
   std::vector<uintptr_t> bpcg_key;
   int64_t bpcg_kernels = 0, bpcg16_kernels = 0;
   int last_bpcg_iters = 0;
-  std::vector<uintptr_t> pcg_graph_key;
+  std::vector<uintptr_t> pcg_graph_key, pcg_graph16_key;
   int64_t pcg_graph_kernels = 0, pcg_graph16_kernels = 0;
   double lambda = 0.0;                           // the mean-zero multiplier
 };

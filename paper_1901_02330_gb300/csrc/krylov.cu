@@ -516,21 +516,19 @@ static bool capture_graph(vem_handle *h, cudaGraphExec_t &slot, int64_t &kernels
   return true;
 }
 
-// The inner PCG's graphs of 4 and of 16 iterations for one set of launch
-// arguments (key).
+// The inner PCG's graph of 4 iterations for one set of launch arguments
+// (key); the 16-iteration graph of the same key is captured later, on first
+// use (pcg_graph16_key).
 template <class F>
 static bool capture_pcg_graphs(vem_handle *h, const std::vector<uintptr_t> &key, F iteration) {
   h->pcg_graph_key.clear();
+  h->pcg_graph16_key.clear();
   const bool ok = capture_graph(h, h->pcg_graph, h->pcg_graph_kernels, [&]() {
-                    for (int k = 0; k < 4; ++k) iteration();
-                  }) &&
-                  capture_graph(h, h->pcg_graph16, h->pcg_graph16_kernels, [&]() {
-                    for (int k = 0; k < 16; ++k) iteration();
-                  });
+    for (int k = 0; k < 4; ++k) iteration();
+  });
   if (ok) h->pcg_graph_key = key;
   return ok;
 }
-
 // One launch of the tiled batched Schur SpMV with kR systems per tile.
 template <class T, int kR>
 static void launch_tiles_r(vem_handle *h, const VemOp &op, const T *sval, const T *u, const T *r, T *w,
@@ -720,14 +718,24 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
       (uintptr_t)tol_bits,
       (uintptr_t)amg, (uintptr_t)(amg ? amg_generation(h->amg) : 0), sizeof(T), (uintptr_t)op.nbatch,
       (uintptr_t)op.S.rows, (uintptr_t)op.S.stored};
-  bool graph = h->pcg_graph != nullptr && h->pcg_graph16 != nullptr && h->pcg_graph_key == key;
+  bool graph = h->pcg_graph != nullptr && h->pcg_graph_key == key;
   if (!graph) graph = capture_pcg_graphs(h, key, iteration);
+  // 16-iteration graphs for the long Jacobi-PCG solves only: with the AMG
+  // each iteration holds a whole V-cycle, the key changes with every
+  // hierarchy, and capturing 16 cycles costs more than their launches save
+  bool g16 = graph && h->pcg_graph16 != nullptr && h->pcg_graph16_key == key;
   int it = 0;
   while (it < maxit) {
     const int end = it + chunk < maxit ? it + chunk : maxit;
     chunk = 4;
     if (graph) {
-      for (; it + kLongIters <= end; it += kLongIters) {
+      if (!g16 && !amg && end - it >= kLongIters) {
+        g16 = capture_graph(h, h->pcg_graph16, h->pcg_graph16_kernels, [&]() {
+          for (int k = 0; k < kLongIters; ++k) iteration();
+        });
+        if (g16) h->pcg_graph16_key = key;
+      }
+      for (; g16 && it + kLongIters <= end; it += kLongIters) {
         VEM_CUDA(h, cudaGraphLaunch(h->pcg_graph16, s));
         count_launches(h->pcg_graph16_kernels);
       }
