@@ -312,7 +312,13 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(int64_t n, T *x, T *r
 // end.  Rows are dealt as in the SpMV (row 32 s + lane of slice s, slices to
 // the warps in turn).  At most maxit updates; the host reads S_PCG_DONE /
 // S_PCG_IT / S_PCG_BAD as after the multi-launch form.
-constexpr int kSmallCgRows = 4096;      // n_p up to this runs in one block
+// One block pays off while S is small enough for one SM's FP64 rate: about
+// 5 us per iteration on 3.6k stored entries (8^3, E0) against ~17 us for the
+// two dependent launches, but ~0.8 ns per stored entry, so it loses beyond
+// ~20k entries (a 1,000-cell CVT mesh at k = 2, 112k entries: 87 against
+// 23 us per iteration).
+constexpr int kSmallCgRows = 4096;        // shared-memory capacity (6 vectors)
+constexpr int64_t kSmallCgStored = 16384; // stored entries of S
 constexpr int kSmallCgThreads = 1024;
 
 // a, b, c summed over the block in a fixed order: a tree over the threads'
@@ -485,12 +491,10 @@ __global__ void k_f32_to_f64(int64_t n, const float *__restrict__ a, double *b) 
 // false, with no graph, when capture or instantiation fails.
 template <class F>
 static bool capture_graph(vem_handle *h, cudaGraphExec_t &slot, int64_t &kernels, F body) {
-  if (slot) {
-    cudaGraphExecDestroy(slot);
-    slot = nullptr;
-  }
   if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
+    if (slot) cudaGraphExecDestroy(slot);
+    slot = nullptr;
     return false;
   }
   cudaStream_t saved = h->stream;
@@ -505,9 +509,23 @@ static bool capture_graph(vem_handle *h, cudaGraphExec_t &slot, int64_t &kernels
   }
   const int64_t nk = launch_count() - l0;
   count_launches(-nk);
-  if (ok) ok = cudaGraphInstantiate(&slot, g, 0) == cudaSuccess;
+  // an executable graph of the same topology (the same launch sequence with
+  // other arguments, e.g. a rebuilt hierarchy of the same depth) is updated
+  // in place, which costs far less than a new instantiation
+  bool updated = false;
+  if (ok && slot) {
+    cudaGraphExecUpdateResultInfo info;
+    updated = cudaGraphExecUpdate(slot, g, &info) == cudaSuccess;
+    if (!updated) cudaGetLastError();
+  }
+  if (!updated && slot) {
+    cudaGraphExecDestroy(slot);
+    slot = nullptr;
+  }
+  if (ok && !updated) ok = cudaGraphInstantiate(&slot, g, 0) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
   if (!ok) {
+    if (slot) cudaGraphExecDestroy(slot);
     slot = nullptr;
     cudaGetLastError();
     return false;
@@ -620,7 +638,7 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   bool amg = false;
   if constexpr (sizeof(T) == sizeof(double)) amg = h->opt.inner != VEM_INNER_PCG;
   const int maxit = h->opt.inner_maxit;
-  if (!amg && op.nbatch == 1 && n <= kSmallCgRows) {
+  if (!amg && op.nbatch == 1 && n <= kSmallCgRows && op.S.stored <= kSmallCgStored) {
     const size_t smem = 6 * (size_t)n * sizeof(T);
     static bool attr_set[2] = {false, false};
     if (!attr_set[sizeof(T) == sizeof(double)]) {

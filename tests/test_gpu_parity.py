@@ -129,14 +129,15 @@ def test_solve_matches_oracle_direct(vs, mname, ename, method, krylov, prec):
     s.close()
 
 
-@pytest.mark.parametrize("n_side", [16, 17], ids=["one-block-pcg", "multi-launch-pcg"])
+@pytest.mark.parametrize("n_side", [12, 17], ids=["one-block-pcg", "multi-launch-pcg"])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 def test_inner_pcg_both_forms(vs, n_side, precision):
     """The inner Jacobi-PCG runs in one thread block for S of up to 4,096
-    rows (16^3 cells: 4,096) and as launches of its multi-block kernels
-    above (17^3: 4,913): both forms reach the oracle's direct solution with
-    a general right-hand side (FP64: 1e-10; mixed: FP32 inner solve, FP64
-    refinement), in FGMRES with the block-triangular preconditioner."""
+    rows and 16,384 stored entries (12^3 cells: 1,728 rows, 7-point rows)
+    and as launches of its multi-block kernels above (17^3: 4,913 rows):
+    both forms reach the oracle's direct solution with a general right-hand
+    side (FP64: 1e-10; mixed: FP32 inner solve, FP64 refinement), in FGMRES
+    with the block-triangular preconditioner."""
     mesh = hex_mesh(n_side)
     K = fields.K_lognormal(mesh.n_cells, seed=9, sigma=1.0)
     f = np.random.default_rng(3).standard_normal(mesh.n_cells)
