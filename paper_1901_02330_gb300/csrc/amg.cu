@@ -818,6 +818,7 @@ __global__ void k_gauss_jordan(int n, double *M, int *err) {
 
 // ------------------------------------------------------------ V-cycle -----
 __device__ __forceinline__ bool cycle_done(const double *sc) {
+  pdl_wait();   // the previous kernel's results first (launch_pdl)
   __shared__ int f;
   if (threadIdx.x == 0) f = (sc && sc[0] != 0.0) ? 1 : 0;
   __syncthreads();
@@ -961,11 +962,11 @@ static void csr_launch(cudaStream_t s, const CsrBuf &M, const T *x, const T *b, 
   const T *v = vals<T>(M);
   count_launch();
   switch (M.lanes) {
-    case 2: k_vc_csr<2, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
-    case 4: k_vc_csr<4, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
-    case 8: k_vc_csr<8, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
-    case 16: k_vc_csr<16, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
-    default: k_vc_csr<32, T, Ty, kMode><<<g, 256, 0, s>>>(M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
+    case 2: launch_pdl(k_vc_csr<2, T, Ty, kMode>, g, 256, 0, s, M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
+    case 4: launch_pdl(k_vc_csr<4, T, Ty, kMode>, g, 256, 0, s, M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
+    case 8: launch_pdl(k_vc_csr<8, T, Ty, kMode>, g, 256, 0, s, M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
+    case 16: launch_pdl(k_vc_csr<16, T, Ty, kMode>, g, 256, 0, s, M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
+    default: launch_pdl(k_vc_csr<32, T, Ty, kMode>, g, 256, 0, s, M.rows, M.rp, M.col, v, x, b, wd, y, sc, xp, c); break;
   }
 }
 
@@ -973,8 +974,8 @@ template <int kMode, class T, class Ty>
 static void sell_launch(cudaStream_t s, const SellMat &A, const T *val, const T *x, const T *b, const T *wd, Ty *y,
                         const double *sc, const T *xp = nullptr, T c = 0) {
   count_launch();
-  k_vc_sell<T, Ty, kMode><<<warps_grid(A.nslices), 256, 0, s>>>(A.rows, A.nslices, A.off, A.col, val, x, b, wd, y,
-                                                                sc, xp, c);
+  launch_pdl(k_vc_sell<T, Ty, kMode>, warps_grid(A.nslices), 256, 0, s, A.rows, A.nslices, A.off, A.col, val, x, b,
+             wd, y, sc, xp, c);
 }
 
 __global__ void k_rp_counts(int64_t n, const int64_t *__restrict__ rp, int64_t *cnt) {
@@ -2357,7 +2358,7 @@ template <> const float *wdcv<float>(const AmgLevel &L) { return L.wdc32; }
 static void blk_launch(cudaStream_t s, const AmgLevel &L, double scale, const double *r, const double *x,
                        const double *xp, double c, double *y, int mode, const double *sc) {
   count_launch();
-  k_blk_apply<<<rows_grid(L.n), 256, 0, s>>>(L.n, L.bs, L.dblk, scale, r, x, xp, c, y, mode, sc);
+  launch_pdl(k_blk_apply, rows_grid(L.n), 256, 0, s, L.n, L.bs, L.dblk, scale, r, x, xp, c, y, mode, sc);
 }
 
 static void coarsest_solve(vem_handle *h, AmgState *S, int l, const double *b, double *x, const double *sc);
@@ -2446,18 +2447,18 @@ static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const do
       else inv = S->cinv32;
       count_launch();
       if constexpr (sizeof(T) == sizeof(Ty)) {
-        k_vc_dense<T><<<g, 256, 0, s>>>((int)L.n, inv, b, x, sc);
+        launch_pdl(k_vc_dense<T>, g, 256, 0, s, (int)L.n, inv, b, x, sc);
       } else {
-        k_vc_dense<T><<<g, 256, 0, s>>>((int)L.n, inv, b, xo, sc);
+        launch_pdl(k_vc_dense<T>, g, 256, 0, s, (int)L.n, inv, b, xo, sc);
         count_launch();
-        k_vc_convert<T, Ty><<<rows_grid(L.n), 256, 0, s>>>(L.n, xo, x, sc);
+        launch_pdl(k_vc_convert<T, Ty>, rows_grid(L.n), 256, 0, s, L.n, (const T *)xo, x, sc);
       }
       return;
     }
     // damped-Jacobi sweeps from zero: x1 = wd b, then x_{k+1} = post(x_k)
     T *xa = L.vx<T>(0), *xb = L.vx<T>(3);
     count_launch();
-    k_vc_pre<T><<<rows_grid(L.n), 256, 0, s>>>(L.n, b, wd, xa, sc);
+    launch_pdl(k_vc_pre<T>, rows_grid(L.n), 256, 0, s, L.n, b, wd, xa, sc);
     for (int k = 1; k < S->csweeps; ++k) {
       if (k == S->csweeps - 1) op_launch<kPost>(s, S, l, (const T *)xa, b, wd, x, sc);
       else op_launch<kPost>(s, S, l, (const T *)xa, b, wd, xb, sc);
@@ -2477,7 +2478,7 @@ static void cycle(vem_handle *h, AmgState *S, int l, const T *b, Ty *x, const do
   const T cc = (T)L.cheb_c;
   const T *wdc = cheb ? wdcv<T>(L) : nullptr;
   count_launch();
-  k_vc_pre<T><<<rows_grid(L.n), 256, 0, s>>>(L.n, b, wd, xa, sc);               // xa = w D^-1 b
+  launch_pdl(k_vc_pre<T>, rows_grid(L.n), 256, 0, s, L.n, b, wd, xa, sc);        // xa = w D^-1 b
   if (cheb) {
     // second Chebyshev step from x0 = 0: xc = xa + c xa + wdc (b - A xa)
     T *xc = L.vx<T>(4);
@@ -2529,12 +2530,12 @@ static void coarsest_solve(vem_handle *h, AmgState *S, int l, const double *b, d
   if (S->csweeps == 0) {
     const int g = (int)std::min<int64_t>((L.n + 7) / 8, 1024);
     count_launch();
-    k_vc_dense<double><<<g, 256, 0, s>>>((int)L.n, S->cinv, b, x, sc);
+    launch_pdl(k_vc_dense<double>, g, 256, 0, s, (int)L.n, (const double *)S->cinv, b, x, sc);
     return;
   }
   double *xa = L.vx<double>(0), *xb = L.vx<double>(3);
   count_launch();
-  k_vc_pre<double><<<rows_grid(L.n), 256, 0, s>>>(L.n, b, L.wd, xa, sc);
+  launch_pdl(k_vc_pre<double>, rows_grid(L.n), 256, 0, s, L.n, b, (const double *)L.wd, xa, sc);
   for (int k = 1; k < S->csweeps; ++k) {
     if (k == S->csweeps - 1) op_launch<kPost>(s, S, l, (const double *)xa, b, (const double *)L.wd, x, sc);
     else op_launch<kPost>(s, S, l, (const double *)xa, b, (const double *)L.wd, xb, sc);

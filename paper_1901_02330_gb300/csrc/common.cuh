@@ -58,6 +58,35 @@ void count_launch();
 void count_launches(int64_t n);   // n may be negative (launches recorded into a graph)
 int64_t launch_count();
 
+// ---- programmatic dependent launch -----------------------------------------
+// The latency-bound chains (V-cycle and inner-CG kernels) are launched with
+// programmatic stream serialisation: a kernel's blocks may be scheduled while
+// the previous kernel of the stream drains, and every such kernel first
+// waits (griddepcontrol.wait) until that kernel has completed and its memory
+// is visible, before it reads or writes anything.  Without the launch
+// attribute the wait returns at once.
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---- reductions -----------------------------------------------------------
 // Deterministic two-pass reductions: every block writes its partial sums to
 // part[slot * kMaxBlocks + block]; a consumer sums the partials of a slot in

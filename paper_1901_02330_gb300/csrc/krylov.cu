@@ -93,6 +93,7 @@ enum { CG_ALPHA = 24, CG_BETA, CG_GPREV, CG_APREV, CG_BB, CG_ITER };
 // The converged flag read once per block and broadcast, so an early return is
 // uniform across the block.
 __device__ __forceinline__ bool block_done(const double *sc) {
+  pdl_wait();   // the previous kernel's results first (launch_pdl)
   __shared__ int f;
   if (threadIdx.x == 0) f = (sc[S_PCG_DONE] != 0.0);
   __syncthreads();
@@ -709,15 +710,17 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
     cudaStream_t cs = h->stream;
     count_launch();
     if (amg) {
-      k_cg_update<T, false><<<nb, kRedThreads, 0, cs>>>(n, x, r, u, p, sv, w, dinv, sc, h->part);
+      launch_pdl(k_cg_update<T, false>, nb, kRedThreads, 0, cs, n, x, r, u, p, sv, (const T *)w, dinv,
+                 (const double *)sc, h->part);
       precondition();
     } else {
-      k_cg_update<T><<<nb, kRedThreads, 0, cs>>>(n, x, r, u, p, sv, w, dinv, sc, h->part);
+      launch_pdl(k_cg_update<T, true>, nb, kRedThreads, 0, cs, n, x, r, u, p, sv, (const T *)w, dinv,
+                 (const double *)sc, h->part);
     }
     if (op.nbatch == 1) {
       count_launch();
-      k_cg_spmv<T><<<nbs, 256, 0, cs>>>(op.S.rows, op.S.nslices, op.S.stored, op.S.off, op.S.col, sval, u, r, w,
-                                        h->part, sc, h->ctr + 1, tol2, nb);
+      launch_pdl(k_cg_spmv<T>, nbs, 256, 0, cs, op.S.rows, op.S.nslices, op.S.stored, op.S.off, op.S.col, sval,
+                 (const T *)u, (const T *)r, w, h->part, sc, h->ctr + 1, tol2, nb);
     } else {
       launch_tiles<T>(h, op, sval, u, r, w, tol2, nb, tile, 0);
     }
