@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--no-general", action="store_true", help="skip the polynomial-data (non-eigenvector) run")
     ap.add_argument("--inner-rtol", type=float, default=INNER_RTOL, help="inner Schur solve tolerance")
+    ap.add_argument("--inner-smoother", default="jacobi", choices=["jacobi", "chebyshev"],
+                    help="smoother of the inner AMG V-cycle")
     ap.add_argument("--element", default="k1", choices=["k1", "e0"])
     ap.add_argument("--inner", default="amg", choices=["pcg", "amg"],
                     help="inner Schur solver: Jacobi-PCG or AMG-preconditioned CG")
@@ -331,7 +333,8 @@ def run_ours(a):
     inner = vs.VEM_INNER_AMG if a.inner == "amg" else vs.VEM_INNER_PCG
     opts = dict(element=elem, krylov=vs.VEM_KRYLOV_FGMRES, restart=30,
                 precond=vs.VEM_PREC_BLOCK_TRI, rtol=RTOL, inner_rtol=a.inner_rtol, inner_maxit=2000,
-                maxit=1000, inner=inner)
+                maxit=1000, inner=inner,
+                inner_smoother=vs.VEM_SMOOTH_CHEBYSHEV if a.inner_smoother == "chebyshev" else vs.VEM_SMOOTH_JACOBI)
 
     # ---------------- device-resident path (value) ----------------
     s = vs.Solver(mesh, stream=sid, device_io=1, **opts)
@@ -549,7 +552,8 @@ def run_ours(a):
                    "element": ("paper k=1 (face P1 + 3 cross moments, P0 pressure)" if a.element == "k1"
                                else "E0 (one flux moment per face, P0 pressure)"),
                    "krylov": "FGMRES(30)", "precond": "block upper-triangular, S = B diag(M)^-1 B^T",
-                   "inner": (f"AMG-PCG (smoothed aggregation, V(1,1)) rtol {a.inner_rtol:g}" if a.inner == "amg"
+                   "inner": (f"AMG-PCG (smoothed aggregation, V-cycle with {a.inner_smoother} smoothing) "
+                             f"rtol {a.inner_rtol:g}" if a.inner == "amg"
                              else f"Jacobi-PCG rtol {a.inner_rtol:g}"), "rtol": RTOL, "K": "identity",
                    "l2": "inputs larger than L2 (saddle matrix ~%.1f GB streamed every step)" % (st["nnz_A"] * 12 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
