@@ -426,7 +426,7 @@ __global__ void k_rhs_cells(int64_t nc, const double *__restrict__ c_vol,
 
 // g_(f,beta) = -sigma |f| sum_g Ginv[g][beta] int_f g_D m^f_g on Dirichlet
 // faces (zero elsewhere), with the Dunavant fan rule of the bface points.
-__global__ void k_rhs_faces(int64_t nf, int nfd, const int8_t *__restrict__ fbc,
+__global__ void k_rhs_faces(int64_t nbf, const int32_t *__restrict__ bface, int nfd, const int8_t *__restrict__ fbc,
                             const int64_t *__restrict__ off, const int64_t *__restrict__ fvp,
                             const int32_t *__restrict__ fv, const double *__restrict__ xyz,
                             const double *__restrict__ f_area, const double *__restrict__ f_cent,
@@ -435,9 +435,10 @@ __global__ void k_rhs_faces(int64_t nf, int nfd, const int8_t *__restrict__ fbc,
                             const int32_t *__restrict__ f_loc, const int64_t *__restrict__ cfp,
                             const int8_t *__restrict__ sig, const double *__restrict__ gD, double *g,
                             int *err) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
-       f += (int64_t)gridDim.x * blockDim.x) {
-    for (int bta = 0; bta < nfd; ++bta) g[nfd * f + bta] = 0.0;
+  // boundary faces only (g is zeroed beforehand)
+  for (int64_t ib = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ib < nbf;
+       ib += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = bface[ib];
     if (fbc[f] != 1 || gD == nullptr) continue;
     const int64_t vb = fvp[f];
     const int m = (int)(fvp[f + 1] - vb);
@@ -541,7 +542,7 @@ vem_status assemble_local(vem_handle *h) {
 // Prescribed face DOFs on flux faces (flag 2): (f, beta) = (1/|f|) int_f
 // (u.n_f) m^f_beta with u.n_f = sigma u_N (u_N given along the outward
 // normal), by the Dunavant fan rule of the bface points; zero elsewhere.
-__global__ void k_flux_fixed(int64_t nf, int nfd, const int8_t *__restrict__ fbc,
+__global__ void k_flux_fixed(int64_t nbf, const int32_t *__restrict__ bface, int nfd, const int8_t *__restrict__ fbc,
                              const int64_t *__restrict__ off, const int64_t *__restrict__ fvp,
                              const int32_t *__restrict__ fv, const double *__restrict__ xyz,
                              const double *__restrict__ f_area, const double *__restrict__ f_cent,
@@ -550,9 +551,10 @@ __global__ void k_flux_fixed(int64_t nf, int nfd, const int8_t *__restrict__ fbc
                              const int32_t *__restrict__ f_loc, const int64_t *__restrict__ cfp,
                              const int8_t *__restrict__ sig, const double *__restrict__ uN, double *xfix,
                              int *err) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
-       f += (int64_t)gridDim.x * blockDim.x) {
-    for (int bta = 0; bta < nfd; ++bta) xfix[nfd * f + bta] = 0.0;
+  // boundary faces only (the caller zeroes xfix)
+  for (int64_t ib = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ib < nbf;
+       ib += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = bface[ib];
     if (fbc[f] != 2 || uN == nullptr) continue;
     const int64_t vb = fvp[f];
     const int m = (int)(fvp[f + 1] - vb);
@@ -589,9 +591,9 @@ __global__ void k_flux_fixed(int64_t nf, int nfd, const int8_t *__restrict__ fbc
 
 vem_status flux_fixed(vem_handle *h, double *xfix) {
   count_launch();
-  k_flux_fixed<<<grid_for(h->nf, 128), 128, 0, h->stream>>>(
-      h->nf, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm, h->f_t1,
-      h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, h->gD_qp, xfix, h->d_err);
+  k_flux_fixed<<<grid_for(h->n_bface, 128), 128, 0, h->stream>>>(
+      h->n_bface, h->bface, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent,
+      h->f_norm, h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, h->gD_qp, xfix, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   return VEM_OK;
 }
@@ -600,9 +602,10 @@ vem_status assemble_rhs_into(vem_handle *h, const double *f_qp, const double *gD
   if (h->nq > 1) return assemble_rhs_k2(h, f_qp, gD_qp, g, F);
   cudaStream_t s = h->stream;
   const int T = 128;
-  count_launch(); k_rhs_faces<<<grid_for(h->nf, T), T, 0, s>>>(
-      h->nf, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm,
-      h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, gD_qp, g, h->d_err);
+  VEM_CUDA(h, cudaMemsetAsync(g, 0, sizeof(double) * h->nfd * h->nf, s));
+  count_launch(); k_rhs_faces<<<grid_for(h->n_bface, T), T, 0, s>>>(
+      h->n_bface, h->bface, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent,
+      h->f_norm, h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, gD_qp, g, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   if (h->nid > 0)
     VEM_CUDA(h, cudaMemsetAsync(g + h->nfd * h->nf, 0, sizeof(double) * h->nid * h->nc, s));

@@ -581,7 +581,8 @@ __global__ void k_rhs_cells_k2(int64_t nc, const int64_t *__restrict__ off, cons
 // faces (zero elsewhere) for the six face moments; the face Gram matrix and
 // the load by the Dunavant degree-4 fan rule of the boundary-face points
 // (exact for products of M_2(f) monomials).
-__global__ void k_rhs_faces_k2(int64_t nf, const int8_t *__restrict__ fbc, const int64_t *__restrict__ off,
+__global__ void k_rhs_faces_k2(int64_t nbf, const int32_t *__restrict__ bface, const int8_t *__restrict__ fbc,
+                               const int64_t *__restrict__ off,
                                const int64_t *__restrict__ fvp, const int32_t *__restrict__ fv,
                                const double *__restrict__ xyz, const double *__restrict__ f_area,
                                const double *__restrict__ f_cent, const double *__restrict__ f_norm,
@@ -590,8 +591,10 @@ __global__ void k_rhs_faces_k2(int64_t nf, const int8_t *__restrict__ fbc, const
                                const int64_t *__restrict__ cfp, const int8_t *__restrict__ sig,
                                const double *__restrict__ gD, double *g, int *err) {
   const int fb[6][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}};
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
-    for (int bt = 0; bt < 6; ++bt) g[6 * f + bt] = 0.0;
+  // boundary faces only (g is zeroed beforehand)
+  for (int64_t ib = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ib < nbf;
+       ib += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = bface[ib];
     if (fbc[f] != 1 || gD == nullptr) continue;
     const int64_t vb = fvp[f];
     const int m = (int)(fvp[f + 1] - vb);
@@ -706,11 +709,12 @@ vem_status flux_modes_k2(vem_handle *h, double *B) {
 vem_status assemble_rhs_k2(vem_handle *h, const double *f_qp, const double *gD_qp, double *g, double *F) {
   cudaStream_t s = h->stream;
   VEM_TRY(cell_points_k2(h));
+  VEM_CUDA(h, cudaMemsetAsync(g, 0, sizeof(double) * 6 * h->nf, s));
   count_launch();
-  k_rhs_faces_k2<<<grid_for(h->nf, 128), 128, 0, s>>>(h->nf, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz,
-                                                        h->f_area, h->f_cent, h->f_norm, h->f_t1, h->f_diam,
-                                                        h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, gD_qp, g,
-                                                        h->d_err);
+  k_rhs_faces_k2<<<grid_for(h->n_bface, 128), 128, 0, s>>>(h->n_bface, h->bface, h->fbc, h->bqp_off, h->fv_ptr,
+                                                            h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm,
+                                                            h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr,
+                                                            h->cf_sigma, gD_qp, g, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   VEM_CUDA(h, cudaMemsetAsync(g + 6 * h->nf, 0, sizeof(double) * 14 * h->nc, s));
   count_launch();

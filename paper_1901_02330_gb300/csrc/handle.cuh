@@ -98,6 +98,8 @@ struct vem_handle {
   vem::SellMat A, S;
   double *rhs = nullptr;                         // [n] = [g; F]
   double *bt_face = nullptr;                     // [2 nf] B entries of each face's cells
+  int32_t *bface = nullptr;                      // [n_bface] the boundary faces, increasing
+  int64_t n_bface = 0;
   // several pressure DOFs per cell: the B^T entries of every flux row of A
   // (pressure column, value), kBtRow per row in row order, zero-padded
   int32_t *bt_col = nullptr;

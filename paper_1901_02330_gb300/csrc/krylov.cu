@@ -641,12 +641,9 @@ static vem_status pcg_solve_t(vem_handle *h, const VemOp &op, const T *sval, con
   const int maxit = h->opt.inner_maxit;
   if (!amg && op.nbatch == 1 && n <= kSmallCgRows && op.S.stored <= kSmallCgStored) {
     const size_t smem = 6 * (size_t)n * sizeof(T);
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == sizeof(double)]) {
-      VEM_CUDA(h, cudaFuncSetAttribute(k_cg_block<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       6 * kSmallCgRows * (int)sizeof(T)));
-      attr_set[sizeof(T) == sizeof(double)] = true;
-    }
+    // per call: the attribute belongs to the current device
+    VEM_CUDA(h, cudaFuncSetAttribute(k_cg_block<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     6 * kSmallCgRows * (int)sizeof(T)));
     // a warp per slice up to 32 warps (a power of two for the tree sums)
     int nthr = 32;
     while (nthr < kSmallCgThreads && nthr < 32 * op.S.nslices) nthr <<= 1;
