@@ -523,8 +523,54 @@ static vem_status sell_layout(vem_handle *h, SellMat &M, int64_t rows, const int
   return VEM_OK;
 }
 
+// The same scan in one block for short arrays (the layouts of small meshes,
+// coarse AMG levels): every thread sums a run of consecutive entries, the
+// run totals are scanned across the block, and each thread writes its run's
+// prefix sums.  One launch instead of three.
+constexpr int kScanOneThreads = 1024;
+constexpr int64_t kScanOneMax = 32768;
+
+__global__ void __launch_bounds__(kScanOneThreads) k_scan_one(int64_t n, const int64_t *__restrict__ in,
+                                                              int64_t *out) {
+  __shared__ int64_t ws[kScanOneThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+  const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t lo = t * per, hi = lo + per < n ? lo + per : n;
+  int64_t run = 0;
+  for (int64_t i = lo; i < hi; ++i) run += in[i];
+  int64_t v = run;   // inclusive scan of the run totals: warp, then across warps
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) ws[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int64_t x = lane < nw ? ws[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    if (lane < nw) ws[lane] = x;
+  }
+  __syncthreads();
+  int64_t acc = v - run + (w > 0 ? ws[w - 1] : 0);   // exclusive prefix of this run
+  if (t == 0) out[0] = 0;
+  for (int64_t i = lo; i < hi; ++i) {
+    acc += in[i];
+    out[i + 1] = acc;
+  }
+}
+
 vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *out, int64_t *total) {
   cudaStream_t s = h->stream;
+  if (n <= kScanOneMax) {
+    count_launch(); k_scan_one<<<1, kScanOneThreads, 0, s>>>(n, cnt, out);
+    VEM_CUDA(h, cudaGetLastError());
+    VEM_CUDA(h, cudaMemcpyAsync(total, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    VEM_CUDA(h, cudaStreamSynchronize(s));
+    return VEM_OK;
+  }
   if (!h->scan_buf) VEM_TRY(dalloc_n(h, &h->scan_buf, kScanBlocks));
   int64_t *bsum = h->scan_buf;
   count_launch(); k_scan_sums<<<kScanBlocks, kScanThreads, 0, s>>>(n, cnt, bsum);
