@@ -253,7 +253,12 @@ vem_status vem_sizes(const vem_handle *h, int64_t *n_u, int64_t *n_p);
  *   which = VEM_QP_BFACE: for every face with face_bc 1 or 2, in face
  *                         order, its fan triangles (x_f, v_i, v_{i+1}) each
  *                         with the 6-point degree-4 rule of Dunavant (1985)
- *                         (n = 6 * sum of those faces' vertex counts).
+ *                         for E0 and K1, Radon's 7-point degree-5 rule for
+ *                         K2 (g_D m^f has degree 5 for the cubic pressures
+ *                         of the k = 2 patch test) (n = 6 or 7 * sum of
+ *                         those faces' vertex counts; an element change
+ *                         between K2 and the others rebuilds the points and
+ *                         clears the boundary data).
  * vem_quadrature_count gives n; vem_quadrature_points writes [n][3]
  * coordinates to xyz_out, a host buffer or a device buffer of the handle's
  * device (the copy's direction follows the pointer; the k = 2 cell set of a

@@ -32,7 +32,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse as sp
 
-from .element import ElementSpec, local_system
+from .element import ElementSpec, boundary_rule, local_system
 from .polyhedron import all_faces, cell_geometry, face_geometry
 
 
@@ -149,15 +149,18 @@ def _parallel_items(mesh, spec, nu_cell, f, gD, nq, bface_rule, processes):
 
 
 def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False, nq=5, flux=None,
-             bface_rule="dunavant4", processes: int = 1) -> System:
+             bface_rule=None, processes: int = 1) -> System:
     """Assemble M, B, g, F.  nu_cell = 1/K per cell (eq. bilin_form, nu = K^-1).
     flux: the vector field u (callable (N,3) -> (N,3)) whose normal component
     is prescribed on faces with flag 2.  bface_rule: the fan rule of the
-    Dirichlet term ('dunavant4', the library's, or 'radon5').
+    boundary data (the Dirichlet term and the prescribed flux moments),
+    'dunavant4' or 'radon5'; by default the library's, boundary_rule(spec).
     processes > 1 computes the per-cell local systems in that many spawned
     worker processes (f, gD must then be picklable, e.g. module-level
     functions); the global sums run in cell order either way, so the result
     is the same bit for bit."""
+    if bface_rule is None:
+        bface_rule = boundary_rule(spec)
     nu_cell = np.asarray(nu_cell, dtype=np.float64)
     n_u = spec.nfd * mesh.n_faces + spec.nid * mesh.n_cells
     n_p = spec.nq * mesh.n_cells
@@ -195,7 +198,7 @@ def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False
     B = sp.csr_matrix((np.concatenate(bvals), (np.concatenate(brows), np.concatenate(bcols))), shape=(n_p, n_u))
     M.sum_duplicates()
     B.sum_duplicates()
-    fixed, fixed_val = prescribed_flux_dofs(mesh, spec, faces, flux)
+    fixed, fixed_val = prescribed_flux_dofs(mesh, spec, faces, flux, bface_rule)
     return System(spec=spec, M=M, B=B, g=g, F=F, n_u=n_u, n_p=n_p,
                   cells=cells if keep_local else None,
                   local=locs if keep_local else None,
@@ -204,11 +207,11 @@ def assemble(mesh, spec: ElementSpec, nu_cell, f=None, gD=None, keep_local=False
                   multiplier=bool(np.any(mesh.face_bc == 2)) and not bool(np.any(mesh.face_bc == 1)))
 
 
-def prescribed_flux_dofs(mesh, spec: ElementSpec, faces, flux):
+def prescribed_flux_dofs(mesh, spec: ElementSpec, faces, flux, rule=None):
     """Indices and values of the face DOFs fixed by the flux datum: on a face
     with flag 2, DOF (f, beta) = (1/|f|) int_f (u . n_f) m_beta^f with n_f
-    the face's global normal and the boundary-face load rule (Dunavant
-    degree 4 on the fan triangles)."""
+    the face's global normal and the boundary-data rule on the fan
+    triangles (boundary_rule(spec) unless given)."""
     from .element import load_face_points
     from .monomials import eval_mono2, mono2
     fl = np.nonzero(mesh.face_bc == 2)[0]
@@ -220,7 +223,7 @@ def prescribed_flux_dofs(mesh, spec: ElementSpec, faces, flux):
     idx, val = [], []
     for f in fl:
         F = faces[f]
-        pts, wts = load_face_points(F)
+        pts, wts = load_face_points(F, rule or boundary_rule(spec))
         un = flux(pts) @ F.normal
         Mf = eval_mono2(betas, pts, F)
         mom = (wts * un) @ Mf / F.area

@@ -89,7 +89,16 @@ def _cell_gram(alphas_a, alphas_b, cell):
     return (cell.qw[:, None] * Ma).T @ Mb
 
 
-def local_system(cell, spec: ElementSpec, nu: float, f=None, gD=None, details=False, bface_rule="dunavant4"):
+def boundary_rule(spec: ElementSpec) -> str:
+    """The fan rule of the boundary data.  The patch test of order k has
+    g_D in P_{k+1} and u.n in P_k on a face, times the face monomials of
+    degree <= k: degree 2k + 1.  Dunavant's degree-4 rule covers E0 and
+    k = 1; k = 2 needs degree 5, Radon's rule (for k >= 3 it is the
+    highest order at hand, not exact)."""
+    return "radon5" if spec.k >= 2 else "dunavant4"
+
+
+def local_system(cell, spec: ElementSpec, nu: float, f=None, gD=None, details=False, bface_rule=None):
     """Local matrices of cell P.  Returns dict(M, B, F, g[, details...]).
 
     Local DOF order: for each face of the cell (in the cell's face order) its
@@ -201,7 +210,7 @@ def local_system(cell, spec: ElementSpec, nu: float, f=None, gD=None, details=Fa
         for i, F in enumerate(faces):
             if F.bc != 1:
                 continue
-            pts, wts = load_face_points(F, bface_rule)
+            pts, wts = load_face_points(F, bface_rule or boundary_rule(spec))
             Mf = eval_mono2(betas, pts, F)
             gm = (wts[:, None] * Mf).T @ gD(pts)     # int_f g_D m^f_gamma
             g[i * nfd:(i + 1) * nfd] = -F.sigma * F.area * (face_ginv[i].T @ gm)
@@ -214,7 +223,8 @@ def local_system(cell, spec: ElementSpec, nu: float, f=None, gD=None, details=Fa
 
 def load_face_points(F, rule="dunavant4"):
     """Boundary-face load rule on the fan (x_f, v_i, v_{i+1}): Dunavant's
-    degree-4 rule (the library's), or rule='radon5', Radon's degree-5 rule."""
+    degree-4 rule, or rule='radon5', Radon's degree-5 rule (boundary_rule
+    gives the one of an element)."""
     tri = {"dunavant4": dunavant4, "radon5": radon5}[rule]
     V = F.verts
     m = V.shape[0]

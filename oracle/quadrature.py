@@ -13,11 +13,12 @@ definitions and independently in the CUDA library:
 * cell load rule for a P0 pressure: one point at the cell barycentre with
   weight |P| (the midpoint rule, exact for linear f);
 * boundary-face rule: the face is fanned into triangles (x_f, v_i, v_{i+1})
-  and each triangle gets the 6-point degree-4 rule of D.A. Dunavant,
-  "High degree efficient symmetrical Gaussian quadrature rules for the
-  triangle", IJNME 21 (1985), Table for p = 4 (the library's rule), or on
-  request Radon's 7-point degree-5 rule, which makes the Dirichlet term of
-  the k = 2 element exact for cubic g_D.
+  and each triangle gets, for E0 and the paper's k = 1, the 6-point
+  degree-4 rule of D.A. Dunavant, "High degree efficient symmetrical
+  Gaussian quadrature rules for the triangle", IJNME 21 (1985), Table for
+  p = 4, and for k = 2 Radon's 7-point degree-5 rule, which makes the
+  boundary data terms of the k = 2 element exact for cubic g_D (the
+  library uses the same pair).
 """
 
 from __future__ import annotations

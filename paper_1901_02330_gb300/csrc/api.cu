@@ -226,7 +226,7 @@ __global__ void k_compact_ids(int64_t n, const int64_t *__restrict__ flag, const
 }
 
 __global__ void k_check_faces(int64_t nf, const int64_t *__restrict__ fvp, const int8_t *__restrict__ fbc,
-                              unsigned long long *ms, int64_t *bq_cnt) {
+                              unsigned long long *ms, int64_t *bq_cnt, int ppt) {
   unsigned long long nflux = 0, ndir = 0, mx = 0;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = fvp[f + 1] - fvp[f];
@@ -242,7 +242,7 @@ __global__ void k_check_faces(int64_t nf, const int64_t *__restrict__ fvp, const
     nflux += fl == 2;
     ndir += fl == 1;
     if (k > 0 && (unsigned long long)k > mx) mx = (unsigned long long)k;
-    bq_cnt[f] = (fl != 0 && k > 0) ? 6 * k : 0;   // boundary-face load points: 6 per fan triangle
+    bq_cnt[f] = (fl != 0 && k > 0) ? ppt * k : 0;   // boundary-face load points: ppt per fan triangle
   }
   warp_add(nflux, &ms[MS_NFLUX]);
   warp_add(ndir, &ms[MS_NDIR]);
@@ -346,7 +346,10 @@ static vem_status create_impl(vem_handle *h, const vem_mesh *m) {
     VEM_CUDA(h, cudaMemcpyAsync(ms, init, sizeof(init), cudaMemcpyHostToDevice, s));
     int64_t *bq_cnt = nullptr;
     VEM_TRY(dalloc_n(h, &bq_cnt, (size_t)h->nf + 1));
-    count_launch(); k_check_faces<<<grid_for(h->nf, 256), 256, 0, s>>>(h->nf, h->fv_ptr, h->fbc, ms, bq_cnt);
+    // the boundary-data rule: Radon's 7 points per fan triangle at k = 2, Dunavant's 6 otherwise
+    h->bq_ppt = h->opt.element == VEM_ELEMENT_K2 ? 7 : 6;
+    count_launch(); k_check_faces<<<grid_for(h->nf, 256), 256, 0, s>>>(h->nf, h->fv_ptr, h->fbc, ms, bq_cnt,
+                                                                       h->bq_ppt);
     count_launch(); k_check_cells<<<grid_for(h->nc, 256), 256, 0, s>>>(h->nc, h->cf_ptr, ms);
     count_launch(); k_check_ids<<<grid_for(h->n_fv, 256), 256, 0, s>>>(h->n_fv, h->fv, h->nv, MSE_VTX, MS_BAD_FV, ms);
     count_launch(); k_check_ids<<<grid_for(h->n_cf, 256), 256, 0, s>>>(h->n_cf, h->cf, h->nf, MSE_FACE, MS_BAD_CF, ms);
@@ -592,6 +595,8 @@ vem_status vem_set_options(vem_handle *h, const vem_options *opt) {
   h->opt = *opt;
   if (elem_changed) {
     set_layout(h);
+    const int ppt = opt->element == VEM_ELEMENT_K2 ? 7 : 6;
+    if (ppt != h->bq_ppt) VEM_TRY(rebuild_bface_points(h, ppt));
     h->assembled = false;
     h->local_ready = false;
     h->rhs_ready = false;

@@ -426,7 +426,8 @@ __global__ void k_rhs_cells(int64_t nc, const double *__restrict__ c_vol,
 
 // g_(f,beta) = -sigma |f| sum_g Ginv[g][beta] int_f g_D m^f_g on Dirichlet
 // faces (zero elsewhere), with the Dunavant fan rule of the bface points.
-__global__ void k_rhs_faces(int64_t nbf, const int32_t *__restrict__ bface, int nfd, const int8_t *__restrict__ fbc,
+__global__ void k_rhs_faces(int64_t nbf, const int32_t *__restrict__ bface, int ppt, int nfd,
+                            const int8_t *__restrict__ fbc,
                             const int64_t *__restrict__ off, const int64_t *__restrict__ fvp,
                             const int32_t *__restrict__ fv, const double *__restrict__ xyz,
                             const double *__restrict__ f_area, const double *__restrict__ f_cent,
@@ -454,9 +455,9 @@ __global__ void k_rhs_faces(int64_t nbf, const int32_t *__restrict__ bface, int 
       const double3 A = load3(xyz, fv[vb + i]);
       const double3 B = load3(xyz, fv[vb + (i + 1) % m]);
       const double areaT = 0.5 * dot3(cross3(sub3(A, xf), sub3(B, xf)), n);
-      for (int q = 0; q < 6; ++q, ++o) {
+      for (int q = 0; q < ppt; ++q, ++o) {
         double l0, l1, l2, wq;
-        dunavant4_point(q, l0, l1, l2, wq);
+        bface_point(ppt, q, l0, l1, l2, wq);
         const double3 x = add3(add3(scale3(xf, l0), scale3(A, l1)), scale3(B, l2));
         const double w = wq * areaT;
         const double3 dx = sub3(x, xf);
@@ -542,7 +543,8 @@ vem_status assemble_local(vem_handle *h) {
 // Prescribed face DOFs on flux faces (flag 2): (f, beta) = (1/|f|) int_f
 // (u.n_f) m^f_beta with u.n_f = sigma u_N (u_N given along the outward
 // normal), by the Dunavant fan rule of the bface points; zero elsewhere.
-__global__ void k_flux_fixed(int64_t nbf, const int32_t *__restrict__ bface, int nfd, const int8_t *__restrict__ fbc,
+__global__ void k_flux_fixed(int64_t nbf, const int32_t *__restrict__ bface, int ppt, int nfd,
+                             const int8_t *__restrict__ fbc,
                              const int64_t *__restrict__ off, const int64_t *__restrict__ fvp,
                              const int32_t *__restrict__ fv, const double *__restrict__ xyz,
                              const double *__restrict__ f_area, const double *__restrict__ f_cent,
@@ -570,9 +572,9 @@ __global__ void k_flux_fixed(int64_t nbf, const int32_t *__restrict__ bface, int
       const double3 A = load3(xyz, fv[vb + i]);
       const double3 B = load3(xyz, fv[vb + (i + 1) % m]);
       const double areaT = 0.5 * dot3(cross3(sub3(A, xf), sub3(B, xf)), n);
-      for (int q = 0; q < 6; ++q, ++o) {
+      for (int q = 0; q < ppt; ++q, ++o) {
         double l0, l1, l2, wq;
-        dunavant4_point(q, l0, l1, l2, wq);
+        bface_point(ppt, q, l0, l1, l2, wq);
         const double3 x = add3(add3(scale3(xf, l0), scale3(A, l1)), scale3(B, l2));
         const double w = wq * areaT;
         const double3 dx = sub3(x, xf);
@@ -592,8 +594,9 @@ __global__ void k_flux_fixed(int64_t nbf, const int32_t *__restrict__ bface, int
 vem_status flux_fixed(vem_handle *h, double *xfix) {
   count_launch();
   k_flux_fixed<<<grid_for(h->n_bface, 128), 128, 0, h->stream>>>(
-      h->n_bface, h->bface, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent,
-      h->f_norm, h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, h->gD_qp, xfix, h->d_err);
+      h->n_bface, h->bface, h->bq_ppt, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area,
+      h->f_cent, h->f_norm, h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, h->gD_qp, xfix,
+      h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   return VEM_OK;
 }
@@ -604,8 +607,8 @@ vem_status assemble_rhs_into(vem_handle *h, const double *f_qp, const double *gD
   const int T = 128;
   VEM_CUDA(h, cudaMemsetAsync(g, 0, sizeof(double) * h->nfd * h->nf, s));
   count_launch(); k_rhs_faces<<<grid_for(h->n_bface, T), T, 0, s>>>(
-      h->n_bface, h->bface, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area, h->f_cent,
-      h->f_norm, h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, gD_qp, g, h->d_err);
+      h->n_bface, h->bface, h->bq_ppt, h->nfd, h->fbc, h->bqp_off, h->fv_ptr, h->fv, h->xyz, h->f_area,
+      h->f_cent, h->f_norm, h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr, h->cf_sigma, gD_qp, g, h->d_err);
   VEM_CUDA(h, cudaGetLastError());
   if (h->nid > 0)
     VEM_CUDA(h, cudaMemsetAsync(g + h->nfd * h->nf, 0, sizeof(double) * h->nid * h->nc, s));

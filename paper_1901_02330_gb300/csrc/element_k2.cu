@@ -140,23 +140,6 @@ __device__ __forceinline__ double ipow(double x, int p) {
   return r;
 }
 
-// Radon's 7-point rule: barycentric coordinates and area fraction of point q
-__device__ __forceinline__ void radon7_point(int q, double &l0, double &l1, double &l2, double &w) {
-  const double s15 = 3.872983346207416885;   // sqrt(15)
-  if (q == 0) {
-    l0 = l1 = l2 = 1.0 / 3.0;
-    w = 9.0 / 40.0;
-    return;
-  }
-  const bool first = q < 4;
-  const double a = first ? (6.0 - s15) / 21.0 : (6.0 + s15) / 21.0;
-  w = first ? (155.0 - s15) / 1200.0 : (155.0 + s15) / 1200.0;
-  const int r = (q - 1) % 3;
-  l0 = (r == 0) ? 1.0 - 2.0 * a : a;
-  l1 = (r == 1) ? 1.0 - 2.0 * a : a;
-  l2 = (r == 2) ? 1.0 - 2.0 * a : a;
-}
-
 // In-place Gauss-Jordan inverse of an SPD n x n matrix (row-major), one thread.
 __device__ void gj_inverse(double *A, int n) {
   for (int k = 0; k < n; ++k) {
@@ -579,10 +562,11 @@ __global__ void k_rhs_cells_k2(int64_t nc, const int64_t *__restrict__ off, cons
 
 // g_(f,beta) = -sigma |f| sum_g Ginv[g][beta] int_f g_D m^f_g on Dirichlet
 // faces (zero elsewhere) for the six face moments; the face Gram matrix and
-// the load by the Dunavant degree-4 fan rule of the boundary-face points
-// (exact for products of M_2(f) monomials).
-__global__ void k_rhs_faces_k2(int64_t nbf, const int32_t *__restrict__ bface, const int8_t *__restrict__ fbc,
-                               const int64_t *__restrict__ off,
+// the load by the boundary-data rule of the boundary-face points (ppt per
+// fan triangle: Radon's degree 5 at k = 2, exact for g_D in P_3 times the
+// M_2(f) monomials, and for the Gram entries).
+__global__ void k_rhs_faces_k2(int64_t nbf, const int32_t *__restrict__ bface, int ppt,
+                               const int8_t *__restrict__ fbc, const int64_t *__restrict__ off,
                                const int64_t *__restrict__ fvp, const int32_t *__restrict__ fv,
                                const double *__restrict__ xyz, const double *__restrict__ f_area,
                                const double *__restrict__ f_cent, const double *__restrict__ f_norm,
@@ -610,9 +594,9 @@ __global__ void k_rhs_faces_k2(int64_t nbf, const int32_t *__restrict__ bface, c
       const double3 A = load3(xyz, fv[vb + i]);
       const double3 B = load3(xyz, fv[vb + (i + 1) % m]);
       const double areaT = 0.5 * dot3(cross3(sub3(A, xf), sub3(B, xf)), n);
-      for (int q = 0; q < 6; ++q, ++o) {
+      for (int q = 0; q < ppt; ++q, ++o) {
         double l0, l1, l2, wq;
-        dunavant4_point(q, l0, l1, l2, wq);
+        bface_point(ppt, q, l0, l1, l2, wq);
         const double3 x = add3(add3(scale3(xf, l0), scale3(A, l1)), scale3(B, l2));
         const double w = wq * areaT;
         const double3 dx = sub3(x, xf);
@@ -711,7 +695,8 @@ vem_status assemble_rhs_k2(vem_handle *h, const double *f_qp, const double *gD_q
   VEM_TRY(cell_points_k2(h));
   VEM_CUDA(h, cudaMemsetAsync(g, 0, sizeof(double) * 6 * h->nf, s));
   count_launch();
-  k_rhs_faces_k2<<<grid_for(h->n_bface, 128), 128, 0, s>>>(h->n_bface, h->bface, h->fbc, h->bqp_off, h->fv_ptr,
+  k_rhs_faces_k2<<<grid_for(h->n_bface, 128), 128, 0, s>>>(h->n_bface, h->bface, h->bq_ppt, h->fbc, h->bqp_off,
+                                                            h->fv_ptr,
                                                             h->fv, h->xyz, h->f_area, h->f_cent, h->f_norm,
                                                             h->f_t1, h->f_diam, h->f_cell, h->f_loc, h->cf_ptr,
                                                             h->cf_sigma, gD_qp, g, h->d_err);

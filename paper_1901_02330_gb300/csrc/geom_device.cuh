@@ -42,4 +42,30 @@ __device__ __forceinline__ void dunavant4_point(int q, double &l0, double &l1, d
   l2 = (r == 0) ? b : a;
 }
 
+// Radon's 7-point degree-5 rule: barycentric coordinates and area fraction
+// of point q.
+__device__ __forceinline__ void radon7_point(int q, double &l0, double &l1, double &l2, double &w) {
+  const double s15 = 3.872983346207416885;   // sqrt(15)
+  if (q == 0) {
+    l0 = l1 = l2 = 1.0 / 3.0;
+    w = 9.0 / 40.0;
+    return;
+  }
+  const bool first = q < 4;
+  const double a = first ? (6.0 - s15) / 21.0 : (6.0 + s15) / 21.0;
+  w = first ? (155.0 - s15) / 1200.0 : (155.0 + s15) / 1200.0;
+  const int r = (q - 1) % 3;
+  l0 = (r == 0) ? 1.0 - 2.0 * a : a;
+  l1 = (r == 1) ? 1.0 - 2.0 * a : a;
+  l2 = (r == 2) ? 1.0 - 2.0 * a : a;
+}
+
+// Point q of the boundary-data rule on a fan triangle: ppt = 6, Dunavant's
+// degree 4 (E0 and the paper's k = 1); ppt = 7, Radon's degree 5 (k = 2,
+// where g_D m^f has degree 5 for g_D in P_3).
+__device__ __forceinline__ void bface_point(int ppt, int q, double &l0, double &l1, double &l2, double &w) {
+  if (ppt == 7) radon7_point(q, l0, l1, l2, w);
+  else dunavant4_point(q, l0, l1, l2, w);
+}
+
 }  // namespace vem

@@ -1,6 +1,8 @@
 // Face and cell geometry (paper Sec. 2: barycentres x_f, x_P, diameters
 // h_f, h_P and the face frame of the scaled face monomials) and the
 // face -> cell adjacency.  One thread per face / per cell.
+#include <algorithm>
+
 #include "handle.cuh"
 #include "geom_device.cuh"
 
@@ -190,9 +192,10 @@ __global__ void k_adjacency_fix(int64_t nf, const int *cnt, const int8_t *fbc, i
   }
 }
 
-// Boundary-face load points: Dunavant degree-4 (6 points) on every fan
-// triangle (x_f, v_i, v_{i+1}) of every Dirichlet or prescribed-flux face.
-__global__ void k_bface_points(int64_t nf, const int8_t *__restrict__ fbc,
+// Boundary-face load points: the boundary-data rule (ppt points, see
+// bface_point) on every fan triangle (x_f, v_i, v_{i+1}) of every Dirichlet
+// or prescribed-flux face.
+__global__ void k_bface_points(int64_t nf, int ppt, const int8_t *__restrict__ fbc,
                                const int64_t *__restrict__ off, const int64_t *__restrict__ fvp,
                                const int32_t *__restrict__ fv, const double *__restrict__ xyz,
                                const double *__restrict__ f_cent, double *out) {
@@ -206,9 +209,9 @@ __global__ void k_bface_points(int64_t nf, const int8_t *__restrict__ fbc,
     for (int i = 0; i < m; ++i) {
       double3 A = load3(xyz, fv[b + i]);
       double3 B = load3(xyz, fv[b + (i + 1) % m]);
-      for (int q = 0; q < 6; ++q) {
+      for (int q = 0; q < ppt; ++q) {
         double l0, l1, l2, w;
-        dunavant4_point(q, l0, l1, l2, w);
+        bface_point(ppt, q, l0, l1, l2, w);
         store3(out, o++, add3(add3(scale3(xf, l0), scale3(A, l1)), scale3(B, l2)));
       }
     }
@@ -263,8 +266,44 @@ vem_status geometry_build(vem_handle *h) {
   VEM_TRY(check_device_errors(h, "mesh geometry"));
   dfree(h, cnt);
   if (h->n_bqp > 0) {
-    count_launch(); k_bface_points<<<grid_for(h->nf, T), T, 0, s>>>(h->nf, h->fbc, h->bqp_off, h->fv_ptr, h->fv,
-                                                     h->xyz, h->f_cent, h->bqp_xyz);
+    count_launch(); k_bface_points<<<grid_for(h->nf, T), T, 0, s>>>(h->nf, h->bq_ppt, h->fbc, h->bqp_off, h->fv_ptr,
+                                                     h->fv, h->xyz, h->f_cent, h->bqp_xyz);
+    VEM_CUDA(h, cudaGetLastError());
+  }
+  return VEM_OK;
+}
+
+// Boundary points per face for the rule of ppt points per fan triangle.
+__global__ void k_bq_count(int64_t nf, int ppt, const int64_t *__restrict__ fvp, const int8_t *__restrict__ fbc,
+                           int64_t *cnt) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x)
+    cnt[f] = fbc[f] != 0 ? ppt * (fvp[f + 1] - fvp[f]) : 0;
+}
+
+// Rebuild the boundary-face points for another rule (an element change
+// between the k = 2 rule and the others): offsets, count, coordinates and a
+// zeroed data buffer of the new size.
+vem_status rebuild_bface_points(vem_handle *h, int ppt) {
+  cudaStream_t s = h->stream;
+  const int T = 128;
+  int64_t *cnt = nullptr;
+  VEM_TRY(dalloc_n(h, &cnt, (size_t)h->nf + 1));
+  count_launch(); k_bq_count<<<grid_for(h->nf, T), T, 0, s>>>(h->nf, ppt, h->fv_ptr, h->fbc, cnt);
+  VEM_CUDA(h, cudaGetLastError());
+  VEM_TRY(scan_counts(h, h->nf, cnt, h->bqp_off, &h->n_bqp));
+  dfree(h, cnt);
+  h->bq_ppt = ppt;
+  dfree(h, h->bqp_xyz);
+  dfree(h, h->gD_qp);
+  h->bqp_xyz = nullptr;
+  h->gD_qp = nullptr;
+  const size_t nq = (size_t)std::max<int64_t>(h->n_bqp, 1);
+  VEM_TRY(dalloc_n(h, &h->bqp_xyz, 3 * nq));
+  VEM_TRY(dalloc_n(h, &h->gD_qp, nq));
+  VEM_CUDA(h, cudaMemsetAsync(h->gD_qp, 0, sizeof(double) * nq, s));
+  if (h->n_bqp > 0) {
+    count_launch(); k_bface_points<<<grid_for(h->nf, T), T, 0, s>>>(h->nf, ppt, h->fbc, h->bqp_off, h->fv_ptr, h->fv,
+                                                                    h->xyz, h->f_cent, h->bqp_xyz);
     VEM_CUDA(h, cudaGetLastError());
   }
   return VEM_OK;

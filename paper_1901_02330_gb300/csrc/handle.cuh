@@ -99,6 +99,7 @@ struct vem_handle {
   double *rhs = nullptr;                         // [n] = [g; F]
   double *bt_face = nullptr;                     // [2 nf] B entries of each face's cells
   int32_t *bface = nullptr;                      // [n_bface] the boundary faces, increasing
+  int bq_ppt = 6;                                // boundary-data points per fan triangle (7 at k = 2)
   int64_t n_bface = 0;
   // several pressure DOFs per cell: the B^T entries of every flux row of A
   // (pressure column, value), kBtRow per row in row order, zero-padded
@@ -257,6 +258,8 @@ vem_status neumann_shift(vem_handle *h, double *xp);
 // Exclusive scan of cnt[n] into out[n + 1] (out[0] = 0); *total = out[n]
 // (synchronises the stream).
 vem_status scan_counts(vem_handle *h, int64_t n, const int64_t *cnt, int64_t *out, int64_t *total);
+// boundary-face points for ppt points per fan triangle (element change)
+vem_status rebuild_bface_points(vem_handle *h, int ppt);
 
 // Smoothed-aggregation AMG (amg.cu): h->amg of S, h->amg_reg of A_reg.
 // setup builds (or rebuilds) the hierarchy in *slot from the level-0

@@ -178,6 +178,41 @@ def _cubic(K=1.0):
     return p, u, f
 
 
+@pytest.mark.parametrize("mname", ["tet2", "prism2", "cvt30"])
+def test_k2_cubic_dirichlet_patch(vs, mname):
+    """Pressure data of a cubic p on the whole boundary, constant K: the
+    library's solution is the interpolant of the exact flux and the P_1
+    moments of p on triangular and Voronoi faces too -- the boundary term
+    int_f g_D m^f has degree 5, which the k = 2 boundary rule (Radon's 7
+    points per fan triangle) integrates exactly."""
+    from oracle import assemble
+    from oracle.element import interpolate
+    from oracle.monomials import eval_mono3, mono3
+    m = {"tet2": lambda: tet_mesh(2), "prism2": lambda: prism_mesh(2),
+         "cvt30": lambda: voronoi_mesh(30, seed=4, lloyd=5)}[mname]()
+    K = 1.7
+    p_ex, u_ex, f_ex = _cubic(K)
+    spec = paper_element(2)
+    s = vs.Solver(m, element=vs.VEM_ELEMENT_K2, krylov=0, precond=0, rtol=1e-12, inner_rtol=1e-13, maxit=6000)
+    try:
+        assert s.quadrature_count(vs.VEM_QP_BFACE) == 7 * sum(
+            int(m.face_vtx_ptr[f + 1] - m.face_vtx_ptr[f]) for f in np.nonzero(m.face_bc)[0])
+        s.set_coefficient(np.full(m.n_cells, K))
+        s.set_data(f_ex, p_ex)
+        u, p, st = s.solve()
+    finally:
+        s.close()
+    sys_ = assemble(m, spec, np.full(m.n_cells, 1.0 / K), keep_local=True)
+    uI = np.zeros(sys_.n_u)
+    for c, cell in enumerate(sys_.cells):
+        uI[sys_.dofmap[c]] = interpolate(cell, spec, u_ex)
+    pI = np.concatenate([(cell.qw * p_ex(cell.qp)) @ eval_mono3(mono3(1), cell.qp, cell.centroid, cell.diameter)
+                         / cell.volume for cell in sys_.cells])
+    assert st["relres"] <= 1e-12
+    np.testing.assert_allclose(u, uI, atol=1e-9 * np.abs(uI).max())
+    np.testing.assert_allclose(p, pI, atol=1e-9 * np.abs(pI).max())
+
+
 def _flux_mesh(name):
     if name == "cvt30":
         m = voronoi_mesh(30, seed=4, lloyd=5)

@@ -108,15 +108,12 @@ def test_patch_k2_dirichlet_radon_rule(mesh):
 
 @pytest.mark.parametrize("mesh", list(MESHES))
 @pytest.mark.parametrize("probname", ["quadratic", "cubic"])
-def test_patch_k2_dirichlet(mesh, probname, monkeypatch):
+def test_patch_k2_dirichlet(mesh, probname):
     """k = 2 with pressure data on the whole boundary, constant K: for p in
     P_3 (flux in [P_2]^3) u_h is the interpolant of the exact flux and p_h the
     P_1 moments of p.  The boundary term -int_f g_D m^f needs degree
-    deg(p) + 2, which the degree-4 boundary data rule covers for p in P_2
-    only; the cubic case therefore swaps in an exact face rule, so that
-    what it checks is the element alone."""
-    if probname == "cubic":
-        monkeypatch.setattr(element, "load_face_points", _exact_face_rule)
+    deg(p) + 2 = 5, which the default boundary rule of k = 2 (Radon's
+    degree 5, boundary_rule) integrates exactly on every face shape."""
     spec = paper_element(2)
     m = MESHES[mesh]()
     K = 1.7
@@ -131,15 +128,16 @@ def test_patch_k2_dirichlet(mesh, probname, monkeypatch):
 
 
 def test_k2_cubic_patch_needs_an_exact_boundary_rule(monkeypatch):
-    """The degree-4 boundary data rule misses the degree-5 part of g_D m^f
-    for a cubic g_D on triangular faces, so the cubic k = 2 patch is not
-    reproduced there; the exact face rule changes g alone (M, B and F are
-    the same matrices) and restores it."""
+    """Why k = 2 takes a degree-5 boundary rule: Dunavant's degree-4 rule
+    misses the degree-5 part of g_D m^f for a cubic g_D on triangular faces,
+    so the cubic k = 2 patch is not reproduced there; an exact face rule
+    changes g alone (M, B and F are the same matrices) and restores it."""
     spec = paper_element(2)
+    assert element.boundary_rule(spec) == "radon5" and element.boundary_rule(paper_element(1)) == "dunavant4"
     m = tet_mesh(2)
     K = 1.7
     p_ex, u_ex, f_ex = _quadratic_and_cubic(K)["cubic"]
-    sys = assemble(m, spec, np.full(m.n_cells, 1.0 / K), f=f_ex, gD=p_ex, keep_local=True)
+    sys = assemble(m, spec, np.full(m.n_cells, 1.0 / K), f=f_ex, gD=p_ex, keep_local=True, bface_rule="dunavant4")
     u, _ = solvers.solve_direct(sys)
     uI = _interp_all(sys, spec, u_ex)
     assert np.abs(u - uI).max() > 1e-6 * np.abs(uI).max()

@@ -99,10 +99,8 @@ def test_mixed_boundary_patch(spec):
 def test_mixed_boundary_patch_k2(mesh):
     """k = 2, pressure data on x = 0 and flux data elsewhere, constant K and
     p in P_3 (flux in [P_2]^3): no multiplier, u_h is the interpolant and
-    p_h the P_1 moments of p.  The Dirichlet faces at x = 0 are rectangles
-    and parallelograms: centrally symmetric, so on their fans the odd part
-    of g_D m^f about the face centroid integrates to zero and the rest has
-    degree <= 4, which the degree-4 face rule integrates exactly."""
+    p_h the P_1 moments of p.  The boundary data rule of k = 2 (degree 5)
+    integrates g_D m^f and (u.n) m^f exactly."""
     from oracle.monomials import eval_mono3, mono3
     spec = paper_element(2)
     base = hex_mesh(2) if mesh == "sheared" else prism_mesh(2)
