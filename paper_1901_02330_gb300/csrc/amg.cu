@@ -145,6 +145,7 @@ struct AmgState {
   int32_t *nstr = nullptr;  size_t c_nstr = 0;
   uint64_t *tup = nullptr;  size_t c_tup = 0;     // tuples and t1: 2 n
   int64_t *cnt = nullptr;   size_t c_cnt = 0;     // counts (n + 1)
+  int *bflag = nullptr;                           // block-row pattern check
   int64_t *scn = nullptr;   size_t c_scn = 0;     // scans (n + 1)
   int32_t *agg1 = nullptr;  size_t c_agg1 = 0;
   double *dg = nullptr;     size_t c_dg = 0;      // diagonal
@@ -1137,6 +1138,90 @@ __global__ void k_blkdiag_rows(int64_t n, int bs, const double *__restrict__ blk
   }
 }
 
+// ---- block-diagonal factors applied without a sparse product ----
+// When the bs rows of every block row of X hold the same columns in the
+// same order (the k = 2 Schur blocks, coarse operators of dense bs x m
+// prolongator blocks), L^-1 X L^-T and D^-1 X keep X's pattern and are one
+// dense pass over its blocks instead of two hashed products.  bad != 0 if
+// some block row differs; with whole_blocks, also if a row's columns do not
+// come in whole, ordered blocks of bs.
+__global__ void k_blockrow_same(DMat X, int bs, int whole_blocks, int *bad) {
+  ROWS_LOOP(i, X.rows) {
+    const int64_t i0 = (i / bs) * bs;
+    int64_t b, b0;
+    int st, st0, L, L0;
+    X.row(i, b, st, L);
+    X.row(i0, b0, st0, L0);
+    bool ok = L == L0 && (!whole_blocks || L % bs == 0);
+    for (int k = 0; ok && k < L; ++k) {
+      const int32_t c = X.col[b + (int64_t)st * k];
+      if (c != X.col[b0 + (int64_t)st0 * k]) ok = false;
+      if (whole_blocks) {
+        const int kb = k - k % bs;
+        if (c % bs != k % bs || c / bs != X.col[b + (int64_t)st * kb] / bs) ok = false;
+      }
+    }
+    if (!ok) atomicOr(bad, 1);
+  }
+}
+
+__global__ void k_row_lengths(DMat X, int64_t *cnt) {
+  ROWS_LOOP(i, X.rows) {
+    int64_t b;
+    int st, L;
+    X.row(i, b, st, L);
+    cnt[i] = L;
+  }
+}
+
+// C = L^-1 A L^-T in A's pattern (CSR rp from A's row lengths):
+// C_(I,a),(J,b) = sum_p Li_I[a][p] sum_q A_(I,p),(J,q) Li_J[b][q].
+__global__ void k_blk_congruence(DMat A, int bs, const double *__restrict__ li, const int64_t *__restrict__ rp,
+                                 int32_t *ccol, double *cval) {
+  ROWS_LOOP(i, A.rows) {
+    const int64_t I = i / bs;
+    const int a = (int)(i - I * bs);
+    int64_t bp[kMaxBs];
+    int stp[kMaxBs], L = 0;
+    for (int p = 0; p < bs; ++p) A.row(I * bs + p, bp[p], stp[p], L);
+    const double *LI = li + I * bs * bs;
+    const int64_t o = rp[i];
+    for (int k = 0; k < L; ++k) {
+      const int32_t c = A.col[bp[a] + (int64_t)stp[a] * k];
+      const int64_t J = c / bs;
+      const int bb = (int)(c - J * bs), kb = k - bb;
+      const double *LJ = li + J * bs * bs + bb * bs;
+      double sum = 0.0;
+      for (int p = 0; p < bs; ++p) {
+        double t = 0.0;
+        for (int q = 0; q <= bb; ++q) t += A.val[bp[p] + (int64_t)stp[p] * (kb + q)] * LJ[q];
+        sum += LI[a * bs + p] * t;
+      }
+      ccol[o + k] = c;
+      cval[o + k] = sum;
+    }
+  }
+}
+
+// C = D^-1 Y in Y's pattern (Y CSR, block rows of identical columns):
+// C_(I,a),k = sum_p Dinv_I[a][p] Y_(I,p),k.
+__global__ void k_blk_left(int64_t n, int bs, const double *__restrict__ dinv, const int64_t *__restrict__ yrp,
+                           const int32_t *__restrict__ ycol, const double *__restrict__ yval, int32_t *ccol,
+                           double *cval) {
+  ROWS_LOOP(i, n) {
+    const int64_t I = i / bs;
+    const int a = (int)(i - I * bs);
+    const double *DI = dinv + I * bs * bs + a * bs;
+    const int64_t o = yrp[i], L = yrp[i + 1] - o;
+    for (int64_t k = 0; k < L; ++k) {
+      double sum = 0.0;
+      for (int p = 0; p < bs; ++p) sum += DI[p] * yval[yrp[I * bs + p] + k];
+      ccol[o + k] = ycol[o + k];
+      cval[o + k] = sum;
+    }
+  }
+}
+
 // Aggregate membership as a CSR matrix (nb x nc): one entry per aggregated block.
 __global__ void k_agg_count(int64_t nb, const int32_t *__restrict__ agg, int64_t *cnt) {
   ROWS_LOOP(I, nb) cnt[I] = agg[I] >= 0 ? 1 : 0;
@@ -2070,6 +2155,19 @@ static vem_status lanczos_max(vem_handle *h, AmgState *S, const CsrBuf &C, int s
   return VEM_OK;
 }
 
+// Whether the block rows of X share their pattern (k_blockrow_same).
+static vem_status block_rows_uniform(vem_handle *h, AmgState *S, const DMat &X, int bs, bool whole, bool *ok) {
+  if (!S->bflag) VEM_TRY(dalloc_n(h, &S->bflag, 1));
+  VEM_CUDA(h, cudaMemsetAsync(S->bflag, 0, sizeof(int), h->stream));
+  count_launch();
+  k_blockrow_same<<<rows_grid(X.rows), 256, 0, h->stream>>>(X, bs, whole ? 1 : 0, S->bflag);
+  int bad = 0;
+  VEM_CUDA(h, cudaMemcpyAsync(&bad, S->bflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  VEM_CUDA(h, cudaStreamSynchronize(h->stream));
+  *ok = bad == 0;
+  return VEM_OK;
+}
+
 // Diagonal blocks, their inverses and the spectral estimate of D^-1 A for
 // level l (block size L.bs).
 static vem_status block_level_setup(vem_handle *h, AmgState *S, int l) {
@@ -2083,15 +2181,28 @@ static vem_status block_level_setup(vem_handle *h, AmgState *S, int l) {
   count_launch();
   k_blk_diag<kMaxBs><<<rows_grid(nb), 256, 0, s>>>(nb, bs, A, L.dblk, L.lblk, h->d_err);
   VEM_TRY(check_device_errors(h, "point-block AMG diagonal blocks"));
-  // C = L^-1 (A L^-T)
-  VEM_TRY(csr_fixed(h, S->bLm, n, n, n * bs));
-  VEM_TRY(csr_fixed(h, S->bLmT, n, n, n * bs));
-  count_launch();
-  k_blkdiag_rows<<<rows_grid(n), 256, 0, s>>>(n, bs, L.lblk, 0, S->bLm.rp, S->bLm.col, S->bLm.val);
-  count_launch();
-  k_blkdiag_rows<<<rows_grid(n), 256, 0, s>>>(n, bs, L.lblk, 1, S->bLmT.rp, S->bLmT.col, S->bLmT.val);
-  VEM_TRY(product(h, S, A, S->bLmT, S->bY, false));
-  VEM_TRY(product(h, S, dview(S->bLm), S->bY, S->bC, false));
+  // C = L^-1 (A L^-T): one pass over A's blocks when its block rows share
+  // their pattern, else two sparse products
+  bool uniform = false;
+  VEM_TRY(block_rows_uniform(h, S, A, bs, true, &uniform));
+  if (uniform) {
+    VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)n + 1));
+    count_launch();
+    k_row_lengths<<<rows_grid(n), 256, 0, s>>>(A, S->cnt);
+    VEM_TRY(csr_layout(h, S->bC, n, n, S->cnt));
+    count_launch();
+    k_blk_congruence<<<rows_grid(n), 256, 0, s>>>(A, bs, L.lblk, S->bC.rp, S->bC.col, S->bC.val);
+    VEM_CUDA(h, cudaGetLastError());
+  } else {
+    VEM_TRY(csr_fixed(h, S->bLm, n, n, n * bs));
+    VEM_TRY(csr_fixed(h, S->bLmT, n, n, n * bs));
+    count_launch();
+    k_blkdiag_rows<<<rows_grid(n), 256, 0, s>>>(n, bs, L.lblk, 0, S->bLm.rp, S->bLm.col, S->bLm.val);
+    count_launch();
+    k_blkdiag_rows<<<rows_grid(n), 256, 0, s>>>(n, bs, L.lblk, 1, S->bLmT.rp, S->bLmT.col, S->bLmT.val);
+    VEM_TRY(product(h, S, A, S->bLmT, S->bY, false));
+    VEM_TRY(product(h, S, dview(S->bLm), S->bY, S->bC, false));
+  }
   unsigned long long *mx = S->ctr + kMaxRounds + 1;
   VEM_CUDA(h, cudaMemsetAsync(mx, 0, sizeof(*mx), s));
   count_launch();
@@ -2183,10 +2294,22 @@ static vem_status block_coarsen(vem_handle *h, AmgState *S, int l, double theta,
   VEM_TRY(check_device_errors(h, "point-block AMG tentative prolongator"));
   // P = T - omega D^-1 (A T)
   VEM_TRY(product(h, S, A, S->bT, S->bY, l == 0));
-  VEM_TRY(csr_fixed(h, S->bLm, n, n, n * bs));
-  count_launch();
-  k_blkdiag_rows<<<rows_grid(n), 256, 0, s>>>(n, bs, L.dblk, 0, S->bLm.rp, S->bLm.col, S->bLm.val);
-  VEM_TRY(product(h, S, dview(S->bLm), S->bY, S->bZ, false));
+  bool uniform = false;
+  VEM_TRY(block_rows_uniform(h, S, dview(S->bY), bs, false, &uniform));
+  if (uniform) {
+    VEM_TRY(grow(h, S->cnt, S->c_cnt, (size_t)n + 1));
+    count_launch();
+    k_row_lengths<<<rows_grid(n), 256, 0, s>>>(dview(S->bY), S->cnt);
+    VEM_TRY(csr_layout(h, S->bZ, n, S->bY.cols, S->cnt));
+    count_launch();
+    k_blk_left<<<rows_grid(n), 256, 0, s>>>(n, bs, L.dblk, S->bY.rp, S->bY.col, S->bY.val, S->bZ.col, S->bZ.val);
+    VEM_CUDA(h, cudaGetLastError());
+  } else {
+    VEM_TRY(csr_fixed(h, S->bLm, n, n, n * bs));
+    count_launch();
+    k_blkdiag_rows<<<rows_grid(n), 256, 0, s>>>(n, bs, L.dblk, 0, S->bLm.rp, S->bLm.col, S->bLm.val);
+    VEM_TRY(product(h, S, dview(S->bLm), S->bY, S->bZ, false));
+  }
   count_launch();
   k_sub_rows<false><<<rows_grid(n), 256, 0, s>>>(n, S->bT.rp, S->bT.col, S->bT.val, S->bZ.rp, S->bZ.col, S->bZ.val,
                                                  L.omega, S->cnt, nullptr, nullptr, nullptr);
