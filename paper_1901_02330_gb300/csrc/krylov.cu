@@ -1063,8 +1063,25 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(int64_t n, const doubl
   double acc[kMD];
 #pragma unroll
   for (int t = 0; t < kMD; ++t) acc[t] = 0.0;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
-       r += (int64_t)gridDim.x * blockDim.x) {
+  // four rows of the grid-stride sequence per step, their loads issued
+  // together (a thread's sums run in the same row order as one row per step)
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; r + 3 * st < n; r += 4 * st) {
+    const double w0 = w[r], w1 = w[r + st], w2 = w[r + 2 * st], w3 = w[r + 3 * st];
+#pragma unroll
+    for (int t = 0; t < kMD; ++t) {
+      if (t < cnt) {
+        const double *Vt = V + (size_t)(i0 + t) * n;
+        const double v0 = Vt[r], v1 = Vt[r + st], v2 = Vt[r + 2 * st], v3 = Vt[r + 3 * st];
+        acc[t] += v0 * w0;
+        acc[t] += v1 * w1;
+        acc[t] += v2 * w2;
+        acc[t] += v3 * w3;
+      }
+    }
+  }
+  for (; r < n; r += st) {
     const double wr = w[r];
 #pragma unroll
     for (int t = 0; t < kMD; ++t)
@@ -1092,8 +1109,30 @@ __global__ void __launch_bounds__(kRedThreads) k_multiaxpy(int64_t n, const doub
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) cs[i] = sgn * c[i];
   __syncthreads();
   double nn = 0.0;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
-       r += (int64_t)gridDim.x * blockDim.x) {
+  // four rows of the grid-stride sequence per step (each row's sum and the
+  // norm's partial run in the same order as one row per step)
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; r + 3 * st < n; r += 4 * st) {
+    double t0 = w[r], t1 = w[r + st], t2 = w[r + 2 * st], t3 = w[r + 3 * st];
+    for (int i = 0; i < cnt; ++i) {
+      const double *Vi = V + (size_t)i * n;
+      const double c = cs[i];
+      t0 += c * Vi[r];
+      t1 += c * Vi[r + st];
+      t2 += c * Vi[r + 2 * st];
+      t3 += c * Vi[r + 3 * st];
+    }
+    w[r] = t0;
+    w[r + st] = t1;
+    w[r + 2 * st] = t2;
+    w[r + 3 * st] = t3;
+    nn += t0 * t0;
+    nn += t1 * t1;
+    nn += t2 * t2;
+    nn += t3 * t3;
+  }
+  for (; r < n; r += st) {
     double t = w[r];
     for (int i = 0; i < cnt; ++i) t += cs[i] * V[(size_t)i * n + r];
     w[r] = t;
