@@ -609,6 +609,8 @@ vem_status vem_set_options(vem_handle *h, const vem_options *opt) {
     h->arhs = nullptr;
     dfree(h, h->diagM);
     h->diagM = nullptr;
+    dfree(h, h->dinvM);
+    h->dinvM = nullptr;
     dfree(h, h->xsol);
     h->xsol = nullptr;
     dfree(h, h->cnt_buf);
@@ -980,6 +982,7 @@ vem_status vem_solve_batched(vem_handle *h, int64_t nbatch, const double *K, con
   const bool regrow = grow || op.A.stored != h->A.stored || op.S.stored != h->S.stored || op.n_u1 != h->n_u;
   VEM_TRY(batch_buf(h, &op.A.val, (size_t)nb * h->A.stored, regrow));
   VEM_TRY(batch_buf(h, &op.diagM, (size_t)nb * h->n_u, regrow));
+  VEM_TRY(batch_buf(h, &op.dinvM, (size_t)nb * h->n_u, regrow));
   VEM_TRY(batch_buf(h, &op.S.val, (size_t)nb * h->S.stored, regrow));
   VEM_TRY(batch_buf(h, &op.s_dinv, (size_t)nb * h->n_p, regrow));
   VEM_TRY(batch_buf(h, &op.S_val32, (size_t)nb * h->S.stored, regrow));

@@ -67,19 +67,21 @@ __global__ void k_rowcount(Layout L, int64_t *cnt) {
 // the 32 rows of a slice is written by one coalesced store.  Ghost rows of
 // the last slice and the padding of short rows get value 0, column 0.
 // Batched use (gridDim.y systems): values of system b at val + b * stored,
-// diag(M) at diagM + b * n_u, local matrices scaled by nu_scale[b * nc + c]
+// diag(M) at diagM + b * n_u (its reciprocal, which the preconditioners
+// multiply by, at dinvM + b * n_u), local matrices scaled by nu_scale[b * nc + c]
 // (the local matrices then hold nu = 1); col == nullptr skips the (shared)
 // column ids.  NFD / NID: face and interior DOFs per face / cell (E0: 1 / 0,
 // K1: 3 / 3), so the local-to-global map runs without divisions.
 template <int NFD, int NID>
 __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
-                       int64_t nrows_pad, int32_t *col, double *val, double *diagM,
+                       int64_t nrows_pad, int32_t *col, double *val, double *diagM, double *dinvM,
                        const double *__restrict__ nu_scale, int64_t stored) {
   const int64_t n = L.n_u + L.nc;
   const int64_t nfr = (int64_t)NFD * L.nf;
   const int64_t bb = blockIdx.y;
   val += bb * stored;
   diagM += bb * L.n_u;
+  dinvM += bb * L.n_u;
   const double *nsc = nu_scale ? nu_scale + bb * L.nc : nullptr;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows_pad;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -145,6 +147,7 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t 
         if (c1 >= 0) PUT(L.n_u + c1, L.Bloc[boff(L, c1) + l1 * NFD]);
       }
       diagM[r] = dg;
+      dinvM[r] = 1.0 / dg;
     } else if (r < L.n_u) {
       if constexpr (NID > 0) {
         const int64_t q = r - nfr;
@@ -164,6 +167,7 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t 
 #pragma unroll
         for (int l2 = 0; l2 < NID; ++l2) PUT(nfr + (int64_t)NID * c + l2, wc * Mr[NFD * k + l2]);
         diagM[r] = wc * Mr[jr];
+        dinvM[r] = 1.0 / diagM[r];
       }
     } else {
       const int64_t c = r - L.n_u;
@@ -176,11 +180,11 @@ __global__ void k_fill(Layout L, const int64_t *__restrict__ off, const int32_t 
 }
 
 static void launch_fill(cudaStream_t s, int nfd, dim3 grid, const Layout &L, const int64_t *off, const int32_t *len,
-                        int64_t npad, int32_t *col, double *val, double *diagM, const double *nu_scale,
-                        int64_t stored) {
+                        int64_t npad, int32_t *col, double *val, double *diagM, double *dinvM,
+                        const double *nu_scale, int64_t stored) {
   count_launch();
-  if (nfd == 3) k_fill<3, 3><<<grid, 256, 0, s>>>(L, off, len, npad, col, val, diagM, nu_scale, stored);
-  else k_fill<1, 0><<<grid, 256, 0, s>>>(L, off, len, npad, col, val, diagM, nu_scale, stored);
+  if (nfd == 3) k_fill<3, 3><<<grid, 256, 0, s>>>(L, off, len, npad, col, val, diagM, dinvM, nu_scale, stored);
+  else k_fill<1, 0><<<grid, 256, 0, s>>>(L, off, len, npad, col, val, diagM, dinvM, nu_scale, stored);
 }
 
 // S = B diag(M)^{-1} B^T: row P holds sum_f B_Pf^2 / M_ff on the diagonal and
@@ -242,11 +246,11 @@ __global__ void k_schur_fill(Layout L, const double *__restrict__ diagM, const i
 }
 
 // Eliminate the prescribed flux DOFs (faces with flag 2): their rows become
-// unit rows, their columns are zeroed elsewhere, diag(M) there is 1 (when
-// diagM is given).
+// unit rows, their columns are zeroed elsewhere, diag(M) and its reciprocal
+// there are 1 (when diagM / dinvM are given).
 __global__ void k_eliminate(int64_t rows, const int64_t *__restrict__ off, const int32_t *__restrict__ len,
                             const int32_t *__restrict__ col, double *val, int nfd, int64_t nf,
-                            const int8_t *__restrict__ fbc, double *diagM) {
+                            const int8_t *__restrict__ fbc, double *diagM, double *dinvM) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
        r += (int64_t)gridDim.x * blockDim.x) {
     const bool fixed_row = r < (int64_t)nfd * nf && fbc[r / nfd] == 2;
@@ -260,6 +264,7 @@ __global__ void k_eliminate(int64_t rows, const int64_t *__restrict__ off, const
       else if (fixed_col) val[p] = 0.0;
     }
     if (fixed_row && diagM) diagM[r] = 1.0;
+    if (fixed_row && dinvM) dinvM[r] = 1.0;
   }
 }
 
@@ -671,15 +676,17 @@ __global__ void k_rowcount_q(Layout L, int64_t *cnt) {
 
 template <int NFD, int NID, int NQ>
 // Batched (gridDim.y systems, as k_fill): values of system blockIdx.y at
-// val + y stored, diag(M) at diagM + y n_u, its nu at nsc + y n_c; col NULL
+// val + y stored, diag(M) at diagM + y n_u (1/diag(M) at dinvM + y n_u), its
+// nu at nsc + y n_c; col NULL
 // writes the values only (the structure is shared).
 __global__ void k_fill_q(Layout L, const int64_t *__restrict__ off, int64_t nrows_pad, int32_t *col, double *val,
-                         double *diagM, const double *__restrict__ nsc, int64_t stored) {
+                         double *diagM, double *dinvM, const double *__restrict__ nsc, int64_t stored) {
   const int64_t nfr = (int64_t)NFD * L.nf;
   const int64_t n = L.n_u + (int64_t)NQ * L.nc;
   const int64_t bb = blockIdx.y;
   val += bb * stored;
   diagM += bb * L.n_u;
+  dinvM += bb * L.n_u;
   nsc += bb * L.nc;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows_pad;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -742,6 +749,7 @@ __global__ void k_fill_q(Layout L, const int64_t *__restrict__ off, int64_t nrow
       if (c1 >= 0)
         for (int q = 0; q < NQ; ++q) PUT(L.n_u + (int64_t)NQ * c1 + q, B1[q * n1 + l1 * NFD + beta]);
       diagM[r] = dg;
+      dinvM[r] = 1.0 / dg;
     } else if (r < L.n_u) {
       const int64_t c = (r - nfr) / NID;
       const int l = (int)(r - nfr - c * NID);
@@ -759,6 +767,7 @@ __global__ void k_fill_q(Layout L, const int64_t *__restrict__ off, int64_t nrow
       for (int l2 = 0; l2 < NID; ++l2) PUT(nfr + (int64_t)NID * c + l2, wc * Mr[NFD * k + l2]);
       for (int q = 0; q < NQ; ++q) PUT(L.n_u + (int64_t)NQ * c + q, Bc[q * nl + jr]);
       diagM[r] = wc * Mr[jr];
+      dinvM[r] = 1.0 / diagM[r];
     } else {
       const int64_t c = (r - L.n_u) / NQ;
       const int q = (int)(r - L.n_u - c * NQ);
@@ -908,10 +917,11 @@ static vem_status assemble_global_q(vem_handle *h) {
   VEM_CUDA(h, cudaGetLastError());
   VEM_TRY(sell_layout(h, h->A, n, cnt));
   if (!h->diagM) VEM_TRY(dalloc_n(h, &h->diagM, (size_t)h->n_u));
+  if (!h->dinvM) VEM_TRY(dalloc_n(h, &h->dinvM, (size_t)h->n_u));
   const int64_t npad = h->A.nslices * 32;
   count_launch();
-  k_fill_q<6, 14, 4><<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, npad, h->A.col, h->A.val, h->diagM, h->nu,
-                                                     h->A.stored);
+  k_fill_q<6, 14, 4><<<grid_for(npad, T), T, 0, s>>>(L, h->A.off, npad, h->A.col, h->A.val, h->diagM, h->dinvM,
+                                                     h->nu, h->A.stored);
   VEM_CUDA(h, cudaGetLastError());
   if (h->n_flux_faces > 0) {
     // prescribed flux DOFs: values, A x_fix moved to the right-hand side,
@@ -923,7 +933,7 @@ static vem_status assemble_global_q(vem_handle *h) {
     spmv(s, h->A, h->xfix, h->rhs_corr);
     count_launch();
     k_eliminate<<<grid_for(n, T), T, 0, s>>>(n, h->A.off, h->A.len, h->A.col, h->A.val, h->nfd, h->nf, h->fbc,
-                                            h->diagM);
+                                            h->diagM, h->dinvM);
     VEM_CUDA(h, cudaGetLastError());
   }
   count_launch(); k_schur_count_q<6, 14, 4><<<grid_for(h->n_p, T), T, 0, s>>>(L, cnt);
@@ -979,9 +989,10 @@ vem_status assemble_global(vem_handle *h) {
   VEM_CUDA(h, cudaGetLastError());
   VEM_TRY(sell_layout(h, h->A, n, cnt));
   if (!h->diagM) VEM_TRY(dalloc_n(h, &h->diagM, (size_t)h->n_u));
+  if (!h->dinvM) VEM_TRY(dalloc_n(h, &h->dinvM, (size_t)h->n_u));
   const int64_t npad = h->A.nslices * 32;
-  launch_fill(s, h->nfd, dim3(grid_for(npad, T)), L, h->A.off, h->A.len, npad, h->A.col, h->A.val, h->diagM, h->nu,
-              h->A.stored);
+  launch_fill(s, h->nfd, dim3(grid_for(npad, T)), L, h->A.off, h->A.len, npad, h->A.col, h->A.val, h->diagM,
+              h->dinvM, h->nu, h->A.stored);
   VEM_CUDA(h, cudaGetLastError());
   if (h->n_flux_faces > 0) {
     // prescribed flux DOFs: values, A x_fix with the full matrix (moved to the
@@ -993,7 +1004,7 @@ vem_status assemble_global(vem_handle *h) {
     spmv(s, h->A, h->xfix, h->rhs_corr);
     count_launch();
     k_eliminate<<<grid_for(n, T), T, 0, s>>>(n, h->A.off, h->A.len, h->A.col, h->A.val, h->nfd, h->nf, h->fbc,
-                                            h->diagM);
+                                            h->diagM, h->dinvM);
     VEM_CUDA(h, cudaGetLastError());
   }
   // ---- S ----
@@ -1056,7 +1067,7 @@ vem_status assemble_reg(vem_handle *h, bool fp32) {
   if (h->n_flux_faces > 0) {
     count_launch();
     k_eliminate<<<grid_for(h->n_u, T), T, 0, s>>>(h->n_u, h->Areg.off, h->Areg.len, h->Areg.col, h->Areg.val,
-                                                 h->nfd, h->nf, h->fbc, nullptr);
+                                                 h->nfd, h->nf, h->fbc, nullptr, nullptr);
     VEM_CUDA(h, cudaGetLastError());
   }
   if (fp32) {
@@ -1285,7 +1296,7 @@ vem_status classify_cells(vem_handle *h) {
 }
 
 // Values of nb systems that share the mesh and the structure of h->A / h->S:
-// A_b, diag(M_b), S_b, 1/diag(S_b) (and FP32 copies), from local matrices
+// A_b, diag(M_b) and its reciprocal, S_b, 1/diag(S_b) (and FP32 copies), from local matrices
 // computed with nu = 1 and scaled per cell by nu_b = 1/K_b.
 vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, VemOp &op) {
   cudaStream_t s = h->stream;
@@ -1297,12 +1308,14 @@ vem_status assemble_batched_values(vem_handle *h, int nb, const double *nu_b, Ve
   if (h->nq > 1) {
     if (h->nfd != 6 || h->nid != 14 || h->nq != 4) return fail(h, VEM_ERR_UNSUPPORTED, "element layout");
     count_launch();
-    k_fill_q<6, 14, 4><<<ga, T, 0, s>>>(L, h->A.off, npad, nullptr, op.A.val, op.diagM, nu_b, h->A.stored);
+    k_fill_q<6, 14, 4><<<ga, T, 0, s>>>(L, h->A.off, npad, nullptr, op.A.val, op.diagM, op.dinvM, nu_b,
+                                        h->A.stored);
     count_launch();
     k_schur_fill_q<6, 14, 4><<<gs, T, 0, s>>>(L, op.diagM, h->S.off, spad, nullptr, op.S.val, op.s_dinv, h->d_err,
                                               h->S.stored);
   } else {
-    launch_fill(s, h->nfd, ga, L, h->A.off, h->A.len, npad, nullptr, op.A.val, op.diagM, nu_b, h->A.stored);
+    launch_fill(s, h->nfd, ga, L, h->A.off, h->A.len, npad, nullptr, op.A.val, op.diagM, op.dinvM, nu_b,
+                h->A.stored);
     count_launch();
     k_schur_fill<<<gs, T, 0, s>>>(L, op.diagM, h->S.off, spad, nullptr, op.S.val, op.s_dinv, h->d_err,
                                   h->S.stored);

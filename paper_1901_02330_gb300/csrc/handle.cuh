@@ -19,7 +19,7 @@ struct AmgState;   // smoothed-aggregation hierarchy (amg.cu)
 // the vector layout [u_0 .. u_{nb-1}; p_0 .. p_{nb-1}].
 struct VemOp {
   vem::SellMat A, S;
-  double *diagM = nullptr, *s_dinv = nullptr;
+  double *diagM = nullptr, *dinvM = nullptr, *s_dinv = nullptr;  // dinvM = 1 / diagM
   float *S_val32 = nullptr, *s_dinv32 = nullptr;
   int64_t n_u = 0, n_p = 0, n = 0;       // stacked sizes
   int64_t n_u1 = 0, n_p1 = 0;            // sizes of one system
@@ -107,6 +107,7 @@ struct vem_handle {
   double *bt_val = nullptr;
   int64_t bt_rows_n = 0;
   double *diagM = nullptr;                       // [n_u]
+  double *dinvM = nullptr;                       // [n_u] 1 / diagM
   double *s_dinv = nullptr;                      // [n_p] 1 / diag(S)
   float *S_val32 = nullptr;                      // FP32 copy of S's values
   float *s_dinv32 = nullptr;                     // FP32 copy of 1 / diag(S)

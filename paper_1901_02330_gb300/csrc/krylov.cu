@@ -866,13 +866,16 @@ __global__ void k_read_sum(const double *part, int nb, double *out) {
   if (threadIdx.x == 0) *out = v;
 }
 
-// z_u = v_u / diag(M) (first n_u entries) and the partial of v_u . z_u
-__global__ void k_diag_scale(int64_t nu, const double *__restrict__ v, const double *__restrict__ dM,
+// z_u = v_u / diag(M) (first n_u entries) and the partial of v_u . z_u.
+// dinv = 1 / diag(M), stored by the assembly: an FP64 division costs several
+// FP64-pipe instructions, a product one, and GB300's FP64 pipe (about two
+// FMAs per clock per SM) bounds a division per row below the HBM rate.
+__global__ void k_diag_scale(int64_t nu, const double *__restrict__ v, const double *__restrict__ dinv,
                              double *z, double *part) {
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double zi = v[i] / dM[i];
+    const double zi = v[i] * dinv[i];
     z[i] = zi;
     s += v[i] * zi;
   }
@@ -880,14 +883,15 @@ __global__ void k_diag_scale(int64_t nu, const double *__restrict__ v, const dou
 }
 
 // Block upper-triangular flux part: z_u = (v_u - B^T z_p) / diag(M), with
-// B^T z_p gathered per face from its (at most two) cells.
+// B^T z_p gathered per face from its (at most two) cells (dinv = 1 / diag(M),
+// as in k_diag_scale).
 // (stacked rows R = b * n_u1 + r; pressure of cell c of system b at b * n_p1 + c)
 // NFD: face DOFs per face (1 for E0, 3 for K1), a constant so the face of a
 // row is found without a division by a run-time value; kBatch: stacked
 // systems (the single system needs no division by n_u1 at all).
 template <int NFD, bool kBatch>
 __global__ void k_tri_flux(int64_t nf, int64_t n_u, int64_t n_u1, int64_t n_p1,
-                           const double *__restrict__ v, const double *__restrict__ dM,
+                           const double *__restrict__ v, const double *__restrict__ dinv,
                            const int32_t *__restrict__ f_cell, const double *__restrict__ bt,
                            const double *__restrict__ zp, double *z) {
   for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < n_u;
@@ -908,21 +912,21 @@ __global__ void k_tri_flux(int64_t nf, int64_t n_u, int64_t n_u1, int64_t n_p1,
         t -= g;
       }
     }
-    z[R] = t / dM[R];
+    z[R] = t * dinv[R];
   }
 }
 
 static void launch_tri_flux(cudaStream_t s, int nfd, bool batch, int64_t nf, int64_t n_u, int64_t n_u1,
-                            int64_t n_p1, const double *v, const double *dM, const int32_t *f_cell,
+                            int64_t n_p1, const double *v, const double *dinv, const int32_t *f_cell,
                             const double *bt, const double *zp, double *z) {
   const int g = grid_for(n_u, 256);
   count_launch();
   if (nfd == 3) {
-    if (batch) k_tri_flux<3, true><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dM, f_cell, bt, zp, z);
-    else k_tri_flux<3, false><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dM, f_cell, bt, zp, z);
+    if (batch) k_tri_flux<3, true><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dinv, f_cell, bt, zp, z);
+    else k_tri_flux<3, false><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dinv, f_cell, bt, zp, z);
   } else {
-    if (batch) k_tri_flux<1, true><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dM, f_cell, bt, zp, z);
-    else k_tri_flux<1, false><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dM, f_cell, bt, zp, z);
+    if (batch) k_tri_flux<1, true><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dinv, f_cell, bt, zp, z);
+    else k_tri_flux<1, false><<<g, 256, 0, s>>>(nf, n_u, n_u1, n_p1, v, dinv, f_cell, bt, zp, z);
   }
 }
 
@@ -934,7 +938,7 @@ static void launch_tri_flux(cudaStream_t s, int nfd, bool batch, int64_t nf, int
 template <bool kBatch>
 __global__ void k_tri_flux_rows(int64_t n_u, int64_t n_u1, int64_t n_p1, const int32_t *__restrict__ bcol,
                                 const double *__restrict__ bval, const double *__restrict__ v,
-                                const double *__restrict__ dM, const double *__restrict__ zp, double *z) {
+                                const double *__restrict__ dinv, const double *__restrict__ zp, double *z) {
   for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < n_u;
        R += (int64_t)gridDim.x * blockDim.x) {
     int64_t b = 0, r = R;
@@ -946,7 +950,7 @@ __global__ void k_tri_flux_rows(int64_t n_u, int64_t n_u1, int64_t n_p1, const i
     double t = v[R];
 #pragma unroll
     for (int k = 0; k < kBtRow; ++k) t -= bval[k * n_u1 + r] * zb[bcol[k * n_u1 + r]];
-    z[R] = t / dM[R];
+    z[R] = t * dinv[R];
   }
 }
 
@@ -1265,7 +1269,7 @@ static vem_status precond(vem_handle *h, const VemOp &op, const double *v, doubl
   }
   if (h->opt.precond == VEM_PREC_BLOCK_DIAG) {
     count_launch();
-    k_diag_scale<<<nblocks_vec(nu), kRedThreads, 0, s>>>(nu, v, op.diagM, z,
+    k_diag_scale<<<nblocks_vec(nu), kRedThreads, 0, s>>>(nu, v, op.dinvM, z,
                                                          minres_partials ? slot(h->part, P_G2U) : nullptr);
     VEM_TRY(pcg_solve(h, op, v + nu, z + nu, wk, &it));
   } else {
@@ -1275,12 +1279,12 @@ static vem_status precond(vem_handle *h, const VemOp &op, const double *v, doubl
       count_launch();
       if (op.nbatch > 1)
         k_tri_flux_rows<true><<<grid_for(nu, 256), 256, 0, s>>>(nu, op.n_u1, op.n_p1, h->bt_col, h->bt_val, v,
-                                                                 op.diagM, z + nu, z);
+                                                                 op.dinvM, z + nu, z);
       else
-        k_tri_flux_rows<false><<<grid_for(nu, 256), 256, 0, s>>>(nu, nu, 0, h->bt_col, h->bt_val, v, op.diagM,
+        k_tri_flux_rows<false><<<grid_for(nu, 256), 256, 0, s>>>(nu, nu, 0, h->bt_col, h->bt_val, v, op.dinvM,
                                                                   z + nu, z);
     } else {
-      launch_tri_flux(s, h->nfd, op.nbatch > 1, h->nf, nu, op.n_u1, op.n_p1, v, op.diagM, h->f_cell, h->bt_face,
+      launch_tri_flux(s, h->nfd, op.nbatch > 1, h->nf, nu, op.n_u1, op.n_p1, v, op.dinvM, h->f_cell, h->bt_face,
                       z + nu, z);
     }
   }
@@ -2155,16 +2159,16 @@ static vem_status sys_precond(vem_handle *h, const VemOp &op, const double *v, d
   *inner += it;
   if (h->opt.precond == VEM_PREC_BLOCK_DIAG) {
     count_launch();
-    k_diag_scale<<<nblocks_vec(nu), kRedThreads, 0, s>>>(nu, v, op.diagM, z, nullptr);
+    k_diag_scale<<<nblocks_vec(nu), kRedThreads, 0, s>>>(nu, v, op.dinvM, z, nullptr);
   } else {
     count_launch();
     k_negate<<<grid_for(np, 256), 256, 0, s>>>(np, z + nu);
     if (h->nq > 1) {
       count_launch();
       k_tri_flux_rows<true><<<grid_for(nu, 256), 256, 0, s>>>(nu, op.n_u1, op.n_p1, h->bt_col, h->bt_val, v,
-                                                               op.diagM, z + nu, z);
+                                                               op.dinvM, z + nu, z);
     } else {
-      launch_tri_flux(s, h->nfd, true, h->nf, nu, op.n_u1, op.n_p1, v, op.diagM, h->f_cell, h->bt_face, z + nu, z);
+      launch_tri_flux(s, h->nfd, true, h->nf, nu, op.n_u1, op.n_p1, v, op.dinvM, h->f_cell, h->bt_face, z + nu, z);
     }
   }
   VEM_CUDA(h, cudaGetLastError());
@@ -2309,6 +2313,7 @@ VemOp single_op(vem_handle *h) {
   op.A = h->A;
   op.S = h->S;
   op.diagM = h->diagM;
+  op.dinvM = h->dinvM;
   op.s_dinv = h->s_dinv;
   op.S_val32 = h->S_val32;
   op.s_dinv32 = h->s_dinv32;
